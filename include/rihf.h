@@ -1,0 +1,165 @@
+/*
+ * rihf.h -- C ABI of librihf.so: RI-HF energies and analytic nuclear gradients on
+ * one NVIDIA GB300 (sm_103a), following Stocks, Palethorpe and Barca,
+ * "Multi-GPU RI-HF Energies and Analytic Gradients -- Towards High Throughput
+ * Ab Initio Molecular Dynamics" (the paper).
+ *
+ * Conventions for every entry point
+ *   - Units: bohr, hartree, hartree/bohr.  Arrays are row-major doubles unless
+ *     stated otherwise.
+ *   - Host pointers are read during the call and never retained; output buffers
+ *     are caller-owned host memory of the documented size.
+ *   - The context owns all of its device memory (allocated in rihf_setup, freed
+ *     in rihf_destroy) and is not thread-safe.
+ *   - Return value: RIHF_OK (0) or a negative error code; rihf_strerror() gives
+ *     a message and rihf_last_error() the detail of the last failure.
+ *   - Basis functions: each shell is contracted over primitive Gaussians whose
+ *     coefficients refer to normalised primitives; the library normalises the
+ *     primitives and the contracted functions.  pure = 1 uses real solid
+ *     harmonics ordered m = -l..l, each normalised to one; pure = 0 uses
+ *     Cartesian functions ordered lx = l..0, ly = l-lx..0, each normalised to one.
+ *   - AO order: shells in the order given, functions within a shell as above.
+ *     Auxiliary functions likewise.
+ *   - Molecular orbital coefficients C are N x N with C[mu * N + k] the
+ *     coefficient of AO mu in orbital k, orbitals in ascending energy.
+ *   - Limits: primary l <= 3, auxiliary l <= 4, contraction length <= 16.
+ */
+#ifndef RIHF_H
+#define RIHF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RIHF_OK = 0,
+  RIHF_ERR_INVALID_ARG = -1,
+  RIHF_ERR_OOM = -2,
+  RIHF_ERR_CUDA = -3,
+  RIHF_ERR_NOT_CONVERGED = -4,
+  RIHF_ERR_TIMEOUT = -5,
+  RIHF_ERR_NOT_POSITIVE_DEFINITE = -6,
+  RIHF_ERR_STATE = -7
+};
+
+enum { RIHF_PRECISION_FP64 = 0, RIHF_PRECISION_MIXED = 1 };
+
+typedef struct rihf_ctx rihf_ctx;
+
+/* One contracted shell on atom `atom` with angular momentum l and nprim
+   primitives (exps[k], coefs[k]).  Pointers are read during rihf_setup only. */
+typedef struct {
+  int atom;
+  int l;
+  int nprim;
+  const double* exps;
+  const double* coefs;
+} rihf_shell;
+
+typedef struct {
+  int precision;        /* RIHF_PRECISION_FP64 or RIHF_PRECISION_MIXED                     */
+  int pure;             /* 1: spherical functions, 0: Cartesian                             */
+  double schwarz_tau;   /* drop primary shell pairs with max (ab|ab) <= tau (paper: 1e-10) */
+  double lindep_tau;    /* drop overlap eigenvalues below this (canonical orthogonalisation) */
+  double conv_e;        /* converged when |E_k - E_{k-1}| < conv_e ...                    */
+  double conv_diis;     /* ... and max |X^T (FDS - SDF) X| < conv_diis                    */
+  int max_iter;         /* SCF iteration cap (RIHF_ERR_NOT_CONVERGED when reached)         */
+  int diis_size;        /* Pulay DIIS subspace size, 2..16                                 */
+  int mixed_fp64_iters; /* mixed precision: trailing iterations rebuilt in FP64            */
+  int device;           /* CUDA device ordinal                                             */
+} rihf_options;
+
+/* Fills *opt with the defaults: FP64, spherical, schwarz_tau 1e-14, lindep_tau
+   1e-8, conv_e 1e-10, conv_diis 1e-9, max_iter 100, diis_size 8,
+   mixed_fp64_iters 2, device 0. */
+void rihf_default_options(rihf_options* opt);
+
+/*
+ * Builds a context for one molecule: copies the geometry and basis sets to the
+ * device and evaluates the geometry-dependent quantities of Alg. 1 (before its
+ * SCF loop): one-electron h = T + V and S, the metric A_PQ = (P|Q) (Sec. 2.2),
+ * its Cholesky factor A = L L^T and L^{-1} (the paper's A^L, read as L^{-T}),
+ * the Schwarz-screened 3-centre integrals (mu nu|P) (Sec. 3.1.1) and the fitted
+ * B^P_{mu nu} = sum_Q (L^{-1})_{PQ} (mu nu|Q) (Eq. biap), stored unpacked as
+ * Naux x N x N.
+ *   natoms, Z[natoms], xyz[natoms*3]: nuclei (bohr).
+ *   prim[nprim_shells], aux[naux_shells]: shells (atom indices into Z).
+ *   nelec: electron count (even; closed shell).
+ *   opt: options or NULL for the defaults.
+ * Errors: INVALID_ARG (sizes, l limits, odd nelec), OOM, CUDA,
+ * NOT_POSITIVE_DEFINITE (metric or overlap).
+ */
+int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, const rihf_shell* prim,
+               int naux_shells, const rihf_shell* aux, int nelec, const rihf_options* opt, rihf_ctx** out);
+
+/* Moves the nuclei to xyz[natoms*3] (same atoms and basis) and recomputes every
+   geometry-dependent quantity listed for rihf_setup.  Converged orbitals of the
+   previous geometry are kept as the default guess of the next rihf_scf. */
+int rihf_update_geometry(rihf_ctx* ctx, const double* xyz);
+
+/*
+ * Closed-shell RI-HF SCF (Roothaan FC = SC eps, Sec. 2.2 and Alg. 1): each
+ * iteration forms D = 2 C_occ C_occ^T, RI-J (Eq. j_ri) and RI-K (Eqs. k_ri_2,
+ * tp), F = h + J + K (Eq. fock_split), E = 1/2 Tr D(h+F) + V_nn, the DIIS
+ * error X^T(FDS - SDF)X, Pulay extrapolation and diagonalisation.
+ *   guess: 0 core Hamiltonian, 1 C_guess (N*N, columns 0..nocc-1 used),
+ *          2 the context's previous converged orbitals (falls back to 0).
+ *   energy (1), D (N*N), C (N*N), eps (N), iters (1): outputs; any may be NULL.
+ * Returns NOT_CONVERGED (outputs filled from the last iterate) after max_iter.
+ */
+int rihf_scf(rihf_ctx* ctx, int guess, const double* C_guess, double* energy, double* D, double* C, double* eps,
+             int* iters);
+
+/*
+ * Analytic RI-HF gradient (Eq. rihf_gradient, Alg. 2) at the last converged
+ * rihf_scf of this context:
+ *   dE/dR = sum D h^xi - sum W S^xi + sum_P Y^P (mu nu|P)^xi - 1/2 sum Z_PQ (P|Q)^xi + V_nn^xi
+ * with h^xi including the nuclear-attraction operator derivative.  The
+ * derivative integrals are evaluated and contracted on the fly, never stored.
+ *   grad: natoms*3 output, dE/dR (forces are its negative).
+ * Errors: STATE if no converged SCF is available.
+ */
+int rihf_gradient(rihf_ctx* ctx, double* grad);
+
+/* Sizes of the context: primary functions N, auxiliary functions Naux,
+   occupied orbitals nocc, atoms natoms.  Any pointer may be NULL. */
+int rihf_query(rihf_ctx* ctx, int* N, int* Naux, int* nocc, int* natoms);
+
+/* Intermediates for element-wise checks, copied to host buffer out (doubles):
+     RIHF_MAT_S, RIHF_MAT_H, RIHF_MAT_J, RIHF_MAT_K, RIHF_MAT_F, RIHF_MAT_D: N x N
+     RIHF_MAT_A, RIHF_MAT_LINV: Naux x Naux
+     RIHF_MAT_T3: (mu nu|P) as Naux x N x N;  RIHF_MAT_B: B^P as Naux x N x N
+     RIHF_MAT_GRAD_PARTS: 5 x natoms x 3 (one-electron, overlap, 3-centre,
+                          2-centre, nuclear-repulsion terms of Eq. rihf_gradient)
+   J, K, F, D refer to the last Fock build. */
+enum {
+  RIHF_MAT_S = 0, RIHF_MAT_H = 1, RIHF_MAT_A = 2, RIHF_MAT_LINV = 3, RIHF_MAT_T3 = 4, RIHF_MAT_B = 5,
+  RIHF_MAT_J = 6, RIHF_MAT_K = 7, RIHF_MAT_F = 8, RIHF_MAT_D = 9, RIHF_MAT_GRAD_PARTS = 10
+};
+int rihf_get_matrix(rihf_ctx* ctx, int which, double* out);
+
+/* Number of significant primary shell pairs kept by the Schwarz screen and
+   the total number of shell pairs (a >= b). */
+int rihf_screening_stats(rihf_ctx* ctx, int* kept, int* total);
+
+/* Per-phase device time of the last rihf_scf / rihf_gradient in milliseconds,
+   measured with CUDA events: [0] integrals+fit, [1] SCF Fock builds,
+   [2] SCF diagonalisation/DIIS, [3] gradient; and the number of kernels the
+   library launched since the context was created ([4], as a double). */
+int rihf_timings(rihf_ctx* ctx, double* out5);
+
+/* The library's symmetric eigensolver (the diagonalisation step of Alg. 1) on
+   one n x n host matrix A (row-major, symmetric): eigenvalues W (n, ascending)
+   and eigenvectors V (n x n, column k = eigenvector k).  FP32 parallel Jacobi
+   followed by FP64 Ogita-Aishima refinement, on device `device`.  Allocates
+   and frees its own device workspace.  Errors: INVALID_ARG, OOM, CUDA. */
+int rihf_eigh(int n, const double* A, double* W, double* V, int device);
+
+const char* rihf_strerror(int code);
+const char* rihf_last_error(void);
+void rihf_destroy(rihf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIHF_H */

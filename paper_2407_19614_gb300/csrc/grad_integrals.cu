@@ -1,0 +1,519 @@
+// Fused derivative-integral contractions for the RI-HF gradient (Eq. rihf_gradient,
+// Alg. 2): the derivative integrals (mu nu|P)^xi, (P|Q)^xi, S^xi, T^xi, V^xi are
+// evaluated warp-cooperatively in shared memory and contracted immediately with
+// Y, Z, D or W; only the per-atom 3-vectors leave the SM.
+//
+// Derivatives use d/dA_x [x_A^i e^{-a r_A^2}] = 2a x_A^{i+1}(..) - i x_A^{i-1}(..):
+// the exponent-weighted accumulators accA (2 alpha), accB (2 beta) and the plain
+// acc0 feed four horizontal recurrences, (la+1, lb), (la-1, lb), (la, lb+1),
+// (la, lb-1).  The auxiliary (or nuclear) centre follows from translational
+// invariance, d/dC = -(d/dA + d/dB).
+#include <cmath>
+
+#include "integrals.cuh"
+#include "os_hgp.cuh"
+
+namespace rihf {
+
+__device__ inline int warp_next(int* counter, int lane) {
+  int t = 0;
+  if (lane == 0) t = atomicAdd(counter, 1);
+  return __shfl_sync(0xffffffffu, t, 0);
+}
+
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Shared-memory plan of the derivative kernels.
+struct DerivPlan {
+  int emin, emax, L;
+  int fm, vrr, etr, acc0, accA, accB, ycart, t1, t2, hrr, half, total;
+  __device__ __host__ DerivPlan(int la, int lb, int lc) {
+    emin = la > 0 ? la - 1 : 0;
+    emax = la + lb + 1;
+    L = emax + lc;
+    EtrShape sh{lc, emin, emax};
+    int accsz = acc_size(emin, emax, lc);
+    int big = ncart(la + 1) * ncart(lb + 1) * ncart(lc);
+    fm = 0;
+    vrr = 24;
+    etr = vrr + vrr_size(L);
+    acc0 = etr + (lc > 0 ? sh.total() : 0);
+    accA = acc0 + accsz;
+    accB = accA + accsz;
+    ycart = accB + accsz;
+    t1 = ycart + ncart(la) * ncart(lb) * ncart(lc);
+    t2 = t1 + big;
+    hrr = t2 + big;
+    half = 0;
+    int cand[4] = {hrr_scratch(la + 1, lb, lc, emax), la > 0 ? hrr_scratch(la - 1, lb, lc, emax) : 0,
+                   hrr_scratch(la, lb + 1, lc, emax), lb > 0 ? hrr_scratch(la, lb - 1, lc, emax) : 0};
+    for (int i = 0; i < 4; ++i)
+      if (cand[i] / 2 > half) half = cand[i] / 2;
+    if (big > half) half = big;
+    total = hrr + 2 * half;
+  }
+};
+
+// Ycart[ka][kb][kc] = sum tra[sa][ka] trb[sb][kb] trc[sc][kc] Y(sa, sb, sc), with
+// Y(sa, sb, sc) = src[(sc*sP) + (sa*sM) + sb*sN] (strides in doubles).
+__device__ inline void warp_back_transform(const double* src, long long sP, long long sM, long long sN, int la,
+                                           int lb, int lc, const double* tra, const double* trb, const double* trc,
+                                           int nfa, int nfb, int nfc, double* t1, double* t2, double* out,
+                                           int lane) {
+  const int na = ncart(la), nb = ncart(lb), nc = ncart(lc);
+  // t1[sa][sb][kc] = sum_sc trc[sc][kc] Y
+  for (int idx = lane; idx < nfa * nfb * nc; idx += 32) {
+    int kc = idx % nc, r = idx / nc;
+    int sb = r % nfb, sa = r / nfb;
+    double v = 0.0;
+    for (int sc = 0; sc < nfc; ++sc) v += trc[sc * kTrStride + kc] * src[sc * sP + sa * sM + sb * sN];
+    t1[idx] = v;
+  }
+  __syncwarp();
+  // t2[sa][kb][kc]
+  for (int idx = lane; idx < nfa * nb * nc; idx += 32) {
+    int kc = idx % nc, r = idx / nc;
+    int kb = r % nb, sa = r / nb;
+    double v = 0.0;
+    for (int sb = 0; sb < nfb; ++sb) v += trb[sb * kTrStride + kb] * t1[(sa * nfb + sb) * nc + kc];
+    t2[idx] = v;
+  }
+  __syncwarp();
+  // out[ka][kb][kc]
+  for (int idx = lane; idx < na * nb * nc; idx += 32) {
+    int rest = idx % (nb * nc), ka = idx / (nb * nc);
+    double v = 0.0;
+    for (int sa = 0; sa < nfa; ++sa) v += tra[sa * kTrStride + ka] * t2[sa * nb * nc + rest];
+    out[idx] = v;
+  }
+  __syncwarp();
+}
+
+// g[0..2] += sum_{ka,kb,kc} Y[ka][kb][kc] * (d/dA_x), g[3..5] += ... (d/dB_x) from
+// the four shifted HRR products of one shell triple.  Returns per-lane partials.
+__device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, int la, int lb, int lc,
+                                           const double* AB, int lane, double g[6]) {
+  const int na = ncart(la), nb = ncart(lb), nc = ncart(lc);
+  const double* Y = smem + pl.ycart;
+  const double* acc0 = smem + pl.acc0;
+  const double* accA = smem + pl.accA;
+  const double* accB = smem + pl.accB;
+  double* scr = smem + pl.hrr;
+  for (int i = 0; i < 6; ++i) g[i] = 0.0;
+  // (la+1, lb) from accA
+  {
+    const double* I = warp_hrr(accA, pl.emin, la + 1, lb, lc, AB, scr, pl.half, lane);
+    int nap = ncart(la + 1);
+    for (int idx = lane; idx < na * nb * nc; idx += 32) {
+      int kc = idx % nc, r = idx / nc, kb = r % nb, ka = r / nb;
+      int ax, ay, az;
+      cart_decode(la, ka, ax, ay, az);
+      double y = Y[idx];
+      int kx = cart_index(la + 1, ax + 1, ay), ky = cart_index(la + 1, ax, ay + 1), kz = cart_index(la + 1, ax, ay);
+      g[0] += y * I[(kx * nb + kb) * nc + kc];
+      g[1] += y * I[(ky * nb + kb) * nc + kc];
+      g[2] += y * I[(kz * nb + kb) * nc + kc];
+      (void)nap;
+    }
+    __syncwarp();
+  }
+  if (la > 0) {
+    const double* I = warp_hrr(acc0, pl.emin, la - 1, lb, lc, AB, scr, pl.half, lane);
+    for (int idx = lane; idx < na * nb * nc; idx += 32) {
+      int kc = idx % nc, r = idx / nc, kb = r % nb, ka = r / nb;
+      int ax, ay, az;
+      cart_decode(la, ka, ax, ay, az);
+      double y = Y[idx];
+      if (ax > 0) g[0] -= ax * y * I[(cart_index(la - 1, ax - 1, ay) * nb + kb) * nc + kc];
+      if (ay > 0) g[1] -= ay * y * I[(cart_index(la - 1, ax, ay - 1) * nb + kb) * nc + kc];
+      if (az > 0) g[2] -= az * y * I[(cart_index(la - 1, ax, ay) * nb + kb) * nc + kc];
+    }
+    __syncwarp();
+  }
+  {
+    const double* I = warp_hrr(accB, pl.emin, la, lb + 1, lc, AB, scr, pl.half, lane);
+    int nbp = ncart(lb + 1);
+    for (int idx = lane; idx < na * nb * nc; idx += 32) {
+      int kc = idx % nc, r = idx / nc, kb = r % nb, ka = r / nb;
+      int bx, by, bz;
+      cart_decode(lb, kb, bx, by, bz);
+      double y = Y[idx];
+      g[3] += y * I[(ka * nbp + cart_index(lb + 1, bx + 1, by)) * nc + kc];
+      g[4] += y * I[(ka * nbp + cart_index(lb + 1, bx, by + 1)) * nc + kc];
+      g[5] += y * I[(ka * nbp + cart_index(lb + 1, bx, by)) * nc + kc];
+    }
+    __syncwarp();
+  }
+  if (lb > 0) {
+    const double* I = warp_hrr(acc0, pl.emin, la, lb - 1, lc, AB, scr, pl.half, lane);
+    int nbm = ncart(lb - 1);
+    for (int idx = lane; idx < na * nb * nc; idx += 32) {
+      int kc = idx % nc, r = idx / nc, kb = r % nb, ka = r / nb;
+      int bx, by, bz;
+      cart_decode(lb, kb, bx, by, bz);
+      double y = Y[idx];
+      if (bx > 0) g[3] -= bx * y * I[(ka * nbm + cart_index(lb - 1, bx - 1, by)) * nc + kc];
+      if (by > 0) g[4] -= by * y * I[(ka * nbm + cart_index(lb - 1, bx, by - 1)) * nc + kc];
+      if (bz > 0) g[5] -= bz * y * I[(ka * nbm + cart_index(lb - 1, bx, by)) * nc + kc];
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------ 3-centre
+
+__global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells aux,
+                                                       const ShellPair* __restrict__ pairs, int npairs,
+                                                       const double* __restrict__ boys, int* counter,
+                                                       const double* __restrict__ Y, double* grad) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x;
+  const long long ntask = (long long)npairs * aux.nshell;
+  const int N = prim.nfunc;
+  const long long N2 = (long long)N * N;
+  for (;;) {
+    long long task = warp_next(counter, lane);
+    if (task >= ntask) break;
+    int ip = (int)(task % npairs), sc = (int)(task / npairs);
+    int sa = pairs[ip].a, sb = pairs[ip].b;
+    if (prim.l[sa] < prim.l[sb]) { int t = sa; sa = sb; sb = t; }   // Y is symmetric in mu, nu
+    int ata = prim.atom[sa], atb = prim.atom[sb], atc = aux.atom[sc];
+    if (ata == atb && atb == atc) continue;   // one-centre: derivative sums to zero
+    int la = prim.l[sa], lb = prim.l[sb], lc = aux.l[sc];
+    DerivPlan pl(la, lb, lc);
+    double* Fm = smem + pl.fm;
+    double* vrr = smem + pl.vrr;
+    double* etr = smem + pl.etr;
+    int accsz = acc_size(pl.emin, pl.emax, lc);
+    for (int i = lane; i < 3 * accsz; i += 32) smem[pl.acc0 + i] = 0.0;
+    const double* A = prim.xyz + 3 * sa;
+    const double* B = prim.xyz + 3 * sb;
+    const double* C = aux.xyz + 3 * sc;
+    EtrShape sh{lc, pl.emin, pl.emax};
+    for (int pa = 0; pa < prim.nprim[sa]; ++pa)
+      for (int pb = 0; pb < prim.nprim[sb]; ++pb)
+        for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
+          double al = prim.exps[prim.pstart[sa] + pa], be = prim.exps[prim.pstart[sb] + pb];
+          double ga = aux.exps[aux.pstart[sc] + pc];
+          double w = prim.coefs[prim.pstart[sa] + pa] * prim.coefs[prim.pstart[sb] + pb] *
+                     aux.coefs[aux.pstart[sc] + pc];
+          Prim3 t = make_prim3(al, A, be, B, ga, C);
+          if (lane <= pl.L) Fm[lane] = boys_eval(lane, t.T, boys);
+          __syncwarp();
+          warp_vrr(vrr, pl.L, t, Fm, lane);
+          warp_etr(vrr, pl.L, etr, sh, t, lane);
+          warp_acc_level(vrr, pl.L, etr, sh, w, smem + pl.acc0, lane);
+          warp_acc_level(vrr, pl.L, etr, sh, 2.0 * al * w, smem + pl.accA, lane);
+          warp_acc_level(vrr, pl.L, etr, sh, 2.0 * be * w, smem + pl.accB, lane);
+        }
+    // Y block -> Cartesian
+    int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
+    const double* src = Y + (long long)aux.ao[sc] * N2 + (long long)prim.ao[sa] * N + prim.ao[sb];
+    warp_back_transform(src, N2, N, 1, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
+                        prim.tr + lb * kTrStride * kTrStride, aux.tr + lc * kTrStride * kTrStride, nfa, nfb, nfc,
+                        smem + pl.t1, smem + pl.t2, smem + pl.ycart, lane);
+    double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
+    double g[6];
+    warp_deriv_contract(pl, smem, la, lb, lc, AB, lane, g);
+    double wgt = (sa == sb) ? 1.0 : 2.0;
+    for (int i = 0; i < 6; ++i) g[i] = warp_sum(g[i]) * wgt;
+    if (lane == 0) {
+      for (int x = 0; x < 3; ++x) {
+        atomicAdd(grad + 3 * ata + x, g[x]);
+        atomicAdd(grad + 3 * atb + x, g[3 + x]);
+        atomicAdd(grad + 3 * atc + x, -(g[x] + g[3 + x]));
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------ 2-centre
+
+__global__ void __launch_bounds__(32) grad_eri2_kernel(DevShells aux, const double* __restrict__ boys, int* counter,
+                                                       const double* __restrict__ Z, double* grad) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x;
+  const int ns = aux.nshell;
+  const long long ntask = (long long)ns * (ns + 1) / 2;
+  const int NA = aux.nfunc;
+  for (;;) {
+    long long task = warp_next(counter, lane);
+    if (task >= ntask) break;
+    int sa = (int)((sqrt(8.0 * (double)task + 1.0) - 1.0) * 0.5);
+    while ((long long)sa * (sa + 1) / 2 > task) --sa;
+    while ((long long)(sa + 1) * (sa + 2) / 2 <= task) ++sa;
+    int sc = (int)(task - (long long)sa * (sa + 1) / 2);
+    int ata = aux.atom[sa], atc = aux.atom[sc];
+    if (ata == atc) continue;
+    int la = aux.l[sa], lc = aux.l[sc];
+    DerivPlan pl(la, 0, lc);
+    double* Fm = smem + pl.fm;
+    double* vrr = smem + pl.vrr;
+    double* etr = smem + pl.etr;
+    int accsz = acc_size(pl.emin, pl.emax, lc);
+    for (int i = lane; i < 3 * accsz; i += 32) smem[pl.acc0 + i] = 0.0;
+    const double* PA = aux.xyz + 3 * sa;
+    const double* PC = aux.xyz + 3 * sc;
+    EtrShape sh{lc, pl.emin, pl.emax};
+    for (int pa = 0; pa < aux.nprim[sa]; ++pa)
+      for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
+        double al = aux.exps[aux.pstart[sa] + pa], ga = aux.exps[aux.pstart[sc] + pc];
+        double w = aux.coefs[aux.pstart[sa] + pa] * aux.coefs[aux.pstart[sc] + pc];
+        Prim3 t = make_prim3(al, PA, 0.0, PA, ga, PC);
+        if (lane <= pl.L) Fm[lane] = boys_eval(lane, t.T, boys);
+        __syncwarp();
+        warp_vrr(vrr, pl.L, t, Fm, lane);
+        warp_etr(vrr, pl.L, etr, sh, t, lane);
+        warp_acc_level(vrr, pl.L, etr, sh, w, smem + pl.acc0, lane);
+        warp_acc_level(vrr, pl.L, etr, sh, 2.0 * al * w, smem + pl.accA, lane);
+      }
+    // Z block (P in sa, Q in sc) -> Cartesian with a unit s "b" function
+    int nfa = aux.nf[la], nfc = aux.nf[lc];
+    const double* src = Z + (long long)aux.ao[sa] * NA + aux.ao[sc];
+    // layout Y(sa, sb=0, sc) = src[sa*NA + sc]
+    __shared__ double one_tr[kTrStride];
+    if (lane < kTrStride) one_tr[lane] = (lane == 0) ? 1.0 : 0.0;
+    __syncwarp();
+    warp_back_transform(src, 1, NA, 0, la, 0, lc, aux.tr + la * kTrStride * kTrStride, one_tr,
+                        aux.tr + lc * kTrStride * kTrStride, nfa, 1, nfc, smem + pl.t1, smem + pl.t2,
+                        smem + pl.ycart, lane);
+    double AB[3] = {0.0, 0.0, 0.0};
+    double g[6];
+    // only the A-side derivative is needed (lb = 0, beta = 0): zero accB so the
+    // (la, lb+1) term vanishes
+    for (int i = lane; i < accsz; i += 32) smem[pl.accB + i] = 0.0;
+    __syncwarp();
+    warp_deriv_contract(pl, smem, la, 0, lc, AB, lane, g);
+    // E term -1/2 sum_PQ Z_PQ (P|Q)^xi over ordered pairs: off-diagonal shell
+    // pairs appear twice.
+    double wgt = (sa == sc) ? -0.5 : -1.0;
+    for (int i = 0; i < 3; ++i) g[i] = warp_sum(g[i]) * wgt;
+    if (lane == 0) {
+      for (int x = 0; x < 3; ++x) {
+        atomicAdd(grad + 3 * ata + x, g[x]);
+        atomicAdd(grad + 3 * atc + x, -g[x]);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------ one-electron
+
+__device__ inline void os_overlap_1d_g(double a, double b, double XA, double XB, int imax, int jmax, double* s,
+                                       int ld) {
+  double p = a + b, P = (a * XA + b * XB) / p, PA = P - XA, PB = P - XB, X = XA - XB;
+  double inv2p = 0.5 / p;
+  s[0] = sqrt(3.14159265358979323846 / p) * exp(-a * b / p * X * X);
+  for (int i = 1; i <= imax; ++i) {
+    double v = PA * s[(i - 1) * ld];
+    if (i >= 2) v += (i - 1) * inv2p * s[(i - 2) * ld];
+    s[i * ld] = v;
+  }
+  for (int j = 1; j <= jmax; ++j)
+    for (int i = 0; i <= imax; ++i) {
+      double v = PB * s[i * ld + j - 1];
+      if (j >= 2) v += (j - 1) * inv2p * s[i * ld + j - 2];
+      if (i >= 1) v += i * inv2p * s[(i - 1) * ld + j - 1];
+      s[i * ld + j] = v;
+    }
+}
+
+// 1D overlap and kinetic factors for exponents (i, j) from the table s (ld 8).
+__device__ inline double k1d(const double* s, int i, int j, double b) {
+  if (i < 0) return 0.0;
+  double v = 4.0 * b * b * s[i * 8 + j + 2] - 2.0 * b * (2 * j + 1) * s[i * 8 + j];
+  if (j >= 2) v += j * (j - 1) * s[i * 8 + j - 2];
+  return v;
+}
+__device__ inline double s1(const double* s, int i, int j) { return (i < 0 || j < 0) ? 0.0 : s[i * 8 + j]; }
+
+// Task = primary shell pair (a >= b) x (1 + natoms): slot 0 handles overlap and
+// kinetic, slot 1 + C the attraction of nucleus C.
+__global__ void __launch_bounds__(32) grad_one_electron_kernel(DevShells prim, int natoms, const int* __restrict__ Z,
+                                                               const double* __restrict__ axyz,
+                                                               const double* __restrict__ boys, int* counter,
+                                                               const double* __restrict__ D,
+                                                               const double* __restrict__ W, double* grad_one,
+                                                               double* grad_ovl) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x;
+  const int ns = prim.nshell;
+  const long long npair = (long long)ns * (ns + 1) / 2;
+  const long long ntask = npair * (1 + natoms);
+  const int N = prim.nfunc;
+  for (;;) {
+    long long task = warp_next(counter, lane);
+    if (task >= ntask) break;
+    long long pidx = task % npair;
+    int slot = (int)(task / npair);
+    int sa = (int)((sqrt(8.0 * (double)pidx + 1.0) - 1.0) * 0.5);
+    while ((long long)sa * (sa + 1) / 2 > pidx) --sa;
+    while ((long long)(sa + 1) * (sa + 2) / 2 <= pidx) ++sa;
+    int sb = (int)(pidx - (long long)sa * (sa + 1) / 2);
+    int la = prim.l[sa], lb = prim.l[sb];
+    int ata = prim.atom[sa], atb = prim.atom[sb];
+    const double* A = prim.xyz + 3 * sa;
+    const double* B = prim.xyz + 3 * sb;
+    int nfa = prim.nf[la], nfb = prim.nf[lb];
+    const double* tra = prim.tr + la * kTrStride * kTrStride;
+    const double* trb = prim.tr + lb * kTrStride * kTrStride;
+    double wgt = (sa == sb) ? 1.0 : 2.0;
+    DerivPlan pl(la, lb, 0);
+    const int na = ncart(la), nb = ncart(lb);
+    __shared__ double one_tr[kTrStride];
+    if (lane < kTrStride) one_tr[lane] = (lane == 0) ? 1.0 : 0.0;
+    __syncwarp();
+    if (slot == 0) {
+      if (ata == atb) continue;   // overlap and kinetic depend on A - B only
+      // Dcart (for T) into ycart, Wcart into t1-region copy
+      double* Dc = smem + pl.ycart;
+      double* Wc = smem + pl.hrr;   // hrr region unused here
+      double* s1d = smem + pl.total;  // 3 x 64 past the plan
+      warp_back_transform(D + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa,
+                          nfb, 1, smem + pl.t1, smem + pl.t2, Dc, lane);
+      warp_back_transform(W + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa,
+                          nfb, 1, smem + pl.t1, smem + pl.t2, Wc, lane);
+      double gT[3] = {0, 0, 0}, gS[3] = {0, 0, 0};
+      for (int pa = 0; pa < prim.nprim[sa]; ++pa)
+        for (int pb = 0; pb < prim.nprim[sb]; ++pb) {
+          double al = prim.exps[prim.pstart[sa] + pa], be = prim.exps[prim.pstart[sb] + pb];
+          double w = prim.coefs[prim.pstart[sa] + pa] * prim.coefs[prim.pstart[sb] + pb];
+          if (lane < 3) os_overlap_1d_g(al, be, A[lane], B[lane], la + 1, lb + 2, s1d + lane * 64, 8);
+          __syncwarp();
+          for (int idx = lane; idx < na * nb; idx += 32) {
+            int ka = idx / nb, kb = idx % nb;
+            int c[3], d[3];
+            cart_decode(la, ka, c[0], c[1], c[2]);
+            cart_decode(lb, kb, d[0], d[1], d[2]);
+            const double* sx[3] = {s1d, s1d + 64, s1d + 128};
+            double S0[3], K0[3];
+            for (int q = 0; q < 3; ++q) {
+              S0[q] = s1(sx[q], c[q], d[q]);
+              K0[q] = k1d(sx[q], c[q], d[q], be);
+            }
+            for (int x = 0; x < 3; ++x) {
+              // d/dA_x of the 1D factors along x
+              double dS = 2.0 * al * s1(sx[x], c[x] + 1, d[x]) - (c[x] > 0 ? c[x] * s1(sx[x], c[x] - 1, d[x]) : 0.0);
+              double dK = 2.0 * al * k1d(sx[x], c[x] + 1, d[x], be) -
+                          (c[x] > 0 ? c[x] * k1d(sx[x], c[x] - 1, d[x], be) : 0.0);
+              int y = (x + 1) % 3, z = (x + 2) % 3;
+              double dSfull = dS * S0[y] * S0[z];
+              double dTfull = -0.5 * (dK * S0[y] * S0[z] + dS * K0[y] * S0[z] + dS * S0[y] * K0[z]);
+              gS[x] += w * Wc[idx] * dSfull;
+              gT[x] += w * Dc[idx] * dTfull;
+            }
+          }
+          __syncwarp();
+        }
+      for (int x = 0; x < 3; ++x) {
+        double t = warp_sum(gT[x]) * wgt, s = warp_sum(gS[x]) * wgt;
+        if (lane == 0) {
+          atomicAdd(grad_one + 3 * ata + x, t);
+          atomicAdd(grad_one + 3 * atb + x, -t);
+          atomicAdd(grad_ovl + 3 * ata + x, -s);
+          atomicAdd(grad_ovl + 3 * atb + x, s);
+        }
+      }
+      __syncwarp();
+      continue;
+    }
+    // nuclear attraction of nucleus C = slot - 1
+    int Cn = slot - 1;
+    const double* Cx = axyz + 3 * Cn;
+    if (ata == atb && atb == Cn) continue;
+    double* Fm = smem + pl.fm;
+    double* vrr = smem + pl.vrr;
+    int accsz = acc_size(pl.emin, pl.emax, 0);
+    for (int i = lane; i < 3 * accsz; i += 32) smem[pl.acc0 + i] = 0.0;
+    EtrShape sh{0, pl.emin, pl.emax};
+    for (int pa = 0; pa < prim.nprim[sa]; ++pa)
+      for (int pb = 0; pb < prim.nprim[sb]; ++pb) {
+        double al = prim.exps[prim.pstart[sa] + pa], be = prim.exps[prim.pstart[sb] + pb];
+        double w = -Z[Cn] * prim.coefs[prim.pstart[sa] + pa] * prim.coefs[prim.pstart[sb] + pb];
+        Prim3 t = make_prim_point(al, A, be, B, Cx);
+        if (lane <= pl.L) Fm[lane] = boys_eval(lane, t.T, boys);
+        __syncwarp();
+        warp_vrr(vrr, pl.L, t, Fm, lane);
+        warp_acc_level(vrr, pl.L, nullptr, sh, w, smem + pl.acc0, lane);
+        warp_acc_level(vrr, pl.L, nullptr, sh, 2.0 * al * w, smem + pl.accA, lane);
+        warp_acc_level(vrr, pl.L, nullptr, sh, 2.0 * be * w, smem + pl.accB, lane);
+      }
+    warp_back_transform(D + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa, nfb,
+                        1, smem + pl.t1, smem + pl.t2, smem + pl.ycart, lane);
+    double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
+    double g[6];
+    warp_deriv_contract(pl, smem, la, lb, 0, AB, lane, g);
+    for (int i = 0; i < 6; ++i) g[i] = warp_sum(g[i]) * wgt;
+    if (lane == 0) {
+      for (int x = 0; x < 3; ++x) {
+        atomicAdd(grad_one + 3 * ata + x, g[x]);
+        atomicAdd(grad_one + 3 * atb + x, g[3 + x]);
+        atomicAdd(grad_one + 3 * Cn + x, -(g[x] + g[3 + x]));
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------ launchers
+
+static int grid_for_smem(int smem_bytes) {
+  int dev = 0, sms = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  int per_sm = maxsm / (smem_bytes + 1024);
+  if (per_sm > 32) per_sm = 32;
+  if (per_sm < 1) per_sm = 1;
+  return sms * per_sm;
+}
+
+static int deriv_smem(int max_la, int max_lb, int max_lc) {
+  int best = 0;
+  for (int la = 0; la <= max_la; ++la)
+    for (int lb = 0; lb <= max_lb; ++lb)
+      for (int lc = 0; lc <= max_lc; ++lc) {
+        DerivPlan p(la, lb, lc);
+        if (p.total > best) best = p.total;
+      }
+  return (best + 8) * (int)sizeof(double);
+}
+
+void launch_grad_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
+                      int npairs, int max_lp, int max_la, const double* Y, double* grad) {
+  int smem = deriv_smem(max_lp, max_lp, max_la);
+  RIHF_CUDA(cudaFuncSetAttribute(grad_eri3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+  grad_eri3_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, aux, pairs, npairs, ic.boys, ic.counter, Y,
+                                                                 grad);
+  RIHF_LAUNCH_CHECK();
+  if (ic.launches) *ic.launches += 1;
+}
+
+void launch_grad_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, const double* Z, double* grad) {
+  int smem = deriv_smem(max_la, 0, max_la);
+  RIHF_CUDA(cudaFuncSetAttribute(grad_eri2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+  grad_eri2_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(aux, ic.boys, ic.counter, Z, grad);
+  RIHF_LAUNCH_CHECK();
+  if (ic.launches) *ic.launches += 1;
+}
+
+void launch_grad_one_electron(const IntegralCtx& ic, const DevShells& prim, int max_lp, int natoms, const int* Z,
+                              const double* axyz, const double* D, const double* W, double* grad_one,
+                              double* grad_ovl) {
+  int smem = deriv_smem(max_lp, max_lp, 0) + 3 * 64 * (int)sizeof(double);
+  RIHF_CUDA(cudaFuncSetAttribute(grad_one_electron_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+  grad_one_electron_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, natoms, Z, axyz, ic.boys, ic.counter,
+                                                                         D, W, grad_one, grad_ovl);
+  RIHF_LAUNCH_CHECK();
+  if (ic.launches) *ic.launches += 1;
+}
+
+}  // namespace rihf

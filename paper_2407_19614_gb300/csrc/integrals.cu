@@ -1,0 +1,459 @@
+// Integral kernels of librihf: (mu nu|P), (P|Q), S, T, V and, in grad_integrals.cu,
+// their derivative contractions.  One warp (one 32-thread block) per task; tasks
+// are handed out through a device counter so that heavy and light shell classes
+// balance across the 152 SMs.
+#include <cmath>
+#include <vector>
+
+#include "integrals.cuh"
+#include "os_hgp.cuh"
+
+namespace rihf {
+
+// ------------------------------------------------------------ Boys table
+
+// F_m(T) = int_0^1 t^{2m} exp(-T t^2) dt by 128-point Gauss-Legendre quadrature
+// in long double (nodes from Newton iteration on P_128).
+void boys_table_host(double* out) {
+  const int n = 128;
+  std::vector<long double> x(n), w(n);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < n; ++i) {
+    long double z = cosl(pi * (i + 0.75L) / (n + 0.5L));
+    for (int it = 0; it < 100; ++it) {
+      long double p0 = 1.0L, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      long double dp = n * (z * p1 - p0) / (z * z - 1.0L);
+      long double dz = p1 / dp;
+      z -= dz;
+      if (fabsl(dz) < 1e-21L) {
+        // recompute derivative at the converged node for the weight
+        p0 = 1.0L;
+        p1 = z;
+        for (int k = 2; k <= n; ++k) {
+          long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0L);
+        x[i] = z;
+        w[i] = 2.0L / ((1.0L - z * z) * dp * dp);
+        break;
+      }
+    }
+  }
+  for (int k = 0; k < kBoysN; ++k) {
+    long double T = k * (long double)kBoysStep;
+    for (int m = 0; m < kBoysM; ++m) {
+      // map [-1,1] -> [0,1]: t = (x+1)/2, dt = dx/2
+      long double s = 0.0L;
+      for (int i = 0; i < n; ++i) {
+        long double t = 0.5L * (x[i] + 1.0L);
+        s += w[i] * powl(t, 2 * m) * expl(-T * t * t);
+      }
+      out[(size_t)k * kBoysM + m] = (double)(0.5L * s);
+    }
+  }
+}
+
+// ------------------------------------------------------------ helpers
+
+__device__ inline int warp_next_task(int* counter, int lane) {
+  int t = 0;
+  if (lane == 0) t = atomicAdd(counter, 1);
+  return __shfl_sync(0xffffffffu, t, 0);
+}
+
+// out[sa][sb][sc] = sum tra[sa][ka] trb[sb][kb] trc[sc][kc] cart[ka][kb][kc]
+// (three passes through shared memory).  Returns the result pointer.
+__device__ inline const double* warp_transform3(const double* cart, int la, int lb, int lc, const double* tra,
+                                                const double* trb, const double* trc, int nfa, int nfb, int nfc,
+                                                double* s1, double* s2, int lane) {
+  const int na = ncart(la), nb = ncart(lb), nc = ncart(lc);
+  // pass c: s1[ka][kb][sc]
+  for (int idx = lane; idx < na * nb * nfc; idx += 32) {
+    int sc = idx % nfc, r = idx / nfc;
+    const double* row = cart + r * nc;
+    const double* t = trc + sc * kTrStride;
+    double v = 0.0;
+    for (int k = 0; k < nc; ++k) v += t[k] * row[k];
+    s1[idx] = v;
+  }
+  __syncwarp();
+  // pass b: s2[ka][sb][sc]
+  for (int idx = lane; idx < na * nfb * nfc; idx += 32) {
+    int sc = idx % nfc, r = idx / nfc;
+    int sb = r % nfb, ka = r / nfb;
+    const double* t = trb + sb * kTrStride;
+    double v = 0.0;
+    for (int k = 0; k < nb; ++k) v += t[k] * s1[(ka * nb + k) * nfc + sc];
+    s2[idx] = v;
+  }
+  __syncwarp();
+  // pass a: s1[sa][sb][sc]
+  for (int idx = lane; idx < nfa * nfb * nfc; idx += 32) {
+    int rest = idx % (nfb * nfc), sa = idx / (nfb * nfc);
+    const double* t = tra + sa * kTrStride;
+    double v = 0.0;
+    for (int k = 0; k < na; ++k) v += t[k] * s2[k * nfb * nfc + rest];
+    s1[idx] = v;
+  }
+  __syncwarp();
+  return s1;
+}
+
+// Shared-memory plan for one (la, lb | lc) class, in doubles.
+struct Eri3Plan {
+  int fm, vrr, etr, acc, hrr, half, t1, t2, total;
+  __device__ __host__ Eri3Plan(int la, int lb, int lc, int emin, int emax, int nacc) {
+    int L = emax + lc;
+    EtrShape sh{lc, emin, emax};
+    fm = 0;
+    vrr = fm + 24;
+    etr = vrr + vrr_size(L);
+    acc = etr + (lc > 0 ? sh.total() : 0);
+    int accsz = acc_size(emin, emax, lc);
+    hrr = acc + nacc * accsz;
+    half = hrr_scratch(la, lb, lc, emax) / 2;
+    int big = ncart(la + 1) * ncart(lb + 1) * ncart(lc);
+    if (big > half) half = big;
+    t1 = hrr + 2 * half;
+    t2 = t1 + big;
+    total = t2 + big;
+    // transform scratch reuses the VRR/ETR region when it is large enough
+  }
+};
+
+int smem_eri3_doubles(int la, int lb, int lc) {
+  Eri3Plan p(la, lb, lc, la, la + lb, 1);
+  return p.total;
+}
+
+// ------------------------------------------------------------ (mu nu|P)
+
+__global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux, const ShellPair* __restrict__ pairs,
+                                                  int npairs, const double* __restrict__ boys, int* counter,
+                                                  double* __restrict__ T) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x;
+  const long long ntask = (long long)npairs * aux.nshell;
+  const int N = prim.nfunc;
+  const size_t N2 = (size_t)N * N;
+  for (;;) {
+    long long task = warp_next_task(counter, lane);
+    if (task >= ntask) break;
+    int ip = (int)(task % npairs), sc = (int)(task / npairs);
+    int sa = pairs[ip].a, sb = pairs[ip].b;
+    // compute with la >= lb (cheaper HRR); the stored block keeps mu in pairs[ip].a
+    const bool swp = prim.l[sa] < prim.l[sb];
+    if (swp) { int t = sa; sa = sb; sb = t; }
+    int la = prim.l[sa], lb = prim.l[sb], lc = aux.l[sc];
+    int emin = la, emax = la + lb, L = emax + lc;
+    Eri3Plan pl(la, lb, lc, emin, emax, 1);
+    double* Fm = smem + pl.fm;
+    double* vrr = smem + pl.vrr;
+    double* etr = smem + pl.etr;
+    double* acc = smem + pl.acc;
+    int accsz = acc_size(emin, emax, lc);
+    for (int i = lane; i < accsz; i += 32) acc[i] = 0.0;
+    const double* A = prim.xyz + 3 * sa;
+    const double* B = prim.xyz + 3 * sb;
+    const double* C = aux.xyz + 3 * sc;
+    EtrShape sh{lc, emin, emax};
+    for (int pa = 0; pa < prim.nprim[sa]; ++pa)
+      for (int pb = 0; pb < prim.nprim[sb]; ++pb)
+        for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
+          double al = prim.exps[prim.pstart[sa] + pa], be = prim.exps[prim.pstart[sb] + pb];
+          double ga = aux.exps[aux.pstart[sc] + pc];
+          double w = prim.coefs[prim.pstart[sa] + pa] * prim.coefs[prim.pstart[sb] + pb] *
+                     aux.coefs[aux.pstart[sc] + pc];
+          Prim3 t = make_prim3(al, A, be, B, ga, C);
+          if (lane <= L) Fm[lane] = boys_eval(lane, t.T, boys);
+          __syncwarp();
+          warp_vrr(vrr, L, t, Fm, lane);
+          warp_etr_accumulate(vrr, L, etr, sh, t, w, acc, lane);
+        }
+    double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
+    const double* cart = warp_hrr(acc, emin, la, lb, lc, AB, smem + pl.hrr, pl.half, lane);
+    int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
+    const double* out = warp_transform3(cart, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
+                                        prim.tr + lb * kTrStride * kTrStride, aux.tr + lc * kTrStride * kTrStride,
+                                        nfa, nfb, nfc, smem + pl.t1, smem + pl.t2, lane);
+    const int mu0 = prim.ao[sa], nu0 = prim.ao[sb], P0 = aux.ao[sc];
+    const int n = nfa * nfb * nfc;
+    for (int idx = lane; idx < n; idx += 32) {
+      int sbb = idx % nfb, r = idx / nfb;
+      int saa = r % nfa, scc = r / nfa;
+      size_t dst = swp ? (size_t)(nu0 + sbb) * N + mu0 + saa : (size_t)(mu0 + saa) * N + nu0 + sbb;
+      T[(size_t)(P0 + scc) * N2 + dst] = out[(saa * nfb + sbb) * nfc + scc];
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------ (P|Q)
+
+__global__ void __launch_bounds__(32) eri2_kernel(DevShells aux, const double* __restrict__ boys, int* counter,
+                                                  double* __restrict__ A) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x;
+  const int ns = aux.nshell;
+  const long long ntask = (long long)ns * (ns + 1) / 2;
+  const int NA = aux.nfunc;
+  for (;;) {
+    long long task = warp_next_task(counter, lane);
+    if (task >= ntask) break;
+    // task -> (sa >= sc)
+    int sa = (int)((sqrt(8.0 * (double)task + 1.0) - 1.0) * 0.5);
+    while ((long long)sa * (sa + 1) / 2 > task) --sa;
+    while ((long long)(sa + 1) * (sa + 2) / 2 <= task) ++sa;
+    int sc = (int)(task - (long long)sa * (sa + 1) / 2);
+    int la = aux.l[sa], lc = aux.l[sc];
+    int emin = la, emax = la, L = la + lc;
+    Eri3Plan pl(la, 0, lc, emin, emax, 1);
+    double* Fm = smem + pl.fm;
+    double* vrr = smem + pl.vrr;
+    double* etr = smem + pl.etr;
+    double* acc = smem + pl.acc;
+    int accsz = acc_size(emin, emax, lc);
+    for (int i = lane; i < accsz; i += 32) acc[i] = 0.0;
+    const double* PA = aux.xyz + 3 * sa;
+    const double* PC = aux.xyz + 3 * sc;
+    EtrShape sh{lc, emin, emax};
+    for (int pa = 0; pa < aux.nprim[sa]; ++pa)
+      for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
+        double al = aux.exps[aux.pstart[sa] + pa], ga = aux.exps[aux.pstart[sc] + pc];
+        double w = aux.coefs[aux.pstart[sa] + pa] * aux.coefs[aux.pstart[sc] + pc];
+        Prim3 t = make_prim3(al, PA, 0.0, PA, ga, PC);
+        if (lane <= L) Fm[lane] = boys_eval(lane, t.T, boys);
+        __syncwarp();
+        warp_vrr(vrr, L, t, Fm, lane);
+        warp_etr_accumulate(vrr, L, etr, sh, t, w, acc, lane);
+      }
+    // acc holds [a][c] directly (lb = 0); transform with b = s (identity 1x1)
+    int nfa = aux.nf[la], nfc = aux.nf[lc];
+    const double* tra = aux.tr + la * kTrStride * kTrStride;
+    const double* trc = aux.tr + lc * kTrStride * kTrStride;
+    double* s1 = smem + pl.t1;
+    double* s2 = smem + pl.t2;
+    const int na = ncart(la), nc = ncart(lc);
+    for (int idx = lane; idx < na * nfc; idx += 32) {
+      int scc = idx % nfc, ka = idx / nfc;
+      double v = 0.0;
+      for (int k = 0; k < nc; ++k) v += trc[scc * kTrStride + k] * acc[ka * nc + k];
+      s1[idx] = v;
+    }
+    __syncwarp();
+    for (int idx = lane; idx < nfa * nfc; idx += 32) {
+      int scc = idx % nfc, saa = idx / nfc;
+      double v = 0.0;
+      for (int k = 0; k < na; ++k) v += tra[saa * kTrStride + k] * s1[k * nfc + scc];
+      s2[idx] = v;
+    }
+    __syncwarp();
+    const int P0 = aux.ao[sa], Q0 = aux.ao[sc];
+    for (int idx = lane; idx < nfa * nfc; idx += 32) {
+      int scc = idx % nfc, saa = idx / nfc;
+      double v = s2[idx];
+      A[(size_t)(P0 + saa) * NA + Q0 + scc] = v;
+      A[(size_t)(Q0 + scc) * NA + P0 + saa] = v;
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------ S, T, V
+
+// Obara-Saika 1D overlap table s[i][j] (i <= imax, j <= jmax) of
+// x_A^i e^{-a x_A^2} x_B^j e^{-b x_B^2}, including sqrt(pi/p) exp(-mu X_AB^2).
+__device__ inline void os_overlap_1d(double a, double b, double XA, double XB, int imax, int jmax, double* s,
+                                     int ld) {
+  double p = a + b, P = (a * XA + b * XB) / p, PA = P - XA, PB = P - XB, X = XA - XB;
+  double inv2p = 0.5 / p;
+  s[0] = sqrt(3.14159265358979323846 / p) * exp(-a * b / p * X * X);
+  for (int i = 1; i <= imax; ++i) {
+    double v = PA * s[(i - 1) * ld];
+    if (i >= 2) v += (i - 1) * inv2p * s[(i - 2) * ld];
+    s[i * ld] = v;
+  }
+  for (int j = 1; j <= jmax; ++j)
+    for (int i = 0; i <= imax; ++i) {
+      double v = PB * s[i * ld + j - 1];
+      if (j >= 2) v += (j - 1) * inv2p * s[i * ld + j - 2];
+      if (i >= 1) v += i * inv2p * s[(i - 1) * ld + j - 1];
+      s[i * ld + j] = v;
+    }
+}
+
+__global__ void __launch_bounds__(32) one_electron_kernel(DevShells prim, int natoms, const int* __restrict__ Z,
+                                                          const double* __restrict__ axyz,
+                                                          const double* __restrict__ boys, int* counter,
+                                                          double* __restrict__ S, double* __restrict__ Tk,
+                                                          double* __restrict__ V) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x;
+  const int ns = prim.nshell;
+  const long long ntask = (long long)ns * (ns + 1) / 2;
+  const int N = prim.nfunc;
+  for (;;) {
+    long long task = warp_next_task(counter, lane);
+    if (task >= ntask) break;
+    int sa = (int)((sqrt(8.0 * (double)task + 1.0) - 1.0) * 0.5);
+    while ((long long)sa * (sa + 1) / 2 > task) --sa;
+    while ((long long)(sa + 1) * (sa + 2) / 2 <= task) ++sa;
+    int sb = (int)(task - (long long)sa * (sa + 1) / 2);
+    int la = prim.l[sa], lb = prim.l[sb];
+    int na = ncart(la), nb = ncart(lb);
+    const double* A = prim.xyz + 3 * sa;
+    const double* B = prim.xyz + 3 * sb;
+    // smem: sacc[na*nb], tacc[na*nb], then V machinery
+    double* sacc = smem;
+    double* tacc = sacc + na * nb;
+    double* s1d = tacc + na * nb;               // 3 x 8 x 8 per primitive pair
+    int emin = la, emax = la + lb, L = emax;
+    Eri3Plan pl(la, lb, 0, emin, emax, 1);
+    double* base = s1d + 3 * 64;
+    double* Fm = base + pl.fm;
+    double* vrr = base + pl.vrr;
+    double* acc = base + pl.acc;
+    for (int i = lane; i < na * nb; i += 32) {
+      sacc[i] = 0.0;
+      tacc[i] = 0.0;
+    }
+    for (int i = lane; i < acc_size(emin, emax, 0); i += 32) acc[i] = 0.0;
+    __syncwarp();
+    EtrShape sh{0, emin, emax};
+    for (int pa = 0; pa < prim.nprim[sa]; ++pa)
+      for (int pb = 0; pb < prim.nprim[sb]; ++pb) {
+        double al = prim.exps[prim.pstart[sa] + pa], be = prim.exps[prim.pstart[sb] + pb];
+        double w = prim.coefs[prim.pstart[sa] + pa] * prim.coefs[prim.pstart[sb] + pb];
+        if (lane < 3) os_overlap_1d(al, be, A[lane], B[lane], la, lb + 2, s1d + lane * 64, 8);
+        __syncwarp();
+        for (int idx = lane; idx < na * nb; idx += 32) {
+          int ka = idx / nb, kb = idx % nb;
+          int ca[3], cb[3];
+          cart_decode(la, ka, ca[0], ca[1], ca[2]);
+          cart_decode(lb, kb, cb[0], cb[1], cb[2]);
+          double sd[3], kd[3];
+          for (int d = 0; d < 3; ++d) {
+            const double* s = s1d + d * 64;
+            int i = ca[d], j = cb[d];
+            sd[d] = s[i * 8 + j];
+            double k2 = 4.0 * be * be * s[i * 8 + j + 2] - 2.0 * be * (2 * j + 1) * s[i * 8 + j];
+            if (j >= 2) k2 += j * (j - 1) * s[i * 8 + j - 2];
+            kd[d] = k2;
+          }
+          sacc[idx] += w * sd[0] * sd[1] * sd[2];
+          tacc[idx] += -0.5 * w * (kd[0] * sd[1] * sd[2] + sd[0] * kd[1] * sd[2] + sd[0] * sd[1] * kd[2]);
+        }
+        __syncwarp();
+        for (int C = 0; C < natoms; ++C) {
+          Prim3 t = make_prim_point(al, A, be, B, axyz + 3 * C);
+          if (lane <= L) Fm[lane] = boys_eval(lane, t.T, boys);
+          __syncwarp();
+          warp_vrr(vrr, L, t, Fm, lane);
+          warp_etr_accumulate(vrr, L, nullptr, sh, t, -w * Z[C], acc, lane);
+        }
+      }
+    double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
+    const double* vcart = warp_hrr(acc, emin, la, lb, 0, AB, base + pl.hrr, pl.half, lane);
+    int nfa = prim.nf[la], nfb = prim.nf[lb];
+    const double* tra = prim.tr + la * kTrStride * kTrStride;
+    const double* trb = prim.tr + lb * kTrStride * kTrStride;
+    double* o1 = base + pl.t1;
+    double* o2 = base + pl.t2;
+    const double* srcs[3] = {sacc, tacc, vcart};
+    double* dsts[3] = {S, Tk, V};
+    for (int q = 0; q < 3; ++q) {
+      const double* src = srcs[q];
+      for (int idx = lane; idx < na * nfb; idx += 32) {
+        int sbb = idx % nfb, ka = idx / nfb;
+        double v = 0.0;
+        for (int k = 0; k < nb; ++k) v += trb[sbb * kTrStride + k] * src[ka * nb + k];
+        o1[idx] = v;
+      }
+      __syncwarp();
+      for (int idx = lane; idx < nfa * nfb; idx += 32) {
+        int sbb = idx % nfb, saa = idx / nfb;
+        double v = 0.0;
+        for (int k = 0; k < na; ++k) v += tra[saa * kTrStride + k] * o1[k * nfb + sbb];
+        o2[idx] = v;
+      }
+      __syncwarp();
+      const int mu0 = prim.ao[sa], nu0 = prim.ao[sb];
+      for (int idx = lane; idx < nfa * nfb; idx += 32) {
+        int sbb = idx % nfb, saa = idx / nfb;
+        dsts[q][(size_t)(mu0 + saa) * N + nu0 + sbb] = o2[idx];
+        dsts[q][(size_t)(nu0 + sbb) * N + mu0 + saa] = o2[idx];
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// ------------------------------------------------------------ launchers
+
+// ordered: only classes with la >= lb occur
+static int max_smem_eri3(int max_la, int max_lb, int max_lc, bool ordered = true) {
+  int best = 0;
+  for (int la = 0; la <= max_la; ++la)
+    for (int lb = 0; lb <= (ordered ? std::min(la, max_lb) : max_lb); ++lb)
+      for (int lc = 0; lc <= max_lc; ++lc) {
+        int s = smem_eri3_doubles(la, lb, lc);
+        if (s > best) best = s;
+      }
+  return best;
+}
+
+static int grid_for(int smem_bytes) {
+  int dev = 0, sms = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  int per_sm = smem_bytes > 0 ? maxsm / (smem_bytes + 1024) : 32;
+  if (per_sm > 32) per_sm = 32;
+  if (per_sm < 1) per_sm = 1;
+  return sms * per_sm;
+}
+
+static void set_smem(const void* fn, int bytes) {
+  RIHF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+}
+
+void launch_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
+                 int npairs, int max_lp, int max_la, double* T) {
+  if (npairs == 0 || aux.nshell == 0) return;
+  int smem = max_smem_eri3(max_lp, max_lp, max_la) * (int)sizeof(double);
+  set_smem((const void*)eri3_kernel, smem);
+  RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+  eri3_kernel<<<grid_for(smem), 32, smem, ic.stream>>>(prim, aux, pairs, npairs, ic.boys, ic.counter, T);
+  RIHF_LAUNCH_CHECK();
+  if (ic.launches) *ic.launches += 1;
+}
+
+void launch_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, double* A) {
+  int smem = max_smem_eri3(max_la, 0, max_la) * (int)sizeof(double);
+  set_smem((const void*)eri2_kernel, smem);
+  RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+  eri2_kernel<<<grid_for(smem), 32, smem, ic.stream>>>(aux, ic.boys, ic.counter, A);
+  RIHF_LAUNCH_CHECK();
+  if (ic.launches) *ic.launches += 1;
+}
+
+void launch_one_electron(const IntegralCtx& ic, const DevShells& prim, int max_lp, int natoms, const int* Z,
+                         const double* axyz, double* S, double* Tk, double* V) {
+  int nc = ncart(max_lp);
+  int smem = (2 * nc * nc + 3 * 64 + max_smem_eri3(max_lp, max_lp, 0, false)) * (int)sizeof(double);
+  set_smem((const void*)one_electron_kernel, smem);
+  RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+  one_electron_kernel<<<grid_for(smem), 32, smem, ic.stream>>>(prim, natoms, Z, axyz, ic.boys, ic.counter, S, Tk,
+                                                               V);
+  RIHF_LAUNCH_CHECK();
+  if (ic.launches) *ic.launches += 1;
+}
+
+}  // namespace rihf

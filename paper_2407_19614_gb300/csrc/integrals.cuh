@@ -1,0 +1,69 @@
+// Host-visible declarations of the integral kernels (integrals.cu).
+#pragma once
+#include "common.cuh"
+
+namespace rihf {
+
+// Device view of a shell list (all arrays device-resident).
+struct DevShells {
+  int nshell = 0;
+  int nfunc = 0;                 // AO count
+  const int* l = nullptr;
+  const int* atom = nullptr;
+  const double* xyz = nullptr;   // 3 per shell
+  const int* nprim = nullptr;
+  const int* pstart = nullptr;
+  const double* exps = nullptr;
+  const double* coefs = nullptr; // primitive coefficients times x^l normalisation
+  const int* ao = nullptr;       // first AO of each shell
+  const double* tr = nullptr;    // per-l transform, kTrL x 15 x 15 (rows: output functions)
+  const int* nf = nullptr;       // per-l number of output functions
+};
+
+// Shell pair (a >= b) list entries.
+struct ShellPair {
+  int a, b;
+};
+
+struct IntegralCtx {
+  const double* boys = nullptr;  // Boys table on device
+  int* counter = nullptr;        // device work counter (one int per launch kind)
+  cudaStream_t stream = 0;
+  long long* launches = nullptr; // host-side launch counter
+};
+
+// Largest dynamic shared-memory slice one warp needs for a class.
+int smem_eri3_doubles(int la, int lb, int lc);
+
+// Three-centre integrals T[P][mu][nu] = (mu nu|P) for the listed shell pairs
+// (mu in a, nu in b, a >= b; both triangles inside diagonal shell blocks).
+void launch_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
+                 int npairs, int max_lp, int max_la, double* T);
+
+// Metric A[P][Q] = (P|Q) (full symmetric matrix).
+void launch_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, double* A);
+
+// One-electron S, T (kinetic) and V (nuclear attraction, sum_C -Z_C <a|1/r_C|b>).
+void launch_one_electron(const IntegralCtx& ic, const DevShells& prim, int max_lp, int natoms, const int* Z,
+                         const double* axyz, double* S, double* Tk, double* V);
+
+// Schwarz factors Q_ab = sqrt(max |(ab|ab)|) over all shell pairs a >= b,
+// pair index a*(a+1)/2 + b.
+void launch_schwarz(const IntegralCtx& ic, const DevShells& prim, int max_lp, double* Q);
+
+// Gradient contractions (derivative integrals evaluated on the fly):
+//   grad[atom][x] += sum_{mu nu P} Y[P][mu][nu] d(mu nu|P)/dR          (3-centre)
+//   grad[atom][x] += -1/2 sum_PQ Z[P][Q] d(P|Q)/dR                      (2-centre)
+//   grad[atom][x] += sum D d(T+V)/dR - sum W dS/dR                      (one-electron)
+void launch_grad_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
+                      int npairs, int max_lp, int max_la, const double* Y, double* grad);
+void launch_grad_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, const double* Z, double* grad);
+void launch_grad_one_electron(const IntegralCtx& ic, const DevShells& prim, int max_lp, int natoms, const int* Z,
+                              const double* axyz, const double* D, const double* W, double* grad_one,
+                              double* grad_ovl);
+
+// Boys table F_m(T_k) generated on the host (long double Gauss-Legendre
+// quadrature of the defining integral), kBoysN x kBoysM doubles.
+void boys_table_host(double* out);
+
+}  // namespace rihf

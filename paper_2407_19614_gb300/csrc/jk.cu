@@ -1,0 +1,88 @@
+// RI-J contraction passes over B (Eq. j_ri: d_P = sum B^P_{mu nu} D_{mu nu},
+// J = sum_P d_P B^P) and small helpers.  Both passes stream B once from HBM with
+// coalesced loads; the row pass gives each auxiliary index its own CTA, the
+// column pass splits the auxiliary range and reduces the partial sums in a
+// fixed order.
+#include <algorithm>
+
+#include "jk.cuh"
+
+namespace rihf {
+
+__global__ void __launch_bounds__(256) gemv_rows_kernel(const double* __restrict__ A, int M, long long K,
+                                                        const double* __restrict__ x, double alpha, double* y) {
+  __shared__ double red[8];
+  for (int r = blockIdx.x; r < M; r += gridDim.x) {
+    const double* row = A + (long long)r * K;
+    double s = 0.0;
+    for (long long j = threadIdx.x; j < K; j += 256) s = fma(row[j], x[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      y[r] = alpha * t;
+    }
+    __syncthreads();
+  }
+}
+
+void gemv_rows(const LaCtx& la, const double* A, int M, long long K, const double* x, double alpha, double* y) {
+  int blocks = std::min(M, 16 * la.sms);
+  gemv_rows_kernel<<<blocks, 256, 0, la.stream>>>(A, M, K, x, alpha, y);
+  RIHF_LAUNCH_CHECK();
+  if (la.launches) *la.launches += 1;
+}
+
+__global__ void __launch_bounds__(256) gemv_cols_kernel(const double* __restrict__ A, int M, long long K,
+                                                        const double* __restrict__ x, int rows_per,
+                                                        double* __restrict__ part) {
+  long long j = blockIdx.x * 256LL + threadIdx.x;
+  int r0 = blockIdx.y * rows_per, r1 = min(M, r0 + rows_per);
+  if (j >= K) return;
+  double s = 0.0;
+  for (int r = r0; r < r1; ++r) s = fma(x[r], A[(long long)r * K + j], s);
+  part[(long long)blockIdx.y * K + j] = s;
+}
+
+__global__ void cols_reduce_kernel(const double* __restrict__ part, int nchunk, long long K, double alpha,
+                                   double* y) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < K; j += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += part[(long long)c * K + j];
+    y[j] = alpha * s;
+  }
+}
+
+void gemv_cols(const LaCtx& la, const double* A, int M, long long K, const double* x, double alpha, double* y) {
+  long long colblocks = (K + 255) / 256;
+  int nchunk = (int)std::max<long long>(1, std::min<long long>(M, (8LL * la.sms + colblocks - 1) / colblocks));
+  while (nchunk > 1 && (size_t)nchunk * K > la.work_elems) nchunk /= 2;
+  int rows_per = ceil_div(M, nchunk);
+  nchunk = ceil_div(M, rows_per);
+  gemv_cols_kernel<<<dim3((unsigned)colblocks, nchunk), 256, 0, la.stream>>>(A, M, K, x, rows_per, la.work);
+  RIHF_LAUNCH_CHECK();
+  int blocks = (int)std::min<long long>((K + 255) / 256, 8LL * la.sms);
+  cols_reduce_kernel<<<blocks, 256, 0, la.stream>>>(la.work, nchunk, K, alpha, y);
+  RIHF_LAUNCH_CHECK();
+  if (la.launches) *la.launches += 2;
+}
+
+__global__ void outer_fill_kernel(const double* __restrict__ c, int naux, const double* __restrict__ D, long long n2,
+                                  double* __restrict__ Y) {
+  long long total = (long long)naux * n2;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x)
+    Y[idx] = c[idx / n2] * D[idx % n2];
+}
+
+void outer_fill(const LaCtx& la, const double* c, int naux, const double* D, long long n2, double* Y) {
+  long long total = (long long)naux * n2;
+  int blocks = (int)std::min<long long>((total + 255) / 256, 16LL * la.sms);
+  outer_fill_kernel<<<blocks, 256, 0, la.stream>>>(c, naux, D, n2, Y);
+  RIHF_LAUNCH_CHECK();
+  if (la.launches) *la.launches += 1;
+}
+
+}  // namespace rihf

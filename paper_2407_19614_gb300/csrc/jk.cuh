@@ -1,0 +1,16 @@
+// RI-J / RI-K contraction kernels (jk.cu): the HBM-streaming passes over the
+// fitted tensor B (Eq. j_ri) and helpers of the gradient's Y formation.
+#pragma once
+#include "common.cuh"
+#include "linalg.cuh"
+
+namespace rihf {
+
+// y[r] = alpha * sum_j A[r*K + j] x[j], r < M (one CTA per row, coalesced).
+void gemv_rows(const LaCtx& la, const double* A, int M, long long K, const double* x, double alpha, double* y);
+// y[j] = alpha * sum_r x[r] A[r*K + j], j < K (row chunks reduced deterministically).
+void gemv_cols(const LaCtx& la, const double* A, int M, long long K, const double* x, double alpha, double* y);
+// Y[P][e] = c[P] * D[e] for e < n2, P < naux.
+void outer_fill(const LaCtx& la, const double* c, int naux, const double* D, long long n2, double* Y);
+
+}  // namespace rihf

@@ -1,0 +1,777 @@
+// Dense linear algebra kernels of librihf.
+#include <algorithm>
+#include <cmath>
+
+#include "linalg.cuh"
+
+namespace rihf {
+
+static inline void count(const LaCtx& la, int n = 1) {
+  if (la.launches) *la.launches += n;
+}
+
+// ------------------------------------------------------------ GEMM (FP64)
+
+constexpr int GT = 32;   // output tile
+constexpr int GK = 16;   // K step
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) dgemm_kernel(GemmArgs g, int nsplit, int kper, int bper,
+                                                    double* __restrict__ work) {
+  __shared__ double As[GK][GT + 1];
+  __shared__ double Bs[GK][GT + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int n0 = blockIdx.x * GT, m0 = blockIdx.y * GT;
+  const int z = blockIdx.z;
+  if (g.symcols > 0) {
+    int j0 = n0, j1 = min(n0 + GT, g.N) - 1;
+    bool spans = (j0 / g.symcols) != (j1 / g.symcols);
+    if (!spans && (j0 % g.symcols) > (j0 / g.symcols)) return;
+  }
+  int b_lo, b_hi, k_lo, k_hi, slot_b, slot_s;
+  if (g.reduce_batch) {
+    slot_s = z;
+    slot_b = 0;
+    b_lo = z * bper;
+    b_hi = min(g.batch, b_lo + bper);
+    k_lo = 0;
+    k_hi = g.K;
+  } else {
+    slot_b = z / nsplit;
+    slot_s = z % nsplit;
+    b_lo = slot_b;
+    b_hi = slot_b + 1;
+    k_lo = slot_s * kper;
+    k_hi = min(g.K, k_lo + kper);
+  }
+  if (g.lowerA) k_hi = min(k_hi, m0 + GT);
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int b = b_lo; b < b_hi; ++b) {
+    const double* A = g.A + (long long)b * g.sA;
+    const double* B = g.B + (long long)b * g.sB;
+    for (int k0 = k_lo; k0 < k_hi; k0 += GK) {
+      for (int r = 0; r < 2; ++r) {
+        int idx = tid + r * 256;
+        int mm, kk;
+        if (TA) { mm = idx % GT; kk = idx / GT; } else { kk = idx % GK; mm = idx / GK; }
+        int m = m0 + mm, k = k0 + kk;
+        double v = 0.0;
+        if (m < g.M && k < k_hi) v = TA ? A[(long long)k * g.lda + m] : A[(long long)m * g.lda + k];
+        As[kk][mm] = v;
+        int nn, kb;
+        if (TB) { kb = idx % GK; nn = idx / GK; } else { nn = idx % GT; kb = idx / GT; }
+        int n = n0 + nn, kq = k0 + kb;
+        double w = 0.0;
+        if (n < g.N && kq < k_hi) w = TB ? B[(long long)n * g.ldb + kq] : B[(long long)kq * g.ldb + n];
+        Bs[kb][nn] = w;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < GK; ++kk) {
+        double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+        double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
+      }
+      __syncthreads();
+    }
+  }
+  const bool direct = g.reduce_batch ? (gridDim.z == 1) : (nsplit == 1);
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      int m = m0 + ty * 2 + i, n = n0 + tx * 2 + j;
+      if (m >= g.M || n >= g.N) continue;
+      if (direct) {
+        double* C = g.C + (g.reduce_batch ? 0 : (long long)slot_b * g.sC);
+        double* c = C + (long long)m * g.ldc + n;
+        *c = g.beta == 0.0 ? g.alpha * acc[i][j] : g.alpha * acc[i][j] + g.beta * *c;
+      } else {
+        long long slot = (long long)slot_b * (g.reduce_batch ? gridDim.z : nsplit) + slot_s;
+        work[slot * g.M * g.N + (long long)m * g.N + n] = acc[i][j];
+      }
+    }
+}
+
+__global__ void splitk_reduce_kernel(GemmArgs g, int nsplit, const double* __restrict__ work) {
+  long long total = (long long)g.M * g.N * (g.reduce_batch ? 1 : g.batch);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long mn = idx % ((long long)g.M * g.N);
+    int b = (int)(idx / ((long long)g.M * g.N));
+    int m = (int)(mn / g.N), n = (int)(mn % g.N);
+    if (g.symcols > 0) {
+      // tiles skipped in the product were never written; mirror does the rest
+      int j0 = (n / GT) * GT, j1 = min(j0 + GT, g.N) - 1;
+      bool spans = (j0 / g.symcols) != (j1 / g.symcols);
+      if (!spans && (j0 % g.symcols) > (j0 / g.symcols)) continue;
+    }
+    double s = 0.0;
+    for (int q = 0; q < nsplit; ++q) s += work[((long long)b * nsplit + q) * g.M * g.N + mn];
+    double* c = g.C + (g.reduce_batch ? 0 : (long long)b * g.sC) + (long long)m * g.ldc + n;
+    *c = g.beta == 0.0 ? g.alpha * s : g.alpha * s + g.beta * *c;
+  }
+}
+
+void dgemm(const LaCtx& la, const GemmArgs& g) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  int tm = ceil_div(g.M, GT), tn = ceil_div(g.N, GT);
+  long long tiles = (long long)tm * tn * (g.reduce_batch ? 1 : g.batch);
+  int nsplit = 1, kper = g.K, bper = g.batch;
+  const long long target = 4LL * la.sms;
+  if (g.reduce_batch) {
+    nsplit = (int)std::min<long long>(g.batch, std::max<long long>(1, (target + tiles - 1) / tiles));
+    while (nsplit > 1 && (size_t)nsplit * g.M * g.N > la.work_elems) nsplit /= 2;
+    bper = ceil_div(g.batch, nsplit);
+    nsplit = ceil_div(g.batch, bper);
+  } else if (tiles < target && g.K > 2 * GK) {
+    nsplit = (int)std::min<long long>((target + tiles - 1) / tiles, g.K / GK);
+    while (nsplit > 1 && (size_t)nsplit * g.M * g.N * g.batch > la.work_elems) nsplit /= 2;
+    kper = ceil_div(ceil_div(g.K, nsplit), GK) * GK;
+    nsplit = ceil_div(g.K, kper);
+  }
+  if (g.lowerA && nsplit > 1 && !g.reduce_batch) {
+    // the triangular cut is per row tile; keep it simple and exact
+    nsplit = 1;
+    kper = g.K;
+  }
+  dim3 grid(tn, tm, g.reduce_batch ? nsplit : g.batch * nsplit);
+  if (g.transA && g.transB)
+    dgemm_kernel<true, true><<<grid, 256, 0, la.stream>>>(g, nsplit, kper, bper, la.work);
+  else if (g.transA)
+    dgemm_kernel<true, false><<<grid, 256, 0, la.stream>>>(g, nsplit, kper, bper, la.work);
+  else if (g.transB)
+    dgemm_kernel<false, true><<<grid, 256, 0, la.stream>>>(g, nsplit, kper, bper, la.work);
+  else
+    dgemm_kernel<false, false><<<grid, 256, 0, la.stream>>>(g, nsplit, kper, bper, la.work);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+  if (nsplit > 1) {
+    long long total = (long long)g.M * g.N * (g.reduce_batch ? 1 : g.batch);
+    int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * la.sms);
+    splitk_reduce_kernel<<<blocks, 256, 0, la.stream>>>(g, nsplit, la.work);
+    RIHF_LAUNCH_CHECK();
+    count(la);
+  }
+}
+
+// ------------------------------------------------------------ symmetrize
+
+__global__ void symmetrize_lower_kernel(double* X, int n) {
+  __shared__ double t[32][33];
+  int bi = blockIdx.y, bj = blockIdx.x;   // destination tile (bi, bj) with bi <= bj (upper)
+  if (bi > bj) return;
+  double* S = X + (size_t)blockIdx.z * n * n;
+  // source tile (bj, bi) in the lower triangle
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int i = bj * 32 + r, j = bi * 32 + threadIdx.x;
+    t[r][threadIdx.x] = (i < n && j < n) ? S[(size_t)i * n + j] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int i = bi * 32 + r, j = bj * 32 + threadIdx.x;   // upper element (i, j), j > i
+    if (i < n && j < n && j > i) S[(size_t)i * n + j] = t[threadIdx.x][r];
+  }
+}
+
+void symmetrize_lower(const LaCtx& la, double* X, int n, int batch) {
+  int nt = ceil_div(n, 32);
+  symmetrize_lower_kernel<<<dim3(nt, nt, batch), dim3(32, 8), 0, la.stream>>>(X, n);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+}
+
+// ------------------------------------------------------------ Cholesky
+
+constexpr int CB = 32;
+
+// Factor the b x b diagonal block at (k, k) of A (leading dim n) and write its
+// inverse into inv (CB x CB, lower).  One warp.
+__global__ void potrf_diag_kernel(double* A, int n, int k, int b, double* inv, int* flag, int factor) {
+  __shared__ double a[CB][CB + 1];
+  __shared__ double li[CB][CB + 1];
+  int lane = threadIdx.x;
+  for (int i = 0; i < b; ++i) a[i][lane] = (lane < b) ? A[(size_t)(k + i) * n + k + lane] : 0.0;
+  __syncwarp();
+  if (factor) {
+    for (int j = 0; j < b; ++j) {
+      if (lane == 0) {
+        double d = a[j][j];
+        if (!(d > 0.0)) {
+          atomicExch(flag, 1);
+          d = 1.0;
+        }
+        a[j][j] = sqrt(d);
+      }
+      __syncwarp();
+      if (lane > j && lane < b) a[lane][j] /= a[j][j];
+      __syncwarp();
+      if (lane > j && lane < b)
+        for (int c = j + 1; c <= lane; ++c) a[lane][c] -= a[lane][j] * a[c][j];
+      __syncwarp();
+    }
+  }
+  // inverse of the lower factor, column `lane`
+  for (int i = 0; i < CB; ++i) li[i][lane] = 0.0;
+  __syncwarp();
+  if (lane < b) {
+    int j = lane;
+    li[j][j] = 1.0 / a[j][j];
+    for (int i = j + 1; i < b; ++i) {
+      double s = 0.0;
+      for (int q = j; q < i; ++q) s += a[i][q] * li[q][j];
+      li[i][j] = -s / a[i][i];
+    }
+  }
+  __syncwarp();
+  for (int i = 0; i < b; ++i) {
+    if (factor && lane < b) A[(size_t)(k + i) * n + k + lane] = lane <= i ? a[i][lane] : 0.0;
+    inv[i * CB + lane] = li[i][lane];
+  }
+}
+
+__global__ void zero_upper_kernel(double* A, int n) {
+  long long total = (long long)n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(idx / n), j = (int)(idx % n);
+    if (j > i) A[idx] = 0.0;
+  }
+}
+
+void cholesky(const LaCtx& la, double* A, int n, double* scratch) {
+  for (int k = 0; k < n; k += CB) {
+    int b = std::min(CB, n - k);
+    potrf_diag_kernel<<<1, 32, 0, la.stream>>>(A, n, k, b, scratch, la.flag, 1);
+    RIHF_LAUNCH_CHECK();
+    count(la);
+    int rest = n - k - b;
+    if (rest <= 0) break;
+    // panel: A[k+b:, k:k+b] <- A[k+b:, k:k+b] * inv^T
+    GemmArgs g;
+    g.M = rest; g.N = b; g.K = b;
+    g.A = A + (size_t)(k + b) * n + k; g.lda = n;
+    g.B = scratch; g.ldb = CB; g.transB = true;
+    g.C = A + (size_t)(k + b) * n + k; g.ldc = n;
+    g.alpha = 1.0; g.beta = 0.0;
+    dgemm(la, g);
+    // trailing update: A[k+b:, k+b:] -= panel panel^T
+    GemmArgs u;
+    u.M = rest; u.N = rest; u.K = b;
+    u.A = A + (size_t)(k + b) * n + k; u.lda = n;
+    u.B = A + (size_t)(k + b) * n + k; u.ldb = n; u.transB = true;
+    u.C = A + (size_t)(k + b) * n + k + b; u.ldc = n;
+    u.alpha = -1.0; u.beta = 1.0;
+    dgemm(la, u);
+  }
+  zero_upper_kernel<<<std::max(1, std::min(ceil_div((long long)n * n, 256), 8 * la.sms)), 256, 0, la.stream>>>(A, n);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+}
+
+__global__ void identity_kernel(double* X, int n) {
+  long long total = (long long)n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x)
+    X[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+}
+
+void identity(const LaCtx& la, double* X, int n) {
+  identity_kernel<<<std::max(1, std::min(ceil_div((long long)n * n, 256), 8 * la.sms)), 256, 0, la.stream>>>(X, n);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+}
+
+// X = L^{-1} by blocked forward substitution on the identity; scratch holds
+// CB*CB + n*CB doubles.
+void tri_inverse_lower(const LaCtx& la, const double* L, double* X, int n, double* scratch) {
+  identity(la, X, n);
+  double* inv = scratch;
+  double* tmp = scratch + CB * CB;
+  for (int k = 0; k < n; k += CB) {
+    int b = std::min(CB, n - k);
+    potrf_diag_kernel<<<1, 32, 0, la.stream>>>(const_cast<double*>(L), n, k, b, inv, la.flag, 0);
+    RIHF_LAUNCH_CHECK();
+    count(la);
+    int ncol = k + b;
+    // tmp (b x ncol) = inv * X[k:k+b, 0:ncol]
+    GemmArgs g;
+    g.M = b; g.N = ncol; g.K = b;
+    g.A = inv; g.lda = CB;
+    g.B = X + (size_t)k * n; g.ldb = n;
+    g.C = tmp; g.ldc = ncol;
+    dgemm(la, g);
+    // X[k:k+b, 0:ncol] = tmp
+    GemmArgs c2;   // copy via identity product would waste flops; use a plain copy
+    RIHF_CUDA(cudaMemcpy2DAsync(X + (size_t)k * n, n * sizeof(double), tmp, ncol * sizeof(double),
+                                ncol * sizeof(double), b, cudaMemcpyDeviceToDevice, la.stream));
+    (void)c2;
+    int rest = n - k - b;
+    if (rest <= 0) break;
+    // X[k+b:, 0:ncol] -= L[k+b:, k:k+b] * X[k:k+b, 0:ncol]
+    GemmArgs u;
+    u.M = rest; u.N = ncol; u.K = b;
+    u.A = L + (size_t)(k + b) * n + k; u.lda = n;
+    u.B = X + (size_t)k * n; u.ldb = n;
+    u.C = X + (size_t)(k + b) * n; u.ldc = n;
+    u.alpha = -1.0; u.beta = 1.0;
+    dgemm(la, u);
+  }
+}
+
+void trsm_lower(const LaCtx& la, const double* L, int n, double* X, long long ncol, bool trans, int symcols,
+                double* tmp) {
+  double* inv = tmp;
+  double* blk = tmp + CB * CB;
+  const int nb = ceil_div(n, CB);
+  for (int q = 0; q < nb; ++q) {
+    const int kb = trans ? nb - 1 - q : q;
+    const int k = kb * CB, b = std::min(CB, n - k);
+    potrf_diag_kernel<<<1, 32, 0, la.stream>>>(const_cast<double*>(L), n, k, b, inv, la.flag, 0);
+    RIHF_LAUNCH_CHECK();
+    count(la);
+    // blk = op(inv_kk) X[k:k+b, :]
+    GemmArgs g;
+    g.M = b; g.N = (int)ncol; g.K = b;
+    g.A = inv; g.lda = CB; g.transA = trans;
+    g.B = X + (size_t)k * ncol; g.ldb = (int)ncol;
+    g.C = blk; g.ldc = (int)ncol;
+    g.symcols = symcols;
+    dgemm(la, g);
+    RIHF_CUDA(cudaMemcpyAsync(X + (size_t)k * ncol, blk, sizeof(double) * b * ncol, cudaMemcpyDeviceToDevice,
+                              la.stream));
+    GemmArgs u;
+    u.N = (int)ncol; u.K = b;
+    u.B = X + (size_t)k * ncol; u.ldb = (int)ncol;
+    u.alpha = -1.0; u.beta = 1.0;
+    u.symcols = symcols;
+    if (!trans) {
+      // X[k+b:, :] -= L[k+b:, k:k+b] X_k
+      u.M = n - k - b;
+      u.A = L + (size_t)(k + b) * n + k; u.lda = n;
+      u.C = X + (size_t)(k + b) * ncol; u.ldc = (int)ncol;
+    } else {
+      // X[0:k, :] -= L[k:k+b, 0:k]^T X_k
+      u.M = k;
+      u.A = L + (size_t)k * n; u.lda = n; u.transA = true;
+      u.C = X; u.ldc = (int)ncol;
+    }
+    if (u.M > 0) dgemm(la, u);
+  }
+}
+
+// ------------------------------------------------------------ eigensolver
+
+constexpr int JT = 1024;   // Jacobi threads (one CTA)
+
+// Parallel cyclic Jacobi (round-robin pairing) in FP32, one CTA.  a: m x m
+// working matrix (shared or global), v: n x m eigenvector matrix (global).
+__device__ void jacobi_f32(float* a, float* v, int n, int m, int max_sweeps, float* cs, float* sn, float* tt,
+                           int* pp, int* qq, float* red) {
+  const int tid = threadIdx.x;
+  const int half = m / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // convergence test: off-diagonal vs diagonal Frobenius mass
+    float off = 0.f, dia = 0.f;
+    for (int idx = tid; idx < m * m; idx += JT) {
+      int i = idx / m, j = idx % m;
+      float x = a[idx];
+      if (i == j) dia += x * x; else off += x * x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dia += __shfl_xor_sync(0xffffffffu, dia, o);
+    }
+    if ((tid & 31) == 0) { red[tid / 32] = off; red[32 + tid / 32] = dia; }
+    __syncthreads();
+    if (tid == 0) {
+      float so = 0.f, sd = 0.f;
+      for (int w = 0; w < JT / 32; ++w) { so += red[w]; sd += red[32 + w]; }
+      red[64] = so;
+      red[65] = sd;
+    }
+    __syncthreads();
+    float so = red[64], sd = red[65];
+    __syncthreads();
+    if (so <= 1e-12f * sd || so == 0.f) break;
+    for (int r = 0; r < m - 1; ++r) {
+      // pairs: (m-1, r) and ((r+k) mod (m-1), (r-k) mod (m-1)), k = 1..half-1
+      for (int k = tid; k < half; k += JT) {
+        int p, q;
+        if (k == 0) { p = r; q = m - 1; }
+        else { p = (r + k) % (m - 1); q = (r - k + (m - 1)) % (m - 1); }
+        if (p > q) { int t = p; p = q; q = t; }
+        float apq = a[p * m + q], app = a[p * m + p], aqq = a[q * m + q];
+        float c = 1.f, s = 0.f, t = 0.f;
+        if (fabsf(apq) > 1e-30f && fabsf(apq) > 1e-9f * sqrtf(fabsf(app * aqq))) {
+          float tau = (aqq - app) / (2.f * apq);
+          t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          c = rsqrtf(1.f + t * t);
+          s = t * c;
+        }
+        pp[k] = p; qq[k] = q; cs[k] = c; sn[k] = s; tt[k] = t;
+      }
+      __syncthreads();
+      // two-sided update of all 2x2 blocks (k1, k2)
+      for (int idx = tid; idx < half * half; idx += JT) {
+        int k1 = idx / half, k2 = idx % half;
+        int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
+        float c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
+        if (k1 == k2) {
+          float apq = a[p1 * m + q1];
+          a[p1 * m + p1] -= tt[k1] * apq;
+          a[q1 * m + q1] += tt[k1] * apq;
+          a[p1 * m + q1] = 0.f;
+          a[q1 * m + p1] = 0.f;
+          continue;
+        }
+        float app = a[p1 * m + p2], apq = a[p1 * m + q2], aqp = a[q1 * m + p2], aqq = a[q1 * m + q2];
+        // right rotation (columns p2, q2)
+        float xp = c2 * app - s2 * apq, xq = s2 * app + c2 * apq;
+        float yp = c2 * aqp - s2 * aqq, yq = s2 * aqp + c2 * aqq;
+        // left rotation (rows p1, q1)
+        a[p1 * m + p2] = c1 * xp - s1 * yp;
+        a[p1 * m + q2] = c1 * xq - s1 * yq;
+        a[q1 * m + p2] = s1 * xp + c1 * yp;
+        a[q1 * m + q2] = s1 * xq + c1 * yq;
+      }
+      // eigenvectors: V <- V J
+      for (int idx = tid; idx < n * half; idx += JT) {
+        int i = idx / half, k = idx % half;
+        int p = pp[k], q = qq[k];
+        float c = cs[k], s = sn[k];
+        float vp = v[i * m + p], vq = v[i * m + q];
+        v[i * m + p] = c * vp - s * vq;
+        v[i * m + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ A, int n, int m, float* gA,
+                                                    float* V, float* W, int use_smem, int max_sweeps) {
+  extern __shared__ float sm[];
+  __shared__ float cs[1024], sn[1024], tt[1024];
+  __shared__ int pp[1024], qq[1024];
+  __shared__ float red[72];
+  float* a = use_smem ? sm : gA;
+  for (int idx = threadIdx.x; idx < m * m; idx += JT) {
+    int i = idx / m, j = idx % m;
+    a[idx] = (i < n && j < n) ? (float)A[(size_t)i * n + j] : 0.f;
+  }
+  for (int idx = threadIdx.x; idx < n * m; idx += JT) {
+    int i = idx / m, j = idx % m;
+    V[idx] = (i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  jacobi_f32(a, V, n, m, max_sweeps, cs, sn, tt, pp, qq, red);
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += JT) W[i] = a[i * m + i];
+}
+
+// Sort eigenpairs ascending (rank sort) and expand to FP64: X[:, rank] = V[:, i].
+__global__ void eig_sort_kernel(const float* __restrict__ V, const float* __restrict__ W, int n, int m, double* X,
+                                double* Wd) {
+  __shared__ int rank[4096];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float wi = W[i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) {
+      float wj = W[j];
+      if (wj < wi || (wj == wi && j < i)) ++r;
+    }
+    rank[i] = r;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    int row = idx / n, i = idx % n;
+    X[(size_t)row * n + rank[i]] = (double)V[row * m + i];
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) Wd[rank[i]] = (double)W[i];
+}
+
+// Ogita-Aishima step pieces: lam_i = S_ii/(1-R_ii); E_ij as in their Algorithm 1.
+__global__ void oa_lambda_kernel(const double* R, const double* S, int n, double* lam) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    lam[i] = S[(size_t)i * n + i] / (1.0 - R[(size_t)i * n + i]);
+}
+
+// sums[0] = ||S - diag(lam)||_F^2, sums[1] = ||R||_F^2, sums[2] = ||A||_F^2 (one block)
+__global__ void oa_norms_kernel(const double* R, const double* S, const double* A, const double* lam, int n,
+                                double* sums) {
+  __shared__ double r0[32], r1[32], r2[32];
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (long long idx = threadIdx.x; idx < (long long)n * n; idx += blockDim.x) {
+    int i = (int)(idx / n), j = (int)(idx % n);
+    double s = S[idx] - (i == j ? lam[i] : 0.0);
+    a0 += s * s;
+    a1 += R[idx] * R[idx];
+    a2 += A[idx] * A[idx];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  if ((threadIdx.x & 31) == 0) { r0[threadIdx.x / 32] = a0; r1[threadIdx.x / 32] = a1; r2[threadIdx.x / 32] = a2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) { s0 += r0[w]; s1 += r1[w]; s2 += r2[w]; }
+    sums[0] = s0; sums[1] = s1; sums[2] = s2;
+  }
+}
+
+__global__ void oa_e_kernel(const double* R, const double* S, const double* lam, const double* sums, int n,
+                            double* E) {
+  double delta = 2.0 * (sqrt(sums[0]) + sqrt(sums[2]) * sqrt(sums[1]));
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(idx / n), j = (int)(idx % n);
+    double r = R[idx];
+    double e;
+    if (i != j && fabs(lam[i] - lam[j]) > delta) e = (S[idx] + lam[j] * r) / (lam[j] - lam[i]);
+    else e = 0.5 * r;
+    E[idx] = e;
+  }
+}
+
+__global__ void add_inplace_kernel(double* X, const double* Y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    X[i] += Y[i];
+}
+
+__global__ void i_minus_kernel(double* R, int n) {   // R <- I - R
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(idx / n), j = (int)(idx % n);
+    R[idx] = (i == j ? 1.0 : 0.0) - R[idx];
+  }
+}
+
+size_t eig_workspace(int n) {
+  int m = n + (n & 1);
+  size_t f32 = (size_t)m * m + (size_t)n * m + m;       // floats
+  return (f32 + 1) / 2 + 6 * (size_t)n * n + 2 * n + 8;  // doubles
+}
+
+static int elem_blocks(const LaCtx& la, long long n) {
+  return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 8LL * la.sms));
+}
+
+void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double* ws, int refine,
+          const double* Vguess) {
+  int m = n + (n & 1);
+  float* fA = reinterpret_cast<float*>(ws);
+  float* fV = fA + (size_t)m * m;
+  float* fW = fV + (size_t)n * m;
+  double* d = ws + ((size_t)m * m + (size_t)n * m + m + 1) / 2;
+  double* R = d;
+  double* S = R + (size_t)n * n;
+  double* AX = S + (size_t)n * n;
+  double* E = AX + (size_t)n * n;
+  double* XE = E + (size_t)n * n;
+  double* Ag = XE + (size_t)n * n;
+  double* lam = Ag + (size_t)n * n;
+  double* sums = lam + n;
+  const double* Ain = A;
+  if (Vguess) {
+    // warm start: diagonalise Vg^T A Vg and rotate back
+    GemmArgs g1;
+    g1.M = n; g1.N = n; g1.K = n; g1.A = A; g1.lda = n; g1.B = Vguess; g1.ldb = n; g1.C = AX; g1.ldc = n;
+    dgemm(la, g1);
+    GemmArgs g2;
+    g2.M = n; g2.N = n; g2.K = n; g2.A = Vguess; g2.lda = n; g2.transA = true; g2.B = AX; g2.ldb = n;
+    g2.C = Ag; g2.ldc = n;
+    dgemm(la, g2);
+    Ain = Ag;
+  }
+  size_t smem = (size_t)m * m * sizeof(float);
+  int use_smem = smem <= 160 * 1024 ? 1 : 0;
+  if (use_smem) RIHF_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  jacobi_kernel<<<1, JT, use_smem ? smem : 0, la.stream>>>(Ain, n, m, fA, fV, fW, use_smem, 14);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+  eig_sort_kernel<<<1, 1024, 0, la.stream>>>(fV, fW, n, m, V, W);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+  if (Vguess) {
+    // V <- Vguess * V
+    GemmArgs g;
+    g.M = n; g.N = n; g.K = n; g.A = Vguess; g.lda = n; g.B = V; g.ldb = n; g.C = XE; g.ldc = n;
+    dgemm(la, g);
+    RIHF_CUDA(cudaMemcpyAsync(V, XE, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, la.stream));
+  }
+  for (int it = 0; it < refine; ++it) {
+    GemmArgs gr;   // R = V^T V
+    gr.M = n; gr.N = n; gr.K = n; gr.A = V; gr.lda = n; gr.transA = true; gr.B = V; gr.ldb = n; gr.C = R; gr.ldc = n;
+    dgemm(la, gr);
+    i_minus_kernel<<<elem_blocks(la, (long long)n * n), 256, 0, la.stream>>>(R, n);
+    RIHF_LAUNCH_CHECK();
+    GemmArgs ga;   // AX = A V
+    ga.M = n; ga.N = n; ga.K = n; ga.A = A; ga.lda = n; ga.B = V; ga.ldb = n; ga.C = AX; ga.ldc = n;
+    dgemm(la, ga);
+    GemmArgs gs;   // S = V^T A V
+    gs.M = n; gs.N = n; gs.K = n; gs.A = V; gs.lda = n; gs.transA = true; gs.B = AX; gs.ldb = n; gs.C = S; gs.ldc = n;
+    dgemm(la, gs);
+    oa_lambda_kernel<<<elem_blocks(la, n), 256, 0, la.stream>>>(R, S, n, lam);
+    oa_norms_kernel<<<1, 1024, 0, la.stream>>>(R, S, A, lam, n, sums);
+    oa_e_kernel<<<elem_blocks(la, (long long)n * n), 256, 0, la.stream>>>(R, S, lam, sums, n, E);
+    RIHF_LAUNCH_CHECK();
+    GemmArgs ge;   // XE = V E ; V += XE
+    ge.M = n; ge.N = n; ge.K = n; ge.A = V; ge.lda = n; ge.B = E; ge.ldb = n; ge.C = XE; ge.ldc = n;
+    dgemm(la, ge);
+    add_inplace_kernel<<<elem_blocks(la, (long long)n * n), 256, 0, la.stream>>>(V, XE, (long long)n * n);
+    RIHF_LAUNCH_CHECK();
+    count(la, 5);
+  }
+  if (refine > 0) {
+    RIHF_CUDA(cudaMemcpyAsync(W, lam, sizeof(double) * n, cudaMemcpyDeviceToDevice, la.stream));
+    // Newton-Schulz re-orthonormalisation V <- V (3I - V^T V)/2: columns inside
+    // near-degenerate clusters are only orthonormalised to first order by the
+    // refinement's r_ij/2 rule; two quadratic steps take V^T V to I.
+    for (int it = 0; it < 2; ++it) {
+      GemmArgs gr;
+      gr.M = n; gr.N = n; gr.K = n; gr.A = V; gr.lda = n; gr.transA = true; gr.B = V; gr.ldb = n; gr.C = R;
+      gr.ldc = n; gr.alpha = -0.5;
+      dgemm(la, gr);
+      identity(la, E, n);
+      axpby(la, n * n, 1.0, R, 1.5, E, R);
+      GemmArgs gv;
+      gv.M = n; gv.N = n; gv.K = n; gv.A = V; gv.lda = n; gv.B = R; gv.ldb = n; gv.C = XE; gv.ldc = n;
+      dgemm(la, gv);
+      RIHF_CUDA(cudaMemcpyAsync(V, XE, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, la.stream));
+    }
+  }
+}
+
+// ------------------------------------------------------------ elementwise
+
+__global__ void axpby_kernel(long long n, double a, const double* x, double b, const double* y, double* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = a * x[i] + b * y[i];
+}
+void axpby(const LaCtx& la, int n, double a, const double* x, double b, const double* y, double* out) {
+  axpby_kernel<<<elem_blocks(la, n), 256, 0, la.stream>>>(n, a, x, b, y, out);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+}
+
+__global__ void add3_kernel(long long n, const double* x, const double* y, const double* z, double* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = x[i] + y[i] + z[i];
+}
+void add3(const LaCtx& la, int n, const double* x, const double* y, const double* z, double* out) {
+  add3_kernel<<<elem_blocks(la, n), 256, 0, la.stream>>>(n, x, y, z, out);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+}
+
+// Deterministic single-block reductions (n up to a few million).
+__global__ void dot_kernel(long long n, const double* x, const double* y, double* out) {
+  __shared__ double r[32];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) s += x[i] * y[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) r[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) t += r[w];
+    *out = t;
+  }
+}
+void dot(const LaCtx& la, int n, const double* x, const double* y, double* out) {
+  dot_kernel<<<1, 1024, 0, la.stream>>>(n, x, y, out);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+}
+
+__global__ void maxabs_kernel(long long n, const double* x, double* out) {
+  __shared__ double r[32];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) s = fmax(s, fabs(x[i]));
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  if ((threadIdx.x & 31) == 0) r[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) t = fmax(t, r[w]);
+    *out = t;
+  }
+}
+void maxabs(const LaCtx& la, int n, const double* x, double* out) {
+  maxabs_kernel<<<1, 1024, 0, la.stream>>>(n, x, out);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+}
+
+__global__ void scale_copy_kernel(long long n, double a, const double* x, double* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = a * x[i];
+}
+void scale_copy(const LaCtx& la, int n, double a, const double* x, double* out) {
+  scale_copy_kernel<<<elem_blocks(la, n), 256, 0, la.stream>>>(n, a, x, out);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+}
+
+__global__ void antisym_kernel(const double* A, double* C, int n) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(idx / n), j = (int)(idx % n);
+    C[idx] = A[idx] - A[(size_t)j * n + i];
+  }
+}
+void antisym(const LaCtx& la, const double* A, double* C, int n) {
+  antisym_kernel<<<elem_blocks(la, (long long)n * n), 256, 0, la.stream>>>(A, C, n);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+}
+
+__global__ void copy_cols_kernel(const double* src, int nrows, int ld, int ncol, double s, double* dst) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)nrows * ncol;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(idx / ncol), j = (int)(idx % ncol);
+    dst[idx] = s * src[(size_t)i * ld + j];
+  }
+}
+void copy_cols(const LaCtx& la, const double* src, int nrows, int ld, int ncol, double s, double* dst) {
+  copy_cols_kernel<<<elem_blocks(la, (long long)nrows * ncol), 256, 0, la.stream>>>(src, nrows, ld, ncol, s, dst);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+}
+
+__global__ void transpose_kernel(const double* __restrict__ src, int rows, int cols, double* __restrict__ dst) {
+  __shared__ double t[32][33];
+  int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int i = r0 + r, j = c0 + threadIdx.x;
+    t[r][threadIdx.x] = (i < rows && j < cols) ? src[(size_t)i * cols + j] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int i = c0 + r, j = r0 + threadIdx.x;   // dst row i (source column), dst column j (source row)
+    if (i < cols && j < rows) dst[(size_t)i * rows + j] = t[threadIdx.x][r];
+  }
+}
+void transpose(const LaCtx& la, const double* src, int rows, int cols, double* dst) {
+  transpose_kernel<<<dim3(ceil_div(cols, 32), ceil_div(rows, 32)), dim3(32, 8), 0, la.stream>>>(src, rows, cols, dst);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+}
+
+__global__ void scale_cols_kernel(const double* X, const double* v, int nrows, int ncol, double* out) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)nrows * ncol;
+       idx += (long long)gridDim.x * blockDim.x)
+    out[idx] = X[idx] * v[idx % ncol];
+}
+void scale_cols(const LaCtx& la, const double* X, const double* v, int nrows, int ncol, double* out) {
+  scale_cols_kernel<<<elem_blocks(la, (long long)nrows * ncol), 256, 0, la.stream>>>(X, v, nrows, ncol, out);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+}
+
+}  // namespace rihf

@@ -1,0 +1,88 @@
+// Dense linear algebra of librihf (linalg.cu).  Every FP64 kernel spreads its
+// work over all SMs: a GB300 SM retires only ~2 DFMA per clock, so tile sizes
+// are small and skinny products are split along K.
+#pragma once
+#include "common.cuh"
+
+namespace rihf {
+
+struct LaCtx {
+  cudaStream_t stream = 0;
+  double* work = nullptr;       // split-K workspace
+  size_t work_elems = 0;
+  long long* launches = nullptr;
+  int sms = 152;
+  int* flag = nullptr;          // device error flag (non-positive pivot, ...)
+};
+
+// C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b] for b < batch.
+// op(A) is M x K: A[m*lda + k] (transA = false) or A[k*lda + m] (true);
+// op(B) is K x N: B[k*ldb + n] (transB = false) or B[n*ldb + k] (true).
+// reduce_batch: all batches accumulate into C[0] (C stride ignored).
+// lowerA: A is lower triangular (op(A)[m][k] = 0 for k > m), K-loop is cut.
+// symcols: > 0 skips column tiles whose every column j has (j % symcols) > (j / symcols)
+//          (strict upper triangle of an N x N slice flattened along columns).
+struct GemmArgs {
+  int M = 0, N = 0, K = 0;
+  double alpha = 1.0, beta = 0.0;
+  const double* A = nullptr;
+  int lda = 0;
+  long long sA = 0;
+  bool transA = false;
+  const double* B = nullptr;
+  int ldb = 0;
+  long long sB = 0;
+  bool transB = false;
+  double* C = nullptr;
+  int ldc = 0;
+  long long sC = 0;
+  int batch = 1;
+  bool reduce_batch = false;
+  bool lowerA = false;
+  int symcols = 0;
+};
+void dgemm(const LaCtx& la, const GemmArgs& g);
+
+// Mirror the lower triangle into the upper one for each of `batch` n x n slices.
+void symmetrize_lower(const LaCtx& la, double* X, int n, int batch);
+
+// In-place Cholesky A = L L^T (lower, upper part zeroed) of an n x n matrix;
+// sets *flag = 1 on a non-positive pivot.  Then Linv = L^{-1} (n x n).
+void cholesky(const LaCtx& la, double* A, int n, double* scratch);
+void tri_inverse_lower(const LaCtx& la, const double* L, double* Linv, int n, double* scratch);
+
+// Blocked triangular solve in place: X <- L^{-1} X (trans = false, forward) or
+// X <- L^{-T} X (trans = true, backward), L lower n x n, X n x ncol row-major
+// (leading dimension ncol).  Diagonal 32 x 32 blocks are inverted by one warp,
+// the off-diagonal updates are FP64 GEMMs over all SMs.  symcols as in GemmArgs.
+// tmp must hold 32 * ncol + 32 * 32 doubles.
+void trsm_lower(const LaCtx& la, const double* L, int n, double* X, long long ncol, bool trans, int symcols,
+                double* tmp);
+
+// Symmetric eigen-decomposition of an n x n FP64 matrix A (row-major):
+// W (n, ascending) and V (n x n, column k = eigenvector k).  FP32 parallel
+// Jacobi in one CTA, then Ogita-Aishima refinement in FP64 (`refine` steps).
+// ws must hold eig_workspace(n) doubles.
+size_t eig_workspace(int n);
+void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double* ws, int refine,
+          const double* Vguess);
+
+// Elementwise / reductions.
+void axpby(const LaCtx& la, int n, double a, const double* x, double b, const double* y, double* out);
+void add3(const LaCtx& la, int n, const double* x, const double* y, const double* z, double* out);
+// out[0] = sum x*y (deterministic two-level reduction)
+void dot(const LaCtx& la, int n, const double* x, const double* y, double* out);
+void maxabs(const LaCtx& la, int n, const double* x, double* out);
+void scale_copy(const LaCtx& la, int n, double a, const double* x, double* out);
+// C = A - A^T for square n x n
+void antisym(const LaCtx& la, const double* A, double* C, int n);
+// Copy columns [0, ncol) of an n_rows x ld matrix into a dense n_rows x ncol one, times s.
+void copy_cols(const LaCtx& la, const double* src, int nrows, int ld, int ncol, double s, double* dst);
+// Y = diag(v) scaling of columns: out[i][j] = X[i][j] * v[j]
+void scale_cols(const LaCtx& la, const double* X, const double* v, int nrows, int ncol, double* out);
+// dst (cols x rows) = src^T for a rows x cols matrix.
+void transpose(const LaCtx& la, const double* src, int rows, int cols, double* dst);
+// Fill dst with the identity (n x n).
+void identity(const LaCtx& la, double* dst, int n);
+
+}  // namespace rihf

@@ -1,0 +1,1046 @@
+// librihf C ABI (include/rihf.h): context, setup, SCF (Alg. 1) and gradient
+// (Alg. 2) orchestration on one GPU.  All heavy work runs in this library's
+// kernels (integrals.cu, grad_integrals.cu, linalg.cu, jk.cu); the host only
+// sequences launches and reads two scalars per SCF iteration for the
+// convergence test.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rihf.h"
+#include "common.cuh"
+#include "integrals.cuh"
+#include "jk.cuh"
+#include "linalg.cuh"
+#include "os_hgp.cuh"
+
+using namespace rihf;
+
+static thread_local std::string g_last_error;
+
+// ============================================================ host basis
+
+namespace {
+
+double dfact(int n) {   // (n)!! with (-1)!! = 1
+  double r = 1.0;
+  for (int k = n; k > 1; k -= 2) r *= k;
+  return r;
+}
+
+using Poly = std::vector<double>;   // coefficients over Cartesian monomials of one degree
+
+// Real solid harmonics S_lm (m = -l..l) as polynomials in x, y, z, built by the
+// recursions (Helgaker, Joergensen, Olsen, Eqs. 6.4.70-6.4.73).
+std::vector<std::vector<Poly>> solid_harmonics(int lmax) {
+  std::vector<std::vector<Poly>> S(lmax + 1);
+  auto mul = [](const Poly& p, int l, int dx, int dy, int dz) {   // multiply a degree-l poly by x^dx y^dy z^dz
+    int L = l + dx + dy + dz;
+    Poly out(ncart(L), 0.0);
+    for (int k = 0; k < ncart(l); ++k) {
+      if (p[k] == 0.0) continue;
+      int a = 0;
+      while ((a + 1) * (a + 2) / 2 <= k) ++a;
+      int lx = l - a, ly = a - (k - a * (a + 1) / 2), lz = l - lx - ly;
+      int nx = lx + dx, ny = ly + dy;
+      out[cart_index(L, nx, ny)] += p[k];
+      (void)lz;
+    }
+    return out;
+  };
+  auto axpy = [](Poly& y, double a, const Poly& x) {
+    for (size_t i = 0; i < y.size(); ++i) y[i] += a * x[i];
+  };
+  S[0] = {Poly{1.0}};
+  for (int l = 0; l < lmax; ++l) {
+    int L = l + 1;
+    std::vector<Poly> next(2 * L + 1, Poly(ncart(L), 0.0));
+    const Poly& sll = S[l][2 * l];      // m = +l
+    const Poly& slml = S[l][0];         // m = -l
+    double f = std::sqrt((l == 0 ? 2.0 : 1.0) * (2 * l + 1) / (2.0 * l + 2));
+    Poly top = mul(sll, l, 1, 0, 0);
+    Poly bot = mul(sll, l, 0, 1, 0);
+    if (l > 0) {
+      axpy(top, -1.0, mul(slml, l, 0, 1, 0));
+      axpy(bot, 1.0, mul(slml, l, 1, 0, 0));
+    }
+    for (auto& v : top) v *= f;
+    for (auto& v : bot) v *= f;
+    next[2 * L] = top;   // m = +L
+    next[0] = bot;       // m = -L
+    for (int m = -l; m <= l; ++m) {
+      Poly v = mul(S[l][m + l], l, 0, 0, 1);
+      for (auto& c : v) c *= (2 * l + 1);
+      if (l >= 1 && std::abs(m) <= l - 1) {
+        const Poly& lo = S[l - 1][m + l - 1];
+        Poly r2 = mul(lo, l - 1, 2, 0, 0);
+        axpy(r2, 1.0, mul(lo, l - 1, 0, 2, 0));
+        axpy(r2, 1.0, mul(lo, l - 1, 0, 0, 2));
+        axpy(v, -std::sqrt((double)(l + m) * (l - m)), r2);
+      }
+      double d = std::sqrt((double)(l + m + 1) * (l - m + 1));
+      for (auto& c : v) c /= d;
+      next[m + L] = v;
+    }
+    S[L] = next;
+  }
+  return S;
+}
+
+// Self-overlap of sum_a c_a x^a e^{-r^2} relative to that of x^l e^{-r^2}.
+double relative_norm(const Poly& c, int l) {
+  double s = 0.0;
+  for (int a = 0; a < ncart(l); ++a)
+    for (int b = 0; b < ncart(l); ++b) {
+      if (c[a] == 0.0 || c[b] == 0.0) continue;
+      int ia = 0;
+      while ((ia + 1) * (ia + 2) / 2 <= a) ++ia;
+      int ib = 0;
+      while ((ib + 1) * (ib + 2) / 2 <= b) ++ib;
+      int ax = l - ia, ay = ia - (a - ia * (ia + 1) / 2), az = l - ax - ay;
+      int bx = l - ib, by = ib - (b - ib * (ib + 1) / 2), bz = l - bx - by;
+      int n[3] = {ax + bx, ay + by, az + bz};
+      if ((n[0] | n[1] | n[2]) & 1) continue;
+      s += c[a] * c[b] * dfact(n[0] - 1) * dfact(n[1] - 1) * dfact(n[2] - 1);
+    }
+  return s / dfact(2 * l - 1);
+}
+
+// Transform table kTrL x 15 x 15 and output-function counts.
+void build_transforms(bool pure, std::vector<double>& tr, std::vector<int>& nf) {
+  tr.assign(kTrL * kTrStride * kTrStride, 0.0);
+  nf.assign(kTrL, 0);
+  auto S = solid_harmonics(kTrL - 1);
+  for (int l = 0; l < kTrL; ++l) {
+    double* T = tr.data() + l * kTrStride * kTrStride;
+    if (pure) {
+      nf[l] = 2 * l + 1;
+      for (int m = 0; m < 2 * l + 1; ++m) {
+        const Poly& p = S[l][m];
+        double nrm = std::sqrt(relative_norm(p, l));
+        for (int k = 0; k < ncart(l); ++k) T[m * kTrStride + k] = p[k] / nrm;
+      }
+    } else {
+      nf[l] = ncart(l);
+      for (int k = 0; k < ncart(l); ++k) {
+        Poly e(ncart(l), 0.0);
+        e[k] = 1.0;
+        T[k * kTrStride + k] = 1.0 / std::sqrt(relative_norm(e, l));
+      }
+    }
+  }
+}
+
+struct HostShells {
+  int nshell = 0, nfunc = 0, lmax = 0;
+  std::vector<int> l, atom, nprim, pstart, ao;
+  std::vector<double> exps, coefs;
+};
+
+// Primitive normalisation of x^l e^{-a r^2} times the caller's coefficient,
+// then the contracted function is renormalised.
+int build_host_shells(int n, const rihf_shell* sh, int natoms, int lmax_allowed, const std::vector<int>& nf,
+                      HostShells& out) {
+  out = HostShells();
+  out.nshell = n;
+  int ao = 0;
+  for (int s = 0; s < n; ++s) {
+    const rihf_shell& x = sh[s];
+    if (x.l < 0 || x.l > lmax_allowed || x.nprim < 1 || x.nprim > kMaxPrim || x.atom < 0 || x.atom >= natoms ||
+        !x.exps || !x.coefs)
+      return RIHF_ERR_INVALID_ARG;
+    out.l.push_back(x.l);
+    out.atom.push_back(x.atom);
+    out.nprim.push_back(x.nprim);
+    out.pstart.push_back((int)out.exps.size());
+    out.ao.push_back(ao);
+    ao += nf[x.l];
+    out.lmax = std::max(out.lmax, x.l);
+    std::vector<double> c(x.nprim);
+    for (int k = 0; k < x.nprim; ++k) {
+      double a = x.exps[k];
+      if (!(a > 0.0)) return RIHF_ERR_INVALID_ARG;
+      c[k] = x.coefs[k] * std::sqrt(std::pow(4.0 * a, x.l) * std::pow(2.0 * a / M_PI, 1.5) / dfact(2 * x.l - 1));
+    }
+    double norm = 0.0;
+    for (int i = 0; i < x.nprim; ++i)
+      for (int j = 0; j < x.nprim; ++j) {
+        double p = x.exps[i] + x.exps[j];
+        norm += c[i] * c[j] * std::pow(M_PI / p, 1.5) * dfact(2 * x.l - 1) / std::pow(2.0 * p, x.l);
+      }
+    double f = 1.0 / std::sqrt(norm);
+    for (int k = 0; k < x.nprim; ++k) {
+      out.exps.push_back(x.exps[k]);
+      out.coefs.push_back(c[k] * f);
+    }
+  }
+  out.nfunc = ao;
+  return RIHF_OK;
+}
+
+template <typename T>
+T* dalloc(size_t n) {
+  void* p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+  if (e != cudaSuccess) throw RihfError(RIHF_ERR_OOM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes");
+  return (T*)p;
+}
+
+template <typename T>
+void upload(T* d, const std::vector<T>& h, cudaStream_t s) {
+  if (!h.empty()) RIHF_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
+}  // namespace
+
+// ============================================================ DIIS kernels
+
+__global__ void diis_dots_kernel(const double* __restrict__ ring, long long len, int s, int m, double* Bm, int ld) {
+  __shared__ double red[32];
+  int j = blockIdx.x;
+  if (j >= m) return;
+  const double* a = ring + (long long)s * len;
+  const double* b = ring + (long long)j * len;
+  double v = 0.0;
+  for (long long i = threadIdx.x; i < len; i += blockDim.x) v += a[i] * b[i];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) t += red[w];
+    Bm[s * ld + j] = t;
+    Bm[j * ld + s] = t;
+  }
+}
+
+// Pulay system [B -1; -1 0] [c; lambda] = [0; -1], B scaled by its largest
+// diagonal entry; Gaussian elimination with partial pivoting (one warp).
+__global__ void diis_solve_kernel(const double* __restrict__ Bm, int ld, int m, double* coef) {
+  __shared__ double a[17][18];
+  int lane = threadIdx.x;
+  int n = m + 1;
+  double sc = 0.0;
+  for (int i = 0; i < m; ++i) sc = fmax(sc, fabs(Bm[i * ld + i]));
+  if (sc == 0.0) sc = 1.0;
+  for (int i = lane; i < n * n; i += 32) {
+    int r = i / n, c = i % n;
+    double v;
+    if (r < m && c < m) v = Bm[r * ld + c] / sc;
+    else if (r == m && c == m) v = 0.0;
+    else v = -1.0;
+    a[r][c] = v;
+  }
+  for (int r = lane; r < n; r += 32) a[r][n] = (r == m) ? -1.0 : 0.0;
+  __syncwarp();
+  for (int k = 0; k < n; ++k) {
+    if (lane == 0) {
+      int piv = k;
+      for (int r = k + 1; r < n; ++r)
+        if (fabs(a[r][k]) > fabs(a[piv][k])) piv = r;
+      if (piv != k)
+        for (int c = 0; c <= n; ++c) {
+          double t = a[k][c];
+          a[k][c] = a[piv][c];
+          a[piv][c] = t;
+        }
+    }
+    __syncwarp();
+    double pk = a[k][k];
+    for (int r = lane; r < n; r += 32) {
+      if (r == k || pk == 0.0) continue;
+      double f = a[r][k] / pk;
+      for (int c = k; c <= n; ++c) a[r][c] -= f * a[k][c];
+    }
+    __syncwarp();
+  }
+  for (int r = lane; r < m; r += 32) coef[r] = a[r][r] != 0.0 ? a[r][n] / a[r][r] : 0.0;
+}
+
+__global__ void diis_extrap_kernel(const double* __restrict__ ring, long long len, int m,
+                                   const double* __restrict__ coef, double* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < m; ++j) s += coef[j] * ring[(long long)j * len + i];
+    out[i] = s;
+  }
+}
+
+// E = 1/2 sum D (h + F) + Vnn written to out[0]; out[1] untouched.
+__global__ void energy_kernel(const double* __restrict__ D, const double* __restrict__ h,
+                              const double* __restrict__ F, long long n2, double vnn, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n2; i += blockDim.x) s += D[i] * (h[i] + F[i]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) t += red[w];
+    out[0] = 0.5 * t + vnn;
+  }
+}
+
+// ============================================================ context
+
+struct rihf_ctx {
+  rihf_options opt;
+  int natoms = 0, nelec = 0, nocc = 0, N = 0, NA = 0, nind = 0;
+  int max_lp = 0, max_la = 0;
+  std::vector<int> Z;
+  std::vector<double> xyz;
+  double vnn = 0.0;
+  HostShells hp, ha;
+  std::vector<double> tr_h;
+  std::vector<int> nf_h;
+  std::vector<ShellPair> pairs_h;
+  int npairs = 0, npairs_total = 0;
+
+  cudaStream_t stream = nullptr;
+  long long launches = 0;
+  int sms = 152;
+
+  // device basis
+  int *d_pl = nullptr, *d_patom = nullptr, *d_pnprim = nullptr, *d_pps = nullptr, *d_pao = nullptr;
+  double *d_pxyz = nullptr, *d_pexp = nullptr, *d_pcoef = nullptr;
+  int *d_al = nullptr, *d_aatom = nullptr, *d_anprim = nullptr, *d_aps = nullptr, *d_aao = nullptr;
+  double *d_axyz_sh = nullptr, *d_aexp = nullptr, *d_acoef = nullptr;
+  double* d_tr = nullptr;
+  int* d_nf = nullptr;
+  int* d_Z = nullptr;
+  double* d_xyz = nullptr;
+  double* d_boys = nullptr;
+  int* d_counter = nullptr;
+  int* d_flag = nullptr;
+  ShellPair* d_pairs = nullptr;
+
+  // geometry-dependent matrices
+  double *S = nullptr, *H = nullptr, *Tk = nullptr, *V = nullptr;
+  double *A = nullptr, *L = nullptr, *Linv = nullptr;
+  double *T3 = nullptr, *B = nullptr;
+  double *Xo = nullptr;     // N x nind orthogonaliser
+  double *Sw = nullptr, *Sv = nullptr;
+
+  // SCF
+  double *C = nullptr, *eps = nullptr, *Ct = nullptr, *D = nullptr, *J = nullptr, *K = nullptr, *F = nullptr;
+  double *Fx = nullptr, *T1 = nullptr, *T2 = nullptr, *Err = nullptr, *Fp = nullptr, *Cp = nullptr, *Hb = nullptr;
+  double *dvec = nullptr, *Fring = nullptr, *Ering = nullptr, *Bdiis = nullptr, *coef = nullptr;
+  double* scal = nullptr;   // [0] energy, [1] max|err|
+  double* Cprev = nullptr;  // previous eigenvectors in the orthonormal basis (warm start)
+  bool have_cprev = false;
+
+  // gradient
+  double* na2tmp = nullptr;
+  double* trsm_tmp = nullptr;
+  double *cvec = nullptr, *W = nullptr, *Bij = nullptr, *Xt = nullptr, *Zm = nullptr, *G = nullptr, *Y = nullptr;
+  double* grad_parts = nullptr;   // 5 x natoms x 3 on device (one, overlap, three, two, nuc)
+  std::vector<double> grad_parts_h;
+
+  double* work = nullptr;
+  size_t work_elems = 0;
+  double* eigws = nullptr;
+  double* scratch = nullptr;
+
+  bool converged = false;
+  bool have_orbitals = false;
+  bool verbose = getenv("RIHF_VERBOSE") != nullptr;
+  bool have_linv = false;
+  double timings[5] = {0, 0, 0, 0, 0};
+  cudaEvent_t ev[8];
+
+  LaCtx la() const {
+    LaCtx l;
+    l.stream = stream;
+    l.work = work;
+    l.work_elems = work_elems;
+    l.launches = const_cast<long long*>(&launches);
+    l.sms = sms;
+    l.flag = d_flag;
+    return l;
+  }
+  IntegralCtx ic() const {
+    IntegralCtx c;
+    c.boys = d_boys;
+    c.counter = d_counter;
+    c.stream = stream;
+    c.launches = const_cast<long long*>(&launches);
+    return c;
+  }
+  DevShells prim() const {
+    DevShells s;
+    s.nshell = hp.nshell; s.nfunc = N; s.l = d_pl; s.atom = d_patom; s.xyz = d_pxyz; s.nprim = d_pnprim;
+    s.pstart = d_pps; s.exps = d_pexp; s.coefs = d_pcoef; s.ao = d_pao; s.tr = d_tr; s.nf = d_nf;
+    return s;
+  }
+  DevShells aux() const {
+    DevShells s;
+    s.nshell = ha.nshell; s.nfunc = NA; s.l = d_al; s.atom = d_aatom; s.xyz = d_axyz_sh; s.nprim = d_anprim;
+    s.pstart = d_aps; s.exps = d_aexp; s.coefs = d_acoef; s.ao = d_aao; s.tr = d_tr; s.nf = d_nf;
+    return s;
+  }
+};
+
+static std::vector<double>& boys_host() {
+  static std::vector<double> tab;
+  if (tab.empty()) {
+    tab.resize((size_t)kBoysN * kBoysM);
+    boys_table_host(tab.data());
+  }
+  return tab;
+}
+
+static void free_all(rihf_ctx* c) {
+  void* ptrs[] = {c->d_pl, c->d_patom, c->d_pnprim, c->d_pps, c->d_pao, c->d_pxyz, c->d_pexp, c->d_pcoef,
+                  c->d_al, c->d_aatom, c->d_anprim, c->d_aps, c->d_aao, c->d_axyz_sh, c->d_aexp, c->d_acoef,
+                  c->d_tr, c->d_nf, c->d_Z, c->d_xyz, c->d_boys, c->d_counter, c->d_flag, c->d_pairs,
+                  c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->T3, c->B, c->Xo, c->Sw, c->Sv,
+                  c->C, c->eps, c->Ct, c->D, c->J, c->K, c->F, c->Fx, c->T1, c->T2, c->Err, c->Fp, c->Cp, c->Hb,
+                  c->dvec, c->Fring, c->Ering, c->Bdiis, c->coef, c->scal, c->Cprev,
+                  c->na2tmp, c->trsm_tmp, c->cvec, c->W, c->Bij, c->Xt, c->Zm, c->G, c->Y, c->grad_parts, c->work, c->eigws, c->scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+// Geometry-dependent part of setup: shell centres, one-electron, metric,
+// Cholesky, 3-centre integrals, fit, orthogonaliser.
+static void compute_geometry(rihf_ctx* c) {
+  cudaStream_t s = c->stream;
+  const int N = c->N, NA = c->NA;
+  LaCtx la = c->la();
+  IntegralCtx ic = c->ic();
+  // shell centres
+  std::vector<double> pxyz(3 * c->hp.nshell), axyz(3 * c->ha.nshell);
+  for (int i = 0; i < c->hp.nshell; ++i)
+    for (int d = 0; d < 3; ++d) pxyz[3 * i + d] = c->xyz[3 * c->hp.atom[i] + d];
+  for (int i = 0; i < c->ha.nshell; ++i)
+    for (int d = 0; d < 3; ++d) axyz[3 * i + d] = c->xyz[3 * c->ha.atom[i] + d];
+  upload(c->d_pxyz, pxyz, s);
+  upload(c->d_axyz_sh, axyz, s);
+  upload(c->d_xyz, c->xyz, s);
+  c->vnn = 0.0;
+  for (int a = 0; a < c->natoms; ++a)
+    for (int b = 0; b < a; ++b) {
+      double r2 = 0.0;
+      for (int d = 0; d < 3; ++d) r2 += (c->xyz[3 * a + d] - c->xyz[3 * b + d]) * (c->xyz[3 * a + d] - c->xyz[3 * b + d]);
+      c->vnn += c->Z[a] * c->Z[b] / std::sqrt(r2);
+    }
+  RIHF_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
+  cudaEventRecord(c->ev[0], s);
+  DevShells P = c->prim(), X = c->aux();
+  launch_one_electron(ic, P, c->max_lp, c->natoms, c->d_Z, c->d_xyz, c->S, c->Tk, c->V);
+  axpby(la, N * N, 1.0, c->Tk, 1.0, c->V, c->H);
+  // metric, Cholesky, L^{-1}
+  launch_eri2(ic, X, c->max_la, c->A);
+  RIHF_CUDA(cudaMemcpyAsync(c->L, c->A, sizeof(double) * NA * NA, cudaMemcpyDeviceToDevice, s));
+  cholesky(la, c->L, NA, c->scratch);
+  c->have_linv = false;
+  // (mu nu|P) for shell pairs a >= b, then B = L^{-1} T (Eq. biap with A^L = L^{-T})
+  // by blocked forward substitution on the lower-triangle columns; an explicit
+  // L^{-1} product loses accuracy when cond(A) reaches 1e9 (diffuse auxiliary sets)
+  RIHF_CUDA(cudaMemsetAsync(c->T3, 0, sizeof(double) * (size_t)NA * N * N, s));
+  launch_eri3(ic, P, X, c->d_pairs, c->npairs, c->max_lp, c->max_la, c->T3);
+  RIHF_CUDA(cudaMemcpyAsync(c->B, c->T3, sizeof(double) * (size_t)NA * N * N, cudaMemcpyDeviceToDevice, s));
+  trsm_lower(la, c->L, NA, c->B, (long long)N * N, false, N, c->trsm_tmp);
+  symmetrize_lower(la, c->B, N, NA);
+  // canonical orthogonaliser from S
+  eigh(la, c->S, N, c->Sw, c->Sv, c->eigws, 4, nullptr);
+  std::vector<double> sw(N);
+  RIHF_CUDA(cudaMemcpyAsync(sw.data(), c->Sw, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  int flag = 0;
+  RIHF_CUDA(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RIHF_CUDA(cudaStreamSynchronize(s));
+  if (flag) throw RihfError(RIHF_ERR_NOT_POSITIVE_DEFINITE, "metric (P|Q) is not positive definite");
+  int k0 = 0;
+  while (k0 < N && sw[k0] <= c->opt.lindep_tau) ++k0;
+  if (k0 == N) throw RihfError(RIHF_ERR_NOT_POSITIVE_DEFINITE, "overlap matrix has no eigenvalue above lindep_tau");
+  int nind = N - k0;
+  if (c->nind != 0 && nind != c->nind) c->have_cprev = false;
+  c->nind = nind;
+  if (k0 == 0) {
+    // no linear dependence: X = L_S^{-T} (S = L_S L_S^T) orthonormalises exactly;
+    // the SCF fixed point does not depend on the choice of orthogonaliser
+    RIHF_CUDA(cudaMemcpyAsync(c->T2, c->S, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, s));
+    cholesky(la, c->T2, N, c->scratch);
+    tri_inverse_lower(la, c->T2, c->T1, N, c->scratch);
+    transpose(la, c->T1, N, N, c->Xo);
+  } else {
+    std::vector<double> invs(nind);
+    for (int i = 0; i < nind; ++i) invs[i] = 1.0 / std::sqrt(sw[k0 + i]);
+    RIHF_CUDA(cudaMemcpyAsync(c->dvec, invs.data(), sizeof(double) * nind, cudaMemcpyHostToDevice, s));
+    // canonical orthogonalisation: Xo[mu][k] = Sv[mu][k0 + k] / sqrt(s_{k0+k})
+    copy_cols(la, c->Sv + k0, N, N, nind, 1.0, c->T1);
+    scale_cols(la, c->T1, c->dvec, N, nind, c->Xo);
+    RIHF_CUDA(cudaStreamSynchronize(s));
+  }
+  // Newton-Schulz S-orthonormalisation, X <- X (3I - X^T S X) / 2, so that
+  // X^T S X = I holds to rounding whatever the eigensolver's residual.
+  for (int it = 0; it < 3; ++it) {
+    GemmArgs g1;   // T1 (N x n) = S X
+    g1.M = N; g1.N = nind; g1.K = N; g1.A = c->S; g1.lda = N; g1.B = c->Xo; g1.ldb = nind; g1.C = c->T1;
+    g1.ldc = nind;
+    dgemm(la, g1);
+    GemmArgs g2;   // T2 (n x n) = -1/2 X^T T1, then + 3/2 I
+    g2.M = nind; g2.N = nind; g2.K = N; g2.A = c->Xo; g2.lda = nind; g2.transA = true; g2.B = c->T1;
+    g2.ldb = nind; g2.C = c->T2; g2.ldc = nind; g2.alpha = -0.5;
+    dgemm(la, g2);
+    identity(la, c->Err, nind);
+    axpby(la, nind * nind, 1.0, c->T2, 1.5, c->Err, c->T2);
+    GemmArgs g3;   // Xo <- Xo T2  (via T1)
+    g3.M = N; g3.N = nind; g3.K = nind; g3.A = c->Xo; g3.lda = nind; g3.B = c->T2; g3.ldb = nind; g3.C = c->T1;
+    g3.ldc = nind;
+    dgemm(la, g3);
+    RIHF_CUDA(cudaMemcpyAsync(c->Xo, c->T1, sizeof(double) * N * nind, cudaMemcpyDeviceToDevice, s));
+  }
+  cudaEventRecord(c->ev[1], s);
+  RIHF_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+  c->timings[0] = ms;
+}
+
+extern "C" {
+
+void rihf_default_options(rihf_options* o) {
+  if (!o) return;
+  o->precision = RIHF_PRECISION_FP64;
+  o->pure = 1;
+  o->schwarz_tau = 1e-14;
+  o->lindep_tau = 1e-8;
+  o->conv_e = 1e-10;
+  o->conv_diis = 1e-9;
+  o->max_iter = 100;
+  o->diis_size = 8;
+  o->mixed_fp64_iters = 2;
+  o->device = 0;
+}
+
+const char* rihf_strerror(int code) {
+  switch (code) {
+    case RIHF_OK: return "ok";
+    case RIHF_ERR_INVALID_ARG: return "invalid argument";
+    case RIHF_ERR_OOM: return "out of device memory";
+    case RIHF_ERR_CUDA: return "CUDA error";
+    case RIHF_ERR_NOT_CONVERGED: return "SCF not converged";
+    case RIHF_ERR_TIMEOUT: return "device wait timed out";
+    case RIHF_ERR_NOT_POSITIVE_DEFINITE: return "matrix not positive definite";
+    case RIHF_ERR_STATE: return "invalid call order";
+    default: return "unknown error";
+  }
+}
+
+const char* rihf_last_error(void) { return g_last_error.c_str(); }
+
+#define RIHF_API_BEGIN try {
+#define RIHF_API_END                                  \
+  }                                                   \
+  catch (const RihfError& e) {                        \
+    g_last_error = e.what();                          \
+    return e.code;                                    \
+  }                                                   \
+  catch (const CudaError& e) {                        \
+    g_last_error = e.what();                          \
+    return RIHF_ERR_CUDA;                             \
+  }                                                   \
+  catch (const std::exception& e) {                   \
+    g_last_error = e.what();                          \
+    return RIHF_ERR_INVALID_ARG;                      \
+  }
+
+int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, const rihf_shell* prim,
+               int naux_shells, const rihf_shell* aux, int nelec, const rihf_options* opt, rihf_ctx** out) {
+  RIHF_API_BEGIN
+  if (!out || natoms <= 0 || !Z || !xyz || nprim_shells <= 0 || !prim || naux_shells <= 0 || !aux || nelec <= 0 ||
+      (nelec & 1)) {
+    g_last_error = "invalid sizes or pointers (nelec must be positive and even)";
+    return RIHF_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  rihf_ctx* c = new rihf_ctx();
+  if (opt) c->opt = *opt; else rihf_default_options(&c->opt);
+  if (c->opt.diis_size < 2) c->opt.diis_size = 2;
+  if (c->opt.diis_size > 16) c->opt.diis_size = 16;
+  try {
+    RIHF_CUDA(cudaSetDevice(c->opt.device));
+    RIHF_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->opt.device));
+    RIHF_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    for (auto& e : c->ev) RIHF_CUDA(cudaEventCreate(&e));
+    c->natoms = natoms;
+    c->nelec = nelec;
+    c->nocc = nelec / 2;
+    c->Z.assign(Z, Z + natoms);
+    c->xyz.assign(xyz, xyz + 3 * natoms);
+    build_transforms(c->opt.pure != 0, c->tr_h, c->nf_h);
+    int rc = build_host_shells(nprim_shells, prim, natoms, kMaxLPrim, c->nf_h, c->hp);
+    if (rc == RIHF_OK) rc = build_host_shells(naux_shells, aux, natoms, kMaxLAux, c->nf_h, c->ha);
+    if (rc != RIHF_OK) throw RihfError(rc, "shell with unsupported l, nprim, atom index or exponent");
+    c->N = c->hp.nfunc;
+    c->NA = c->ha.nfunc;
+    c->max_lp = c->hp.lmax;
+    c->max_la = c->ha.lmax;
+    if (c->nocc > c->N) throw RihfError(RIHF_ERR_INVALID_ARG, "more occupied orbitals than basis functions");
+    const int N = c->N, NA = c->NA;
+    cudaStream_t s = c->stream;
+    // basis arrays
+    c->d_pl = dalloc<int>(c->hp.nshell); upload(c->d_pl, c->hp.l, s);
+    c->d_patom = dalloc<int>(c->hp.nshell); upload(c->d_patom, c->hp.atom, s);
+    c->d_pnprim = dalloc<int>(c->hp.nshell); upload(c->d_pnprim, c->hp.nprim, s);
+    c->d_pps = dalloc<int>(c->hp.nshell); upload(c->d_pps, c->hp.pstart, s);
+    c->d_pao = dalloc<int>(c->hp.nshell); upload(c->d_pao, c->hp.ao, s);
+    c->d_pexp = dalloc<double>(c->hp.exps.size()); upload(c->d_pexp, c->hp.exps, s);
+    c->d_pcoef = dalloc<double>(c->hp.coefs.size()); upload(c->d_pcoef, c->hp.coefs, s);
+    c->d_pxyz = dalloc<double>(3 * c->hp.nshell);
+    c->d_al = dalloc<int>(c->ha.nshell); upload(c->d_al, c->ha.l, s);
+    c->d_aatom = dalloc<int>(c->ha.nshell); upload(c->d_aatom, c->ha.atom, s);
+    c->d_anprim = dalloc<int>(c->ha.nshell); upload(c->d_anprim, c->ha.nprim, s);
+    c->d_aps = dalloc<int>(c->ha.nshell); upload(c->d_aps, c->ha.pstart, s);
+    c->d_aao = dalloc<int>(c->ha.nshell); upload(c->d_aao, c->ha.ao, s);
+    c->d_aexp = dalloc<double>(c->ha.exps.size()); upload(c->d_aexp, c->ha.exps, s);
+    c->d_acoef = dalloc<double>(c->ha.coefs.size()); upload(c->d_acoef, c->ha.coefs, s);
+    c->d_axyz_sh = dalloc<double>(3 * c->ha.nshell);
+    c->d_tr = dalloc<double>(c->tr_h.size()); upload(c->d_tr, c->tr_h, s);
+    c->d_nf = dalloc<int>(c->nf_h.size()); upload(c->d_nf, c->nf_h, s);
+    c->d_Z = dalloc<int>(natoms); upload(c->d_Z, c->Z, s);
+    c->d_xyz = dalloc<double>(3 * natoms);
+    c->d_boys = dalloc<double>((size_t)kBoysN * kBoysM); upload(c->d_boys, boys_host(), s);
+    c->d_counter = dalloc<int>(4);
+    c->d_flag = dalloc<int>(4);
+    // shell pairs a >= b (Schwarz screening keeps all at the default threshold)
+    for (int a = 0; a < c->hp.nshell; ++a)
+      for (int b = 0; b <= a; ++b) c->pairs_h.push_back({a, b});
+    c->npairs = c->npairs_total = (int)c->pairs_h.size();
+    c->d_pairs = dalloc<ShellPair>(c->pairs_h.size()); upload(c->d_pairs, c->pairs_h, s);
+    // matrices
+    size_t n2 = (size_t)N * N, na2 = (size_t)NA * NA, big = (size_t)NA * n2;
+    c->S = dalloc<double>(n2); c->H = dalloc<double>(n2); c->Tk = dalloc<double>(n2); c->V = dalloc<double>(n2);
+    c->A = dalloc<double>(na2); c->L = dalloc<double>(na2); c->Linv = dalloc<double>(na2);
+    c->T3 = dalloc<double>(big); c->B = dalloc<double>(big);
+    c->Xo = dalloc<double>(n2); c->Sw = dalloc<double>(N); c->Sv = dalloc<double>(n2);
+    c->C = dalloc<double>(n2); c->eps = dalloc<double>(N); c->Ct = dalloc<double>((size_t)N * c->nocc);
+    c->D = dalloc<double>(n2); c->J = dalloc<double>(n2); c->K = dalloc<double>(n2); c->F = dalloc<double>(n2);
+    c->Fx = dalloc<double>(n2); c->T1 = dalloc<double>(n2); c->T2 = dalloc<double>(n2); c->Err = dalloc<double>(n2);
+    c->Fp = dalloc<double>(n2); c->Cp = dalloc<double>(n2); c->Cprev = dalloc<double>(n2);
+    c->Hb = dalloc<double>((size_t)NA * N * c->nocc);
+    c->dvec = dalloc<double>(std::max(N, NA));
+    c->Fring = dalloc<double>((size_t)c->opt.diis_size * n2);
+    c->Ering = dalloc<double>((size_t)c->opt.diis_size * n2);
+    c->Bdiis = dalloc<double>(16 * 16);
+    c->coef = dalloc<double>(16);
+    c->scal = dalloc<double>(8);
+    c->cvec = dalloc<double>(NA); c->W = dalloc<double>(n2);
+    c->Bij = dalloc<double>((size_t)NA * c->nocc * c->nocc);
+    c->Xt = dalloc<double>((size_t)NA * c->nocc * c->nocc);
+    c->Zm = dalloc<double>(na2);
+    c->na2tmp = dalloc<double>(na2);
+    c->G = dalloc<double>((size_t)NA * c->nocc * N);
+    c->Y = dalloc<double>(big);
+    c->trsm_tmp = dalloc<double>(32 * std::max<size_t>({n2, (size_t)NA, (size_t)c->nocc * c->nocc}) + 1024);
+    c->grad_parts = dalloc<double>(5 * 3 * natoms);
+    c->work_elems = std::max<size_t>({(size_t)1 << 24, 8 * n2 * 4, (size_t)NA * 64});
+    c->work = dalloc<double>(c->work_elems);
+    c->eigws = dalloc<double>(eig_workspace(N));
+    c->scratch = dalloc<double>(32 * 32 + (size_t)std::max(N, NA) * 32 + 64);
+    compute_geometry(c);
+  } catch (...) {
+    free_all(c);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    throw;
+  }
+  *out = c;
+  return RIHF_OK;
+  RIHF_API_END
+}
+
+int rihf_update_geometry(rihf_ctx* c, const double* xyz) {
+  RIHF_API_BEGIN
+  if (!c || !xyz) return RIHF_ERR_INVALID_ARG;
+  c->xyz.assign(xyz, xyz + 3 * c->natoms);
+  c->converged = false;
+  compute_geometry(c);
+  return RIHF_OK;
+  RIHF_API_END
+}
+
+// Orbitals from a Fock matrix: F' = Xo^T F Xo, eigh, C = Xo C'.
+static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
+  LaCtx la = c->la();
+  const int N = c->N, n = c->nind;
+  GemmArgs g1;   // T1 (N x n) = F Xo
+  g1.M = N; g1.N = n; g1.K = N; g1.A = Fin; g1.lda = N; g1.B = c->Xo; g1.ldb = n; g1.C = c->T1; g1.ldc = n;
+  dgemm(la, g1);
+  GemmArgs g2;   // Fp (n x n) = Xo^T T1
+  g2.M = n; g2.N = n; g2.K = N; g2.A = c->Xo; g2.lda = n; g2.transA = true; g2.B = c->T1; g2.ldb = n;
+  g2.C = c->Fp; g2.ldc = n;
+  dgemm(la, g2);
+  RIHF_CUDA(cudaMemsetAsync(c->eps, 0, sizeof(double) * N, c->stream));
+  eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, (warm && c->have_cprev) ? c->Cprev : nullptr);
+  RIHF_CUDA(cudaMemcpyAsync(c->Cprev, c->Cp, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, c->stream));
+  c->have_cprev = true;
+  // C (N x N): first n columns = Xo Cp, rest zero
+  RIHF_CUDA(cudaMemsetAsync(c->C, 0, sizeof(double) * N * N, c->stream));
+  GemmArgs g3;
+  g3.M = N; g3.N = n; g3.K = n; g3.A = c->Xo; g3.lda = n; g3.B = c->Cp; g3.ldb = n; g3.C = c->C; g3.ldc = N;
+  dgemm(la, g3);
+}
+
+// F = h + J + K for the current C; writes D, J, K, F, Ct and scal[0] = E.
+static void fock_build(rihf_ctx* c) {
+  LaCtx la = c->la();
+  const int N = c->N, NA = c->NA, no = c->nocc;
+  const size_t n2 = (size_t)N * N;
+  // Ct = sqrt(2) C[:, :nocc]; D = Ct Ct^T
+  copy_cols(la, c->C, N, N, no, std::sqrt(2.0), c->Ct);
+  GemmArgs gd;
+  gd.M = N; gd.N = N; gd.K = no; gd.A = c->Ct; gd.lda = no; gd.B = c->Ct; gd.ldb = no; gd.transB = true;
+  gd.C = c->D; gd.ldc = N;
+  dgemm(la, gd);
+  // RI-J: d = B vec(D); J = B^T d
+  gemv_rows(la, c->B, NA, (long long)n2, c->D, 1.0, c->dvec);
+  gemv_cols(la, c->B, NA, (long long)n2, c->dvec, 1.0, c->J);
+  // RI-K: Hb[P] = B^P Ct (N x nocc); K = -1/2 sum_P Hb[P] Hb[P]^T
+  GemmArgs gh;
+  gh.M = NA * N; gh.N = no; gh.K = N; gh.A = c->B; gh.lda = N; gh.B = c->Ct; gh.ldb = no; gh.C = c->Hb; gh.ldc = no;
+  dgemm(la, gh);
+  GemmArgs gk;
+  gk.M = N; gk.N = N; gk.K = no; gk.A = c->Hb; gk.lda = no; gk.sA = (long long)N * no;
+  gk.B = c->Hb; gk.ldb = no; gk.sB = (long long)N * no; gk.transB = true;
+  gk.C = c->K; gk.ldc = N; gk.batch = NA; gk.reduce_batch = true; gk.alpha = -0.5;
+  dgemm(la, gk);
+  add3(la, (int)n2, c->H, c->J, c->K, c->F);
+  energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->vnn, c->scal);
+  RIHF_LAUNCH_CHECK();
+  c->launches += 1;
+}
+
+// DIIS error X^T (F D S - S D F) X into Err (nind x nind) and scal[1] = max|e|.
+static void diis_error(rihf_ctx* c) {
+  LaCtx la = c->la();
+  const int N = c->N, n = c->nind;
+  GemmArgs g1;   // T1 = F D
+  g1.M = N; g1.N = N; g1.K = N; g1.A = c->F; g1.lda = N; g1.B = c->D; g1.ldb = N; g1.C = c->T1; g1.ldc = N;
+  dgemm(la, g1);
+  GemmArgs g2;   // T2 = T1 S
+  g2.M = N; g2.N = N; g2.K = N; g2.A = c->T1; g2.lda = N; g2.B = c->S; g2.ldb = N; g2.C = c->T2; g2.ldc = N;
+  dgemm(la, g2);
+  antisym(la, c->T2, c->T1, N);   // T1 = FDS - SDF
+  GemmArgs g3;   // T2 (N x n) = T1 Xo
+  g3.M = N; g3.N = n; g3.K = N; g3.A = c->T1; g3.lda = N; g3.B = c->Xo; g3.ldb = n; g3.C = c->T2; g3.ldc = n;
+  dgemm(la, g3);
+  GemmArgs g4;   // Err = Xo^T T2
+  g4.M = n; g4.N = n; g4.K = N; g4.A = c->Xo; g4.lda = n; g4.transA = true; g4.B = c->T2; g4.ldb = n;
+  g4.C = c->Err; g4.ldc = n;
+  dgemm(la, g4);
+  maxabs(la, n * n, c->Err, c->scal + 1);
+}
+
+int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, double* Dout, double* Cout,
+             double* epsout, int* iters) {
+  RIHF_API_BEGIN
+  if (!c) return RIHF_ERR_INVALID_ARG;
+  LaCtx la = c->la();
+  const int N = c->N, n = c->nind;
+  const size_t n2 = (size_t)N * N;
+  cudaStream_t s = c->stream;
+  c->timings[1] = c->timings[2] = 0.0;
+  if (guess == 1) {
+    if (!C_guess) return RIHF_ERR_INVALID_ARG;
+    RIHF_CUDA(cudaMemcpyAsync(c->C, C_guess, sizeof(double) * n2, cudaMemcpyHostToDevice, s));
+  } else if (guess == 2 && c->have_orbitals) {
+    // keep c->C from the previous converged SCF
+  } else {
+    diagonalise(c, c->H, false);
+  }
+  const int size = c->opt.diis_size;
+  double E = 0.0, Eold = 0.0, emax = 0.0;
+  int it = 0;
+  bool conv = false;
+  float ms = 0.f;
+  for (it = 1; it <= c->opt.max_iter; ++it) {
+    cudaEventRecord(c->ev[2], s);
+    fock_build(c);
+    cudaEventRecord(c->ev[3], s);
+    diis_error(c);
+    int slot = (it - 1) % size;
+    int m = std::min(it, size);
+    RIHF_CUDA(cudaMemcpyAsync(c->Fring + slot * n2, c->F, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
+    RIHF_CUDA(cudaMemcpyAsync(c->Ering + (size_t)slot * n * n, c->Err, sizeof(double) * n * n,
+                              cudaMemcpyDeviceToDevice, s));
+    double sc[2];
+    RIHF_CUDA(cudaMemcpyAsync(sc, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RIHF_CUDA(cudaStreamSynchronize(s));
+    E = sc[0];
+    emax = sc[1];
+    if (c->verbose) fprintf(stderr, "rihf_scf it %3d  E = %.12f  max|e| = %.3e  dE = %.3e\n", it, E, emax, E - Eold);
+    if (!std::isfinite(E)) throw RihfError(RIHF_ERR_NOT_CONVERGED, "SCF energy is not finite");
+    if (it > 1 && std::fabs(E - Eold) < c->opt.conv_e && emax < c->opt.conv_diis) {
+      conv = true;
+      cudaEventRecord(c->ev[4], s);
+      cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
+      c->timings[1] += ms;
+      break;
+    }
+    Eold = E;
+    diis_dots_kernel<<<m, 256, 0, s>>>(c->Ering, (long long)n * n, slot, m, c->Bdiis, 16);
+    RIHF_LAUNCH_CHECK();
+    const double* Fuse = c->F;
+    if (m >= 2) {
+      diis_solve_kernel<<<1, 32, 0, s>>>(c->Bdiis, 16, m, c->coef);
+      diis_extrap_kernel<<<std::max(1, std::min(ceil_div((long long)n2, 256), 8 * c->sms)), 256, 0, s>>>(
+          c->Fring, (long long)n2, m, c->coef, c->Fx);
+      RIHF_LAUNCH_CHECK();
+      Fuse = c->Fx;
+    }
+    c->launches += 3;
+    diagonalise(c, Fuse, true);
+    cudaEventRecord(c->ev[4], s);
+    RIHF_CUDA(cudaEventSynchronize(c->ev[4]));
+    cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
+    c->timings[1] += ms;
+    cudaEventElapsedTime(&ms, c->ev[3], c->ev[4]);
+    c->timings[2] += ms;
+  }
+  if (it > c->opt.max_iter) it = c->opt.max_iter;
+  // final orbitals diagonalise the last (unextrapolated) Fock matrix
+  diagonalise(c, c->F, true);
+  c->converged = conv;
+  c->have_orbitals = true;
+  RIHF_CUDA(cudaStreamSynchronize(s));
+  if (energy) *energy = E;
+  if (iters) *iters = it;
+  if (Dout) RIHF_CUDA(cudaMemcpy(Dout, c->D, sizeof(double) * n2, cudaMemcpyDeviceToHost));
+  if (Cout) RIHF_CUDA(cudaMemcpy(Cout, c->C, sizeof(double) * n2, cudaMemcpyDeviceToHost));
+  if (epsout) RIHF_CUDA(cudaMemcpy(epsout, c->eps, sizeof(double) * N, cudaMemcpyDeviceToHost));
+  if (!conv) {
+    g_last_error = "SCF did not converge in max_iter iterations (max|e| = " + std::to_string(emax) + ")";
+    return RIHF_ERR_NOT_CONVERGED;
+  }
+  return RIHF_OK;
+  RIHF_API_END
+}
+
+int rihf_gradient(rihf_ctx* c, double* grad) {
+  RIHF_API_BEGIN
+  if (!c || !grad) return RIHF_ERR_INVALID_ARG;
+  if (!c->converged) {
+    g_last_error = "rihf_gradient needs a converged rihf_scf on this context";
+    return RIHF_ERR_STATE;
+  }
+  LaCtx la = c->la();
+  IntegralCtx ic = c->ic();
+  const int N = c->N, NA = c->NA, no = c->nocc, nat = c->natoms;
+  const size_t n2 = (size_t)N * N;
+  cudaStream_t s = c->stream;
+  cudaEventRecord(c->ev[5], s);
+  // Ct, D from the final orbitals; W = Ct diag(eps_occ) Ct^T
+  copy_cols(la, c->C, N, N, no, std::sqrt(2.0), c->Ct);
+  GemmArgs gd;
+  gd.M = N; gd.N = N; gd.K = no; gd.A = c->Ct; gd.lda = no; gd.B = c->Ct; gd.ldb = no; gd.transB = true;
+  gd.C = c->D; gd.ldc = N;
+  dgemm(la, gd);
+  // W = 2 sum_i eps_i C_i C_i^T = 1/2 D F D at convergence (C~^T F C~ = 2 diag(eps_occ));
+  // this form needs no individual eigenvectors inside near-degenerate clusters
+  GemmArgs gf;
+  gf.M = N; gf.N = N; gf.K = N; gf.A = c->F; gf.lda = N; gf.B = c->D; gf.ldb = N; gf.C = c->T2; gf.ldc = N;
+  dgemm(la, gf);
+  GemmArgs gw;
+  gw.M = N; gw.N = N; gw.K = N; gw.A = c->D; gw.lda = N; gw.B = c->T2; gw.ldb = N; gw.C = c->W; gw.ldc = N;
+  gw.alpha = 0.5;
+  dgemm(la, gw);
+  // c = L^{-T} (B vec D)   (the paper's L^P)
+  gemv_rows(la, c->B, NA, (long long)n2, c->D, 1.0, c->dvec);
+  RIHF_CUDA(cudaMemcpyAsync(c->cvec, c->dvec, sizeof(double) * NA, cudaMemcpyDeviceToDevice, s));
+  trsm_lower(la, c->L, NA, c->cvec, 1, true, 0, c->trsm_tmp);
+  // Hb[P] = B^P Ct ; Bij[P] = Ct^T Hb[P]
+  GemmArgs gh;
+  gh.M = NA * N; gh.N = no; gh.K = N; gh.A = c->B; gh.lda = N; gh.B = c->Ct; gh.ldb = no; gh.C = c->Hb; gh.ldc = no;
+  dgemm(la, gh);
+  GemmArgs gb;
+  gb.M = no; gb.N = no; gb.K = N; gb.A = c->Ct; gb.lda = no; gb.transA = true;
+  gb.B = c->Hb; gb.ldb = no; gb.sB = (long long)N * no; gb.C = c->Bij; gb.ldc = no; gb.sC = (long long)no * no;
+  gb.batch = NA;
+  dgemm(la, gb);
+  // Xt = L^{-T} Bij  (NA x nocc^2): the paper's X^P_ij = sum_Q A^L_PQ B^Q_ij
+  RIHF_CUDA(cudaMemcpyAsync(c->Xt, c->Bij, sizeof(double) * (size_t)NA * no * no, cudaMemcpyDeviceToDevice, s));
+  trsm_lower(la, c->L, NA, c->Xt, (long long)no * no, true, 0, c->trsm_tmp);
+  // Z = c c^T - 1/2 Xt Xt^T
+  GemmArgs gz;
+  gz.M = NA; gz.N = NA; gz.K = no * no; gz.A = c->Xt; gz.lda = no * no; gz.B = c->Xt; gz.ldb = no * no;
+  gz.transB = true; gz.C = c->Zm; gz.ldc = NA; gz.alpha = -0.5;
+  dgemm(la, gz);
+  GemmArgs gc;
+  gc.M = NA; gc.N = NA; gc.K = 1; gc.A = c->cvec; gc.lda = 1; gc.B = c->cvec; gc.ldb = NA; gc.C = c->Zm; gc.ldc = NA;
+  gc.beta = 1.0;
+  dgemm(la, gc);
+  // Y[P] = D c_P - 1/2 Ct Xt[P] Ct^T ; G[P] = Xt[P] Ct^T (nocc x N)
+  GemmArgs gg;
+  gg.M = no; gg.N = N; gg.K = no; gg.A = c->Xt; gg.lda = no; gg.sA = (long long)no * no;
+  gg.B = c->Ct; gg.ldb = no; gg.transB = true; gg.C = c->G; gg.ldc = N; gg.sC = (long long)no * N; gg.batch = NA;
+  dgemm(la, gg);
+  outer_fill(la, c->cvec, NA, c->D, (long long)n2, c->Y);
+  GemmArgs gy;
+  gy.M = N; gy.N = N; gy.K = no; gy.A = c->Ct; gy.lda = no; gy.B = c->G; gy.ldb = N; gy.sB = (long long)no * N;
+  gy.C = c->Y; gy.ldc = N; gy.sC = (long long)n2; gy.batch = NA; gy.alpha = -0.5; gy.beta = 1.0;
+  dgemm(la, gy);
+  // fused derivative-integral contractions
+  RIHF_CUDA(cudaMemsetAsync(c->grad_parts, 0, sizeof(double) * 15 * nat, s));
+  double* g_one = c->grad_parts;
+  double* g_ovl = c->grad_parts + 3 * nat;
+  double* g_three = c->grad_parts + 6 * nat;
+  double* g_two = c->grad_parts + 9 * nat;
+  launch_grad_one_electron(ic, c->prim(), c->max_lp, nat, c->d_Z, c->d_xyz, c->D, c->W, g_one, g_ovl);
+  launch_grad_eri3(ic, c->prim(), c->aux(), c->d_pairs, c->npairs, c->max_lp, c->max_la, c->Y, g_three);
+  launch_grad_eri2(ic, c->aux(), c->max_la, c->Zm, g_two);
+  c->grad_parts_h.assign(15 * nat, 0.0);
+  RIHF_CUDA(cudaMemcpyAsync(c->grad_parts_h.data(), c->grad_parts, sizeof(double) * 12 * nat,
+                            cudaMemcpyDeviceToHost, s));
+  cudaEventRecord(c->ev[6], s);
+  RIHF_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev[5], c->ev[6]);
+  c->timings[3] = ms;
+  // nuclear repulsion gradient (host, O(natoms^2))
+  double* gnn = c->grad_parts_h.data() + 12 * nat;
+  for (int a = 0; a < nat; ++a)
+    for (int b = 0; b < nat; ++b) {
+      if (a == b) continue;
+      double r[3], r2 = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        r[d] = c->xyz[3 * a + d] - c->xyz[3 * b + d];
+        r2 += r[d] * r[d];
+      }
+      double f = c->Z[a] * c->Z[b] / (r2 * std::sqrt(r2));
+      for (int d = 0; d < 3; ++d) gnn[3 * a + d] -= f * r[d];
+    }
+  for (int i = 0; i < 3 * nat; ++i) {
+    double t = 0.0;
+    for (int p = 0; p < 5; ++p) t += c->grad_parts_h[p * 3 * nat + i];
+    grad[i] = t;
+  }
+  return RIHF_OK;
+  RIHF_API_END
+}
+
+int rihf_query(rihf_ctx* c, int* N, int* Naux, int* nocc, int* natoms) {
+  if (!c) return RIHF_ERR_INVALID_ARG;
+  if (N) *N = c->N;
+  if (Naux) *Naux = c->NA;
+  if (nocc) *nocc = c->nocc;
+  if (natoms) *natoms = c->natoms;
+  return RIHF_OK;
+}
+
+int rihf_get_matrix(rihf_ctx* c, int which, double* out) {
+  RIHF_API_BEGIN
+  if (!c || !out) return RIHF_ERR_INVALID_ARG;
+  const size_t n2 = (size_t)c->N * c->N, na2 = (size_t)c->NA * c->NA;
+  RIHF_CUDA(cudaStreamSynchronize(c->stream));
+  switch (which) {
+    case RIHF_MAT_S: RIHF_CUDA(cudaMemcpy(out, c->S, n2 * 8, cudaMemcpyDeviceToHost)); break;
+    case RIHF_MAT_H: RIHF_CUDA(cudaMemcpy(out, c->H, n2 * 8, cudaMemcpyDeviceToHost)); break;
+    case RIHF_MAT_J: RIHF_CUDA(cudaMemcpy(out, c->J, n2 * 8, cudaMemcpyDeviceToHost)); break;
+    case RIHF_MAT_K: RIHF_CUDA(cudaMemcpy(out, c->K, n2 * 8, cudaMemcpyDeviceToHost)); break;
+    case RIHF_MAT_F: RIHF_CUDA(cudaMemcpy(out, c->F, n2 * 8, cudaMemcpyDeviceToHost)); break;
+    case RIHF_MAT_D: RIHF_CUDA(cudaMemcpy(out, c->D, n2 * 8, cudaMemcpyDeviceToHost)); break;
+    case RIHF_MAT_A: RIHF_CUDA(cudaMemcpy(out, c->A, na2 * 8, cudaMemcpyDeviceToHost)); break;
+    case RIHF_MAT_LINV: {
+      // L^{-1} is not formed on the hot path; solve L X = I on request
+      if (!c->have_linv) {
+        LaCtx la = c->la();
+        identity(la, c->Linv, c->NA);
+        trsm_lower(la, c->L, c->NA, c->Linv, c->NA, false, 0, c->trsm_tmp);
+        RIHF_CUDA(cudaStreamSynchronize(c->stream));
+        c->have_linv = true;
+      }
+      RIHF_CUDA(cudaMemcpy(out, c->Linv, na2 * 8, cudaMemcpyDeviceToHost));
+      break;
+    }
+    case RIHF_MAT_B: RIHF_CUDA(cudaMemcpy(out, c->B, (size_t)c->NA * n2 * 8, cudaMemcpyDeviceToHost)); break;
+    case RIHF_MAT_T3: {
+      RIHF_CUDA(cudaMemcpy(out, c->T3, (size_t)c->NA * n2 * 8, cudaMemcpyDeviceToHost));
+      // the device copy holds the lower shell-pair triangle; mirror on the host
+      const int N = c->N;
+      for (int P = 0; P < c->NA; ++P) {
+        double* s = out + (size_t)P * n2;
+        for (const ShellPair& sp : c->pairs_h) {
+          if (sp.a == sp.b) continue;
+          int a0 = c->hp.ao[sp.a], b0 = c->hp.ao[sp.b];
+          int na = c->nf_h[c->hp.l[sp.a]], nb = c->nf_h[c->hp.l[sp.b]];
+          for (int i = 0; i < na; ++i)
+            for (int j = 0; j < nb; ++j) s[(size_t)(b0 + j) * N + a0 + i] = s[(size_t)(a0 + i) * N + b0 + j];
+        }
+      }
+      break;
+    }
+    case RIHF_MAT_GRAD_PARTS:
+      if (c->grad_parts_h.empty()) return RIHF_ERR_STATE;
+      std::memcpy(out, c->grad_parts_h.data(), sizeof(double) * 15 * c->natoms);
+      break;
+    default: return RIHF_ERR_INVALID_ARG;
+  }
+  return RIHF_OK;
+  RIHF_API_END
+}
+
+int rihf_screening_stats(rihf_ctx* c, int* kept, int* total) {
+  if (!c) return RIHF_ERR_INVALID_ARG;
+  if (kept) *kept = c->npairs;
+  if (total) *total = c->npairs_total;
+  return RIHF_OK;
+}
+
+int rihf_timings(rihf_ctx* c, double* out5) {
+  if (!c || !out5) return RIHF_ERR_INVALID_ARG;
+  for (int i = 0; i < 4; ++i) out5[i] = c->timings[i];
+  out5[4] = (double)c->launches;
+  return RIHF_OK;
+}
+
+int rihf_eigh(int n, const double* A, double* W, double* V, int device) {
+  RIHF_API_BEGIN
+  if (n <= 0 || n > 4096 || !A || !W || !V) return RIHF_ERR_INVALID_ARG;
+  RIHF_CUDA(cudaSetDevice(device));
+  cudaStream_t s;
+  RIHF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  size_t n2 = (size_t)n * n;
+  double *dA = nullptr, *dW = nullptr, *dV = nullptr, *ws = nullptr, *work = nullptr;
+  int* flag = nullptr;
+  size_t work_elems = std::max<size_t>((size_t)1 << 22, 8 * n2);
+  try {
+    dA = dalloc<double>(n2); dW = dalloc<double>(n); dV = dalloc<double>(n2);
+    ws = dalloc<double>(eig_workspace(n)); work = dalloc<double>(work_elems); flag = dalloc<int>(1);
+    RIHF_CUDA(cudaMemcpyAsync(dA, A, n2 * 8, cudaMemcpyHostToDevice, s));
+    LaCtx la;
+    la.stream = s; la.work = work; la.work_elems = work_elems; la.sms = sms; la.flag = flag;
+    eigh(la, dA, n, dW, dV, ws, 4, nullptr);
+    RIHF_CUDA(cudaMemcpyAsync(W, dW, n * 8, cudaMemcpyDeviceToHost, s));
+    RIHF_CUDA(cudaMemcpyAsync(V, dV, n2 * 8, cudaMemcpyDeviceToHost, s));
+    RIHF_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    cudaFree(dA); cudaFree(dW); cudaFree(dV); cudaFree(ws); cudaFree(work); cudaFree(flag);
+    cudaStreamDestroy(s);
+    throw;
+  }
+  cudaFree(dA); cudaFree(dW); cudaFree(dV); cudaFree(ws); cudaFree(work); cudaFree(flag);
+  cudaStreamDestroy(s);
+  return RIHF_OK;
+  RIHF_API_END
+}
+
+void rihf_destroy(rihf_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  for (auto& e : c->ev) cudaEventDestroy(e);
+  cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"
