@@ -148,6 +148,20 @@ int rihf_screening_stats(rihf_ctx* ctx, int* kept, int* total);
    library launched since the context was created ([4], as a double). */
 int rihf_timings(rihf_ctx* ctx, double* out5);
 
+/* The CUDA stream (cudaStream_t, returned as void*) on which the context
+   launches all of its work; callers may record CUDA events on it. */
+void* rihf_stream(rihf_ctx* ctx);
+
+/* Per-kernel tracing.  rihf_trace(ctx, 1) clears the statistics and starts
+   timing every instrumented launch with CUDA events on the context stream
+   (adds two event records per launch); rihf_trace(ctx, 0) stops.
+   rihf_trace_stats fills, for up to `max` traced kernels: names (48 chars
+   each, NUL-terminated), launches, total device milliseconds and the
+   algorithmic work of those launches (flops or bytes; kind: 0 = FP64 flops,
+   1 = HBM bytes, 2 = FP32/tensor flops).  Returns the number of kernels. */
+int rihf_trace(rihf_ctx* ctx, int enable);
+int rihf_trace_stats(rihf_ctx* ctx, int max, char* names, double* launches, double* ms, double* work, int* kind);
+
 /* The library's symmetric eigensolver (the diagonalisation step of Alg. 1) on
    one n x n host matrix A (row-major, symmetric): eigenvalues W (n, ascending)
    and eigenvectors V (n x n, column k = eigenvector k).  FP32 parallel Jacobi

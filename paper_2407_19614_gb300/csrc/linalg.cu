@@ -240,6 +240,34 @@ __global__ void zero_upper_kernel(double* A, int n) {
   }
 }
 
+// Panel of the blocked Cholesky: rows r >= k+b of A[:, k:k+b] solve
+// y L_kk^T = a_r by forward substitution (one thread per row).
+__global__ void __launch_bounds__(256) chol_panel_kernel(double* A, int n, int k, int b) {
+  __shared__ double l[CB][CB + 1];
+  for (int i = threadIdx.x; i < CB * CB; i += blockDim.x) {
+    int r = i / CB, c = i % CB;
+    l[r][c] = (r < b && c < b) ? A[(size_t)(k + r) * n + k + c] : 0.0;
+  }
+  __syncthreads();
+  for (int r = k + b + blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    double* row = A + (size_t)r * n + k;
+    double y[CB];
+#pragma unroll
+    for (int i = 0; i < CB; ++i) y[i] = i < b ? row[i] : 0.0;
+#pragma unroll
+    for (int i = 0; i < CB; ++i) {
+      if (i >= b) break;
+      double s = y[i];
+#pragma unroll
+      for (int q = 0; q < i; ++q) s -= l[i][q] * y[q];
+      y[i] = s / l[i][i];
+    }
+#pragma unroll
+    for (int i = 0; i < CB; ++i)
+      if (i < b) row[i] = y[i];
+  }
+}
+
 void cholesky(const LaCtx& la, double* A, int n, double* scratch) {
   for (int k = 0; k < n; k += CB) {
     int b = std::min(CB, n - k);
@@ -248,14 +276,10 @@ void cholesky(const LaCtx& la, double* A, int n, double* scratch) {
     count(la);
     int rest = n - k - b;
     if (rest <= 0) break;
-    // panel: A[k+b:, k:k+b] <- A[k+b:, k:k+b] * inv^T
-    GemmArgs g;
-    g.M = rest; g.N = b; g.K = b;
-    g.A = A + (size_t)(k + b) * n + k; g.lda = n;
-    g.B = scratch; g.ldb = CB; g.transB = true;
-    g.C = A + (size_t)(k + b) * n + k; g.ldc = n;
-    g.alpha = 1.0; g.beta = 0.0;
-    dgemm(la, g);
+    // panel: A[k+b:, k:k+b] <- A[k+b:, k:k+b] L_kk^{-T} by substitution
+    chol_panel_kernel<<<std::max(1, std::min(ceil_div(rest, 256), 4 * la.sms)), 256, 0, la.stream>>>(A, n, k, b);
+    RIHF_LAUNCH_CHECK();
+    count(la);
     // trailing update: A[k+b:, k+b:] -= panel panel^T
     GemmArgs u;
     u.M = rest; u.N = rest; u.K = b;
@@ -320,27 +344,62 @@ void tri_inverse_lower(const LaCtx& la, const double* L, double* X, int n, doubl
   }
 }
 
+// Substitution inside one diagonal block: every thread owns one column j of the
+// b x ncol slab X[k:k+b, :] and solves L_kk y = x (trans = 0) or L_kk^T y = x
+// (trans = 1) in registers; L_kk is staged in shared memory.  Substitution (not
+// a product with an explicit block inverse) keeps the accuracy of the classical
+// algorithm when the auxiliary functions of one atom make L_kk ill-conditioned.
+__global__ void __launch_bounds__(256) trsv_block_kernel(const double* __restrict__ L, int n, int k, int b,
+                                                         double* __restrict__ X, long long ncol, int trans,
+                                                         int symcols) {
+  __shared__ double l[CB][CB + 1];
+  for (int i = threadIdx.x; i < CB * CB; i += blockDim.x) {
+    int r = i / CB, c = i % CB;
+    l[r][c] = (r < b && c < b) ? L[(size_t)(k + r) * n + k + c] : 0.0;
+  }
+  __syncthreads();
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < ncol; j += (long long)gridDim.x * blockDim.x) {
+    if (symcols > 0 && (j % symcols) > (j / symcols)) continue;   // strict upper triangle: never used
+    double y[CB];
+#pragma unroll
+    for (int i = 0; i < CB; ++i) y[i] = i < b ? X[(size_t)(k + i) * ncol + j] : 0.0;
+    if (!trans) {
+#pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        if (i >= b) break;
+        double s = y[i];
+#pragma unroll
+        for (int q = 0; q < i; ++q) s -= l[i][q] * y[q];
+        y[i] = s / l[i][i];
+      }
+    } else {
+#pragma unroll
+      for (int i = CB - 1; i >= 0; --i) {
+        if (i >= b) continue;
+        double s = y[i];
+#pragma unroll
+        for (int q = i + 1; q < CB; ++q)
+          if (q < b) s -= l[q][i] * y[q];
+        y[i] = s / l[i][i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < CB; ++i)
+      if (i < b) X[(size_t)(k + i) * ncol + j] = y[i];
+  }
+}
+
 void trsm_lower(const LaCtx& la, const double* L, int n, double* X, long long ncol, bool trans, int symcols,
                 double* tmp) {
-  double* inv = tmp;
-  double* blk = tmp + CB * CB;
+  (void)tmp;
   const int nb = ceil_div(n, CB);
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((ncol + 255) / 256, 16LL * la.sms));
   for (int q = 0; q < nb; ++q) {
     const int kb = trans ? nb - 1 - q : q;
     const int k = kb * CB, b = std::min(CB, n - k);
-    potrf_diag_kernel<<<1, 32, 0, la.stream>>>(const_cast<double*>(L), n, k, b, inv, la.flag, 0);
+    trsv_block_kernel<<<blocks, 256, 0, la.stream>>>(L, n, k, b, X, ncol, trans ? 1 : 0, symcols);
     RIHF_LAUNCH_CHECK();
     count(la);
-    // blk = op(inv_kk) X[k:k+b, :]
-    GemmArgs g;
-    g.M = b; g.N = (int)ncol; g.K = b;
-    g.A = inv; g.lda = CB; g.transA = trans;
-    g.B = X + (size_t)k * ncol; g.ldb = (int)ncol;
-    g.C = blk; g.ldc = (int)ncol;
-    g.symcols = symcols;
-    dgemm(la, g);
-    RIHF_CUDA(cudaMemcpyAsync(X + (size_t)k * ncol, blk, sizeof(double) * b * ncol, cudaMemcpyDeviceToDevice,
-                              la.stream));
     GemmArgs u;
     u.N = (int)ncol; u.K = b;
     u.B = X + (size_t)k * ncol; u.ldb = (int)ncol;
@@ -374,11 +433,12 @@ __device__ void jacobi_f32(float* a, float* v, int n, int m, int max_sweeps, flo
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     // convergence test: off-diagonal vs diagonal Frobenius mass
     float off = 0.f, dia = 0.f;
-    for (int idx = tid; idx < m * m; idx += JT) {
-      int i = idx / m, j = idx % m;
-      float x = a[idx];
-      if (i == j) dia += x * x; else off += x * x;
-    }
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int i = warp; i < m; i += JT / 32)
+      for (int j = lane; j < m; j += 32) {
+        float x = a[i * m + j];
+        if (i == j) dia += x * x; else off += x * x;
+      }
     for (int o = 16; o > 0; o >>= 1) {
       off += __shfl_xor_sync(0xffffffffu, off, o);
       dia += __shfl_xor_sync(0xffffffffu, dia, o);
@@ -394,7 +454,8 @@ __device__ void jacobi_f32(float* a, float* v, int n, int m, int max_sweeps, flo
     __syncthreads();
     float so = red[64], sd = red[65];
     __syncthreads();
-    if (so <= 1e-12f * sd || so == 0.f) break;
+    // FP32 stops near its rounding floor; the FP64 refinement takes over
+    if (so <= 1e-10f * sd || so == 0.f) break;
     for (int r = 0; r < m - 1; ++r) {
       // pairs: (m-1, r) and ((r+k) mod (m-1), (r-k) mod (m-1)), k = 1..half-1
       for (int k = tid; k < half; k += JT) {
@@ -413,38 +474,41 @@ __device__ void jacobi_f32(float* a, float* v, int n, int m, int max_sweeps, flo
         pp[k] = p; qq[k] = q; cs[k] = c; sn[k] = s; tt[k] = t;
       }
       __syncthreads();
-      // two-sided update of all 2x2 blocks (k1, k2)
-      for (int idx = tid; idx < half * half; idx += JT) {
-        int k1 = idx / half, k2 = idx % half;
-        int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
-        float c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
-        if (k1 == k2) {
-          float apq = a[p1 * m + q1];
-          a[p1 * m + p1] -= tt[k1] * apq;
-          a[q1 * m + q1] += tt[k1] * apq;
-          a[p1 * m + q1] = 0.f;
-          a[q1 * m + p1] = 0.f;
-          continue;
+      // two-sided update of all 2x2 blocks (k1, k2): warp per k1, lane per k2
+      for (int k1 = warp; k1 < half; k1 += JT / 32) {
+        const int p1 = pp[k1], q1 = qq[k1];
+        const float c1 = cs[k1], s1 = sn[k1];
+        for (int k2 = lane; k2 < half; k2 += 32) {
+          const int p2 = pp[k2], q2 = qq[k2];
+          if (k1 == k2) {
+            float apq = a[p1 * m + q1];
+            a[p1 * m + p1] -= tt[k1] * apq;
+            a[q1 * m + q1] += tt[k1] * apq;
+            a[p1 * m + q1] = 0.f;
+            a[q1 * m + p1] = 0.f;
+            continue;
+          }
+          const float c2 = cs[k2], s2 = sn[k2];
+          float app = a[p1 * m + p2], apq = a[p1 * m + q2], aqp = a[q1 * m + p2], aqq = a[q1 * m + q2];
+          // right rotation (columns p2, q2)
+          float xp = c2 * app - s2 * apq, xq = s2 * app + c2 * apq;
+          float yp = c2 * aqp - s2 * aqq, yq = s2 * aqp + c2 * aqq;
+          // left rotation (rows p1, q1)
+          a[p1 * m + p2] = c1 * xp - s1 * yp;
+          a[p1 * m + q2] = c1 * xq - s1 * yq;
+          a[q1 * m + p2] = s1 * xp + c1 * yp;
+          a[q1 * m + q2] = s1 * xq + c1 * yq;
         }
-        float app = a[p1 * m + p2], apq = a[p1 * m + q2], aqp = a[q1 * m + p2], aqq = a[q1 * m + q2];
-        // right rotation (columns p2, q2)
-        float xp = c2 * app - s2 * apq, xq = s2 * app + c2 * apq;
-        float yp = c2 * aqp - s2 * aqq, yq = s2 * aqp + c2 * aqq;
-        // left rotation (rows p1, q1)
-        a[p1 * m + p2] = c1 * xp - s1 * yp;
-        a[p1 * m + q2] = c1 * xq - s1 * yq;
-        a[q1 * m + p2] = s1 * xp + c1 * yp;
-        a[q1 * m + q2] = s1 * xq + c1 * yq;
       }
       // eigenvectors: V <- V J
-      for (int idx = tid; idx < n * half; idx += JT) {
-        int i = idx / half, k = idx % half;
-        int p = pp[k], q = qq[k];
-        float c = cs[k], s = sn[k];
-        float vp = v[i * m + p], vq = v[i * m + q];
-        v[i * m + p] = c * vp - s * vq;
-        v[i * m + q] = s * vp + c * vq;
-      }
+      for (int i = warp; i < n; i += JT / 32)
+        for (int k = lane; k < half; k += 32) {
+          int p = pp[k], q = qq[k];
+          float c = cs[k], s = sn[k];
+          float vp = v[i * m + p], vq = v[i * m + q];
+          v[i * m + p] = c * vp - s * vq;
+          v[i * m + q] = s * vp + c * vq;
+        }
       __syncthreads();
     }
   }
@@ -469,6 +533,92 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ A
   jacobi_f32(a, V, n, m, max_sweeps, cs, sn, tt, pp, qq, red);
   __syncthreads();
   for (int i = threadIdx.x; i < m; i += JT) W[i] = a[i * m + i];
+}
+
+// One-sided (Hestenes) Jacobi in FP32, one CTA: with B = A + sigma I positive
+// definite (sigma from a Gershgorin bound), column rotations U <- U J drive the
+// columns of U = B V to mutual orthogonality; then v_j = u_j / |u_j| and
+// lambda_j = |u_j| - sigma.  Only U (n x n, column-major, shared memory when it
+// fits) is stored; a warp owns one column pair per round (round-robin pairing),
+// its dot products reduced with shuffles.
+__global__ void __launch_bounds__(JT) jacobi1s_kernel(const double* __restrict__ A, int n, int m, float* gU, float* V,
+                                                      float* W, int use_smem, int max_sweeps) {
+  extern __shared__ float sm[];
+  __shared__ float red[32];
+  __shared__ int notconv;
+  float* U = use_smem ? sm : gU;   // column j at U[j*n .. j*n+n)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // Gershgorin shift: sigma = max_i sum_j |A_ij| (+ a margin) makes A + sigma I PD
+  float g = 0.f;
+  for (int i = warp; i < n; i += JT / 32) {
+    float s = 0.f;
+    for (int j = lane; j < n; j += 32) s += fabsf((float)A[(size_t)i * n + j]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    g = fmaxf(g, s);
+  }
+  if (lane == 0) red[warp] = g;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < JT / 32; ++w) t = fmaxf(t, red[w]);
+    red[0] = 1.05f * t + 1e-20f;
+  }
+  __syncthreads();
+  const float sigma = red[0];
+  for (int j = warp; j < n; j += JT / 32)
+    for (int i = lane; i < n; i += 32) U[(size_t)j * n + i] = (float)A[(size_t)i * n + j] + (i == j ? sigma : 0.f);
+  __syncthreads();
+  const int half = m / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) notconv = 0;
+    __syncthreads();
+    for (int r = 0; r < m - 1; ++r) {
+      for (int k = warp; k < half; k += JT / 32) {
+        int p, q;
+        if (k == 0) { p = r; q = m - 1; }
+        else { p = (r + k) % (m - 1); q = (r - k + (m - 1)) % (m - 1); }
+        if (p >= n || q >= n) continue;   // padding column
+        float* up = U + (size_t)p * n;
+        float* uq = U + (size_t)q * n;
+        float a = 0.f, b = 0.f, c = 0.f;
+        for (int i = lane; i < n; i += 32) {
+          float x = up[i], y = uq[i];
+          a = fmaf(x, x, a);
+          b = fmaf(y, y, b);
+          c = fmaf(x, y, c);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        if (fabsf(c) <= 2e-6f * sqrtf(a * b)) continue;
+        if (lane == 0) notconv = 1;
+        float zeta = (b - a) / (2.f * c);
+        float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        float cs = rsqrtf(1.f + t * t), sn = cs * t;
+        for (int i = lane; i < n; i += 32) {
+          float x = up[i], y = uq[i];
+          up[i] = cs * x - sn * y;
+          uq[i] = sn * x + cs * y;
+        }
+      }
+      __syncthreads();
+    }
+    if (!notconv) break;
+    __syncthreads();
+  }
+  // eigenpairs: v_j = u_j / |u_j|, lambda_j = |u_j| - sigma; V row-major n x m
+  for (int j = warp; j < n; j += JT / 32) {
+    const float* u = U + (size_t)j * n;
+    float s = 0.f;
+    for (int i = lane; i < n; i += 32) s = fmaf(u[i], u[i], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    float nrm = sqrtf(s);
+    float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+    for (int i = lane; i < n; i += 32) V[(size_t)i * m + j] = u[i] * inv;
+    if (lane == 0) W[j] = nrm - sigma;
+  }
 }
 
 // Sort eigenpairs ascending (rank sort) and expand to FP64: X[:, rank] = V[:, i].
@@ -561,9 +711,46 @@ static int elem_blocks(const LaCtx& la, long long n) {
   return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 8LL * la.sms));
 }
 
+// Ascending reorder of FP64 eigenpairs: Vout[:, rank(i)] = V[:, i], Wout[rank(i)] = lam[i].
+__global__ void eig_sort64_kernel(const double* __restrict__ V, const double* __restrict__ lam, int n, double* Vout,
+                                  double* Wout) {
+  __shared__ int rank[4096];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double wi = lam[i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) {
+      double wj = lam[j];
+      if (wj < wi || (wj == wi && j < i)) ++r;
+    }
+    rank[i] = r;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    int row = idx / n, i = idx % n;
+    Vout[(size_t)row * n + rank[i]] = V[(size_t)row * n + i];
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) Wout[rank[i]] = lam[i];
+}
+
 void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double* ws, int refine,
-          const double* Vguess) {
+          const double* Vguess, bool skip_jacobi) {
   int m = n + (n & 1);
+  if (skip_jacobi && Vguess && refine > 0) {
+    // Late SCF iterations: the previous eigenvectors are already close, so the
+    // FP64 refinement alone converges (quadratically) without a Jacobi pass.
+    double* d = ws + ((size_t)m * m + (size_t)n * m + m + 1) / 2;
+    double* Vs = d + 4 * (size_t)n * n;   // the XE slot of the workspace
+    double* lam = d + 6 * (size_t)n * n;
+    RIHF_CUDA(cudaMemcpyAsync(V, Vguess, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, la.stream));
+    eigh(la, A, n, W, V, ws, -refine, nullptr, false);
+    eig_sort64_kernel<<<1, 1024, 0, la.stream>>>(V, lam, n, Vs, W);
+    RIHF_LAUNCH_CHECK();
+    count(la);
+    RIHF_CUDA(cudaMemcpyAsync(V, Vs, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, la.stream));
+    return;
+  }
+  const bool refine_only = refine < 0;   // V already holds the starting vectors
+  if (refine_only) refine = -refine;
   float* fA = reinterpret_cast<float*>(ws);
   float* fV = fA + (size_t)m * m;
   float* fW = fV + (size_t)n * m;
@@ -577,6 +764,7 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
   double* lam = Ag + (size_t)n * n;
   double* sums = lam + n;
   const double* Ain = A;
+  if (!refine_only) {
   if (Vguess) {
     // warm start: diagonalise Vg^T A Vg and rotate back
     GemmArgs g1;
@@ -588,10 +776,11 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
     dgemm(la, g2);
     Ain = Ag;
   }
-  size_t smem = (size_t)m * m * sizeof(float);
-  int use_smem = smem <= 160 * 1024 ? 1 : 0;
-  if (use_smem) RIHF_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  jacobi_kernel<<<1, JT, use_smem ? smem : 0, la.stream>>>(Ain, n, m, fA, fV, fW, use_smem, 14);
+  size_t smem = (size_t)n * n * sizeof(float);
+  int use_smem = smem <= 215 * 1024 ? 1 : 0;
+  if (use_smem)
+    RIHF_CUDA(cudaFuncSetAttribute(jacobi1s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  jacobi1s_kernel<<<1, JT, use_smem ? smem : 0, la.stream>>>(Ain, n, m, fA, fV, fW, use_smem, 20);
   RIHF_LAUNCH_CHECK();
   count(la);
   eig_sort_kernel<<<1, 1024, 0, la.stream>>>(fV, fW, n, m, V, W);
@@ -604,6 +793,7 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
     dgemm(la, g);
     RIHF_CUDA(cudaMemcpyAsync(V, XE, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, la.stream));
   }
+  }   // !refine_only
   for (int it = 0; it < refine; ++it) {
     GemmArgs gr;   // R = V^T V
     gr.M = n; gr.N = n; gr.K = n; gr.A = V; gr.lda = n; gr.transA = true; gr.B = V; gr.ldb = n; gr.C = R; gr.ldc = n;

@@ -64,8 +64,9 @@ void trsm_lower(const LaCtx& la, const double* L, int n, double* X, long long nc
 // Jacobi in one CTA, then Ogita-Aishima refinement in FP64 (`refine` steps).
 // ws must hold eig_workspace(n) doubles.
 size_t eig_workspace(int n);
+// skip_jacobi: start the refinement from Vguess directly (late SCF iterations).
 void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double* ws, int refine,
-          const double* Vguess);
+          const double* Vguess, bool skip_jacobi = false);
 
 // Elementwise / reductions.
 void axpby(const LaCtx& la, int n, double a, const double* x, double b, const double* y, double* out);

@@ -287,9 +287,87 @@ __global__ void energy_kernel(const double* __restrict__ D, const double* __rest
   }
 }
 
+// ============================================================ tracing
+
+struct TraceStat {
+  long long launches = 0;
+  double ms = 0.0, work = 0.0;
+  int kind = 0;
+};
+struct TracePending {
+  std::string name;
+  double work;
+  int kind;
+  cudaEvent_t a, b;
+};
+
+struct Tracer {
+  bool on = false;
+  std::vector<std::pair<std::string, TraceStat>> stats;
+  std::vector<TracePending> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (pool.empty()) {
+      cudaEvent_t e;
+      RIHF_CUDA(cudaEventCreate(&e));
+      return e;
+    }
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  // Resolve recorded pairs (the stream must be idle).
+  void flush() {
+    for (auto& p : pending) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, p.a, p.b);
+      TraceStat* st = nullptr;
+      for (auto& kv : stats)
+        if (kv.first == p.name) st = &kv.second;
+      if (!st) {
+        stats.push_back({p.name, TraceStat()});
+        st = &stats.back().second;
+      }
+      st->launches += 1;
+      st->ms += ms;
+      st->work += p.work;
+      st->kind = p.kind;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  ~Tracer() {
+    for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+// RAII scope: events around one instrumented launch (or fused launch group).
+struct TraceScope {
+  Tracer* t;
+  cudaStream_t s;
+  TracePending p;
+  TraceScope(Tracer& tr, cudaStream_t st, const char* name, double work, int kind) : t(tr.on ? &tr : nullptr), s(st) {
+    if (!t) return;
+    p.name = name;
+    p.work = work;
+    p.kind = kind;
+    p.a = t->get();
+    p.b = t->get();
+    cudaEventRecord(p.a, s);
+  }
+  ~TraceScope() {
+    if (!t) return;
+    cudaEventRecord(p.b, s);
+    t->pending.push_back(p);
+  }
+};
+
 // ============================================================ context
 
 struct rihf_ctx {
+  Tracer tracer;
   rihf_options opt;
   int natoms = 0, nelec = 0, nocc = 0, N = 0, NA = 0, nind = 0;
   int max_lp = 0, max_la = 0;
@@ -351,6 +429,7 @@ struct rihf_ctx {
   bool have_orbitals = false;
   bool verbose = getenv("RIHF_VERBOSE") != nullptr;
   bool have_linv = false;
+  double last_err = 1.0;   // max|e| of the latest SCF iteration
   double timings[5] = {0, 0, 0, 0, 0};
   cudaEvent_t ev[8];
 
@@ -433,23 +512,29 @@ static void compute_geometry(rihf_ctx* c) {
   RIHF_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
   cudaEventRecord(c->ev[0], s);
   DevShells P = c->prim(), X = c->aux();
-  launch_one_electron(ic, P, c->max_lp, c->natoms, c->d_Z, c->d_xyz, c->S, c->Tk, c->V);
+  { TraceScope t(c->tracer, s, "one_electron_kernel (S,T,V)", 3.0 * N * N * 8, 1);
+    launch_one_electron(ic, P, c->max_lp, c->natoms, c->d_Z, c->d_xyz, c->S, c->Tk, c->V); }
   axpby(la, N * N, 1.0, c->Tk, 1.0, c->V, c->H);
   // metric, Cholesky, L^{-1}
-  launch_eri2(ic, X, c->max_la, c->A);
+  { TraceScope t(c->tracer, s, "eri2_kernel (P|Q)", (double)NA * NA * 8, 1);
+    launch_eri2(ic, X, c->max_la, c->A); }
   RIHF_CUDA(cudaMemcpyAsync(c->L, c->A, sizeof(double) * NA * NA, cudaMemcpyDeviceToDevice, s));
-  cholesky(la, c->L, NA, c->scratch);
+  { TraceScope t(c->tracer, s, "cholesky A=LL^T", (double)NA * NA * NA / 3.0, 0);
+    cholesky(la, c->L, NA, c->scratch); }
   c->have_linv = false;
   // (mu nu|P) for shell pairs a >= b, then B = L^{-1} T (Eq. biap with A^L = L^{-T})
   // by blocked forward substitution on the lower-triangle columns; an explicit
   // L^{-1} product loses accuracy when cond(A) reaches 1e9 (diffuse auxiliary sets)
   RIHF_CUDA(cudaMemsetAsync(c->T3, 0, sizeof(double) * (size_t)NA * N * N, s));
-  launch_eri3(ic, P, X, c->d_pairs, c->npairs, c->max_lp, c->max_la, c->T3);
+  { TraceScope t(c->tracer, s, "eri3_kernel (mu nu|P)", (double)NA * N * (N + 1) / 2 * 8, 1);
+    launch_eri3(ic, P, X, c->d_pairs, c->npairs, c->max_lp, c->max_la, c->T3); }
   RIHF_CUDA(cudaMemcpyAsync(c->B, c->T3, sizeof(double) * (size_t)NA * N * N, cudaMemcpyDeviceToDevice, s));
-  trsm_lower(la, c->L, NA, c->B, (long long)N * N, false, N, c->trsm_tmp);
+  { TraceScope t(c->tracer, s, "fit trsm B=L^-1 T", (double)NA * NA * N * (N + 1) / 2, 0);
+    trsm_lower(la, c->L, NA, c->B, (long long)N * N, false, N, c->trsm_tmp); }
   symmetrize_lower(la, c->B, N, NA);
   // canonical orthogonaliser from S
-  eigh(la, c->S, N, c->Sw, c->Sv, c->eigws, 4, nullptr);
+  { TraceScope t(c->tracer, s, "eigh S", 0.0, 0);
+    eigh(la, c->S, N, c->Sw, c->Sv, c->eigws, 4, nullptr); }
   std::vector<double> sw(N);
   RIHF_CUDA(cudaMemcpyAsync(sw.data(), c->Sw, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
   int flag = 0;
@@ -467,7 +552,8 @@ static void compute_geometry(rihf_ctx* c) {
     // the SCF fixed point does not depend on the choice of orthogonaliser
     RIHF_CUDA(cudaMemcpyAsync(c->T2, c->S, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, s));
     cholesky(la, c->T2, N, c->scratch);
-    tri_inverse_lower(la, c->T2, c->T1, N, c->scratch);
+    identity(la, c->T1, N);
+    trsm_lower(la, c->T2, N, c->T1, N, false, 0, c->trsm_tmp);
     transpose(la, c->T1, N, N, c->Xo);
   } else {
     std::vector<double> invs(nind);
@@ -499,6 +585,7 @@ static void compute_geometry(rihf_ctx* c) {
   }
   cudaEventRecord(c->ev[1], s);
   RIHF_CUDA(cudaStreamSynchronize(s));
+  c->tracer.flush();
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
   c->timings[0] = ms;
@@ -679,7 +766,30 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
   g2.C = c->Fp; g2.ldc = n;
   dgemm(la, g2);
   RIHF_CUDA(cudaMemsetAsync(c->eps, 0, sizeof(double) * N, c->stream));
-  eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, (warm && c->have_cprev) ? c->Cprev : nullptr);
+  {
+    const bool use_prev = warm && c->have_cprev;
+    const bool skip = use_prev && c->last_err < 1e-3;
+    TraceScope t(c->tracer, c->stream, skip ? "eigh F' (refine only)" : "eigh F' (jacobi+refine)", 0.0, 0);
+    eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, use_prev ? c->Cprev : nullptr, skip);
+    if (skip) {
+      // guard: the refinement from the previous vectors must end orthonormal;
+      // otherwise redo the step with a Jacobi pass
+      GemmArgs go;
+      go.M = n; go.N = n; go.K = n; go.A = c->Cp; go.lda = n; go.transA = true; go.B = c->Cp; go.ldb = n;
+      go.C = c->T2; go.ldc = n;
+      dgemm(la, go);
+      identity(la, c->T1, n);
+      axpby(la, n * n, 1.0, c->T2, -1.0, c->T1, c->T2);
+      maxabs(la, n * n, c->T2, c->scal + 2);
+      double dev = 0.0;
+      RIHF_CUDA(cudaMemcpyAsync(&dev, c->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      RIHF_CUDA(cudaStreamSynchronize(c->stream));
+      if (!(dev < 1e-8)) {
+        if (c->verbose || getenv("RIHF_VERBOSE")) fprintf(stderr, "rihf: refine-only eigh deviation %.3e, redo\n", dev);
+        eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, c->Cprev, false);
+      }
+    }
+  }
   RIHF_CUDA(cudaMemcpyAsync(c->Cprev, c->Cp, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, c->stream));
   c->have_cprev = true;
   // C (N x N): first n columns = Xo Cp, rest zero
@@ -701,17 +811,21 @@ static void fock_build(rihf_ctx* c) {
   gd.C = c->D; gd.ldc = N;
   dgemm(la, gd);
   // RI-J: d = B vec(D); J = B^T d
-  gemv_rows(la, c->B, NA, (long long)n2, c->D, 1.0, c->dvec);
-  gemv_cols(la, c->B, NA, (long long)n2, c->dvec, 1.0, c->J);
+  { TraceScope t(c->tracer, c->stream, "RI-J d=B.D (gemv_rows)", (double)NA * n2 * 8, 1);
+    gemv_rows(la, c->B, NA, (long long)n2, c->D, 1.0, c->dvec); }
+  { TraceScope t(c->tracer, c->stream, "RI-J J=B^T d (gemv_cols)", (double)NA * n2 * 8, 1);
+    gemv_cols(la, c->B, NA, (long long)n2, c->dvec, 1.0, c->J); }
   // RI-K: Hb[P] = B^P Ct (N x nocc); K = -1/2 sum_P Hb[P] Hb[P]^T
   GemmArgs gh;
   gh.M = NA * N; gh.N = no; gh.K = N; gh.A = c->B; gh.lda = N; gh.B = c->Ct; gh.ldb = no; gh.C = c->Hb; gh.ldc = no;
-  dgemm(la, gh);
+  { TraceScope t(c->tracer, c->stream, "RI-K H=B C~ (dgemm)", 2.0 * NA * n2 * no, 0);
+    dgemm(la, gh); }
   GemmArgs gk;
   gk.M = N; gk.N = N; gk.K = no; gk.A = c->Hb; gk.lda = no; gk.sA = (long long)N * no;
   gk.B = c->Hb; gk.ldb = no; gk.sB = (long long)N * no; gk.transB = true;
   gk.C = c->K; gk.ldc = N; gk.batch = NA; gk.reduce_batch = true; gk.alpha = -0.5;
-  dgemm(la, gk);
+  { TraceScope t(c->tracer, c->stream, "RI-K K=-1/2 sum H H^T (dgemm)", 2.0 * NA * n2 * no, 0);
+    dgemm(la, gk); }
   add3(la, (int)n2, c->H, c->J, c->K, c->F);
   energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->vnn, c->scal);
   RIHF_LAUNCH_CHECK();
@@ -752,7 +866,25 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
     if (!C_guess) return RIHF_ERR_INVALID_ARG;
     RIHF_CUDA(cudaMemcpyAsync(c->C, C_guess, sizeof(double) * n2, cudaMemcpyHostToDevice, s));
   } else if (guess == 2 && c->have_orbitals) {
-    // keep c->C from the previous converged SCF
+    // previous converged orbitals (the paper's AIMD guess, Sec. 3.3); after a
+    // geometry change they are re-orthonormalised against the new overlap:
+    // M = Co^T S Co = L_M L_M^T, Co <- Co L_M^{-T} (Cholesky / Gram-Schmidt,
+    // stable however far the nuclei moved)
+    const int no = c->nocc;
+    copy_cols(la, c->C, N, N, no, 1.0, c->Ct);
+    GemmArgs g1;   // T1 (N x no) = S Co
+    g1.M = N; g1.N = no; g1.K = N; g1.A = c->S; g1.lda = N; g1.B = c->Ct; g1.ldb = no; g1.C = c->T1; g1.ldc = no;
+    dgemm(la, g1);
+    GemmArgs g2;   // T2 (no x no) = Co^T T1
+    g2.M = no; g2.N = no; g2.K = N; g2.A = c->Ct; g2.lda = no; g2.transA = true; g2.B = c->T1; g2.ldb = no;
+    g2.C = c->T2; g2.ldc = no;
+    dgemm(la, g2);
+    cholesky(la, c->T2, no, c->scratch);
+    transpose(la, c->Ct, N, no, c->T1);                        // T1 = Co^T (no x N)
+    trsm_lower(la, c->T2, no, c->T1, N, false, 0, c->trsm_tmp);   // L_M^{-1} Co^T
+    transpose(la, c->T1, no, N, c->Ct);
+    RIHF_CUDA(cudaMemcpy2DAsync(c->C, N * sizeof(double), c->Ct, no * sizeof(double), no * sizeof(double), N,
+                                cudaMemcpyDeviceToDevice, s));
   } else {
     diagonalise(c, c->H, false);
   }
@@ -776,7 +908,8 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
     RIHF_CUDA(cudaStreamSynchronize(s));
     E = sc[0];
     emax = sc[1];
-    if (c->verbose) fprintf(stderr, "rihf_scf it %3d  E = %.12f  max|e| = %.3e  dE = %.3e\n", it, E, emax, E - Eold);
+    c->last_err = emax;
+    if (c->verbose || getenv("RIHF_VERBOSE")) fprintf(stderr, "rihf_scf it %3d  E = %.12f  max|e| = %.3e  dE = %.3e\n", it, E, emax, E - Eold);
     if (!std::isfinite(E)) throw RihfError(RIHF_ERR_NOT_CONVERGED, "SCF energy is not finite");
     if (it > 1 && std::fabs(E - Eold) < c->opt.conv_e && emax < c->opt.conv_diis) {
       conv = true;
@@ -811,6 +944,7 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   c->converged = conv;
   c->have_orbitals = true;
   RIHF_CUDA(cudaStreamSynchronize(s));
+  c->tracer.flush();
   if (energy) *energy = E;
   if (iters) *iters = it;
   if (Dout) RIHF_CUDA(cudaMemcpy(Dout, c->D, sizeof(double) * n2, cudaMemcpyDeviceToHost));
@@ -886,21 +1020,26 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   GemmArgs gy;
   gy.M = N; gy.N = N; gy.K = no; gy.A = c->Ct; gy.lda = no; gy.B = c->G; gy.ldb = N; gy.sB = (long long)no * N;
   gy.C = c->Y; gy.ldc = N; gy.sC = (long long)n2; gy.batch = NA; gy.alpha = -0.5; gy.beta = 1.0;
-  dgemm(la, gy);
+  { TraceScope t(c->tracer, s, "grad Y=Dc-1/2 C~XC~^T (dgemm)", 2.0 * NA * n2 * no, 0);
+    dgemm(la, gy); }
   // fused derivative-integral contractions
   RIHF_CUDA(cudaMemsetAsync(c->grad_parts, 0, sizeof(double) * 15 * nat, s));
   double* g_one = c->grad_parts;
   double* g_ovl = c->grad_parts + 3 * nat;
   double* g_three = c->grad_parts + 6 * nat;
   double* g_two = c->grad_parts + 9 * nat;
-  launch_grad_one_electron(ic, c->prim(), c->max_lp, nat, c->d_Z, c->d_xyz, c->D, c->W, g_one, g_ovl);
-  launch_grad_eri3(ic, c->prim(), c->aux(), c->d_pairs, c->npairs, c->max_lp, c->max_la, c->Y, g_three);
-  launch_grad_eri2(ic, c->aux(), c->max_la, c->Zm, g_two);
+  { TraceScope t(c->tracer, s, "grad_one_electron_kernel", 0.0, 0);
+    launch_grad_one_electron(ic, c->prim(), c->max_lp, nat, c->d_Z, c->d_xyz, c->D, c->W, g_one, g_ovl); }
+  { TraceScope t(c->tracer, s, "grad_eri3_kernel (fused d(mu nu|P) . Y)", (double)NA * N * (N + 1) / 2 * 8, 1);
+    launch_grad_eri3(ic, c->prim(), c->aux(), c->d_pairs, c->npairs, c->max_lp, c->max_la, c->Y, g_three); }
+  { TraceScope t(c->tracer, s, "grad_eri2_kernel (fused d(P|Q) . Z)", (double)NA * NA * 8, 1);
+    launch_grad_eri2(ic, c->aux(), c->max_la, c->Zm, g_two); }
   c->grad_parts_h.assign(15 * nat, 0.0);
   RIHF_CUDA(cudaMemcpyAsync(c->grad_parts_h.data(), c->grad_parts, sizeof(double) * 12 * nat,
                             cudaMemcpyDeviceToHost, s));
   cudaEventRecord(c->ev[6], s);
   RIHF_CUDA(cudaStreamSynchronize(s));
+  c->tracer.flush();
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev[5], c->ev[6]);
   c->timings[3] = ms;
@@ -999,6 +1138,37 @@ int rihf_timings(rihf_ctx* c, double* out5) {
   for (int i = 0; i < 4; ++i) out5[i] = c->timings[i];
   out5[4] = (double)c->launches;
   return RIHF_OK;
+}
+
+void* rihf_stream(rihf_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+int rihf_trace(rihf_ctx* c, int enable) {
+  if (!c) return RIHF_ERR_INVALID_ARG;
+  cudaStreamSynchronize(c->stream);
+  c->tracer.flush();
+  if (enable) c->tracer.stats.clear();
+  c->tracer.on = enable != 0;
+  return RIHF_OK;
+}
+
+int rihf_trace_stats(rihf_ctx* c, int max, char* names, double* launches, double* ms, double* work, int* kind) {
+  if (!c || max < 0) return RIHF_ERR_INVALID_ARG;
+  cudaStreamSynchronize(c->stream);
+  c->tracer.flush();
+  int n = 0;
+  for (auto& kv : c->tracer.stats) {
+    if (n >= max) break;
+    if (names) {
+      std::strncpy(names + 48 * n, kv.first.c_str(), 47);
+      names[48 * n + 47] = 0;
+    }
+    if (launches) launches[n] = (double)kv.second.launches;
+    if (ms) ms[n] = kv.second.ms;
+    if (work) work[n] = kv.second.work;
+    if (kind) kind[n] = kv.second.kind;
+    ++n;
+  }
+  return (int)std::min<size_t>(c->tracer.stats.size(), (size_t)std::max(max, 0)) >= 0 ? n : n;
 }
 
 int rihf_eigh(int n, const double* A, double* W, double* V, int device) {

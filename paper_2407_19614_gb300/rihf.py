@@ -42,7 +42,7 @@ class rihf_options(ctypes.Structure):
 
 EXPORTS = ["rihf_default_options", "rihf_setup", "rihf_update_geometry", "rihf_scf", "rihf_gradient",
            "rihf_query", "rihf_get_matrix", "rihf_screening_stats", "rihf_timings", "rihf_strerror",
-           "rihf_last_error", "rihf_destroy", "rihf_eigh"]
+           "rihf_last_error", "rihf_destroy", "rihf_eigh", "rihf_stream", "rihf_trace", "rihf_trace_stats"]
 
 _lib = None
 
@@ -71,6 +71,12 @@ def load(path: str = LIB_PATH):
     lib.rihf_strerror.restype = ctypes.c_char_p
     lib.rihf_last_error.argtypes = []
     lib.rihf_last_error.restype = ctypes.c_char_p
+    lib.rihf_stream.argtypes = [P]
+    lib.rihf_stream.restype = P
+    lib.rihf_trace.argtypes = [P, I]
+    lib.rihf_trace.restype = I
+    lib.rihf_trace_stats.argtypes = [P, I, P, P, P, P, P]
+    lib.rihf_trace_stats.restype = I
     lib.rihf_eigh.argtypes = [I, P, P, P, I]
     lib.rihf_eigh.restype = I
     lib.rihf_destroy.argtypes = [P]
@@ -182,6 +188,25 @@ class Context:
         k, t = ctypes.c_int(), ctypes.c_int()
         _check(self.lib.rihf_screening_stats(self.h, ctypes.byref(k), ctypes.byref(t)))
         return k.value, t.value
+
+    def stream(self) -> int:
+        """cudaStream_t of the context (as an integer handle)."""
+        return int(self.lib.rihf_stream(self.h) or 0)
+
+    def trace(self, enable: bool):
+        _check(self.lib.rihf_trace(self.h, int(bool(enable))))
+
+    def trace_stats(self, max_kernels=64):
+        names = ctypes.create_string_buffer(48 * max_kernels)
+        la, ms, wk = np.zeros(max_kernels), np.zeros(max_kernels), np.zeros(max_kernels)
+        kind = np.zeros(max_kernels, dtype=np.int32)
+        n = self.lib.rihf_trace_stats(self.h, max_kernels, names, _p(la), _p(ms), _p(wk), _p(kind))
+        out = []
+        for i in range(n):
+            nm = names.raw[48 * i:48 * (i + 1)].split(b"\0")[0].decode()
+            out.append(dict(name=nm, launches=int(la[i]), ms=float(ms[i]), work=float(wk[i]),
+                            kind=["fp64_flops", "hbm_bytes", "fp32_flops"][int(kind[i])]))
+        return out
 
     def timings(self):
         t = np.zeros(5)

@@ -180,6 +180,27 @@ def batch_sizes(count=256, seed=0, lo=3, hi=20):
     return rng.integers(lo, hi + 1, size=count)
 
 
+AMU_TO_ME = 1822.888486
+FS_TO_AU = 41.341374575751
+KB_HARTREE = 3.166811563e-6
+MASS_AMU = {1: 1.008, 8: 15.999}
+
+
+def masses_au(Z):
+    """Nuclear masses (electron masses) for atomic numbers Z."""
+    return np.array([MASS_AMU[int(z)] * AMU_TO_ME for z in Z])
+
+
+def maxwell_boltzmann(Z, temperature=300.0, seed=0):
+    """Seeded Maxwell-Boltzmann velocities (bohr per atomic time unit) with the
+    centre-of-mass momentum removed."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    m = masses_au(Z)
+    v = rng.normal(size=(len(m), 3)) * np.sqrt(KB_HARTREE * temperature / m)[:, None]
+    v -= (m[:, None] * v).sum(0) / m.sum()
+    return v
+
+
 def tiny_atom_basis(Z=2, a0=0.5, ratio=3.0, nprim=(3,), aux_lmax=None):
     """Single atom at the origin with an even-tempered primary set and, when
     ``aux_lmax`` is given, an auxiliary set holding every pair-sum exponent
