@@ -148,6 +148,10 @@ int rihf_screening_stats(rihf_ctx* ctx, int* kept, int* total);
    library launched since the context was created ([4], as a double). */
 int rihf_timings(rihf_ctx* ctx, double* out5);
 
+/* Fock builds of the last rihf_scf by precision: FP32 (mixed-precision
+   iterations) and FP64.  Either pointer may be NULL. */
+int rihf_scf_stats(rihf_ctx* ctx, int* fp32_builds, int* fp64_builds);
+
 /* The CUDA stream (cudaStream_t, returned as void*) on which the context
    launches all of its work; callers may record CUDA events on it. */
 void* rihf_stream(rihf_ctx* ctx);

@@ -69,6 +69,67 @@ void gemv_cols(const LaCtx& la, const double* A, int M, long long K, const doubl
   if (la.launches) *la.launches += 2;
 }
 
+__global__ void __launch_bounds__(256) gemv_rows_f32_kernel(const float* __restrict__ A, int M, long long K,
+                                                            const float* __restrict__ x, double alpha, double* y) {
+  __shared__ double red[8];
+  for (int r = blockIdx.x; r < M; r += gridDim.x) {
+    const float4* row = reinterpret_cast<const float4*>(A + (long long)r * K);
+    const float4* xv = reinterpret_cast<const float4*>(x);
+    float s = 0.f;
+    long long K4 = K / 4;
+    for (long long j = threadIdx.x; j < K4; j += 256) {
+      float4 a = row[j], b = xv[j];
+      s = fmaf(a.x, b.x, s); s = fmaf(a.y, b.y, s); s = fmaf(a.z, b.z, s); s = fmaf(a.w, b.w, s);
+    }
+    for (long long j = 4 * K4 + threadIdx.x; j < K; j += 256) s = fmaf(A[(long long)r * K + j], x[j], s);
+    double d = s;
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      y[r] = alpha * t;
+    }
+    __syncthreads();
+  }
+}
+
+void gemv_rows_f32(const LaCtx& la, const float* A, int M, long long K, const float* x, double alpha, double* y) {
+  int blocks = std::min(M, 16 * la.sms);
+  const bool aligned = (K % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
+                       ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+  if (!aligned) throw RihfError(-1, "gemv_rows_f32 needs 16-byte aligned rows");
+  gemv_rows_f32_kernel<<<blocks, 256, 0, la.stream>>>(A, M, K, x, alpha, y);
+  RIHF_LAUNCH_CHECK();
+  if (la.launches) *la.launches += 1;
+}
+
+__global__ void __launch_bounds__(256) gemv_cols_f32_kernel(const float* __restrict__ A, int M, long long K,
+                                                            const double* __restrict__ x, int rows_per,
+                                                            double* __restrict__ part) {
+  long long j = blockIdx.x * 256LL + threadIdx.x;
+  int r0 = blockIdx.y * rows_per, r1 = min(M, r0 + rows_per);
+  if (j >= K) return;
+  float s = 0.f;
+  for (int r = r0; r < r1; ++r) s = fmaf((float)x[r], A[(long long)r * K + j], s);
+  part[(long long)blockIdx.y * K + j] = (double)s;
+}
+
+void gemv_cols_f32(const LaCtx& la, const float* A, int M, long long K, const double* x, double alpha, double* y) {
+  long long colblocks = (K + 255) / 256;
+  int nchunk = (int)std::max<long long>(1, std::min<long long>(M, (8LL * la.sms + colblocks - 1) / colblocks));
+  while (nchunk > 1 && (size_t)nchunk * K > la.work_elems) nchunk /= 2;
+  int rows_per = ceil_div(M, nchunk);
+  nchunk = ceil_div(M, rows_per);
+  gemv_cols_f32_kernel<<<dim3((unsigned)colblocks, nchunk), 256, 0, la.stream>>>(A, M, K, x, rows_per, la.work);
+  RIHF_LAUNCH_CHECK();
+  int blocks = (int)std::min<long long>((K + 255) / 256, 8LL * la.sms);
+  cols_reduce_kernel<<<blocks, 256, 0, la.stream>>>(la.work, nchunk, K, alpha, y);
+  RIHF_LAUNCH_CHECK();
+  if (la.launches) *la.launches += 2;
+}
+
 __global__ void outer_fill_kernel(const double* __restrict__ c, int naux, const double* __restrict__ D, long long n2,
                                   double* __restrict__ Y) {
   long long total = (long long)naux * n2;

@@ -10,6 +10,10 @@ namespace rihf {
 void gemv_rows(const LaCtx& la, const double* A, int M, long long K, const double* x, double alpha, double* y);
 // y[j] = alpha * sum_r x[r] A[r*K + j], j < K (row chunks reduced deterministically).
 void gemv_cols(const LaCtx& la, const double* A, int M, long long K, const double* x, double alpha, double* y);
+// FP32 operand versions (mixed-precision SCF iterations): products and
+// per-thread partial sums in FP32, cross-thread sums and outputs in FP64.
+void gemv_rows_f32(const LaCtx& la, const float* A, int M, long long K, const float* x, double alpha, double* y);
+void gemv_cols_f32(const LaCtx& la, const float* A, int M, long long K, const double* x, double alpha, double* y);
 // Y[P][e] = c[P] * D[e] for e < n2, P < naux.
 void outer_fill(const LaCtx& la, const double* c, int naux, const double* D, long long n2, double* Y);
 

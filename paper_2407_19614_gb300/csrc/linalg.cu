@@ -156,6 +156,143 @@ void dgemm(const LaCtx& la, const GemmArgs& g) {
   }
 }
 
+// ------------------------------------------------------------ GEMM (FP32)
+
+constexpr int ST = 64;   // output tile
+constexpr int SK = 16;   // K step
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) sgemm_kernel(SGemmArgs g, int nsplit, int kper, int bper, float* work) {
+  __shared__ float As[SK][ST + 4];
+  __shared__ float Bs[SK][ST + 4];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int n0 = blockIdx.x * ST, m0 = blockIdx.y * ST;
+  const int z = blockIdx.z;
+  int b_lo, b_hi, k_lo, k_hi, slot_b, slot_s;
+  if (g.reduce_batch) {
+    slot_s = z; slot_b = 0; b_lo = z * bper; b_hi = min(g.batch, b_lo + bper); k_lo = 0; k_hi = g.K;
+  } else {
+    slot_b = z / nsplit; slot_s = z % nsplit; b_lo = slot_b; b_hi = slot_b + 1;
+    k_lo = slot_s * kper; k_hi = min(g.K, k_lo + kper);
+  }
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int b = b_lo; b < b_hi; ++b) {
+    const float* A = g.A + (long long)b * g.sA;
+    const float* B = g.B + (long long)b * g.sB;
+    for (int k0 = k_lo; k0 < k_hi; k0 += SK) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        int idx = tid + r * 256;   // 1024 = 64 x 16
+        int mm, kk;
+        if (TA) { mm = idx % ST; kk = idx / ST; } else { kk = idx % SK; mm = idx / SK; }
+        int m = m0 + mm, k = k0 + kk;
+        float v = 0.f;
+        if (m < g.M && k < k_hi) v = TA ? A[(long long)k * g.lda + m] : A[(long long)m * g.lda + k];
+        As[kk][mm] = v;
+        int nn, kb;
+        if (TB) { kb = idx % SK; nn = idx / SK; } else { nn = idx % ST; kb = idx / ST; }
+        int n = n0 + nn, kq = k0 + kb;
+        float w = 0.f;
+        if (n < g.N && kq < k_hi) w = TB ? B[(long long)n * g.ldb + kq] : B[(long long)kq * g.ldb + n];
+        Bs[kb][nn] = w;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < SK; ++kk) {
+        float a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+  const int nslots = g.reduce_batch ? (int)gridDim.z : nsplit;
+  const bool direct = nslots == 1;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
+      if (m >= g.M || n >= g.N) continue;
+      if (direct && !g.Cd) {
+        float* c = g.C + (g.reduce_batch ? 0 : (long long)slot_b * g.sC) + (long long)m * g.ldc + n;
+        *c = (float)(g.beta == 0.0 ? g.alpha * acc[i][j] : g.alpha * acc[i][j] + g.beta * *c);
+      } else {
+        long long slot = (long long)slot_b * nslots + slot_s;
+        work[slot * g.M * g.N + (long long)m * g.N + n] = acc[i][j];
+      }
+    }
+}
+
+__global__ void sgemm_reduce_kernel(SGemmArgs g, int nslots, const float* __restrict__ work) {
+  long long total = (long long)g.M * g.N * (g.reduce_batch ? 1 : g.batch);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long mn = idx % ((long long)g.M * g.N);
+    int b = (int)(idx / ((long long)g.M * g.N));
+    int m = (int)(mn / g.N), n = (int)(mn % g.N);
+    double s = 0.0;
+    for (int q = 0; q < nslots; ++q) s += (double)work[((long long)b * nslots + q) * g.M * g.N + mn];
+    long long off = (g.reduce_batch ? 0 : (long long)b * g.sC) + (long long)m * g.ldc + n;
+    if (g.Cd) g.Cd[off] = g.beta == 0.0 ? g.alpha * s : g.alpha * s + g.beta * g.Cd[off];
+    else g.C[off] = (float)(g.beta == 0.0 ? g.alpha * s : g.alpha * s + g.beta * g.C[off]);
+  }
+}
+
+void sgemm(const LaCtx& la, const SGemmArgs& g) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  int tm = ceil_div(g.M, ST), tn = ceil_div(g.N, ST);
+  long long tiles = (long long)tm * tn * (g.reduce_batch ? 1 : g.batch);
+  int nsplit = 1, kper = g.K, bper = g.batch;
+  const long long target = 4LL * la.sms;
+  const size_t cap = la.work_elems * 2;   // the workspace holds twice as many floats
+  if (g.reduce_batch) {
+    nsplit = (int)std::min<long long>(g.batch, std::max<long long>(1, (target + tiles - 1) / tiles));
+    while (nsplit > 1 && (size_t)nsplit * g.M * g.N > cap) nsplit /= 2;
+    bper = ceil_div(g.batch, nsplit);
+    nsplit = ceil_div(g.batch, bper);
+  } else if (tiles < target && g.K > 4 * SK) {
+    nsplit = (int)std::min<long long>((target + tiles - 1) / tiles, g.K / (2 * SK));
+    while (nsplit > 1 && (size_t)nsplit * g.M * g.N * g.batch > cap) nsplit /= 2;
+    kper = ceil_div(ceil_div(g.K, nsplit), SK) * SK;
+    nsplit = ceil_div(g.K, kper);
+  }
+  float* work = reinterpret_cast<float*>(la.work);
+  dim3 grid(tn, tm, g.reduce_batch ? nsplit : g.batch * nsplit);
+  if (g.transA && g.transB) sgemm_kernel<true, true><<<grid, 256, 0, la.stream>>>(g, nsplit, kper, bper, work);
+  else if (g.transA) sgemm_kernel<true, false><<<grid, 256, 0, la.stream>>>(g, nsplit, kper, bper, work);
+  else if (g.transB) sgemm_kernel<false, true><<<grid, 256, 0, la.stream>>>(g, nsplit, kper, bper, work);
+  else sgemm_kernel<false, false><<<grid, 256, 0, la.stream>>>(g, nsplit, kper, bper, work);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+  if (nsplit > 1 || g.Cd) {
+    long long total = (long long)g.M * g.N * (g.reduce_batch ? 1 : g.batch);
+    int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * la.sms);
+    sgemm_reduce_kernel<<<blocks, 256, 0, la.stream>>>(g, nsplit, work);
+    RIHF_LAUNCH_CHECK();
+    count(la);
+  }
+}
+
+__global__ void to_float_kernel(const double* __restrict__ in, long long n, float* __restrict__ out, double s) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)(s * in[i]);
+}
+void to_float(const LaCtx& la, const double* in, long long n, float* out, double scale) {
+  int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 16LL * la.sms));
+  to_float_kernel<<<blocks, 256, 0, la.stream>>>(in, n, out, scale);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+}
+
 // ------------------------------------------------------------ symmetrize
 
 __global__ void symmetrize_lower_kernel(double* X, int n) {

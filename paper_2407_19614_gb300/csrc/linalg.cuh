@@ -43,6 +43,31 @@ struct GemmArgs {
 };
 void dgemm(const LaCtx& la, const GemmArgs& g);
 
+// FP32 operands, FP32 accumulation (CUDA cores, 64 x 64 tiles).  Same
+// conventions as GemmArgs; when Cd is set the result goes to the FP64 matrix Cd
+// (alpha * sum + beta * Cd, split partial sums added in FP64), else to C (FP32).
+struct SGemmArgs {
+  int M = 0, N = 0, K = 0;
+  double alpha = 1.0, beta = 0.0;
+  const float* A = nullptr;
+  int lda = 0;
+  long long sA = 0;
+  bool transA = false;
+  const float* B = nullptr;
+  int ldb = 0;
+  long long sB = 0;
+  bool transB = false;
+  float* C = nullptr;
+  double* Cd = nullptr;
+  int ldc = 0;
+  long long sC = 0;
+  int batch = 1;
+  bool reduce_batch = false;
+};
+void sgemm(const LaCtx& la, const SGemmArgs& g);
+// out[i] = (float) in[i]
+void to_float(const LaCtx& la, const double* in, long long n, float* out, double scale = 1.0);
+
 // Mirror the lower triangle into the upper one for each of `batch` n x n slices.
 void symmetrize_lower(const LaCtx& la, double* X, int n, int batch);
 

@@ -415,6 +415,10 @@ struct rihf_ctx {
 
   // gradient
   double* na2tmp = nullptr;
+  // mixed precision: FP32 copy of B and FP32 operands of the SCF-iteration builds
+  float *B32 = nullptr, *D32 = nullptr, *Ct32 = nullptr, *H32 = nullptr, *G32 = nullptr;
+  double *Fprev = nullptr, *Dprev = nullptr;
+  int fp32_builds = 0, last_iters = 0;
   double* trsm_tmp = nullptr;
   double *cvec = nullptr, *W = nullptr, *Bij = nullptr, *Xt = nullptr, *Zm = nullptr, *G = nullptr, *Y = nullptr;
   double* grad_parts = nullptr;   // 5 x natoms x 3 on device (one, overlap, three, two, nuc)
@@ -481,7 +485,7 @@ static void free_all(rihf_ctx* c) {
                   c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->T3, c->B, c->Xo, c->Sw, c->Sv,
                   c->C, c->eps, c->Ct, c->D, c->J, c->K, c->F, c->Fx, c->T1, c->T2, c->Err, c->Fp, c->Cp, c->Hb,
                   c->dvec, c->Fring, c->Ering, c->Bdiis, c->coef, c->scal, c->Cprev,
-                  c->na2tmp, c->trsm_tmp, c->cvec, c->W, c->Bij, c->Xt, c->Zm, c->G, c->Y, c->grad_parts, c->work, c->eigws, c->scratch};
+                  c->na2tmp, c->trsm_tmp, c->B32, c->D32, c->Ct32, c->H32, c->G32, c->Fprev, c->Dprev, c->cvec, c->W, c->Bij, c->Xt, c->Zm, c->G, c->Y, c->grad_parts, c->work, c->eigws, c->scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -532,29 +536,53 @@ static void compute_geometry(rihf_ctx* c) {
   { TraceScope t(c->tracer, s, "fit trsm B=L^-1 T", (double)NA * NA * N * (N + 1) / 2, 0);
     trsm_lower(la, c->L, NA, c->B, (long long)N * N, false, N, c->trsm_tmp); }
   symmetrize_lower(la, c->B, N, NA);
-  // canonical orthogonaliser from S
-  { TraceScope t(c->tracer, s, "eigh S", 0.0, 0);
-    eigh(la, c->S, N, c->Sw, c->Sv, c->eigws, 4, nullptr); }
-  std::vector<double> sw(N);
-  RIHF_CUDA(cudaMemcpyAsync(sw.data(), c->Sw, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  if (c->B32) to_float(la, c->B, (long long)NA * N * N, c->B32);
   int flag = 0;
   RIHF_CUDA(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   RIHF_CUDA(cudaStreamSynchronize(s));
   if (flag) throw RihfError(RIHF_ERR_NOT_POSITIVE_DEFINITE, "metric (P|Q) is not positive definite");
+  // Orthogonaliser.  First try X = L_S^{-T} (S = L_S L_S^T); since
+  // lambda_min(S) >= 1 / Tr(S^{-1}) = 1 / ||L_S^{-1}||_F^2, a bound above
+  // lindep_tau proves that canonical orthogonalisation would drop nothing, and
+  // then the SCF fixed point does not depend on the choice of orthogonaliser.
   int k0 = 0;
-  while (k0 < N && sw[k0] <= c->opt.lindep_tau) ++k0;
-  if (k0 == N) throw RihfError(RIHF_ERR_NOT_POSITIVE_DEFINITE, "overlap matrix has no eigenvalue above lindep_tau");
-  int nind = N - k0;
-  if (c->nind != 0 && nind != c->nind) c->have_cprev = false;
-  c->nind = nind;
-  if (k0 == 0) {
-    // no linear dependence: X = L_S^{-T} (S = L_S L_S^T) orthonormalises exactly;
-    // the SCF fixed point does not depend on the choice of orthogonaliser
+  bool chol_ok = false;
+  {
+    TraceScope t(c->tracer, s, "orthogonaliser (cholesky S)", (double)N * N * N / 3.0, 0);
     RIHF_CUDA(cudaMemcpyAsync(c->T2, c->S, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, s));
     cholesky(la, c->T2, N, c->scratch);
     identity(la, c->T1, N);
     trsm_lower(la, c->T2, N, c->T1, N, false, 0, c->trsm_tmp);
+    dot(la, N * N, c->T1, c->T1, c->scal + 3);
+    double tr = 0.0;
+    RIHF_CUDA(cudaMemcpyAsync(&tr, c->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+    RIHF_CUDA(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RIHF_CUDA(cudaStreamSynchronize(s));
+    chol_ok = !flag && std::isfinite(tr) && tr > 0.0 && 1.0 / tr > c->opt.lindep_tau;
+    RIHF_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
+  }
+  std::vector<double> sw;
+  if (!chol_ok) {
+    TraceScope t(c->tracer, s, "eigh S", 0.0, 0);
+    eigh(la, c->S, N, c->Sw, c->Sv, c->eigws, 4, nullptr);
+    sw.resize(N);
+    RIHF_CUDA(cudaMemcpyAsync(sw.data(), c->Sw, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+    RIHF_CUDA(cudaStreamSynchronize(s));
+    while (k0 < N && sw[k0] <= c->opt.lindep_tau) ++k0;
+    if (k0 == N) throw RihfError(RIHF_ERR_NOT_POSITIVE_DEFINITE, "overlap matrix has no eigenvalue above lindep_tau");
+  }
+  int nind = N - k0;
+  if (c->nind != 0 && nind != c->nind) c->have_cprev = false;
+  c->nind = nind;
+  if (chol_ok) {
     transpose(la, c->T1, N, N, c->Xo);
+  } else if (k0 == 0) {
+    // Cholesky failed the bound but nothing is dropped: canonical with all vectors
+    std::vector<double> invs(nind);
+    for (int i = 0; i < nind; ++i) invs[i] = 1.0 / std::sqrt(sw[i]);
+    RIHF_CUDA(cudaMemcpyAsync(c->dvec, invs.data(), sizeof(double) * nind, cudaMemcpyHostToDevice, s));
+    scale_cols(la, c->Sv, c->dvec, N, nind, c->Xo);
+    RIHF_CUDA(cudaStreamSynchronize(s));
   } else {
     std::vector<double> invs(nind);
     for (int i = 0; i < nind; ++i) invs[i] = 1.0 / std::sqrt(sw[k0 + i]);
@@ -566,7 +594,7 @@ static void compute_geometry(rihf_ctx* c) {
   }
   // Newton-Schulz S-orthonormalisation, X <- X (3I - X^T S X) / 2, so that
   // X^T S X = I holds to rounding whatever the eigensolver's residual.
-  for (int it = 0; it < 3; ++it) {
+  for (int it = 0; it < (chol_ok ? 1 : 3); ++it) {
     GemmArgs g1;   // T1 (N x n) = S X
     g1.M = N; g1.N = nind; g1.K = N; g1.A = c->S; g1.lda = N; g1.B = c->Xo; g1.ldb = nind; g1.C = c->T1;
     g1.ldc = nind;
@@ -726,6 +754,15 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     c->na2tmp = dalloc<double>(na2);
     c->G = dalloc<double>((size_t)NA * c->nocc * N);
     c->Y = dalloc<double>(big);
+    if (c->opt.precision == RIHF_PRECISION_MIXED) {
+      c->B32 = dalloc<float>(big);
+      c->D32 = dalloc<float>(n2);
+      c->Ct32 = dalloc<float>((size_t)N * c->nocc);
+      c->H32 = dalloc<float>((size_t)NA * N * c->nocc);
+      c->G32 = dalloc<float>(big);
+      c->Fprev = dalloc<double>(n2);
+      c->Dprev = dalloc<double>(n2);
+    }
     c->trsm_tmp = dalloc<double>(32 * std::max<size_t>({n2, (size_t)NA, (size_t)c->nocc * c->nocc}) + 1024);
     c->grad_parts = dalloc<double>(5 * 3 * natoms);
     c->work_elems = std::max<size_t>({(size_t)1 << 24, 8 * n2 * 4, (size_t)NA * 64});
@@ -800,7 +837,7 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
 }
 
 // F = h + J + K for the current C; writes D, J, K, F, Ct and scal[0] = E.
-static void fock_build(rihf_ctx* c) {
+static void fock_build(rihf_ctx* c, bool fp32) {
   LaCtx la = c->la();
   const int N = c->N, NA = c->NA, no = c->nocc;
   const size_t n2 = (size_t)N * N;
@@ -810,6 +847,36 @@ static void fock_build(rihf_ctx* c) {
   gd.M = N; gd.N = N; gd.K = no; gd.A = c->Ct; gd.lda = no; gd.B = c->Ct; gd.ldb = no; gd.transB = true;
   gd.C = c->D; gd.ldc = N;
   dgemm(la, gd);
+  if (fp32) {
+    // Incremental mixed-precision build: F = F_prev + J(dD) + K(dD) with
+    // dD = D - D_prev in FP32.  J is linear in D (two passes over B32); K uses
+    // the density form of Eq. k_ri_1, G^P = B^P dD, K(dD) = -1/2 sum_P G^P B^P,
+    // so the FP32 rounding error scales with |dD|, not with |K|.
+    axpby(la, (int)n2, 1.0, c->D, -1.0, c->Dprev, c->T1);
+    to_float(la, c->T1, (long long)n2, c->D32);
+    { TraceScope t(c->tracer, c->stream, "RI-J d=B.dD (fp32 gemv_rows)", (double)NA * n2 * 4, 1);
+      gemv_rows_f32(la, c->B32, NA, (long long)n2, c->D32, 1.0, c->dvec); }
+    { TraceScope t(c->tracer, c->stream, "RI-J dJ=B^T d (fp32 gemv_cols)", (double)NA * n2 * 4, 1);
+      gemv_cols_f32(la, c->B32, NA, (long long)n2, c->dvec, 1.0, c->J); }
+    SGemmArgs sg;   // G (NA*N x N) = B32 (NA*N x N) dD (N x N)
+    sg.M = NA * N; sg.N = N; sg.K = N; sg.A = c->B32; sg.lda = N; sg.B = c->D32; sg.ldb = N; sg.C = c->G32;
+    sg.ldc = N;
+    { TraceScope t(c->tracer, c->stream, "RI-K G=B dD (fp32 sgemm)", 2.0 * NA * n2 * N, 2);
+      sgemm(la, sg); }
+    SGemmArgs sk;   // dK = -1/2 sum_P G^P B^P
+    sk.M = N; sk.N = N; sk.K = N; sk.A = c->G32; sk.lda = N; sk.sA = (long long)n2;
+    sk.B = c->B32; sk.ldb = N; sk.sB = (long long)n2;
+    sk.Cd = c->K; sk.ldc = N; sk.batch = NA; sk.reduce_batch = true; sk.alpha = -0.5;
+    { TraceScope t(c->tracer, c->stream, "RI-K dK=-1/2 sum G B (fp32 sgemm)", 2.0 * NA * n2 * N, 2);
+      sgemm(la, sk); }
+    add3(la, (int)n2, c->Fprev, c->J, c->K, c->F);
+    RIHF_CUDA(cudaMemcpyAsync(c->Fprev, c->F, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
+    RIHF_CUDA(cudaMemcpyAsync(c->Dprev, c->D, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
+    energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->vnn, c->scal);
+    RIHF_LAUNCH_CHECK();
+    c->launches += 1;
+    return;
+  }
   // RI-J: d = B vec(D); J = B^T d
   { TraceScope t(c->tracer, c->stream, "RI-J d=B.D (gemv_rows)", (double)NA * n2 * 8, 1);
     gemv_rows(la, c->B, NA, (long long)n2, c->D, 1.0, c->dvec); }
@@ -826,6 +893,45 @@ static void fock_build(rihf_ctx* c) {
   gk.C = c->K; gk.ldc = N; gk.batch = NA; gk.reduce_batch = true; gk.alpha = -0.5;
   { TraceScope t(c->tracer, c->stream, "RI-K K=-1/2 sum H H^T (dgemm)", 2.0 * NA * n2 * no, 0);
     dgemm(la, gk); }
+  add3(la, (int)n2, c->H, c->J, c->K, c->F);
+  if (c->Fprev) {   // reference for the next incremental build
+    RIHF_CUDA(cudaMemcpyAsync(c->Fprev, c->F, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
+    RIHF_CUDA(cudaMemcpyAsync(c->Dprev, c->D, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->vnn, c->scal);
+  RIHF_LAUNCH_CHECK();
+  c->launches += 1;
+}
+
+// Full mixed-precision Fock build (early SCF iterations): D and C~ from the
+// current orbitals in FP64, RI-J and RI-K (Eqs. j_ri, k_ri_2, tp) from the FP32
+// copy of B with FP32 products; cross-block sums and F in FP64.
+static void fock_build_fp32(rihf_ctx* c) {
+  LaCtx la = c->la();
+  const int N = c->N, NA = c->NA, no = c->nocc;
+  const size_t n2 = (size_t)N * N;
+  copy_cols(la, c->C, N, N, no, std::sqrt(2.0), c->Ct);
+  GemmArgs gd;
+  gd.M = N; gd.N = N; gd.K = no; gd.A = c->Ct; gd.lda = no; gd.B = c->Ct; gd.ldb = no; gd.transB = true;
+  gd.C = c->D; gd.ldc = N;
+  dgemm(la, gd);
+  to_float(la, c->D, (long long)n2, c->D32);
+  to_float(la, c->Ct, (long long)N * no, c->Ct32);
+  { TraceScope t(c->tracer, c->stream, "RI-J d=B.D (fp32 gemv_rows)", (double)NA * n2 * 4, 1);
+    gemv_rows_f32(la, c->B32, NA, (long long)n2, c->D32, 1.0, c->dvec); }
+  { TraceScope t(c->tracer, c->stream, "RI-J J=B^T d (fp32 gemv_cols)", (double)NA * n2 * 4, 1);
+    gemv_cols_f32(la, c->B32, NA, (long long)n2, c->dvec, 1.0, c->J); }
+  SGemmArgs sh;
+  sh.M = NA * N; sh.N = no; sh.K = N; sh.A = c->B32; sh.lda = N; sh.B = c->Ct32; sh.ldb = no; sh.C = c->H32;
+  sh.ldc = no;
+  { TraceScope t(c->tracer, c->stream, "RI-K H=B C~ (fp32 sgemm)", 2.0 * NA * n2 * no, 2);
+    sgemm(la, sh); }
+  SGemmArgs sk;
+  sk.M = N; sk.N = N; sk.K = no; sk.A = c->H32; sk.lda = no; sk.sA = (long long)N * no;
+  sk.B = c->H32; sk.ldb = no; sk.sB = (long long)N * no; sk.transB = true;
+  sk.Cd = c->K; sk.ldc = N; sk.batch = NA; sk.reduce_batch = true; sk.alpha = -0.5;
+  { TraceScope t(c->tracer, c->stream, "RI-K K=-1/2 sum H H^T (fp32 sgemm)", 2.0 * NA * n2 * no, 2);
+    sgemm(la, sk); }
   add3(la, (int)n2, c->H, c->J, c->K, c->F);
   energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->vnn, c->scal);
   RIHF_LAUNCH_CHECK();
@@ -893,9 +999,22 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   int it = 0;
   bool conv = false;
   float ms = 0.f;
+  // Precision ladder (mixed mode): the first Fock build of every SCF is a full
+  // FP64 build; the following ones are incremental FP32 builds (error ~ |dD|);
+  // when the convergence test passes on an incremental build, one more full
+  // FP64 build must pass it too, so the converged energy and density are those
+  // of an FP64 Fock matrix.  A full rebuild every 12 increments bounds drift.
+  const bool mixed = c->opt.precision == RIHF_PRECISION_MIXED && c->B32 != nullptr;
+  bool full_next = !mixed, fp64_tail = !mixed;
+  double best_fp32 = 1e300;
+  c->fp32_builds = 0;
   for (it = 1; it <= c->opt.max_iter; ++it) {
     cudaEventRecord(c->ev[2], s);
-    fock_build(c);
+    const bool full = !mixed || full_next;
+    if (full) fock_build(c, false);
+    else fock_build_fp32(c);
+    if (!full) ++c->fp32_builds;
+    full_next = fp64_tail;
     cudaEventRecord(c->ev[3], s);
     diis_error(c);
     int slot = (it - 1) % size;
@@ -911,7 +1030,17 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
     c->last_err = emax;
     if (c->verbose || getenv("RIHF_VERBOSE")) fprintf(stderr, "rihf_scf it %3d  E = %.12f  max|e| = %.3e  dE = %.3e\n", it, E, emax, E - Eold);
     if (!std::isfinite(E)) throw RihfError(RIHF_ERR_NOT_CONVERGED, "SCF energy is not finite");
-    if (it > 1 && std::fabs(E - Eold) < c->opt.conv_e && emax < c->opt.conv_diis) {
+    const bool crit = it > 1 && std::fabs(E - Eold) < c->opt.conv_e && emax < c->opt.conv_diis;
+    // FP32 builds only while the SCF error is large and still falling; their
+    // rounding is amplified by large MO coefficients in near-dependent bases,
+    // so the ladder moves to FP64 at max|e| < 1e-2 or at the first FP32
+    // iteration that does not improve; convergence is declared on FP64 builds.
+    if (mixed && !fp64_tail) {
+      if (emax < 1e-2 || crit || !(emax < 0.8 * best_fp32)) fp64_tail = true;
+      best_fp32 = std::min(best_fp32, emax);
+    }
+    full_next = fp64_tail;
+    if (crit && full) {
       conv = true;
       cudaEventRecord(c->ev[4], s);
       cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
@@ -947,6 +1076,7 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   c->tracer.flush();
   if (energy) *energy = E;
   if (iters) *iters = it;
+  c->last_iters = it;
   if (Dout) RIHF_CUDA(cudaMemcpy(Dout, c->D, sizeof(double) * n2, cudaMemcpyDeviceToHost));
   if (Cout) RIHF_CUDA(cudaMemcpy(Cout, c->C, sizeof(double) * n2, cudaMemcpyDeviceToHost));
   if (epsout) RIHF_CUDA(cudaMemcpy(epsout, c->eps, sizeof(double) * N, cudaMemcpyDeviceToHost));
@@ -1141,6 +1271,13 @@ int rihf_timings(rihf_ctx* c, double* out5) {
 }
 
 void* rihf_stream(rihf_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+int rihf_scf_stats(rihf_ctx* c, int* fp32_builds, int* fp64_builds) {
+  if (!c) return RIHF_ERR_INVALID_ARG;
+  if (fp32_builds) *fp32_builds = c->fp32_builds;
+  if (fp64_builds) *fp64_builds = c->last_iters - c->fp32_builds;
+  return RIHF_OK;
+}
 
 int rihf_trace(rihf_ctx* c, int enable) {
   if (!c) return RIHF_ERR_INVALID_ARG;

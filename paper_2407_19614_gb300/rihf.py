@@ -42,7 +42,8 @@ class rihf_options(ctypes.Structure):
 
 EXPORTS = ["rihf_default_options", "rihf_setup", "rihf_update_geometry", "rihf_scf", "rihf_gradient",
            "rihf_query", "rihf_get_matrix", "rihf_screening_stats", "rihf_timings", "rihf_strerror",
-           "rihf_last_error", "rihf_destroy", "rihf_eigh", "rihf_stream", "rihf_trace", "rihf_trace_stats"]
+           "rihf_last_error", "rihf_destroy", "rihf_eigh", "rihf_stream", "rihf_trace", "rihf_trace_stats",
+           "rihf_scf_stats"]
 
 _lib = None
 
@@ -71,6 +72,8 @@ def load(path: str = LIB_PATH):
     lib.rihf_strerror.restype = ctypes.c_char_p
     lib.rihf_last_error.argtypes = []
     lib.rihf_last_error.restype = ctypes.c_char_p
+    lib.rihf_scf_stats.argtypes = [P, P, P]
+    lib.rihf_scf_stats.restype = I
     lib.rihf_stream.argtypes = [P]
     lib.rihf_stream.restype = P
     lib.rihf_trace.argtypes = [P, I]
@@ -188,6 +191,11 @@ class Context:
         k, t = ctypes.c_int(), ctypes.c_int()
         _check(self.lib.rihf_screening_stats(self.h, ctypes.byref(k), ctypes.byref(t)))
         return k.value, t.value
+
+    def scf_stats(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.rihf_scf_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return dict(fp32_builds=a.value, fp64_builds=b.value)
 
     def stream(self) -> int:
         """cudaStream_t of the context (as an integer handle)."""
