@@ -173,6 +173,21 @@ int rihf_trace_stats(rihf_ctx* ctx, int max, char* names, double* launches, doub
    and frees its own device workspace.  Errors: INVALID_ARG, OOM, CUDA. */
 int rihf_eigh(int n, const double* A, double* W, double* V, int device);
 
+/* Allocation-free variant of rihf_eigh (the paper has no counterpart: this is a
+   service for callers that cannot allocate device memory, such as an MD engine
+   that owns a fixed memory pool and forbids cudaMalloc inside its time loop).
+   A, W, V are DEVICE pointers: A n x n symmetric (row-major, read only),
+   W (n) ascending eigenvalues, V (n x n, column k = eigenvector k); stream is a
+   cudaStream_t (NULL = the default stream); the call is asynchronous on it.
+   n must not exceed 256: the workspace is one fixed device array in the
+   library (about 7.9 MB, held on every GPU that loads the library until exit);
+   larger n return RIHF_ERR_INVALID_ARG.  No memory is allocated or freed.
+   The first call on each device resolves the array's device address (make it
+   before any stream capture).  All calls share the array: calls whose work
+   overlaps on the GPU (different streams or host threads) race and must be
+   serialised by the caller.  Errors: INVALID_ARG, CUDA. */
+int rihf_eigh_noalloc(int n, const double* A, double* W, double* V, void* stream);
+
 const char* rihf_strerror(int code);
 const char* rihf_last_error(void);
 void rihf_destroy(rihf_ctx* ctx);

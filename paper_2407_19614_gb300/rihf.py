@@ -43,7 +43,7 @@ class rihf_options(ctypes.Structure):
 EXPORTS = ["rihf_default_options", "rihf_setup", "rihf_update_geometry", "rihf_scf", "rihf_gradient",
            "rihf_query", "rihf_get_matrix", "rihf_screening_stats", "rihf_timings", "rihf_strerror",
            "rihf_last_error", "rihf_destroy", "rihf_eigh", "rihf_stream", "rihf_trace", "rihf_trace_stats",
-           "rihf_scf_stats"]
+           "rihf_scf_stats", "rihf_eigh_noalloc"]
 
 _lib = None
 
@@ -80,6 +80,8 @@ def load(path: str = LIB_PATH):
     lib.rihf_trace.restype = I
     lib.rihf_trace_stats.argtypes = [P, I, P, P, P, P, P]
     lib.rihf_trace_stats.restype = I
+    lib.rihf_eigh_noalloc.argtypes = [I, P, P, P, P]
+    lib.rihf_eigh_noalloc.restype = I
     lib.rihf_eigh.argtypes = [I, P, P, P, I]
     lib.rihf_eigh.restype = I
     lib.rihf_destroy.argtypes = [P]
@@ -130,6 +132,13 @@ def eigh(A, device=0):
     V = np.zeros((n, n))
     _check(load().rihf_eigh(n, _p(A), _p(W), _p(V), int(device)))
     return W, V
+
+
+def eigh_noalloc(n, A_dev, W_dev, V_dev, stream=0):
+    """Allocation-free eigensolver on caller-owned DEVICE buffers (integer
+    device addresses, e.g. torch.Tensor.data_ptr()); returns the status code."""
+    return load().rihf_eigh_noalloc(int(n), ctypes.c_void_p(A_dev), ctypes.c_void_p(W_dev), ctypes.c_void_p(V_dev),
+                                    ctypes.c_void_p(stream) if stream else None)
 
 
 class Context:
