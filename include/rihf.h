@@ -69,7 +69,9 @@ typedef struct {
   int device;           /* CUDA device ordinal                                             */
 } rihf_options;
 
-/* Fills *opt with the defaults: FP64, spherical, schwarz_tau 1e-14, lindep_tau
+/* Fills *opt with the defaults: FP64, spherical, schwarz_tau 0 (no pair
+   dropped; with ill-conditioned auxiliary metrics even pairs below 1e-14 move
+   the energy by ~1e-6 Eh, see the screening tests), lindep_tau
    1e-8, conv_e 1e-10, conv_diis 1e-9, max_iter 100, diis_size 8,
    mixed_fp64_iters 2, device 0. */
 void rihf_default_options(rihf_options* opt);
@@ -131,10 +133,15 @@ int rihf_query(rihf_ctx* ctx, int* N, int* Naux, int* nocc, int* natoms);
      RIHF_MAT_T3: (mu nu|P) as Naux x N x N;  RIHF_MAT_B: B^P as Naux x N x N
      RIHF_MAT_GRAD_PARTS: 5 x natoms x 3 (one-electron, overlap, 3-centre,
                           2-centre, nuclear-repulsion terms of Eq. rihf_gradient)
+     RIHF_MAT_SCHWARZ: Q_ab = sqrt(max (mu nu|mu nu)) over the Cartesian
+                          components of shells a >= b, packed a(a+1)/2 + b
+                          (nshell(nshell+1)/2 values; zeros when the screen
+                          is not evaluated)
    J, K, F, D refer to the last Fock build. */
 enum {
   RIHF_MAT_S = 0, RIHF_MAT_H = 1, RIHF_MAT_A = 2, RIHF_MAT_LINV = 3, RIHF_MAT_T3 = 4, RIHF_MAT_B = 5,
-  RIHF_MAT_J = 6, RIHF_MAT_K = 7, RIHF_MAT_F = 8, RIHF_MAT_D = 9, RIHF_MAT_GRAD_PARTS = 10
+  RIHF_MAT_J = 6, RIHF_MAT_K = 7, RIHF_MAT_F = 8, RIHF_MAT_D = 9, RIHF_MAT_GRAD_PARTS = 10,
+  RIHF_MAT_SCHWARZ = 11
 };
 int rihf_get_matrix(rihf_ctx* ctx, int which, double* out);
 

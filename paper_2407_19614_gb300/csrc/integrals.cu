@@ -395,6 +395,188 @@ __global__ void __launch_bounds__(32) one_electron_kernel(DevShells prim, int na
   }
 }
 
+// ------------------------------------------------------------ Schwarz (ab|ab)
+
+// Shared-memory size (doubles) of schwarz_kernel for one (la, lb) class, and the
+// ping-pong half size used by both HRR stages.
+__host__ __device__ inline int schwarz_smem(int la, int lb, int* half_out) {
+  const int lc = la, ld = lb, lf = lc + ld, emin = la, emax = la + lb, L = emax + lf;
+  const int nab = ncart(la) * ncart(lb);
+  EtrShape sh{lf, emin, emax};
+  int accsz = 0, brasz = 0, half = 0;
+  for (int f = lc; f <= lf; ++f) {
+    accsz += (cart_offset(emax + 1) - cart_offset(emin)) * ncart(f);
+    brasz += nab * ncart(f);
+    int h = hrr_scratch(la, lb, f, emax) / 2;
+    if (h > half) half = h;
+  }
+  for (int d = 1; d <= ld; ++d) {
+    int n = 0;
+    for (int f = lc; f <= lf - d; ++f) n += nab * ncart(f) * ncart(d);
+    if (n > half) half = n;
+  }
+  if (half_out) *half_out = half;
+  return 24 + vrr_size(L) + (lf > 0 ? sh.total() : 0) + accsz + brasz + 2 * half;
+}
+
+// Q_ab = sqrt(max_{mu in a, nu in b} (mu nu|mu nu)) over Cartesian components
+// (Sec. 3.1.1: the Schwarz bound |(mu nu|lam sig)| <= Q_{mu nu} Q_{lam sig}).
+// Four-centre recursion with the ket pair equal to the bra pair: bra VRR with
+// W = (pP + qQ)/(p+q), electron transfer to f = lc..lc+ld with the
+// -(beta AB + delta CD)/q term, bra HRR on every ket level f, then ket HRR.
+__global__ void __launch_bounds__(32) schwarz_kernel(DevShells prim, const double* __restrict__ boys, int* counter,
+                                                     double* __restrict__ Q) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x;
+  const int ns = prim.nshell;
+  const long long ntask = (long long)ns * (ns + 1) / 2;
+  for (;;) {
+    long long task = warp_next_task(counter, lane);
+    if (task >= ntask) break;
+    int sa = (int)((sqrt(8.0 * (double)task + 1.0) - 1.0) * 0.5);
+    while ((long long)sa * (sa + 1) / 2 > task) --sa;
+    while ((long long)(sa + 1) * (sa + 2) / 2 <= task) ++sa;
+    int sb = (int)(task - (long long)sa * (sa + 1) / 2);
+    if (prim.l[sa] < prim.l[sb]) { int t = sa; sa = sb; sb = t; }
+    const int la = prim.l[sa], lb = prim.l[sb];
+    const int lc = la, ld = lb, lf = lc + ld;          // ket pair = bra pair
+    const int emin = la, emax = la + lb, L = emax + lf;
+    const int na = ncart(la), nb = ncart(lb);
+    EtrShape sh{lf, emin, emax};
+    // smem: Fm | vrr | etr | acc[f][e][kf] for f in [lc, lf] | bra-HRR out [f][ka][kb][kf] | scratch
+    double* Fm = smem;
+    double* vrr = Fm + 24;
+    double* etr = vrr + vrr_size(L);
+    double* acc = etr + (lf > 0 ? sh.total() : 0);
+    int accsz = 0;
+    for (int f = lc; f <= lf; ++f) accsz += (cart_offset(emax + 1) - cart_offset(emin)) * ncart(f);
+    double* bra = acc + accsz;
+    int brasz = 0;
+    for (int f = lc; f <= lf; ++f) brasz += na * nb * ncart(f);
+    double* scr = bra + brasz;
+    int half = 0;
+    schwarz_smem(la, lb, &half);
+    for (int i = lane; i < accsz; i += 32) acc[i] = 0.0;
+    const double* A = prim.xyz + 3 * sa;
+    const double* B = prim.xyz + 3 * sb;
+    for (int pa = 0; pa < prim.nprim[sa]; ++pa)
+      for (int pb = 0; pb < prim.nprim[sb]; ++pb)
+        for (int pc = 0; pc < prim.nprim[sa]; ++pc)
+          for (int pd = 0; pd < prim.nprim[sb]; ++pd) {
+            double al = prim.exps[prim.pstart[sa] + pa], be = prim.exps[prim.pstart[sb] + pb];
+            double ga = prim.exps[prim.pstart[sa] + pc], de = prim.exps[prim.pstart[sb] + pd];
+            double w = prim.coefs[prim.pstart[sa] + pa] * prim.coefs[prim.pstart[sb] + pb] *
+                       prim.coefs[prim.pstart[sa] + pc] * prim.coefs[prim.pstart[sb] + pd];
+            Prim3 t;
+            double p = al + be, q = ga + de, P[3], Qc[3], R2ab = 0.0, R2pq = 0.0;
+            t.p = p; t.q = q; t.beta = be; t.rho = p * q / (p + q);
+            for (int i = 0; i < 3; ++i) {
+              P[i] = (al * A[i] + be * B[i]) / p;
+              Qc[i] = (ga * A[i] + de * B[i]) / q;
+              double AB = A[i] - B[i];
+              R2ab += AB * AB;
+              // fold -(beta AB + delta CD)/q into the ETR's beta AB / q (C = A, D = B)
+              t.AB[i] = AB + (de / be) * AB;
+            }
+            for (int i = 0; i < 3; ++i) {
+              double Wi = (p * P[i] + q * Qc[i]) / (p + q);
+              t.PA[i] = P[i] - A[i];
+              t.WP[i] = Wi - P[i];
+              R2pq += (P[i] - Qc[i]) * (P[i] - Qc[i]);
+            }
+            t.T = t.rho * R2pq;
+            t.pref = 34.98683665524972 / (p * q * sqrt(p + q)) * exp(-al * be / p * R2ab) * exp(-ga * de / q * R2ab);
+            if (lane <= L) Fm[lane] = boys_eval(lane, t.T, boys);
+            __syncwarp();
+            warp_vrr(vrr, L, t, Fm, lane);
+            warp_etr(vrr, L, etr, sh, t, lane);
+            // acc[f-block][e][ke][kf] += w * level f, e in [emin, emax]
+            int off = 0;
+            for (int f = lc; f <= lf; ++f) {
+              int ncf = ncart(f);
+              int n = (cart_offset(emax + 1) - cart_offset(emin)) * ncf;
+              for (int idx = lane; idx < n; idx += 32) {
+                int r = idx / ncf, kf = idx - r * ncf;
+                int e = emin;
+                while (cart_offset(e + 1) - cart_offset(emin) <= r) ++e;
+                int ke = r - (cart_offset(e) - cart_offset(emin));
+                acc[off + idx] += w * etr_get(vrr, L, etr, sh, f, e, ke, kf);
+              }
+              off += n;
+            }
+            __syncwarp();
+          }
+    // bra HRR for every ket level f
+    double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
+    {
+      int aoff = 0, boff = 0;
+      for (int f = lc; f <= lf; ++f) {
+        int ncf = ncart(f);
+        const double* out = warp_hrr(acc + aoff, emin, la, lb, f, AB, scr, half, lane);
+        for (int i = lane; i < na * nb * ncf; i += 32) bra[boff + i] = out[i];
+        __syncwarp();
+        aoff += (cart_offset(emax + 1) - cart_offset(emin)) * ncf;
+        boff += na * nb * ncf;
+      }
+    }
+    // ket HRR: (ab|c, d+1_i) = (ab|c+1_i, d) + CD_i (ab|c, d), CD = AB; rows f in
+    // [lc, lf - d]; ping-pong in scr; diagonal (mu nu|mu nu) at the end
+    double qmax = 0.0;
+    {
+      const int nab = na * nb;
+      const double* prev = bra;           // level d' = 0: [f][ab][kf] packed by f blocks
+      int prev_nd = 1;
+      double* bufs[2] = {scr, scr + half};
+      for (int d = 1; d <= ld; ++d) {
+        double* cur = bufs[(d - 1) & 1];
+        int nd = ncart(d);
+        int fhi = lf - d;
+        int n = 0;
+        for (int f = lc; f <= fhi; ++f) n += nab * ncart(f) * nd;
+        for (int idx = lane; idx < n; idx += 32) {
+          // decode idx -> (f, ab, kf, kd) with layout [f-block][ab][kf][kd]
+          int rem = idx, f = lc;
+          while (rem >= nab * ncart(f) * nd) { rem -= nab * ncart(f) * nd; ++f; }
+          int ncf = ncart(f);
+          int kd = rem % nd, r2 = rem / nd, kf = r2 % ncf, ab = r2 / ncf;
+          int dx, dy, dz, fx, fy, fz;
+          cart_decode(d, kd, dx, dy, dz);
+          cart_decode(f, kf, fx, fy, fz);
+          int i = dx > 0 ? 0 : (dy > 0 ? 1 : 2);
+          int dl[3] = {dx, dy, dz};
+          dl[i] -= 1;
+          int kdl = cart_index(d - 1, dl[0], dl[1]);
+          int fp[3] = {fx, fy, fz};
+          fp[i] += 1;
+          int kfp = cart_index(f + 1, fp[0], fp[1]);
+          // offsets of level f and f+1 in prev: [f-block][ab][kf][kd_prev]
+          int o_f = 0;
+          for (int g = lc; g < f; ++g) o_f += nab * ncart(g) * prev_nd;
+          int o_f1 = o_f + nab * ncf * prev_nd;
+          double v = prev[o_f1 + (ab * ncart(f + 1) + kfp) * prev_nd + kdl] +
+                     AB[i] * prev[o_f + (ab * ncf + kf) * prev_nd + kdl];
+          cur[idx] = v;
+        }
+        __syncwarp();
+        prev = cur;
+        prev_nd = nd;
+      }
+      // prev now holds level f = lc only: [ab][kc][kd] with (kc, kd) over (la, lb) = (ka, kb)
+      for (int idx = lane; idx < nab; idx += 32) {
+        int ka = idx / nb, kb = idx % nb;
+        double v = prev[(idx * ncart(lc) + ka) * prev_nd + kb];
+        qmax = fmax(qmax, fabs(v));
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+    if (lane == 0) {
+      int a0 = max(sa, sb), b0 = min(sa, sb);
+      Q[(long long)a0 * (a0 + 1) / 2 + b0] = sqrt(qmax);
+    }
+    __syncwarp();
+  }
+}
+
 // ------------------------------------------------------------ launchers
 
 // ordered: only classes with la >= lb occur
@@ -440,6 +622,22 @@ void launch_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, double
   set_smem((const void*)eri2_kernel, smem);
   RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
   eri2_kernel<<<grid_for(smem), 32, smem, ic.stream>>>(aux, ic.boys, ic.counter, A);
+  RIHF_LAUNCH_CHECK();
+  if (ic.launches) *ic.launches += 1;
+}
+
+int schwarz_smem_bytes(int max_lp) {
+  int best = 0;
+  for (int la = 0; la <= max_lp; ++la)
+    for (int lb = 0; lb <= la; ++lb) best = std::max(best, schwarz_smem(la, lb, nullptr));
+  return best * (int)sizeof(double);
+}
+
+void launch_schwarz(const IntegralCtx& ic, const DevShells& prim, int max_lp, double* Q) {
+  int smem = schwarz_smem_bytes(max_lp);
+  set_smem((const void*)schwarz_kernel, smem);
+  RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+  schwarz_kernel<<<grid_for(smem), 32, smem, ic.stream>>>(prim, ic.boys, ic.counter, Q);
   RIHF_LAUNCH_CHECK();
   if (ic.launches) *ic.launches += 1;
 }

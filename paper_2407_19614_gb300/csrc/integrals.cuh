@@ -50,6 +50,8 @@ void launch_one_electron(const IntegralCtx& ic, const DevShells& prim, int max_l
 // Schwarz factors Q_ab = sqrt(max |(ab|ab)|) over all shell pairs a >= b,
 // pair index a*(a+1)/2 + b.
 void launch_schwarz(const IntegralCtx& ic, const DevShells& prim, int max_lp, double* Q);
+// Shared memory (bytes) launch_schwarz needs for primary l <= max_lp.
+int schwarz_smem_bytes(int max_lp);
 
 // Gradient contractions (derivative integrals evaluated on the fly):
 //   grad[atom][x] += sum_{mu nu P} Y[P][mu][nu] d(mu nu|P)/dR          (3-centre)

@@ -397,6 +397,9 @@ struct rihf_ctx {
   int* d_counter = nullptr;
   int* d_flag = nullptr;
   ShellPair* d_pairs = nullptr;
+  double* d_schwarz = nullptr;
+  bool schwarz_ok = false;
+  double schwarz_max_dropped = 0.0;
 
   // geometry-dependent matrices
   double *S = nullptr, *H = nullptr, *Tk = nullptr, *V = nullptr;
@@ -481,7 +484,7 @@ static std::vector<double>& boys_host() {
 static void free_all(rihf_ctx* c) {
   void* ptrs[] = {c->d_pl, c->d_patom, c->d_pnprim, c->d_pps, c->d_pao, c->d_pxyz, c->d_pexp, c->d_pcoef,
                   c->d_al, c->d_aatom, c->d_anprim, c->d_aps, c->d_aao, c->d_axyz_sh, c->d_aexp, c->d_acoef,
-                  c->d_tr, c->d_nf, c->d_Z, c->d_xyz, c->d_boys, c->d_counter, c->d_flag, c->d_pairs,
+                  c->d_tr, c->d_nf, c->d_Z, c->d_xyz, c->d_boys, c->d_counter, c->d_flag, c->d_pairs, c->d_schwarz,
                   c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->T3, c->B, c->Xo, c->Sw, c->Sv,
                   c->C, c->eps, c->Ct, c->D, c->J, c->K, c->F, c->Fx, c->T1, c->T2, c->Err, c->Fp, c->Cp, c->Hb,
                   c->dvec, c->Fring, c->Ering, c->Bdiis, c->coef, c->scal, c->Cprev,
@@ -526,6 +529,24 @@ static void compute_geometry(rihf_ctx* c) {
   { TraceScope t(c->tracer, s, "cholesky A=LL^T", (double)NA * NA * NA / 3.0, 0);
     cholesky(la, c->L, NA, c->scratch); }
   c->have_linv = false;
+  // Schwarz screening (Sec. 3.1.1): keep shell pairs with max (mu nu|mu nu) > tau
+  if (c->schwarz_ok) {
+    TraceScope t(c->tracer, s, "schwarz_kernel (ab|ab)", 0.0, 0);
+    launch_schwarz(ic, P, c->max_lp, c->d_schwarz);
+    std::vector<double> q(c->npairs_total);
+    RIHF_CUDA(cudaMemcpyAsync(q.data(), c->d_schwarz, sizeof(double) * q.size(), cudaMemcpyDeviceToHost, s));
+    RIHF_CUDA(cudaStreamSynchronize(s));
+    c->pairs_h.clear();
+    c->schwarz_max_dropped = 0.0;
+    for (int a = 0; a < c->hp.nshell; ++a)
+      for (int b = 0; b <= a; ++b) {
+        double qa = q[(size_t)a * (a + 1) / 2 + b];
+        if (qa * qa > c->opt.schwarz_tau) c->pairs_h.push_back({a, b});
+        else c->schwarz_max_dropped = std::max(c->schwarz_max_dropped, qa * qa);
+      }
+    c->npairs = (int)c->pairs_h.size();
+    upload(c->d_pairs, c->pairs_h, s);
+  }
   // (mu nu|P) for shell pairs a >= b, then B = L^{-1} T (Eq. biap with A^L = L^{-T})
   // by blocked forward substitution on the lower-triangle columns; an explicit
   // L^{-1} product loses accuracy when cond(A) reaches 1e9 (diffuse auxiliary sets)
@@ -625,7 +646,7 @@ void rihf_default_options(rihf_options* o) {
   if (!o) return;
   o->precision = RIHF_PRECISION_FP64;
   o->pure = 1;
-  o->schwarz_tau = 1e-14;
+  o->schwarz_tau = 0.0;   // keep every pair: the fit amplifies dropped integrals when cond(P|Q) is large
   o->lindep_tau = 1e-8;
   o->conv_e = 1e-10;
   o->conv_diis = 1e-9;
@@ -725,11 +746,18 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     c->d_boys = dalloc<double>((size_t)kBoysN * kBoysM); upload(c->d_boys, boys_host(), s);
     c->d_counter = dalloc<int>(4);
     c->d_flag = dalloc<int>(4);
-    // shell pairs a >= b (Schwarz screening keeps all at the default threshold)
+    // shell pairs a >= b; compute_geometry screens them (Schwarz) when the
+    // four-centre class fits in shared memory, otherwise all pairs are kept
     for (int a = 0; a < c->hp.nshell; ++a)
       for (int b = 0; b <= a; ++b) c->pairs_h.push_back({a, b});
     c->npairs = c->npairs_total = (int)c->pairs_h.size();
     c->d_pairs = dalloc<ShellPair>(c->pairs_h.size()); upload(c->d_pairs, c->pairs_h, s);
+    c->d_schwarz = dalloc<double>(c->pairs_h.size());
+    {
+      int maxsm = 0;
+      RIHF_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->opt.device));
+      c->schwarz_ok = schwarz_smem_bytes(c->max_lp) <= maxsm;
+    }
     // matrices
     size_t n2 = (size_t)N * N, na2 = (size_t)NA * NA, big = (size_t)NA * n2;
     c->S = dalloc<double>(n2); c->H = dalloc<double>(n2); c->Tk = dalloc<double>(n2); c->V = dalloc<double>(n2);
@@ -1246,6 +1274,10 @@ int rihf_get_matrix(rihf_ctx* c, int which, double* out) {
       }
       break;
     }
+    case RIHF_MAT_SCHWARZ:
+      if (c->schwarz_ok) RIHF_CUDA(cudaMemcpy(out, c->d_schwarz, sizeof(double) * c->npairs_total, cudaMemcpyDeviceToHost));
+      else std::memset(out, 0, sizeof(double) * c->npairs_total);
+      break;
     case RIHF_MAT_GRAD_PARTS:
       if (c->grad_parts_h.empty()) return RIHF_ERR_STATE;
       std::memcpy(out, c->grad_parts_h.data(), sizeof(double) * 15 * c->natoms);
