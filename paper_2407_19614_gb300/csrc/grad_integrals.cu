@@ -36,7 +36,7 @@ struct DerivPlan {
     L = emax + lc;
     EtrShape sh{lc, emin, emax};
     int accsz = acc_size(emin, emax, lc);
-    int big = ncart(la + 1) * ncart(lb + 1) * ncart(lc);
+    int nabc = ncart(la) * ncart(lb) * ncart(lc);
     fm = 0;
     vrr = 24;
     etr = vrr + vrr_size(L);
@@ -44,15 +44,14 @@ struct DerivPlan {
     accA = acc0 + accsz;
     accB = accA + accsz;
     ycart = accB + accsz;
-    t1 = ycart + ncart(la) * ncart(lb) * ncart(lc);
-    t2 = t1 + big;
-    hrr = t2 + big;
-    half = 0;
+    hrr = ycart + nabc;
+    half = nabc;   // the Y back-transform scratch (t1, t2) reuses the HRR region
     int cand[4] = {hrr_scratch(la + 1, lb, lc, emax), la > 0 ? hrr_scratch(la - 1, lb, lc, emax) : 0,
                    hrr_scratch(la, lb + 1, lc, emax), lb > 0 ? hrr_scratch(la, lb - 1, lc, emax) : 0};
     for (int i = 0; i < 4; ++i)
       if (cand[i] / 2 > half) half = cand[i] / 2;
-    if (big > half) half = big;
+    t1 = hrr;
+    t2 = hrr + half;
     total = hrr + 2 * half;
   }
 };
@@ -372,8 +371,8 @@ __global__ void __launch_bounds__(32) grad_one_electron_kernel(DevShells prim, i
       if (ata == atb) continue;   // overlap and kinetic depend on A - B only
       // Dcart (for T) into ycart, Wcart into t1-region copy
       double* Dc = smem + pl.ycart;
-      double* Wc = smem + pl.hrr;   // hrr region unused here
-      double* s1d = smem + pl.total;  // 3 x 64 past the plan
+      double* Wc = smem + pl.total;   // past the plan (the HRR region holds t1/t2)
+      double* s1d = Wc + 128;         // 3 x 64
       warp_back_transform(D + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa,
                           nfb, 1, smem + pl.t1, smem + pl.t2, Dc, lane);
       warp_back_transform(W + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa,
@@ -507,7 +506,7 @@ void launch_grad_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, c
 void launch_grad_one_electron(const IntegralCtx& ic, const DevShells& prim, int max_lp, int natoms, const int* Z,
                               const double* axyz, const double* D, const double* W, double* grad_one,
                               double* grad_ovl) {
-  int smem = deriv_smem(max_lp, max_lp, 0) + 3 * 64 * (int)sizeof(double);
+  int smem = deriv_smem(max_lp, max_lp, 0) + (128 + 3 * 64) * (int)sizeof(double);
   RIHF_CUDA(cudaFuncSetAttribute(grad_one_electron_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
   grad_one_electron_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, natoms, Z, axyz, ic.boys, ic.counter,

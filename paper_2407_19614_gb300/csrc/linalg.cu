@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(GemmArgs g, int nsplit, int 
     bool spans = (j0 / g.symcols) != (j1 / g.symcols);
     if (!spans && (j0 % g.symcols) > (j0 / g.symcols)) return;
   }
+  if (g.lower_only && n0 > m0) return;
   int b_lo, b_hi, k_lo, k_hi, slot_b, slot_s;
   if (g.reduce_batch) {
     slot_s = z;
@@ -107,6 +108,7 @@ __global__ void splitk_reduce_kernel(GemmArgs g, int nsplit, const double* __res
       bool spans = (j0 / g.symcols) != (j1 / g.symcols);
       if (!spans && (j0 % g.symcols) > (j0 / g.symcols)) continue;
     }
+    if (g.lower_only && (n / GT) > (m / GT)) continue;
     double s = 0.0;
     for (int q = 0; q < nsplit; ++q) s += work[((long long)b * nsplit + q) * g.M * g.N + mn];
     double* c = g.C + (g.reduce_batch ? 0 : (long long)b * g.sC) + (long long)m * g.ldc + n;

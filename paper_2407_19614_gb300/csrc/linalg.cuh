@@ -40,6 +40,7 @@ struct GemmArgs {
   bool reduce_batch = false;
   bool lowerA = false;
   int symcols = 0;
+  bool lower_only = false;   // symmetric result: compute tiles on/below the diagonal only
 };
 void dgemm(const LaCtx& la, const GemmArgs& g);
 

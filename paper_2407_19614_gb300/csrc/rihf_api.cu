@@ -833,7 +833,7 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
   RIHF_CUDA(cudaMemsetAsync(c->eps, 0, sizeof(double) * N, c->stream));
   {
     const bool use_prev = warm && c->have_cprev;
-    const bool skip = use_prev && c->last_err < 1e-3;
+    const bool skip = use_prev && c->last_err < 1e-2;
     TraceScope t(c->tracer, c->stream, skip ? "eigh F' (refine only)" : "eigh F' (jacobi+refine)", 0.0, 0);
     eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, use_prev ? c->Cprev : nullptr, skip);
     if (skip) {
@@ -919,8 +919,10 @@ static void fock_build(rihf_ctx* c, bool fp32) {
   gk.M = N; gk.N = N; gk.K = no; gk.A = c->Hb; gk.lda = no; gk.sA = (long long)N * no;
   gk.B = c->Hb; gk.ldb = no; gk.sB = (long long)N * no; gk.transB = true;
   gk.C = c->K; gk.ldc = N; gk.batch = NA; gk.reduce_batch = true; gk.alpha = -0.5;
+  gk.lower_only = true;   // K is symmetric: lower tiles only, then mirror
   { TraceScope t(c->tracer, c->stream, "RI-K K=-1/2 sum H H^T (dgemm)", 2.0 * NA * n2 * no, 0);
-    dgemm(la, gk); }
+    dgemm(la, gk);
+    symmetrize_lower(la, c->K, N, 1); }
   add3(la, (int)n2, c->H, c->J, c->K, c->F);
   if (c->Fprev) {   // reference for the next incremental build
     RIHF_CUDA(cudaMemcpyAsync(c->Fprev, c->F, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
@@ -1164,11 +1166,13 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   GemmArgs gz;
   gz.M = NA; gz.N = NA; gz.K = no * no; gz.A = c->Xt; gz.lda = no * no; gz.B = c->Xt; gz.ldb = no * no;
   gz.transB = true; gz.C = c->Zm; gz.ldc = NA; gz.alpha = -0.5;
+  gz.lower_only = true;   // Z is symmetric
   dgemm(la, gz);
   GemmArgs gc;
   gc.M = NA; gc.N = NA; gc.K = 1; gc.A = c->cvec; gc.lda = 1; gc.B = c->cvec; gc.ldb = NA; gc.C = c->Zm; gc.ldc = NA;
   gc.beta = 1.0;
   dgemm(la, gc);
+  symmetrize_lower(la, c->Zm, NA, 1);
   // Y[P] = D c_P - 1/2 Ct Xt[P] Ct^T ; G[P] = Xt[P] Ct^T (nocc x N)
   GemmArgs gg;
   gg.M = no; gg.N = N; gg.K = no; gg.A = c->Xt; gg.lda = no; gg.sA = (long long)no * no;
