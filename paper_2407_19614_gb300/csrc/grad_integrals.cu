@@ -165,18 +165,19 @@ __device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, in
 // ------------------------------------------------------------ 3-centre
 
 __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells aux,
-                                                       const ShellPair* __restrict__ pairs, int npairs,
+                                                       const ShellPair* __restrict__ pairs,
+                                                       const int2* __restrict__ tasks, long long ntask,
                                                        const double* __restrict__ boys, int* counter,
                                                        const double* __restrict__ Y, double* grad) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x;
-  const long long ntask = (long long)npairs * aux.nshell;
   const int N = prim.nfunc;
   const long long N2 = (long long)N * N;
   for (;;) {
     long long task = warp_next(counter, lane);
     if (task >= ntask) break;
-    int ip = (int)(task % npairs), sc = (int)(task / npairs);
+    const int2 tk = tasks[task];
+    int ip = tk.x, sc = tk.y;
     int sa = pairs[ip].a, sb = pairs[ip].b;
     if (prim.l[sa] < prim.l[sb]) { int t = sa; sa = sb; sb = t; }   // Y is symmetric in mu, nu
     int ata = prim.atom[sa], atb = prim.atom[sb], atc = aux.atom[sc];
@@ -483,15 +484,23 @@ static int deriv_smem(int max_la, int max_lb, int max_lc) {
   return (best + 8) * (int)sizeof(double);
 }
 
+int smem_grad_doubles(int la, int lb, int lc) {
+  DerivPlan p(la, lb, lc);
+  return p.total + 8;
+}
+
 void launch_grad_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
-                      int npairs, int max_lp, int max_la, const double* Y, double* grad) {
-  int smem = deriv_smem(max_lp, max_lp, max_la);
-  RIHF_CUDA(cudaFuncSetAttribute(grad_eri3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
-  grad_eri3_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, aux, pairs, npairs, ic.boys, ic.counter, Y,
-                                                                 grad);
-  RIHF_LAUNCH_CHECK();
-  if (ic.launches) *ic.launches += 1;
+                      const TaskGroup* groups, int ngroups, const double* Y, double* grad) {
+  for (int g = 0; g < ngroups; ++g) {
+    if (groups[g].ntask == 0) continue;
+    int smem = groups[g].smem_grad;
+    RIHF_CUDA(cudaFuncSetAttribute(grad_eri3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+    grad_eri3_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, aux, pairs, groups[g].tasks,
+                                                                   groups[g].ntask, ic.boys, ic.counter, Y, grad);
+    RIHF_LAUNCH_CHECK();
+    if (ic.launches) *ic.launches += 1;
+  }
 }
 
 void launch_grad_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, const double* Z, double* grad) {

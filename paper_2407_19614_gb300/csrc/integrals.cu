@@ -136,17 +136,18 @@ int smem_eri3_doubles(int la, int lb, int lc) {
 // ------------------------------------------------------------ (mu nu|P)
 
 __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux, const ShellPair* __restrict__ pairs,
-                                                  int npairs, const double* __restrict__ boys, int* counter,
+                                                  const int2* __restrict__ tasks, long long ntask,
+                                                  const double* __restrict__ boys, int* counter,
                                                   double* __restrict__ T) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x;
-  const long long ntask = (long long)npairs * aux.nshell;
   const int N = prim.nfunc;
   const size_t N2 = (size_t)N * N;
   for (;;) {
     long long task = warp_next_task(counter, lane);
     if (task >= ntask) break;
-    int ip = (int)(task % npairs), sc = (int)(task / npairs);
+    const int2 tk = tasks[task];
+    int ip = tk.x, sc = tk.y;
     int sa = pairs[ip].a, sb = pairs[ip].b;
     // compute with la >= lb (cheaper HRR); the stored block keeps mu in pairs[ip].a
     const bool swp = prim.l[sa] < prim.l[sb];
@@ -607,14 +608,50 @@ static void set_smem(const void* fn, int bytes) {
 }
 
 void launch_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
-                 int npairs, int max_lp, int max_la, double* T) {
-  if (npairs == 0 || aux.nshell == 0) return;
-  int smem = max_smem_eri3(max_lp, max_lp, max_la) * (int)sizeof(double);
-  set_smem((const void*)eri3_kernel, smem);
-  RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
-  eri3_kernel<<<grid_for(smem), 32, smem, ic.stream>>>(prim, aux, pairs, npairs, ic.boys, ic.counter, T);
-  RIHF_LAUNCH_CHECK();
-  if (ic.launches) *ic.launches += 1;
+                 const TaskGroup* groups, int ngroups, double* T) {
+  for (int g = 0; g < ngroups; ++g) {
+    if (groups[g].ntask == 0) continue;
+    int smem = groups[g].smem_eri3;
+    set_smem((const void*)eri3_kernel, smem);
+    RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+    eri3_kernel<<<grid_for(smem), 32, smem, ic.stream>>>(prim, aux, pairs, groups[g].tasks, groups[g].ntask,
+                                                         ic.boys, ic.counter, T);
+    RIHF_LAUNCH_CHECK();
+    if (ic.launches) *ic.launches += 1;
+  }
+}
+
+// Class-grouped task lists: every (pair, auxiliary shell) task goes to the first
+// group whose shared-memory bound covers both its integral and its derivative
+// class, so light classes run with many resident warps per SM.
+void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim,
+                       const std::vector<int>& laux, std::vector<std::vector<int2>>& tasks,
+                       std::vector<int>& smem_eri3, std::vector<int>& smem_grad) {
+  // about 17, 7 and at most 2 warps per SM (228 KB shared memory, 1 KB reserved per block)
+  const int limits[kTaskGroups] = {12 * 1024, 28 * 1024, 1 << 30};
+  constexpr int nl = kMaxLPrim + 1, nc = kMaxLAux + 1;
+  int se[nl][nl][nc], sg[nl][nl][nc], grp[nl][nl][nc];
+  for (int la = 0; la < nl; ++la)
+    for (int lb = 0; lb < nl; ++lb)
+      for (int lc = 0; lc < nc; ++lc) {
+        se[la][lb][lc] = smem_eri3_doubles(la, lb, lc) * (int)sizeof(double);
+        sg[la][lb][lc] = smem_grad_doubles(la, lb, lc) * (int)sizeof(double);
+        int need = std::max(se[la][lb][lc], sg[la][lb][lc]), g = 0;
+        while (g + 1 < kTaskGroups && need > limits[g]) ++g;
+        grp[la][lb][lc] = g;
+      }
+  tasks.assign(kTaskGroups, {});
+  smem_eri3.assign(kTaskGroups, 0);
+  smem_grad.assign(kTaskGroups, 0);
+  for (int c = 0; c < (int)laux.size(); ++c)
+    for (int p = 0; p < (int)pairs.size(); ++p) {
+      int la = lprim[pairs[p].a], lb = lprim[pairs[p].b];
+      if (la < lb) std::swap(la, lb);
+      const int lc = laux[c], g = grp[la][lb][lc];
+      tasks[g].push_back(make_int2(p, c));
+      smem_eri3[g] = std::max(smem_eri3[g], se[la][lb][lc]);
+      smem_grad[g] = std::max(smem_grad[g], sg[la][lb][lc]);
+    }
 }
 
 void launch_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, double* A) {

@@ -1,5 +1,7 @@
 // Host-visible declarations of the integral kernels (integrals.cu).
 #pragma once
+#include <vector>
+
 #include "common.cuh"
 
 namespace rihf {
@@ -32,13 +34,26 @@ struct IntegralCtx {
   long long* launches = nullptr; // host-side launch counter
 };
 
-// Largest dynamic shared-memory slice one warp needs for a class.
+// Shared memory (doubles) one warp needs for a (la >= lb | lc) class of the
+// integral and of the derivative kernel.
 int smem_eri3_doubles(int la, int lb, int lc);
+int smem_grad_doubles(int la, int lb, int lc);
+
+// (pair index, auxiliary shell) tasks of one shared-memory class group.
+constexpr int kTaskGroups = 3;
+struct TaskGroup {
+  const int2* tasks = nullptr;
+  long long ntask = 0;
+  int smem_eri3 = 0, smem_grad = 0;   // bytes
+};
+void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim,
+                       const std::vector<int>& laux, std::vector<std::vector<int2>>& tasks,
+                       std::vector<int>& smem_eri3, std::vector<int>& smem_grad);
 
 // Three-centre integrals T[P][mu][nu] = (mu nu|P) for the listed shell pairs
 // (mu in a, nu in b, a >= b; both triangles inside diagonal shell blocks).
 void launch_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
-                 int npairs, int max_lp, int max_la, double* T);
+                 const TaskGroup* groups, int ngroups, double* T);
 
 // Metric A[P][Q] = (P|Q) (full symmetric matrix).
 void launch_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, double* A);
@@ -58,7 +73,7 @@ int schwarz_smem_bytes(int max_lp);
 //   grad[atom][x] += -1/2 sum_PQ Z[P][Q] d(P|Q)/dR                      (2-centre)
 //   grad[atom][x] += sum D d(T+V)/dR - sum W dS/dR                      (one-electron)
 void launch_grad_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
-                      int npairs, int max_lp, int max_la, const double* Y, double* grad);
+                      const TaskGroup* groups, int ngroups, const double* Y, double* grad);
 void launch_grad_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, const double* Z, double* grad);
 void launch_grad_one_electron(const IntegralCtx& ic, const DevShells& prim, int max_lp, int natoms, const int* Z,
                               const double* axyz, const double* D, const double* W, double* grad_one,

@@ -397,6 +397,8 @@ struct rihf_ctx {
   int* d_counter = nullptr;
   int* d_flag = nullptr;
   ShellPair* d_pairs = nullptr;
+  int2* d_tasks = nullptr;           // (pair, auxiliary shell) tasks, grouped by shared-memory class
+  TaskGroup groups[kTaskGroups];
   double* d_schwarz = nullptr;
   bool schwarz_ok = false;
   double schwarz_max_dropped = 0.0;
@@ -481,10 +483,26 @@ static std::vector<double>& boys_host() {
   return tab;
 }
 
+// Rebuild the class-grouped 3-centre task lists from the current pair list.
+static void refresh_tasks(rihf_ctx* c) {
+  std::vector<std::vector<int2>> tasks;
+  std::vector<int> se, sg;
+  build_task_groups(c->pairs_h, c->hp.l, c->ha.l, tasks, se, sg);
+  size_t off = 0;
+  for (int g = 0; g < kTaskGroups; ++g) {
+    c->groups[g].tasks = c->d_tasks + off;
+    c->groups[g].ntask = (long long)tasks[g].size();
+    c->groups[g].smem_eri3 = se[g];
+    c->groups[g].smem_grad = sg[g];
+    upload(c->d_tasks + off, tasks[g], c->stream);
+    off += tasks[g].size();
+  }
+}
+
 static void free_all(rihf_ctx* c) {
   void* ptrs[] = {c->d_pl, c->d_patom, c->d_pnprim, c->d_pps, c->d_pao, c->d_pxyz, c->d_pexp, c->d_pcoef,
                   c->d_al, c->d_aatom, c->d_anprim, c->d_aps, c->d_aao, c->d_axyz_sh, c->d_aexp, c->d_acoef,
-                  c->d_tr, c->d_nf, c->d_Z, c->d_xyz, c->d_boys, c->d_counter, c->d_flag, c->d_pairs, c->d_schwarz,
+                  c->d_tr, c->d_nf, c->d_Z, c->d_xyz, c->d_boys, c->d_counter, c->d_flag, c->d_pairs, c->d_tasks, c->d_schwarz,
                   c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->T3, c->B, c->Xo, c->Sw, c->Sv,
                   c->C, c->eps, c->Ct, c->D, c->J, c->K, c->F, c->Fx, c->T1, c->T2, c->Err, c->Fp, c->Cp, c->Hb,
                   c->dvec, c->Fring, c->Ering, c->Bdiis, c->coef, c->scal, c->Cprev,
@@ -536,6 +554,7 @@ static void compute_geometry(rihf_ctx* c) {
     std::vector<double> q(c->npairs_total);
     RIHF_CUDA(cudaMemcpyAsync(q.data(), c->d_schwarz, sizeof(double) * q.size(), cudaMemcpyDeviceToHost, s));
     RIHF_CUDA(cudaStreamSynchronize(s));
+    const std::vector<ShellPair> old = c->pairs_h;
     c->pairs_h.clear();
     c->schwarz_max_dropped = 0.0;
     for (int a = 0; a < c->hp.nshell; ++a)
@@ -544,15 +563,21 @@ static void compute_geometry(rihf_ctx* c) {
         if (qa * qa > c->opt.schwarz_tau) c->pairs_h.push_back({a, b});
         else c->schwarz_max_dropped = std::max(c->schwarz_max_dropped, qa * qa);
       }
-    c->npairs = (int)c->pairs_h.size();
-    upload(c->d_pairs, c->pairs_h, s);
+    const bool same = old.size() == c->pairs_h.size() &&
+                      std::equal(old.begin(), old.end(), c->pairs_h.begin(),
+                                 [](const ShellPair& x, const ShellPair& y) { return x.a == y.a && x.b == y.b; });
+    if (!same) {
+      c->npairs = (int)c->pairs_h.size();
+      upload(c->d_pairs, c->pairs_h, s);
+      refresh_tasks(c);
+    }
   }
   // (mu nu|P) for shell pairs a >= b, then B = L^{-1} T (Eq. biap with A^L = L^{-T})
   // by blocked forward substitution on the lower-triangle columns; an explicit
   // L^{-1} product loses accuracy when cond(A) reaches 1e9 (diffuse auxiliary sets)
   RIHF_CUDA(cudaMemsetAsync(c->T3, 0, sizeof(double) * (size_t)NA * N * N, s));
   { TraceScope t(c->tracer, s, "eri3_kernel (mu nu|P)", (double)NA * N * (N + 1) / 2 * 8, 1);
-    launch_eri3(ic, P, X, c->d_pairs, c->npairs, c->max_lp, c->max_la, c->T3); }
+    launch_eri3(ic, P, X, c->d_pairs, c->groups, kTaskGroups, c->T3); }
   RIHF_CUDA(cudaMemcpyAsync(c->B, c->T3, sizeof(double) * (size_t)NA * N * N, cudaMemcpyDeviceToDevice, s));
   { TraceScope t(c->tracer, s, "fit trsm B=L^-1 T", (double)NA * NA * N * (N + 1) / 2, 0);
     trsm_lower(la, c->L, NA, c->B, (long long)N * N, false, N, c->trsm_tmp); }
@@ -753,6 +778,8 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     c->npairs = c->npairs_total = (int)c->pairs_h.size();
     c->d_pairs = dalloc<ShellPair>(c->pairs_h.size()); upload(c->d_pairs, c->pairs_h, s);
     c->d_schwarz = dalloc<double>(c->pairs_h.size());
+    c->d_tasks = dalloc<int2>(c->pairs_h.size() * (size_t)c->ha.nshell);
+    refresh_tasks(c);
     {
       int maxsm = 0;
       RIHF_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->opt.device));
@@ -1193,7 +1220,7 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   { TraceScope t(c->tracer, s, "grad_one_electron_kernel", 0.0, 0);
     launch_grad_one_electron(ic, c->prim(), c->max_lp, nat, c->d_Z, c->d_xyz, c->D, c->W, g_one, g_ovl); }
   { TraceScope t(c->tracer, s, "grad_eri3_kernel (fused d(mu nu|P) . Y)", (double)NA * N * (N + 1) / 2 * 8, 1);
-    launch_grad_eri3(ic, c->prim(), c->aux(), c->d_pairs, c->npairs, c->max_lp, c->max_la, c->Y, g_three); }
+    launch_grad_eri3(ic, c->prim(), c->aux(), c->d_pairs, c->groups, kTaskGroups, c->Y, g_three); }
   { TraceScope t(c->tracer, s, "grad_eri2_kernel (fused d(P|Q) . Z)", (double)NA * NA * 8, 1);
     launch_grad_eri2(ic, c->aux(), c->max_la, c->Zm, g_two); }
   c->grad_parts_h.assign(15 * nat, 0.0);
