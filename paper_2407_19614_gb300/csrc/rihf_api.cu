@@ -17,6 +17,7 @@
 #include "jk.cuh"
 #include "linalg.cuh"
 #include "os_hgp.cuh"
+#include "tc_gemm.cuh"
 
 using namespace rihf;
 
@@ -1400,6 +1401,62 @@ int rihf_eigh(int n, const double* A, double* W, double* V, int device) {
   }
   cudaFree(dA); cudaFree(dW); cudaFree(dV); cudaFree(ws); cudaFree(work); cudaFree(flag);
   cudaStreamDestroy(s);
+  return RIHF_OK;
+  RIHF_API_END
+}
+
+int rihf_tc_dgemm(int M, int N, int K, const double* A, const double* B, double* C, int digits, int kblock,
+                  int device) {
+  RIHF_API_BEGIN
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || digits < 1 || digits > kOzMaxDigits || kblock < 0)
+    return RIHF_ERR_INVALID_ARG;
+  RIHF_CUDA(cudaSetDevice(device));
+  cudaStream_t s;
+  RIHF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  std::vector<void*> bufs;
+  auto alloc = [&](size_t bytes) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) throw RihfError(RIHF_ERR_OOM, "cudaMalloc failed");
+    bufs.push_back(p);
+    return p;
+  };
+  auto release = [&]() {
+    for (void* p : bufs) cudaFree(p);
+    cudaStreamDestroy(s);
+  };
+  try {
+    const int kchunks = (K + kOzChunk - 1) / kOzChunk;
+    const int kbc = kblock > 0 ? std::min(kblock, kchunks) : kchunks;
+    const int nkb = (kchunks + kbc - 1) / kbc;
+    double* dA = (double*)alloc(sizeof(double) * M * K);
+    double* dB = (double*)alloc(sizeof(double) * N * K);
+    double* dC = (double*)alloc(sizeof(double) * M * N);
+    int* flag = (int*)alloc(4 * sizeof(int));
+    uint16_t* pa = (uint16_t*)alloc(2 * oz_plane_elems(M, K, digits));
+    uint16_t* pb = (uint16_t*)alloc(2 * oz_plane_elems(N, K, digits));
+    int* ea = (int*)alloc(sizeof(int) * ((M + kOzTileM - 1) / kOzTileM * kOzTileM) * nkb);
+    int* eb = (int*)alloc(sizeof(int) * ((N + kOzTileM - 1) / kOzTileM * kOzTileM) * nkb);
+    RIHF_CUDA(cudaMemcpyAsync(dA, A, sizeof(double) * M * K, cudaMemcpyHostToDevice, s));
+    RIHF_CUDA(cudaMemcpyAsync(dB, B, sizeof(double) * N * K, cudaMemcpyHostToDevice, s));
+    RIHF_CUDA(cudaMemsetAsync(dC, 0, sizeof(double) * M * N, s));
+    RIHF_CUDA(cudaMemsetAsync(flag, 0, 4 * sizeof(int), s));
+    LaCtx la;
+    la.stream = s; la.flag = flag;
+    OzGemmArgs g;
+    g.A = oz_slice(la, dA, M, K, K, 1, 0, K, digits, kbc, pa, ea);
+    g.B = oz_slice(la, dB, N, K, K, 1, 0, K, digits, kbc, pb, eb);
+    g.M = M; g.N = N; g.s = digits; g.C = dC; g.cs_m1 = N; g.cs_n = 1; g.atomic = nkb > 1;
+    oz_gemm(la, g);
+    int hflag[4];
+    RIHF_CUDA(cudaMemcpyAsync(C, dC, sizeof(double) * M * N, cudaMemcpyDeviceToHost, s));
+    RIHF_CUDA(cudaMemcpyAsync(hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, s));
+    RIHF_CUDA(cudaStreamSynchronize(s));
+    if (hflag[1]) throw RihfError(RIHF_ERR_TIMEOUT, "tensor-core GEMM: a bounded wait ran out");
+  } catch (...) {
+    release();
+    throw;
+  }
+  release();
   return RIHF_OK;
   RIHF_API_END
 }

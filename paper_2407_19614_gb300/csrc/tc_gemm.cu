@@ -1,0 +1,427 @@
+// BF16 digit-plane GEMM on the 5th-generation tensor cores (tcgen05 + TMEM),
+// operands staged in shared memory by bulk asynchronous copies.  See
+// tc_gemm.cuh for the number format.
+#include <algorithm>
+
+#include "../../include/rihf.h"
+#include "tc_gemm.cuh"
+
+namespace rihf {
+
+namespace {
+
+constexpr int kOzThreads = 256;
+constexpr int kPlaneElems = kOzTileM * kOzChunk;          // 8192 BF16 = 16 KB
+constexpr int kSmemA = kOzMaxDigits * kPlaneElems * 2;     // 112 KB
+constexpr int kSmemB = kOzMaxDigits * 64 * kOzChunk * 2;   // 56 KB (N tile <= 64)
+constexpr int kSmemBytes = kSmemA + kSmemB + 1024 + 64;
+constexpr int kTmemCols = 512;
+constexpr int kMaxChunksPerBlock = 30;   // int64 headroom: chunks * 2^57 < 2^62
+constexpr unsigned long long kWaitNs = 2000000000ULL;     // bounded waits: 2 s
+
+// ------------------------------------------------------------ PTX wrappers
+
+__device__ inline uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Spin on an mbarrier phase with a wall-clock limit; false when it ran out.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ inline void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ inline void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ inline void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D (TMEM) = A (smem) . B (smem)^T [+ D], BF16 inputs, FP32 accumulator.
+__device__ inline void mma_bf16(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ inline void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+
+// 32 lanes x 8 consecutive 32-bit columns; thread i gets lane (base + i).
+__device__ inline void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+
+__device__ inline void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, no swizzle, K-major core matrices of
+// 8 rows x 16 bytes: 128 B between K-adjacent core matrices (leading byte
+// offset), 1024 B between 8-row groups (stride byte offset), version 1.
+__device__ inline uint64_t smem_desc(uint32_t addr) {
+  const uint64_t base = ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ULL << 46);
+  return base | (uint64_t)((addr & 0x3FFFF) >> 4);
+}
+
+// ------------------------------------------------------------ number format
+
+// x as a signed fixed-point integer V = x * 2^{1077 - E} (|V| < 2^55 when E is
+// the largest biased exponent of the block), rounded to nearest.
+__device__ inline long long oz_fixed(double x, int E) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7FF);
+  if (e == 0 || E == 0) return 0;
+  const long long mant = (long long)((bits & ((1ULL << 52) - 1)) | (1ULL << 52));
+  const int sh = E - e - 2;
+  long long V;
+  if (sh < 0) V = mant << (-sh);
+  else if (sh == 0) V = mant;
+  else if (sh < 62) V = (mant + (1LL << (sh - 1))) >> sh;
+  else V = 0;
+  return (bits >> 63) ? -V : V;
+}
+
+// BF16 bit pattern of a small integer |d| <= 256 (exact).
+__device__ inline uint32_t bf16_of_int(int d) {
+  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+  return __float_as_uint(f) >> 16;
+}
+
+// S * 2^e2 as the nearest double (integer construction, no FP64 arithmetic).
+__device__ inline double oz_to_double(long long S, int e2) {
+  if (S == 0) return 0.0;
+  const unsigned long long sign = S < 0 ? (1ULL << 63) : 0ULL;
+  const unsigned long long a = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+  const int lz = __clzll((long long)a);
+  const unsigned long long n = a << lz;
+  unsigned long long m = n >> 11;
+  const unsigned long long rem = n & 0x7FF;
+  if (rem > 0x400 || (rem == 0x400 && (m & 1))) ++m;
+  int ex = 63 - lz + e2;
+  if (m >> 53) {
+    m >>= 1;
+    ++ex;
+  }
+  const int be = ex + 1023;
+  if (be <= 0) return 0.0;
+  if (be >= 2047) return __longlong_as_double((long long)(sign | (0x7FFULL << 52)));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (m & ((1ULL << 52) - 1))));
+}
+
+// ------------------------------------------------------------ slicing
+
+// One 8-lane group per row; lane j owns K elements 8j..8j+7 of every chunk.
+__global__ void __launch_bounds__(kOzThreads) oz_slice_kernel(const double* __restrict__ X, int rows, int K,
+                                                              long long s_r, long long s_k1, long long s_k2, int KR,
+                                                              int kchunks, int smax, int kb_chunks, int nkb,
+                                                              uint16_t* __restrict__ planes, int* __restrict__ exps) {
+  const int tid = threadIdx.x;
+  const int r = blockIdx.x * (kOzThreads / 8) + (tid >> 3);
+  const int j = tid & 7;
+  const int kb = blockIdx.y;
+  const int c0 = kb * kb_chunks, c1 = min(c0 + kb_chunks, kchunks);
+  const bool rv = r < rows;
+  const double* Xr = X + (long long)(rv ? r : 0) * s_r;
+  auto load = [&](int k) -> double {
+    if (!rv || k >= K) return 0.0;
+    const int q = k / KR, m = k - q * KR;
+    return Xr[(long long)m * s_k1 + (long long)q * s_k2];
+  };
+  int emax = 0;
+  for (int c = c0; c < c1; ++c)
+    for (int e = 0; e < 8; ++e) {
+      const double x = load(c * kOzChunk + 8 * j + e);
+      emax = max(emax, (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF));
+    }
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 2));
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 4));
+  if (j == 0) exps[(size_t)r * nkb + kb] = emax;
+  const int rt = r / kOzTileM, rr = r % kOzTileM;
+  for (int c = c0; c < c1; ++c) {
+    long long V[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) V[e] = oz_fixed(load(c * kOzChunk + 8 * j + e), emax);
+    uint16_t* dst = planes + ((size_t)rt * kchunks + c) * smax * kPlaneElems + (rr / 8) * 512 + j * 64 + (rr % 8) * 8;
+    for (int t = 0; t < smax; ++t) {
+      const int p = 48 - 8 * t;
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        int d0, d1;
+        if (p > 0) {
+          d0 = (int)((V[e] + (1LL << (p - 1))) >> p);
+          d1 = (int)((V[e + 1] + (1LL << (p - 1))) >> p);
+          V[e] -= (long long)d0 << p;
+          V[e + 1] -= (long long)d1 << p;
+        } else {
+          d0 = (int)V[e];
+          d1 = (int)V[e + 1];
+          V[e] = V[e + 1] = 0;
+        }
+        w[e / 2] = bf16_of_int(d0) | (bf16_of_int(d1) << 16);
+      }
+      *reinterpret_cast<uint4*>(dst + (size_t)t * kPlaneElems) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// ------------------------------------------------------------ GEMM
+
+// One CTA per (row tile, column tile, K block).  Thread 0 issues the bulk
+// copies and the MMAs; all eight warps drain the s TMEM accumulators after
+// every chunk (warp w reads TMEM lanes 32 (w % 4).. and half w / 4 of the
+// columns) into int64 fixed-point sums; the next chunk's copies overlap that
+// drain.
+__global__ void __launch_bounds__(kOzThreads, 1)
+    oz_gemm_kernel(OzOperand A, OzOperand B, int M, int N, int s, int TN, int mtiles, int ntiles, int nsplit,
+                   int lower_only, double alpha, double* C, long long MR, long long cs_m1, long long cs_m2,
+                   long long cs_n, int atomic, int* flag) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* As = smem;
+  uint8_t* Bs = smem + kSmemA;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Bs + kSmemB);   // [0] copies landed, [1] MMAs done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int split = blockIdx.x % nsplit, tile = blockIdx.x / nsplit;
+  const int mt = tile % mtiles, nt = tile / mtiles;
+  if (nt >= ntiles) return;
+  if (lower_only && mt * kOzTileM + kOzTileM - 1 < nt * TN) return;
+  const int c0 = split * A.kb_chunks, c1 = min(c0 + A.kb_chunks, A.kchunks);
+  if (c0 >= c1) return;
+
+  if (warp == 0) tmem_alloc(tslot, kTmemCols);
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = *tslot;
+
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                         ((uint32_t)(kOzTileM >> 4) << 24);
+  const uint32_t a_s = smem_addr(As), b_s = smem_addr(Bs);
+  const int b_rt = (nt * TN) / kOzTileM, b_off = (nt * TN) % kOzTileM;
+  const uint32_t a_bytes = (uint32_t)s * kPlaneElems * 2, b_plane = (uint32_t)TN * kOzChunk * 2;
+
+  auto issue_loads = [&](int c) {
+    mbar_expect_tx(&bars[0], a_bytes + (uint32_t)s * b_plane);
+    bulk_load(As, A.planes + ((size_t)mt * A.kchunks + c) * A.smax * kPlaneElems, a_bytes, &bars[0]);
+    for (int u = 0; u < s; ++u)
+      bulk_load(Bs + u * b_plane,
+                B.planes + (((size_t)b_rt * B.kchunks + c) * B.smax + u) * kPlaneElems + (size_t)b_off * kOzChunk,
+                b_plane, &bars[0]);
+  };
+
+  // epilogue ownership: row (TMEM lane) and a half of the tile's columns
+  const int row = 32 * (warp & 3) + lane;
+  const int ncol = TN / 2, col0 = (warp >> 2) * ncol;
+  const uint32_t t_row = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
+  long long acc[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) acc[q] = 0;
+
+  uint32_t ph_ld = 0, ph_mma = 0;
+  bool ld_pending = false, mma_pending = false, bad = false;
+  if (tid == 0) {
+    issue_loads(c0);
+    ld_pending = true;
+  }
+  for (int c = c0; c < c1; ++c) {
+    if (tid == 0) {
+      if (!mbar_wait(&bars[0], ph_ld)) {
+        bad = true;
+      } else {
+        ld_pending = false;
+        ph_ld ^= 1;
+        tc_fence_after();
+        for (int j = 0; j < kOzChunk / 16; ++j)
+          for (int t = 1; t <= s; ++t)
+            for (int u = 1; u <= s + 1 - t; ++u) {
+              const uint32_t d = taddr + (uint32_t)((t + u - 2) * TN);
+              const uint64_t ad = smem_desc(a_s + (uint32_t)((t - 1) * kPlaneElems * 2 + j * 256));
+              const uint64_t bd = smem_desc(b_s + (uint32_t)((u - 1) * b_plane + j * 256));
+              mma_bf16(d, ad, bd, idesc, (j > 0 || t > 1) ? 1u : 0u);
+            }
+        mma_commit(&bars[1]);
+        mma_pending = true;
+      }
+    }
+    if (__syncthreads_or(bad)) {
+      bad = true;
+      break;
+    }
+    const bool ok = mbar_wait(&bars[1], ph_mma);
+    if (__syncthreads_or(!ok)) {
+      bad = true;
+      break;
+    }
+    ph_mma ^= 1;
+    mma_pending = false;
+    tc_fence_after();
+    if (tid == 0 && c + 1 < c1) {
+      issue_loads(c + 1);
+      ld_pending = true;
+    }
+    for (int g = 2; g <= s + 1; ++g) {
+      const int sh = 37 - 8 * (g - 2);
+      const uint32_t tg = t_row + (uint32_t)((g - 2) * TN + col0);
+      uint32_t r[4][8];
+#pragma unroll
+      for (int q8 = 0; q8 < 4; ++q8)
+        if (8 * q8 < ncol) tmem_ld8(tg + 8 * q8, r[q8]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int q8 = 0; q8 < 4; ++q8) {
+        if (8 * q8 < ncol) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const long long v = (long long)__float2int_rn(__uint_as_float(r[q8][i]));
+            acc[8 * q8 + i] += sh >= 0 ? (v << sh) : (v >> (-sh));
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+
+  if (!bad) {
+    const long long m = (long long)mt * kOzTileM + row;
+    if (m < M) {
+      const int ea = A.exps[(size_t)m * A.nkb + split];
+      const long long cbase = (m % MR) * cs_m1 + (m / MR) * cs_m2;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int n = nt * TN + col0 + q;
+        if (q < ncol && n < N) {
+          const int eb = B.exps[(size_t)n * B.nkb + split];
+          double v = oz_to_double(acc[q], ea + eb - 2095);
+          if (alpha != 1.0) v *= alpha;
+          double* dst = C + cbase + (long long)n * cs_n;
+          if (atomic) atomicAdd(dst, v);
+          else *dst = v;
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(flag + 1, 1);
+    // let copies and MMAs still in flight finish before the CTA releases its
+    // shared memory and tensor memory (bounded as well)
+    if (ld_pending) mbar_wait(&bars[0], ph_ld);
+    if (mma_pending) mbar_wait(&bars[1], ph_mma);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(taddr, kTmemCols);
+  }
+}
+
+}  // namespace
+
+OzOperand oz_slice(const LaCtx& la, const double* X, int rows, int K, long long s_r, long long s_k1,
+                   long long s_k2, int KR, int smax, int kb_chunks, uint16_t* planes, int* exps) {
+  if (rows <= 0 || K <= 0 || smax < 1 || smax > kOzMaxDigits || KR <= 0)
+    throw RihfError(RIHF_ERR_INVALID_ARG, "oz_slice: bad arguments");
+  OzOperand op;
+  op.planes = planes;
+  op.exps = exps;
+  op.rows = rows;
+  op.rows_pad = (rows + kOzTileM - 1) / kOzTileM * kOzTileM;
+  op.kchunks = (K + kOzChunk - 1) / kOzChunk;
+  op.smax = smax;
+  op.kb_chunks = (kb_chunks <= 0 || kb_chunks > op.kchunks) ? op.kchunks : kb_chunks;
+  op.nkb = (op.kchunks + op.kb_chunks - 1) / op.kb_chunks;
+  dim3 grid(op.rows_pad / (kOzThreads / 8), op.nkb);
+  oz_slice_kernel<<<grid, kOzThreads, 0, la.stream>>>(X, rows, K, s_r, s_k1, s_k2, KR, op.kchunks, smax,
+                                                      op.kb_chunks, op.nkb, planes, exps);
+  RIHF_LAUNCH_CHECK();
+  if (la.launches) *la.launches += 1;
+  return op;
+}
+
+void oz_gemm(const LaCtx& la, const OzGemmArgs& g) {
+  if (g.M <= 0 || g.N <= 0) return;
+  const OzOperand &A = g.A, &B = g.B;
+  if (g.s < 1 || g.s > kOzMaxDigits || g.s > A.smax || g.s > B.smax || A.kchunks != B.kchunks ||
+      A.kb_chunks != B.kb_chunks || A.nkb != B.nkb || A.rows < g.M || B.rows < g.N)
+    throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: operands do not match");
+  if (A.kb_chunks > kMaxChunksPerBlock)
+    throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: K block longer than the int64 accumulator allows");
+  if (!g.atomic && A.nkb > 1) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: K blocks need atomic output");
+  // column tile: the whole of N when it fits (multiple of 16), else 64 so that
+  // no tile straddles a 128-row plane
+  const int TN = g.N <= 64 ? (g.N + 15) / 16 * 16 : 64;
+  if (g.s * TN > kTmemCols) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: accumulators exceed TMEM");
+  const int mtiles = (g.M + kOzTileM - 1) / kOzTileM, ntiles = (g.N + TN - 1) / TN;
+  RIHF_CUDA(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  const long long nblocks = (long long)mtiles * ntiles * A.nkb;
+  oz_gemm_kernel<<<(unsigned)nblocks, kOzThreads, kSmemBytes, la.stream>>>(
+      A, B, g.M, g.N, g.s, TN, mtiles, ntiles, A.nkb, g.lower_only ? 1 : 0, g.alpha, g.C, g.MR, g.cs_m1, g.cs_m2,
+      g.cs_n, g.atomic ? 1 : 0, la.flag);
+  RIHF_LAUNCH_CHECK();
+  if (la.launches) *la.launches += 1;
+}
+
+}  // namespace rihf

@@ -43,7 +43,7 @@ class rihf_options(ctypes.Structure):
 EXPORTS = ["rihf_default_options", "rihf_setup", "rihf_update_geometry", "rihf_scf", "rihf_gradient",
            "rihf_query", "rihf_get_matrix", "rihf_screening_stats", "rihf_timings", "rihf_strerror",
            "rihf_last_error", "rihf_destroy", "rihf_eigh", "rihf_stream", "rihf_trace", "rihf_trace_stats",
-           "rihf_scf_stats", "rihf_eigh_noalloc"]
+           "rihf_scf_stats", "rihf_eigh_noalloc", "rihf_tc_dgemm"]
 
 _lib = None
 
@@ -84,6 +84,8 @@ def load(path: str = LIB_PATH):
     lib.rihf_eigh_noalloc.restype = I
     lib.rihf_eigh.argtypes = [I, P, P, P, I]
     lib.rihf_eigh.restype = I
+    lib.rihf_tc_dgemm.argtypes = [I, I, I, P, P, P, I, I, I]
+    lib.rihf_tc_dgemm.restype = I
     lib.rihf_destroy.argtypes = [P]
     lib.rihf_destroy.restype = None
     for name in ("rihf_setup", "rihf_update_geometry", "rihf_scf", "rihf_gradient", "rihf_query",
@@ -132,6 +134,19 @@ def eigh(A, device=0):
     V = np.zeros((n, n))
     _check(load().rihf_eigh(n, _p(A), _p(W), _p(V), int(device)))
     return W, V
+
+
+def tc_dgemm(A, B, digits=7, kblock=0, device=0):
+    """C = A B^T on the tensor cores from BF16 digit planes (A: M x K, B: N x K)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("A and B need the same number of columns")
+    C = np.zeros((M, N))
+    _check(load().rihf_tc_dgemm(M, N, K, _p(A), _p(B), _p(C), int(digits), int(kblock), int(device)))
+    return C
 
 
 def eigh_noalloc(n, A_dev, W_dev, V_dev, stream=0):
