@@ -65,7 +65,8 @@ typedef struct {
   double conv_diis;     /* ... and max |X^T (FDS - SDF) X| < conv_diis                    */
   int max_iter;         /* SCF iteration cap (RIHF_ERR_NOT_CONVERGED when reached)         */
   int diis_size;        /* Pulay DIIS subspace size, 2..16                                 */
-  int mixed_fp64_iters; /* mixed precision: trailing iterations rebuilt in FP64            */
+  int mixed_digits;     /* mixed precision: BF16 digits of the tensor-core RI-K (1..7);   */
+                        /* 0 = ladder 5 -> 6 -> 7 digits as max|e| falls                 */
   int device;           /* CUDA device ordinal                                             */
 } rihf_options;
 
@@ -73,7 +74,11 @@ typedef struct {
    dropped; with ill-conditioned auxiliary metrics even pairs below 1e-14 move
    the energy by ~1e-6 Eh, see the screening tests), lindep_tau
    1e-8, conv_e 1e-10, conv_diis 1e-9, max_iter 100, diis_size 8,
-   mixed_fp64_iters 2, device 0. */
+   mixed_digits 0, device 0.
+   Mixed precision (RIHF_PRECISION_MIXED): RI-K in the SCF iterations runs on
+   the tensor cores from BF16 digit planes (see rihf_tc_dgemm); RI-J, D, DIIS,
+   the diagonalisation and the gradient stay FP64; convergence is declared only
+   on an FP64 Fock build that follows the tensor-core iterations. */
 void rihf_default_options(rihf_options* opt);
 
 /*
@@ -155,9 +160,9 @@ int rihf_screening_stats(rihf_ctx* ctx, int* kept, int* total);
    library launched since the context was created ([4], as a double). */
 int rihf_timings(rihf_ctx* ctx, double* out5);
 
-/* Fock builds of the last rihf_scf by precision: FP32 (mixed-precision
-   iterations) and FP64.  Either pointer may be NULL. */
-int rihf_scf_stats(rihf_ctx* ctx, int* fp32_builds, int* fp64_builds);
+/* Fock builds of the last rihf_scf by precision: tensor-core RI-K builds
+   (mixed-precision iterations) and FP64 builds.  Either pointer may be NULL. */
+int rihf_scf_stats(rihf_ctx* ctx, int* tc_builds, int* fp64_builds);
 
 /* The CUDA stream (cudaStream_t, returned as void*) on which the context
    launches all of its work; callers may record CUDA events on it. */
@@ -169,7 +174,8 @@ void* rihf_stream(rihf_ctx* ctx);
    rihf_trace_stats fills, for up to `max` traced kernels: names (48 chars
    each, NUL-terminated), launches, total device milliseconds and the
    algorithmic work of those launches (flops or bytes; kind: 0 = FP64 flops,
-   1 = HBM bytes, 2 = FP32/tensor flops).  Returns the number of kernels. */
+   1 = HBM bytes, 2 = FP32 flops, 3 = BF16 tensor-core flops issued).  Returns
+   the number of kernels. */
 int rihf_trace(rihf_ctx* ctx, int enable);
 int rihf_trace_stats(rihf_ctx* ctx, int max, char* names, double* launches, double* ms, double* work, int* kind);
 

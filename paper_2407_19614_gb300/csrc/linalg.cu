@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ A
 // fits) is stored; a warp owns one column pair per round (round-robin pairing),
 // its dot products reduced with shuffles.
 __global__ void __launch_bounds__(JT) jacobi1s_kernel(const double* __restrict__ A, int n, int m, float* gU, float* V,
-                                                      float* W, int use_smem, int max_sweeps) {
+                                                      float* W, int use_smem, int max_sweeps, float tol) {
   extern __shared__ float sm[];
   __shared__ float red[32];
   __shared__ int notconv;
@@ -731,7 +731,7 @@ __global__ void __launch_bounds__(JT) jacobi1s_kernel(const double* __restrict__
           b += __shfl_xor_sync(0xffffffffu, b, o);
           c += __shfl_xor_sync(0xffffffffu, c, o);
         }
-        if (fabsf(c) <= 2e-6f * sqrtf(a * b)) continue;
+        if (fabsf(c) <= tol * sqrtf(a * b)) continue;
         if (lane == 0) notconv = 1;
         float zeta = (b - a) / (2.f * c);
         float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
@@ -919,7 +919,10 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
   int use_smem = smem <= 215 * 1024 ? 1 : 0;
   if (use_smem)
     RIHF_CUDA(cudaFuncSetAttribute(jacobi1s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  jacobi1s_kernel<<<1, JT, use_smem ? smem : 0, la.stream>>>(Ain, n, m, fA, fV, fW, use_smem, 20);
+  // a looser stop (n eps) leaves close clusters too coarse for the FP64
+  // refinement to separate
+  const float tol = 2e-6f;
+  jacobi1s_kernel<<<1, JT, use_smem ? smem : 0, la.stream>>>(Ain, n, m, fA, fV, fW, use_smem, 20, tol);
   RIHF_LAUNCH_CHECK();
   count(la);
   eig_sort_kernel<<<1, 1024, 0, la.stream>>>(fV, fW, n, m, V, W);

@@ -272,6 +272,26 @@ __global__ void diis_extrap_kernel(const double* __restrict__ ring, long long le
   }
 }
 
+// out[0] = max_ij |A_ij - sub * delta_ij| over all i, j (offdiag = 0) or over
+// i != j only (offdiag = 1); one block.
+__global__ void eig_check_kernel(const double* __restrict__ A, int n, double sub, int offdiag, double* out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (long long idx = threadIdx.x; idx < (long long)n * n; idx += blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    if (offdiag && i == j) continue;
+    m = fmax(m, fabs(A[idx] - (i == j ? sub : 0.0)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+    out[0] = t;
+  }
+}
+
 // E = 1/2 sum D (h + F) + Vnn written to out[0]; out[1] untouched.
 __global__ void energy_kernel(const double* __restrict__ D, const double* __restrict__ h,
                               const double* __restrict__ F, long long n2, double vnn, double* out) {
@@ -422,9 +442,12 @@ struct rihf_ctx {
   // gradient
   double* na2tmp = nullptr;
   // mixed precision: FP32 copy of B and FP32 operands of the SCF-iteration builds
-  float *B32 = nullptr, *D32 = nullptr, *Ct32 = nullptr, *H32 = nullptr, *G32 = nullptr;
-  double *Fprev = nullptr, *Dprev = nullptr;
-  int fp32_builds = 0, last_iters = 0;
+  // mixed precision: BF16 digit planes of B (per geometry), C~^T and H (per
+  // build) for the tensor-core RI-K, with their block exponents
+  uint16_t *Bpl = nullptr, *Cpl = nullptr, *Hpl = nullptr;
+  int *Bex = nullptr, *Cex = nullptr, *Hex = nullptr;
+  OzOperand Bop;
+  int tc_builds = 0, last_iters = 0, last_digits = 0;
   double* trsm_tmp = nullptr;
   double *cvec = nullptr, *W = nullptr, *Bij = nullptr, *Xt = nullptr, *Zm = nullptr, *G = nullptr, *Y = nullptr;
   double* grad_parts = nullptr;   // 5 x natoms x 3 on device (one, overlap, three, two, nuc)
@@ -507,7 +530,7 @@ static void free_all(rihf_ctx* c) {
                   c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->T3, c->B, c->Xo, c->Sw, c->Sv,
                   c->C, c->eps, c->Ct, c->D, c->J, c->K, c->F, c->Fx, c->T1, c->T2, c->Err, c->Fp, c->Cp, c->Hb,
                   c->dvec, c->Fring, c->Ering, c->Bdiis, c->coef, c->scal, c->Cprev,
-                  c->na2tmp, c->trsm_tmp, c->B32, c->D32, c->Ct32, c->H32, c->G32, c->Fprev, c->Dprev, c->cvec, c->W, c->Bij, c->Xt, c->Zm, c->G, c->Y, c->grad_parts, c->work, c->eigws, c->scratch};
+                  c->na2tmp, c->trsm_tmp, c->Bpl, c->Cpl, c->Hpl, c->Bex, c->Cex, c->Hex, c->cvec, c->W, c->Bij, c->Xt, c->Zm, c->G, c->Y, c->grad_parts, c->work, c->eigws, c->scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -583,7 +606,10 @@ static void compute_geometry(rihf_ctx* c) {
   { TraceScope t(c->tracer, s, "fit trsm B=L^-1 T", (double)NA * NA * N * (N + 1) / 2, 0);
     trsm_lower(la, c->L, NA, c->B, (long long)N * N, false, N, c->trsm_tmp); }
   symmetrize_lower(la, c->B, N, NA);
-  if (c->B32) to_float(la, c->B, (long long)NA * N * N, c->B32);
+  if (c->Bpl) {   // digit planes of B for the tensor-core RI-K (rows (P, mu), K = nu)
+    TraceScope t(c->tracer, s, "B digit planes (oz_slice)", (double)NA * N * N * (8 + 2 * kOzMaxDigits), 1);
+    c->Bop = oz_slice(la, c->B, NA * N, N, N, 1, 0, N, kOzMaxDigits, 0, c->Bpl, c->Bex);
+  }
   int flag = 0;
   RIHF_CUDA(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   RIHF_CUDA(cudaStreamSynchronize(s));
@@ -678,7 +704,7 @@ void rihf_default_options(rihf_options* o) {
   o->conv_diis = 1e-9;
   o->max_iter = 100;
   o->diis_size = 8;
-  o->mixed_fp64_iters = 2;
+  o->mixed_digits = 0;
   o->device = 0;
 }
 
@@ -811,13 +837,13 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     c->G = dalloc<double>((size_t)NA * c->nocc * N);
     c->Y = dalloc<double>(big);
     if (c->opt.precision == RIHF_PRECISION_MIXED) {
-      c->B32 = dalloc<float>(big);
-      c->D32 = dalloc<float>(n2);
-      c->Ct32 = dalloc<float>((size_t)N * c->nocc);
-      c->H32 = dalloc<float>((size_t)NA * N * c->nocc);
-      c->G32 = dalloc<float>(big);
-      c->Fprev = dalloc<double>(n2);
-      c->Dprev = dalloc<double>(n2);
+      const int nkb_max = (NA * c->nocc + kOzChunk - 1) / kOzChunk;
+      c->Bpl = dalloc<uint16_t>(oz_plane_elems(NA * N, N, kOzMaxDigits));
+      c->Bex = dalloc<int>(oz_plane_elems(NA * N, 1, 1) / kOzChunk);
+      c->Cpl = dalloc<uint16_t>(oz_plane_elems(c->nocc, N, kOzMaxDigits));
+      c->Cex = dalloc<int>(oz_plane_elems(c->nocc, 1, 1) / kOzChunk);
+      c->Hpl = dalloc<uint16_t>(oz_plane_elems(N, NA * c->nocc, kOzMaxDigits));
+      c->Hex = dalloc<int>(oz_plane_elems(N, 1, 1) / kOzChunk * nkb_max);
     }
     c->trsm_tmp = dalloc<double>(32 * std::max<size_t>({n2, (size_t)NA, (size_t)c->nocc * c->nocc}) + 1024);
     c->grad_parts = dalloc<double>(5 * 3 * natoms);
@@ -860,25 +886,44 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
   dgemm(la, g2);
   RIHF_CUDA(cudaMemsetAsync(c->eps, 0, sizeof(double) * N, c->stream));
   {
+    // refinement from the previous eigenvectors once the SCF error is moderate;
+    // the guard below falls back to a Jacobi pass unless the refined vectors
+    // are orthonormal and diagonalise F'
     const bool use_prev = warm && c->have_cprev;
     const bool skip = use_prev && c->last_err < 1e-2;
-    TraceScope t(c->tracer, c->stream, skip ? "eigh F' (refine only)" : "eigh F' (jacobi+refine)", 0.0, 0);
-    eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, use_prev ? c->Cprev : nullptr, skip);
+    {
+      TraceScope t(c->tracer, c->stream, skip ? "eigh F' (refine only)" : "eigh F' (jacobi+refine)", 0.0, 0);
+      eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, use_prev ? c->Cprev : nullptr, skip);
+    }
     if (skip) {
       // guard: the refinement from the previous vectors must end orthonormal;
       // otherwise redo the step with a Jacobi pass
-      GemmArgs go;
+      GemmArgs go;   // T2 = Cp^T Cp
       go.M = n; go.N = n; go.K = n; go.A = c->Cp; go.lda = n; go.transA = true; go.B = c->Cp; go.ldb = n;
       go.C = c->T2; go.ldc = n;
       dgemm(la, go);
-      identity(la, c->T1, n);
-      axpby(la, n * n, 1.0, c->T2, -1.0, c->T1, c->T2);
-      maxabs(la, n * n, c->T2, c->scal + 2);
-      double dev = 0.0;
-      RIHF_CUDA(cudaMemcpyAsync(&dev, c->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      eig_check_kernel<<<1, 1024, 0, c->stream>>>(c->T2, n, 1.0, 0, c->scal + 2);
+      GemmArgs gf;   // T1 = F' Cp, T2 = Cp^T T1
+      gf.M = n; gf.N = n; gf.K = n; gf.A = c->Fp; gf.lda = n; gf.B = c->Cp; gf.ldb = n; gf.C = c->T1; gf.ldc = n;
+      dgemm(la, gf);
+      GemmArgs gt;
+      gt.M = n; gt.N = n; gt.K = n; gt.A = c->Cp; gt.lda = n; gt.transA = true; gt.B = c->T1; gt.ldb = n;
+      gt.C = c->T2; gt.ldc = n;
+      dgemm(la, gt);
+      eig_check_kernel<<<1, 1024, 0, c->stream>>>(c->T2, n, 0.0, 1, c->scal + 3);
+      RIHF_LAUNCH_CHECK();
+      c->launches += 2;
+      double dev[2] = {0.0, 0.0};
+      RIHF_CUDA(cudaMemcpyAsync(dev, c->scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       RIHF_CUDA(cudaStreamSynchronize(c->stream));
-      if (!(dev < 1e-8)) {
-        if (c->verbose || getenv("RIHF_VERBOSE")) fprintf(stderr, "rihf: refine-only eigh deviation %.3e, redo\n", dev);
+      // eigenvector errors of the order of the SCF error do not slow the SCF
+      // (the refined vectors typically leave |C^T F' C|_offdiag ~ max|e|); the
+      // guard only catches a refinement that went astray
+      const double offd_tol = std::max(1e-8, 10.0 * c->last_err);
+      if (!(dev[0] < 1e-8) || !(dev[1] < offd_tol)) {
+        if (c->verbose || getenv("RIHF_VERBOSE"))
+          fprintf(stderr, "rihf: refine-only eigh deviation %.3e, off-diagonal %.3e, redo\n", dev[0], dev[1]);
+        TraceScope t(c->tracer, c->stream, "eigh F' (jacobi redo)", 0.0, 0);
         eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, c->Cprev, false);
       }
     }
@@ -893,7 +938,7 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
 }
 
 // F = h + J + K for the current C; writes D, J, K, F, Ct and scal[0] = E.
-static void fock_build(rihf_ctx* c, bool fp32) {
+static void fock_build(rihf_ctx* c) {
   LaCtx la = c->la();
   const int N = c->N, NA = c->NA, no = c->nocc;
   const size_t n2 = (size_t)N * N;
@@ -903,36 +948,6 @@ static void fock_build(rihf_ctx* c, bool fp32) {
   gd.M = N; gd.N = N; gd.K = no; gd.A = c->Ct; gd.lda = no; gd.B = c->Ct; gd.ldb = no; gd.transB = true;
   gd.C = c->D; gd.ldc = N;
   dgemm(la, gd);
-  if (fp32) {
-    // Incremental mixed-precision build: F = F_prev + J(dD) + K(dD) with
-    // dD = D - D_prev in FP32.  J is linear in D (two passes over B32); K uses
-    // the density form of Eq. k_ri_1, G^P = B^P dD, K(dD) = -1/2 sum_P G^P B^P,
-    // so the FP32 rounding error scales with |dD|, not with |K|.
-    axpby(la, (int)n2, 1.0, c->D, -1.0, c->Dprev, c->T1);
-    to_float(la, c->T1, (long long)n2, c->D32);
-    { TraceScope t(c->tracer, c->stream, "RI-J d=B.dD (fp32 gemv_rows)", (double)NA * n2 * 4, 1);
-      gemv_rows_f32(la, c->B32, NA, (long long)n2, c->D32, 1.0, c->dvec); }
-    { TraceScope t(c->tracer, c->stream, "RI-J dJ=B^T d (fp32 gemv_cols)", (double)NA * n2 * 4, 1);
-      gemv_cols_f32(la, c->B32, NA, (long long)n2, c->dvec, 1.0, c->J); }
-    SGemmArgs sg;   // G (NA*N x N) = B32 (NA*N x N) dD (N x N)
-    sg.M = NA * N; sg.N = N; sg.K = N; sg.A = c->B32; sg.lda = N; sg.B = c->D32; sg.ldb = N; sg.C = c->G32;
-    sg.ldc = N;
-    { TraceScope t(c->tracer, c->stream, "RI-K G=B dD (fp32 sgemm)", 2.0 * NA * n2 * N, 2);
-      sgemm(la, sg); }
-    SGemmArgs sk;   // dK = -1/2 sum_P G^P B^P
-    sk.M = N; sk.N = N; sk.K = N; sk.A = c->G32; sk.lda = N; sk.sA = (long long)n2;
-    sk.B = c->B32; sk.ldb = N; sk.sB = (long long)n2;
-    sk.Cd = c->K; sk.ldc = N; sk.batch = NA; sk.reduce_batch = true; sk.alpha = -0.5;
-    { TraceScope t(c->tracer, c->stream, "RI-K dK=-1/2 sum G B (fp32 sgemm)", 2.0 * NA * n2 * N, 2);
-      sgemm(la, sk); }
-    add3(la, (int)n2, c->Fprev, c->J, c->K, c->F);
-    RIHF_CUDA(cudaMemcpyAsync(c->Fprev, c->F, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
-    RIHF_CUDA(cudaMemcpyAsync(c->Dprev, c->D, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
-    energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->vnn, c->scal);
-    RIHF_LAUNCH_CHECK();
-    c->launches += 1;
-    return;
-  }
   // RI-J: d = B vec(D); J = B^T d
   { TraceScope t(c->tracer, c->stream, "RI-J d=B.D (gemv_rows)", (double)NA * n2 * 8, 1);
     gemv_rows(la, c->B, NA, (long long)n2, c->D, 1.0, c->dvec); }
@@ -952,19 +967,16 @@ static void fock_build(rihf_ctx* c, bool fp32) {
     dgemm(la, gk);
     symmetrize_lower(la, c->K, N, 1); }
   add3(la, (int)n2, c->H, c->J, c->K, c->F);
-  if (c->Fprev) {   // reference for the next incremental build
-    RIHF_CUDA(cudaMemcpyAsync(c->Fprev, c->F, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
-    RIHF_CUDA(cudaMemcpyAsync(c->Dprev, c->D, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
-  }
   energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->vnn, c->scal);
   RIHF_LAUNCH_CHECK();
   c->launches += 1;
 }
 
-// Full mixed-precision Fock build (early SCF iterations): D and C~ from the
-// current orbitals in FP64, RI-J and RI-K (Eqs. j_ri, k_ri_2, tp) from the FP32
-// copy of B with FP32 products; cross-block sums and F in FP64.
-static void fock_build_fp32(rihf_ctx* c) {
+// Mixed-precision Fock build: D, RI-J (Eq. j_ri) and everything else in FP64;
+// RI-K (Eqs. k_ri_2, tp) on the tensor cores from `digits` BF16 digit planes:
+// H = B C~ with B's planes cut once per geometry, then K = -1/2 sum_P H^P H^P^T
+// with H cut per K block (one block per split of the long (P, i) axis).
+static void fock_build_tc(rihf_ctx* c, int digits) {
   LaCtx la = c->la();
   const int N = c->N, NA = c->NA, no = c->nocc;
   const size_t n2 = (size_t)N * N;
@@ -973,23 +985,39 @@ static void fock_build_fp32(rihf_ctx* c) {
   gd.M = N; gd.N = N; gd.K = no; gd.A = c->Ct; gd.lda = no; gd.B = c->Ct; gd.ldb = no; gd.transB = true;
   gd.C = c->D; gd.ldc = N;
   dgemm(la, gd);
-  to_float(la, c->D, (long long)n2, c->D32);
-  to_float(la, c->Ct, (long long)N * no, c->Ct32);
-  { TraceScope t(c->tracer, c->stream, "RI-J d=B.D (fp32 gemv_rows)", (double)NA * n2 * 4, 1);
-    gemv_rows_f32(la, c->B32, NA, (long long)n2, c->D32, 1.0, c->dvec); }
-  { TraceScope t(c->tracer, c->stream, "RI-J J=B^T d (fp32 gemv_cols)", (double)NA * n2 * 4, 1);
-    gemv_cols_f32(la, c->B32, NA, (long long)n2, c->dvec, 1.0, c->J); }
-  SGemmArgs sh;
-  sh.M = NA * N; sh.N = no; sh.K = N; sh.A = c->B32; sh.lda = N; sh.B = c->Ct32; sh.ldb = no; sh.C = c->H32;
-  sh.ldc = no;
-  { TraceScope t(c->tracer, c->stream, "RI-K H=B C~ (fp32 sgemm)", 2.0 * NA * n2 * no, 2);
-    sgemm(la, sh); }
-  SGemmArgs sk;
-  sk.M = N; sk.N = N; sk.K = no; sk.A = c->H32; sk.lda = no; sk.sA = (long long)N * no;
-  sk.B = c->H32; sk.ldb = no; sk.sB = (long long)N * no; sk.transB = true;
-  sk.Cd = c->K; sk.ldc = N; sk.batch = NA; sk.reduce_batch = true; sk.alpha = -0.5;
-  { TraceScope t(c->tracer, c->stream, "RI-K K=-1/2 sum H H^T (fp32 sgemm)", 2.0 * NA * n2 * no, 2);
-    sgemm(la, sk); }
+  { TraceScope t(c->tracer, c->stream, "RI-J d=B.D (gemv_rows)", (double)NA * n2 * 8, 1);
+    gemv_rows(la, c->B, NA, (long long)n2, c->D, 1.0, c->dvec); }
+  { TraceScope t(c->tracer, c->stream, "RI-J J=B^T d (gemv_cols)", (double)NA * n2 * 8, 1);
+    gemv_cols(la, c->B, NA, (long long)n2, c->dvec, 1.0, c->J); }
+  const double prod = oz_products(digits);
+  const int npad = (no + 15) / 16 * 16, kpadN = (N + kOzChunk - 1) / kOzChunk * kOzChunk;
+  OzOperand Cop = oz_slice(la, c->Ct, no, N, 1, no, 0, N, digits, 0, c->Cpl, c->Cex);
+  OzGemmArgs g1;   // H[(P, mu)][i] = sum_nu B[(P, mu)][nu] C~[nu][i]
+  g1.A = c->Bop; g1.B = Cop; g1.M = NA * N; g1.N = no; g1.s = digits; g1.C = c->Hb; g1.cs_m1 = no; g1.cs_n = 1;
+  { TraceScope t(c->tracer, c->stream, "RI-K H=B C~ (tcgen05 digits)",
+                 2.0 * c->Bop.rows_pad * npad * kpadN * prod, 3);
+    oz_gemm(la, g1); }
+  // K blocks of the (P, i) axis: enough splits to cover the SMs, at most 30
+  // chunks each (int64 headroom of the accumulators)
+  const int kch = (NA * no + kOzChunk - 1) / kOzChunk;
+  const int TN = N <= 64 ? (N + 15) / 16 * 16 : 64;
+  int lower_tiles = 0;
+  for (int mt = 0; mt * kOzTileM < N; ++mt)
+    for (int nt = 0; nt * TN < N; ++nt)
+      if (mt * kOzTileM + kOzTileM - 1 >= nt * TN) ++lower_tiles;
+  const int nsplit = std::max((kch + 29) / 30, std::max(1, c->sms / std::max(1, lower_tiles)));
+  const int kbc = (kch + nsplit - 1) / nsplit;
+  OzOperand Hop;
+  { TraceScope t(c->tracer, c->stream, "RI-K H digit planes (oz_slice)", (double)NA * N * no * (8 + 2 * digits), 1);
+    Hop = oz_slice(la, c->Hb, N, NA * no, no, 1, (long long)N * no, no, digits, kbc, c->Hpl, c->Hex); }
+  RIHF_CUDA(cudaMemsetAsync(c->K, 0, sizeof(double) * n2, c->stream));
+  OzGemmArgs g2;   // K = -1/2 sum_(P, i) H[mu][(P, i)] H[nu][(P, i)], lower tiles
+  g2.A = Hop; g2.B = Hop; g2.M = N; g2.N = N; g2.s = digits; g2.alpha = -0.5; g2.C = c->K; g2.cs_m1 = N;
+  g2.cs_n = 1; g2.atomic = true; g2.lower_only = true;
+  { TraceScope t(c->tracer, c->stream, "RI-K K=-1/2 sum H H^T (tcgen05 digits)",
+                 2.0 * lower_tiles * kOzTileM * TN * (double)kch * kOzChunk * prod, 3);
+    oz_gemm(la, g2);
+    symmetrize_lower(la, c->K, N, 1); }
   add3(la, (int)n2, c->H, c->J, c->K, c->F);
   energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->vnn, c->scal);
   RIHF_LAUNCH_CHECK();
@@ -1035,6 +1063,28 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
     // M = Co^T S Co = L_M L_M^T, Co <- Co L_M^{-T} (Cholesky / Gram-Schmidt,
     // stable however far the nuclei moved)
     const int no = c->nocc;
+    if (c->have_cprev) {
+      // previous eigenvectors expressed in the new orthonormal basis,
+      // C' = Xo^T S C_AO (Xo^T S Xo = I), as the eigensolver's starting vectors
+      GemmArgs m1;   // T1 (N x n) = S C[:, :n]
+      m1.M = N; m1.N = n; m1.K = N; m1.A = c->S; m1.lda = N; m1.B = c->C; m1.ldb = N; m1.C = c->T1; m1.ldc = n;
+      dgemm(la, m1);
+      GemmArgs m2;   // T2 (n x n) = Xo^T T1
+      m2.M = n; m2.N = n; m2.K = N; m2.A = c->Xo; m2.lda = n; m2.transA = true; m2.B = c->T1; m2.ldb = n;
+      m2.C = c->T2; m2.ldc = n;
+      dgemm(la, m2);
+      // orthonormal again by Cholesky (Gram-Schmidt): M = V^T V = L L^T,
+      // Cprev^T = L^{-1} V^T; large nuclear steps leave V far from orthonormal
+      GemmArgs m3;   // Cprev = T2^T T2
+      m3.M = n; m3.N = n; m3.K = n; m3.A = c->T2; m3.lda = n; m3.transA = true; m3.B = c->T2; m3.ldb = n;
+      m3.C = c->Cprev; m3.ldc = n;
+      dgemm(la, m3);
+      RIHF_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
+      cholesky(la, c->Cprev, n, c->scratch);
+      transpose(la, c->T2, n, n, c->T1);                                // T1 = V^T
+      trsm_lower(la, c->Cprev, n, c->T1, n, false, 0, c->trsm_tmp);     // L^{-1} V^T
+      transpose(la, c->T1, n, n, c->Cprev);
+    }
     copy_cols(la, c->C, N, N, no, 1.0, c->Ct);
     GemmArgs g1;   // T1 (N x no) = S Co
     g1.M = N; g1.N = no; g1.K = N; g1.A = c->S; g1.lda = N; g1.B = c->Ct; g1.ldb = no; g1.C = c->T1; g1.ldc = no;
@@ -1057,22 +1107,33 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   int it = 0;
   bool conv = false;
   float ms = 0.f;
-  // Precision ladder (mixed mode): the first Fock build of every SCF is a full
-  // FP64 build; the following ones are incremental FP32 builds (error ~ |dD|);
-  // when the convergence test passes on an incremental build, one more full
-  // FP64 build must pass it too, so the converged energy and density are those
-  // of an FP64 Fock matrix.  A full rebuild every 12 increments bounds drift.
-  const bool mixed = c->opt.precision == RIHF_PRECISION_MIXED && c->B32 != nullptr;
-  bool full_next = !mixed, fp64_tail = !mixed;
-  double best_fp32 = 1e300;
-  c->fp32_builds = 0;
+  // Precision ladder (mixed mode): RI-K on the tensor cores with a digit count
+  // that follows the SCF error (5 digits, about 39 bits, while max|e| > 1e-2;
+  // 6 while > 1e-5; then 7, about 55 bits), or the fixed count of
+  // opt.mixed_digits.  When the convergence test passes on a tensor-core build,
+  // the next build is FP64 and convergence is declared only on an FP64 build,
+  // so the converged energy and density are those of an FP64 Fock matrix.
+  // Three tensor-core builds in a row without a new lowest max|e| also move the
+  // ladder to FP64.
+  const bool mixed = c->opt.precision == RIHF_PRECISION_MIXED && c->Bpl != nullptr;
+  bool fp64_next = !mixed;
+  double best_tc = 1e300, emax_prev = 1.0;
+  int stall = 0;
+  c->tc_builds = 0;
+  RIHF_CUDA(cudaMemsetAsync(c->d_flag + 1, 0, sizeof(int), s));
   for (it = 1; it <= c->opt.max_iter; ++it) {
     cudaEventRecord(c->ev[2], s);
-    const bool full = !mixed || full_next;
-    if (full) fock_build(c, false);
-    else fock_build_fp32(c);
-    if (!full) ++c->fp32_builds;
-    full_next = fp64_tail;
+    const bool full = fp64_next;
+    if (full) {
+      fock_build(c);
+    } else {
+      int digits = c->opt.mixed_digits;
+      if (digits <= 0) digits = emax_prev > 1e-2 ? 5 : emax_prev > 1e-5 ? 6 : 7;
+      digits = std::min(digits, kOzMaxDigits);
+      c->last_digits = digits;
+      fock_build_tc(c, digits);
+      ++c->tc_builds;
+    }
     cudaEventRecord(c->ev[3], s);
     diis_error(c);
     int slot = (it - 1) % size;
@@ -1089,15 +1150,16 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
     if (c->verbose || getenv("RIHF_VERBOSE")) fprintf(stderr, "rihf_scf it %3d  E = %.12f  max|e| = %.3e  dE = %.3e\n", it, E, emax, E - Eold);
     if (!std::isfinite(E)) throw RihfError(RIHF_ERR_NOT_CONVERGED, "SCF energy is not finite");
     const bool crit = it > 1 && std::fabs(E - Eold) < c->opt.conv_e && emax < c->opt.conv_diis;
-    // FP32 builds only while the SCF error is large and still falling; their
-    // rounding is amplified by large MO coefficients in near-dependent bases,
-    // so the ladder moves to FP64 at max|e| < 1e-2 or at the first FP32
-    // iteration that does not improve; convergence is declared on FP64 builds.
-    if (mixed && !fp64_tail) {
-      if (emax < 1e-2 || crit || !(emax < 0.8 * best_fp32)) fp64_tail = true;
-      best_fp32 = std::min(best_fp32, emax);
+    emax_prev = emax;
+    if (mixed && !full) {
+      if (emax < best_tc) {
+        best_tc = emax;
+        stall = 0;
+      } else {
+        ++stall;
+      }
+      if (crit || stall >= 3) fp64_next = true;
     }
-    full_next = fp64_tail;
     if (crit && full) {
       conv = true;
       cudaEventRecord(c->ev[4], s);
@@ -1130,8 +1192,11 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   diagonalise(c, c->F, true);
   c->converged = conv;
   c->have_orbitals = true;
+  int tc_flag = 0;
+  RIHF_CUDA(cudaMemcpyAsync(&tc_flag, c->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   RIHF_CUDA(cudaStreamSynchronize(s));
   c->tracer.flush();
+  if (tc_flag) throw RihfError(RIHF_ERR_TIMEOUT, "tensor-core RI-K: a bounded device wait ran out");
   if (energy) *energy = E;
   if (iters) *iters = it;
   c->last_iters = it;
@@ -1336,10 +1401,10 @@ int rihf_timings(rihf_ctx* c, double* out5) {
 
 void* rihf_stream(rihf_ctx* c) { return c ? (void*)c->stream : nullptr; }
 
-int rihf_scf_stats(rihf_ctx* c, int* fp32_builds, int* fp64_builds) {
+int rihf_scf_stats(rihf_ctx* c, int* tc_builds, int* fp64_builds) {
   if (!c) return RIHF_ERR_INVALID_ARG;
-  if (fp32_builds) *fp32_builds = c->fp32_builds;
-  if (fp64_builds) *fp64_builds = c->last_iters - c->fp32_builds;
+  if (tc_builds) *tc_builds = c->tc_builds;
+  if (fp64_builds) *fp64_builds = c->last_iters - c->tc_builds;
   return RIHF_OK;
 }
 

@@ -36,7 +36,7 @@ class rihf_shell(ctypes.Structure):
 class rihf_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("pure", ctypes.c_int), ("schwarz_tau", ctypes.c_double),
                 ("lindep_tau", ctypes.c_double), ("conv_e", ctypes.c_double), ("conv_diis", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("diis_size", ctypes.c_int), ("mixed_fp64_iters", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("diis_size", ctypes.c_int), ("mixed_digits", ctypes.c_int),
                 ("device", ctypes.c_int)]
 
 
@@ -220,7 +220,7 @@ class Context:
     def scf_stats(self):
         a, b = ctypes.c_int(), ctypes.c_int()
         _check(self.lib.rihf_scf_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
-        return dict(fp32_builds=a.value, fp64_builds=b.value)
+        return dict(tc_builds=a.value, fp64_builds=b.value)
 
     def stream(self) -> int:
         """cudaStream_t of the context (as an integer handle)."""
@@ -238,7 +238,7 @@ class Context:
         for i in range(n):
             nm = names.raw[48 * i:48 * (i + 1)].split(b"\0")[0].decode()
             out.append(dict(name=nm, launches=int(la[i]), ms=float(ms[i]), work=float(wk[i]),
-                            kind=["fp64_flops", "hbm_bytes", "fp32_flops"][int(kind[i])]))
+                            kind=["fp64_flops", "hbm_bytes", "fp32_flops", "bf16_tensor_flops"][int(kind[i])]))
         return out
 
     def timings(self):
