@@ -233,9 +233,22 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="untimed: setup, one SCF and one gradient of the workload (for ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_step:
+        from paper_2407_19614_gb300 import rihf as R
+        from paper_2407_19614_gb300 import workloads as W
+        R.load()
+        prec = R.PRECISION_MIXED if args.precision == "mixed" else R.PRECISION_FP64
+        ctx = R.Context(W.water8(0), precision=prec, **CONV)
+        out = ctx.scf(outputs=False)
+        g = ctx.gradient()
+        print(json.dumps({"energy": out["energy"], "iterations": out["iterations"], "grad_max": float(abs(g).max())}))
+        ctx.close()
+        return 0
 
     world, rank, local, pg = dist_setup()
     import torch
