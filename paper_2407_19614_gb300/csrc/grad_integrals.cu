@@ -38,7 +38,7 @@ struct DerivPlan {
     int accsz = acc_size(emin, emax, lc);
     int nabc = ncart(la) * ncart(lb) * ncart(lc);
     fm = 0;
-    vrr = 24;
+    vrr = kFmRegion;
     etr = vrr + vrr_size(L);
     acc0 = etr + (lc > 0 ? sh.total() : 0);
     accA = acc0 + accsz;
@@ -165,7 +165,7 @@ __device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, in
 // ------------------------------------------------------------ 3-centre
 
 __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells aux,
-                                                       const ShellPair* __restrict__ pairs,
+                                                       const ShellPair* __restrict__ pairs, PairTable ptab,
                                                        const int2* __restrict__ tasks, long long ntask,
                                                        const double* __restrict__ boys, int* counter,
                                                        const double* __restrict__ Y, double* grad) {
@@ -193,22 +193,23 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
     const double* B = prim.xyz + 3 * sb;
     const double* C = aux.xyz + 3 * sc;
     EtrShape sh{lc, pl.emin, pl.emax};
-    for (int pa = 0; pa < prim.nprim[sa]; ++pa)
-      for (int pb = 0; pb < prim.nprim[sb]; ++pb)
-        for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
-          double al = prim.exps[prim.pstart[sa] + pa], be = prim.exps[prim.pstart[sb] + pb];
-          double ga = aux.exps[aux.pstart[sc] + pc];
-          double w = prim.coefs[prim.pstart[sa] + pa] * prim.coefs[prim.pstart[sb] + pb] *
-                     aux.coefs[aux.pstart[sc] + pc];
-          Prim3 t = make_prim3(al, A, be, B, ga, C);
-          if (lane <= pl.L) Fm[lane] = boys_eval(lane, t.T, boys);
-          __syncwarp();
-          warp_vrr(vrr, pl.L, t, Fm, lane);
-          warp_etr(vrr, pl.L, etr, sh, t, lane);
-          warp_acc_level(vrr, pl.L, etr, sh, w, smem + pl.acc0, lane);
-          warp_acc_level(vrr, pl.L, etr, sh, 2.0 * al * w, smem + pl.accA, lane);
-          warp_acc_level(vrr, pl.L, etr, sh, 2.0 * be * w, smem + pl.accB, lane);
-        }
+    const double ABv[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
+    const PairPrim* pr = ptab.pp + ptab.off[ip];
+    const int nab = prim.nprim[sa] * prim.nprim[sb];
+    for (int ab = 0; ab < nab; ++ab) {
+      const PairPrim q = pr[ab];
+      for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
+        const int ic = aux.pstart[sc] + pc;
+        Prim3 t = make_prim3_pp(q, aux.exps[ic], aux.iexps[ic], aux.coefs[ic], C, ABv);
+        if (lane <= pl.L) Fm[lane] = boys_eval(lane, t.T, boys);
+        __syncwarp();
+        warp_vrr(vrr, pl.L, t, Fm, lane);
+        warp_etr(vrr, pl.L, etr, sh, t, Fm, lane);
+        warp_acc_level(vrr, pl.L, etr, sh, 1.0, smem + pl.acc0, lane);
+        warp_acc_level(vrr, pl.L, etr, sh, 2.0 * q.alpha, smem + pl.accA, lane);
+        warp_acc_level(vrr, pl.L, etr, sh, 2.0 * q.beta, smem + pl.accB, lane);
+      }
+    }
     // Y block -> Cartesian
     int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
     const double* src = Y + (long long)aux.ao[sc] * N2 + (long long)prim.ao[sa] * N + prim.ao[sb];
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(32) grad_eri2_kernel(DevShells aux, const doub
         if (lane <= pl.L) Fm[lane] = boys_eval(lane, t.T, boys);
         __syncwarp();
         warp_vrr(vrr, pl.L, t, Fm, lane);
-        warp_etr(vrr, pl.L, etr, sh, t, lane);
+        warp_etr(vrr, pl.L, etr, sh, t, Fm, lane);
         warp_acc_level(vrr, pl.L, etr, sh, w, smem + pl.acc0, lane);
         warp_acc_level(vrr, pl.L, etr, sh, 2.0 * al * w, smem + pl.accA, lane);
       }
@@ -490,13 +491,13 @@ int smem_grad_doubles(int la, int lb, int lc) {
 }
 
 void launch_grad_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
-                      const TaskGroup* groups, int ngroups, const double* Y, double* grad) {
+                      const PairTable& pt, const TaskGroup* groups, int ngroups, const double* Y, double* grad) {
   for (int g = 0; g < ngroups; ++g) {
     if (groups[g].ntask == 0) continue;
     int smem = groups[g].smem_grad;
     RIHF_CUDA(cudaFuncSetAttribute(grad_eri3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
-    grad_eri3_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, aux, pairs, groups[g].tasks,
+    grad_eri3_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks,
                                                                    groups[g].ntask, ic.boys, ic.counter, Y, grad);
     RIHF_LAUNCH_CHECK();
     if (ic.launches) *ic.launches += 1;

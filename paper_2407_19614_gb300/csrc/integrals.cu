@@ -113,7 +113,7 @@ struct Eri3Plan {
     int L = emax + lc;
     EtrShape sh{lc, emin, emax};
     fm = 0;
-    vrr = fm + 24;
+    vrr = fm + kFmRegion;
     etr = vrr + vrr_size(L);
     acc = etr + (lc > 0 ? sh.total() : 0);
     int accsz = acc_size(emin, emax, lc);
@@ -136,7 +136,7 @@ int smem_eri3_doubles(int la, int lb, int lc) {
 // ------------------------------------------------------------ (mu nu|P)
 
 __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux, const ShellPair* __restrict__ pairs,
-                                                  const int2* __restrict__ tasks, long long ntask,
+                                                  PairTable ptab, const int2* __restrict__ tasks, long long ntask,
                                                   const double* __restrict__ boys, int* counter,
                                                   double* __restrict__ T) {
   extern __shared__ double smem[];
@@ -164,21 +164,21 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
     const double* A = prim.xyz + 3 * sa;
     const double* B = prim.xyz + 3 * sb;
     const double* C = aux.xyz + 3 * sc;
+    const double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
     EtrShape sh{lc, emin, emax};
-    for (int pa = 0; pa < prim.nprim[sa]; ++pa)
-      for (int pb = 0; pb < prim.nprim[sb]; ++pb)
-        for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
-          double al = prim.exps[prim.pstart[sa] + pa], be = prim.exps[prim.pstart[sb] + pb];
-          double ga = aux.exps[aux.pstart[sc] + pc];
-          double w = prim.coefs[prim.pstart[sa] + pa] * prim.coefs[prim.pstart[sb] + pb] *
-                     aux.coefs[aux.pstart[sc] + pc];
-          Prim3 t = make_prim3(al, A, be, B, ga, C);
-          if (lane <= L) Fm[lane] = boys_eval(lane, t.T, boys);
-          __syncwarp();
-          warp_vrr(vrr, L, t, Fm, lane);
-          warp_etr_accumulate(vrr, L, etr, sh, t, w, acc, lane);
-        }
-    double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
+    const PairPrim* pr = ptab.pp + ptab.off[ip];
+    const int nab = prim.nprim[sa] * prim.nprim[sb];
+    for (int ab = 0; ab < nab; ++ab) {
+      const PairPrim q = pr[ab];
+      for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
+        const int ic = aux.pstart[sc] + pc;
+        Prim3 t = make_prim3_pp(q, aux.exps[ic], aux.iexps[ic], aux.coefs[ic], C, AB);
+        if (lane <= L) Fm[lane] = boys_eval(lane, t.T, boys);
+        __syncwarp();
+        warp_vrr(vrr, L, t, Fm, lane);
+        warp_etr_accumulate(vrr, L, etr, sh, t, 1.0, acc, Fm, lane);
+      }
+    }
     const double* cart = warp_hrr(acc, emin, la, lb, lc, AB, smem + pl.hrr, pl.half, lane);
     int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
     const double* out = warp_transform3(cart, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(32) eri2_kernel(DevShells aux, const double* _
         if (lane <= L) Fm[lane] = boys_eval(lane, t.T, boys);
         __syncwarp();
         warp_vrr(vrr, L, t, Fm, lane);
-        warp_etr_accumulate(vrr, L, etr, sh, t, w, acc, lane);
+        warp_etr_accumulate(vrr, L, etr, sh, t, w, acc, Fm, lane);
       }
     // acc holds [a][c] directly (lb = 0); transform with b = s (identity 1x1)
     int nfa = aux.nf[la], nfc = aux.nf[lc];
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(32) one_electron_kernel(DevShells prim, int na
           if (lane <= L) Fm[lane] = boys_eval(lane, t.T, boys);
           __syncwarp();
           warp_vrr(vrr, L, t, Fm, lane);
-          warp_etr_accumulate(vrr, L, nullptr, sh, t, -w * Z[C], acc, lane);
+          warp_etr_accumulate(vrr, L, nullptr, sh, t, -w * Z[C], acc, Fm, lane);
         }
       }
     double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
@@ -417,7 +417,7 @@ __host__ __device__ inline int schwarz_smem(int la, int lb, int* half_out) {
     if (n > half) half = n;
   }
   if (half_out) *half_out = half;
-  return 24 + vrr_size(L) + (lf > 0 ? sh.total() : 0) + accsz + brasz + 2 * half;
+  return kFmRegion + vrr_size(L) + (lf > 0 ? sh.total() : 0) + accsz + brasz + 2 * half;
 }
 
 // Q_ab = sqrt(max_{mu in a, nu in b} (mu nu|mu nu)) over Cartesian components
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(32) schwarz_kernel(DevShells prim, const doubl
     EtrShape sh{lf, emin, emax};
     // smem: Fm | vrr | etr | acc[f][e][kf] for f in [lc, lf] | bra-HRR out [f][ka][kb][kf] | scratch
     double* Fm = smem;
-    double* vrr = Fm + 24;
+    double* vrr = Fm + kFmRegion;
     double* etr = vrr + vrr_size(L);
     double* acc = etr + (lf > 0 ? sh.total() : 0);
     int accsz = 0;
@@ -487,10 +487,11 @@ __global__ void __launch_bounds__(32) schwarz_kernel(DevShells prim, const doubl
             }
             t.T = t.rho * R2pq;
             t.pref = 34.98683665524972 / (p * q * sqrt(p + q)) * exp(-al * be / p * R2ab) * exp(-ga * de / q * R2ab);
+            prim3_factors(t);
             if (lane <= L) Fm[lane] = boys_eval(lane, t.T, boys);
             __syncwarp();
             warp_vrr(vrr, L, t, Fm, lane);
-            warp_etr(vrr, L, etr, sh, t, lane);
+            warp_etr(vrr, L, etr, sh, t, Fm, lane);
             // acc[f-block][e][ke][kf] += w * level f, e in [emin, emax]
             int off = 0;
             for (int f = lc; f <= lf; ++f) {
@@ -608,17 +609,67 @@ static void set_smem(const void* fn, int bytes) {
 }
 
 void launch_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
-                 const TaskGroup* groups, int ngroups, double* T) {
+                 const PairTable& pt, const TaskGroup* groups, int ngroups, double* T) {
   for (int g = 0; g < ngroups; ++g) {
     if (groups[g].ntask == 0) continue;
     int smem = groups[g].smem_eri3;
     set_smem((const void*)eri3_kernel, smem);
     RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
-    eri3_kernel<<<grid_for(smem), 32, smem, ic.stream>>>(prim, aux, pairs, groups[g].tasks, groups[g].ntask,
+    eri3_kernel<<<grid_for(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks, groups[g].ntask,
                                                          ic.boys, ic.counter, T);
     RIHF_LAUNCH_CHECK();
     if (ic.launches) *ic.launches += 1;
   }
+}
+
+// ------------------------------------------------------------ pair table
+
+// One thread per shell pair: p, 1/p, P, P - A and the Gaussian-product
+// prefactor of every primitive pair, in the la >= lb order of the kernels.
+__global__ void pair_prim_kernel(DevShells prim, const ShellPair* __restrict__ pairs, int npairs,
+                                 const int* __restrict__ off, PairPrim* __restrict__ pp) {
+  const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= npairs) return;
+  int sa = pairs[ip].a, sb = pairs[ip].b;
+  if (prim.l[sa] < prim.l[sb]) { int t = sa; sa = sb; sb = t; }
+  const double* A = prim.xyz + 3 * sa;
+  const double* B = prim.xyz + 3 * sb;
+  double R2 = 0.0;
+  for (int i = 0; i < 3; ++i) R2 += (A[i] - B[i]) * (A[i] - B[i]);
+  PairPrim* out = pp + off[ip];
+  const int nb = prim.nprim[sb];
+  for (int pa = 0; pa < prim.nprim[sa]; ++pa)
+    for (int pb = 0; pb < nb; ++pb) {
+      const double al = prim.exps[prim.pstart[sa] + pa], be = prim.exps[prim.pstart[sb] + pb];
+      const double p = al + be, ip_ = 1.0 / p;
+      PairPrim q;
+      q.p = p;
+      q.inv_p = ip_;
+      q.alpha = al;
+      q.beta = be;
+      q.K = 34.98683665524972 * prim.coefs[prim.pstart[sa] + pa] * prim.coefs[prim.pstart[sb] + pb] *
+            exp(-al * be * ip_ * R2) * ip_;
+      for (int i = 0; i < 3; ++i) {
+        q.P[i] = (al * A[i] + be * B[i]) * ip_;
+        q.PA[i] = q.P[i] - A[i];
+      }
+      q.pad = 0.0;
+      out[pa * nb + pb] = q;
+    }
+}
+
+std::vector<int> pair_prim_offsets(const std::vector<ShellPair>& pairs, const std::vector<int>& nprim) {
+  std::vector<int> off(pairs.size() + 1, 0);
+  for (size_t i = 0; i < pairs.size(); ++i) off[i + 1] = off[i] + nprim[pairs[i].a] * nprim[pairs[i].b];
+  return off;
+}
+
+void launch_pair_prims(const IntegralCtx& ic, const DevShells& prim, const ShellPair* pairs, int npairs,
+                       const int* off, PairPrim* pp) {
+  if (npairs <= 0) return;
+  pair_prim_kernel<<<(npairs + 127) / 128, 128, 0, ic.stream>>>(prim, pairs, npairs, off, pp);
+  RIHF_LAUNCH_CHECK();
+  if (ic.launches) *ic.launches += 1;
 }
 
 // Class-grouped task lists: every (pair, auxiliary shell) task goes to the first

@@ -16,6 +16,7 @@ struct DevShells {
   const int* nprim = nullptr;
   const int* pstart = nullptr;
   const double* exps = nullptr;
+  const double* iexps = nullptr; // 1 / exps
   const double* coefs = nullptr; // primitive coefficients times x^l normalisation
   const int* ao = nullptr;       // first AO of each shell
   const double* tr = nullptr;    // per-l transform, kTrL x 15 x 15 (rows: output functions)
@@ -27,12 +28,29 @@ struct ShellPair {
   int a, b;
 };
 
+struct PairPrim;   // os_hgp.cuh
+// Primitive-pair data of the listed shell pairs: entries off[i] ..
+// off[i] + nprim(a) nprim(b) - 1 of pp for pair i, ordered (pa, pb) with the
+// pair's shells swapped to la >= lb (the order the kernels evaluate in).
+struct PairTable {
+  const PairPrim* pp = nullptr;
+  const int* off = nullptr;
+};
+// Offsets for a pair list (host), and the per-geometry build of the table.
+std::vector<int> pair_prim_offsets(const std::vector<ShellPair>& pairs, const std::vector<int>& nprim);
+
+
 struct IntegralCtx {
   const double* boys = nullptr;  // Boys table on device
   int* counter = nullptr;        // device work counter (one int per launch kind)
   cudaStream_t stream = 0;
   long long* launches = nullptr; // host-side launch counter
 };
+
+// Build the primitive-pair table for `npairs` pairs (device), into pp (sized
+// by the last offset from pair_prim_offsets plus the last pair's count).
+void launch_pair_prims(const IntegralCtx& ic, const DevShells& prim, const ShellPair* pairs, int npairs,
+                       const int* off, PairPrim* pp);
 
 // Shared memory (doubles) one warp needs for a (la >= lb | lc) class of the
 // integral and of the derivative kernel.
@@ -53,7 +71,7 @@ void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<in
 // Three-centre integrals T[P][mu][nu] = (mu nu|P) for the listed shell pairs
 // (mu in a, nu in b, a >= b; both triangles inside diagonal shell blocks).
 void launch_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
-                 const TaskGroup* groups, int ngroups, double* T);
+                 const PairTable& pt, const TaskGroup* groups, int ngroups, double* T);
 
 // Metric A[P][Q] = (P|Q) (full symmetric matrix).
 void launch_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, double* A);
@@ -73,7 +91,7 @@ int schwarz_smem_bytes(int max_lp);
 //   grad[atom][x] += -1/2 sum_PQ Z[P][Q] d(P|Q)/dR                      (2-centre)
 //   grad[atom][x] += sum D d(T+V)/dR - sum W dS/dR                      (one-electron)
 void launch_grad_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
-                      const TaskGroup* groups, int ngroups, const double* Y, double* grad);
+                      const PairTable& pt, const TaskGroup* groups, int ngroups, const double* Y, double* grad);
 void launch_grad_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, const double* Z, double* grad);
 void launch_grad_one_electron(const IntegralCtx& ic, const DevShells& prim, int max_lp, int natoms, const int* Z,
                               const double* axyz, const double* D, const double* W, double* grad_one,

@@ -22,6 +22,14 @@ constexpr double kBoysStep = 0.05;
 constexpr double kBoysTmax = 40.0;
 constexpr int kBoysTaylor = 7;
 
+// Per-primitive scalar region at the head of every warp's shared-memory slice:
+// Boys values F_m (24), then the recursion factors k / (2p) and k / (2q) for
+// k = 0..23.  On GB300 every FP64 warp instruction occupies the SM's narrow
+// FP64 pipe whatever its active-lane count, so these factors are read from
+// shared memory instead of being rebuilt (int -> double, multiply) per element.
+constexpr int kFmRegion = 72;
+constexpr int kH2p = 24, kH2q = 48;
+
 // Cartesian (or solid harmonic) transform per l: rows = output functions,
 // cols = Cartesian components; kTrStride x kTrStride per l.
 constexpr int kTrStride = 15;
@@ -39,9 +47,11 @@ __device__ inline double boys_eval(int m, double T, const double* __restrict__ t
     double d = T - k * kBoysStep;
     const double* row = tab + (size_t)k * kBoysM + m;
     // sum_j F_{m+j}(T_k) (-d)^j / j!   (d/dT F_m = -F_{m+1})
+    // 1/j as constants: an FP64 division costs a dozen FP64-pipe instructions
+    const double inv_j[kBoysTaylor] = {0.0, 1.0, 0.5, 1.0 / 3.0, 0.25, 0.2, 1.0 / 6.0};
     double s = row[kBoysTaylor - 1];
 #pragma unroll
-    for (int j = kBoysTaylor - 1; j >= 1; --j) s = row[j - 1] - d * s / j;
+    for (int j = kBoysTaylor - 1; j >= 1; --j) s = fma(-d * inv_j[j], s, row[j - 1]);
     return s;
   }
   double f = 0.5 * sqrt(3.14159265358979323846 / T);
@@ -68,7 +78,58 @@ struct Prim3 {
   double beta;            // exponent of the bra's second function
   double pref;            // prefactor of [00|00]^(m)
   double T;               // Boys argument
+  double inv2p, rp;       // 1/(2p), rho/p                  (vertical recurrence)
+  double inv2q, poq;      // 1/(2q), p/q                    (electron transfer)
+  double bqAB[3];         // beta AB_i / q                  (electron transfer)
 };
+
+// Shell-pair primitive data (a, b) with la >= lb, built once per geometry.
+struct PairPrim {
+  double p, inv_p, alpha, beta;
+  double K;               // 2 pi^{5/2} c_a c_b exp(-alpha beta/p |AB|^2) / p
+  double P[3], PA[3];
+  double pad;
+};
+
+// Three-centre triple from the pair table and one auxiliary primitive
+// (exponent ga, 1/ga, contraction coefficient cc at C): one rsqrt, no division.
+__device__ inline Prim3 make_prim3_pp(const PairPrim& q, double ga, double iga, double cc, const double* C,
+                                      const double* AB) {
+  Prim3 t;
+  t.p = q.p;
+  t.q = ga;
+  t.beta = q.beta;
+  const double CP0 = C[0] - q.P[0], CP1 = C[1] - q.P[1], CP2 = C[2] - q.P[2];
+  const double R2 = fma(CP0, CP0, fma(CP1, CP1, CP2 * CP2));
+  const double r = rsqrt(q.p + ga);      // (p + gamma)^{-1/2}
+  const double gi = ga * (r * r);        // gamma / (p + gamma)
+  t.rho = q.p * gi;
+  t.rp = gi;
+  t.WP[0] = gi * CP0;
+  t.WP[1] = gi * CP1;
+  t.WP[2] = gi * CP2;
+  t.T = t.rho * R2;
+  t.pref = q.K * (cc * iga) * r;
+  t.inv2p = 0.5 * q.inv_p;
+  t.inv2q = 0.5 * iga;
+  t.poq = q.p * iga;
+  const double bq = q.beta * iga;
+  for (int i = 0; i < 3; ++i) {
+    t.PA[i] = q.PA[i];
+    t.AB[i] = AB[i];
+    t.bqAB[i] = bq * AB[i];
+  }
+  return t;
+}
+
+// The derived recursion factors of a triple whose p, q, rho, beta, AB are set.
+__device__ inline void prim3_factors(Prim3& t) {
+  t.inv2p = 0.5 / t.p;
+  t.rp = t.rho / t.p;
+  t.inv2q = 0.5 / t.q;
+  t.poq = t.p / t.q;
+  for (int i = 0; i < 3; ++i) t.bqAB[i] = t.beta / t.q * t.AB[i];
+}
 
 // Normal three-centre triple (ab|c): A(alpha), B(beta), C(gamma).
 __device__ inline Prim3 make_prim3(double al, const double* A, double be, const double* B, double ga,
@@ -95,6 +156,7 @@ __device__ inline Prim3 make_prim3(double al, const double* A, double be, const 
   t.T = t.rho * R2pq;
   const double two_pi_52 = 34.98683665524972;   // 2 pi^{5/2}
   t.pref = two_pi_52 / (p * ga * sqrt(pq)) * exp(-al * be / p * R2ab);
+  prim3_factors(t);
   return t;
 }
 
@@ -118,6 +180,11 @@ __device__ inline Prim3 make_prim_point(double al, const double* A, double be, c
   }
   t.T = p * R2pc;
   t.pref = 6.283185307179586 / p * exp(-al * be / p * R2ab);
+  t.inv2p = 0.5 / p;
+  t.rp = 1.0;
+  t.inv2q = 0.0;
+  t.poq = 0.0;
+  t.bqAB[0] = t.bqAB[1] = t.bqAB[2] = 0.0;
   return t;
 }
 
@@ -174,10 +241,18 @@ __device__ __host__ inline int hrr_scratch(int la, int lb, int lc, int emax) {
 // [e0|00]^(m) for e = 0..L, m = 0..L-e into vrr; Fm (smem, L+1) must hold the
 // Boys values.  Obara-Saika:
 //   [e+1_i]^(m) = PA_i [e]^(m) + WP_i [e]^(m+1) + e_i/(2p) ([e-1_i]^(m) - rho/p [e-1_i]^(m+1))
-__device__ inline void warp_vrr(double* vrr, int L, const Prim3& t, const double* Fm, int lane) {
-  for (int m = lane; m <= L; m += 32) vrr[m] = t.pref * Fm[m];
+// Fm points at the warp's kFmRegion block: F_m in [0, L], and this routine
+// writes the k/(2p), k/(2q) factors at kH2p, kH2q for the electron transfer.
+__device__ inline void warp_vrr(double* vrr, int L, const Prim3& t, double* Fm, int lane) {
+  if (lane <= L) {
+    const double k = (double)lane;
+    vrr[lane] = t.pref * Fm[lane];
+    Fm[kH2p + lane] = k * t.inv2p;
+    Fm[kH2q + lane] = k * t.inv2q;
+  }
   __syncwarp();
-  const double inv2p = 0.5 / t.p, rp = t.rho / t.p;
+  const double* h2p = Fm + kH2p;
+  const double rp = t.rp;
   int off_m2 = 0, off_m1 = 0, off = L + 1;   // offsets of levels e-2, e-1, e
   for (int e = 1; e <= L; ++e) {
     int nc = ncart(e), nc1 = ncart(e - 1), nc2 = e >= 2 ? ncart(e - 2) : 0;
@@ -195,7 +270,7 @@ __device__ inline void warp_vrr(double* vrr, int L, const Prim3& t, const double
       if (ei > 0) {
         c1[i] -= 1;
         int k2 = cart_index(e - 2, c1[0], c1[1]);
-        v += ei * inv2p * (vrr[off_m2 + m * nc2 + k2] - rp * vrr[off_m2 + (m + 1) * nc2 + k2]);
+        v = fma(h2p[ei], fma(-rp, vrr[off_m2 + (m + 1) * nc2 + k2], vrr[off_m2 + m * nc2 + k2]), v);
       }
       vrr[off + m * nc + k] = v;
     }
@@ -235,10 +310,12 @@ __device__ inline void warp_acc_level(const double* vrr, int L, const double* et
   __syncwarp();
 }
 
+// Fm: the warp's scalar region after warp_vrr (reads the k/(2q) factors).
 __device__ inline void warp_etr(const double* vrr, int L, double* etr, const EtrShape& sh, const Prim3& t,
-                                int lane) {
+                                const double* Fm, int lane) {
   const int lc = sh.lc;
-  const double inv2q = 0.5 / t.q, poq = t.p / t.q, bq = t.beta / t.q;
+  const double poq = t.poq;
+  const double* h2q = Fm + kH2q;
   auto get = [&](int c, int e, int ke, int kc) -> double { return etr_get(vrr, L, etr, sh, c, e, ke, kc); };
   for (int c = 1; c <= lc; ++c) {
     int lo = sh.elo(c), hi = sh.ehi(c);
@@ -262,18 +339,18 @@ __device__ inline void warp_etr(const double* vrr, int L, double* etr, const Etr
       // - p/q [e+1_i|c'] - beta AB_i / q [e|c']
       eo[i] += 1;
       double v = -poq * get(c - 1, e + 1, cart_index(e + 1, eo[0], eo[1]), kcl);
-      v -= bq * t.AB[i] * get(c - 1, e, ke, kcl);
+      v = fma(-t.bqAB[i], get(c - 1, e, ke, kcl), v);
       eo[i] -= 1;
       if (eo[i] > 0) {   // e_i/(2q) [e-1_i|c']
         int ei = eo[i];
         eo[i] -= 1;
-        v += ei * inv2q * get(c - 1, e - 1, cart_index(e - 1, eo[0], eo[1]), kcl);
+        v = fma(h2q[ei], get(c - 1, e - 1, cart_index(e - 1, eo[0], eo[1]), kcl), v);
         eo[i] += 1;
       }
       if (cl[i] > 0) {   // c'_i/(2q) [e|c'-1_i]
         int ci = cl[i];
         cl[i] -= 1;
-        v += ci * inv2q * get(c - 2, e, ke, cart_index(c - 2, cl[0], cl[1]));
+        v = fma(h2q[ci], get(c - 2, e, ke, cart_index(c - 2, cl[0], cl[1])), v);
       }
       lvl[idx] = v;
     }
@@ -282,8 +359,8 @@ __device__ inline void warp_etr(const double* vrr, int L, double* etr, const Etr
 }
 
 __device__ inline void warp_etr_accumulate(const double* vrr, int L, double* etr, const EtrShape& sh,
-                                           const Prim3& t, double w, double* acc, int lane) {
-  warp_etr(vrr, L, etr, sh, t, lane);
+                                           const Prim3& t, double w, double* acc, const double* Fm, int lane) {
+  warp_etr(vrr, L, etr, sh, t, Fm, lane);
   warp_acc_level(vrr, L, etr, sh, w, acc, lane);
 }
 

@@ -407,9 +407,11 @@ struct rihf_ctx {
 
   // device basis
   int *d_pl = nullptr, *d_patom = nullptr, *d_pnprim = nullptr, *d_pps = nullptr, *d_pao = nullptr;
-  double *d_pxyz = nullptr, *d_pexp = nullptr, *d_pcoef = nullptr;
+  double *d_pxyz = nullptr, *d_pexp = nullptr, *d_pcoef = nullptr, *d_piexp = nullptr;
   int *d_al = nullptr, *d_aatom = nullptr, *d_anprim = nullptr, *d_aps = nullptr, *d_aao = nullptr;
-  double *d_axyz_sh = nullptr, *d_aexp = nullptr, *d_acoef = nullptr;
+  double *d_axyz_sh = nullptr, *d_aexp = nullptr, *d_acoef = nullptr, *d_aiexp = nullptr;
+  int* d_pp_off = nullptr;        // primitive-pair table offsets per listed shell pair
+  PairPrim* d_pp = nullptr;       // primitive-pair data (per geometry)
   double* d_tr = nullptr;
   int* d_nf = nullptr;
   int* d_Z = nullptr;
@@ -484,16 +486,22 @@ struct rihf_ctx {
     c.launches = const_cast<long long*>(&launches);
     return c;
   }
+  PairTable ptab() const {
+    PairTable t;
+    t.pp = d_pp;
+    t.off = d_pp_off;
+    return t;
+  }
   DevShells prim() const {
     DevShells s;
     s.nshell = hp.nshell; s.nfunc = N; s.l = d_pl; s.atom = d_patom; s.xyz = d_pxyz; s.nprim = d_pnprim;
-    s.pstart = d_pps; s.exps = d_pexp; s.coefs = d_pcoef; s.ao = d_pao; s.tr = d_tr; s.nf = d_nf;
+    s.pstart = d_pps; s.exps = d_pexp; s.iexps = d_piexp; s.coefs = d_pcoef; s.ao = d_pao; s.tr = d_tr; s.nf = d_nf;
     return s;
   }
   DevShells aux() const {
     DevShells s;
     s.nshell = ha.nshell; s.nfunc = NA; s.l = d_al; s.atom = d_aatom; s.xyz = d_axyz_sh; s.nprim = d_anprim;
-    s.pstart = d_aps; s.exps = d_aexp; s.coefs = d_acoef; s.ao = d_aao; s.tr = d_tr; s.nf = d_nf;
+    s.pstart = d_aps; s.exps = d_aexp; s.iexps = d_aiexp; s.coefs = d_acoef; s.ao = d_aao; s.tr = d_tr; s.nf = d_nf;
     return s;
   }
 };
@@ -509,6 +517,7 @@ static std::vector<double>& boys_host() {
 
 // Rebuild the class-grouped 3-centre task lists from the current pair list.
 static void refresh_tasks(rihf_ctx* c) {
+  upload(c->d_pp_off, pair_prim_offsets(c->pairs_h, c->hp.nprim), c->stream);
   std::vector<std::vector<int2>> tasks;
   std::vector<int> se, sg;
   build_task_groups(c->pairs_h, c->hp.l, c->ha.l, tasks, se, sg);
@@ -526,6 +535,7 @@ static void refresh_tasks(rihf_ctx* c) {
 static void free_all(rihf_ctx* c) {
   void* ptrs[] = {c->d_pl, c->d_patom, c->d_pnprim, c->d_pps, c->d_pao, c->d_pxyz, c->d_pexp, c->d_pcoef,
                   c->d_al, c->d_aatom, c->d_anprim, c->d_aps, c->d_aao, c->d_axyz_sh, c->d_aexp, c->d_acoef,
+                  c->d_piexp, c->d_aiexp, c->d_pp_off, c->d_pp,
                   c->d_tr, c->d_nf, c->d_Z, c->d_xyz, c->d_boys, c->d_counter, c->d_flag, c->d_pairs, c->d_tasks, c->d_schwarz,
                   c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->T3, c->B, c->Xo, c->Sw, c->Sv,
                   c->C, c->eps, c->Ct, c->D, c->J, c->K, c->F, c->Fx, c->T1, c->T2, c->Err, c->Fp, c->Cp, c->Hb,
@@ -601,7 +611,8 @@ static void compute_geometry(rihf_ctx* c) {
   // L^{-1} product loses accuracy when cond(A) reaches 1e9 (diffuse auxiliary sets)
   RIHF_CUDA(cudaMemsetAsync(c->T3, 0, sizeof(double) * (size_t)NA * N * N, s));
   { TraceScope t(c->tracer, s, "eri3_kernel (mu nu|P)", (double)NA * N * (N + 1) / 2 * 8, 1);
-    launch_eri3(ic, P, X, c->d_pairs, c->groups, kTaskGroups, c->T3); }
+    launch_pair_prims(ic, P, c->d_pairs, c->npairs, c->d_pp_off, c->d_pp);
+    launch_eri3(ic, P, X, c->d_pairs, c->ptab(), c->groups, kTaskGroups, c->T3); }
   RIHF_CUDA(cudaMemcpyAsync(c->B, c->T3, sizeof(double) * (size_t)NA * N * N, cudaMemcpyDeviceToDevice, s));
   { TraceScope t(c->tracer, s, "fit trsm B=L^-1 T", (double)NA * NA * N * (N + 1) / 2, 0);
     trsm_lower(la, c->L, NA, c->B, (long long)N * N, false, N, c->trsm_tmp); }
@@ -781,6 +792,11 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     c->d_pps = dalloc<int>(c->hp.nshell); upload(c->d_pps, c->hp.pstart, s);
     c->d_pao = dalloc<int>(c->hp.nshell); upload(c->d_pao, c->hp.ao, s);
     c->d_pexp = dalloc<double>(c->hp.exps.size()); upload(c->d_pexp, c->hp.exps, s);
+    {
+      std::vector<double> ie(c->hp.exps.size());
+      for (size_t i = 0; i < ie.size(); ++i) ie[i] = 1.0 / c->hp.exps[i];
+      c->d_piexp = dalloc<double>(ie.size()); upload(c->d_piexp, ie, s);
+    }
     c->d_pcoef = dalloc<double>(c->hp.coefs.size()); upload(c->d_pcoef, c->hp.coefs, s);
     c->d_pxyz = dalloc<double>(3 * c->hp.nshell);
     c->d_al = dalloc<int>(c->ha.nshell); upload(c->d_al, c->ha.l, s);
@@ -789,6 +805,11 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     c->d_aps = dalloc<int>(c->ha.nshell); upload(c->d_aps, c->ha.pstart, s);
     c->d_aao = dalloc<int>(c->ha.nshell); upload(c->d_aao, c->ha.ao, s);
     c->d_aexp = dalloc<double>(c->ha.exps.size()); upload(c->d_aexp, c->ha.exps, s);
+    {
+      std::vector<double> ie(c->ha.exps.size());
+      for (size_t i = 0; i < ie.size(); ++i) ie[i] = 1.0 / c->ha.exps[i];
+      c->d_aiexp = dalloc<double>(ie.size()); upload(c->d_aiexp, ie, s);
+    }
     c->d_acoef = dalloc<double>(c->ha.coefs.size()); upload(c->d_acoef, c->ha.coefs, s);
     c->d_axyz_sh = dalloc<double>(3 * c->ha.nshell);
     c->d_tr = dalloc<double>(c->tr_h.size()); upload(c->d_tr, c->tr_h, s);
@@ -806,6 +827,8 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     c->d_pairs = dalloc<ShellPair>(c->pairs_h.size()); upload(c->d_pairs, c->pairs_h, s);
     c->d_schwarz = dalloc<double>(c->pairs_h.size());
     c->d_tasks = dalloc<int2>(c->pairs_h.size() * (size_t)c->ha.nshell);
+    c->d_pp_off = dalloc<int>(c->pairs_h.size() + 1);
+    c->d_pp = dalloc<PairPrim>(std::max(1, pair_prim_offsets(c->pairs_h, c->hp.nprim).back()));
     refresh_tasks(c);
     {
       int maxsm = 0;
@@ -1286,7 +1309,7 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   { TraceScope t(c->tracer, s, "grad_one_electron_kernel", 0.0, 0);
     launch_grad_one_electron(ic, c->prim(), c->max_lp, nat, c->d_Z, c->d_xyz, c->D, c->W, g_one, g_ovl); }
   { TraceScope t(c->tracer, s, "grad_eri3_kernel (fused d(mu nu|P) . Y)", (double)NA * N * (N + 1) / 2 * 8, 1);
-    launch_grad_eri3(ic, c->prim(), c->aux(), c->d_pairs, c->groups, kTaskGroups, c->Y, g_three); }
+    launch_grad_eri3(ic, c->prim(), c->aux(), c->d_pairs, c->ptab(), c->groups, kTaskGroups, c->Y, g_three); }
   { TraceScope t(c->tracer, s, "grad_eri2_kernel (fused d(P|Q) . Z)", (double)NA * NA * 8, 1);
     launch_grad_eri2(ic, c->aux(), c->max_la, c->Zm, g_two); }
   c->grad_parts_h.assign(15 * nat, 0.0);
