@@ -110,7 +110,18 @@ int rihf_update_geometry(rihf_ctx* ctx, const double* xyz);
  * tp), F = h + J + K (Eq. fock_split), E = 1/2 Tr D(h+F) + V_nn, the DIIS
  * error X^T(FDS - SDF)X, Pulay extrapolation and diagonalisation.
  *   guess: 0 core Hamiltonian, 1 C_guess (N*N, columns 0..nocc-1 used),
- *          2 the context's previous converged orbitals (falls back to 0).
+ *          2 the context's previous converged orbitals (the paper's AIMD
+ *            guess, Sec. 3.3; falls back to 0),
+ *          3 density extrapolation D_x = 3 D_t - 3 D_{t-1} + D_{t-2} over the
+ *            last three converged SCFs of this context (falls back to 2),
+ *          4 learned: D_x plus the correction of the network configured by
+ *            rihf_learn_config, once it beats D_x on its last training
+ *            example (else D_x; falls back to 2).  With guesses 3 and 4 the
+ *            previous occupied orbitals are projected onto the predicted
+ *            density (C <- D_pred S C, then S-orthonormalised).
+ *          Every converged SCF pushes its D, S and nuclear positions into the
+ *          three-deep history; a guess-4 SCF first trains the network on its
+ *          own example (rihf_learn_config).
  *   energy (1), D (N*N), C (N*N), eps (N), iters (1): outputs; any may be NULL.
  * Returns NOT_CONVERGED (outputs filled from the last iterate) after max_iter.
  */
@@ -142,11 +153,15 @@ int rihf_query(rihf_ctx* ctx, int* N, int* Naux, int* nocc, int* natoms);
                           components of shells a >= b, packed a(a+1)/2 + b
                           (nshell(nshell+1)/2 values; zeros when the screen
                           is not evaluated)
+     RIHF_MAT_DPRED: N x N, the predicted density of the last guess-3 or
+                          guess-4 SCF (extrapolation plus network correction)
+     RIHF_MAT_FEATURES: N(N+1)/2 x 12, the network's features of that guess
+                          (stored in FP32, returned as doubles)
    J, K, F, D refer to the last Fock build. */
 enum {
   RIHF_MAT_S = 0, RIHF_MAT_H = 1, RIHF_MAT_A = 2, RIHF_MAT_LINV = 3, RIHF_MAT_T3 = 4, RIHF_MAT_B = 5,
   RIHF_MAT_J = 6, RIHF_MAT_K = 7, RIHF_MAT_F = 8, RIHF_MAT_D = 9, RIHF_MAT_GRAD_PARTS = 10,
-  RIHF_MAT_SCHWARZ = 11
+  RIHF_MAT_SCHWARZ = 11, RIHF_MAT_DPRED = 12, RIHF_MAT_FEATURES = 13
 };
 int rihf_get_matrix(rihf_ctx* ctx, int which, double* out);
 
@@ -215,6 +230,42 @@ int rihf_eigh_noalloc(int n, const double* A, double* W, double* V, void* stream
    Errors: INVALID_ARG, OOM, CUDA, TIMEOUT (a bounded device wait ran out). */
 int rihf_tc_dgemm(int M, int N, int K, const double* A, const double* B, double* C, int digits, int kblock,
                   int device);
+
+/* Learned SCF guess (guess 4 of rihf_scf): an elementwise-shared two-layer MLP
+   x (12 features) -> tanh(W1 x + b1) (hidden units) -> y = w2 . h + b2 over the
+   lower-triangle density elements mu >= nu, predicting
+   (D_{t+1} - D_x) / scale.  Features: D_t, D_{t-1}, D_{t-2}, D_x, S_{t+1}, S_t,
+   |R_A - R_B| / 10 bohr at t+1, t, t-1 (A, B the atoms of mu, nu), same-atom
+   flag, (l_mu + l_nu) / 4, |l_mu - l_nu| / 4.  Weights are used in BF16 (FP32
+   master copies), products accumulated in FP32, loss (1/M) sum (y - t)^2,
+   Adam (0.9, 0.999, 1e-8).  scale = RMS of the first target.
+   rihf_learn_config (re)initialises the network from `seed` (W1 ~
+   U(+-1/sqrt(12)), w2 ~ U(+-0.1/sqrt(hidden)), biases 0): hidden in 32..512
+   (multiple of 32); the first `train_steps` guess-4 SCFs with enough history
+   each run `adam_iters` Adam steps at learning rate lr on their example after
+   converging.  Errors: INVALID_ARG, OOM, CUDA. */
+int rihf_learn_config(rihf_ctx* ctx, int hidden, int train_steps, int adam_iters, double lr,
+                      unsigned long long seed);
+/* trained_steps; last_ratio = sum (y - t)^2 / sum t^2 of the last training
+   example before its update (below 1: the network beat D_x on an unseen
+   example; guess 4 uses the network only below 0.9); last_guess = the guess
+   kind the last rihf_scf actually used (0, 1, 2, 3 or 4; guess 4 runs the
+   network once it has trained on three examples and the median of its last
+   three out-of-sample ratios is below 0.8); scale.  Any pointer may be NULL. */
+int rihf_learn_stats(rihf_ctx* ctx, int* trained_steps, double* last_ratio, int* last_guess, double* scale);
+/* The network's FP32 master parameters (layout of rihf_mlp_eval) into out;
+   INVALID_ARG before rihf_learn_config. */
+int rihf_learn_params(rihf_ctx* ctx, float* out);
+/* The network's kernels on host buffers (no context): params (mlp_nparams =
+   12 hidden + 2 hidden + 1 floats, layout W1[hidden][12], b1, w2, b2) are
+   rounded to BF16 as in training; X is M x 12 row-major.  y (M, or NULL) gets
+   the forward pass; with targets t (M): grad (params layout) = dL/dparams,
+   loss2 = {sum (y - t)^2, sum t^2}; with lr > 0, iters >= 1 and params_out:
+   `iters` full-batch Adam steps from zero moments, params_out = the master
+   parameters after them and losses[k] (optional) = sum (y - t)^2 before step
+   k.  Errors: INVALID_ARG, OOM, CUDA. */
+int rihf_mlp_eval(int hidden, int M, const float* params, const float* X, const float* t, float lr, int iters,
+                  float* y, float* grad, float* params_out, float* loss2, float* losses, int device);
 
 const char* rihf_strerror(int code);
 const char* rihf_last_error(void);

@@ -19,7 +19,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librihf.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["rihf_api.cu", "integrals.cu", "grad_integrals.cu", "linalg.cu", "jk.cu", "eigh_noalloc.cu", "tc_gemm.cu"]
+SOURCES = ["rihf_api.cu", "integrals.cu", "grad_integrals.cu", "linalg.cu", "jk.cu", "eigh_noalloc.cu", "tc_gemm.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

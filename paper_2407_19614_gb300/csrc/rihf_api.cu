@@ -17,6 +17,7 @@
 #include "jk.cuh"
 #include "linalg.cuh"
 #include "os_hgp.cuh"
+#include "mlp.cuh"
 #include "tc_gemm.cuh"
 
 using namespace rihf;
@@ -450,6 +451,28 @@ struct rihf_ctx {
   int *Bex = nullptr, *Cex = nullptr, *Hex = nullptr;
   OzOperand Bop;
   int tc_builds = 0, last_iters = 0, last_digits = 0;
+
+  // learned / extrapolated guess: the last three converged densities, the
+  // overlap and nuclear positions of the last geometry, features of the
+  // current step and the network
+  int *d_ao_atom = nullptr, *d_ao_l = nullptr;
+  double* hist_D[3] = {nullptr, nullptr, nullptr};   // D_t, D_{t-1}, D_{t-2}
+  double* hist_S = nullptr;                          // S_t
+  double* hist_xyz[2] = {nullptr, nullptr};          // R_t, R_{t-1}
+  int nhist = 0;
+  double* Dpred = nullptr;
+  float *mlX = nullptr, *mly = nullptr, *mlt = nullptr;
+  double* mlDx = nullptr;
+  double* ml_sums = nullptr;                          // feature scale sums (device, 3)
+  double ml_sd = 0.0, ml_ss = 0.0, ml_sr = 0.0;       // feature scales, fixed at the first build
+  static constexpr int kReplay = 8;                   // training examples kept for replay
+  float *rep_X = nullptr, *rep_t = nullptr;
+  int nrep = 0, rep_head = 0;
+  MlpDev net;
+  bool net_on = false, pending_example = false;
+  int train_steps = 200, adam_iters = 4, trained_steps = 0, last_guess = 0;
+  double ml_lr = 1e-3, ml_scale = 0.0, ml_last_ratio = 1e300;
+  double ml_ratios[3] = {1e300, 1e300, 1e300};        // last three out-of-sample ratios
   double* trsm_tmp = nullptr;
   double *cvec = nullptr, *W = nullptr, *Bij = nullptr, *Xt = nullptr, *Zm = nullptr, *G = nullptr, *Y = nullptr;
   double* grad_parts = nullptr;   // 5 x natoms x 3 on device (one, overlap, three, two, nuc)
@@ -536,6 +559,9 @@ static void free_all(rihf_ctx* c) {
   void* ptrs[] = {c->d_pl, c->d_patom, c->d_pnprim, c->d_pps, c->d_pao, c->d_pxyz, c->d_pexp, c->d_pcoef,
                   c->d_al, c->d_aatom, c->d_anprim, c->d_aps, c->d_aao, c->d_axyz_sh, c->d_aexp, c->d_acoef,
                   c->d_piexp, c->d_aiexp, c->d_pp_off, c->d_pp,
+                  c->d_ao_atom, c->d_ao_l, c->hist_D[0], c->hist_D[1], c->hist_D[2], c->hist_S, c->hist_xyz[0],
+                  c->hist_xyz[1], c->Dpred, c->mlX, c->mly, c->mlt, c->mlDx, c->ml_sums, c->rep_X, c->rep_t, c->net.master, c->net.wbf, c->net.grad,
+                  c->net.m, c->net.v, c->net.loss,
                   c->d_tr, c->d_nf, c->d_Z, c->d_xyz, c->d_boys, c->d_counter, c->d_flag, c->d_pairs, c->d_tasks, c->d_schwarz,
                   c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->T3, c->B, c->Xo, c->Sw, c->Sv,
                   c->C, c->eps, c->Ct, c->D, c->J, c->K, c->F, c->Fx, c->T1, c->T2, c->Err, c->Fp, c->Cp, c->Hb,
@@ -869,6 +895,28 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
       c->Hex = dalloc<int>(oz_plane_elems(N, 1, 1) / kOzChunk * nkb_max);
     }
     c->trsm_tmp = dalloc<double>(32 * std::max<size_t>({n2, (size_t)NA, (size_t)c->nocc * c->nocc}) + 1024);
+    {   // guess history and learned-guess buffers
+      std::vector<int> aoat(N), aol(N);
+      for (int i = 0; i < c->hp.nshell; ++i)
+        for (int k = 0; k < c->nf_h[c->hp.l[i]]; ++k) {
+          aoat[c->hp.ao[i] + k] = c->hp.atom[i];
+          aol[c->hp.ao[i] + k] = c->hp.l[i];
+        }
+      c->d_ao_atom = dalloc<int>(N); upload(c->d_ao_atom, aoat, s);
+      c->d_ao_l = dalloc<int>(N); upload(c->d_ao_l, aol, s);
+      for (auto& h : c->hist_D) h = dalloc<double>(n2);
+      c->hist_S = dalloc<double>(n2);
+      for (auto& h : c->hist_xyz) h = dalloc<double>(3 * natoms);
+      c->Dpred = dalloc<double>(n2);
+      const size_t M = (size_t)N * (N + 1) / 2;
+      c->mlX = dalloc<float>(M * kMlpF);
+      c->mly = dalloc<float>(M);
+      c->mlt = dalloc<float>(M);
+      c->mlDx = dalloc<double>(M);
+      c->ml_sums = dalloc<double>(3);
+      c->rep_X = dalloc<float>(M * kMlpF * rihf_ctx::kReplay);
+      c->rep_t = dalloc<float>(M * rihf_ctx::kReplay);
+    }
     c->grad_parts = dalloc<double>(5 * 3 * natoms);
     c->work_elems = std::max<size_t>({(size_t)1 << 24, 8 * n2 * 4, (size_t)NA * 64});
     c->work = dalloc<double>(c->work_elems);
@@ -1068,6 +1116,60 @@ static void diis_error(rihf_ctx* c) {
   maxabs(la, n * n, c->Err, c->scal + 1);
 }
 
+// After a converged SCF: one online training step of the network on this
+// geometry's example (features built for the guess, target = converged D minus
+// the extrapolation, scaled by the RMS of the first target), then push D, S and
+// the nuclear positions into the history.
+static void learn_and_push_history(rihf_ctx* c) {
+  cudaStream_t s = c->stream;
+  const int N = c->N;
+  const size_t n2 = (size_t)N * N;
+  if (c->pending_example) {
+    const int M = N * (N + 1) / 2;
+    if (c->ml_scale <= 0.0) {
+      // RMS of the first target fixes the output scale
+      mlp_target(s, N, c->D, c->mlDx, 1.0, c->mlt);
+      std::vector<float> t(M);
+      RIHF_CUDA(cudaMemcpyAsync(t.data(), c->mlt, sizeof(float) * M, cudaMemcpyDeviceToHost, s));
+      RIHF_CUDA(cudaStreamSynchronize(s));
+      double ss = 0.0;
+      for (float v : t) ss += (double)v * v;
+      c->ml_scale = std::max(std::sqrt(ss / M), 1e-12);
+    }
+    mlp_target(s, N, c->D, c->mlDx, c->ml_scale, c->mlt);
+    // out-of-sample check on this (not yet seen) example, then replay
+    // training on the last kReplay examples
+    float first[2] = {0.f, 0.f};
+    mlp_backward(s, c->net, c->mlX, c->mlt, M);
+    RIHF_CUDA(cudaMemcpyAsync(first, c->net.loss, sizeof(first), cudaMemcpyDeviceToHost, s));
+    RIHF_CUDA(cudaMemcpyAsync(c->rep_X + (size_t)c->rep_head * M * kMlpF, c->mlX, sizeof(float) * M * kMlpF,
+                              cudaMemcpyDeviceToDevice, s));
+    RIHF_CUDA(cudaMemcpyAsync(c->rep_t + (size_t)c->rep_head * M, c->mlt, sizeof(float) * M,
+                              cudaMemcpyDeviceToDevice, s));
+    c->rep_head = (c->rep_head + 1) % rihf_ctx::kReplay;
+    c->nrep = std::min(c->nrep + 1, rihf_ctx::kReplay);
+    for (int k = 0; k < c->adam_iters; ++k) {
+      mlp_backward(s, c->net, c->rep_X, c->rep_t, c->nrep * M);
+      mlp_adam(s, c->net, (float)c->ml_lr);
+    }
+    c->launches += 2 + 2 * c->adam_iters;
+    RIHF_CUDA(cudaStreamSynchronize(s));
+    // loss of the network before this step's update, relative to the
+    // extrapolation's (y = 0): an out-of-sample check of the prediction
+    c->ml_last_ratio = first[1] > 0.f ? (double)first[0] / first[1] : 1e300;
+    c->ml_ratios[c->trained_steps % 3] = c->ml_last_ratio;
+    ++c->trained_steps;
+    c->pending_example = false;
+  }
+  std::swap(c->hist_D[2], c->hist_D[1]);
+  std::swap(c->hist_D[1], c->hist_D[0]);
+  RIHF_CUDA(cudaMemcpyAsync(c->hist_D[0], c->D, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
+  RIHF_CUDA(cudaMemcpyAsync(c->hist_S, c->S, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
+  std::swap(c->hist_xyz[1], c->hist_xyz[0]);
+  RIHF_CUDA(cudaMemcpyAsync(c->hist_xyz[0], c->d_xyz, sizeof(double) * 3 * c->natoms, cudaMemcpyDeviceToDevice, s));
+  c->nhist = std::min(c->nhist + 1, 3);
+}
+
 int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, double* Dout, double* Cout,
              double* epsout, int* iters) {
   RIHF_API_BEGIN
@@ -1080,7 +1182,7 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   if (guess == 1) {
     if (!C_guess) return RIHF_ERR_INVALID_ARG;
     RIHF_CUDA(cudaMemcpyAsync(c->C, C_guess, sizeof(double) * n2, cudaMemcpyHostToDevice, s));
-  } else if (guess == 2 && c->have_orbitals) {
+  } else if (guess >= 2 && guess <= 4 && c->have_orbitals) {
     // previous converged orbitals (the paper's AIMD guess, Sec. 3.3); after a
     // geometry change they are re-orthonormalised against the new overlap:
     // M = Co^T S Co = L_M L_M^T, Co <- Co L_M^{-T} (Cholesky / Gram-Schmidt,
@@ -1109,6 +1211,48 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
       transpose(la, c->T1, n, n, c->Cprev);
     }
     copy_cols(la, c->C, N, N, no, 1.0, c->Ct);
+    c->last_guess = 2;
+    c->pending_example = false;
+    if (guess >= 3 && c->nhist >= 3) {
+      // density guess: three-point extrapolation D_x = 3 D_t - 3 D_{t-1} + D_{t-2}
+      // (guess 3) plus, for guess 4, the network's correction once it beats
+      // the extrapolation on its last training example; the previous occupied
+      // orbitals are carried into the predicted occupied space by one
+      // projection Co <- D_pred S Co before the Gram-Schmidt step below
+      if (c->ml_sd <= 0.0) {
+        // feature scales: RMS of the first observed changes (fixed from then on)
+        mlp_scale_sums(s, N, c->hist_D[0], c->hist_D[1], c->S, c->hist_S, c->d_xyz, c->hist_xyz[0], c->d_ao_atom,
+                       c->ml_sums);
+        double sums[3];
+        RIHF_CUDA(cudaMemcpyAsync(sums, c->ml_sums, sizeof(sums), cudaMemcpyDeviceToHost, s));
+        RIHF_CUDA(cudaStreamSynchronize(s));
+        const double Mh = (double)N * (N + 1) / 2;
+        c->ml_sd = std::max(std::sqrt(sums[0] / Mh), 1e-12);
+        c->ml_ss = std::max(std::sqrt(sums[1] / Mh), 1e-12);
+        c->ml_sr = std::max(std::sqrt(sums[2] / Mh), 1e-12);
+        c->launches += 1;
+      }
+      mlp_features(s, N, c->hist_D[0], c->hist_D[1], c->hist_D[2], c->S, c->hist_S, c->d_xyz, c->hist_xyz[0],
+                   c->hist_xyz[1], c->d_ao_atom, c->d_ao_l, c->ml_sd, c->ml_ss, c->ml_sr, c->mlX, c->mlDx);
+      const int M = N * (N + 1) / 2;
+      // the network is used while the median of its last three out-of-sample
+      // ratios (loss / loss of the bare extrapolation) is below 0.8
+      double r3[3] = {c->ml_ratios[0], c->ml_ratios[1], c->ml_ratios[2]};
+      std::sort(r3, r3 + 3);
+      const bool use_net = guess == 4 && c->net_on && c->trained_steps >= 3 && r3[1] < 0.8;
+      if (use_net) mlp_forward(s, c->net, c->mlX, M, c->mly);
+      mlp_apply(s, N, c->mlDx, use_net ? c->mly : nullptr, c->ml_scale, c->Dpred);
+      c->launches += use_net ? 3 : 2;
+      c->last_guess = use_net ? 4 : 3;
+      c->pending_example = guess == 4 && c->net_on && c->trained_steps < c->train_steps;
+      GemmArgs p1;   // T1 (N x no) = S Co
+      p1.M = N; p1.N = no; p1.K = N; p1.A = c->S; p1.lda = N; p1.B = c->Ct; p1.ldb = no; p1.C = c->T1; p1.ldc = no;
+      dgemm(la, p1);
+      GemmArgs p2;   // Co = D_pred T1
+      p2.M = N; p2.N = no; p2.K = N; p2.A = c->Dpred; p2.lda = N; p2.B = c->T1; p2.ldb = no; p2.C = c->Ct;
+      p2.ldc = no;
+      dgemm(la, p2);
+    }
     GemmArgs g1;   // T1 (N x no) = S Co
     g1.M = N; g1.N = no; g1.K = N; g1.A = c->S; g1.lda = N; g1.B = c->Ct; g1.ldb = no; g1.C = c->T1; g1.ldc = no;
     dgemm(la, g1);
@@ -1124,6 +1268,8 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
                                 cudaMemcpyDeviceToDevice, s));
   } else {
     diagonalise(c, c->H, false);
+    c->last_guess = 0;
+    c->pending_example = false;
   }
   const int size = c->opt.diis_size;
   double E = 0.0, Eold = 0.0, emax = 0.0;
@@ -1220,6 +1366,7 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   RIHF_CUDA(cudaStreamSynchronize(s));
   c->tracer.flush();
   if (tc_flag) throw RihfError(RIHF_ERR_TIMEOUT, "tensor-core RI-K: a bounded device wait ran out");
+  if (conv) learn_and_push_history(c);
   if (energy) *energy = E;
   if (iters) *iters = it;
   c->last_iters = it;
@@ -1394,6 +1541,16 @@ int rihf_get_matrix(rihf_ctx* c, int which, double* out) {
       }
       break;
     }
+    case RIHF_MAT_FEATURES: {
+      const size_t nf = (size_t)c->N * (c->N + 1) / 2 * kMlpF;
+      std::vector<float> f(nf);
+      RIHF_CUDA(cudaMemcpy(f.data(), c->mlX, sizeof(float) * nf, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < nf; ++i) out[i] = f[i];
+      break;
+    }
+    case RIHF_MAT_DPRED:
+      RIHF_CUDA(cudaMemcpy(out, c->Dpred, n2 * 8, cudaMemcpyDeviceToHost));
+      break;
     case RIHF_MAT_SCHWARZ:
       if (c->schwarz_ok) RIHF_CUDA(cudaMemcpy(out, c->d_schwarz, sizeof(double) * c->npairs_total, cudaMemcpyDeviceToHost));
       else std::memset(out, 0, sizeof(double) * c->npairs_total);
@@ -1404,6 +1561,145 @@ int rihf_get_matrix(rihf_ctx* c, int which, double* out) {
       break;
     default: return RIHF_ERR_INVALID_ARG;
   }
+  return RIHF_OK;
+  RIHF_API_END
+}
+
+// Seeded initial weights: W1 ~ U(-1/sqrt(F), 1/sqrt(F)), w2 ~ U(-0.1/sqrt(H), 0.1/sqrt(H)), biases 0
+// (splitmix64 stream, so the same seed gives the same network on any host).
+static std::vector<float> mlp_init_params(int H, unsigned long long seed) {
+  std::vector<float> p(mlp_nparams(H), 0.f);
+  unsigned long long x = seed;
+  auto next = [&]() {
+    unsigned long long z = (x += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);   // [0, 1)
+  };
+  const double a1 = 1.0 / std::sqrt((double)kMlpF), a2 = 0.1 / std::sqrt((double)H);
+  for (int i = 0; i < H * kMlpF; ++i) p[i] = (float)((2.0 * next() - 1.0) * a1);
+  for (int j = 0; j < H; ++j) p[H * kMlpF + H + j] = (float)((2.0 * next() - 1.0) * a2);
+  return p;
+}
+
+static void mlp_alloc(MlpDev& net, int H) {
+  const int np = mlp_nparams(H);
+  net.H = H;
+  net.master = dalloc<float>(np);
+  net.wbf = dalloc<uint16_t>(np);
+  net.grad = dalloc<float>(np);
+  net.m = dalloc<float>(np);
+  net.v = dalloc<float>(np);
+  net.loss = dalloc<float>(2);
+  net.adam_t = 0;
+}
+
+int rihf_learn_config(rihf_ctx* c, int hidden, int train_steps, int adam_iters, double lr, unsigned long long seed) {
+  RIHF_API_BEGIN
+  if (!c || hidden < 32 || hidden > kMlpMaxH || hidden % 32 || train_steps < 0 || adam_iters < 1 || !(lr > 0.0))
+    return RIHF_ERR_INVALID_ARG;
+  cudaStream_t s = c->stream;
+  if (c->net.master) {
+    void* ptrs[] = {c->net.master, c->net.wbf, c->net.grad, c->net.m, c->net.v, c->net.loss};
+    RIHF_CUDA(cudaStreamSynchronize(s));
+    for (void* p : ptrs) cudaFree(p);
+    c->net = MlpDev();
+  }
+  mlp_alloc(c->net, hidden);
+  const int np = mlp_nparams(hidden);
+  std::vector<float> p = mlp_init_params(hidden, seed);
+  RIHF_CUDA(cudaMemcpyAsync(c->net.master, p.data(), sizeof(float) * np, cudaMemcpyHostToDevice, s));
+  RIHF_CUDA(cudaMemsetAsync(c->net.m, 0, sizeof(float) * np, s));
+  RIHF_CUDA(cudaMemsetAsync(c->net.v, 0, sizeof(float) * np, s));
+  mlp_round_weights(s, c->net);
+  RIHF_CUDA(cudaStreamSynchronize(s));
+  c->net_on = true;
+  c->train_steps = train_steps;
+  c->adam_iters = adam_iters;
+  c->ml_lr = lr;
+  c->trained_steps = 0;
+  c->ml_scale = 0.0;
+  c->ml_sd = c->ml_ss = c->ml_sr = 0.0;
+  c->nrep = c->rep_head = 0;
+  c->ml_last_ratio = 1e300;
+  c->ml_ratios[0] = c->ml_ratios[1] = c->ml_ratios[2] = 1e300;
+  return RIHF_OK;
+  RIHF_API_END
+}
+
+int rihf_learn_stats(rihf_ctx* c, int* trained_steps, double* last_ratio, int* last_guess, double* scale) {
+  if (!c) return RIHF_ERR_INVALID_ARG;
+  if (trained_steps) *trained_steps = c->trained_steps;
+  if (last_ratio) *last_ratio = c->ml_last_ratio;
+  if (last_guess) *last_guess = c->last_guess;
+  if (scale) *scale = c->ml_scale;
+  return RIHF_OK;
+}
+
+int rihf_learn_params(rihf_ctx* c, float* out) {
+  RIHF_API_BEGIN
+  if (!c || !out || !c->net_on) return RIHF_ERR_INVALID_ARG;
+  RIHF_CUDA(cudaStreamSynchronize(c->stream));
+  RIHF_CUDA(cudaMemcpy(out, c->net.master, sizeof(float) * mlp_nparams(c->net.H), cudaMemcpyDeviceToHost));
+  return RIHF_OK;
+  RIHF_API_END
+}
+
+int rihf_mlp_eval(int hidden, int M, const float* params, const float* X, const float* t, float lr, int iters,
+                  float* y, float* grad, float* params_out, float* loss2, float* losses, int device) {
+  RIHF_API_BEGIN
+  if (hidden < 32 || hidden > kMlpMaxH || hidden % 32 || M < 0 || !params || (M > 0 && !X) ||
+      (t == nullptr && (grad || loss2 || params_out || losses)) || (params_out && (!(lr > 0.f) || iters < 1)) ||
+      (losses && !params_out))
+    return RIHF_ERR_INVALID_ARG;
+  RIHF_CUDA(cudaSetDevice(device));
+  cudaStream_t s;
+  RIHF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  MlpDev net;
+  float *dX = nullptr, *dt = nullptr, *dy = nullptr;
+  auto release = [&]() {
+    void* ptrs[] = {net.master, net.wbf, net.grad, net.m, net.v, net.loss, dX, dt, dy};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    cudaStreamDestroy(s);
+  };
+  try {
+    const int np = mlp_nparams(hidden);
+    mlp_alloc(net, hidden);
+    const size_t Mx = std::max(M, 1);
+    dX = dalloc<float>(Mx * kMlpF);
+    dt = dalloc<float>(Mx);
+    dy = dalloc<float>(Mx);
+    RIHF_CUDA(cudaMemcpyAsync(net.master, params, sizeof(float) * np, cudaMemcpyHostToDevice, s));
+    if (M > 0) RIHF_CUDA(cudaMemcpyAsync(dX, X, sizeof(float) * M * kMlpF, cudaMemcpyHostToDevice, s));
+    if (t && M > 0) RIHF_CUDA(cudaMemcpyAsync(dt, t, sizeof(float) * M, cudaMemcpyHostToDevice, s));
+    RIHF_CUDA(cudaMemsetAsync(net.m, 0, sizeof(float) * np, s));
+    RIHF_CUDA(cudaMemsetAsync(net.v, 0, sizeof(float) * np, s));
+    mlp_round_weights(s, net);
+    if (y) {
+      mlp_forward(s, net, dX, M, dy);
+      if (M > 0) RIHF_CUDA(cudaMemcpyAsync(y, dy, sizeof(float) * M, cudaMemcpyDeviceToHost, s));
+    }
+    if (t) {
+      mlp_backward(s, net, dX, dt, M);
+      if (grad) RIHF_CUDA(cudaMemcpyAsync(grad, net.grad, sizeof(float) * np, cudaMemcpyDeviceToHost, s));
+      if (loss2) RIHF_CUDA(cudaMemcpyAsync(loss2, net.loss, 2 * sizeof(float), cudaMemcpyDeviceToHost, s));
+      if (params_out) {
+        for (int k = 0; k < iters; ++k) {
+          if (k > 0) mlp_backward(s, net, dX, dt, M);
+          if (losses) RIHF_CUDA(cudaMemcpyAsync(losses + k, net.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+          mlp_adam(s, net, lr);
+        }
+        RIHF_CUDA(cudaMemcpyAsync(params_out, net.master, sizeof(float) * np, cudaMemcpyDeviceToHost, s));
+      }
+    }
+    RIHF_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    release();
+    throw;
+  }
+  release();
   return RIHF_OK;
   RIHF_API_END
 }

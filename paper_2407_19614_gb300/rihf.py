@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "librihf.so")
 RIHF_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED", -5: "TIMEOUT",
           -6: "NOT_POSITIVE_DEFINITE", -7: "STATE"}
-MAT = dict(S=0, H=1, A=2, LINV=3, T3=4, B=5, J=6, K=7, F=8, D=9, GRAD_PARTS=10, SCHWARZ=11)
+MAT = dict(S=0, H=1, A=2, LINV=3, T3=4, B=5, J=6, K=7, F=8, D=9, GRAD_PARTS=10, SCHWARZ=11, DPRED=12, FEATURES=13)
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 
 
@@ -43,7 +43,8 @@ class rihf_options(ctypes.Structure):
 EXPORTS = ["rihf_default_options", "rihf_setup", "rihf_update_geometry", "rihf_scf", "rihf_gradient",
            "rihf_query", "rihf_get_matrix", "rihf_screening_stats", "rihf_timings", "rihf_strerror",
            "rihf_last_error", "rihf_destroy", "rihf_eigh", "rihf_stream", "rihf_trace", "rihf_trace_stats",
-           "rihf_scf_stats", "rihf_eigh_noalloc", "rihf_tc_dgemm"]
+           "rihf_scf_stats", "rihf_eigh_noalloc", "rihf_tc_dgemm", "rihf_learn_config", "rihf_learn_stats",
+           "rihf_mlp_eval", "rihf_learn_params"]
 
 _lib = None
 
@@ -86,6 +87,14 @@ def load(path: str = LIB_PATH):
     lib.rihf_eigh.restype = I
     lib.rihf_tc_dgemm.argtypes = [I, I, I, P, P, P, I, I, I]
     lib.rihf_tc_dgemm.restype = I
+    lib.rihf_learn_config.argtypes = [P, I, I, I, D, ctypes.c_ulonglong]
+    lib.rihf_learn_config.restype = I
+    lib.rihf_learn_stats.argtypes = [P, P, P, P, P]
+    lib.rihf_learn_stats.restype = I
+    lib.rihf_mlp_eval.argtypes = [I, I, P, P, P, ctypes.c_float, I, P, P, P, P, P, I]
+    lib.rihf_mlp_eval.restype = I
+    lib.rihf_learn_params.argtypes = [P, P]
+    lib.rihf_learn_params.restype = I
     lib.rihf_destroy.argtypes = [P]
     lib.rihf_destroy.restype = None
     for name in ("rihf_setup", "rihf_update_geometry", "rihf_scf", "rihf_gradient", "rihf_query",
@@ -149,6 +158,38 @@ def tc_dgemm(A, B, digits=7, kblock=0, device=0):
     return C
 
 
+MLP_F = 12
+
+
+def mlp_nparams(hidden):
+    return hidden * MLP_F + 2 * hidden + 1
+
+
+def mlp_eval(params, X, t=None, lr=0.0, iters=1, hidden=256, device=0):
+    """The learned guess's BF16 network kernels on host arrays: returns dict with
+    y (forward) and, with targets t, grad, loss2 and (lr > 0) params after `iters`
+    Adam steps with the loss before each step in losses."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    M = X.shape[0]
+    y = np.zeros(M, dtype=np.float32)
+    out = dict(y=y)
+    tt = grad = loss2 = pout = losses = None
+    if t is not None:
+        tt = np.ascontiguousarray(t, dtype=np.float32)
+        grad = np.zeros_like(p)
+        loss2 = np.zeros(2, dtype=np.float32)
+        out.update(grad=grad, loss2=loss2)
+        if lr > 0:
+            pout = np.zeros_like(p)
+            losses = np.zeros(int(iters), dtype=np.float32)
+            out["params"] = pout
+            out["losses"] = losses
+    _check(load().rihf_mlp_eval(int(hidden), M, _p(p), _p(X), _p(tt), float(lr), int(iters), _p(y), _p(grad),
+                                _p(pout), _p(loss2), _p(losses), int(device)))
+    return out
+
+
 def eigh_noalloc(n, A_dev, W_dev, V_dev, stream=0):
     """Allocation-free eigensolver on caller-owned DEVICE buffers (integer
     device addresses, e.g. torch.Tensor.data_ptr()); returns the status code."""
@@ -182,6 +223,23 @@ class Context:
 
     __del__ = close
 
+    def learn_config(self, hidden=256, train_steps=200, adam_iters=4, lr=1e-3, seed=0):
+        _check(self.lib.rihf_learn_config(self.h, int(hidden), int(train_steps), int(adam_iters), float(lr),
+                                          int(seed)))
+        self._hidden = int(hidden)
+
+    def learn_stats(self):
+        n, g = ctypes.c_int(), ctypes.c_int()
+        r, sc = ctypes.c_double(), ctypes.c_double()
+        self.lib.rihf_learn_stats(self.h, ctypes.byref(n), ctypes.byref(r), ctypes.byref(g), ctypes.byref(sc))
+        return dict(trained_steps=n.value, last_ratio=r.value, last_guess=g.value, scale=sc.value)
+
+    def learn_params(self, hidden=None):
+        n = mlp_nparams(hidden or self._hidden)
+        out = np.zeros(n, dtype=np.float32)
+        _check(self.lib.rihf_learn_params(self.h, _p(out)))
+        return out
+
     def update_geometry(self, xyz):
         x = np.ascontiguousarray(xyz, dtype=np.float64)
         _check(self.lib.rihf_update_geometry(self.h, _p(x)))
@@ -207,7 +265,7 @@ class Context:
         N, NA = self.N, self.Naux
         shapes = dict(S=(N, N), H=(N, N), J=(N, N), K=(N, N), F=(N, N), D=(N, N), A=(NA, NA), LINV=(NA, NA),
                       T3=(NA, N, N), B=(NA, N, N), GRAD_PARTS=(5, self.natoms, 3),
-                      SCHWARZ=(self.screening_stats()[1],))
+                      SCHWARZ=(self.screening_stats()[1],), DPRED=(N, N), FEATURES=(N * (N + 1) // 2, MLP_F))
         out = np.zeros(shapes[name])
         _check(self.lib.rihf_get_matrix(self.h, MAT[name], _p(out)))
         return out
