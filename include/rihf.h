@@ -68,13 +68,15 @@ typedef struct {
   int mixed_digits;     /* mixed precision: BF16 digits of the tensor-core RI-K (1..7);   */
                         /* 0 = ladder 5 -> 6 -> 7 digits as max|e| falls                 */
   int device;           /* CUDA device ordinal                                             */
+  int cuda_graphs;      /* 1: each SCF iteration's Fock build and DIIS error are captured  */
+                        /* once per precision variant and replayed as a CUDA graph        */
 } rihf_options;
 
 /* Fills *opt with the defaults: FP64, spherical, schwarz_tau 0 (no pair
    dropped; with ill-conditioned auxiliary metrics even pairs below 1e-14 move
    the energy by ~1e-6 Eh, see the screening tests), lindep_tau
    1e-8, conv_e 1e-10, conv_diis 1e-9, max_iter 100, diis_size 8,
-   mixed_digits 0, device 0.
+   mixed_digits 0, device 0, cuda_graphs 1.
    Mixed precision (RIHF_PRECISION_MIXED): RI-K in the SCF iterations runs on
    the tensor cores from BF16 digit planes (see rihf_tc_dgemm); RI-J, D, DIIS,
    the diagonalisation and the gradient stay FP64; convergence is declared only
@@ -138,6 +140,20 @@ int rihf_scf(rihf_ctx* ctx, int guess, const double* C_guess, double* energy, do
  * Errors: STATE if no converged SCF is available.
  */
 int rihf_gradient(rihf_ctx* ctx, double* grad);
+
+/*
+ * One AIMD step for a batch of independent molecules (contexts of any sizes):
+ * for each i, rihf_update_geometry(ctx[i], xyz[i]) when xyz and xyz[i] are
+ * non-NULL, rihf_scf(ctx[i], guess) and rihf_gradient(ctx[i]).  The molecules
+ * run concurrently, each on its context's stream, driven by nthreads host
+ * threads (0: one per hardware thread, at most nmol), so kernels of small
+ * molecules overlap on the GPU.  Outputs (each may be NULL): energies[nmol],
+ * grads = the molecules' natoms_i x 3 gradients concatenated in order,
+ * iters[nmol].  Contexts must be distinct.  Returns the first error of the
+ * batch (rihf_last_error names the molecule) or RIHF_OK.
+ */
+int rihf_batch_step(int nmol, rihf_ctx* const* ctx, const double* const* xyz, int guess, double* energies,
+                    double* grads, int* iters, int nthreads);
 
 /* Sizes of the context: primary functions N, auxiliary functions Naux,
    occupied orbitals nocc, atoms natoms.  Any pointer may be NULL. */

@@ -32,6 +32,11 @@ struct RihfError : std::runtime_error {
 
 #define RIHF_LAUNCH_CHECK() RIHF_CUDA(cudaGetLastError())
 
+// Raise (never lower) a kernel's dynamic shared-memory limit.  The attribute
+// is process-wide, so contexts driven from several host threads must not set
+// it back below a size another thread is about to launch with; serialised.
+void raise_smem_limit(const void* kernel, int bytes);
+
 __host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 __host__ __device__ constexpr int nsph(int l) { return 2 * l + 1; }
 // Number of Cartesian components of all shells 0..l-1 (offset of shell l in a

@@ -495,7 +495,7 @@ void launch_grad_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShe
   for (int g = 0; g < ngroups; ++g) {
     if (groups[g].ntask == 0) continue;
     int smem = groups[g].smem_grad;
-    RIHF_CUDA(cudaFuncSetAttribute(grad_eri3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    raise_smem_limit((const void*)grad_eri3_kernel, smem);
     RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
     grad_eri3_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks,
                                                                    groups[g].ntask, ic.boys, ic.counter, Y, grad);
@@ -506,7 +506,7 @@ void launch_grad_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShe
 
 void launch_grad_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, const double* Z, double* grad) {
   int smem = deriv_smem(max_la, 0, max_la);
-  RIHF_CUDA(cudaFuncSetAttribute(grad_eri2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  raise_smem_limit((const void*)grad_eri2_kernel, smem);
   RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
   grad_eri2_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(aux, ic.boys, ic.counter, Z, grad);
   RIHF_LAUNCH_CHECK();
@@ -517,7 +517,7 @@ void launch_grad_one_electron(const IntegralCtx& ic, const DevShells& prim, int 
                               const double* axyz, const double* D, const double* W, double* grad_one,
                               double* grad_ovl) {
   int smem = deriv_smem(max_lp, max_lp, 0) + (128 + 3 * 64) * (int)sizeof(double);
-  RIHF_CUDA(cudaFuncSetAttribute(grad_one_electron_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  raise_smem_limit((const void*)grad_one_electron_kernel, smem);
   RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
   grad_one_electron_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, natoms, Z, axyz, ic.boys, ic.counter,
                                                                          D, W, grad_one, grad_ovl);

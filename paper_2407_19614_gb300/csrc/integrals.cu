@@ -605,7 +605,7 @@ static int grid_for(int smem_bytes) {
 }
 
 static void set_smem(const void* fn, int bytes) {
-  RIHF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  raise_smem_limit(fn, bytes);
 }
 
 void launch_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
@@ -670,6 +670,96 @@ void launch_pair_prims(const IntegralCtx& ic, const DevShells& prim, const Shell
   pair_prim_kernel<<<(npairs + 127) / 128, 128, 0, ic.stream>>>(prim, pairs, npairs, off, pp);
   RIHF_LAUNCH_CHECK();
   if (ic.launches) *ic.launches += 1;
+}
+
+// ------------------------------------------------------------ flop model
+
+namespace {
+
+double vrr_flops(int L) {
+  double f = 3.0 * (L + 1);   // prefactor and the k/(2p), k/(2q) tables
+  for (int e = 1; e <= L; ++e)
+    for (int k = 0; k < ncart(e); ++k) {
+      int lx, ly, lz;
+      cart_decode(e, k, lx, ly, lz);
+      int c[3] = {lx, ly, lz};
+      const int i = lx > 0 ? 0 : (ly > 0 ? 1 : 2);
+      c[i] -= 1;
+      f += (L - e + 1) * (3.0 + (c[i] > 0 ? 4.0 : 0.0));
+    }
+  return f;
+}
+
+double etr_flops(const EtrShape& sh) {
+  double f = 0.0;
+  for (int c = 1; c <= sh.lc; ++c)
+    for (int e = sh.elo(c); e <= sh.ehi(c); ++e)
+      for (int ke = 0; ke < ncart(e); ++ke)
+        for (int kc = 0; kc < ncart(c); ++kc) {
+          int ex, ey, ez, cx, cy, cz;
+          cart_decode(e, ke, ex, ey, ez);
+          cart_decode(c, kc, cx, cy, cz);
+          const int i = cx > 0 ? 0 : (cy > 0 ? 1 : 2);
+          const int eo[3] = {ex, ey, ez};
+          int cl[3] = {cx, cy, cz};
+          cl[i] -= 1;
+          f += 3.0 + (eo[i] > 0 ? 2.0 : 0.0) + (cl[i] > 0 ? 2.0 : 0.0);
+        }
+  return f;
+}
+
+double hrr_flops(int la, int lb, int lc) {
+  double f = 0.0;
+  for (int b = 1; b <= lb; ++b)
+    f += 2.0 * (cart_offset(la + lb - b + 1) - cart_offset(la)) * ncart(b) * ncart(lc);
+  return f;
+}
+
+}  // namespace
+
+void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim, const std::vector<int>& nprim,
+                const std::vector<int>& patom, const std::vector<int>& laux, const std::vector<int>& naux_prim,
+                const std::vector<int>& aatom, const std::vector<int>& nf, double* eri3, double* grad3) {
+  constexpr int nl = kMaxLPrim + 1, nc = kMaxLAux + 1;
+  double e_prim[nl][nl][nc], e_task[nl][nl][nc], g_prim[nl][nl][nc], g_task[nl][nl][nc];
+  for (int la = 0; la < nl; ++la)
+    for (int lb = 0; lb <= la; ++lb)
+      for (int lc = 0; lc < nc; ++lc) {
+        const int na = ncart(la), nb = ncart(lb), ncc = ncart(lc);
+        const int fa = nf[la], fb = nf[lb], fc = nf[lc];
+        const double setup = 25.0;
+        {
+          const int L = la + lb + lc;
+          e_prim[la][lb][lc] = setup + 14.0 * (L + 1) + vrr_flops(L) + etr_flops(EtrShape{lc, la, la + lb}) +
+                               2.0 * acc_size(la, la + lb, lc);
+          e_task[la][lb][lc] = hrr_flops(la, lb, lc) +
+                               2.0 * ((double)na * nb * fc * ncc + (double)na * fb * fc * nb + (double)fa * fb * fc * na);
+        }
+        {
+          const int emin = la > 0 ? la - 1 : 0, emax = la + lb + 1, L = emax + lc;
+          g_prim[la][lb][lc] = setup + 14.0 * (L + 1) + vrr_flops(L) + etr_flops(EtrShape{lc, emin, emax}) +
+                               6.0 * acc_size(emin, emax, lc);
+          g_task[la][lb][lc] = 2.0 * ((double)fa * fb * ncc * fc + (double)fa * nb * ncc * fb + (double)na * nb * ncc * fa) +
+                               hrr_flops(la + 1, lb, lc) + (la > 0 ? hrr_flops(la - 1, lb, lc) : 0.0) +
+                               hrr_flops(la, lb + 1, lc) + (lb > 0 ? hrr_flops(la, lb - 1, lc) : 0.0) +
+                               24.0 * na * nb * ncc;
+        }
+      }
+  double fe = 0.0, fg = 0.0;
+  for (const ShellPair& sp : pairs) {
+    int a = sp.a, b = sp.b;
+    if (lprim[a] < lprim[b]) std::swap(a, b);
+    const int la = lprim[a], lb = lprim[b];
+    const double npab = (double)nprim[a] * nprim[b];
+    for (int c = 0; c < (int)laux.size(); ++c) {
+      const int lc = laux[c];
+      const double np3 = npab * naux_prim[c];
+      fe += np3 * e_prim[la][lb][lc] + e_task[la][lb][lc];
+      if (!(patom[a] == patom[b] && patom[b] == aatom[c])) fg += np3 * g_prim[la][lb][lc] + g_task[la][lb][lc];
+    }
+  }
+  *eri3 = fe;
+  *grad3 = fg;
 }
 
 // Class-grouped task lists: every (pair, auxiliary shell) task goes to the first

@@ -68,6 +68,17 @@ void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<in
                        const std::vector<int>& laux, std::vector<std::vector<int2>>& tasks,
                        std::vector<int>& smem_eri3, std::vector<int>& smem_grad);
 
+// Algorithmic FP64 operation counts (an FMA counts two) of the 3-centre
+// integral and derivative kernels over all (pair, auxiliary shell) tasks, from
+// the loop structure of their recursions: per primitive triple the setup, Boys
+// Taylor steps, vertical recurrence, electron transfer and accumulation(s); per
+// task the horizontal recurrence(s), the spherical transforms and, for the
+// gradient, the back-transform of Y and the contraction.  One-centre triples
+// are skipped by the derivative kernel and not counted.
+void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim, const std::vector<int>& nprim,
+                const std::vector<int>& patom, const std::vector<int>& laux, const std::vector<int>& naux_prim,
+                const std::vector<int>& aatom, const std::vector<int>& nf, double* eri3, double* grad3);
+
 // Three-centre integrals T[P][mu][nu] = (mu nu|P) for the listed shell pairs
 // (mu in a, nu in b, a >= b; both triangles inside diagonal shell blocks).
 void launch_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,

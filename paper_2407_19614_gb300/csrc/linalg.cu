@@ -4,6 +4,26 @@
 
 #include "linalg.cuh"
 
+#include <mutex>
+#include <unordered_map>
+
+namespace rihf {
+
+void raise_smem_limit(const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cur;
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = 0;
+  RIHF_CUDA(cudaGetDevice(&dev));
+  const void* key = (const void*)((const char*)kernel + dev);   // per device
+  auto it = cur.find(key);
+  if (it != cur.end() && it->second >= bytes) return;
+  RIHF_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  cur[key] = bytes;
+}
+
+}  // namespace rihf
+
 namespace rihf {
 
 static inline void count(const LaCtx& la, int n = 1) {
@@ -918,7 +938,7 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
   size_t smem = (size_t)n * n * sizeof(float);
   int use_smem = smem <= 215 * 1024 ? 1 : 0;
   if (use_smem)
-    RIHF_CUDA(cudaFuncSetAttribute(jacobi1s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    raise_smem_limit((const void*)jacobi1s_kernel, (int)smem);
   // a looser stop (n eps) leaves close clusters too coarse for the FP64
   // refinement to separate
   const float tol = 2e-6f;

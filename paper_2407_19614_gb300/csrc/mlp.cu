@@ -289,7 +289,7 @@ void mlp_forward(cudaStream_t s, const MlpDev& net, const float* X, int M, float
   check_h(net.H);
   if (M <= 0) return;
   const size_t smem = tile_smem(net.H);
-  if (smem > 48 * 1024) RIHF_CUDA(cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 48 * 1024) raise_smem_limit((const void*)mlp_fwd_kernel, (int)smem);
   const int tiles = (M + kTE - 1) / kTE;
   mlp_fwd_kernel<<<std::min(tiles, 1024), net.H, smem, s>>>(net.wbf, net.H, X, M, y);
   RIHF_LAUNCH_CHECK();
@@ -301,7 +301,7 @@ void mlp_backward(cudaStream_t s, const MlpDev& net, const float* X, const float
   RIHF_CUDA(cudaMemsetAsync(net.loss, 0, 2 * sizeof(float), s));
   if (M <= 0) return;
   const size_t smem = tile_smem(net.H);
-  if (smem > 48 * 1024) RIHF_CUDA(cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 48 * 1024) raise_smem_limit((const void*)mlp_bwd_kernel, (int)smem);
   const int tiles = (M + kTE - 1) / kTE;
   mlp_bwd_kernel<<<std::min(tiles, 304), net.H, smem, s>>>(net.wbf, net.H, X, t, M, net.grad, net.loss);
   RIHF_LAUNCH_CHECK();

@@ -62,7 +62,7 @@ __device__ inline double boys_eval(int m, double T, const double* __restrict__ t
 }
 
 // Decode component k of a Cartesian shell of angular momentum l.
-__device__ inline void cart_decode(int l, int k, int& lx, int& ly, int& lz) {
+__host__ __device__ inline void cart_decode(int l, int k, int& lx, int& ly, int& lz) {
   int a = 0;
   while ((a + 1) * (a + 2) / 2 <= k) ++a;
   lx = l - a;

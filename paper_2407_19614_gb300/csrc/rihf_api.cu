@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/rihf.h"
@@ -294,8 +295,11 @@ __global__ void eig_check_kernel(const double* __restrict__ A, int n, double sub
 }
 
 // E = 1/2 sum D (h + F) + Vnn written to out[0]; out[1] untouched.
+// vnn is read from device memory (out[5]) so that captured CUDA graphs stay
+// valid when the geometry changes.
 __global__ void energy_kernel(const double* __restrict__ D, const double* __restrict__ h,
-                              const double* __restrict__ F, long long n2, double vnn, double* out) {
+                              const double* __restrict__ F, long long n2, double* out) {
+  const double vnn = out[5];
   __shared__ double red[32];
   double s = 0.0;
   for (long long i = threadIdx.x; i < n2; i += blockDim.x) s += D[i] * (h[i] + F[i]);
@@ -451,6 +455,15 @@ struct rihf_ctx {
   int *Bex = nullptr, *Cex = nullptr, *Hex = nullptr;
   OzOperand Bop;
   int tc_builds = 0, last_iters = 0, last_digits = 0;
+  double flops_eri3 = 0.0, flops_grad3 = 0.0;   // algorithmic FP64 operations of the 3-centre kernels
+  int k_nsplit = 0;             // K splits of the tensor-core K GEMM (0: not tuned yet)
+  // per-iteration CUDA graphs (Fock build + DIIS error), one per variant:
+  // [0] FP64 build, [d] tensor-core build with d digits
+  struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+  } graphs[kOzMaxDigits + 1];
+  bool graphs_ok = true;
 
   // learned / extrapolated guess: the last three converged densities, the
   // overlap and nuclear positions of the last geometry, features of the
@@ -529,12 +542,13 @@ struct rihf_ctx {
   }
 };
 
-static std::vector<double>& boys_host() {
-  static std::vector<double> tab;
-  if (tab.empty()) {
-    tab.resize((size_t)kBoysN * kBoysM);
-    boys_table_host(tab.data());
-  }
+static const std::vector<double>& boys_host() {
+  // built once, thread-safely (function-local static initialisation)
+  static const std::vector<double> tab = [] {
+    std::vector<double> t((size_t)kBoysN * kBoysM);
+    boys_table_host(t.data());
+    return t;
+  }();
   return tab;
 }
 
@@ -544,6 +558,8 @@ static void refresh_tasks(rihf_ctx* c) {
   std::vector<std::vector<int2>> tasks;
   std::vector<int> se, sg;
   build_task_groups(c->pairs_h, c->hp.l, c->ha.l, tasks, se, sg);
+  task_flops(c->pairs_h, c->hp.l, c->hp.nprim, c->hp.atom, c->ha.l, c->ha.nprim, c->ha.atom, c->nf_h, &c->flops_eri3,
+             &c->flops_grad3);
   size_t off = 0;
   for (int g = 0; g < kTaskGroups; ++g) {
     c->groups[g].tasks = c->d_tasks + off;
@@ -594,6 +610,7 @@ static void compute_geometry(rihf_ctx* c) {
       for (int d = 0; d < 3; ++d) r2 += (c->xyz[3 * a + d] - c->xyz[3 * b + d]) * (c->xyz[3 * a + d] - c->xyz[3 * b + d]);
       c->vnn += c->Z[a] * c->Z[b] / std::sqrt(r2);
     }
+  RIHF_CUDA(cudaMemcpyAsync(c->scal + 5, &c->vnn, sizeof(double), cudaMemcpyHostToDevice, s));
   RIHF_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
   cudaEventRecord(c->ev[0], s);
   DevShells P = c->prim(), X = c->aux();
@@ -636,7 +653,7 @@ static void compute_geometry(rihf_ctx* c) {
   // by blocked forward substitution on the lower-triangle columns; an explicit
   // L^{-1} product loses accuracy when cond(A) reaches 1e9 (diffuse auxiliary sets)
   RIHF_CUDA(cudaMemsetAsync(c->T3, 0, sizeof(double) * (size_t)NA * N * N, s));
-  { TraceScope t(c->tracer, s, "eri3_kernel (mu nu|P)", (double)NA * N * (N + 1) / 2 * 8, 1);
+  { TraceScope t(c->tracer, s, "eri3_kernel (mu nu|P)", c->flops_eri3, 0);
     launch_pair_prims(ic, P, c->d_pairs, c->npairs, c->d_pp_off, c->d_pp);
     launch_eri3(ic, P, X, c->d_pairs, c->ptab(), c->groups, kTaskGroups, c->T3); }
   RIHF_CUDA(cudaMemcpyAsync(c->B, c->T3, sizeof(double) * (size_t)NA * N * N, cudaMemcpyDeviceToDevice, s));
@@ -682,7 +699,14 @@ static void compute_geometry(rihf_ctx* c) {
     if (k0 == N) throw RihfError(RIHF_ERR_NOT_POSITIVE_DEFINITE, "overlap matrix has no eigenvalue above lindep_tau");
   }
   int nind = N - k0;
-  if (c->nind != 0 && nind != c->nind) c->have_cprev = false;
+  if (c->nind != 0 && nind != c->nind) {
+    c->have_cprev = false;
+    for (auto& g : c->graphs)   // captured iterations assume the old basis size
+      if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+      }
+  }
   c->nind = nind;
   if (chol_ok) {
     transpose(la, c->T1, N, N, c->Xo);
@@ -743,6 +767,7 @@ void rihf_default_options(rihf_options* o) {
   o->diis_size = 8;
   o->mixed_digits = 0;
   o->device = 0;
+  o->cuda_graphs = 1;
 }
 
 const char* rihf_strerror(int code) {
@@ -1038,7 +1063,7 @@ static void fock_build(rihf_ctx* c) {
     dgemm(la, gk);
     symmetrize_lower(la, c->K, N, 1); }
   add3(la, (int)n2, c->H, c->J, c->K, c->F);
-  energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->vnn, c->scal);
+  energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->scal);
   RIHF_LAUNCH_CHECK();
   c->launches += 1;
 }
@@ -1047,6 +1072,51 @@ static void fock_build(rihf_ctx* c) {
 // RI-K (Eqs. k_ri_2, tp) on the tensor cores from `digits` BF16 digit planes:
 // H = B C~ with B's planes cut once per geometry, then K = -1/2 sum_P H^P H^P^T
 // with H cut per K block (one block per split of the long (P, i) axis).
+// Autotuner of the tensor-core K GEMM: the number of splits of the long (P, i)
+// axis (one CTA per lower tile and split; at most 30 chunks per split) is timed
+// for a few candidates around one wave of CTAs on the first build (H is
+// already formed), and the fastest is kept for the context.
+static int tune_k_splits(rihf_ctx* c, int digits, int kch, int lower_tiles) {
+  LaCtx la = c->la();
+  const int N = c->N, NA = c->NA, no = c->nocc;
+  const int lo = (kch + 29) / 30;
+  const int wave = std::max(1, c->sms / std::max(1, lower_tiles));
+  std::vector<int> cand;
+  for (int k : {wave / 2, wave, 2 * wave, 4 * wave}) {
+    const int v = std::min(std::max(k, lo), kch);
+    if (std::find(cand.begin(), cand.end(), v) == cand.end()) cand.push_back(v);
+  }
+  int best = cand[0];
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  RIHF_CUDA(cudaEventCreate(&e0));
+  RIHF_CUDA(cudaEventCreate(&e1));
+  for (int ns : cand) {
+    const int kbc = (kch + ns - 1) / ns;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {   // the first pass warms up
+      RIHF_CUDA(cudaEventRecord(e0, c->stream));
+      OzOperand Hop = oz_slice(la, c->Hb, N, NA * no, no, 1, (long long)N * no, no, digits, kbc, c->Hpl, c->Hex);
+      RIHF_CUDA(cudaMemsetAsync(c->K, 0, sizeof(double) * N * N, c->stream));
+      OzGemmArgs g2;
+      g2.A = Hop; g2.B = Hop; g2.M = N; g2.N = N; g2.s = digits; g2.alpha = -0.5; g2.C = c->K; g2.cs_m1 = N;
+      g2.cs_n = 1; g2.atomic = true; g2.lower_only = true;
+      oz_gemm(la, g2);
+      RIHF_CUDA(cudaEventRecord(e1, c->stream));
+      RIHF_CUDA(cudaEventSynchronize(e1));
+      RIHF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = ns;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (c->verbose || getenv("RIHF_VERBOSE")) fprintf(stderr, "rihf: K GEMM splits %d (%.3f ms)\n", best, best_ms);
+  return best;
+}
+
 static void fock_build_tc(rihf_ctx* c, int digits) {
   LaCtx la = c->la();
   const int N = c->N, NA = c->NA, no = c->nocc;
@@ -1076,8 +1146,8 @@ static void fock_build_tc(rihf_ctx* c, int digits) {
   for (int mt = 0; mt * kOzTileM < N; ++mt)
     for (int nt = 0; nt * TN < N; ++nt)
       if (mt * kOzTileM + kOzTileM - 1 >= nt * TN) ++lower_tiles;
-  const int nsplit = std::max((kch + 29) / 30, std::max(1, c->sms / std::max(1, lower_tiles)));
-  const int kbc = (kch + nsplit - 1) / nsplit;
+  if (c->k_nsplit <= 0) c->k_nsplit = tune_k_splits(c, digits, kch, lower_tiles);
+  const int kbc = (kch + c->k_nsplit - 1) / c->k_nsplit;
   OzOperand Hop;
   { TraceScope t(c->tracer, c->stream, "RI-K H digit planes (oz_slice)", (double)NA * N * no * (8 + 2 * digits), 1);
     Hop = oz_slice(la, c->Hb, N, NA * no, no, 1, (long long)N * no, no, digits, kbc, c->Hpl, c->Hex); }
@@ -1090,7 +1160,7 @@ static void fock_build_tc(rihf_ctx* c, int digits) {
     oz_gemm(la, g2);
     symmetrize_lower(la, c->K, N, 1); }
   add3(la, (int)n2, c->H, c->J, c->K, c->F);
-  energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->vnn, c->scal);
+  energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->scal);
   RIHF_LAUNCH_CHECK();
   c->launches += 1;
 }
@@ -1168,6 +1238,54 @@ static void learn_and_push_history(rihf_ctx* c) {
   std::swap(c->hist_xyz[1], c->hist_xyz[0]);
   RIHF_CUDA(cudaMemcpyAsync(c->hist_xyz[0], c->d_xyz, sizeof(double) * 3 * c->natoms, cudaMemcpyDeviceToDevice, s));
   c->nhist = std::min(c->nhist + 1, 3);
+}
+
+// One SCF iteration's Fock build (variant 0: FP64, d: tensor-core RI-K with d
+// digits) and DIIS error, replayed from a CUDA graph captured on first use
+// (launch overhead matters for small molecules in batches).  The captured
+// work reads and writes only the context's fixed buffers; the autotuner runs
+// eagerly before the first capture of a tensor-core variant.
+static void fock_and_error(rihf_ctx* c, int variant) {
+  auto eager = [&]() {
+    if (variant == 0) fock_build(c);
+    else fock_build_tc(c, variant);
+    diis_error(c);
+  };
+  if (!c->opt.cuda_graphs || !c->graphs_ok || c->tracer.on || (variant > 0 && c->k_nsplit <= 0)) {
+    eager();
+    return;
+  }
+  auto& g = c->graphs[variant];
+  if (!g.exec) {
+    const long long l0 = c->launches;
+    RIHF_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t graph = nullptr;
+    try {
+      eager();
+    } catch (...) {
+      cudaStreamEndCapture(c->stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      c->launches = l0;
+      c->graphs_ok = false;
+      eager();
+      return;
+    }
+    RIHF_CUDA(cudaStreamEndCapture(c->stream, &graph));
+    const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    g.launches = c->launches - l0;
+    c->launches = l0;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g.exec = nullptr;
+      c->graphs_ok = false;
+      eager();
+      return;
+    }
+  }
+  RIHF_CUDA(cudaGraphLaunch(g.exec, c->stream));
+  c->launches += g.launches;
 }
 
 int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, double* Dout, double* Cout,
@@ -1293,18 +1411,16 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   for (it = 1; it <= c->opt.max_iter; ++it) {
     cudaEventRecord(c->ev[2], s);
     const bool full = fp64_next;
-    if (full) {
-      fock_build(c);
-    } else {
+    int variant = 0;
+    if (!full) {
       int digits = c->opt.mixed_digits;
       if (digits <= 0) digits = emax_prev > 1e-2 ? 5 : emax_prev > 1e-5 ? 6 : 7;
-      digits = std::min(digits, kOzMaxDigits);
-      c->last_digits = digits;
-      fock_build_tc(c, digits);
+      variant = std::min(digits, kOzMaxDigits);
+      c->last_digits = variant;
       ++c->tc_builds;
     }
+    fock_and_error(c, variant);
     cudaEventRecord(c->ev[3], s);
-    diis_error(c);
     int slot = (it - 1) % size;
     int m = std::min(it, size);
     RIHF_CUDA(cudaMemcpyAsync(c->Fring + slot * n2, c->F, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
@@ -1455,7 +1571,7 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   double* g_two = c->grad_parts + 9 * nat;
   { TraceScope t(c->tracer, s, "grad_one_electron_kernel", 0.0, 0);
     launch_grad_one_electron(ic, c->prim(), c->max_lp, nat, c->d_Z, c->d_xyz, c->D, c->W, g_one, g_ovl); }
-  { TraceScope t(c->tracer, s, "grad_eri3_kernel (fused d(mu nu|P) . Y)", (double)NA * N * (N + 1) / 2 * 8, 1);
+  { TraceScope t(c->tracer, s, "grad_eri3_kernel (fused d(mu nu|P) . Y)", c->flops_grad3, 0);
     launch_grad_eri3(ic, c->prim(), c->aux(), c->d_pairs, c->ptab(), c->groups, kTaskGroups, c->Y, g_three); }
   { TraceScope t(c->tracer, s, "grad_eri2_kernel (fused d(P|Q) . Z)", (double)NA * NA * 8, 1);
     launch_grad_eri2(ic, c->aux(), c->max_la, c->Zm, g_two); }
@@ -1634,6 +1750,52 @@ int rihf_learn_stats(rihf_ctx* c, int* trained_steps, double* last_ratio, int* l
   if (last_ratio) *last_ratio = c->ml_last_ratio;
   if (last_guess) *last_guess = c->last_guess;
   if (scale) *scale = c->ml_scale;
+  return RIHF_OK;
+}
+
+int rihf_batch_step(int nmol, rihf_ctx* const* ctx, const double* const* xyz, int guess, double* energies,
+                    double* grads, int* iters, int nthreads) {
+  if (nmol < 0 || (nmol > 0 && !ctx)) return RIHF_ERR_INVALID_ARG;
+  for (int i = 0; i < nmol; ++i)
+    if (!ctx[i]) return RIHF_ERR_INVALID_ARG;
+  std::vector<size_t> goff(nmol + 1, 0);
+  for (int i = 0; i < nmol; ++i) goff[i + 1] = goff[i] + 3 * (size_t)ctx[i]->natoms;
+  std::vector<int> rc(nmol, RIHF_OK);
+  std::vector<std::string> err(nmol);
+  auto work = [&](int w, int nw) {
+    for (int i = w; i < nmol; i += nw) {
+      rihf_ctx* c = ctx[i];
+      if (cudaSetDevice(c->opt.device) != cudaSuccess) {
+        rc[i] = RIHF_ERR_CUDA;
+        continue;
+      }
+      int r = RIHF_OK, it = 0;
+      double e = 0.0;
+      std::vector<double> gl;
+      double* gp = grads ? grads + goff[i] : (gl.resize(3 * (size_t)c->natoms), gl.data());
+      if (xyz && xyz[i]) r = rihf_update_geometry(c, xyz[i]);
+      if (r == RIHF_OK) r = rihf_scf(c, guess, nullptr, &e, nullptr, nullptr, nullptr, &it);
+      if (r == RIHF_OK) r = rihf_gradient(c, gp);
+      if (r != RIHF_OK) err[i] = rihf_last_error();
+      rc[i] = r;
+      if (energies) energies[i] = e;
+      if (iters) iters[i] = it;
+    }
+  };
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nw = std::max(1, std::min(nmol, nthreads > 0 ? nthreads : hw));
+  if (nw <= 1) {
+    work(0, 1);
+  } else {
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nw; ++w) pool.emplace_back(work, w, nw);
+    for (auto& t : pool) t.join();
+  }
+  for (int i = 0; i < nmol; ++i)
+    if (rc[i] != RIHF_OK) {
+      g_last_error = "molecule " + std::to_string(i) + ": " + err[i];
+      return rc[i];
+    }
   return RIHF_OK;
 }
 
@@ -1848,6 +2010,8 @@ int rihf_tc_dgemm(int M, int N, int K, const double* A, const double* B, double*
 void rihf_destroy(rihf_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   free_all(c);
   for (auto& e : c->ev) cudaEventDestroy(e);
   cudaStreamDestroy(c->stream);

@@ -415,7 +415,7 @@ void oz_gemm(const LaCtx& la, const OzGemmArgs& g) {
   const int TN = g.N <= 64 ? (g.N + 15) / 16 * 16 : 64;
   if (g.s * TN > kTmemCols) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: accumulators exceed TMEM");
   const int mtiles = (g.M + kOzTileM - 1) / kOzTileM, ntiles = (g.N + TN - 1) / TN;
-  RIHF_CUDA(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  raise_smem_limit((const void*)oz_gemm_kernel, kSmemBytes);
   const long long nblocks = (long long)mtiles * ntiles * A.nkb;
   oz_gemm_kernel<<<(unsigned)nblocks, kOzThreads, kSmemBytes, la.stream>>>(
       A, B, g.M, g.N, g.s, TN, mtiles, ntiles, A.nkb, g.lower_only ? 1 : 0, g.alpha, g.C, g.MR, g.cs_m1, g.cs_m2,

@@ -37,14 +37,14 @@ class rihf_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("pure", ctypes.c_int), ("schwarz_tau", ctypes.c_double),
                 ("lindep_tau", ctypes.c_double), ("conv_e", ctypes.c_double), ("conv_diis", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("diis_size", ctypes.c_int), ("mixed_digits", ctypes.c_int),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("cuda_graphs", ctypes.c_int)]
 
 
 EXPORTS = ["rihf_default_options", "rihf_setup", "rihf_update_geometry", "rihf_scf", "rihf_gradient",
            "rihf_query", "rihf_get_matrix", "rihf_screening_stats", "rihf_timings", "rihf_strerror",
            "rihf_last_error", "rihf_destroy", "rihf_eigh", "rihf_stream", "rihf_trace", "rihf_trace_stats",
            "rihf_scf_stats", "rihf_eigh_noalloc", "rihf_tc_dgemm", "rihf_learn_config", "rihf_learn_stats",
-           "rihf_mlp_eval", "rihf_learn_params"]
+           "rihf_mlp_eval", "rihf_learn_params", "rihf_batch_step"]
 
 _lib = None
 
@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH):
     lib.rihf_mlp_eval.restype = I
     lib.rihf_learn_params.argtypes = [P, P]
     lib.rihf_learn_params.restype = I
+    lib.rihf_batch_step.argtypes = [I, P, P, I, P, P, P, I]
+    lib.rihf_batch_step.restype = I
     lib.rihf_destroy.argtypes = [P]
     lib.rihf_destroy.restype = None
     for name in ("rihf_setup", "rihf_update_geometry", "rihf_scf", "rihf_gradient", "rihf_query",
@@ -188,6 +190,33 @@ def mlp_eval(params, X, t=None, lr=0.0, iters=1, hidden=256, device=0):
     _check(load().rihf_mlp_eval(int(hidden), M, _p(p), _p(X), _p(tt), float(lr), int(iters), _p(y), _p(grad),
                                 _p(pout), _p(loss2), _p(losses), int(device)))
     return out
+
+
+def batch_step(contexts, xyz=None, guess=2, nthreads=0):
+    """One AIMD step (update geometry, SCF, gradient) for a batch of contexts,
+    run concurrently; returns energies, the per-molecule gradients and iterations."""
+    n = len(contexts)
+    hs = (ctypes.c_void_p * n)(*[c.h.value for c in contexts])
+    keep = []
+    xp = None
+    if xyz is not None:
+        arr = (ctypes.c_void_p * n)()
+        for i, x in enumerate(xyz):
+            if x is not None:
+                a = np.ascontiguousarray(x, dtype=np.float64)
+                keep.append(a)
+                arr[i] = a.ctypes.data
+        xp = arr
+    E = np.zeros(n)
+    it = np.zeros(n, dtype=np.int32)
+    sizes = [c.natoms * 3 for c in contexts]
+    G = np.zeros(sum(sizes))
+    _check(load().rihf_batch_step(n, hs, xp, int(guess), _p(E), _p(G), _p(it), int(nthreads)))
+    grads, o = [], 0
+    for c, s in zip(contexts, sizes):
+        grads.append(G[o:o + s].reshape(c.natoms, 3))
+        o += s
+    return E, grads, it
 
 
 def eigh_noalloc(n, A_dev, W_dev, V_dev, stream=0):
