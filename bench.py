@@ -215,8 +215,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "(H2O)8 RI-HF E+grad AIMD step, N=192, Naux=848, spherical, dt 0.5 fs",
-                   "precision": "fp64", "scf_iters_assumed": 12},
+        "config": {"workload": "(H2O)8 RI-HF E+grad AIMD step, N=192, Naux=848, spherical, dt 0.5 fs, "
+                               "previous-orbital guess",
+                   "precision": "fp64 (CPU oracle)", "scf_iters_assumed": 12},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncore, "kind": "oracle",
                          "sample": r["sample"] + "; per step %.1f s of CPU work" % statistics.median(samples)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -280,7 +281,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison run (mixed only)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=0,
@@ -312,64 +314,24 @@ def main():
 
     torch.cuda.set_device(local)
     R.load()
-    prec = R.PRECISION_MIXED if args.precision == "mixed" else R.PRECISION_FP64
-    mol = W.water8(rank)
-    ctx = R.Context(mol, precision=prec, device=local, **CONV)
-    traj = Trajectory(ctx, mol, rank, R)
-    stream = torch.cuda.ExternalStream(ctx.stream(), device=local)
-    for _ in range(max(args.warmup, 0)):
-        traj.step()
-
-    # ---- timed region 1: device time (CUDA events on the library stream)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    launches0 = ctx.timings()["launches"]
-    it0 = len(traj.iters)
-    Etot0 = traj.total_energy()
-    ctx.trace(True)
-    barrier(pg)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            traj.step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-    barrier(pg)
-    ms = e0.elapsed_time(e1)
-    ms_max = allreduce_max(pg, ms, local)
-    launches = ctx.timings()["launches"] - launches0
-    stats = ctx.trace_stats()
-    ctx.trace(False)
-    iters = traj.iters[it0:]
-    Etot1 = traj.total_energy()
-
-    # ---- timed region 2: end to end through the public API, host buffers
-    xyz_pinned = torch.empty(mol.natoms * 3, dtype=torch.float64, pin_memory=True).numpy()
-    barrier(pg)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        a = -traj.g / traj.m
-        traj.x = traj.x + traj.v * traj.dt + 0.5 * a * traj.dt ** 2
-        xyz_pinned[:] = traj.x.reshape(-1)
-        ctx.update_geometry(xyz_pinned.reshape(-1, 3))
-        out = ctx.scf(guess=2, outputs=False)
-        g_new = ctx.gradient()
-        traj.v = traj.v + 0.5 * (a - g_new / traj.m) * traj.dt
-        traj.g, traj.E = g_new, out["energy"]
-    torch.cuda.synchronize()
-    e2e_s = allreduce_max(pg, time.perf_counter() - t0, local)
-    barrier(pg)
-
+    main_prec = args.precision
+    res = measure_path(R, W, torch, main_prec, args, rank, local, pg, trace=True)
+    cmp = None
+    if main_prec == "mixed" and not args.no_compare:
+        # the FP64 path on the same trajectory: its throughput, and the largest
+        # per-step energy difference of the two paths (the |dE| of the metric)
+        cmp = measure_path(R, W, torch, "fp64", args, rank, local, pg, trace=False)
     if rank != 0:
         return 0
-    value = world * args.steps / (ms_max / 1e3)
+    world = res["world"]
+    value = world * args.steps / (res["ms_max"] / 1e3)
+    stats = res["stats"]
     pk, pk_src = peaks()
     roof = None
-    if stats:
-        dom = max(stats, key=lambda s: s["ms"])
-        timed = [s for s in stats if s["work"] > 0]
+    kernels = [s for s in stats if not s["name"].startswith("SCF iteration graph")]
+    if kernels:
+        dom = max(kernels, key=lambda s: s["ms"])
+        timed = [s for s in kernels if s["work"] > 0]
         roof_k = dom if dom["work"] > 0 else max(timed, key=lambda s: s["ms"])
         per_launch_s = roof_k["ms"] / roof_k["launches"] / 1e3
         work = roof_k["work"] / roof_k["launches"]
@@ -398,32 +360,100 @@ def main():
                 "dominant_kernel": dom["name"], "dominant_share": dom["ms"] / sum(s["ms"] for s in stats)}
     cpu = None
     if not args.no_cpu_baseline:
-        r = cpu_oracle_sample(float(np.mean(iters)))
+        r = cpu_oracle_sample(float(np.mean(res["iters"])))
         cpu = {"value": 1.0 / r["step_s"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": r["sample"]}
-    grad_bytes = mol.natoms * 3 * 8
+    grad_bytes = res["natoms"] * 3 * 8
+    config = {"workload": "(H2O)8 RI-HF E+grad AIMD step, N=192, Naux=848, spherical, dt 0.5 fs, "
+                          "previous-orbital guess",
+              "precision": main_prec, "parallelism": "replicas" if world > 1 else "1 GPU",
+              "l2": "inputs larger than L2 (B = 250 MB)", "scf_conv": CONV,
+              "scf_iters_avg": float(np.mean(res["iters"])), "energy_drift_eh": res["drift"],
+              "kernel_times": "CUDA events per launch on the library stream during the timed steps; SCF "
+                              "iterations replay as CUDA graphs and are timed as a unit"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "bf16 digit planes (RI-K) + f64", "data": "synthetic",
-        "config": {"workload": "(H2O)8 RI-HF E+grad AIMD step, N=192, Naux=848, spherical, dt 0.5 fs, "
-                               "previous-orbital guess",
-                   "precision": args.precision, "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "l2": "inputs larger than L2 (B = 250 MB)", "scf_conv": CONV,
-                   "scf_iters_avg": float(np.mean(iters)),
-                   "energy_drift_eh": Etot1 - Etot0},
+        "ms_per_step": res["ms_max"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if main_prec == "fp64" else "bf16 digit planes (RI-K) + f64", "data": "synthetic",
+        "config": config,
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": grad_bytes,
-                "d2h_bytes_per_step": grad_bytes + 8 + int(np.mean(iters)) * 16},
-        "clocks": clk.summary(),
-        "gpu_launches": int(launches),
+        "e2e": {"value": world * args.steps / res["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": grad_bytes,
+                "d2h_bytes_per_step": grad_bytes + 8 + int(np.mean(res["iters"])) * 16},
+        "clocks": res["clocks"],
+        "gpu_launches": int(res["launches"]),
         "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()} for s in
                     sorted(stats, key=lambda s: -s["ms"])],
     }
+    if cmp is not None:
+        dE = float(np.max(np.abs(np.array(res["energies"]) - np.array(cmp["energies"]))))
+        line["fp64_path"] = {"value": world * args.steps / (cmp["ms_max"] / 1e3), "unit": UNIT,
+                             "ms_per_step": cmp["ms_max"] / args.steps,
+                             "scf_iters_avg": float(np.mean(cmp["iters"])),
+                             "gpu_launches": int(cmp["launches"])}
+        config["max_abs_dE_vs_fp64_path_eh"] = dE
     print(json.dumps(line))
-    ctx.close()
     return 0
+
+
+def measure_path(R, W, torch, precision, args, rank, local, pg, trace):
+    """Warm-up and timed AIMD steps of one context (device time by CUDA events on
+    the library stream, then the end-to-end pass through the public API)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    prec = R.PRECISION_MIXED if precision == "mixed" else R.PRECISION_FP64
+    mol = W.water8(rank)
+    ctx = R.Context(mol, precision=prec, device=local, **CONV)
+    traj = Trajectory(ctx, mol, rank, R)
+    stream = torch.cuda.ExternalStream(ctx.stream(), device=local)
+    for _ in range(max(args.warmup, 0)):
+        traj.step()
+    # ---- timed region 1: device time (CUDA events on the library stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.timings()["launches"]
+    it0 = len(traj.iters)
+    Etot0 = traj.total_energy()
+    energies = []
+    ctx.trace(bool(trace))
+    barrier(pg)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            traj.step()
+            energies.append(traj.E)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(pg)
+    ms = e0.elapsed_time(e1)
+    ms_max = allreduce_max(pg, ms, local)
+    launches = ctx.timings()["launches"] - launches0
+    stats = ctx.trace_stats() if trace else []
+    ctx.trace(False)
+    iters = traj.iters[it0:]
+    drift = traj.total_energy() - Etot0
+
+    # ---- timed region 2: end to end through the public API, host buffers
+    xyz_pinned = torch.empty(mol.natoms * 3, dtype=torch.float64, pin_memory=True).numpy()
+    barrier(pg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        a = -traj.g / traj.m
+        traj.x = traj.x + traj.v * traj.dt + 0.5 * a * traj.dt ** 2
+        xyz_pinned[:] = traj.x.reshape(-1)
+        ctx.update_geometry(xyz_pinned.reshape(-1, 3))
+        out = ctx.scf(guess=2, outputs=False)
+        g_new = ctx.gradient()
+        traj.v = traj.v + 0.5 * (a - g_new / traj.m) * traj.dt
+        traj.g, traj.E = g_new, out["energy"]
+    torch.cuda.synchronize()
+    e2e_s = allreduce_max(pg, time.perf_counter() - t0, local)
+    barrier(pg)
+    out = dict(world=world, ms_max=ms_max, launches=launches, stats=stats, iters=iters, drift=drift,
+               e2e_s=e2e_s, clocks=clk.summary(), energies=energies, natoms=mol.natoms)
+    ctx.close()
+    return out
 
 
 if __name__ == "__main__":

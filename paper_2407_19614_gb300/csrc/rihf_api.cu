@@ -1251,13 +1251,15 @@ static void fock_and_error(rihf_ctx* c, int variant) {
     else fock_build_tc(c, variant);
     diis_error(c);
   };
-  if (!c->opt.cuda_graphs || !c->graphs_ok || c->tracer.on || (variant > 0 && c->k_nsplit <= 0)) {
+  if (!c->opt.cuda_graphs || !c->graphs_ok || (variant > 0 && c->k_nsplit <= 0)) {
     eager();
     return;
   }
   auto& g = c->graphs[variant];
   if (!g.exec) {
     const long long l0 = c->launches;
+    const bool tr = c->tracer.on;   // no trace events inside the captured graph
+    c->tracer.on = false;
     RIHF_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     cudaGraph_t graph = nullptr;
     try {
@@ -1268,9 +1270,11 @@ static void fock_and_error(rihf_ctx* c, int variant) {
       cudaGetLastError();
       c->launches = l0;
       c->graphs_ok = false;
+      c->tracer.on = tr;
       eager();
       return;
     }
+    c->tracer.on = tr;
     RIHF_CUDA(cudaStreamEndCapture(c->stream, &graph));
     const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -1284,7 +1288,15 @@ static void fock_and_error(rihf_ctx* c, int variant) {
       return;
     }
   }
-  RIHF_CUDA(cudaGraphLaunch(g.exec, c->stream));
+  {
+    static const char* names[kOzMaxDigits + 1] = {
+        "SCF iteration graph: FP64 Fock build + DIIS error", "SCF iteration graph: tensor-core RI-K, 1 digit",
+        "SCF iteration graph: tensor-core RI-K, 2 digits", "SCF iteration graph: tensor-core RI-K, 3 digits",
+        "SCF iteration graph: tensor-core RI-K, 4 digits", "SCF iteration graph: tensor-core RI-K, 5 digits",
+        "SCF iteration graph: tensor-core RI-K, 6 digits", "SCF iteration graph: tensor-core RI-K, 7 digits"};
+    TraceScope t(c->tracer, c->stream, names[variant], 0.0, 0);
+    RIHF_CUDA(cudaGraphLaunch(g.exec, c->stream));
+  }
   c->launches += g.launches;
 }
 
