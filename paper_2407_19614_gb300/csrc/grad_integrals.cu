@@ -15,14 +15,16 @@
 
 namespace rihf {
 
+template <int W = 32>
 __device__ inline int warp_next(int* counter, int lane) {
   int t = 0;
   if (lane == 0) t = atomicAdd(counter, 1);
-  return __shfl_sync(0xffffffffu, t, 0);
+  return __shfl_sync(lane_group_mask<W>(), t, (threadIdx.x & 31) / W * W);
 }
 
+template <int W = 32>
 __device__ inline double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(lane_group_mask<W>(), v, o);
   return v;
 }
 
@@ -58,41 +60,43 @@ struct DerivPlan {
 
 // Ycart[ka][kb][kc] = sum tra[sa][ka] trb[sb][kb] trc[sc][kc] Y(sa, sb, sc), with
 // Y(sa, sb, sc) = src[(sc*sP) + (sa*sM) + sb*sN] (strides in doubles).
+template <int W = 32>
 __device__ inline void warp_back_transform(const double* src, long long sP, long long sM, long long sN, int la,
                                            int lb, int lc, const double* tra, const double* trb, const double* trc,
                                            int nfa, int nfb, int nfc, double* t1, double* t2, double* out,
                                            int lane) {
   const int na = ncart(la), nb = ncart(lb), nc = ncart(lc);
   // t1[sa][sb][kc] = sum_sc trc[sc][kc] Y
-  for (int idx = lane; idx < nfa * nfb * nc; idx += 32) {
+  for (int idx = lane; idx < nfa * nfb * nc; idx += W) {
     int kc = idx % nc, r = idx / nc;
     int sb = r % nfb, sa = r / nfb;
     double v = 0.0;
     for (int sc = 0; sc < nfc; ++sc) v += trc[sc * kTrStride + kc] * src[sc * sP + sa * sM + sb * sN];
     t1[idx] = v;
   }
-  __syncwarp();
+  __syncwarp(lane_group_mask<W>());
   // t2[sa][kb][kc]
-  for (int idx = lane; idx < nfa * nb * nc; idx += 32) {
+  for (int idx = lane; idx < nfa * nb * nc; idx += W) {
     int kc = idx % nc, r = idx / nc;
     int kb = r % nb, sa = r / nb;
     double v = 0.0;
     for (int sb = 0; sb < nfb; ++sb) v += trb[sb * kTrStride + kb] * t1[(sa * nfb + sb) * nc + kc];
     t2[idx] = v;
   }
-  __syncwarp();
+  __syncwarp(lane_group_mask<W>());
   // out[ka][kb][kc]
-  for (int idx = lane; idx < na * nb * nc; idx += 32) {
+  for (int idx = lane; idx < na * nb * nc; idx += W) {
     int rest = idx % (nb * nc), ka = idx / (nb * nc);
     double v = 0.0;
     for (int sa = 0; sa < nfa; ++sa) v += tra[sa * kTrStride + ka] * t2[sa * nb * nc + rest];
     out[idx] = v;
   }
-  __syncwarp();
+  __syncwarp(lane_group_mask<W>());
 }
 
 // g[0..2] += sum_{ka,kb,kc} Y[ka][kb][kc] * (d/dA_x), g[3..5] += ... (d/dB_x) from
 // the four shifted HRR products of one shell triple.  Returns per-lane partials.
+template <int W = 32>
 __device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, int la, int lb, int lc,
                                            const double* AB, int lane, double g[6]) {
   const int na = ncart(la), nb = ncart(lb), nc = ncart(lc);
@@ -104,9 +108,9 @@ __device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, in
   for (int i = 0; i < 6; ++i) g[i] = 0.0;
   // (la+1, lb) from accA
   {
-    const double* I = warp_hrr(accA, pl.emin, la + 1, lb, lc, AB, scr, pl.half, lane);
+    const double* I = warp_hrr<W>(accA, pl.emin, la + 1, lb, lc, AB, scr, pl.half, lane);
     int nap = ncart(la + 1);
-    for (int idx = lane; idx < na * nb * nc; idx += 32) {
+    for (int idx = lane; idx < na * nb * nc; idx += W) {
       int kc = idx % nc, r = idx / nc, kb = r % nb, ka = r / nb;
       int ax, ay, az;
       cart_decode(la, ka, ax, ay, az);
@@ -117,11 +121,11 @@ __device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, in
       g[2] += y * I[(kz * nb + kb) * nc + kc];
       (void)nap;
     }
-    __syncwarp();
+    __syncwarp(lane_group_mask<W>());
   }
   if (la > 0) {
-    const double* I = warp_hrr(acc0, pl.emin, la - 1, lb, lc, AB, scr, pl.half, lane);
-    for (int idx = lane; idx < na * nb * nc; idx += 32) {
+    const double* I = warp_hrr<W>(acc0, pl.emin, la - 1, lb, lc, AB, scr, pl.half, lane);
+    for (int idx = lane; idx < na * nb * nc; idx += W) {
       int kc = idx % nc, r = idx / nc, kb = r % nb, ka = r / nb;
       int ax, ay, az;
       cart_decode(la, ka, ax, ay, az);
@@ -130,12 +134,12 @@ __device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, in
       if (ay > 0) g[1] -= ay * y * I[(cart_index(la - 1, ax, ay - 1) * nb + kb) * nc + kc];
       if (az > 0) g[2] -= az * y * I[(cart_index(la - 1, ax, ay) * nb + kb) * nc + kc];
     }
-    __syncwarp();
+    __syncwarp(lane_group_mask<W>());
   }
   {
-    const double* I = warp_hrr(accB, pl.emin, la, lb + 1, lc, AB, scr, pl.half, lane);
+    const double* I = warp_hrr<W>(accB, pl.emin, la, lb + 1, lc, AB, scr, pl.half, lane);
     int nbp = ncart(lb + 1);
-    for (int idx = lane; idx < na * nb * nc; idx += 32) {
+    for (int idx = lane; idx < na * nb * nc; idx += W) {
       int kc = idx % nc, r = idx / nc, kb = r % nb, ka = r / nb;
       int bx, by, bz;
       cart_decode(lb, kb, bx, by, bz);
@@ -144,12 +148,12 @@ __device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, in
       g[4] += y * I[(ka * nbp + cart_index(lb + 1, bx, by + 1)) * nc + kc];
       g[5] += y * I[(ka * nbp + cart_index(lb + 1, bx, by)) * nc + kc];
     }
-    __syncwarp();
+    __syncwarp(lane_group_mask<W>());
   }
   if (lb > 0) {
-    const double* I = warp_hrr(acc0, pl.emin, la, lb - 1, lc, AB, scr, pl.half, lane);
+    const double* I = warp_hrr<W>(acc0, pl.emin, la, lb - 1, lc, AB, scr, pl.half, lane);
     int nbm = ncart(lb - 1);
-    for (int idx = lane; idx < na * nb * nc; idx += 32) {
+    for (int idx = lane; idx < na * nb * nc; idx += W) {
       int kc = idx % nc, r = idx / nc, kb = r % nb, ka = r / nb;
       int bx, by, bz;
       cart_decode(lb, kb, bx, by, bz);
@@ -158,23 +162,25 @@ __device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, in
       if (by > 0) g[4] -= by * y * I[(ka * nbm + cart_index(lb - 1, bx, by - 1)) * nc + kc];
       if (bz > 0) g[5] -= bz * y * I[(ka * nbm + cart_index(lb - 1, bx, by)) * nc + kc];
     }
-    __syncwarp();
+    __syncwarp(lane_group_mask<W>());
   }
 }
 
 // ------------------------------------------------------------ 3-centre
 
+template <int W>
 __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells aux,
                                                        const ShellPair* __restrict__ pairs, PairTable ptab,
                                                        const int2* __restrict__ tasks, long long ntask,
                                                        const double* __restrict__ boys, int* counter,
-                                                       const double* __restrict__ Y, double* grad) {
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x;
+                                                       const double* __restrict__ Y, double* grad, int slice) {
+  extern __shared__ double smem_all[];
+  const int lane = threadIdx.x % W;
+  double* smem = smem_all + (threadIdx.x / W) * slice;   // this task group's slice
   const int N = prim.nfunc;
   const long long N2 = (long long)N * N;
   for (;;) {
-    long long task = warp_next(counter, lane);
+    long long task = warp_next<W>(counter, lane);
     if (task >= ntask) break;
     const int2 tk = tasks[task];
     int ip = tk.x, sc = tk.y;
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
     double* vrr = smem + pl.vrr;
     double* etr = smem + pl.etr;
     int accsz = acc_size(pl.emin, pl.emax, lc);
-    for (int i = lane; i < 3 * accsz; i += 32) smem[pl.acc0 + i] = 0.0;
+    for (int i = lane; i < 3 * accsz; i += W) smem[pl.acc0 + i] = 0.0;
     const double* A = prim.xyz + 3 * sa;
     const double* B = prim.xyz + 3 * sb;
     const double* C = aux.xyz + 3 * sc;
@@ -201,26 +207,26 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
       for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
         const int ic = aux.pstart[sc] + pc;
         Prim3 t = make_prim3_pp(q, aux.exps[ic], aux.iexps[ic], aux.coefs[ic], C, ABv);
-        if (lane <= pl.L) Fm[lane] = boys_eval(lane, t.T, boys);
-        __syncwarp();
-        warp_vrr(vrr, pl.L, t, Fm, lane);
-        warp_etr(vrr, pl.L, etr, sh, t, Fm, lane);
-        warp_acc_level(vrr, pl.L, etr, sh, 1.0, smem + pl.acc0, lane);
-        warp_acc_level(vrr, pl.L, etr, sh, 2.0 * q.alpha, smem + pl.accA, lane);
-        warp_acc_level(vrr, pl.L, etr, sh, 2.0 * q.beta, smem + pl.accB, lane);
+        for (int m = lane; m <= pl.L; m += W) Fm[m] = boys_eval(m, t.T, boys);
+        __syncwarp(lane_group_mask<W>());
+        warp_vrr<W>(vrr, pl.L, t, Fm, lane);
+        warp_etr<W>(vrr, pl.L, etr, sh, t, Fm, lane);
+        warp_acc_level<W>(vrr, pl.L, etr, sh, 1.0, smem + pl.acc0, lane);
+        warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.alpha, smem + pl.accA, lane);
+        warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.beta, smem + pl.accB, lane);
       }
     }
     // Y block -> Cartesian
     int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
     const double* src = Y + (long long)aux.ao[sc] * N2 + (long long)prim.ao[sa] * N + prim.ao[sb];
-    warp_back_transform(src, N2, N, 1, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
+    warp_back_transform<W>(src, N2, N, 1, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
                         prim.tr + lb * kTrStride * kTrStride, aux.tr + lc * kTrStride * kTrStride, nfa, nfb, nfc,
                         smem + pl.t1, smem + pl.t2, smem + pl.ycart, lane);
     double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
     double g[6];
-    warp_deriv_contract(pl, smem, la, lb, lc, AB, lane, g);
+    warp_deriv_contract<W>(pl, smem, la, lb, lc, AB, lane, g);
     double wgt = (sa == sb) ? 1.0 : 2.0;
-    for (int i = 0; i < 6; ++i) g[i] = warp_sum(g[i]) * wgt;
+    for (int i = 0; i < 6; ++i) g[i] = warp_sum<W>(g[i]) * wgt;
     if (lane == 0) {
       for (int x = 0; x < 3; ++x) {
         atomicAdd(grad + 3 * ata + x, g[x]);
@@ -228,7 +234,7 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
         atomicAdd(grad + 3 * atc + x, -(g[x] + g[3 + x]));
       }
     }
-    __syncwarp();
+    __syncwarp(lane_group_mask<W>());
   }
 }
 
@@ -494,11 +500,20 @@ void launch_grad_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShe
                       const PairTable& pt, const TaskGroup* groups, int ngroups, const double* Y, double* grad) {
   for (int g = 0; g < ngroups; ++g) {
     if (groups[g].ntask == 0) continue;
-    int smem = groups[g].smem_grad;
-    raise_smem_limit((const void*)grad_eri3_kernel, smem);
+    const int W = groups[g].width, slice = groups[g].smem_grad / (int)sizeof(double);
+    const int smem = (32 / W) * slice * (int)sizeof(double);
     RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
-    grad_eri3_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks,
-                                                                   groups[g].ntask, ic.boys, ic.counter, Y, grad);
+    if (W == 8) {
+      raise_smem_limit((const void*)grad_eri3_kernel<8>, smem);
+      grad_eri3_kernel<8><<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks,
+                                                                        groups[g].ntask, ic.boys, ic.counter, Y,
+                                                                        grad, slice);
+    } else {
+      raise_smem_limit((const void*)grad_eri3_kernel<32>, smem);
+      grad_eri3_kernel<32><<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks,
+                                                                         groups[g].ntask, ic.boys, ic.counter, Y,
+                                                                         grad, slice);
+    }
     RIHF_LAUNCH_CHECK();
     if (ic.launches) *ic.launches += 1;
   }

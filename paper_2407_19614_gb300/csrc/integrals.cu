@@ -62,20 +62,22 @@ void boys_table_host(double* out) {
 
 // ------------------------------------------------------------ helpers
 
+template <int W = 32>
 __device__ inline int warp_next_task(int* counter, int lane) {
   int t = 0;
   if (lane == 0) t = atomicAdd(counter, 1);
-  return __shfl_sync(0xffffffffu, t, 0);
+  return __shfl_sync(lane_group_mask<W>(), t, (threadIdx.x & 31) / W * W);
 }
 
 // out[sa][sb][sc] = sum tra[sa][ka] trb[sb][kb] trc[sc][kc] cart[ka][kb][kc]
 // (three passes through shared memory).  Returns the result pointer.
+template <int W = 32>
 __device__ inline const double* warp_transform3(const double* cart, int la, int lb, int lc, const double* tra,
                                                 const double* trb, const double* trc, int nfa, int nfb, int nfc,
                                                 double* s1, double* s2, int lane) {
   const int na = ncart(la), nb = ncart(lb), nc = ncart(lc);
   // pass c: s1[ka][kb][sc]
-  for (int idx = lane; idx < na * nb * nfc; idx += 32) {
+  for (int idx = lane; idx < na * nb * nfc; idx += W) {
     int sc = idx % nfc, r = idx / nfc;
     const double* row = cart + r * nc;
     const double* t = trc + sc * kTrStride;
@@ -83,9 +85,9 @@ __device__ inline const double* warp_transform3(const double* cart, int la, int 
     for (int k = 0; k < nc; ++k) v += t[k] * row[k];
     s1[idx] = v;
   }
-  __syncwarp();
+  __syncwarp(lane_group_mask<W>());
   // pass b: s2[ka][sb][sc]
-  for (int idx = lane; idx < na * nfb * nfc; idx += 32) {
+  for (int idx = lane; idx < na * nfb * nfc; idx += W) {
     int sc = idx % nfc, r = idx / nfc;
     int sb = r % nfb, ka = r / nfb;
     const double* t = trb + sb * kTrStride;
@@ -93,16 +95,16 @@ __device__ inline const double* warp_transform3(const double* cart, int la, int 
     for (int k = 0; k < nb; ++k) v += t[k] * s1[(ka * nb + k) * nfc + sc];
     s2[idx] = v;
   }
-  __syncwarp();
+  __syncwarp(lane_group_mask<W>());
   // pass a: s1[sa][sb][sc]
-  for (int idx = lane; idx < nfa * nfb * nfc; idx += 32) {
+  for (int idx = lane; idx < nfa * nfb * nfc; idx += W) {
     int rest = idx % (nfb * nfc), sa = idx / (nfb * nfc);
     const double* t = tra + sa * kTrStride;
     double v = 0.0;
     for (int k = 0; k < na; ++k) v += t[k] * s2[k * nfb * nfc + rest];
     s1[idx] = v;
   }
-  __syncwarp();
+  __syncwarp(lane_group_mask<W>());
   return s1;
 }
 
@@ -135,16 +137,18 @@ int smem_eri3_doubles(int la, int lb, int lc) {
 
 // ------------------------------------------------------------ (mu nu|P)
 
+template <int W>
 __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux, const ShellPair* __restrict__ pairs,
                                                   PairTable ptab, const int2* __restrict__ tasks, long long ntask,
                                                   const double* __restrict__ boys, int* counter,
-                                                  double* __restrict__ T) {
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x;
+                                                  double* __restrict__ T, int slice) {
+  extern __shared__ double smem_all[];
+  const int lane = threadIdx.x % W;
+  double* smem = smem_all + (threadIdx.x / W) * slice;   // this task group's slice
   const int N = prim.nfunc;
   const size_t N2 = (size_t)N * N;
   for (;;) {
-    long long task = warp_next_task(counter, lane);
+    long long task = warp_next_task<W>(counter, lane);
     if (task >= ntask) break;
     const int2 tk = tasks[task];
     int ip = tk.x, sc = tk.y;
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
     double* etr = smem + pl.etr;
     double* acc = smem + pl.acc;
     int accsz = acc_size(emin, emax, lc);
-    for (int i = lane; i < accsz; i += 32) acc[i] = 0.0;
+    for (int i = lane; i < accsz; i += W) acc[i] = 0.0;
     const double* A = prim.xyz + 3 * sa;
     const double* B = prim.xyz + 3 * sb;
     const double* C = aux.xyz + 3 * sc;
@@ -173,26 +177,26 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
       for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
         const int ic = aux.pstart[sc] + pc;
         Prim3 t = make_prim3_pp(q, aux.exps[ic], aux.iexps[ic], aux.coefs[ic], C, AB);
-        if (lane <= L) Fm[lane] = boys_eval(lane, t.T, boys);
-        __syncwarp();
-        warp_vrr(vrr, L, t, Fm, lane);
-        warp_etr_accumulate(vrr, L, etr, sh, t, 1.0, acc, Fm, lane);
+        for (int m = lane; m <= L; m += W) Fm[m] = boys_eval(m, t.T, boys);
+        __syncwarp(lane_group_mask<W>());
+        warp_vrr<W>(vrr, L, t, Fm, lane);
+        warp_etr_accumulate<W>(vrr, L, etr, sh, t, 1.0, acc, Fm, lane);
       }
     }
-    const double* cart = warp_hrr(acc, emin, la, lb, lc, AB, smem + pl.hrr, pl.half, lane);
+    const double* cart = warp_hrr<W>(acc, emin, la, lb, lc, AB, smem + pl.hrr, pl.half, lane);
     int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
-    const double* out = warp_transform3(cart, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
+    const double* out = warp_transform3<W>(cart, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
                                         prim.tr + lb * kTrStride * kTrStride, aux.tr + lc * kTrStride * kTrStride,
                                         nfa, nfb, nfc, smem + pl.t1, smem + pl.t2, lane);
     const int mu0 = prim.ao[sa], nu0 = prim.ao[sb], P0 = aux.ao[sc];
     const int n = nfa * nfb * nfc;
-    for (int idx = lane; idx < n; idx += 32) {
+    for (int idx = lane; idx < n; idx += W) {
       int sbb = idx % nfb, r = idx / nfb;
       int saa = r % nfa, scc = r / nfa;
       size_t dst = swp ? (size_t)(nu0 + sbb) * N + mu0 + saa : (size_t)(mu0 + saa) * N + nu0 + sbb;
       T[(size_t)(P0 + scc) * N2 + dst] = out[(saa * nfb + sbb) * nfc + scc];
     }
-    __syncwarp();
+    __syncwarp(lane_group_mask<W>());
   }
 }
 
@@ -612,11 +616,18 @@ void launch_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& 
                  const PairTable& pt, const TaskGroup* groups, int ngroups, double* T) {
   for (int g = 0; g < ngroups; ++g) {
     if (groups[g].ntask == 0) continue;
-    int smem = groups[g].smem_eri3;
-    set_smem((const void*)eri3_kernel, smem);
+    const int W = groups[g].width, slice = groups[g].smem_eri3 / (int)sizeof(double);
+    const int smem = (32 / W) * slice * (int)sizeof(double);
     RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
-    eri3_kernel<<<grid_for(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks, groups[g].ntask,
-                                                         ic.boys, ic.counter, T);
+    if (W == 8) {
+      set_smem((const void*)eri3_kernel<8>, smem);
+      eri3_kernel<8><<<grid_for(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks,
+                                                              groups[g].ntask, ic.boys, ic.counter, T, slice);
+    } else {
+      set_smem((const void*)eri3_kernel<32>, smem);
+      eri3_kernel<32><<<grid_for(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks,
+                                                               groups[g].ntask, ic.boys, ic.counter, T, slice);
+    }
     RIHF_LAUNCH_CHECK();
     if (ic.launches) *ic.launches += 1;
   }
@@ -768,8 +779,9 @@ void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lpr
 void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim,
                        const std::vector<int>& laux, std::vector<std::vector<int2>>& tasks,
                        std::vector<int>& smem_eri3, std::vector<int>& smem_grad) {
-  // about 17, 7 and at most 2 warps per SM (228 KB shared memory, 1 KB reserved per block)
-  const int limits[kTaskGroups] = {12 * 1024, 28 * 1024, 1 << 30};
+  // group 0: tiny classes as 8-lane groups (4 tasks per warp); then about 17,
+  // 7 and at most 2 warps per SM (228 KB shared memory, 1 KB reserved per block)
+  const int limits[kTaskGroups] = {3584, 12 * 1024, 28 * 1024, 1 << 30};
   constexpr int nl = kMaxLPrim + 1, nc = kMaxLAux + 1;
   int se[nl][nl][nc], sg[nl][nl][nc], grp[nl][nl][nc];
   for (int la = 0; la < nl; ++la)

@@ -58,12 +58,15 @@ int smem_eri3_doubles(int la, int lb, int lc);
 int smem_grad_doubles(int la, int lb, int lc);
 
 // (pair index, auxiliary shell) tasks of one shared-memory class group.
-constexpr int kTaskGroups = 3;
+constexpr int kTaskGroups = 4;
 struct TaskGroup {
   const int2* tasks = nullptr;
   long long ntask = 0;
-  int smem_eri3 = 0, smem_grad = 0;   // bytes
+  int smem_eri3 = 0, smem_grad = 0;   // bytes per task
+  int width = 32;                     // lanes per task (8: four tasks per warp)
 };
+// Lanes per task of class group g (group 0 holds the tiny classes).
+inline int task_group_width(int g) { return g == 0 ? 8 : 32; }
 void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim,
                        const std::vector<int>& laux, std::vector<std::vector<int2>>& tasks,
                        std::vector<int>& smem_eri3, std::vector<int>& smem_grad);

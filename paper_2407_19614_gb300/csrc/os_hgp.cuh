@@ -188,6 +188,14 @@ __device__ inline Prim3 make_prim_point(double al, const double* A, double be, c
   return t;
 }
 
+// Lanes of one task group: W consecutive lanes of a warp (W = 32: the whole
+// warp).  Small shell classes run W = 8 groups, four tasks per warp, so the
+// narrow FP64 pipe is not spent on idle lanes.
+template <int W>
+__device__ inline unsigned lane_group_mask() {
+  return W == 32 ? 0xffffffffu : (((1u << W) - 1u) << ((threadIdx.x & 31) / W * W));
+}
+
 // ---------------------------------------------------------------- layouts
 
 // VRR table [e][m][k], e = 0..L, m = 0..L-e.
@@ -243,21 +251,22 @@ __device__ __host__ inline int hrr_scratch(int la, int lb, int lc, int emax) {
 //   [e+1_i]^(m) = PA_i [e]^(m) + WP_i [e]^(m+1) + e_i/(2p) ([e-1_i]^(m) - rho/p [e-1_i]^(m+1))
 // Fm points at the warp's kFmRegion block: F_m in [0, L], and this routine
 // writes the k/(2p), k/(2q) factors at kH2p, kH2q for the electron transfer.
+template <int W = 32>
 __device__ inline void warp_vrr(double* vrr, int L, const Prim3& t, double* Fm, int lane) {
-  if (lane <= L) {
-    const double k = (double)lane;
-    vrr[lane] = t.pref * Fm[lane];
-    Fm[kH2p + lane] = k * t.inv2p;
-    Fm[kH2q + lane] = k * t.inv2q;
+  for (int m = lane; m <= L; m += W) {
+    const double k = (double)m;
+    vrr[m] = t.pref * Fm[m];
+    Fm[kH2p + m] = k * t.inv2p;
+    Fm[kH2q + m] = k * t.inv2q;
   }
-  __syncwarp();
+  __syncwarp(lane_group_mask<W>());
   const double* h2p = Fm + kH2p;
   const double rp = t.rp;
   int off_m2 = 0, off_m1 = 0, off = L + 1;   // offsets of levels e-2, e-1, e
   for (int e = 1; e <= L; ++e) {
     int nc = ncart(e), nc1 = ncart(e - 1), nc2 = e >= 2 ? ncart(e - 2) : 0;
     int n = nc * (L - e + 1);
-    for (int idx = lane; idx < n; idx += 32) {
+    for (int idx = lane; idx < n; idx += W) {
       int m = idx / nc, k = idx - m * nc;
       int lx, ly, lz;
       cart_decode(e, k, lx, ly, lz);
@@ -277,7 +286,7 @@ __device__ inline void warp_vrr(double* vrr, int L, const Prim3& t, double* Fm, 
     off_m2 = off_m1;
     off_m1 = off;
     off += n;
-    __syncwarp();
+    __syncwarp(lane_group_mask<W>());
   }
 }
 
@@ -295,22 +304,24 @@ __device__ inline double etr_get(const double* vrr, int L, const double* etr, co
 }
 
 // acc[e][ke][kc] += w * level lc (level 0 is the VRR m = 0 slice).
+template <int W = 32>
 __device__ inline void warp_acc_level(const double* vrr, int L, const double* etr, const EtrShape& sh, double w,
                                       double* acc, int lane) {
   const int lc = sh.lc;
   int n = acc_size(sh.emin, sh.emax, lc);
   int ncc = ncart(lc);
-  for (int idx = lane; idx < n; idx += 32) {
+  for (int idx = lane; idx < n; idx += W) {
     int r = idx / ncc, kc = idx - r * ncc;
     int e = sh.emin;
     while (cart_offset(e + 1) - cart_offset(sh.emin) <= r) ++e;
     int ke = r - (cart_offset(e) - cart_offset(sh.emin));
     acc[idx] += w * etr_get(vrr, L, etr, sh, lc, e, ke, kc);
   }
-  __syncwarp();
+  __syncwarp(lane_group_mask<W>());
 }
 
 // Fm: the warp's scalar region after warp_vrr (reads the k/(2q) factors).
+template <int W = 32>
 __device__ inline void warp_etr(const double* vrr, int L, double* etr, const EtrShape& sh, const Prim3& t,
                                 const double* Fm, int lane) {
   const int lc = sh.lc;
@@ -323,7 +334,7 @@ __device__ inline void warp_etr(const double* vrr, int L, double* etr, const Etr
     int nrows = cart_offset(hi + 1) - cart_offset(lo);
     int n = nrows * ncc;
     double* lvl = etr + sh.level_off(c);
-    for (int idx = lane; idx < n; idx += 32) {
+    for (int idx = lane; idx < n; idx += W) {
       int r = idx / ncc, kc = idx - r * ncc;
       int e = lo;
       while (cart_offset(e + 1) - cart_offset(lo) <= r) ++e;
@@ -354,14 +365,15 @@ __device__ inline void warp_etr(const double* vrr, int L, double* etr, const Etr
       }
       lvl[idx] = v;
     }
-    __syncwarp();
+    __syncwarp(lane_group_mask<W>());
   }
 }
 
+template <int W = 32>
 __device__ inline void warp_etr_accumulate(const double* vrr, int L, double* etr, const EtrShape& sh,
                                            const Prim3& t, double w, double* acc, const double* Fm, int lane) {
-  warp_etr(vrr, L, etr, sh, t, Fm, lane);
-  warp_acc_level(vrr, L, etr, sh, w, acc, lane);
+  warp_etr<W>(vrr, L, etr, sh, t, Fm, lane);
+  warp_acc_level<W>(vrr, L, etr, sh, w, acc, lane);
 }
 
 // ---------------------------------------------------------------- HRR
@@ -369,6 +381,7 @@ __device__ inline void warp_etr_accumulate(const double* vrr, int L, double* etr
 // (a, b+1_i| = (a+1_i, b| + AB_i (a, b|.  Input acc [e][ke][kc] for e in
 // [emin, emax]; output out[ka][kb][kc] for (la, lb).  Returns pointer to the
 // result (inside scratch or acc itself when lb == 0).
+template <int W = 32>
 __device__ inline const double* warp_hrr(const double* acc, int emin, int la, int lb, int lc, const double* AB,
                                          double* scratch, int half, int lane) {
   const int ncc = ncart(lc);
@@ -384,7 +397,7 @@ __device__ inline const double* warp_hrr(const double* acc, int emin, int la, in
     int nrows = cart_offset(ahi + 1) - cart_offset(la);
     int nb = ncart(b);
     int n = nrows * nb * ncc;
-    for (int idx = lane; idx < n; idx += 32) {
+    for (int idx = lane; idx < n; idx += W) {
       int kc = idx % ncc;
       int rest = idx / ncc;
       int kb = rest % nb;
@@ -408,7 +421,7 @@ __device__ inline const double* warp_hrr(const double* acc, int emin, int la, in
       double v = prev[(rp * prev_nb + kbl) * ncc + kc] + AB[i] * prev[(r0 * prev_nb + kbl) * ncc + kc];
       cur[idx] = v;
     }
-    __syncwarp();
+    __syncwarp(lane_group_mask<W>());
     prev = cur;
     prev_nb = nb;
   }

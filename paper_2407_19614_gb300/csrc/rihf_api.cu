@@ -566,6 +566,7 @@ static void refresh_tasks(rihf_ctx* c) {
     c->groups[g].ntask = (long long)tasks[g].size();
     c->groups[g].smem_eri3 = se[g];
     c->groups[g].smem_grad = sg[g];
+    c->groups[g].width = task_group_width(g);
     upload(c->d_tasks + off, tasks[g], c->stream);
     off += tasks[g].size();
   }
