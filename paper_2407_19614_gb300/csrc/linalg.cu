@@ -3,6 +3,7 @@
 #include <cmath>
 
 #include "linalg.cuh"
+#include "tc_gemm.cuh"
 
 #include <mutex>
 #include <unordered_map>
@@ -576,6 +577,42 @@ void trsm_lower(const LaCtx& la, const double* L, int n, double* X, long long nc
       u.C = X; u.ldc = (int)ncol;
     }
     if (u.M > 0) dgemm(la, u);
+  }
+}
+
+void trsm_lower_tc(const LaCtx& la, const double* L, int n, double* X, long long ncol, int symcols,
+                   const TrsmTcScratch& sc) {
+  constexpr int PB = kOzChunk;   // panel = one K chunk of the digit-plane GEMM
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((ncol + 255) / 256, 16LL * la.sms));
+  for (int k = 0; k < n; k += PB) {
+    const int pb = std::min(PB, n - k);
+    // the panel in FP64: 32-row substitution blocks and their in-panel updates
+    for (int k2 = k; k2 < k + pb; k2 += CB) {
+      const int b = std::min(CB, k + pb - k2);
+      trsv_block_kernel<<<blocks, 256, 0, la.stream>>>(L, n, k2, b, X, ncol, 0, symcols);
+      RIHF_LAUNCH_CHECK();
+      count(la);
+      const int m2 = k + pb - (k2 + b);
+      if (m2 > 0) {
+        GemmArgs u;
+        u.M = m2; u.N = (int)ncol; u.K = b;
+        u.A = L + (size_t)(k2 + b) * n + k2; u.lda = n;
+        u.B = X + (size_t)k2 * ncol; u.ldb = (int)ncol;
+        u.C = X + (size_t)(k2 + b) * ncol; u.ldc = (int)ncol;
+        u.alpha = -1.0; u.beta = 1.0; u.symcols = symcols;
+        dgemm(la, u);
+      }
+    }
+    // rows below the panel: X2 -= L21 X1 on the tensor cores
+    const int M = n - k - pb;
+    if (M <= 0) continue;
+    OzGemmArgs g;
+    g.A = oz_slice(la, L + (size_t)(k + pb) * n + k, M, pb, n, 1, 0, pb, kOzMaxDigits, 0, sc.planes_L, sc.exps_L);
+    g.B = oz_slice(la, X + (size_t)k * ncol, (int)ncol, pb, 1, ncol, 0, pb, kOzMaxDigits, 0, sc.planes_X, sc.exps_X);
+    g.M = M; g.N = (int)ncol; g.s = kOzMaxDigits; g.alpha = -1.0;
+    g.C = X + (size_t)(k + pb) * ncol; g.cs_m1 = ncol; g.cs_n = 1;
+    g.accumulate = true; g.symcols = symcols;
+    oz_gemm(la, g);
   }
 }
 

@@ -72,6 +72,20 @@ void to_float(const LaCtx& la, const double* in, long long n, float* out, double
 // Mirror the lower triangle into the upper one for each of `batch` n x n slices.
 void symmetrize_lower(const LaCtx& la, double* X, int n, int batch);
 
+// Forward substitution X <- L^{-1} X (as trsm_lower with trans = false) whose
+// rank-64 updates of the rows below each 64-row panel run on the tensor cores
+// as 7-digit BF16 digit-plane GEMMs (FP64-class products, tc_gemm.cuh); the
+// panels themselves are solved in FP64.  Scratch: digit planes and exponents
+// for a 64-column slice of L (n rows) and for the panel of X (ncol rows).
+struct TrsmTcScratch {
+  uint16_t* planes_L = nullptr;
+  int* exps_L = nullptr;
+  uint16_t* planes_X = nullptr;
+  int* exps_X = nullptr;
+};
+void trsm_lower_tc(const LaCtx& la, const double* L, int n, double* X, long long ncol, int symcols,
+                   const TrsmTcScratch& sc);
+
 // In-place Cholesky A = L L^T (lower, upper part zeroed) of an n x n matrix;
 // sets *flag = 1 on a non-positive pivot.  Then Linv = L^{-1} (n x n).
 void cholesky(const LaCtx& la, double* A, int n, double* scratch);

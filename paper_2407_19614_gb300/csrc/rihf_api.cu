@@ -454,6 +454,7 @@ struct rihf_ctx {
   uint16_t *Bpl = nullptr, *Cpl = nullptr, *Hpl = nullptr;
   int *Bex = nullptr, *Cex = nullptr, *Hex = nullptr;
   OzOperand Bop;
+  TrsmTcScratch trsm_sc;          // tensor-core fit (mixed mode)
   int tc_builds = 0, last_iters = 0, last_digits = 0;
   double flops_eri3 = 0.0, flops_grad3 = 0.0;   // algorithmic FP64 operations of the 3-centre kernels
   int k_nsplit = 0;             // K splits of the tensor-core K GEMM (0: not tuned yet)
@@ -575,7 +576,8 @@ static void refresh_tasks(rihf_ctx* c) {
 static void free_all(rihf_ctx* c) {
   void* ptrs[] = {c->d_pl, c->d_patom, c->d_pnprim, c->d_pps, c->d_pao, c->d_pxyz, c->d_pexp, c->d_pcoef,
                   c->d_al, c->d_aatom, c->d_anprim, c->d_aps, c->d_aao, c->d_axyz_sh, c->d_aexp, c->d_acoef,
-                  c->d_piexp, c->d_aiexp, c->d_pp_off, c->d_pp,
+                  c->d_piexp, c->d_aiexp, c->d_pp_off, c->d_pp, c->trsm_sc.planes_L, c->trsm_sc.exps_L,
+                  c->trsm_sc.planes_X, c->trsm_sc.exps_X,
                   c->d_ao_atom, c->d_ao_l, c->hist_D[0], c->hist_D[1], c->hist_D[2], c->hist_S, c->hist_xyz[0],
                   c->hist_xyz[1], c->Dpred, c->mlX, c->mly, c->mlt, c->mlDx, c->ml_sums, c->rep_X, c->rep_t, c->net.master, c->net.wbf, c->net.grad,
                   c->net.m, c->net.v, c->net.loss,
@@ -658,8 +660,14 @@ static void compute_geometry(rihf_ctx* c) {
     launch_pair_prims(ic, P, c->d_pairs, c->npairs, c->d_pp_off, c->d_pp);
     launch_eri3(ic, P, X, c->d_pairs, c->ptab(), c->groups, kTaskGroups, c->T3); }
   RIHF_CUDA(cudaMemcpyAsync(c->B, c->T3, sizeof(double) * (size_t)NA * N * N, cudaMemcpyDeviceToDevice, s));
-  { TraceScope t(c->tracer, s, "fit trsm B=L^-1 T", (double)NA * NA * N * (N + 1) / 2, 0);
-    trsm_lower(la, c->L, NA, c->B, (long long)N * N, false, N, c->trsm_tmp); }
+  if (c->trsm_sc.planes_X) {
+    // mixed mode: rank-64 updates on the tensor cores (7 digits), panels in FP64
+    TraceScope t(c->tracer, s, "fit trsm B=L^-1 T (tcgen05 digit updates)", (double)NA * NA * N * (N + 1) / 2, 0);
+    trsm_lower_tc(la, c->L, NA, c->B, (long long)N * N, N, c->trsm_sc);
+  } else {
+    TraceScope t(c->tracer, s, "fit trsm B=L^-1 T", (double)NA * NA * N * (N + 1) / 2, 0);
+    trsm_lower(la, c->L, NA, c->B, (long long)N * N, false, N, c->trsm_tmp);
+  }
   symmetrize_lower(la, c->B, N, NA);
   if (c->Bpl) {   // digit planes of B for the tensor-core RI-K (rows (P, mu), K = nu)
     TraceScope t(c->tracer, s, "B digit planes (oz_slice)", (double)NA * N * N * (8 + 2 * kOzMaxDigits), 1);
@@ -919,6 +927,10 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
       c->Cex = dalloc<int>(oz_plane_elems(c->nocc, 1, 1) / kOzChunk);
       c->Hpl = dalloc<uint16_t>(oz_plane_elems(N, NA * c->nocc, kOzMaxDigits));
       c->Hex = dalloc<int>(oz_plane_elems(N, 1, 1) / kOzChunk * nkb_max);
+      c->trsm_sc.planes_L = dalloc<uint16_t>(oz_plane_elems(NA, kOzChunk, kOzMaxDigits));
+      c->trsm_sc.exps_L = dalloc<int>(oz_plane_elems(NA, 1, 1) / kOzChunk);
+      c->trsm_sc.planes_X = dalloc<uint16_t>(oz_plane_elems(N * N, kOzChunk, kOzMaxDigits));
+      c->trsm_sc.exps_X = dalloc<int>(oz_plane_elems(N * N, 1, 1) / kOzChunk);
     }
     c->trsm_tmp = dalloc<double>(32 * std::max<size_t>({n2, (size_t)NA, (size_t)c->nocc * c->nocc}) + 1024);
     {   // guess history and learned-guess buffers

@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(kOzThreads) oz_slice_kernel(const double* __re
 // drain.
 __global__ void __launch_bounds__(kOzThreads, 1)
     oz_gemm_kernel(OzOperand A, OzOperand B, int M, int N, int s, int TN, int mtiles, int ntiles, int nsplit,
-                   int lower_only, double alpha, double* C, long long MR, long long cs_m1, long long cs_m2,
-                   long long cs_n, int atomic, int* flag) {
+                   int lower_only, int symcols, double alpha, double* C, long long MR, long long cs_m1,
+                   long long cs_m2, long long cs_n, int atomic, int* flag) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* As = smem;
@@ -243,6 +243,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const int mt = tile % mtiles, nt = tile / mtiles;
   if (nt >= ntiles) return;
   if (lower_only && mt * kOzTileM + kOzTileM - 1 < nt * TN) return;
+  if (symcols > 0) {   // skip a column tile that lies wholly in the strict upper triangle
+    bool any = false;
+    for (int q = 0; q < TN && !any; ++q) {
+      const int n = nt * TN + q;
+      any = n < N && (n % symcols) <= (n / symcols);
+    }
+    if (!any) return;
+  }
   const int c0 = split * A.kb_chunks, c1 = min(c0 + A.kb_chunks, A.kchunks);
   if (c0 >= c1) return;
 
@@ -358,7 +366,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           double v = oz_to_double(acc[q], ea + eb - 2095);
           if (alpha != 1.0) v *= alpha;
           double* dst = C + cbase + (long long)n * cs_n;
-          if (atomic) atomicAdd(dst, v);
+          if (atomic == 1) atomicAdd(dst, v);
+          else if (atomic == 2) *dst += v;
           else *dst = v;
         }
       }
@@ -410,6 +419,7 @@ void oz_gemm(const LaCtx& la, const OzGemmArgs& g) {
   if (A.kb_chunks > kMaxChunksPerBlock)
     throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: K block longer than the int64 accumulator allows");
   if (!g.atomic && A.nkb > 1) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: K blocks need atomic output");
+  if (g.atomic && g.accumulate) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: atomic and accumulate");
   // column tile: the whole of N when it fits (multiple of 16), else 64 so that
   // no tile straddles a 128-row plane
   const int TN = g.N <= 64 ? (g.N + 15) / 16 * 16 : 64;
@@ -418,8 +428,8 @@ void oz_gemm(const LaCtx& la, const OzGemmArgs& g) {
   raise_smem_limit((const void*)oz_gemm_kernel, kSmemBytes);
   const long long nblocks = (long long)mtiles * ntiles * A.nkb;
   oz_gemm_kernel<<<(unsigned)nblocks, kOzThreads, kSmemBytes, la.stream>>>(
-      A, B, g.M, g.N, g.s, TN, mtiles, ntiles, A.nkb, g.lower_only ? 1 : 0, g.alpha, g.C, g.MR, g.cs_m1, g.cs_m2,
-      g.cs_n, g.atomic ? 1 : 0, la.flag);
+      A, B, g.M, g.N, g.s, TN, mtiles, ntiles, A.nkb, g.lower_only ? 1 : 0, g.symcols, g.alpha, g.C, g.MR, g.cs_m1,
+      g.cs_m2, g.cs_n, g.atomic ? 1 : (g.accumulate ? 2 : 0), la.flag);
   RIHF_LAUNCH_CHECK();
   if (la.launches) *la.launches += 1;
 }

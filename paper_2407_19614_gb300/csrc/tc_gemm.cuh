@@ -55,8 +55,11 @@ OzOperand oz_slice(const LaCtx& la, const double* X, int rows, int K, long long 
 
 // C(m, n) = alpha * sum_k A(m, k) B(n, k) using s <= min(A.smax, B.smax) digits.
 // Output element (m, n) at C[(m % MR) * cs_m1 + (m / MR) * cs_m2 + n * cs_n];
-// atomic: added with atomicAdd (C must be initialised), else stored.
+// atomic: added with atomicAdd (C must be initialised); accumulate: C += (one
+// writer per element: a single K block); else stored.
 // lower_only: only tiles that meet m >= n are computed (symmetric results).
+// symcols > 0: column tiles whose every column n has (n % symcols) > (n / symcols)
+// (strict upper triangle of a symcols x symcols slice flattened along n) are skipped.
 // All CTAs of a K split must share one exponent block: A.kb_chunks == B.kb_chunks
 // and the kernel runs one split per exponent block.  Sets la.flag[1] = 1 if a
 // bounded wait on the tensor core or the copy engine ran out (la.flag must
@@ -70,7 +73,9 @@ struct OzGemmArgs {
   long long MR = 1LL << 62;
   long long cs_m1 = 0, cs_m2 = 0, cs_n = 1;
   bool atomic = false;
+  bool accumulate = false;
   bool lower_only = false;
+  int symcols = 0;
 };
 void oz_gemm(const LaCtx& la, const OzGemmArgs& g);
 

@@ -71,3 +71,20 @@ def test_mixed_fixed_digit_counts_converge(digits):
     st = ctx.scf_stats()
     assert st["tc_builds"] >= 3
     assert abs(out["energy"] - r.E) <= 1e-6
+
+
+def test_tensor_core_fit_matches_fp64_fit():
+    # B = L^{-1} T with the rank-64 updates on the tensor cores (7 digits) against
+    # the FP64 substitution: the digits carry 55 bits of each row's largest
+    # element per 64-column block, so the two solves agree to near FP64
+    # rounding even through cond(L) ~ 5e4
+    R = _R()
+    mol = W.water8(0)
+    b64 = R.Context(mol).matrix("B")
+    bmx = R.Context(mol, precision=R.PRECISION_MIXED).matrix("B")
+    N = b64.shape[1]
+    il = np.tril_indices(N)
+    d = np.abs(bmx[:, il[0], il[1]] - b64[:, il[0], il[1]]).max()
+    scale = np.abs(b64).max()
+    print("\nmax |B_tc - B_fp64| = %.3e (max |B| = %.3e)" % (d, scale))
+    assert d <= 1e-10 * scale
