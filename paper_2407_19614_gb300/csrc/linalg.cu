@@ -348,7 +348,9 @@ constexpr int CB = 32;
 
 // Factor the b x b diagonal block at (k, k) of A (leading dim n) and write its
 // inverse into inv (CB x CB, lower).  One warp.
-__global__ void potrf_diag_kernel(double* A, int n, int k, int b, double* inv, int* flag, int factor) {
+// want_inv = 0 skips the block inverse (the Cholesky panel substitutes instead).
+__global__ void potrf_diag_kernel(double* A, int n, int k, int b, double* inv, int* flag, int factor,
+                                  int want_inv = 1) {
   __shared__ double a[CB][CB + 1];
   __shared__ double li[CB][CB + 1];
   int lane = threadIdx.x;
@@ -371,6 +373,12 @@ __global__ void potrf_diag_kernel(double* A, int n, int k, int b, double* inv, i
         for (int c = j + 1; c <= lane; ++c) a[lane][c] -= a[lane][j] * a[c][j];
       __syncwarp();
     }
+  }
+  if (!want_inv) {
+    if (factor)
+      for (int i = 0; i < b; ++i)
+        if (lane < b) A[(size_t)(k + i) * n + k + lane] = lane <= i ? a[i][lane] : 0.0;
+    return;
   }
   // inverse of the lower factor, column `lane`
   for (int i = 0; i < CB; ++i) li[i][lane] = 0.0;
@@ -431,7 +439,7 @@ __global__ void __launch_bounds__(256) chol_panel_kernel(double* A, int n, int k
 void cholesky(const LaCtx& la, double* A, int n, double* scratch) {
   for (int k = 0; k < n; k += CB) {
     int b = std::min(CB, n - k);
-    potrf_diag_kernel<<<1, 32, 0, la.stream>>>(A, n, k, b, scratch, la.flag, 1);
+    potrf_diag_kernel<<<1, 32, 0, la.stream>>>(A, n, k, b, scratch, la.flag, 1, 0);
     RIHF_LAUNCH_CHECK();
     count(la);
     int rest = n - k - b;
@@ -929,7 +937,7 @@ __global__ void eig_sort64_kernel(const double* __restrict__ V, const double* __
 }
 
 void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double* ws, int refine,
-          const double* Vguess, bool skip_jacobi) {
+          const double* Vguess, bool skip_jacobi, int max_sweeps) {
   int m = n + (n & 1);
   if (skip_jacobi && Vguess && refine > 0) {
     // Late SCF iterations: the previous eigenvectors are already close, so the
@@ -979,7 +987,7 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
   // a looser stop (n eps) leaves close clusters too coarse for the FP64
   // refinement to separate
   const float tol = 2e-6f;
-  jacobi1s_kernel<<<1, JT, use_smem ? smem : 0, la.stream>>>(Ain, n, m, fA, fV, fW, use_smem, 20, tol);
+  jacobi1s_kernel<<<1, JT, use_smem ? smem : 0, la.stream>>>(Ain, n, m, fA, fV, fW, use_smem, max_sweeps, tol);
   RIHF_LAUNCH_CHECK();
   count(la);
   eig_sort_kernel<<<1, 1024, 0, la.stream>>>(fV, fW, n, m, V, W);

@@ -1002,7 +1002,10 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
     const bool skip = use_prev && c->last_err < 1e-2;
     {
       TraceScope t(c->tracer, c->stream, skip ? "eigh F' (refine only)" : "eigh F' (jacobi+refine)", 0.0, 0);
-      eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, use_prev ? c->Cprev : nullptr, skip);
+      // warm-started iterations: three Jacobi sweeps (from the previous
+      // vectors); their eigenvectors only need the accuracy of the SCF iterate
+      const int sweeps = use_prev ? 3 : 20;
+      eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, use_prev ? c->Cprev : nullptr, skip, sweeps);
     }
     if (skip) {
       // guard: the refinement from the previous vectors must end orthonormal;
