@@ -455,6 +455,10 @@ struct rihf_ctx {
   int *Bex = nullptr, *Cex = nullptr, *Hex = nullptr;
   OzOperand Bop;
   TrsmTcScratch trsm_sc;          // tensor-core fit (mixed mode)
+  // tensor-core gradient GEMMs (mixed mode): planes of C~ as a B operand
+  // (rows N, K = nocc), of G' (rows Naux N, K = nocc) and of X~ (rows Naux, K = nocc^2)
+  uint16_t *Ctpl = nullptr, *Gpl = nullptr, *Xpl = nullptr;
+  int *Ctex = nullptr, *Gex = nullptr, *Xex = nullptr;
   int tc_builds = 0, last_iters = 0, last_digits = 0;
   double flops_eri3 = 0.0, flops_grad3 = 0.0;   // algorithmic FP64 operations of the 3-centre kernels
   int k_nsplit = 0;             // K splits of the tensor-core K GEMM (0: not tuned yet)
@@ -577,6 +581,7 @@ static void free_all(rihf_ctx* c) {
   void* ptrs[] = {c->d_pl, c->d_patom, c->d_pnprim, c->d_pps, c->d_pao, c->d_pxyz, c->d_pexp, c->d_pcoef,
                   c->d_al, c->d_aatom, c->d_anprim, c->d_aps, c->d_aao, c->d_axyz_sh, c->d_aexp, c->d_acoef,
                   c->d_piexp, c->d_aiexp, c->d_pp_off, c->d_pp, c->trsm_sc.planes_L, c->trsm_sc.exps_L,
+                  c->Ctpl, c->Gpl, c->Xpl, c->Ctex, c->Gex, c->Xex,
                   c->trsm_sc.planes_X, c->trsm_sc.exps_X,
                   c->d_ao_atom, c->d_ao_l, c->hist_D[0], c->hist_D[1], c->hist_D[2], c->hist_S, c->hist_xyz[0],
                   c->hist_xyz[1], c->Dpred, c->mlX, c->mly, c->mlt, c->mlDx, c->ml_sums, c->rep_X, c->rep_t, c->net.master, c->net.wbf, c->net.grad,
@@ -931,6 +936,13 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
       c->trsm_sc.exps_L = dalloc<int>(oz_plane_elems(NA, 1, 1) / kOzChunk);
       c->trsm_sc.planes_X = dalloc<uint16_t>(oz_plane_elems(N * N, kOzChunk, kOzMaxDigits));
       c->trsm_sc.exps_X = dalloc<int>(oz_plane_elems(N * N, 1, 1) / kOzChunk);
+      const int no = c->nocc;
+      c->Ctpl = dalloc<uint16_t>(oz_plane_elems(N, no, kOzMaxDigits));
+      c->Ctex = dalloc<int>(oz_plane_elems(N, 1, 1) / kOzChunk);
+      c->Gpl = dalloc<uint16_t>(oz_plane_elems(NA * N, no, kOzMaxDigits));
+      c->Gex = dalloc<int>(oz_plane_elems(NA * N, 1, 1) / kOzChunk);
+      c->Xpl = dalloc<uint16_t>(oz_plane_elems(NA, no * no, kOzMaxDigits));
+      c->Xex = dalloc<int>(oz_plane_elems(NA, 1, 1) / kOzChunk);
     }
     c->trsm_tmp = dalloc<double>(32 * std::max<size_t>({n2, (size_t)NA, (size_t)c->nocc * c->nocc}) + 1024);
     {   // guess history and learned-guess buffers
@@ -1035,8 +1047,10 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
       if (!(dev[0] < 1e-8) || !(dev[1] < offd_tol)) {
         if (c->verbose || getenv("RIHF_VERBOSE"))
           fprintf(stderr, "rihf: refine-only eigh deviation %.3e, off-diagonal %.3e, redo\n", dev[0], dev[1]);
+        // warm-started from near-converged vectors: three Jacobi sweeps reach
+        // the FP32 floor, the four FP64 refinement steps the rest
         TraceScope t(c->tracer, c->stream, "eigh F' (jacobi redo)", 0.0, 0);
-        eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, c->Cprev, false);
+        eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 4, c->Cprev, false, 3);
       }
     }
   }
@@ -1558,9 +1572,20 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   RIHF_CUDA(cudaMemcpyAsync(c->cvec, c->dvec, sizeof(double) * NA, cudaMemcpyDeviceToDevice, s));
   trsm_lower(la, c->L, NA, c->cvec, 1, true, 0, c->trsm_tmp);
   // Hb[P] = B^P Ct ; Bij[P] = Ct^T Hb[P]
-  GemmArgs gh;
-  gh.M = NA * N; gh.N = no; gh.K = N; gh.A = c->B; gh.lda = N; gh.B = c->Ct; gh.ldb = no; gh.C = c->Hb; gh.ldc = no;
-  dgemm(la, gh);
+  const bool tc = c->Gpl != nullptr;   // mixed mode: 7-digit tensor-core GEMMs (FP64-class products)
+  if (tc) {
+    TraceScope t(c->tracer, s, "grad H=B C~ (tcgen05 7 digits)", 0.0, 0);
+    OzOperand Cop = oz_slice(la, c->Ct, no, N, 1, no, 0, N, kOzMaxDigits, 0, c->Cpl, c->Cex);
+    OzGemmArgs g1;
+    g1.A = c->Bop; g1.B = Cop; g1.M = NA * N; g1.N = no; g1.s = kOzMaxDigits; g1.C = c->Hb; g1.cs_m1 = no;
+    g1.cs_n = 1;
+    oz_gemm(la, g1);
+  } else {
+    GemmArgs gh;
+    gh.M = NA * N; gh.N = no; gh.K = N; gh.A = c->B; gh.lda = N; gh.B = c->Ct; gh.ldb = no; gh.C = c->Hb;
+    gh.ldc = no;
+    dgemm(la, gh);
+  }
   GemmArgs gb;
   gb.M = no; gb.N = no; gb.K = N; gb.A = c->Ct; gb.lda = no; gb.transA = true;
   gb.B = c->Hb; gb.ldb = no; gb.sB = (long long)N * no; gb.C = c->Bij; gb.ldc = no; gb.sC = (long long)no * no;
@@ -1570,27 +1595,54 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   RIHF_CUDA(cudaMemcpyAsync(c->Xt, c->Bij, sizeof(double) * (size_t)NA * no * no, cudaMemcpyDeviceToDevice, s));
   trsm_lower(la, c->L, NA, c->Xt, (long long)no * no, true, 0, c->trsm_tmp);
   // Z = c c^T - 1/2 Xt Xt^T
-  GemmArgs gz;
-  gz.M = NA; gz.N = NA; gz.K = no * no; gz.A = c->Xt; gz.lda = no * no; gz.B = c->Xt; gz.ldb = no * no;
-  gz.transB = true; gz.C = c->Zm; gz.ldc = NA; gz.alpha = -0.5;
-  gz.lower_only = true;   // Z is symmetric
-  dgemm(la, gz);
+  if (tc && (no * no + kOzChunk - 1) / kOzChunk <= 30) {
+    TraceScope t(c->tracer, s, "grad Z=-1/2 X X^T (tcgen05 7 digits)", 0.0, 0);
+    OzOperand Xop = oz_slice(la, c->Xt, NA, no * no, (long long)no * no, 1, 0, no * no, kOzMaxDigits, 0, c->Xpl,
+                             c->Xex);
+    OzGemmArgs gz;
+    gz.A = Xop; gz.B = Xop; gz.M = NA; gz.N = NA; gz.s = kOzMaxDigits; gz.alpha = -0.5; gz.C = c->Zm;
+    gz.cs_m1 = NA; gz.cs_n = 1; gz.lower_only = true;
+    oz_gemm(la, gz);
+  } else {
+    GemmArgs gz;
+    gz.M = NA; gz.N = NA; gz.K = no * no; gz.A = c->Xt; gz.lda = no * no; gz.B = c->Xt; gz.ldb = no * no;
+    gz.transB = true; gz.C = c->Zm; gz.ldc = NA; gz.alpha = -0.5;
+    gz.lower_only = true;   // Z is symmetric
+    dgemm(la, gz);
+  }
   GemmArgs gc;
   gc.M = NA; gc.N = NA; gc.K = 1; gc.A = c->cvec; gc.lda = 1; gc.B = c->cvec; gc.ldb = NA; gc.C = c->Zm; gc.ldc = NA;
   gc.beta = 1.0;
   dgemm(la, gc);
   symmetrize_lower(la, c->Zm, NA, 1);
-  // Y[P] = D c_P - 1/2 Ct Xt[P] Ct^T ; G[P] = Xt[P] Ct^T (nocc x N)
-  GemmArgs gg;
-  gg.M = no; gg.N = N; gg.K = no; gg.A = c->Xt; gg.lda = no; gg.sA = (long long)no * no;
-  gg.B = c->Ct; gg.ldb = no; gg.transB = true; gg.C = c->G; gg.ldc = N; gg.sC = (long long)no * N; gg.batch = NA;
-  dgemm(la, gg);
+  // Y[P] = D c_P - 1/2 Ct Xt[P] Ct^T
   outer_fill(la, c->cvec, NA, c->D, (long long)n2, c->Y);
-  GemmArgs gy;
-  gy.M = N; gy.N = N; gy.K = no; gy.A = c->Ct; gy.lda = no; gy.B = c->G; gy.ldb = N; gy.sB = (long long)no * N;
-  gy.C = c->Y; gy.ldc = N; gy.sC = (long long)n2; gy.batch = NA; gy.alpha = -0.5; gy.beta = 1.0;
-  { TraceScope t(c->tracer, s, "grad Y=Dc-1/2 C~XC~^T (dgemm)", 2.0 * NA * n2 * no, 0);
-    dgemm(la, gy); }
+  if (tc) {
+    // G'[P] = Ct Xt[P] (N x nocc, Xt[P] symmetric), then one GEMM over rows
+    // (P, mu): Y[(P, mu)][nu] += -1/2 sum_i G'[(P, mu)][i] Ct[nu][i]
+    GemmArgs gg;
+    gg.M = N; gg.N = no; gg.K = no; gg.A = c->Ct; gg.lda = no; gg.B = c->Xt; gg.ldb = no;
+    gg.sB = (long long)no * no; gg.C = c->G; gg.ldc = no; gg.sC = (long long)N * no; gg.batch = NA;
+    dgemm(la, gg);
+    TraceScope t(c->tracer, s, "grad Y=Dc-1/2 C~XC~^T (tcgen05 7 digits)", 0.0, 0);
+    OzOperand Gop = oz_slice(la, c->G, NA * N, no, no, 1, 0, no, kOzMaxDigits, 0, c->Gpl, c->Gex);
+    OzOperand Top = oz_slice(la, c->Ct, N, no, no, 1, 0, no, kOzMaxDigits, 0, c->Ctpl, c->Ctex);
+    OzGemmArgs gy;
+    gy.A = Gop; gy.B = Top; gy.M = NA * N; gy.N = N; gy.s = kOzMaxDigits; gy.alpha = -0.5; gy.C = c->Y;
+    gy.cs_m1 = N; gy.cs_n = 1; gy.accumulate = true;
+    oz_gemm(la, gy);
+  } else {
+    // G[P] = Xt[P] Ct^T (nocc x N)
+    GemmArgs gg;
+    gg.M = no; gg.N = N; gg.K = no; gg.A = c->Xt; gg.lda = no; gg.sA = (long long)no * no;
+    gg.B = c->Ct; gg.ldb = no; gg.transB = true; gg.C = c->G; gg.ldc = N; gg.sC = (long long)no * N; gg.batch = NA;
+    dgemm(la, gg);
+    GemmArgs gy;
+    gy.M = N; gy.N = N; gy.K = no; gy.A = c->Ct; gy.lda = no; gy.B = c->G; gy.ldb = N; gy.sB = (long long)no * N;
+    gy.C = c->Y; gy.ldc = N; gy.sC = (long long)n2; gy.batch = NA; gy.alpha = -0.5; gy.beta = 1.0;
+    TraceScope t(c->tracer, s, "grad Y=Dc-1/2 C~XC~^T (dgemm)", 2.0 * NA * n2 * no, 0);
+    dgemm(la, gy);
+  }
   // fused derivative-integral contractions
   RIHF_CUDA(cudaMemsetAsync(c->grad_parts, 0, sizeof(double) * 15 * nat, s));
   double* g_one = c->grad_parts;
