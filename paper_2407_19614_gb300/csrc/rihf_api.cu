@@ -467,7 +467,9 @@ struct rihf_ctx {
   struct IterGraph {
     cudaGraphExec_t exec = nullptr;
     long long launches = 0;
+    long long uses = 0;
   } graphs[kOzMaxDigits + 1];
+  IterGraph diag_graphs[4];   // diagonalisation: [refine-only, warm Jacobi] x [F, extrapolated F]
   bool graphs_ok = true;
 
   // learned / extrapolated guess: the last three converged densities, the
@@ -715,11 +717,14 @@ static void compute_geometry(rihf_ctx* c) {
   int nind = N - k0;
   if (c->nind != 0 && nind != c->nind) {
     c->have_cprev = false;
-    for (auto& g : c->graphs)   // captured iterations assume the old basis size
-      if (g.exec) {
-        cudaGraphExecDestroy(g.exec);
-        g.exec = nullptr;
-      }
+    for (auto* arr : {c->graphs, c->diag_graphs}) {   // captured work assumes the old basis size
+      const int cnt = arr == c->graphs ? kOzMaxDigits + 1 : 4;
+      for (int i = 0; i < cnt; ++i)
+        if (arr[i].exec) {
+          cudaGraphExecDestroy(arr[i].exec);
+          arr[i].exec = nullptr;
+        }
+    }
   }
   c->nind = nind;
   if (chol_ok) {
@@ -995,38 +1000,100 @@ int rihf_update_geometry(rihf_ctx* c, const double* xyz) {
 }
 
 // Orbitals from a Fock matrix: F' = Xo^T F Xo, eigh, C = Xo C'.
+// Runs `body` (work on the context stream only, no host synchronisation) from
+// the CUDA graph in g, capturing it on its second use (the first runs eagerly,
+// so one-time set-up such as kernel attributes happens outside a capture);
+// eagerly when graphs are off or a capture fails.  Trace events are not
+// captured; the replay is traced as one entry named `name`.
+extern "C++" {
+template <class Body>
+static void graph_or_eager(rihf_ctx* c, rihf_ctx::IterGraph& g, const char* name, Body&& body) {
+  if (!c->opt.cuda_graphs || !c->graphs_ok || g.uses++ == 0) {
+    TraceScope t(c->tracer, c->stream, name, 0.0, 0);
+    body();
+    return;
+  }
+  if (!g.exec) {
+    const long long l0 = c->launches;
+    const bool tr = c->tracer.on;
+    c->tracer.on = false;
+    RIHF_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t graph = nullptr;
+    try {
+      body();
+    } catch (...) {
+      cudaStreamEndCapture(c->stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      c->launches = l0;
+      c->graphs_ok = false;
+      c->tracer.on = tr;
+      TraceScope t(c->tracer, c->stream, name, 0.0, 0);
+      body();
+      return;
+    }
+    c->tracer.on = tr;
+    RIHF_CUDA(cudaStreamEndCapture(c->stream, &graph));
+    const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    g.launches = c->launches - l0;
+    c->launches = l0;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g.exec = nullptr;
+      c->graphs_ok = false;
+      TraceScope t(c->tracer, c->stream, name, 0.0, 0);
+      body();
+      return;
+    }
+  }
+  TraceScope t(c->tracer, c->stream, name, 0.0, 0);
+  RIHF_CUDA(cudaGraphLaunch(g.exec, c->stream));
+  c->launches += g.launches;
+}
+}  // extern "C++"
+
 static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
   LaCtx la = c->la();
   const int N = c->N, n = c->nind;
-  GemmArgs g1;   // T1 (N x n) = F Xo
-  g1.M = N; g1.N = n; g1.K = N; g1.A = Fin; g1.lda = N; g1.B = c->Xo; g1.ldb = n; g1.C = c->T1; g1.ldc = n;
-  dgemm(la, g1);
-  GemmArgs g2;   // Fp (n x n) = Xo^T T1
-  g2.M = n; g2.N = n; g2.K = N; g2.A = c->Xo; g2.lda = n; g2.transA = true; g2.B = c->T1; g2.ldb = n;
-  g2.C = c->Fp; g2.ldc = n;
-  dgemm(la, g2);
-  RIHF_CUDA(cudaMemsetAsync(c->eps, 0, sizeof(double) * N, c->stream));
-  {
-    // refinement from the previous eigenvectors once the SCF error is moderate;
-    // the guard below falls back to a Jacobi pass unless the refined vectors
-    // are orthonormal and diagonalise F'
-    const bool use_prev = warm && c->have_cprev;
-    const bool skip = use_prev && c->last_err < 1e-2;
-    {
-      TraceScope t(c->tracer, c->stream, skip ? "eigh F' (refine only)" : "eigh F' (jacobi+refine)", 0.0, 0);
-      // warm-started iterations: three Jacobi sweeps (from the previous
-      // vectors); their eigenvectors only need the accuracy of the SCF iterate
-      const int sweeps = use_prev ? 3 : 20;
-      eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, use_prev ? c->Cprev : nullptr, skip, sweeps);
-    }
-    if (skip) {
-      // guard: the refinement from the previous vectors must end orthonormal;
-      // otherwise redo the step with a Jacobi pass
+  // refinement from the previous eigenvectors once the SCF error is moderate;
+  // the guard below falls back to a Jacobi pass unless the refined vectors
+  // are orthonormal and diagonalise F'
+  const bool use_prev = warm && c->have_cprev;
+  const bool skip = use_prev && c->last_err < 1e-2;
+  auto form_fp = [&]() {
+    GemmArgs g1;   // T1 (N x n) = F Xo
+    g1.M = N; g1.N = n; g1.K = N; g1.A = Fin; g1.lda = N; g1.B = c->Xo; g1.ldb = n; g1.C = c->T1; g1.ldc = n;
+    dgemm(la, g1);
+    GemmArgs g2;   // Fp (n x n) = Xo^T T1
+    g2.M = n; g2.N = n; g2.K = N; g2.A = c->Xo; g2.lda = n; g2.transA = true; g2.B = c->T1; g2.ldb = n;
+    g2.C = c->Fp; g2.ldc = n;
+    dgemm(la, g2);
+    RIHF_CUDA(cudaMemsetAsync(c->eps, 0, sizeof(double) * N, c->stream));
+  };
+  if (!use_prev) {
+    // cold start: a full Jacobi pass, not replayed
+    form_fp();
+    TraceScope t(c->tracer, c->stream, "eigh F' (jacobi+refine)", 0.0, 0);
+    eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, nullptr, false, 20);
+  } else if (!skip) {
+    // warm-started iterations: three Jacobi sweeps (from the previous
+    // vectors); their eigenvectors only need the accuracy of the SCF iterate
+    graph_or_eager(c, c->diag_graphs[2 + (Fin == c->F ? 0 : 1)], "eigh F' (jacobi+refine)", [&]() {
+      form_fp();
+      eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, c->Cprev, false, 3);
+    });
+  } else {
+    graph_or_eager(c, c->diag_graphs[Fin == c->F ? 0 : 1], "eigh F' (refine only)", [&]() {
+      form_fp();
+      eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, c->Cprev, true, 20);
+      // guard: orthonormality and the off-diagonal of Cp^T F' Cp
       GemmArgs go;   // T2 = Cp^T Cp
       go.M = n; go.N = n; go.K = n; go.A = c->Cp; go.lda = n; go.transA = true; go.B = c->Cp; go.ldb = n;
       go.C = c->T2; go.ldc = n;
       dgemm(la, go);
       eig_check_kernel<<<1, 1024, 0, c->stream>>>(c->T2, n, 1.0, 0, c->scal + 2);
+      RIHF_LAUNCH_CHECK();
       GemmArgs gf;   // T1 = F' Cp, T2 = Cp^T T1
       gf.M = n; gf.N = n; gf.K = n; gf.A = c->Fp; gf.lda = n; gf.B = c->Cp; gf.ldb = n; gf.C = c->T1; gf.ldc = n;
       dgemm(la, gf);
@@ -1037,21 +1104,21 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
       eig_check_kernel<<<1, 1024, 0, c->stream>>>(c->T2, n, 0.0, 1, c->scal + 3);
       RIHF_LAUNCH_CHECK();
       c->launches += 2;
-      double dev[2] = {0.0, 0.0};
-      RIHF_CUDA(cudaMemcpyAsync(dev, c->scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      RIHF_CUDA(cudaStreamSynchronize(c->stream));
-      // eigenvector errors of the order of the SCF error do not slow the SCF
-      // (the refined vectors typically leave |C^T F' C|_offdiag ~ max|e|); the
-      // guard only catches a refinement that went astray
-      const double offd_tol = std::max(1e-8, 10.0 * c->last_err);
-      if (!(dev[0] < 1e-8) || !(dev[1] < offd_tol)) {
-        if (c->verbose || getenv("RIHF_VERBOSE"))
-          fprintf(stderr, "rihf: refine-only eigh deviation %.3e, off-diagonal %.3e, redo\n", dev[0], dev[1]);
-        // warm-started from near-converged vectors: three Jacobi sweeps reach
-        // the FP32 floor, the four FP64 refinement steps the rest
-        TraceScope t(c->tracer, c->stream, "eigh F' (jacobi redo)", 0.0, 0);
-        eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 4, c->Cprev, false, 3);
-      }
+    });
+    double dev[2] = {0.0, 0.0};
+    RIHF_CUDA(cudaMemcpyAsync(dev, c->scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    RIHF_CUDA(cudaStreamSynchronize(c->stream));
+    // eigenvector errors of the order of the SCF error do not slow the SCF
+    // (the refined vectors typically leave |C^T F' C|_offdiag ~ max|e|); the
+    // guard only catches a refinement that went astray
+    const double offd_tol = std::max(1e-8, 10.0 * c->last_err);
+    if (!(dev[0] < 1e-8) || !(dev[1] < offd_tol)) {
+      if (c->verbose || getenv("RIHF_VERBOSE"))
+        fprintf(stderr, "rihf: refine-only eigh deviation %.3e, off-diagonal %.3e, redo\n", dev[0], dev[1]);
+      // warm-started from near-converged vectors: three Jacobi sweeps reach
+      // the FP32 floor, the four FP64 refinement steps the rest
+      TraceScope t(c->tracer, c->stream, "eigh F' (jacobi redo)", 0.0, 0);
+      eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 4, c->Cprev, false, 3);
     }
   }
   RIHF_CUDA(cudaMemcpyAsync(c->Cprev, c->Cp, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, c->stream));
@@ -2091,6 +2158,8 @@ void rihf_destroy(rihf_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto& g : c->diag_graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   free_all(c);
   for (auto& e : c->ev) cudaEventDestroy(e);
