@@ -927,7 +927,7 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     c->scal = dalloc<double>(8);
     c->cvec = dalloc<double>(NA); c->W = dalloc<double>(n2);
     c->Bij = dalloc<double>((size_t)NA * c->nocc * c->nocc);
-    c->Xt = dalloc<double>((size_t)NA * c->nocc * c->nocc);
+    c->Xt = dalloc<double>((size_t)NA * (c->nocc * c->nocc + 1));   // [X~ | c] per row P
     c->Zm = dalloc<double>(na2);
     c->na2tmp = dalloc<double>(na2);
     c->G = dalloc<double>((size_t)NA * c->nocc * N);
@@ -1414,6 +1414,7 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   const size_t n2 = (size_t)N * N;
   cudaStream_t s = c->stream;
   c->timings[1] = c->timings[2] = 0.0;
+  cudaEventRecord(c->ev[7], s);   // SCF start (diagonalisation time = total - builds)
   if (guess == 1) {
     if (!C_guess) return RIHF_ERR_INVALID_ARG;
     RIHF_CUDA(cudaMemcpyAsync(c->C, C_guess, sizeof(double) * n2, cudaMemcpyHostToDevice, s));
@@ -1546,6 +1547,8 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
     double sc[2];
     RIHF_CUDA(cudaMemcpyAsync(sc, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     RIHF_CUDA(cudaStreamSynchronize(s));
+    cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);   // both recorded before the sync
+    c->timings[1] += ms;
     E = sc[0];
     emax = sc[1];
     c->prev_err = c->last_err;
@@ -1565,30 +1568,26 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
     }
     if (crit && full) {
       conv = true;
-      cudaEventRecord(c->ev[4], s);
-      cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
-      c->timings[1] += ms;
       break;
     }
     Eold = E;
-    diis_dots_kernel<<<m, 256, 0, s>>>(c->Ering, (long long)n * n, slot, m, c->Bdiis, 16);
-    RIHF_LAUNCH_CHECK();
     const double* Fuse = c->F;
-    if (m >= 2) {
-      diis_solve_kernel<<<1, 32, 0, s>>>(c->Bdiis, 16, m, c->coef);
-      diis_extrap_kernel<<<std::max(1, std::min(ceil_div((long long)n2, 256), 8 * c->sms)), 256, 0, s>>>(
-          c->Fring, (long long)n2, m, c->coef, c->Fx);
+    {
+      TraceScope t(c->tracer, s, "DIIS (dots, solve, extrapolation)", 0.0, 0);
+      diis_dots_kernel<<<m, 256, 0, s>>>(c->Ering, (long long)n * n, slot, m, c->Bdiis, 16);
       RIHF_LAUNCH_CHECK();
-      Fuse = c->Fx;
+      if (m >= 2) {
+        diis_solve_kernel<<<1, 32, 0, s>>>(c->Bdiis, 16, m, c->coef);
+        diis_extrap_kernel<<<std::max(1, std::min(ceil_div((long long)n2, 256), 8 * c->sms)), 256, 0, s>>>(
+            c->Fring, (long long)n2, m, c->coef, c->Fx);
+        RIHF_LAUNCH_CHECK();
+        Fuse = c->Fx;
+      }
     }
     c->launches += 3;
+    // no host synchronisation here: the next Fock build queues behind the
+    // diagonalisation on the stream
     diagonalise(c, Fuse, true);
-    cudaEventRecord(c->ev[4], s);
-    RIHF_CUDA(cudaEventSynchronize(c->ev[4]));
-    cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
-    c->timings[1] += ms;
-    cudaEventElapsedTime(&ms, c->ev[3], c->ev[4]);
-    c->timings[2] += ms;
   }
   if (it > c->opt.max_iter) it = c->opt.max_iter;
   // final orbitals diagonalise the last (unextrapolated) Fock matrix
@@ -1597,7 +1596,10 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   c->have_orbitals = true;
   int tc_flag = 0;
   RIHF_CUDA(cudaMemcpyAsync(&tc_flag, c->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  cudaEventRecord(c->ev[4], s);
   RIHF_CUDA(cudaStreamSynchronize(s));
+  cudaEventElapsedTime(&ms, c->ev[7], c->ev[4]);
+  c->timings[2] = std::max(0.0, (double)ms - c->timings[1]);
   c->tracer.flush();
   if (tc_flag) throw RihfError(RIHF_ERR_TIMEOUT, "tensor-core RI-K: a bounded device wait ran out");
   if (conv) learn_and_push_history(c);
@@ -1643,10 +1645,10 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   gw.M = N; gw.N = N; gw.K = N; gw.A = c->D; gw.lda = N; gw.B = c->T2; gw.ldb = N; gw.C = c->W; gw.ldc = N;
   gw.alpha = 0.5;
   dgemm(la, gw);
-  // c = L^{-T} (B vec D)   (the paper's L^P)
-  gemv_rows(la, c->B, NA, (long long)n2, c->D, 1.0, c->dvec);
-  RIHF_CUDA(cudaMemcpyAsync(c->cvec, c->dvec, sizeof(double) * NA, cudaMemcpyDeviceToDevice, s));
-  trsm_lower(la, c->L, NA, c->cvec, 1, true, 0, c->trsm_tmp);
+  // d = B vec D; c = L^{-T} d (the paper's L^P) is solved below together with X~
+  { TraceScope t(c->tracer, s, "grad d = B D (gemv_rows)", (double)NA * n2 * 8, 1);
+    gemv_rows(la, c->B, NA, (long long)n2, c->D, 1.0, c->dvec); }
+  const long long ldx = (long long)no * no + 1;   // row P of Xt: X~^P (nocc^2) then c_P
   // Hb[P] = B^P Ct ; Bij[P] = Ct^T Hb[P]
   const bool tc = c->Gpl != nullptr;   // mixed mode: 7-digit tensor-core GEMMs (FP64-class products)
   if (tc) {
@@ -1662,18 +1664,26 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
     gh.ldc = no;
     dgemm(la, gh);
   }
-  GemmArgs gb;
-  gb.M = no; gb.N = no; gb.K = N; gb.A = c->Ct; gb.lda = no; gb.transA = true;
-  gb.B = c->Hb; gb.ldb = no; gb.sB = (long long)N * no; gb.C = c->Bij; gb.ldc = no; gb.sC = (long long)no * no;
-  gb.batch = NA;
-  dgemm(la, gb);
-  // Xt = L^{-T} Bij  (NA x nocc^2): the paper's X^P_ij = sum_Q A^L_PQ B^Q_ij
-  RIHF_CUDA(cudaMemcpyAsync(c->Xt, c->Bij, sizeof(double) * (size_t)NA * no * no, cudaMemcpyDeviceToDevice, s));
-  trsm_lower(la, c->L, NA, c->Xt, (long long)no * no, true, 0, c->trsm_tmp);
+  { TraceScope t(c->tracer, s, "grad Bij = C~^T H (batched dgemm)", 2.0 * NA * N * no * no, 0);
+    GemmArgs gb;
+    gb.M = no; gb.N = no; gb.K = N; gb.A = c->Ct; gb.lda = no; gb.transA = true;
+    gb.B = c->Hb; gb.ldb = no; gb.sB = (long long)N * no; gb.C = c->Bij; gb.ldc = no; gb.sC = (long long)no * no;
+    gb.batch = NA;
+    dgemm(la, gb); }
+  // [X~ | c] = L^{-T} [Bij | d]  (NA x (nocc^2 + 1)): the paper's X^P_ij = sum_Q A^L_PQ B^Q_ij
+  // and L^P in one blocked solve (the solve is latency-bound, one extra column is free)
+  { TraceScope t(c->tracer, s, "grad [X | c] = L^-T [Bij | d] (trsm)", (double)NA * NA * ldx, 0);
+    RIHF_CUDA(cudaMemcpy2DAsync(c->Xt, ldx * sizeof(double), c->Bij, (size_t)no * no * sizeof(double),
+                                (size_t)no * no * sizeof(double), NA, cudaMemcpyDeviceToDevice, s));
+    RIHF_CUDA(cudaMemcpy2DAsync(c->Xt + (size_t)no * no, ldx * sizeof(double), c->dvec, sizeof(double),
+                                sizeof(double), NA, cudaMemcpyDeviceToDevice, s));
+    trsm_lower(la, c->L, NA, c->Xt, ldx, true, 0, c->trsm_tmp);
+    RIHF_CUDA(cudaMemcpy2DAsync(c->cvec, sizeof(double), c->Xt + (size_t)no * no, ldx * sizeof(double),
+                                sizeof(double), NA, cudaMemcpyDeviceToDevice, s)); }
   // Z = c c^T - 1/2 Xt Xt^T
   if (tc && (no * no + kOzChunk - 1) / kOzChunk <= 30) {
     TraceScope t(c->tracer, s, "grad Z=-1/2 X X^T (tcgen05 7 digits)", 0.0, 0);
-    OzOperand Xop = oz_slice(la, c->Xt, NA, no * no, (long long)no * no, 1, 0, no * no, kOzMaxDigits, 0, c->Xpl,
+    OzOperand Xop = oz_slice(la, c->Xt, NA, no * no, ldx, 1, 0, no * no, kOzMaxDigits, 0, c->Xpl,
                              c->Xex);
     OzGemmArgs gz;
     gz.A = Xop; gz.B = Xop; gz.M = NA; gz.N = NA; gz.s = kOzMaxDigits; gz.alpha = -0.5; gz.C = c->Zm;
@@ -1681,7 +1691,7 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
     oz_gemm(la, gz);
   } else {
     GemmArgs gz;
-    gz.M = NA; gz.N = NA; gz.K = no * no; gz.A = c->Xt; gz.lda = no * no; gz.B = c->Xt; gz.ldb = no * no;
+    gz.M = NA; gz.N = NA; gz.K = no * no; gz.A = c->Xt; gz.lda = (int)ldx; gz.B = c->Xt; gz.ldb = (int)ldx;
     gz.transB = true; gz.C = c->Zm; gz.ldc = NA; gz.alpha = -0.5;
     gz.lower_only = true;   // Z is symmetric
     dgemm(la, gz);
@@ -1696,10 +1706,11 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   if (tc) {
     // G'[P] = Ct Xt[P] (N x nocc, Xt[P] symmetric), then one GEMM over rows
     // (P, mu): Y[(P, mu)][nu] += -1/2 sum_i G'[(P, mu)][i] Ct[nu][i]
-    GemmArgs gg;
-    gg.M = N; gg.N = no; gg.K = no; gg.A = c->Ct; gg.lda = no; gg.B = c->Xt; gg.ldb = no;
-    gg.sB = (long long)no * no; gg.C = c->G; gg.ldc = no; gg.sC = (long long)N * no; gg.batch = NA;
-    dgemm(la, gg);
+    { TraceScope t(c->tracer, s, "grad G' = C~ X (batched dgemm)", 2.0 * NA * N * no * no, 0);
+      GemmArgs gg;
+      gg.M = N; gg.N = no; gg.K = no; gg.A = c->Ct; gg.lda = no; gg.B = c->Xt; gg.ldb = no;
+      gg.sB = ldx; gg.C = c->G; gg.ldc = no; gg.sC = (long long)N * no; gg.batch = NA;
+      dgemm(la, gg); }
     TraceScope t(c->tracer, s, "grad Y=Dc-1/2 C~XC~^T (tcgen05 7 digits)", 0.0, 0);
     OzOperand Gop = oz_slice(la, c->G, NA * N, no, no, 1, 0, no, kOzMaxDigits, 0, c->Gpl, c->Gex);
     OzOperand Top = oz_slice(la, c->Ct, N, no, no, 1, 0, no, kOzMaxDigits, 0, c->Ctpl, c->Ctex);
@@ -1710,7 +1721,7 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   } else {
     // G[P] = Xt[P] Ct^T (nocc x N)
     GemmArgs gg;
-    gg.M = no; gg.N = N; gg.K = no; gg.A = c->Xt; gg.lda = no; gg.sA = (long long)no * no;
+    gg.M = no; gg.N = N; gg.K = no; gg.A = c->Xt; gg.lda = no; gg.sA = ldx;
     gg.B = c->Ct; gg.ldb = no; gg.transB = true; gg.C = c->G; gg.ldc = N; gg.sC = (long long)no * N; gg.batch = NA;
     dgemm(la, gg);
     GemmArgs gy;
