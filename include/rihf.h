@@ -236,13 +236,13 @@ int rihf_eigh_noalloc(int n, const double* A, double* W, double* V, void* stream
    mixed-precision RI-K builds, Eqs. k_ri_2 and tp).  A is M x K, B is N x K,
    C is M x N, all row-major FP64 HOST buffers owned by the caller (inputs
    copied in, C overwritten).  Every row of A and B is split, per K block of
-   64 * kblock columns (kblock = 0: all of K in one block), into `digits`
+   32 * kblock columns (kblock = 0: all of K in one block), into `digits`
    balanced 8-bit BF16 digits relative to the row's largest exponent in that
    block; the digit pairs (t, u) with t + u <= digits + 1 run as tcgen05 BF16
    MMAs with exact FP32 accumulation in tensor memory, folded into int64 sums
    and converted to FP64 once per output element.  digits = 7 keeps 55 bits of
-   max|A row| * max|B row| per K block.  digits in 1..7, kblock <= 30 (int64
-   headroom).  Uses the current device `device`; allocates its own buffers.
+   max|A row| * max|B row| per K block.  digits in 1..7, K blocks of at most
+   60 chunks of 32 (int64 headroom): kblock <= 60, and kblock = 0 needs K <= 1920.  Uses the current device `device`; allocates its own buffers.
    Errors: INVALID_ARG, OOM, CUDA, TIMEOUT (a bounded device wait ran out). */
 int rihf_tc_dgemm(int M, int N, int K, const double* A, const double* B, double* C, int digits, int kblock,
                   int device);

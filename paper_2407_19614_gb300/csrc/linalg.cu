@@ -590,7 +590,7 @@ void trsm_lower(const LaCtx& la, const double* L, int n, double* X, long long nc
 
 void trsm_lower_tc(const LaCtx& la, const double* L, int n, double* X, long long ncol, int symcols,
                    const TrsmTcScratch& sc) {
-  constexpr int PB = kOzChunk;   // panel = one K chunk of the digit-plane GEMM
+  constexpr int PB = kTrsmPanel;   // panel width (K of each digit-plane update)
   const int blocks = (int)std::max<long long>(1, std::min<long long>((ncol + 255) / 256, 16LL * la.sms));
   for (int k = 0; k < n; k += PB) {
     const int pb = std::min(PB, n - k);
@@ -615,8 +615,8 @@ void trsm_lower_tc(const LaCtx& la, const double* L, int n, double* X, long long
     const int M = n - k - pb;
     if (M <= 0) continue;
     OzGemmArgs g;
-    g.A = oz_slice(la, L + (size_t)(k + pb) * n + k, M, pb, n, 1, 0, pb, kOzMaxDigits, 0, sc.planes_L, sc.exps_L);
-    g.B = oz_slice(la, X + (size_t)k * ncol, (int)ncol, pb, 1, ncol, 0, pb, kOzMaxDigits, 0, sc.planes_X, sc.exps_X);
+    g.A = oz_slice(la, L + (size_t)(k + pb) * n + k, M, pb, n, 1, 0, pb, kOzMaxDigits, 0, sc.L);
+    g.B = oz_slice(la, X + (size_t)k * ncol, (int)ncol, pb, 1, ncol, 0, pb, kOzMaxDigits, 0, sc.X);
     g.M = M; g.N = (int)ncol; g.s = kOzMaxDigits; g.alpha = -1.0;
     g.C = X + (size_t)(k + pb) * ncol; g.cs_m1 = ncol; g.cs_n = 1;
     g.accumulate = true; g.symcols = symcols;

@@ -3,6 +3,7 @@
 // are small and skinny products are split along K.
 #pragma once
 #include "common.cuh"
+#include "tc_gemm_buf.cuh"
 
 namespace rihf {
 
@@ -75,13 +76,11 @@ void symmetrize_lower(const LaCtx& la, double* X, int n, int batch);
 // Forward substitution X <- L^{-1} X (as trsm_lower with trans = false) whose
 // rank-64 updates of the rows below each 64-row panel run on the tensor cores
 // as 7-digit BF16 digit-plane GEMMs (FP64-class products, tc_gemm.cuh); the
-// panels themselves are solved in FP64.  Scratch: digit planes and exponents
-// for a 64-column slice of L (n rows) and for the panel of X (ncol rows).
+// panels themselves are solved in FP64.  Scratch: oz_buf_alloc(n, kTrsmPanel,
+// 7, 1) for L and oz_buf_alloc(ncol, kTrsmPanel, 7, 1) for the panel of X.
+constexpr int kTrsmPanel = 64;
 struct TrsmTcScratch {
-  uint16_t* planes_L = nullptr;
-  int* exps_L = nullptr;
-  uint16_t* planes_X = nullptr;
-  int* exps_X = nullptr;
+  OzBuf L, X;   // kTrsmPanel-column slices of L (n rows) and of the X panel (ncol rows)
 };
 void trsm_lower_tc(const LaCtx& la, const double* L, int n, double* X, long long ncol, int symcols,
                    const TrsmTcScratch& sc);

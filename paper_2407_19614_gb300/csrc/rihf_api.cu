@@ -453,14 +453,12 @@ struct rihf_ctx {
   // mixed precision: FP32 copy of B and FP32 operands of the SCF-iteration builds
   // mixed precision: BF16 digit planes of B (per geometry), C~^T and H (per
   // build) for the tensor-core RI-K, with their block exponents
-  uint16_t *Bpl = nullptr, *Cpl = nullptr, *Hpl = nullptr;
-  int *Bex = nullptr, *Cex = nullptr, *Hex = nullptr;
+  OzBuf Bz, Cz, Hz;
   OzOperand Bop;
   TrsmTcScratch trsm_sc;          // tensor-core fit (mixed mode)
   // tensor-core gradient GEMMs (mixed mode): planes of C~ as a B operand
   // (rows N, K = nocc), of G' (rows Naux N, K = nocc) and of X~ (rows Naux, K = nocc^2)
-  uint16_t *Ctpl = nullptr, *Gpl = nullptr, *Xpl = nullptr;
-  int *Ctex = nullptr, *Gex = nullptr, *Xex = nullptr;
+  OzBuf Ctz, Gz, Xz;
   int tc_builds = 0, last_iters = 0, last_digits = 0;
   double flops_eri3 = 0.0, flops_grad3 = 0.0;   // algorithmic FP64 operations of the 3-centre kernels
   int k_nsplit = 0;             // K splits of the tensor-core K GEMM (0: not tuned yet)
@@ -585,9 +583,7 @@ static void refresh_tasks(rihf_ctx* c) {
 static void free_all(rihf_ctx* c) {
   void* ptrs[] = {c->d_pl, c->d_patom, c->d_pnprim, c->d_pps, c->d_pao, c->d_pxyz, c->d_pexp, c->d_pcoef,
                   c->d_al, c->d_aatom, c->d_anprim, c->d_aps, c->d_aao, c->d_axyz_sh, c->d_aexp, c->d_acoef,
-                  c->d_piexp, c->d_aiexp, c->d_pp_off, c->d_pp, c->trsm_sc.planes_L, c->trsm_sc.exps_L,
-                  c->Ctpl, c->Gpl, c->Xpl, c->Ctex, c->Gex, c->Xex,
-                  c->trsm_sc.planes_X, c->trsm_sc.exps_X,
+                  c->d_piexp, c->d_aiexp, c->d_pp_off, c->d_pp,
                   c->d_ao_atom, c->d_ao_l, c->hist_D[0], c->hist_D[1], c->hist_D[2], c->hist_S, c->hist_xyz[0],
                   c->hist_xyz[1], c->Dpred, c->mlX, c->mly, c->mlt, c->mlDx, c->ml_sums, c->rep_X, c->rep_t, c->net.master, c->net.wbf, c->net.grad,
                   c->net.m, c->net.v, c->net.loss,
@@ -595,9 +591,10 @@ static void free_all(rihf_ctx* c) {
                   c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->T3, c->B, c->Xo, c->Sw, c->Sv,
                   c->C, c->eps, c->Ct, c->D, c->J, c->K, c->F, c->Fx, c->T1, c->T2, c->Err, c->Fp, c->Cp, c->Hb,
                   c->dvec, c->Fring, c->Ering, c->Bdiis, c->coef, c->scal, c->Cprev,
-                  c->na2tmp, c->trsm_tmp, c->Bpl, c->Cpl, c->Hpl, c->Bex, c->Cex, c->Hex, c->cvec, c->W, c->Bij, c->Xt, c->Zm, c->G, c->Y, c->grad_parts, c->work, c->eigws, c->scratch};
+                  c->na2tmp, c->trsm_tmp, c->cvec, c->W, c->Bij, c->Xt, c->Zm, c->G, c->Y, c->grad_parts, c->work, c->eigws, c->scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (OzBuf* b : {&c->Bz, &c->Cz, &c->Hz, &c->Ctz, &c->Gz, &c->Xz, &c->trsm_sc.L, &c->trsm_sc.X}) oz_buf_free(*b);
 }
 
 // Geometry-dependent part of setup: shell centres, one-electron, metric,
@@ -670,7 +667,7 @@ static void compute_geometry(rihf_ctx* c) {
     launch_pair_prims(ic, P, c->d_pairs, c->npairs, c->d_pp_off, c->d_pp);
     launch_eri3(ic, P, X, c->d_pairs, c->ptab(), c->groups, kTaskGroups, c->T3); }
   RIHF_CUDA(cudaMemcpyAsync(c->B, c->T3, sizeof(double) * (size_t)NA * N * N, cudaMemcpyDeviceToDevice, s));
-  if (c->trsm_sc.planes_X) {
+  if (c->trsm_sc.X.planes) {
     // mixed mode: rank-64 updates on the tensor cores (7 digits), panels in FP64
     TraceScope t(c->tracer, s, "fit trsm B=L^-1 T (tcgen05 digit updates)", (double)NA * NA * N * (N + 1) / 2, 0);
     trsm_lower_tc(la, c->L, NA, c->B, (long long)N * N, N, c->trsm_sc);
@@ -679,9 +676,9 @@ static void compute_geometry(rihf_ctx* c) {
     trsm_lower(la, c->L, NA, c->B, (long long)N * N, false, N, c->trsm_tmp);
   }
   symmetrize_lower(la, c->B, N, NA);
-  if (c->Bpl) {   // digit planes of B for the tensor-core RI-K (rows (P, mu), K = nu)
+  if (c->Bz.planes) {   // digit planes of B for the tensor-core RI-K (rows (P, mu), K = nu)
     TraceScope t(c->tracer, s, "B digit planes (oz_slice)", (double)NA * N * N * (8 + 2 * kOzMaxDigits), 1);
-    c->Bop = oz_slice(la, c->B, NA * N, N, N, 1, 0, N, kOzMaxDigits, 0, c->Bpl, c->Bex);
+    c->Bop = oz_slice(la, c->B, NA * N, N, N, 1, 0, N, kOzMaxDigits, 0, c->Bz);
   }
   int flag = 0;
   RIHF_CUDA(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -934,23 +931,15 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     c->Y = dalloc<double>(big);
     if (c->opt.precision == RIHF_PRECISION_MIXED) {
       const int nkb_max = (NA * c->nocc + kOzChunk - 1) / kOzChunk;
-      c->Bpl = dalloc<uint16_t>(oz_plane_elems(NA * N, N, kOzMaxDigits));
-      c->Bex = dalloc<int>(oz_plane_elems(NA * N, 1, 1) / kOzChunk);
-      c->Cpl = dalloc<uint16_t>(oz_plane_elems(c->nocc, N, kOzMaxDigits));
-      c->Cex = dalloc<int>(oz_plane_elems(c->nocc, 1, 1) / kOzChunk);
-      c->Hpl = dalloc<uint16_t>(oz_plane_elems(N, NA * c->nocc, kOzMaxDigits));
-      c->Hex = dalloc<int>(oz_plane_elems(N, 1, 1) / kOzChunk * nkb_max);
-      c->trsm_sc.planes_L = dalloc<uint16_t>(oz_plane_elems(NA, kOzChunk, kOzMaxDigits));
-      c->trsm_sc.exps_L = dalloc<int>(oz_plane_elems(NA, 1, 1) / kOzChunk);
-      c->trsm_sc.planes_X = dalloc<uint16_t>(oz_plane_elems(N * N, kOzChunk, kOzMaxDigits));
-      c->trsm_sc.exps_X = dalloc<int>(oz_plane_elems(N * N, 1, 1) / kOzChunk);
       const int no = c->nocc;
-      c->Ctpl = dalloc<uint16_t>(oz_plane_elems(N, no, kOzMaxDigits));
-      c->Ctex = dalloc<int>(oz_plane_elems(N, 1, 1) / kOzChunk);
-      c->Gpl = dalloc<uint16_t>(oz_plane_elems(NA * N, no, kOzMaxDigits));
-      c->Gex = dalloc<int>(oz_plane_elems(NA * N, 1, 1) / kOzChunk);
-      c->Xpl = dalloc<uint16_t>(oz_plane_elems(NA, no * no, kOzMaxDigits));
-      c->Xex = dalloc<int>(oz_plane_elems(NA, 1, 1) / kOzChunk);
+      c->Bz = oz_buf_alloc(NA * N, N, kOzMaxDigits, 1);
+      c->Cz = oz_buf_alloc(no, N, kOzMaxDigits, 1);
+      c->Hz = oz_buf_alloc(N, NA * no, kOzMaxDigits, nkb_max);
+      c->trsm_sc.L = oz_buf_alloc(NA, kTrsmPanel, kOzMaxDigits, 1);
+      c->trsm_sc.X = oz_buf_alloc(N * N, kTrsmPanel, kOzMaxDigits, 1);
+      c->Ctz = oz_buf_alloc(N, no, kOzMaxDigits, 1);
+      c->Gz = oz_buf_alloc(NA * N, no, kOzMaxDigits, 1);
+      c->Xz = oz_buf_alloc(NA, no * no, kOzMaxDigits, 1);
     }
     c->trsm_tmp = dalloc<double>(32 * std::max<size_t>({n2, (size_t)NA, (size_t)c->nocc * c->nocc}) + 1024);
     {   // guess history and learned-guess buffers
@@ -1184,7 +1173,7 @@ static void fock_build(rihf_ctx* c) {
 static int tune_k_splits(rihf_ctx* c, int digits, int kch, int lower_tiles) {
   LaCtx la = c->la();
   const int N = c->N, NA = c->NA, no = c->nocc;
-  const int lo = (kch + 29) / 30;
+  const int lo = (kch + kOzMaxChunksPerBlock - 1) / kOzMaxChunksPerBlock;
   const int wave = std::max(1, c->sms / std::max(1, lower_tiles));
   std::vector<int> cand;
   for (int k : {wave / 2, wave, 2 * wave, 4 * wave}) {
@@ -1201,7 +1190,7 @@ static int tune_k_splits(rihf_ctx* c, int digits, int kch, int lower_tiles) {
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {   // the first pass warms up
       RIHF_CUDA(cudaEventRecord(e0, c->stream));
-      OzOperand Hop = oz_slice(la, c->Hb, N, NA * no, no, 1, (long long)N * no, no, digits, kbc, c->Hpl, c->Hex);
+      OzOperand Hop = oz_slice(la, c->Hb, N, NA * no, no, 1, (long long)N * no, no, digits, kbc, c->Hz);
       RIHF_CUDA(cudaMemsetAsync(c->K, 0, sizeof(double) * N * N, c->stream));
       OzGemmArgs g2;
       g2.A = Hop; g2.B = Hop; g2.M = N; g2.N = N; g2.s = digits; g2.alpha = -0.5; g2.C = c->K; g2.cs_m1 = N;
@@ -1237,16 +1226,16 @@ static void fock_build_tc(rihf_ctx* c, int digits) {
     gemv_cols(la, c->B, NA, (long long)n2, c->dvec, 1.0, c->J); }
   const double prod = oz_products(digits);
   const int npad = (no + 15) / 16 * 16, kpadN = (N + kOzChunk - 1) / kOzChunk * kOzChunk;
-  OzOperand Cop = oz_slice(la, c->Ct, no, N, 1, no, 0, N, digits, 0, c->Cpl, c->Cex);
+  OzOperand Cop = oz_slice(la, c->Ct, no, N, 1, no, 0, N, digits, 0, c->Cz);
   OzGemmArgs g1;   // H[(P, mu)][i] = sum_nu B[(P, mu)][nu] C~[nu][i]
   g1.A = c->Bop; g1.B = Cop; g1.M = NA * N; g1.N = no; g1.s = digits; g1.C = c->Hb; g1.cs_m1 = no; g1.cs_n = 1;
   { TraceScope t(c->tracer, c->stream, "RI-K H=B C~ (tcgen05 digits)",
                  2.0 * c->Bop.rows_pad * npad * kpadN * prod, 3);
     oz_gemm(la, g1); }
-  // K blocks of the (P, i) axis: enough splits to cover the SMs, at most 30
-  // chunks each (int64 headroom of the accumulators)
+  // K blocks of the (P, i) axis: enough splits to cover the SMs, at most
+  // kOzMaxChunksPerBlock chunks each (int64 headroom of the accumulators)
   const int kch = (NA * no + kOzChunk - 1) / kOzChunk;
-  const int TN = N <= 64 ? (N + 15) / 16 * 16 : 64;
+  const int TN = N <= kOzMaxTN ? (N + 15) / 16 * 16 : kOzMaxTN;   // as oz_gemm picks it
   int lower_tiles = 0;
   for (int mt = 0; mt * kOzTileM < N; ++mt)
     for (int nt = 0; nt * TN < N; ++nt)
@@ -1255,7 +1244,7 @@ static void fock_build_tc(rihf_ctx* c, int digits) {
   const int kbc = (kch + c->k_nsplit - 1) / c->k_nsplit;
   OzOperand Hop;
   { TraceScope t(c->tracer, c->stream, "RI-K H digit planes (oz_slice)", (double)NA * N * no * (8 + 2 * digits), 1);
-    Hop = oz_slice(la, c->Hb, N, NA * no, no, 1, (long long)N * no, no, digits, kbc, c->Hpl, c->Hex); }
+    Hop = oz_slice(la, c->Hb, N, NA * no, no, 1, (long long)N * no, no, digits, kbc, c->Hz); }
   RIHF_CUDA(cudaMemsetAsync(c->K, 0, sizeof(double) * n2, c->stream));
   OzGemmArgs g2;   // K = -1/2 sum_(P, i) H[mu][(P, i)] H[nu][(P, i)], lower tiles
   g2.A = Hop; g2.B = Hop; g2.M = N; g2.N = N; g2.s = digits; g2.alpha = -0.5; g2.C = c->K; g2.cs_m1 = N;
@@ -1520,7 +1509,7 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   // so the converged energy and density are those of an FP64 Fock matrix.
   // Three tensor-core builds in a row without a new lowest max|e| also move the
   // ladder to FP64.
-  const bool mixed = c->opt.precision == RIHF_PRECISION_MIXED && c->Bpl != nullptr;
+  const bool mixed = c->opt.precision == RIHF_PRECISION_MIXED && c->Bz.planes != nullptr;
   bool fp64_next = !mixed;
   double best_tc = 1e300, emax_prev = 1.0;
   int stall = 0;
@@ -1650,10 +1639,10 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
     gemv_rows(la, c->B, NA, (long long)n2, c->D, 1.0, c->dvec); }
   const long long ldx = (long long)no * no + 1;   // row P of Xt: X~^P (nocc^2) then c_P
   // Hb[P] = B^P Ct ; Bij[P] = Ct^T Hb[P]
-  const bool tc = c->Gpl != nullptr;   // mixed mode: 7-digit tensor-core GEMMs (FP64-class products)
+  const bool tc = c->Gz.planes != nullptr;   // mixed mode: 7-digit tensor-core GEMMs (FP64-class products)
   if (tc) {
     TraceScope t(c->tracer, s, "grad H=B C~ (tcgen05 7 digits)", 0.0, 0);
-    OzOperand Cop = oz_slice(la, c->Ct, no, N, 1, no, 0, N, kOzMaxDigits, 0, c->Cpl, c->Cex);
+    OzOperand Cop = oz_slice(la, c->Ct, no, N, 1, no, 0, N, kOzMaxDigits, 0, c->Cz);
     OzGemmArgs g1;
     g1.A = c->Bop; g1.B = Cop; g1.M = NA * N; g1.N = no; g1.s = kOzMaxDigits; g1.C = c->Hb; g1.cs_m1 = no;
     g1.cs_n = 1;
@@ -1681,10 +1670,9 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
     RIHF_CUDA(cudaMemcpy2DAsync(c->cvec, sizeof(double), c->Xt + (size_t)no * no, ldx * sizeof(double),
                                 sizeof(double), NA, cudaMemcpyDeviceToDevice, s)); }
   // Z = c c^T - 1/2 Xt Xt^T
-  if (tc && (no * no + kOzChunk - 1) / kOzChunk <= 30) {
+  if (tc && (no * no + kOzChunk - 1) / kOzChunk <= kOzMaxChunksPerBlock) {
     TraceScope t(c->tracer, s, "grad Z=-1/2 X X^T (tcgen05 7 digits)", 0.0, 0);
-    OzOperand Xop = oz_slice(la, c->Xt, NA, no * no, ldx, 1, 0, no * no, kOzMaxDigits, 0, c->Xpl,
-                             c->Xex);
+    OzOperand Xop = oz_slice(la, c->Xt, NA, no * no, ldx, 1, 0, no * no, kOzMaxDigits, 0, c->Xz);
     OzGemmArgs gz;
     gz.A = Xop; gz.B = Xop; gz.M = NA; gz.N = NA; gz.s = kOzMaxDigits; gz.alpha = -0.5; gz.C = c->Zm;
     gz.cs_m1 = NA; gz.cs_n = 1; gz.lower_only = true;
@@ -1712,8 +1700,8 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
       gg.sB = ldx; gg.C = c->G; gg.ldc = no; gg.sC = (long long)N * no; gg.batch = NA;
       dgemm(la, gg); }
     TraceScope t(c->tracer, s, "grad Y=Dc-1/2 C~XC~^T (tcgen05 7 digits)", 0.0, 0);
-    OzOperand Gop = oz_slice(la, c->G, NA * N, no, no, 1, 0, no, kOzMaxDigits, 0, c->Gpl, c->Gex);
-    OzOperand Top = oz_slice(la, c->Ct, N, no, no, 1, 0, no, kOzMaxDigits, 0, c->Ctpl, c->Ctex);
+    OzOperand Gop = oz_slice(la, c->G, NA * N, no, no, 1, 0, no, kOzMaxDigits, 0, c->Gz);
+    OzOperand Top = oz_slice(la, c->Ct, N, no, no, 1, 0, no, kOzMaxDigits, 0, c->Ctz);
     OzGemmArgs gy;
     gy.A = Gop; gy.B = Top; gy.M = NA * N; gy.N = N; gy.s = kOzMaxDigits; gy.alpha = -0.5; gy.C = c->Y;
     gy.cs_m1 = N; gy.cs_n = 1; gy.accumulate = true;
@@ -2145,10 +2133,15 @@ int rihf_tc_dgemm(int M, int N, int K, const double* A, const double* B, double*
     double* dB = (double*)alloc(sizeof(double) * N * K);
     double* dC = (double*)alloc(sizeof(double) * M * N);
     int* flag = (int*)alloc(4 * sizeof(int));
-    uint16_t* pa = (uint16_t*)alloc(2 * oz_plane_elems(M, K, digits));
-    uint16_t* pb = (uint16_t*)alloc(2 * oz_plane_elems(N, K, digits));
-    int* ea = (int*)alloc(sizeof(int) * ((M + kOzTileM - 1) / kOzTileM * kOzTileM) * nkb);
-    int* eb = (int*)alloc(sizeof(int) * ((N + kOzTileM - 1) / kOzTileM * kOzTileM) * nkb);
+    OzBuf za, zb;
+    za.cap = oz_plane_elems(M, K, digits);
+    za.ecap = (size_t)(M + kOzTileM - 1) / kOzTileM * kOzTileM * nkb;
+    zb.cap = oz_plane_elems(N, K, digits);
+    zb.ecap = (size_t)(N + kOzTileM - 1) / kOzTileM * kOzTileM * nkb;
+    za.planes = (uint16_t*)alloc(sizeof(uint16_t) * za.cap);
+    zb.planes = (uint16_t*)alloc(sizeof(uint16_t) * zb.cap);
+    za.exps = (int*)alloc(sizeof(int) * za.ecap);
+    zb.exps = (int*)alloc(sizeof(int) * zb.ecap);
     RIHF_CUDA(cudaMemcpyAsync(dA, A, sizeof(double) * M * K, cudaMemcpyHostToDevice, s));
     RIHF_CUDA(cudaMemcpyAsync(dB, B, sizeof(double) * N * K, cudaMemcpyHostToDevice, s));
     RIHF_CUDA(cudaMemsetAsync(dC, 0, sizeof(double) * M * N, s));
@@ -2156,8 +2149,8 @@ int rihf_tc_dgemm(int M, int N, int K, const double* A, const double* B, double*
     LaCtx la;
     la.stream = s; la.flag = flag;
     OzGemmArgs g;
-    g.A = oz_slice(la, dA, M, K, K, 1, 0, K, digits, kbc, pa, ea);
-    g.B = oz_slice(la, dB, N, K, K, 1, 0, K, digits, kbc, pb, eb);
+    g.A = oz_slice(la, dA, M, K, K, 1, 0, K, digits, kbc, za);
+    g.B = oz_slice(la, dB, N, K, K, 1, 0, K, digits, kbc, zb);
     g.M = M; g.N = N; g.s = digits; g.C = dC; g.cs_m1 = N; g.cs_n = 1; g.atomic = nkb > 1;
     oz_gemm(la, g);
     int hflag[4];

@@ -11,12 +11,15 @@ namespace rihf {
 namespace {
 
 constexpr int kOzThreads = 256;
-constexpr int kPlaneElems = kOzTileM * kOzChunk;          // 8192 BF16 = 16 KB
-constexpr int kSmemA = kOzMaxDigits * kPlaneElems * 2;     // 112 KB
-constexpr int kSmemB = kOzMaxDigits * 64 * kOzChunk * 2;   // 56 KB (N tile <= 64)
-constexpr int kSmemBytes = kSmemA + kSmemB + 1024 + 64;
-constexpr int kTmemCols = 512;
-constexpr int kMaxChunksPerBlock = 30;   // int64 headroom: chunks * 2^57 < 2^62
+constexpr int kPlaneElems = kOzTileM * kOzChunk;                // 4096 BF16 = 8 KB
+constexpr int kSmemA = kOzMaxDigits * kPlaneElems * 2;           // 56 KB
+constexpr int kSmemB = kOzMaxDigits * kOzMaxTN * kOzChunk * 2;   // 14 KB
+// at least 80 KB so that at most two CTAs share an SM (2 x 256 TMEM columns)
+constexpr int kSmemUsed = kSmemA + kSmemB + 1024 + 64;
+constexpr int kSmemBytes = kSmemUsed > 80 * 1024 ? kSmemUsed : 80 * 1024;
+constexpr int kTmemCols = 256;                                   // two CTAs per SM
+constexpr int kMaxChunksPerBlock = kOzMaxChunksPerBlock;
+constexpr int kCoreK = kOzChunk / 8;                             // core matrices along K per chunk
 constexpr unsigned long long kWaitNs = 2000000000ULL;     // bounded waits: 2 s
 
 // ------------------------------------------------------------ PTX wrappers
@@ -111,9 +114,9 @@ __device__ inline void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.alig
 
 // Shared-memory matrix descriptor, no swizzle, K-major core matrices of
 // 8 rows x 16 bytes: 128 B between K-adjacent core matrices (leading byte
-// offset), 1024 B between 8-row groups (stride byte offset), version 1.
+// offset), kCoreK * 128 B between 8-row groups (stride byte offset), version 1.
 __device__ inline uint64_t smem_desc(uint32_t addr) {
-  const uint64_t base = ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ULL << 46);
+  const uint64_t base = ((uint64_t)(128 >> 4) << 16) | ((uint64_t)((kCoreK * 128) >> 4) << 32) | (1ULL << 46);
   return base | (uint64_t)((addr & 0x3FFFF) >> 4);
 }
 
@@ -164,14 +167,14 @@ __device__ inline double oz_to_double(long long S, int e2) {
 
 // ------------------------------------------------------------ slicing
 
-// One 8-lane group per row; lane j owns K elements 8j..8j+7 of every chunk.
+// One kCoreK-lane group per row; lane j owns K elements 8j..8j+7 of every chunk.
 __global__ void __launch_bounds__(kOzThreads) oz_slice_kernel(const double* __restrict__ X, int rows, int K,
                                                               long long s_r, long long s_k1, long long s_k2, int KR,
                                                               int kchunks, int smax, int kb_chunks, int nkb,
                                                               uint16_t* __restrict__ planes, int* __restrict__ exps) {
   const int tid = threadIdx.x;
-  const int r = blockIdx.x * (kOzThreads / 8) + (tid >> 3);
-  const int j = tid & 7;
+  const int r = blockIdx.x * (kOzThreads / kCoreK) + tid / kCoreK;
+  const int j = tid % kCoreK;
   const int kb = blockIdx.y;
   const int c0 = kb * kb_chunks, c1 = min(c0 + kb_chunks, kchunks);
   const bool rv = r < rows;
@@ -187,16 +190,16 @@ __global__ void __launch_bounds__(kOzThreads) oz_slice_kernel(const double* __re
       const double x = load(c * kOzChunk + 8 * j + e);
       emax = max(emax, (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF));
     }
-  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
-  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 2));
-  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 4));
+#pragma unroll
+  for (int o = 1; o < kCoreK; o <<= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
   if (j == 0) exps[(size_t)r * nkb + kb] = emax;
   const int rt = r / kOzTileM, rr = r % kOzTileM;
   for (int c = c0; c < c1; ++c) {
     long long V[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) V[e] = oz_fixed(load(c * kOzChunk + 8 * j + e), emax);
-    uint16_t* dst = planes + ((size_t)rt * kchunks + c) * smax * kPlaneElems + (rr / 8) * 512 + j * 64 + (rr % 8) * 8;
+    uint16_t* dst =
+        planes + ((size_t)rt * kchunks + c) * smax * kPlaneElems + (rr / 8) * (kCoreK * 64) + j * 64 + (rr % 8) * 8;
     for (int t = 0; t < smax; ++t) {
       const int p = 48 - 8 * t;
       uint32_t w[4];
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(kOzThreads) oz_slice_kernel(const double* __re
 // every chunk (warp w reads TMEM lanes 32 (w % 4).. and half w / 4 of the
 // columns) into int64 fixed-point sums; the next chunk's copies overlap that
 // drain.
-__global__ void __launch_bounds__(kOzThreads, 1)
+__global__ void __launch_bounds__(kOzThreads, 2)
     oz_gemm_kernel(OzOperand A, OzOperand B, int M, int N, int s, int TN, int mtiles, int ntiles, int nsplit,
                    int lower_only, int symcols, double alpha, double* C, long long MR, long long cs_m1,
                    long long cs_m2, long long cs_n, int atomic, int* flag) {
@@ -284,9 +287,9 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const int row = 32 * (warp & 3) + lane;
   const int ncol = TN / 2, col0 = (warp >> 2) * ncol;
   const uint32_t t_row = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
-  long long acc[32];
+  long long acc[kOzMaxTN / 2];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) acc[q] = 0;
+  for (int q = 0; q < kOzMaxTN / 2; ++q) acc[q] = 0;
 
   uint32_t ph_ld = 0, ph_mma = 0;
   bool ld_pending = false, mma_pending = false, bad = false;
@@ -333,13 +336,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     for (int g = 2; g <= s + 1; ++g) {
       const int sh = 37 - 8 * (g - 2);
       const uint32_t tg = t_row + (uint32_t)((g - 2) * TN + col0);
-      uint32_t r[4][8];
+      uint32_t r[kOzMaxTN / 16][8];
 #pragma unroll
-      for (int q8 = 0; q8 < 4; ++q8)
+      for (int q8 = 0; q8 < kOzMaxTN / 16; ++q8)
         if (8 * q8 < ncol) tmem_ld8(tg + 8 * q8, r[q8]);
       tmem_wait_ld();
 #pragma unroll
-      for (int q8 = 0; q8 < 4; ++q8) {
+      for (int q8 = 0; q8 < kOzMaxTN / 16; ++q8) {
         if (8 * q8 < ncol) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -359,7 +362,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const int ea = A.exps[(size_t)m * A.nkb + split];
       const long long cbase = (m % MR) * cs_m1 + (m / MR) * cs_m2;
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
+      for (int q = 0; q < kOzMaxTN / 2; ++q) {
         const int n = nt * TN + col0 + q;
         if (q < ncol && n < N) {
           const int eb = B.exps[(size_t)n * B.nkb + split];
@@ -389,10 +392,33 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 
 }  // namespace
 
+OzBuf oz_buf_alloc(int rows, int K, int smax, int nkb) {
+  OzBuf b;
+  b.cap = oz_plane_elems(rows, K, smax);
+  b.ecap = (size_t)((rows + kOzTileM - 1) / kOzTileM) * kOzTileM * std::max(nkb, 1);
+  void* p = nullptr;
+  if (cudaMalloc(&p, sizeof(uint16_t) * b.cap) != cudaSuccess) throw RihfError(RIHF_ERR_OOM, "cudaMalloc failed");
+  b.planes = static_cast<uint16_t*>(p);
+  if (cudaMalloc(&p, sizeof(int) * b.ecap) != cudaSuccess) {
+    cudaFree(b.planes);
+    throw RihfError(RIHF_ERR_OOM, "cudaMalloc failed");
+  }
+  b.exps = static_cast<int*>(p);
+  return b;
+}
+
+void oz_buf_free(OzBuf& b) {
+  if (b.planes) cudaFree(b.planes);
+  if (b.exps) cudaFree(b.exps);
+  b = OzBuf();
+}
+
 OzOperand oz_slice(const LaCtx& la, const double* X, int rows, int K, long long s_r, long long s_k1,
-                   long long s_k2, int KR, int smax, int kb_chunks, uint16_t* planes, int* exps) {
+                   long long s_k2, int KR, int smax, int kb_chunks, const OzBuf& buf) {
   if (rows <= 0 || K <= 0 || smax < 1 || smax > kOzMaxDigits || KR <= 0)
     throw RihfError(RIHF_ERR_INVALID_ARG, "oz_slice: bad arguments");
+  uint16_t* planes = buf.planes;
+  int* exps = buf.exps;
   OzOperand op;
   op.planes = planes;
   op.exps = exps;
@@ -402,7 +428,9 @@ OzOperand oz_slice(const LaCtx& la, const double* X, int rows, int K, long long 
   op.smax = smax;
   op.kb_chunks = (kb_chunks <= 0 || kb_chunks > op.kchunks) ? op.kchunks : kb_chunks;
   op.nkb = (op.kchunks + op.kb_chunks - 1) / op.kb_chunks;
-  dim3 grid(op.rows_pad / (kOzThreads / 8), op.nkb);
+  if (oz_plane_elems(rows, K, smax) > buf.cap || (size_t)op.rows_pad * op.nkb > buf.ecap)
+    throw RihfError(RIHF_ERR_INVALID_ARG, "oz_slice: digit-plane buffer too small");
+  dim3 grid(op.rows_pad / (kOzThreads / kCoreK), op.nkb);
   oz_slice_kernel<<<grid, kOzThreads, 0, la.stream>>>(X, rows, K, s_r, s_k1, s_k2, KR, op.kchunks, smax,
                                                       op.kb_chunks, op.nkb, planes, exps);
   RIHF_LAUNCH_CHECK();
@@ -420,9 +448,9 @@ void oz_gemm(const LaCtx& la, const OzGemmArgs& g) {
     throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: K block longer than the int64 accumulator allows");
   if (!g.atomic && A.nkb > 1) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: K blocks need atomic output");
   if (g.atomic && g.accumulate) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: atomic and accumulate");
-  // column tile: the whole of N when it fits (multiple of 16), else 64 so that
-  // no tile straddles a 128-row plane
-  const int TN = g.N <= 64 ? (g.N + 15) / 16 * 16 : 64;
+  // column tile: the whole of N when it fits (multiple of 16), else kOzMaxTN
+  // (a divisor of 128, so no tile straddles a 128-row plane)
+  const int TN = g.N <= kOzMaxTN ? (g.N + 15) / 16 * 16 : kOzMaxTN;
   if (g.s * TN > kTmemCols) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: accumulators exceed TMEM");
   const int mtiles = (g.M + kOzTileM - 1) / kOzTileM, ntiles = (g.N + TN - 1) / TN;
   raise_smem_limit((const void*)oz_gemm_kernel, kSmemBytes);

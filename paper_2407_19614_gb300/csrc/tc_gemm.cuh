@@ -6,7 +6,7 @@
 // Every digit is exact in BF16.  A product of rows is the sum over digit pairs
 // (t, u) of exact integer dot products; pairs on one anti-diagonal g = t + u
 // share a weight and accumulate in one FP32 TMEM accumulator, exactly, because
-// |sum| <= 7 * 64 * 128^2 < 2^23 for a 64-wide K chunk.  Pairs with
+// |sum| <= 7 * 32 * 128^2 < 2^22 for a 32-wide K chunk.  Pairs with
 // t + u > s + 1 are dropped (their weight is below 2^{-8s} of the leading
 // term).  After each chunk the s accumulators are read back (tcgen05.ld) and
 // folded into one int64 fixed-point sum per output element; the final FP64
@@ -20,16 +20,14 @@
 
 #include "common.cuh"
 #include "linalg.cuh"
+#include "tc_gemm_buf.cuh"
 
 namespace rihf {
 
-constexpr int kOzChunk = 64;        // K elements per chunk (one smem stage)
-constexpr int kOzTileM = 128;       // rows per operand tile (UMMA M)
-constexpr int kOzMaxDigits = 7;
-
 // Digit planes of one operand.  Layout: for row tile rt (128 rows), K chunk c
-// and digit t, a 128 x 64 BF16 block in the no-swizzle K-major core-matrix
-// order: element (r, k) at ((r / 8) * 8 + k / 8) * 64 + (r % 8) * 8 + k % 8.
+// and digit t, a 128 x kOzChunk BF16 block in the no-swizzle K-major
+// core-matrix order: element (r, k) at ((r / 8) * (kOzChunk / 8) + k / 8) * 64
+// + (r % 8) * 8 + k % 8.
 // Block index ((rt * kchunks + c) * smax + t).  exps[r * nkb + kb] is the
 // largest biased FP64 exponent in row r over K block kb (0 if all zero).
 struct OzOperand {
@@ -41,17 +39,12 @@ struct OzOperand {
   int nkb = 1, kb_chunks = 0;
 };
 
-inline size_t oz_plane_elems(int rows, int K, int smax) {
-  size_t rp = (size_t)((rows + kOzTileM - 1) / kOzTileM) * kOzTileM;
-  size_t kc = (size_t)((K + kOzChunk - 1) / kOzChunk);
-  return rp * kc * kOzChunk * smax;
-}
-
 // Slice X (rows x K, element (r, k) at X[r*s_r + (k % KR)*s_k1 + (k / KR)*s_k2])
 // into smax digit planes; K blocks of kb_chunks chunks get their own exponent.
-// planes needs oz_plane_elems(rows, K, smax) entries, exps rows_pad * nkb.
+// Needs oz_plane_elems(rows, K, smax) plane and rows_pad * nkb exponent entries
+// in buf (RIHF_ERR_INVALID_ARG otherwise).
 OzOperand oz_slice(const LaCtx& la, const double* X, int rows, int K, long long s_r, long long s_k1,
-                   long long s_k2, int KR, int smax, int kb_chunks, uint16_t* planes, int* exps);
+                   long long s_k2, int KR, int smax, int kb_chunks, const OzBuf& buf);
 
 // C(m, n) = alpha * sum_k A(m, k) B(n, k) using s <= min(A.smax, B.smax) digits.
 // Output element (m, n) at C[(m % MR) * cs_m1 + (m / MR) * cs_m2 + n * cs_n];

@@ -19,7 +19,7 @@ def _bound(A, B, digits, kblock):
     M, K = A.shape
     N = B.shape[0]
     bits = min(7 + 8 * (digits - 1), 55)
-    kb = 64 * kblock if kblock else K
+    kb = 32 * kblock if kblock else K
     bound = np.zeros((M, N))
     for k0 in range(0, K, kb):
         a = np.abs(A[:, k0:k0 + kb]).max(axis=1)
@@ -39,7 +39,7 @@ def _case(M, N, K, seed, wide=False):
     return A, B
 
 
-@pytest.mark.parametrize("M,N,K", [(300, 70, 200), (128, 40, 192), (257, 16, 64), (33, 129, 1000)])
+@pytest.mark.parametrize("M,N,K", [(300, 70, 200), (128, 40, 192), (257, 16, 64), (33, 129, 1000), (64, 33, 31)])
 def test_tc_dgemm_seven_digits(M, N, K):
     A, B = _case(M, N, K, seed=M + N + K)
     C = rihf.tc_dgemm(A, B, digits=7)
@@ -79,8 +79,8 @@ def test_tc_dgemm_small_integers_exact():
 
 
 def test_tc_dgemm_rejects_bad_arguments():
-    A = np.ones((4, 64 * 40))
+    A = np.ones((4, 32 * 80))
     with pytest.raises(rihf.RihfError):
         rihf.tc_dgemm(A, A, digits=8)
-    with pytest.raises(rihf.RihfError):   # 31 chunks per block would overflow the int64 sums
-        rihf.tc_dgemm(A, A, digits=7, kblock=31)
+    with pytest.raises(rihf.RihfError):   # 61 chunks per block would overflow the int64 sums
+        rihf.tc_dgemm(A, A, digits=7, kblock=61)
