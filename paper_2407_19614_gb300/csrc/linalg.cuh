@@ -14,6 +14,7 @@ struct LaCtx {
   long long* launches = nullptr;
   int sms = 152;
   int* flag = nullptr;          // device error flag (non-positive pivot, ...)
+  int* sched = nullptr;         // two ints, zero between launches: work counter of the tensor-core GEMM
 };
 
 // C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b] for b < batch.

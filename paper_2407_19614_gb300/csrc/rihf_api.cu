@@ -426,6 +426,7 @@ struct rihf_ctx {
   double* d_boys = nullptr;
   int* d_counter = nullptr;
   int* d_flag = nullptr;
+  int* d_sched = nullptr;   // work counter of the tensor-core GEMM (zero between launches)
   ShellPair* d_pairs = nullptr;
   int2* d_tasks = nullptr;           // (pair, auxiliary shell) tasks, grouped by shared-memory class
   TaskGroup groups[kTaskGroups];
@@ -520,6 +521,7 @@ struct rihf_ctx {
     l.launches = const_cast<long long*>(&launches);
     l.sms = sms;
     l.flag = d_flag;
+    l.sched = d_sched;
     return l;
   }
   IntegralCtx ic() const {
@@ -587,7 +589,7 @@ static void free_all(rihf_ctx* c) {
                   c->d_ao_atom, c->d_ao_l, c->hist_D[0], c->hist_D[1], c->hist_D[2], c->hist_S, c->hist_xyz[0],
                   c->hist_xyz[1], c->Dpred, c->mlX, c->mly, c->mlt, c->mlDx, c->ml_sums, c->rep_X, c->rep_t, c->net.master, c->net.wbf, c->net.grad,
                   c->net.m, c->net.v, c->net.loss,
-                  c->d_tr, c->d_nf, c->d_Z, c->d_xyz, c->d_boys, c->d_counter, c->d_flag, c->d_pairs, c->d_tasks, c->d_schwarz,
+                  c->d_tr, c->d_nf, c->d_Z, c->d_xyz, c->d_boys, c->d_counter, c->d_flag, c->d_sched, c->d_pairs, c->d_tasks, c->d_schwarz,
                   c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->T3, c->B, c->Xo, c->Sw, c->Sv,
                   c->C, c->eps, c->Ct, c->D, c->J, c->K, c->F, c->Fx, c->T1, c->T2, c->Err, c->Fp, c->Cp, c->Hb,
                   c->dvec, c->Fring, c->Ering, c->Bdiis, c->coef, c->scal, c->Cprev,
@@ -889,6 +891,8 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     c->d_boys = dalloc<double>((size_t)kBoysN * kBoysM); upload(c->d_boys, boys_host(), s);
     c->d_counter = dalloc<int>(4);
     c->d_flag = dalloc<int>(4);
+    c->d_sched = dalloc<int>(2);
+    RIHF_CUDA(cudaMemset(c->d_sched, 0, 2 * sizeof(int)));
     // shell pairs a >= b; compute_geometry screens them (Schwarz) when the
     // four-centre class fits in shared memory, otherwise all pairs are kept
     for (int a = 0; a < c->hp.nshell; ++a)
@@ -2112,6 +2116,8 @@ int rihf_tc_dgemm(int M, int N, int K, const double* A, const double* B, double*
   if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || digits < 1 || digits > kOzMaxDigits || kblock < 0)
     return RIHF_ERR_INVALID_ARG;
   RIHF_CUDA(cudaSetDevice(device));
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   cudaStream_t s;
   RIHF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   std::vector<void*> bufs;
@@ -2147,7 +2153,8 @@ int rihf_tc_dgemm(int M, int N, int K, const double* A, const double* B, double*
     RIHF_CUDA(cudaMemsetAsync(dC, 0, sizeof(double) * M * N, s));
     RIHF_CUDA(cudaMemsetAsync(flag, 0, 4 * sizeof(int), s));
     LaCtx la;
-    la.stream = s; la.flag = flag;
+    la.stream = s; la.flag = flag; la.sched = flag + 2;
+    la.sms = sms;
     OzGemmArgs g;
     g.A = oz_slice(la, dA, M, K, K, 1, 0, K, digits, kbc, za);
     g.B = oz_slice(la, dB, N, K, K, 1, 0, K, digits, kbc, zb);

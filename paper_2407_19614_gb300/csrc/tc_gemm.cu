@@ -10,14 +10,8 @@ namespace rihf {
 
 namespace {
 
-constexpr int kOzThreads = 256;
+constexpr int kOzThreads = 256;                                  // slicing kernel
 constexpr int kPlaneElems = kOzTileM * kOzChunk;                // 4096 BF16 = 8 KB
-constexpr int kSmemA = kOzMaxDigits * kPlaneElems * 2;           // 56 KB
-constexpr int kSmemB = kOzMaxDigits * kOzMaxTN * kOzChunk * 2;   // 14 KB
-// at least 80 KB so that at most two CTAs share an SM (2 x 256 TMEM columns)
-constexpr int kSmemUsed = kSmemA + kSmemB + 1024 + 64;
-constexpr int kSmemBytes = kSmemUsed > 80 * 1024 ? kSmemUsed : 80 * 1024;
-constexpr int kTmemCols = 256;                                   // two CTAs per SM
 constexpr int kMaxChunksPerBlock = kOzMaxChunksPerBlock;
 constexpr int kCoreK = kOzChunk / 8;                             // core matrices along K per chunk
 constexpr unsigned long long kWaitNs = 2000000000ULL;     // bounded waits: 2 s
@@ -224,167 +218,315 @@ __global__ void __launch_bounds__(kOzThreads) oz_slice_kernel(const double* __re
 }
 
 // ------------------------------------------------------------ GEMM
+//
+// Persistent, warp-specialised kernel (one CTA per SM: it holds all 512 TMEM
+// columns).  Work items are (row tile, column tile, K block) triples taken from
+// a global counter, so tiles that the symmetry options skip cost nothing and
+// the SMs stay balanced.
+//   warp 9 (one lane): takes items, streams their K chunks' digit planes into
+//     a ring of shared-memory stages with bulk copies;
+//   warp 8 (one lane): issues the MMAs of each chunk, diagonal by diagonal, and
+//     commits stage releases and, every G chunks, a full accumulator group;
+//   warps 0-7: drain the s TMEM accumulators of each group (a row and half the
+//     columns per thread) into int64 fixed-point sums; each diagonal is
+//     released (its own mbarrier) as soon as it is in registers, so the next
+//     group's MMAs on it overlap the conversion of the rest.
+// A group spans G = floor(1024 / s) / kOzChunk chunks: every diagonal sum then
+// stays below s * 32G * 128^2 <= 2^24 and is exact in FP32.  Every wait is
+// bounded; the first one that runs out raises a shared abort flag, all roles
+// leave, the copies and MMAs still in flight are awaited (bounded) and
+// la.flag[1] is set.
 
-// One CTA per (row tile, column tile, K block).  Thread 0 issues the bulk
-// copies and the MMAs; all eight warps drain the s TMEM accumulators after
-// every chunk (warp w reads TMEM lanes 32 (w % 4).. and half w / 4 of the
-// columns) into int64 fixed-point sums; the next chunk's copies overlap that
-// drain.
-__global__ void __launch_bounds__(kOzThreads, 2)
-    oz_gemm_kernel(OzOperand A, OzOperand B, int M, int N, int s, int TN, int mtiles, int ntiles, int nsplit,
-                   int lower_only, int symcols, double alpha, double* C, long long MR, long long cs_m1,
-                   long long cs_m2, long long cs_n, int atomic, int* flag) {
+constexpr int kGemmThreads = 320;
+constexpr int kDrainThreads = 256;
+constexpr int kMaxStages = 4;
+constexpr int kItemSlots = 2;
+constexpr int kTmemCols = 512;
+constexpr int kSmemMax = 227 * 1024;
+constexpr int kSmemMin = 116 * 1024;   // more than half an SM's shared memory: one CTA per SM
+constexpr int kBookBytes = 1024;
+
+struct OzBook {
+  uint64_t full[kMaxStages], empty[kMaxStages];
+  uint64_t accfull, accempty[kOzMaxDigits];
+  uint64_t item_full[kItemSlots], item_empty[kItemSlots];
+  int item[kItemSlots];
+  uint32_t tslot;
+  int abort;
+  int issued, consumed;
+};
+static_assert(sizeof(OzBook) <= kBookBytes, "bookkeeping block");
+
+struct OzTiling {
+  int M, N, TN, mtiles, ntiles, nsplit, nitems, nfast;
+  int lower_only, symcols, kb_chunks, kchunks;
+  int s, G, nst, stage_bytes;
+};
+
+__device__ inline void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Wait for a phase; false if the shared abort flag is up or the time ran out
+// (which raises the flag).
+__device__ inline bool oz_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (global_ns() - t0 > kWaitNs) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+__device__ inline void oz_decode(const OzTiling& T, int idx, int& mt, int& nt, int& split, int& c0, int& c1) {
+  split = idx % T.nsplit;
+  const int tile = idx / T.nsplit;
+  if (T.nfast) {
+    nt = tile % T.ntiles;
+    mt = tile / T.ntiles;
+  } else {
+    mt = tile % T.mtiles;
+    nt = tile / T.mtiles;
+  }
+  c0 = split * T.kb_chunks;
+  c1 = min(c0 + T.kb_chunks, T.kchunks);
+}
+
+// Whether an item has work: a non-empty K range, a tile that meets the lower
+// triangle (lower_only), a column tile with a needed column (symcols).
+__device__ inline bool oz_valid(const OzTiling& T, int mt, int nt, int c0, int c1) {
+  if (c0 >= c1) return false;
+  if (T.lower_only && mt * kOzTileM + kOzTileM - 1 < nt * T.TN) return false;
+  if (T.symcols > 0) {
+    // columns n = a * symcols + b are needed when b <= a; a range inside one
+    // a holds b from n0 % symcols up, a range across two holds b = 0
+    const int n0 = nt * T.TN, n1 = min(n0 + T.TN, T.N) - 1;
+    const int a0 = n0 / T.symcols;
+    if (n1 / T.symcols == a0 && n0 % T.symcols > a0) return false;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    oz_gemm_kernel(OzOperand A, OzOperand B, OzTiling T, double alpha, double* C, long long MR, long long cs_m1,
+                   long long cs_m2, long long cs_n, int atomic, int* flag, int* sched) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* As = smem;
-  uint8_t* Bs = smem + kSmemA;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Bs + kSmemB);   // [0] copies landed, [1] MMAs done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
-
+  OzBook* bk = reinterpret_cast<OzBook*>(smem + (size_t)T.nst * T.stage_bytes);
+  volatile int* abort = &bk->abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int split = blockIdx.x % nsplit, tile = blockIdx.x / nsplit;
-  const int mt = tile % mtiles, nt = tile / mtiles;
-  if (nt >= ntiles) return;
-  if (lower_only && mt * kOzTileM + kOzTileM - 1 < nt * TN) return;
-  if (symcols > 0) {   // skip a column tile that lies wholly in the strict upper triangle
-    bool any = false;
-    for (int q = 0; q < TN && !any; ++q) {
-      const int n = nt * TN + q;
-      any = n < N && (n % symcols) <= (n / symcols);
-    }
-    if (!any) return;
-  }
-  const int c0 = split * A.kb_chunks, c1 = min(c0 + A.kb_chunks, A.kchunks);
-  if (c0 >= c1) return;
+  const int s = T.s, TN = T.TN;
+  const uint32_t a_bytes = (uint32_t)s * kPlaneElems * 2, b_plane = (uint32_t)TN * kOzChunk * 2;
 
-  if (warp == 0) tmem_alloc(tslot, kTmemCols);
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int i = 0; i < T.nst; ++i) {
+      mbar_init(&bk->full[i], 1);
+      mbar_init(&bk->empty[i], 1);
+    }
+    mbar_init(&bk->accfull, 1);
+    for (int d = 0; d < kOzMaxDigits; ++d) mbar_init(&bk->accempty[d], kDrainThreads);
+    for (int k = 0; k < kItemSlots; ++k) {
+      mbar_init(&bk->item_full[k], 1);
+      mbar_init(&bk->item_empty[k], kDrainThreads + 1);
+    }
+    bk->abort = 0;
+    bk->issued = bk->consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (warp == 8) tmem_alloc(&bk->tslot, kTmemCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t taddr = *tslot;
+  const uint32_t taddr = bk->tslot;
 
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                         ((uint32_t)(kOzTileM >> 4) << 24);
-  const uint32_t a_s = smem_addr(As), b_s = smem_addr(Bs);
-  const int b_rt = (nt * TN) / kOzTileM, b_off = (nt * TN) % kOzTileM;
-  const uint32_t a_bytes = (uint32_t)s * kPlaneElems * 2, b_plane = (uint32_t)TN * kOzChunk * 2;
-
-  auto issue_loads = [&](int c) {
-    mbar_expect_tx(&bars[0], a_bytes + (uint32_t)s * b_plane);
-    bulk_load(As, A.planes + ((size_t)mt * A.kchunks + c) * A.smax * kPlaneElems, a_bytes, &bars[0]);
-    for (int u = 0; u < s; ++u)
-      bulk_load(Bs + u * b_plane,
-                B.planes + (((size_t)b_rt * B.kchunks + c) * B.smax + u) * kPlaneElems + (size_t)b_off * kOzChunk,
-                b_plane, &bars[0]);
-  };
-
-  // epilogue ownership: row (TMEM lane) and a half of the tile's columns
-  const int row = 32 * (warp & 3) + lane;
-  const int ncol = TN / 2, col0 = (warp >> 2) * ncol;
-  const uint32_t t_row = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
-  long long acc[kOzMaxTN / 2];
-#pragma unroll
-  for (int q = 0; q < kOzMaxTN / 2; ++q) acc[q] = 0;
-
-  uint32_t ph_ld = 0, ph_mma = 0;
-  bool ld_pending = false, mma_pending = false, bad = false;
-  if (tid == 0) {
-    issue_loads(c0);
-    ld_pending = true;
-  }
-  for (int c = c0; c < c1; ++c) {
-    if (tid == 0) {
-      if (!mbar_wait(&bars[0], ph_ld)) {
-        bad = true;
-      } else {
-        ld_pending = false;
-        ph_ld ^= 1;
-        tc_fence_after();
-        for (int j = 0; j < kOzChunk / 16; ++j)
-          for (int t = 1; t <= s; ++t)
-            for (int u = 1; u <= s + 1 - t; ++u) {
-              const uint32_t d = taddr + (uint32_t)((t + u - 2) * TN);
-              const uint64_t ad = smem_desc(a_s + (uint32_t)((t - 1) * kPlaneElems * 2 + j * 256));
-              const uint64_t bd = smem_desc(b_s + (uint32_t)((u - 1) * b_plane + j * 256));
-              mma_bf16(d, ad, bd, idesc, (j > 0 || t > 1) ? 1u : 0u);
-            }
-        mma_commit(&bars[1]);
-        mma_pending = true;
+  if (warp == 9) {
+    if (lane == 0) {   // ---------------- producer
+      uint32_t i = 0;
+      bool ok = true;
+      for (int q = 0; ok; ++q) {
+        int idx, mt = 0, nt = 0, split = 0, c0 = 0, c1 = 0;
+        for (;;) {
+          idx = atomicAdd(sched, 1);
+          if (idx >= T.nitems) break;
+          oz_decode(T, idx, mt, nt, split, c0, c1);
+          if (oz_valid(T, mt, nt, c0, c1)) break;
+        }
+        const int slot = q % kItemSlots;
+        if (q >= kItemSlots && !oz_wait(&bk->item_empty[slot], ((q / kItemSlots) - 1) & 1, abort)) break;
+        bk->item[slot] = idx < T.nitems ? idx : -1;
+        mbar_arrive(&bk->item_full[slot]);
+        if (idx >= T.nitems) break;
+        const int b_rt = (nt * TN) / kOzTileM, b_off = (nt * TN) % kOzTileM;
+        for (int c = c0; c < c1; ++c, ++i) {
+          const int st = (int)(i % (uint32_t)T.nst);
+          if (i >= (uint32_t)T.nst && !oz_wait(&bk->empty[st], ((i / T.nst) - 1) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          uint8_t* As = smem + (size_t)st * T.stage_bytes;
+          uint8_t* Bs = As + a_bytes;
+          mbar_expect_tx(&bk->full[st], a_bytes + (uint32_t)s * b_plane);
+          bulk_load(As, A.planes + ((size_t)mt * A.kchunks + c) * A.smax * kPlaneElems, a_bytes, &bk->full[st]);
+          for (int u = 0; u < s; ++u)
+            bulk_load(Bs + u * b_plane,
+                      B.planes + (((size_t)b_rt * B.kchunks + c) * B.smax + u) * kPlaneElems +
+                          (size_t)b_off * kOzChunk,
+                      b_plane, &bk->full[st]);
+        }
+      }
+      bk->issued = (int)i;
+      // every CTA counts itself once it takes no more items; the last one
+      // resets the counters for the next launch on this stream
+      __threadfence();
+      if (atomicAdd(sched + 1, 1) == (int)gridDim.x - 1) {
+        atomicExch(sched, 0);
+        atomicExch(sched + 1, 0);
       }
     }
-    if (__syncthreads_or(bad)) {
-      bad = true;
-      break;
+    __syncwarp();
+  } else if (warp == 8) {
+    if (lane == 0) {   // ---------------- MMA issuer
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                             ((uint32_t)(kOzTileM >> 4) << 24);
+      uint32_t i = 0, grp = 0;
+      int last_st = -1;
+      uint32_t last_par = 0;
+      bool ok = true;
+      for (int q = 0; ok; ++q) {
+        const int slot = q % kItemSlots;
+        if (!oz_wait(&bk->item_full[slot], (q / kItemSlots) & 1, abort)) break;
+        const int idx = *(volatile int*)&bk->item[slot];
+        mbar_arrive(&bk->item_empty[slot]);
+        if (idx < 0) break;
+        int mt, nt, split, c0, c1;
+        oz_decode(T, idx, mt, nt, split, c0, c1);
+        for (int c = c0; c < c1; ++c, ++i) {
+          const int st = (int)(i % (uint32_t)T.nst);
+          if (!oz_wait(&bk->full[st], (i / T.nst) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const bool first = (c - c0) % T.G == 0, last = (c - c0) % T.G == T.G - 1 || c == c1 - 1;
+          const uint32_t a_s = smem_addr(smem + (size_t)st * T.stage_bytes), b_s = a_s + a_bytes;
+          for (int j = 0; j < kOzChunk / 16 && ok; ++j)
+            for (int g = 2; g <= s + 1; ++g) {
+              if (first && j == 0 && grp > 0) {
+                if (!oz_wait(&bk->accempty[g - 2], (grp - 1) & 1, abort)) {
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+              }
+              const uint32_t d = taddr + (uint32_t)((g - 2) * TN);
+              for (int t = 1; t < g; ++t) {
+                const uint64_t ad = smem_desc(a_s + (uint32_t)((t - 1) * kPlaneElems * 2 + j * 256));
+                const uint64_t bd = smem_desc(b_s + (uint32_t)((g - t - 1) * b_plane + j * 256));
+                mma_bf16(d, ad, bd, idesc, (first && j == 0 && t == 1) ? 0u : 1u);
+              }
+            }
+          mma_commit(&bk->empty[st]);   // the stage is free once these MMAs are done
+          last_st = st;
+          last_par = (i / T.nst) & 1;
+          if (!ok) {
+            ++i;
+            break;
+          }
+          if (last) {
+            mma_commit(&bk->accfull);
+            ++grp;
+          }
+        }
+      }
+      bk->consumed = (int)i;
+      if (*abort && last_st >= 0) mbar_wait(&bk->empty[last_st], last_par);   // MMAs in flight
     }
-    const bool ok = mbar_wait(&bars[1], ph_mma);
-    if (__syncthreads_or(!ok)) {
-      bad = true;
-      break;
-    }
-    ph_mma ^= 1;
-    mma_pending = false;
-    tc_fence_after();
-    if (tid == 0 && c + 1 < c1) {
-      issue_loads(c + 1);
-      ld_pending = true;
-    }
-    for (int g = 2; g <= s + 1; ++g) {
-      const int sh = 37 - 8 * (g - 2);
-      const uint32_t tg = t_row + (uint32_t)((g - 2) * TN + col0);
-      uint32_t r[kOzMaxTN / 16][8];
+    __syncwarp();
+  } else {   // ---------------- drain: warps 0-7
+    const int row = 32 * (warp & 3) + lane;
+    const int ncol = TN / 2, col0 = (warp >> 2) * ncol;
+    const uint32_t t_row = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
+    uint32_t grp = 0;
+    for (int q = 0;; ++q) {
+      const int slot = q % kItemSlots;
+      bool ok = oz_wait(&bk->item_full[slot], (q / kItemSlots) & 1, abort);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      const int idx = *(volatile int*)&bk->item[slot];
+      mbar_arrive(&bk->item_empty[slot]);
+      if (idx < 0) break;
+      int mt, nt, split, c0, c1;
+      oz_decode(T, idx, mt, nt, split, c0, c1);
+      long long acc[kOzMaxTN / 2];
 #pragma unroll
-      for (int q8 = 0; q8 < kOzMaxTN / 16; ++q8)
-        if (8 * q8 < ncol) tmem_ld8(tg + 8 * q8, r[q8]);
-      tmem_wait_ld();
+      for (int k = 0; k < kOzMaxTN / 2; ++k) acc[k] = 0;
+      for (int c = c0; c < c1 && ok; c += T.G) {
+        ok = oz_wait(&bk->accfull, grp & 1, abort);
+        if (!__all_sync(0xffffffffu, ok)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int g = 2; g <= s + 1; ++g) {
+          const int sh = 37 - 8 * (g - 2);
+          const uint32_t tg = t_row + (uint32_t)((g - 2) * TN + col0);
+          uint32_t r[kOzMaxTN / 16][8];
 #pragma unroll
-      for (int q8 = 0; q8 < kOzMaxTN / 16; ++q8) {
-        if (8 * q8 < ncol) {
+          for (int q8 = 0; q8 < kOzMaxTN / 16; ++q8)
+            if (8 * q8 < ncol) tmem_ld8(tg + 8 * q8, r[q8]);
+          tmem_wait_ld();
+          tc_fence_before();
+          mbar_arrive(&bk->accempty[g - 2]);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const long long v = (long long)__float2int_rn(__uint_as_float(r[q8][i]));
-            acc[8 * q8 + i] += sh >= 0 ? (v << sh) : (v >> (-sh));
+          for (int q8 = 0; q8 < kOzMaxTN / 16; ++q8) {
+            if (8 * q8 < ncol) {
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const long long v = (long long)__float2int_rn(__uint_as_float(r[q8][e]));
+                acc[8 * q8 + e] += sh >= 0 ? (v << sh) : (v >> (-sh));
+              }
+            }
+          }
+        }
+        ++grp;
+      }
+      if (!ok) break;
+      const long long m = (long long)mt * kOzTileM + row;
+      if (m < T.M) {
+        const int ea = A.exps[(size_t)m * A.nkb + split];
+        const long long cbase = (m % MR) * cs_m1 + (m / MR) * cs_m2;
+#pragma unroll
+        for (int k = 0; k < kOzMaxTN / 2; ++k) {
+          const int n = nt * TN + col0 + k;
+          if (k < ncol && n < T.N) {
+            const int eb = B.exps[(size_t)n * B.nkb + split];
+            double v = oz_to_double(acc[k], ea + eb - 2095);
+            if (alpha != 1.0) v *= alpha;
+            double* dst = C + cbase + (long long)n * cs_n;
+            if (atomic == 1) atomicAdd(dst, v);
+            else if (atomic == 2) *dst += v;
+            else *dst = v;
           }
         }
       }
     }
-    tc_fence_before();
-    __syncthreads();
   }
 
-  if (!bad) {
-    const long long m = (long long)mt * kOzTileM + row;
-    if (m < M) {
-      const int ea = A.exps[(size_t)m * A.nkb + split];
-      const long long cbase = (m % MR) * cs_m1 + (m / MR) * cs_m2;
-#pragma unroll
-      for (int q = 0; q < kOzMaxTN / 2; ++q) {
-        const int n = nt * TN + col0 + q;
-        if (q < ncol && n < N) {
-          const int eb = B.exps[(size_t)n * B.nkb + split];
-          double v = oz_to_double(acc[q], ea + eb - 2095);
-          if (alpha != 1.0) v *= alpha;
-          double* dst = C + cbase + (long long)n * cs_n;
-          if (atomic == 1) atomicAdd(dst, v);
-          else if (atomic == 2) *dst += v;
-          else *dst = v;
-        }
-      }
+  __syncthreads();
+  if (*abort) {
+    if (warp == 9 && lane == 0) {
+      // copies still in flight: chunks issued but never consumed
+      for (int i = bk->consumed; i < bk->issued; ++i) mbar_wait(&bk->full[i % T.nst], (i / T.nst) & 1);
     }
-  } else if (tid == 0) {
-    atomicOr(flag + 1, 1);
-    // let copies and MMAs still in flight finish before the CTA releases its
-    // shared memory and tensor memory (bounded as well)
-    if (ld_pending) mbar_wait(&bars[0], ph_ld);
-    if (mma_pending) mbar_wait(&bars[1], ph_mma);
+    if (tid == 0) atomicOr(flag + 1, 1);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 8) {
     tc_fence_after();
     tmem_dealloc(taddr, kTmemCols);
   }
@@ -448,16 +590,35 @@ void oz_gemm(const LaCtx& la, const OzGemmArgs& g) {
     throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: K block longer than the int64 accumulator allows");
   if (!g.atomic && A.nkb > 1) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: K blocks need atomic output");
   if (g.atomic && g.accumulate) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: atomic and accumulate");
+  if (!la.sched) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: no work counter");
   // column tile: the whole of N when it fits (multiple of 16), else kOzMaxTN
   // (a divisor of 128, so no tile straddles a 128-row plane)
-  const int TN = g.N <= kOzMaxTN ? (g.N + 15) / 16 * 16 : kOzMaxTN;
-  if (g.s * TN > kTmemCols) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: accumulators exceed TMEM");
-  const int mtiles = (g.M + kOzTileM - 1) / kOzTileM, ntiles = (g.N + TN - 1) / TN;
-  raise_smem_limit((const void*)oz_gemm_kernel, kSmemBytes);
-  const long long nblocks = (long long)mtiles * ntiles * A.nkb;
-  oz_gemm_kernel<<<(unsigned)nblocks, kOzThreads, kSmemBytes, la.stream>>>(
-      A, B, g.M, g.N, g.s, TN, mtiles, ntiles, A.nkb, g.lower_only ? 1 : 0, g.symcols, g.alpha, g.C, g.MR, g.cs_m1,
-      g.cs_m2, g.cs_n, g.atomic ? 1 : (g.accumulate ? 2 : 0), la.flag);
+  OzTiling T;
+  T.M = g.M;
+  T.N = g.N;
+  T.TN = g.N <= kOzMaxTN ? (g.N + 15) / 16 * 16 : kOzMaxTN;
+  T.s = g.s;
+  if (T.s * T.TN > kTmemCols) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: accumulators exceed TMEM");
+  T.mtiles = (g.M + kOzTileM - 1) / kOzTileM;
+  T.ntiles = (g.N + T.TN - 1) / T.TN;
+  T.nsplit = A.nkb;
+  const long long nitems = (long long)T.mtiles * T.ntiles * T.nsplit;
+  if (nitems >= (1LL << 30)) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: too many tiles");
+  T.nitems = (int)nitems;
+  T.nfast = g.M > g.N ? 1 : 0;   // items next to each other share the larger operand's tile
+  T.lower_only = g.lower_only ? 1 : 0;
+  T.symcols = g.symcols;
+  T.kb_chunks = A.kb_chunks;
+  T.kchunks = A.kchunks;
+  T.G = std::max(1, (1024 / T.s) / kOzChunk);
+  T.stage_bytes = T.s * (kPlaneElems * 2 + T.TN * kOzChunk * 2);
+  T.nst = std::min(kMaxStages, (kSmemMax - kBookBytes - 1024) / T.stage_bytes);
+  if (T.nst < 1) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: stage exceeds shared memory");
+  const int smem = std::max(kSmemMin, T.nst * T.stage_bytes + kBookBytes + 1024);
+  raise_smem_limit((const void*)oz_gemm_kernel, kSmemMax);
+  const int grid = (int)std::min<long long>(nitems, la.sms > 0 ? la.sms : 152);
+  oz_gemm_kernel<<<grid, kGemmThreads, smem, la.stream>>>(A, B, T, g.alpha, g.C, g.MR, g.cs_m1, g.cs_m2, g.cs_n,
+                                                          g.atomic ? 1 : (g.accumulate ? 2 : 0), la.flag, la.sched);
   RIHF_LAUNCH_CHECK();
   if (la.launches) *la.launches += 1;
 }

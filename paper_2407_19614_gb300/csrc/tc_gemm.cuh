@@ -5,12 +5,13 @@
 // digits d_t in [-128, 128] (t = 1..s, weights 2^{48-8(t-1)} on a 2^-55 grid).
 // Every digit is exact in BF16.  A product of rows is the sum over digit pairs
 // (t, u) of exact integer dot products; pairs on one anti-diagonal g = t + u
-// share a weight and accumulate in one FP32 TMEM accumulator, exactly, because
-// |sum| <= 7 * 32 * 128^2 < 2^22 for a 32-wide K chunk.  Pairs with
-// t + u > s + 1 are dropped (their weight is below 2^{-8s} of the leading
-// term).  After each chunk the s accumulators are read back (tcgen05.ld) and
-// folded into one int64 fixed-point sum per output element; the final FP64
-// value is built from the integer and the two block exponents.
+// share a weight and accumulate in one FP32 TMEM accumulator, exactly, as long
+// as |sum| <= s * K' * 128^2 <= 2^24 over the K' elements accumulated between
+// read-outs (K' = 128 for s = 7).  Pairs with t + u > s + 1 are dropped (their
+// weight is below 2^{-8s} of the leading term).  Every K' elements the s
+// accumulators are read back (tcgen05.ld) and folded into one int64
+// fixed-point sum per output element; the final FP64 value is built from the
+// integer and the two block exponents.
 //
 // s = 7 keeps 55 bits relative to max|row| * max|col| of each K block;
 // fewer digits trade accuracy for tensor work (s (s + 1) / 2 BF16 MMAs per
@@ -56,7 +57,7 @@ OzOperand oz_slice(const LaCtx& la, const double* X, int rows, int K, long long 
 // All CTAs of a K split must share one exponent block: A.kb_chunks == B.kb_chunks
 // and the kernel runs one split per exponent block.  Sets la.flag[1] = 1 if a
 // bounded wait on the tensor core or the copy engine ran out (la.flag must
-// point to at least two ints).
+// point to at least two ints; la.sched to two zeroed ints owned by the stream).
 struct OzGemmArgs {
   OzOperand A, B;
   int M = 0, N = 0;

@@ -9,7 +9,7 @@ namespace rihf {
 constexpr int kOzChunk = 32;        // K elements per chunk (one smem stage)
 constexpr int kOzTileM = 128;       // rows per operand tile (UMMA M)
 constexpr int kOzMaxDigits = 7;
-constexpr int kOzMaxTN = 32;        // columns per output tile (TMEM: 7 x 32 of 256)
+constexpr int kOzMaxTN = 64;        // columns per output tile (TMEM: 7 x 64 of 512)
 constexpr int kOzMaxChunksPerBlock = 60;   // int64 headroom: chunks * 2^56 < 2^62
 
 // Plane entries for `rows` x `K` with smax digits (rows padded to the tile).

@@ -7,6 +7,8 @@ than 2^{-8s} of the leading term, so
     |C - A B^T| <= c 2^{-(7 + 8(s-1))} K max|A_row| max|B_row|
 with a small constant c (8 here, covering both sources and the final rounding).
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -39,7 +41,8 @@ def _case(M, N, K, seed, wide=False):
     return A, B
 
 
-@pytest.mark.parametrize("M,N,K", [(300, 70, 200), (128, 40, 192), (257, 16, 64), (33, 129, 1000), (64, 33, 31)])
+@pytest.mark.parametrize("M,N,K", [(300, 70, 200), (128, 40, 192), (257, 16, 64), (33, 129, 1000), (64, 33, 31),
+                                   (20000, 100, 96)])
 def test_tc_dgemm_seven_digits(M, N, K):
     A, B = _case(M, N, K, seed=M + N + K)
     C = rihf.tc_dgemm(A, B, digits=7)
@@ -84,3 +87,42 @@ def test_tc_dgemm_rejects_bad_arguments():
         rihf.tc_dgemm(A, A, digits=8)
     with pytest.raises(rihf.RihfError):   # 61 chunks per block would overflow the int64 sums
         rihf.tc_dgemm(A, A, digits=7, kblock=61)
+
+
+def _value_of_digits(d):
+    """The number in [1, 2) whose seven balanced base-256 digits (weights
+    2^(48 - 8t) on the 2^-54 grid of its own exponent) are d."""
+    V = sum(dt << (48 - 8 * t) for t, dt in enumerate(d))
+    assert V % 4 == 0 and 2 ** 54 <= V < 2 ** 55
+    return V / 2.0 ** 54          # exact: V / 4 has 53 bits
+
+
+@pytest.mark.parametrize("digits,K", [(7, 1024), (5, 960)])
+def test_tc_dgemm_accumulators_near_two_to_the_24(digits, K):
+    """Digits close to +-127 with alternating signs make every product on an
+    anti-diagonal of the digit pairs carry the same sign, so the FP32 TMEM sums
+    between read-outs reach s * K' * 127^2 ~ 2^23.8 (K' = 32 floor(1024 / s / 32)
+    elements: 128 for 7 digits, 192 for 5).  The result must equal, bit for
+    bit, the integer replica of the digit-pair sums read out every K' elements
+    (a white-box model of the read-out schedule: an FP32 sum that lost a bit
+    changes it)."""
+    dA = [127, -127, 127, -127, 127, -127, 124]
+    dB = [127, -125, 123, -121, 119, -117, 116]
+    xa, xb = _value_of_digits(dA), _value_of_digits(dB)
+    M, N = 130, 40
+    A = np.full((M, K), xa)
+    B = np.full((N, K), xb)
+    C = rihf.tc_dgemm(A, B, digits=digits)
+    Kr = 32 * ((1024 // digits) // 32)
+    S = 0
+    for k0 in range(0, K, Kr):
+        kk = min(Kr, K - k0)
+        for g in range(2, digits + 2):
+            v = kk * sum(dA[t - 1] * dB[g - t - 1] for t in range(1, g))
+            assert abs(v) < 2 ** 24
+            sh = 37 - 8 * (g - 2)
+            S += v << sh if sh >= 0 else v >> -sh
+    expect = float(Fraction(S, 2 ** 49))     # both exponents are those of [1, 2)
+    assert np.all(C == expect), (C.min() - expect, C.max() - expect)
+    bits = min(7 + 8 * (digits - 1), 55)
+    assert abs(expect - K * xa * xb) <= 8 * 2.0 ** -bits * K * 4
