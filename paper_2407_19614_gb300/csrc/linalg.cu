@@ -353,6 +353,7 @@ __global__ void potrf_diag_kernel(double* A, int n, int k, int b, double* inv, i
                                   int want_inv = 1) {
   __shared__ double a[CB][CB + 1];
   __shared__ double li[CB][CB + 1];
+  __shared__ double rpiv;
   int lane = threadIdx.x;
   for (int i = 0; i < b; ++i) a[i][lane] = (lane < b) ? A[(size_t)(k + i) * n + k + lane] : 0.0;
   __syncwarp();
@@ -365,9 +366,10 @@ __global__ void potrf_diag_kernel(double* A, int n, int k, int b, double* inv, i
           d = 1.0;
         }
         a[j][j] = sqrt(d);
+        rpiv = 1.0 / a[j][j];
       }
       __syncwarp();
-      if (lane > j && lane < b) a[lane][j] /= a[j][j];
+      if (lane > j && lane < b) a[lane][j] *= rpiv;
       __syncwarp();
       if (lane > j && lane < b)
         for (int c = j + 1; c <= lane; ++c) a[lane][c] -= a[lane][j] * a[c][j];
@@ -409,13 +411,18 @@ __global__ void zero_upper_kernel(double* A, int n) {
 }
 
 // Panel of the blocked Cholesky: rows r >= k+b of A[:, k:k+b] solve
-// y L_kk^T = a_r by forward substitution (one thread per row).
+// y L_kk^T = a_r by forward substitution (one thread per row; the blocks are
+// one warp wide so that the rows, each a chain of dependent FP64 operations,
+// spread over as many SMs as there are warps of rows).
 __global__ void __launch_bounds__(256) chol_panel_kernel(double* A, int n, int k, int b) {
   __shared__ double l[CB][CB + 1];
+  __shared__ double rd[CB];
   for (int i = threadIdx.x; i < CB * CB; i += blockDim.x) {
     int r = i / CB, c = i % CB;
     l[r][c] = (r < b && c < b) ? A[(size_t)(k + r) * n + k + c] : 0.0;
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < CB; i += blockDim.x) rd[i] = i < b ? 1.0 / l[i][i] : 0.0;
   __syncthreads();
   for (int r = k + b + blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     double* row = A + (size_t)r * n + k;
@@ -428,7 +435,7 @@ __global__ void __launch_bounds__(256) chol_panel_kernel(double* A, int n, int k
       double s = y[i];
 #pragma unroll
       for (int q = 0; q < i; ++q) s -= l[i][q] * y[q];
-      y[i] = s / l[i][i];
+      y[i] = s * rd[i];
     }
 #pragma unroll
     for (int i = 0; i < CB; ++i)
@@ -445,7 +452,7 @@ void cholesky(const LaCtx& la, double* A, int n, double* scratch) {
     int rest = n - k - b;
     if (rest <= 0) break;
     // panel: A[k+b:, k:k+b] <- A[k+b:, k:k+b] L_kk^{-T} by substitution
-    chol_panel_kernel<<<std::max(1, std::min(ceil_div(rest, 256), 4 * la.sms)), 256, 0, la.stream>>>(A, n, k, b);
+    chol_panel_kernel<<<std::max(1, std::min(ceil_div(rest, 32), 8 * la.sms)), 32, 0, la.stream>>>(A, n, k, b);
     RIHF_LAUNCH_CHECK();
     count(la);
     // trailing update: A[k+b:, k+b:] -= panel panel^T
@@ -521,10 +528,13 @@ __global__ void __launch_bounds__(256) trsv_block_kernel(const double* __restric
                                                          double* __restrict__ X, long long ncol, int trans,
                                                          int symcols) {
   __shared__ double l[CB][CB + 1];
+  __shared__ double rd[CB];
   for (int i = threadIdx.x; i < CB * CB; i += blockDim.x) {
     int r = i / CB, c = i % CB;
     l[r][c] = (r < b && c < b) ? L[(size_t)(k + r) * n + k + c] : 0.0;
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < CB; i += blockDim.x) rd[i] = i < b ? 1.0 / l[i][i] : 0.0;
   __syncthreads();
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < ncol; j += (long long)gridDim.x * blockDim.x) {
     if (symcols > 0 && (j % symcols) > (j / symcols)) continue;   // strict upper triangle: never used
@@ -538,7 +548,7 @@ __global__ void __launch_bounds__(256) trsv_block_kernel(const double* __restric
         double s = y[i];
 #pragma unroll
         for (int q = 0; q < i; ++q) s -= l[i][q] * y[q];
-        y[i] = s / l[i][i];
+        y[i] = s * rd[i];
       }
     } else {
 #pragma unroll
@@ -548,7 +558,7 @@ __global__ void __launch_bounds__(256) trsv_block_kernel(const double* __restric
 #pragma unroll
         for (int q = i + 1; q < CB; ++q)
           if (q < b) s -= l[q][i] * y[q];
-        y[i] = s / l[i][i];
+        y[i] = s * rd[i];
       }
     }
 #pragma unroll
@@ -557,15 +567,24 @@ __global__ void __launch_bounds__(256) trsv_block_kernel(const double* __restric
   }
 }
 
+// Launch shape of trsv_block_kernel: every column is a chain of dependent FP64
+// operations, so narrow blocks spread few columns over many SMs.
+static void trsv_shape(const LaCtx& la, long long ncol, int& blocks, int& threads) {
+  const long long per = (ncol + 2LL * la.sms - 1) / (2LL * la.sms);   // columns per block for two blocks per SM
+  threads = (int)std::min<long long>(256, std::max<long long>(32, (per + 31) / 32 * 32));
+  blocks = (int)std::max<long long>(1, std::min<long long>((ncol + threads - 1) / threads, 16LL * la.sms));
+}
+
 void trsm_lower(const LaCtx& la, const double* L, int n, double* X, long long ncol, bool trans, int symcols,
                 double* tmp) {
   (void)tmp;
   const int nb = ceil_div(n, CB);
-  const int blocks = (int)std::max<long long>(1, std::min<long long>((ncol + 255) / 256, 16LL * la.sms));
+  int blocks, threads;
+  trsv_shape(la, ncol, blocks, threads);
   for (int q = 0; q < nb; ++q) {
     const int kb = trans ? nb - 1 - q : q;
     const int k = kb * CB, b = std::min(CB, n - k);
-    trsv_block_kernel<<<blocks, 256, 0, la.stream>>>(L, n, k, b, X, ncol, trans ? 1 : 0, symcols);
+    trsv_block_kernel<<<blocks, threads, 0, la.stream>>>(L, n, k, b, X, ncol, trans ? 1 : 0, symcols);
     RIHF_LAUNCH_CHECK();
     count(la);
     GemmArgs u;
@@ -591,13 +610,14 @@ void trsm_lower(const LaCtx& la, const double* L, int n, double* X, long long nc
 void trsm_lower_tc(const LaCtx& la, const double* L, int n, double* X, long long ncol, int symcols,
                    const TrsmTcScratch& sc) {
   constexpr int PB = kTrsmPanel;   // panel width (K of each digit-plane update)
-  const int blocks = (int)std::max<long long>(1, std::min<long long>((ncol + 255) / 256, 16LL * la.sms));
+  int blocks, threads;
+  trsv_shape(la, ncol, blocks, threads);
   for (int k = 0; k < n; k += PB) {
     const int pb = std::min(PB, n - k);
     // the panel in FP64: 32-row substitution blocks and their in-panel updates
     for (int k2 = k; k2 < k + pb; k2 += CB) {
       const int b = std::min(CB, k + pb - k2);
-      trsv_block_kernel<<<blocks, 256, 0, la.stream>>>(L, n, k2, b, X, ncol, 0, symcols);
+      trsv_block_kernel<<<blocks, threads, 0, la.stream>>>(L, n, k2, b, X, ncol, 0, symcols);
       RIHF_LAUNCH_CHECK();
       count(la);
       const int m2 = k + pb - (k2 + b);
@@ -627,6 +647,7 @@ void trsm_lower_tc(const LaCtx& la, const double* L, int n, double* X, long long
 // ------------------------------------------------------------ eigensolver
 
 constexpr int JT = 1024;   // Jacobi threads (one CTA)
+constexpr int kJRows = 8;  // rows per lane of the register-resident one-sided Jacobi (n <= 256)
 
 // Parallel cyclic Jacobi (round-robin pairing) in FP32, one CTA.  a: m x m
 // working matrix (shared or global), v: n x m eigenvector matrix (global).
@@ -744,11 +765,16 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ A
 // columns of U = B V to mutual orthogonality; then v_j = u_j / |u_j| and
 // lambda_j = |u_j| - sigma.  Only U (n x n, column-major, shared memory when it
 // fits) is stored; a warp owns one column pair per round (round-robin pairing),
-// its dot products reduced with shuffles.
+// its dot products reduced with shuffles.  For n <= 256 a pair's columns stay
+// in registers between the dot product and the rotation, and the squared
+// column norms are carried along by the rotation identities
+// |u_p'|^2 = |u_p|^2 - t (u_p . u_q), |u_q'|^2 = |u_q|^2 + t (u_p . u_q)
+// (recomputed at every sweep), so a pair costs one reduction, not three.
 __global__ void __launch_bounds__(JT) jacobi1s_kernel(const double* __restrict__ A, int n, int m, float* gU, float* V,
                                                       float* W, int use_smem, int max_sweeps, float tol) {
   extern __shared__ float sm[];
   __shared__ float red[32];
+  __shared__ float nrm[32 * kJRows];
   __shared__ int notconv;
   float* U = use_smem ? sm : gU;   // column j at U[j*n .. j*n+n)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -773,10 +799,59 @@ __global__ void __launch_bounds__(JT) jacobi1s_kernel(const double* __restrict__
     for (int i = lane; i < n; i += 32) U[(size_t)j * n + i] = (float)A[(size_t)i * n + j] + (i == j ? sigma : 0.f);
   __syncthreads();
   const int half = m / 2;
+  const bool in_regs = n <= 32 * kJRows;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (tid == 0) notconv = 0;
+    if (in_regs) {
+      for (int j = warp; j < n; j += JT / 32) {
+        const float* u = U + (size_t)j * n;
+        float s2 = 0.f;
+        for (int i = lane; i < n; i += 32) s2 = fmaf(u[i], u[i], s2);
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        if (lane == 0) nrm[j] = s2;
+      }
+    }
     __syncthreads();
-    for (int r = 0; r < m - 1; ++r) {
+    for (int r = 0; r < m - 1 && in_regs; ++r) {
+      for (int k = warp; k < half; k += JT / 32) {
+        int p, q;
+        if (k == 0) { p = r; q = m - 1; }
+        else { p = (r + k) % (m - 1); q = (r - k + (m - 1)) % (m - 1); }
+        if (p >= n || q >= n) continue;   // padding column
+        float* up = U + (size_t)p * n;
+        float* uq = U + (size_t)q * n;
+        float x[kJRows], y[kJRows];
+        float c = 0.f;
+#pragma unroll
+        for (int e = 0; e < kJRows; ++e) {
+          const int i = lane + 32 * e;
+          x[e] = i < n ? up[i] : 0.f;
+          y[e] = i < n ? uq[i] : 0.f;
+          c = fmaf(x[e], y[e], c);
+        }
+        const float a = nrm[p], b = nrm[q];
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (fabsf(c) <= tol * sqrtf(a * b)) continue;
+        if (lane == 0) notconv = 1;
+        float zeta = (b - a) / (2.f * c);
+        float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        float cs = rsqrtf(1.f + t * t), sn = cs * t;
+#pragma unroll
+        for (int e = 0; e < kJRows; ++e) {
+          const int i = lane + 32 * e;
+          if (i < n) {
+            up[i] = cs * x[e] - sn * y[e];
+            uq[i] = sn * x[e] + cs * y[e];
+          }
+        }
+        if (lane == 0) {
+          nrm[p] = a - t * c;
+          nrm[q] = b + t * c;
+        }
+      }
+      __syncthreads();
+    }
+    for (int r = 0; r < m - 1 && !in_regs; ++r) {
       for (int k = warp; k < half; k += JT / 32) {
         int p, q;
         if (k == 0) { p = r; q = m - 1; }
@@ -852,12 +927,15 @@ __global__ void oa_lambda_kernel(const double* R, const double* S, int n, double
     lam[i] = S[(size_t)i * n + i] / (1.0 - R[(size_t)i * n + i]);
 }
 
-// sums[0] = ||S - diag(lam)||_F^2, sums[1] = ||R||_F^2, sums[2] = ||A||_F^2 (one block)
+// Partial sums of ||S - diag(lam)||_F^2, ||R||_F^2 and ||A||_F^2, block b into
+// part[3b .. 3b+2] (oa_e_kernel folds them in a fixed order).
+constexpr int kOaParts = 64;
 __global__ void oa_norms_kernel(const double* R, const double* S, const double* A, const double* lam, int n,
-                                double* sums) {
+                                double* part) {
   __shared__ double r0[32], r1[32], r2[32];
   double a0 = 0, a1 = 0, a2 = 0;
-  for (long long idx = threadIdx.x; idx < (long long)n * n; idx += blockDim.x) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * n;
+       idx += (long long)gridDim.x * blockDim.x) {
     int i = (int)(idx / n), j = (int)(idx % n);
     double s = S[idx] - (i == j ? lam[i] : 0.0);
     a0 += s * s;
@@ -874,13 +952,29 @@ __global__ void oa_norms_kernel(const double* R, const double* S, const double* 
   if (threadIdx.x == 0) {
     double s0 = 0, s1 = 0, s2 = 0;
     for (int w = 0; w < (int)blockDim.x / 32; ++w) { s0 += r0[w]; s1 += r1[w]; s2 += r2[w]; }
-    sums[0] = s0; sums[1] = s1; sums[2] = s2;
+    part[3 * blockIdx.x] = s0; part[3 * blockIdx.x + 1] = s1; part[3 * blockIdx.x + 2] = s2;
   }
 }
 
-__global__ void oa_e_kernel(const double* R, const double* S, const double* lam, const double* sums, int n,
-                            double* E) {
-  double delta = 2.0 * (sqrt(sums[0]) + sqrt(sums[2]) * sqrt(sums[1]));
+__global__ void oa_e_kernel(const double* R, const double* S, const double* lam, const double* part, int nparts,
+                            int n, double* E) {
+  __shared__ double sh_delta;
+  if (threadIdx.x < 32) {   // fold the partial sums (fixed order: deterministic)
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int b = threadIdx.x; b < nparts; b += 32) {
+      s0 += part[3 * b];
+      s1 += part[3 * b + 1];
+      s2 += part[3 * b + 2];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (threadIdx.x == 0) sh_delta = 2.0 * (sqrt(s0) + sqrt(s2) * sqrt(s1));
+  }
+  __syncthreads();
+  const double delta = sh_delta;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * n;
        idx += (long long)gridDim.x * blockDim.x) {
     int i = (int)(idx / n), j = (int)(idx % n);
@@ -1014,8 +1108,11 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
     gs.M = n; gs.N = n; gs.K = n; gs.A = V; gs.lda = n; gs.transA = true; gs.B = AX; gs.ldb = n; gs.C = S; gs.ldc = n;
     dgemm(la, gs);
     oa_lambda_kernel<<<elem_blocks(la, n), 256, 0, la.stream>>>(R, S, n, lam);
-    oa_norms_kernel<<<1, 1024, 0, la.stream>>>(R, S, A, lam, n, sums);
-    oa_e_kernel<<<elem_blocks(la, (long long)n * n), 256, 0, la.stream>>>(R, S, lam, sums, n, E);
+    // partial norms in the XE slot (written only by the update GEMM below)
+    const int nparts = (int)std::max<long long>(1, std::min<long long>(kOaParts, (long long)n * n / 1024));
+    double* part = (long long)n * n >= 3LL * nparts ? XE : sums;   // sums: 8 doubles, enough for one part
+    oa_norms_kernel<<<nparts, 256, 0, la.stream>>>(R, S, A, lam, n, part);
+    oa_e_kernel<<<elem_blocks(la, (long long)n * n), 256, 0, la.stream>>>(R, S, lam, part, nparts, n, E);
     RIHF_LAUNCH_CHECK();
     GemmArgs ge;   // XE = V E ; V += XE
     ge.M = n; ge.N = n; ge.K = n; ge.A = V; ge.lda = n; ge.B = E; ge.ldb = n; ge.C = XE; ge.ldc = n;

@@ -497,19 +497,55 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       if (!ok) break;
       const long long m = (long long)mt * kOzTileM + row;
       if (m < T.M) {
-        const int ea = A.exps[(size_t)m * A.nkb + split];
-        const long long cbase = (m % MR) * cs_m1 + (m / MR) * cs_m2;
+        // all of the thread's values first (the exponent loads overlap), then
+        // the stores: 16-byte pairs when the row is contiguous and aligned
+        const int ea = A.exps[(size_t)m * A.nkb + split] - 2095;
+        const int n0 = nt * TN + col0;
+        const int nv = min(ncol, T.N - n0);
+        double v[kOzMaxTN / 2];
 #pragma unroll
         for (int k = 0; k < kOzMaxTN / 2; ++k) {
-          const int n = nt * TN + col0 + k;
-          if (k < ncol && n < T.N) {
-            const int eb = B.exps[(size_t)n * B.nkb + split];
-            double v = oz_to_double(acc[k], ea + eb - 2095);
-            if (alpha != 1.0) v *= alpha;
-            double* dst = C + cbase + (long long)n * cs_n;
-            if (atomic == 1) atomicAdd(dst, v);
-            else if (atomic == 2) *dst += v;
-            else *dst = v;
+          v[k] = 0.0;
+          if (k < nv) {
+            v[k] = oz_to_double(acc[k], ea + B.exps[(size_t)(n0 + k) * B.nkb + split]);
+            if (alpha != 1.0) v[k] *= alpha;
+          }
+        }
+        double* dst = C + (m % MR) * cs_m1 + (m / MR) * cs_m2 + (long long)n0 * cs_n;
+        if (atomic == 1) {
+#pragma unroll
+          for (int k = 0; k < kOzMaxTN / 2; ++k)
+            if (k < nv) atomicAdd(dst + (long long)k * cs_n, v[k]);
+        } else if (cs_n == 1 && ((uintptr_t)dst & 15) == 0) {
+          double2* d2 = reinterpret_cast<double2*>(dst);
+          if (atomic == 2) {
+#pragma unroll
+            for (int k0 = 0; k0 < kOzMaxTN / 4; k0 += 4) {   // four pairs in flight at a time
+              double2 old[4];
+#pragma unroll
+              for (int k = k0; k < k0 + 4; ++k)
+                if (2 * k + 1 < nv) old[k - k0] = d2[k];
+#pragma unroll
+              for (int k = k0; k < k0 + 4; ++k) {
+                if (2 * k + 1 < nv) d2[k] = make_double2(old[k - k0].x + v[2 * k], old[k - k0].y + v[2 * k + 1]);
+                else if (2 * k < nv) dst[2 * k] += v[2 * k];
+              }
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < kOzMaxTN / 4; ++k) {
+              if (2 * k + 1 < nv) d2[k] = make_double2(v[2 * k], v[2 * k + 1]);
+              else if (2 * k < nv) dst[2 * k] = v[2 * k];
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < kOzMaxTN / 2; ++k) {
+            if (k < nv) {
+              double* d = dst + (long long)k * cs_n;
+              if (atomic == 2) *d += v[k];
+              else *d = v[k];
+            }
           }
         }
       }
