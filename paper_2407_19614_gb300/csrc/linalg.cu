@@ -455,13 +455,15 @@ void cholesky(const LaCtx& la, double* A, int n, double* scratch) {
     chol_panel_kernel<<<std::max(1, std::min(ceil_div(rest, 32), 8 * la.sms)), 32, 0, la.stream>>>(A, n, k, b);
     RIHF_LAUNCH_CHECK();
     count(la);
-    // trailing update: A[k+b:, k+b:] -= panel panel^T
+    // trailing update: A[k+b:, k+b:] -= panel panel^T, lower tiles only (the
+    // factorisation never reads the upper triangle; it is zeroed at the end)
     GemmArgs u;
     u.M = rest; u.N = rest; u.K = b;
     u.A = A + (size_t)(k + b) * n + k; u.lda = n;
     u.B = A + (size_t)(k + b) * n + k; u.ldb = n; u.transB = true;
     u.C = A + (size_t)(k + b) * n + k + b; u.ldc = n;
     u.alpha = -1.0; u.beta = 1.0;
+    u.lower_only = true;
     dgemm(la, u);
   }
   zero_upper_kernel<<<std::max(1, std::min(ceil_div((long long)n * n, 256), 8 * la.sms)), 256, 0, la.stream>>>(A, n);

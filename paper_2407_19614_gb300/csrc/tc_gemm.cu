@@ -161,59 +161,74 @@ __device__ inline double oz_to_double(long long S, int e2) {
 
 // ------------------------------------------------------------ slicing
 
-// One kCoreK-lane group per row; lane j owns K elements 8j..8j+7 of every chunk.
-__global__ void __launch_bounds__(kOzThreads) oz_slice_kernel(const double* __restrict__ X, int rows, int K,
-                                                              long long s_r, long long s_k1, long long s_k2, int KR,
-                                                              int kchunks, int smax, int kb_chunks, int nkb,
-                                                              uint16_t* __restrict__ planes, int* __restrict__ exps) {
+// Both passes run one thread per (row, chunk, lane j): a kCoreK-lane group per
+// row, lane j owning K elements 8j..8j+7 of the chunk (blockIdx.y = chunk).
+// Element (r, k) of the operand is X[r*s_r + (k % KR)*s_k1 + (k / KR)*s_k2].
+struct OzSrc {
+  const double* X;
+  int rows, K;
+  long long s_r, s_k1, s_k2;
+  int KR;
+};
+
+__device__ inline double oz_load(const OzSrc& S, int r, int k) {
+  if (r >= S.rows || k >= S.K) return 0.0;
+  const int q = k / S.KR, m = k - q * S.KR;
+  return S.X[(long long)r * S.s_r + (long long)m * S.s_k1 + (long long)q * S.s_k2];
+}
+
+// exps[r * nkb + kb] = largest biased exponent of row r over K block kb
+// (exps zeroed before; atomicMax is order-independent).
+__global__ void __launch_bounds__(kOzThreads) oz_emax_kernel(OzSrc S, int kb_chunks, int nkb, int* __restrict__ exps) {
   const int tid = threadIdx.x;
   const int r = blockIdx.x * (kOzThreads / kCoreK) + tid / kCoreK;
   const int j = tid % kCoreK;
-  const int kb = blockIdx.y;
-  const int c0 = kb * kb_chunks, c1 = min(c0 + kb_chunks, kchunks);
-  const bool rv = r < rows;
-  const double* Xr = X + (long long)(rv ? r : 0) * s_r;
-  auto load = [&](int k) -> double {
-    if (!rv || k >= K) return 0.0;
-    const int q = k / KR, m = k - q * KR;
-    return Xr[(long long)m * s_k1 + (long long)q * s_k2];
-  };
+  const int c = blockIdx.y;
   int emax = 0;
-  for (int c = c0; c < c1; ++c)
-    for (int e = 0; e < 8; ++e) {
-      const double x = load(c * kOzChunk + 8 * j + e);
-      emax = max(emax, (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF));
-    }
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const double x = oz_load(S, r, c * kOzChunk + 8 * j + e);
+    emax = max(emax, (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF));
+  }
 #pragma unroll
   for (int o = 1; o < kCoreK; o <<= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-  if (j == 0) exps[(size_t)r * nkb + kb] = emax;
+  if (j == 0 && r < S.rows && emax > 0) atomicMax(exps + (size_t)r * nkb + c / kb_chunks, emax);
+}
+
+// The digits of chunk c of row r relative to its block exponent.
+__global__ void __launch_bounds__(kOzThreads) oz_slice_kernel(OzSrc S, int kchunks, int smax, int kb_chunks, int nkb,
+                                                              const int* __restrict__ exps,
+                                                              uint16_t* __restrict__ planes) {
+  const int tid = threadIdx.x;
+  const int r = blockIdx.x * (kOzThreads / kCoreK) + tid / kCoreK;
+  const int j = tid % kCoreK;
+  const int c = blockIdx.y;
+  const int emax = exps[(size_t)r * nkb + c / kb_chunks];
+  long long V[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) V[e] = oz_fixed(oz_load(S, r, c * kOzChunk + 8 * j + e), emax);
   const int rt = r / kOzTileM, rr = r % kOzTileM;
-  for (int c = c0; c < c1; ++c) {
-    long long V[8];
+  uint16_t* dst =
+      planes + ((size_t)rt * kchunks + c) * smax * kPlaneElems + (rr / 8) * (kCoreK * 64) + j * 64 + (rr % 8) * 8;
+  for (int t = 0; t < smax; ++t) {
+    const int p = 48 - 8 * t;
+    uint32_t w[4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) V[e] = oz_fixed(load(c * kOzChunk + 8 * j + e), emax);
-    uint16_t* dst =
-        planes + ((size_t)rt * kchunks + c) * smax * kPlaneElems + (rr / 8) * (kCoreK * 64) + j * 64 + (rr % 8) * 8;
-    for (int t = 0; t < smax; ++t) {
-      const int p = 48 - 8 * t;
-      uint32_t w[4];
-#pragma unroll
-      for (int e = 0; e < 8; e += 2) {
-        int d0, d1;
-        if (p > 0) {
-          d0 = (int)((V[e] + (1LL << (p - 1))) >> p);
-          d1 = (int)((V[e + 1] + (1LL << (p - 1))) >> p);
-          V[e] -= (long long)d0 << p;
-          V[e + 1] -= (long long)d1 << p;
-        } else {
-          d0 = (int)V[e];
-          d1 = (int)V[e + 1];
-          V[e] = V[e + 1] = 0;
-        }
-        w[e / 2] = bf16_of_int(d0) | (bf16_of_int(d1) << 16);
+    for (int e = 0; e < 8; e += 2) {
+      int d0, d1;
+      if (p > 0) {
+        d0 = (int)((V[e] + (1LL << (p - 1))) >> p);
+        d1 = (int)((V[e + 1] + (1LL << (p - 1))) >> p);
+        V[e] -= (long long)d0 << p;
+        V[e + 1] -= (long long)d1 << p;
+      } else {
+        d0 = (int)V[e];
+        d1 = (int)V[e + 1];
+        V[e] = V[e + 1] = 0;
       }
-      *reinterpret_cast<uint4*>(dst + (size_t)t * kPlaneElems) = make_uint4(w[0], w[1], w[2], w[3]);
+      w[e / 2] = bf16_of_int(d0) | (bf16_of_int(d1) << 16);
     }
+    *reinterpret_cast<uint4*>(dst + (size_t)t * kPlaneElems) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -608,11 +623,15 @@ OzOperand oz_slice(const LaCtx& la, const double* X, int rows, int K, long long 
   op.nkb = (op.kchunks + op.kb_chunks - 1) / op.kb_chunks;
   if (oz_plane_elems(rows, K, smax) > buf.cap || (size_t)op.rows_pad * op.nkb > buf.ecap)
     throw RihfError(RIHF_ERR_INVALID_ARG, "oz_slice: digit-plane buffer too small");
-  dim3 grid(op.rows_pad / (kOzThreads / kCoreK), op.nkb);
-  oz_slice_kernel<<<grid, kOzThreads, 0, la.stream>>>(X, rows, K, s_r, s_k1, s_k2, KR, op.kchunks, smax,
-                                                      op.kb_chunks, op.nkb, planes, exps);
+  if (op.kchunks > 65535) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_slice: K too long");
+  OzSrc S{X, rows, K, s_r, s_k1, s_k2, KR};
+  dim3 grid(op.rows_pad / (kOzThreads / kCoreK), op.kchunks);
+  RIHF_CUDA(cudaMemsetAsync(exps, 0, sizeof(int) * (size_t)op.rows_pad * op.nkb, la.stream));
+  oz_emax_kernel<<<grid, kOzThreads, 0, la.stream>>>(S, op.kb_chunks, op.nkb, exps);
   RIHF_LAUNCH_CHECK();
-  if (la.launches) *la.launches += 1;
+  oz_slice_kernel<<<grid, kOzThreads, 0, la.stream>>>(S, op.kchunks, smax, op.kb_chunks, op.nkb, exps, planes);
+  RIHF_LAUNCH_CHECK();
+  if (la.launches) *la.launches += 2;
   return op;
 }
 
