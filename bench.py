@@ -266,7 +266,7 @@ def run_batch(args):
     line = {"metric": "batched RI-HF AIMD molecule-steps/s (E+grad)", "value": len(ctxs) * args.steps / wall,
             "unit": "molecule-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "bf16 digit planes (RI-K) + f64", "data": "synthetic",
+            "dtype": "f64" if args.precision == "fp64" else "bf16 digit planes (RI-K, fit, gradient products) + f64", "data": "synthetic",
             "config": {"workload": "%d water clusters, 3..%d molecules (sizes %s), config-1 basis, dt 0.5 fs"
                                    % (len(ctxs), args.batch_max, np.bincount(sizes).tolist()),
                        "precision": args.precision, "scf_iters_avg": float(np.mean(iters))}}
@@ -374,7 +374,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": res["ms_max"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if main_prec == "fp64" else "bf16 digit planes (RI-K) + f64", "data": "synthetic",
+        "dtype": "f64" if main_prec == "fp64" else "bf16 digit planes (RI-K, fit, gradient products) + f64", "data": "synthetic",
         "config": config,
         "roofline": roof,
         "cpu_baseline": cpu,

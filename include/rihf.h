@@ -70,17 +70,23 @@ typedef struct {
   int device;           /* CUDA device ordinal                                             */
   int cuda_graphs;      /* 1: each SCF iteration's Fock build and DIIS error are captured  */
                         /* once per precision variant and replayed as a CUDA graph        */
+  int confirm_fp64;     /* mixed precision: 1 = convergence is confirmed on an FP64 Fock  */
+                        /* build; 0 = on a 7-digit build (55-bit products per K block)   */
 } rihf_options;
 
 /* Fills *opt with the defaults: FP64, spherical, schwarz_tau 0 (no pair
    dropped; with ill-conditioned auxiliary metrics even pairs below 1e-14 move
    the energy by ~1e-6 Eh, see the screening tests), lindep_tau
    1e-8, conv_e 1e-10, conv_diis 1e-9, max_iter 100, diis_size 8,
-   mixed_digits 0, device 0, cuda_graphs 1.
+   mixed_digits 0, device 0, cuda_graphs 1, confirm_fp64 0.
    Mixed precision (RIHF_PRECISION_MIXED): RI-K in the SCF iterations runs on
-   the tensor cores from BF16 digit planes (see rihf_tc_dgemm); RI-J, D, DIIS,
-   the diagonalisation and the gradient stay FP64; convergence is declared only
-   on an FP64 Fock build that follows the tensor-core iterations. */
+   the tensor cores from BF16 digit planes (see rihf_tc_dgemm) with 5, 6, then
+   7 digits as the SCF error falls; the fit B = L^{-1} T and the gradient's
+   products H, Z and Y use 7 digits (FP64-class: 55 bits of every row's
+   largest element per K block); RI-J, D, DIIS, the diagonalisation, the
+   Cholesky factors and the integrals stay FP64.  When the convergence test
+   passes on a ladder build, the next build is a confirmation build (7 digits,
+   or FP64 with confirm_fp64 = 1) and convergence is declared only on one. */
 void rihf_default_options(rihf_options* opt);
 
 /*
@@ -191,9 +197,11 @@ int rihf_screening_stats(rihf_ctx* ctx, int* kept, int* total);
    library launched since the context was created ([4], as a double). */
 int rihf_timings(rihf_ctx* ctx, double* out5);
 
-/* Fock builds of the last rihf_scf by precision: tensor-core RI-K builds
-   (mixed-precision iterations) and FP64 builds.  Either pointer may be NULL. */
-int rihf_scf_stats(rihf_ctx* ctx, int* tc_builds, int* fp64_builds);
+/* Fock builds of the last rihf_scf: tensor-core RI-K builds of the precision
+   ladder, FP64 builds, and confirmation builds (7-digit tensor-core builds
+   after the ladder's convergence test passed; with confirm_fp64 = 1 these are
+   the FP64 builds instead and the count is 0).  Any pointer may be NULL. */
+int rihf_scf_stats(rihf_ctx* ctx, int* tc_builds, int* fp64_builds, int* confirm_builds);
 
 /* The CUDA stream (cudaStream_t, returned as void*) on which the context
    launches all of its work; callers may record CUDA events on it. */

@@ -460,7 +460,7 @@ struct rihf_ctx {
   // tensor-core gradient GEMMs (mixed mode): planes of C~ as a B operand
   // (rows N, K = nocc), of G' (rows Naux N, K = nocc) and of X~ (rows Naux, K = nocc^2)
   OzBuf Ctz, Gz, Xz;
-  int tc_builds = 0, last_iters = 0, last_digits = 0;
+  int tc_builds = 0, confirm_builds = 0, last_iters = 0, last_digits = 0;
   double flops_eri3 = 0.0, flops_grad3 = 0.0;   // algorithmic FP64 operations of the 3-centre kernels
   int k_nsplit = 0;             // K splits of the tensor-core K GEMM (0: not tuned yet)
   // per-iteration CUDA graphs (Fock build + DIIS error), one per variant:
@@ -789,6 +789,7 @@ void rihf_default_options(rihf_options* o) {
   o->mixed_digits = 0;
   o->device = 0;
   o->cuda_graphs = 1;
+  o->confirm_fp64 = 0;
 }
 
 const char* rihf_strerror(int code) {
@@ -1508,16 +1509,18 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   // Precision ladder (mixed mode): RI-K on the tensor cores with a digit count
   // that follows the SCF error (5 digits, about 39 bits, while max|e| > 1e-2;
   // 6 while > 1e-5; then 7, about 55 bits), or the fixed count of
-  // opt.mixed_digits.  When the convergence test passes on a tensor-core build,
-  // the next build is FP64 and convergence is declared only on an FP64 build,
-  // so the converged energy and density are those of an FP64 Fock matrix.
-  // Three tensor-core builds in a row without a new lowest max|e| also move the
-  // ladder to FP64.
+  // opt.mixed_digits.  When the convergence test passes on a ladder build, the
+  // next build is a confirmation build and convergence is declared only on
+  // one: 7 digits (products with FP64-class accuracy, 55 bits per K block),
+  // or FP64 with opt.confirm_fp64; either way the converged energy and density
+  // do not carry the ladder's shorter digit counts.  Three ladder builds in a
+  // row without a new lowest max|e| also move on to confirmation builds.
   const bool mixed = c->opt.precision == RIHF_PRECISION_MIXED && c->Bz.planes != nullptr;
   bool fp64_next = !mixed;
   double best_tc = 1e300, emax_prev = 1.0;
   int stall = 0;
   c->tc_builds = 0;
+  c->confirm_builds = 0;
   RIHF_CUDA(cudaMemsetAsync(c->d_flag + 1, 0, sizeof(int), s));
   for (it = 1; it <= c->opt.max_iter; ++it) {
     cudaEventRecord(c->ev[2], s);
@@ -1529,6 +1532,10 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
       variant = std::min(digits, kOzMaxDigits);
       c->last_digits = variant;
       ++c->tc_builds;
+    } else if (mixed && !c->opt.confirm_fp64) {
+      variant = kOzMaxDigits;
+      c->last_digits = variant;
+      ++c->confirm_builds;
     }
     fock_and_error(c, variant);
     cudaEventRecord(c->ev[3], s);
@@ -2041,10 +2048,11 @@ int rihf_timings(rihf_ctx* c, double* out5) {
 
 void* rihf_stream(rihf_ctx* c) { return c ? (void*)c->stream : nullptr; }
 
-int rihf_scf_stats(rihf_ctx* c, int* tc_builds, int* fp64_builds) {
+int rihf_scf_stats(rihf_ctx* c, int* tc_builds, int* fp64_builds, int* confirm_builds) {
   if (!c) return RIHF_ERR_INVALID_ARG;
   if (tc_builds) *tc_builds = c->tc_builds;
-  if (fp64_builds) *fp64_builds = c->last_iters - c->tc_builds;
+  if (fp64_builds) *fp64_builds = c->last_iters - c->tc_builds - c->confirm_builds;
+  if (confirm_builds) *confirm_builds = c->confirm_builds;
   return RIHF_OK;
 }
 

@@ -37,7 +37,7 @@ class rihf_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("pure", ctypes.c_int), ("schwarz_tau", ctypes.c_double),
                 ("lindep_tau", ctypes.c_double), ("conv_e", ctypes.c_double), ("conv_diis", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("diis_size", ctypes.c_int), ("mixed_digits", ctypes.c_int),
-                ("device", ctypes.c_int), ("cuda_graphs", ctypes.c_int)]
+                ("device", ctypes.c_int), ("cuda_graphs", ctypes.c_int), ("confirm_fp64", ctypes.c_int)]
 
 
 EXPORTS = ["rihf_default_options", "rihf_setup", "rihf_update_geometry", "rihf_scf", "rihf_gradient",
@@ -73,7 +73,7 @@ def load(path: str = LIB_PATH):
     lib.rihf_strerror.restype = ctypes.c_char_p
     lib.rihf_last_error.argtypes = []
     lib.rihf_last_error.restype = ctypes.c_char_p
-    lib.rihf_scf_stats.argtypes = [P, P, P]
+    lib.rihf_scf_stats.argtypes = [P, P, P, P]
     lib.rihf_scf_stats.restype = I
     lib.rihf_stream.argtypes = [P]
     lib.rihf_stream.restype = P
@@ -305,9 +305,9 @@ class Context:
         return k.value, t.value
 
     def scf_stats(self):
-        a, b = ctypes.c_int(), ctypes.c_int()
-        _check(self.lib.rihf_scf_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
-        return dict(tc_builds=a.value, fp64_builds=b.value)
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.rihf_scf_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return dict(tc_builds=a.value, fp64_builds=b.value, confirm_builds=c.value)
 
     def stream(self) -> int:
         """cudaStream_t of the context (as an integer handle)."""

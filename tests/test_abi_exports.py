@@ -48,4 +48,5 @@ def test_binding_loads_and_matches_header(libpath):
     assert lib.rihf_strerror(-4) == b"SCF not converged"
     o = R.default_options()
     assert o.diis_size == 8 and o.pure == 1
+    assert o.cuda_graphs == 1 and o.confirm_fp64 == 0   # the struct's tail matches the header
 

@@ -1,9 +1,10 @@
 """Mixed-precision SCF (RI-K on the tensor cores from BF16 digit planes in the
-SCF iterations, an FP64 Fock build to declare convergence) against the FP64 CPU
-oracle, through the C ABI.
+SCF iterations, a confirmation build with FP64-class products -- 7 digits, or
+FP64 on request -- to declare convergence) against the FP64 CPU oracle,
+through the C ABI.
 
 Tolerances: |dE| <= 1e-6 Eh and max |dF| <= 1e-5 Eh/bohr against the FP64
-oracle; the precision ladder ends on an FP64 Fock build, so the result is in
+oracle; the precision ladder ends on a confirmation build, so the result is in
 practice as close as the FP64 path.
 """
 import json
@@ -34,10 +35,24 @@ def test_mixed_monomer_energy_gradient():
     ctx = R.Context(mol, precision=R.PRECISION_MIXED, conv_e=1e-10, conv_diis=1e-8, max_iter=100)
     out = ctx.scf()
     st = ctx.scf_stats()
-    assert st["tc_builds"] >= 3 and st["fp64_builds"] >= 1
+    assert st["tc_builds"] >= 3 and st["confirm_builds"] >= 1 and st["fp64_builds"] == 0
     assert abs(out["energy"] - r.E) <= 1e-6
     grad = ctx.gradient()
     assert np.abs(grad - g.grad).max() <= 1e-5
+
+
+def test_mixed_confirmation_on_fp64_build_agrees():
+    # the same SCF with the FP64 confirmation build: the two confirmations
+    # accept states that agree to far below the mixed tolerance
+    R = _R()
+    mol = W.water_monomer(0)
+    kw = dict(precision=R.PRECISION_MIXED, conv_e=1e-10, conv_diis=1e-8, max_iter=100)
+    e7 = R.Context(mol, **kw).scf()["energy"]
+    ctx = R.Context(mol, confirm_fp64=1, **kw)
+    e64 = ctx.scf()["energy"]
+    st = ctx.scf_stats()
+    assert st["fp64_builds"] >= 1 and st["confirm_builds"] == 0 and st["tc_builds"] >= 3
+    assert abs(e7 - e64) <= 1e-8
 
 
 def test_mixed_water8_against_golden_and_fp64_path():
@@ -47,8 +62,8 @@ def test_mixed_water8_against_golden_and_fp64_path():
     ctx = R.Context(mol, precision=R.PRECISION_MIXED, conv_e=1e-10, conv_diis=5e-9, max_iter=100)
     out = ctx.scf()
     st = ctx.scf_stats()
-    # most iterations run on the tensor cores; FP64 builds only confirm convergence
-    assert st["tc_builds"] >= 5 and st["fp64_builds"] <= 3
+    # most iterations run the ladder; a few 7-digit builds confirm convergence
+    assert st["tc_builds"] >= 5 and st["fp64_builds"] == 0 and 1 <= st["confirm_builds"] <= 3
     assert abs(out["energy"] - gold["energy"]) <= 1e-6
     grad = ctx.gradient()
     assert np.abs(grad - np.array(gold["grad"])).max() <= 1e-5
@@ -59,8 +74,8 @@ def test_mixed_water8_against_golden_and_fp64_path():
 
 @pytest.mark.parametrize("digits", [5, 6, 7])
 def test_mixed_fixed_digit_counts_converge(digits):
-    # a fixed digit count: the FP64 confirmation build accepts the SCF state
-    # only when the tensor-core iterations already reached the FP64 fixed point
+    # a fixed digit count: the 7-digit confirmation build accepts the SCF state
+    # only when the ladder iterations already reached the FP64-class fixed point
     R = _R()
     mol = W.water_monomer(1)
     s = O.System(mol)
