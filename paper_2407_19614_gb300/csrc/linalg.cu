@@ -1033,7 +1033,7 @@ __global__ void eig_sort64_kernel(const double* __restrict__ V, const double* __
 }
 
 void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double* ws, int refine,
-          const double* Vguess, bool skip_jacobi, int max_sweeps) {
+          const double* Vguess, bool skip_jacobi, int max_sweeps, int ns_steps) {
   int m = n + (n & 1);
   if (skip_jacobi && Vguess && refine > 0) {
     // Late SCF iterations: the previous eigenvectors are already close, so the
@@ -1042,7 +1042,7 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
     double* Vs = d + 4 * (size_t)n * n;   // the XE slot of the workspace
     double* lam = d + 6 * (size_t)n * n;
     RIHF_CUDA(cudaMemcpyAsync(V, Vguess, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, la.stream));
-    eigh(la, A, n, W, V, ws, -refine, nullptr, false);
+    eigh(la, A, n, W, V, ws, -refine, nullptr, false, max_sweeps, ns_steps);
     eig_sort64_kernel<<<1, 1024, 0, la.stream>>>(V, lam, n, Vs, W);
     RIHF_LAUNCH_CHECK();
     count(la);
@@ -1128,7 +1128,7 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
     // Newton-Schulz re-orthonormalisation V <- V (3I - V^T V)/2: columns inside
     // near-degenerate clusters are only orthonormalised to first order by the
     // refinement's r_ij/2 rule; two quadratic steps take V^T V to I.
-    for (int it = 0; it < 2; ++it) {
+    for (int it = 0; it < ns_steps; ++it) {
       GemmArgs gr;
       gr.M = n; gr.N = n; gr.K = n; gr.A = V; gr.lda = n; gr.transA = true; gr.B = V; gr.ldb = n; gr.C = R;
       gr.ldc = n; gr.alpha = -0.5;

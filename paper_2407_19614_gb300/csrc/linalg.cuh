@@ -105,10 +105,11 @@ void trsm_lower(const LaCtx& la, const double* L, int n, double* X, long long nc
 // ws must hold eig_workspace(n) doubles.
 size_t eig_workspace(int n);
 // skip_jacobi: start the refinement from Vguess directly (late SCF iterations).
-// max_sweeps caps the FP32 Jacobi sweeps (early SCF iterations need the
-// eigenvectors only to the accuracy of the SCF itself).
+// max_sweeps caps the FP32 Jacobi sweeps and ns_steps the Newton-Schulz
+// re-orthonormalisation steps after the refinement (early SCF iterations need
+// the eigenvectors only to the accuracy of the SCF itself).
 void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double* ws, int refine,
-          const double* Vguess, bool skip_jacobi = false, int max_sweeps = 20);
+          const double* Vguess, bool skip_jacobi = false, int max_sweeps = 20, int ns_steps = 2);
 
 // Elementwise / reductions.
 void axpby(const LaCtx& la, int n, double a, const double* x, double b, const double* y, double* out);

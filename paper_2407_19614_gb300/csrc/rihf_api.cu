@@ -470,7 +470,8 @@ struct rihf_ctx {
     long long launches = 0;
     long long uses = 0;
   } graphs[kOzMaxDigits + 1];
-  IterGraph diag_graphs[4];   // diagonalisation: [refine-only, warm Jacobi] x [F, extrapolated F]
+  // diagonalisation: [refine-only, warm Jacobi, light warm Jacobi] x [F, extrapolated F]
+  IterGraph diag_graphs[6];
   bool graphs_ok = true;
 
   // learned / extrapolated guess: the last three converged densities, the
@@ -720,7 +721,7 @@ static void compute_geometry(rihf_ctx* c) {
   if (c->nind != 0 && nind != c->nind) {
     c->have_cprev = false;
     for (auto* arr : {c->graphs, c->diag_graphs}) {   // captured work assumes the old basis size
-      const int cnt = arr == c->graphs ? kOzMaxDigits + 1 : 4;
+      const int cnt = arr == c->graphs ? kOzMaxDigits + 1 : 6;
       for (int i = 0; i < cnt; ++i)
         if (arr[i].exec) {
           cudaGraphExecDestroy(arr[i].exec);
@@ -1074,11 +1075,18 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
     TraceScope t(c->tracer, c->stream, "eigh F' (jacobi+refine)", 0.0, 0);
     eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, nullptr, false, 20);
   } else if (!skip) {
-    // warm-started iterations: three Jacobi sweeps (from the previous
-    // vectors); their eigenvectors only need the accuracy of the SCF iterate
-    graph_or_eager(c, c->diag_graphs[2 + (Fin == c->F ? 0 : 1)], "eigh F' (jacobi+refine)", [&]() {
+    // warm-started iterations (max|e| >= 1e-2): Jacobi sweeps from the
+    // previous vectors, then FP64 refinement; these iterations need the
+    // eigenvectors only to the accuracy of the SCF iterate, and the later
+    // refine-only iterations start from them.  Below max|e| = 0.1 (the first
+    // iterations after a nuclear step) two sweeps reach ~1e-5 and one
+    // refinement and one re-orthonormalisation step suffice; larger errors
+    // (a cold start) take three sweeps and three refinement steps.
+    const bool light = c->last_err < 0.1;
+    graph_or_eager(c, c->diag_graphs[(light ? 4 : 2) + (Fin == c->F ? 0 : 1)], "eigh F' (jacobi+refine)", [&]() {
       form_fp();
-      eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, c->Cprev, false, 3);
+      if (light) eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 1, c->Cprev, false, 2, 1);
+      else eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 3, c->Cprev, false, 3);
     });
   } else {
     graph_or_eager(c, c->diag_graphs[Fin == c->F ? 0 : 1], "eigh F' (refine only)", [&]() {
