@@ -69,6 +69,86 @@ void gemv_cols(const LaCtx& la, const double* A, int M, long long K, const doubl
   if (la.launches) *la.launches += 2;
 }
 
+// One CTA per slice r; warp w takes rows mu = w, w + 8, ..., lanes the columns
+// nu <= mu of the row (fixed order per thread and a fixed reduction tree).
+__global__ void __launch_bounds__(256) gemv_rows_sym_kernel(const double* __restrict__ A, int M, int N,
+                                                            const double* __restrict__ x, double alpha, double* y) {
+  __shared__ double red[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long n2 = (long long)N * N;
+  for (int r = blockIdx.x; r < M; r += gridDim.x) {
+    const double* slice = A + (long long)r * n2;
+    double s = 0.0, t = 0.0;   // strictly lower part, diagonal (one FP64 FMA per element)
+    for (int mu = warp; mu < N; mu += 8) {
+      const double* row = slice + (long long)mu * N;
+      const double* xr = x + (long long)mu * N;
+      for (int nu = lane; nu < mu; nu += 32) s = fma(row[nu], xr[nu], s);
+      if (lane == (mu & 31)) t = fma(row[mu], xr[mu], t);
+    }
+    s = 2.0 * s + t;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      y[r] = alpha * t;
+    }
+    __syncthreads();
+  }
+}
+
+void gemv_rows_sym(const LaCtx& la, const double* A, int M, int N, const double* x, double alpha, double* y) {
+  int blocks = std::min(M, 16 * la.sms);
+  gemv_rows_sym_kernel<<<blocks, 256, 0, la.stream>>>(A, M, N, x, alpha, y);
+  RIHF_LAUNCH_CHECK();
+  if (la.launches) *la.launches += 1;
+}
+
+// Thread per element j = mu N + nu of the flattened slice; the upper triangle
+// (nu > mu) is neither read nor written until the reduction mirrors it.
+__global__ void __launch_bounds__(256) gemv_cols_sym_kernel(const double* __restrict__ A, int M, int N,
+                                                            const double* __restrict__ x, int rows_per,
+                                                            double* __restrict__ part) {
+  const long long n2 = (long long)N * N;
+  const long long j = blockIdx.x * 256LL + threadIdx.x;
+  if (j >= n2) return;
+  const int mu = (int)(j / N), nu = (int)(j - (long long)mu * N);
+  if (nu > mu) return;
+  int r0 = blockIdx.y * rows_per, r1 = min(M, r0 + rows_per);
+  double s = 0.0;
+  for (int r = r0; r < r1; ++r) s = fma(x[r], A[(long long)r * n2 + j], s);
+  part[(long long)blockIdx.y * n2 + j] = s;
+}
+
+__global__ void cols_reduce_sym_kernel(const double* __restrict__ part, int nchunk, int N, double alpha, double* y) {
+  const long long n2 = (long long)N * N;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n2; j += (long long)gridDim.x * blockDim.x) {
+    const int mu = (int)(j / N), nu = (int)(j - (long long)mu * N);
+    if (nu > mu) continue;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += part[(long long)c * n2 + j];
+    y[j] = alpha * s;
+    y[(long long)nu * N + mu] = alpha * s;
+  }
+}
+
+void gemv_cols_sym(const LaCtx& la, const double* A, int M, int N, const double* x, double alpha, double* y) {
+  const long long n2 = (long long)N * N;
+  long long colblocks = (n2 + 255) / 256;
+  // about half the column blocks do work: twice the row chunks of the full pass
+  int nchunk = (int)std::max<long long>(1, std::min<long long>(M, (16LL * la.sms + colblocks - 1) / colblocks));
+  while (nchunk > 1 && (size_t)nchunk * n2 > la.work_elems) nchunk /= 2;
+  int rows_per = ceil_div(M, nchunk);
+  nchunk = ceil_div(M, rows_per);
+  gemv_cols_sym_kernel<<<dim3((unsigned)colblocks, nchunk), 256, 0, la.stream>>>(A, M, N, x, rows_per, la.work);
+  RIHF_LAUNCH_CHECK();
+  int blocks = (int)std::min<long long>((n2 + 255) / 256, 8LL * la.sms);
+  cols_reduce_sym_kernel<<<blocks, 256, 0, la.stream>>>(la.work, nchunk, N, alpha, y);
+  RIHF_LAUNCH_CHECK();
+  if (la.launches) *la.launches += 2;
+}
+
 __global__ void __launch_bounds__(256) gemv_rows_f32_kernel(const float* __restrict__ A, int M, long long K,
                                                             const float* __restrict__ x, double alpha, double* y) {
   __shared__ double red[8];

@@ -1152,10 +1152,10 @@ static void fock_build(rihf_ctx* c) {
   gd.C = c->D; gd.ldc = N;
   dgemm(la, gd);
   // RI-J: d = B vec(D); J = B^T d
-  { TraceScope t(c->tracer, c->stream, "RI-J d=B.D (gemv_rows)", (double)NA * n2 * 8, 1);
-    gemv_rows(la, c->B, NA, (long long)n2, c->D, 1.0, c->dvec); }
-  { TraceScope t(c->tracer, c->stream, "RI-J J=B^T d (gemv_cols)", (double)NA * n2 * 8, 1);
-    gemv_cols(la, c->B, NA, (long long)n2, c->dvec, 1.0, c->J); }
+  { TraceScope t(c->tracer, c->stream, "RI-J d=B.D (gemv_rows, lower triangles)", (double)NA * N * (N + 1) * 4, 1);
+    gemv_rows_sym(la, c->B, NA, N, c->D, 1.0, c->dvec); }
+  { TraceScope t(c->tracer, c->stream, "RI-J J=B^T d (gemv_cols, lower triangles)", (double)NA * N * (N + 1) * 4, 1);
+    gemv_cols_sym(la, c->B, NA, N, c->dvec, 1.0, c->J); }
   // RI-K: Hb[P] = B^P Ct (N x nocc); K = -1/2 sum_P Hb[P] Hb[P]^T
   GemmArgs gh;
   gh.M = NA * N; gh.N = no; gh.K = N; gh.A = c->B; gh.lda = N; gh.B = c->Ct; gh.ldb = no; gh.C = c->Hb; gh.ldc = no;
@@ -1233,10 +1233,10 @@ static void fock_build_tc(rihf_ctx* c, int digits) {
   gd.M = N; gd.N = N; gd.K = no; gd.A = c->Ct; gd.lda = no; gd.B = c->Ct; gd.ldb = no; gd.transB = true;
   gd.C = c->D; gd.ldc = N;
   dgemm(la, gd);
-  { TraceScope t(c->tracer, c->stream, "RI-J d=B.D (gemv_rows)", (double)NA * n2 * 8, 1);
-    gemv_rows(la, c->B, NA, (long long)n2, c->D, 1.0, c->dvec); }
-  { TraceScope t(c->tracer, c->stream, "RI-J J=B^T d (gemv_cols)", (double)NA * n2 * 8, 1);
-    gemv_cols(la, c->B, NA, (long long)n2, c->dvec, 1.0, c->J); }
+  { TraceScope t(c->tracer, c->stream, "RI-J d=B.D (gemv_rows, lower triangles)", (double)NA * N * (N + 1) * 4, 1);
+    gemv_rows_sym(la, c->B, NA, N, c->D, 1.0, c->dvec); }
+  { TraceScope t(c->tracer, c->stream, "RI-J J=B^T d (gemv_cols, lower triangles)", (double)NA * N * (N + 1) * 4, 1);
+    gemv_cols_sym(la, c->B, NA, N, c->dvec, 1.0, c->J); }
   const double prod = oz_products(digits);
   const int npad = (no + 15) / 16 * 16, kpadN = (N + kOzChunk - 1) / kOzChunk * kOzChunk;
   OzOperand Cop = oz_slice(la, c->Ct, no, N, 1, no, 0, N, digits, 0, c->Cz);
@@ -1654,8 +1654,8 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   gw.alpha = 0.5;
   dgemm(la, gw);
   // d = B vec D; c = L^{-T} d (the paper's L^P) is solved below together with X~
-  { TraceScope t(c->tracer, s, "grad d = B D (gemv_rows)", (double)NA * n2 * 8, 1);
-    gemv_rows(la, c->B, NA, (long long)n2, c->D, 1.0, c->dvec); }
+  { TraceScope t(c->tracer, s, "grad d = B D (gemv_rows, lower triangles)", (double)NA * N * (N + 1) * 4, 1);
+    gemv_rows_sym(la, c->B, NA, N, c->D, 1.0, c->dvec); }
   const long long ldx = (long long)no * no + 1;   // row P of Xt: X~^P (nocc^2) then c_P
   // Hb[P] = B^P Ct ; Bij[P] = Ct^T Hb[P]
   const bool tc = c->Gz.planes != nullptr;   // mixed mode: 7-digit tensor-core GEMMs (FP64-class products)

@@ -428,7 +428,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           }
           tc_fence_after();
           const bool first = (c - c0) % T.G == 0, last = (c - c0) % T.G == T.G - 1 || c == c1 - 1;
-          const uint32_t a_s = smem_addr(smem + (size_t)st * T.stage_bytes), b_s = a_s + a_bytes;
+          // descriptors of the stage's first planes; plane and K-step offsets go
+          // into the 14-bit address field (shared addresses stay below 256 KB)
+          const uint32_t a_s = smem_addr(smem + (size_t)st * T.stage_bytes);
+          const uint64_t a_d0 = smem_desc(a_s), b_d0 = smem_desc(a_s + a_bytes);
           for (int j = 0; j < kOzChunk / 16 && ok; ++j)
             for (int g = 2; g <= s + 1; ++g) {
               if (first && j == 0 && grp > 0) {
@@ -439,10 +442,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 tc_fence_after();
               }
               const uint32_t d = taddr + (uint32_t)((g - 2) * TN);
-              for (int t = 1; t < g; ++t) {
-                const uint64_t ad = smem_desc(a_s + (uint32_t)((t - 1) * kPlaneElems * 2 + j * 256));
-                const uint64_t bd = smem_desc(b_s + (uint32_t)((g - t - 1) * b_plane + j * 256));
-                mma_bf16(d, ad, bd, idesc, (first && j == 0 && t == 1) ? 0u : 1u);
+              uint64_t ad = a_d0 + (uint64_t)((j * 256) >> 4);
+              uint64_t bd = b_d0 + (uint64_t)(((g - 2) * b_plane + j * 256) >> 4);
+              const uint64_t a_step = (kPlaneElems * 2) >> 4, b_step = b_plane >> 4;
+              mma_bf16(d, ad, bd, idesc, (first && j == 0) ? 0u : 1u);
+              for (int t = 2; t < g; ++t) {
+                ad += a_step;
+                bd -= b_step;
+                mma_bf16(d, ad, bd, idesc, 1u);
               }
             }
           mma_commit(&bk->empty[st]);   // the stage is free once these MMAs are done
