@@ -96,14 +96,15 @@ __device__ inline void warp_back_transform(const double* src, long long sP, long
 
 // g[0..2] += sum_{ka,kb,kc} Y[ka][kb][kc] * (d/dA_x), g[3..5] += ... (d/dB_x) from
 // the four shifted HRR products of one shell triple.  Returns per-lane partials.
+// The (la+1) and (lb+1) terms come from accA and accB times sA and sB (a single
+// primitive triple passes one accumulator for all three and sA = 2 alpha,
+// sB = 2 beta; contracted triples pass their three weighted sums and 1, 1).
 template <int W = 32>
-__device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, int la, int lb, int lc,
+__device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, const double* acc0, const double* accA,
+                                           const double* accB, double sA, double sB, int la, int lb, int lc,
                                            const double* AB, int lane, double g[6]) {
   const int na = ncart(la), nb = ncart(lb), nc = ncart(lc);
   const double* Y = smem + pl.ycart;
-  const double* acc0 = smem + pl.acc0;
-  const double* accA = smem + pl.accA;
-  const double* accB = smem + pl.accB;
   double* scr = smem + pl.hrr;
   for (int i = 0; i < 6; ++i) g[i] = 0.0;
   // (la+1, lb) from accA
@@ -121,6 +122,7 @@ __device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, in
       g[2] += y * I[(kz * nb + kb) * nc + kc];
       (void)nap;
     }
+    for (int i = 0; i < 3; ++i) g[i] *= sA;
     __syncwarp(lane_group_mask<W>());
   }
   if (la > 0) {
@@ -148,6 +150,7 @@ __device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, in
       g[4] += y * I[(ka * nbp + cart_index(lb + 1, bx, by + 1)) * nc + kc];
       g[5] += y * I[(ka * nbp + cart_index(lb + 1, bx, by)) * nc + kc];
     }
+    for (int i = 3; i < 6; ++i) g[i] *= sB;
     __syncwarp(lane_group_mask<W>());
   }
   if (lb > 0) {
@@ -194,14 +197,19 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
     double* vrr = smem + pl.vrr;
     double* etr = smem + pl.etr;
     int accsz = acc_size(pl.emin, pl.emax, lc);
-    for (int i = lane; i < 3 * accsz; i += W) smem[pl.acc0 + i] = 0.0;
+    const PairPrim* pr = ptab.pp + ptab.off[ip];
+    const int nab = prim.nprim[sa] * prim.nprim[sb];
+    // one primitive triple and a ket above s: the last electron-transfer level
+    // is the (unweighted) accumulator, read in place; the derivative weights
+    // 2 alpha and 2 beta scale the contracted sums instead
+    const bool single = nab == 1 && aux.nprim[sc] == 1 && lc > 0;
+    if (!single)
+      for (int i = lane; i < 3 * accsz; i += W) smem[pl.acc0 + i] = 0.0;
     const double* A = prim.xyz + 3 * sa;
     const double* B = prim.xyz + 3 * sb;
     const double* C = aux.xyz + 3 * sc;
     EtrShape sh{lc, pl.emin, pl.emax};
     const double ABv[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
-    const PairPrim* pr = ptab.pp + ptab.off[ip];
-    const int nab = prim.nprim[sa] * prim.nprim[sb];
     for (int ab = 0; ab < nab; ++ab) {
       const PairPrim q = pr[ab];
       for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
@@ -211,9 +219,11 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
         __syncwarp(lane_group_mask<W>());
         warp_vrr<W>(vrr, pl.L, t, Fm, lane);
         warp_etr<W>(vrr, pl.L, etr, sh, t, Fm, lane);
-        warp_acc_level<W>(vrr, pl.L, etr, sh, 1.0, smem + pl.acc0, lane);
-        warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.alpha, smem + pl.accA, lane);
-        warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.beta, smem + pl.accB, lane);
+        if (!single) {
+          warp_acc_level<W>(vrr, pl.L, etr, sh, 1.0, smem + pl.acc0, lane);
+          warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.alpha, smem + pl.accA, lane);
+          warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.beta, smem + pl.accB, lane);
+        }
       }
     }
     // Y block -> Cartesian
@@ -224,7 +234,13 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
                         smem + pl.t1, smem + pl.t2, smem + pl.ycart, lane);
     double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
     double g[6];
-    warp_deriv_contract<W>(pl, smem, la, lb, lc, AB, lane, g);
+    if (single) {
+      const double* lvl = etr + sh.level_off(lc);
+      warp_deriv_contract<W>(pl, smem, lvl, lvl, lvl, 2.0 * pr[0].alpha, 2.0 * pr[0].beta, la, lb, lc, AB, lane, g);
+    } else {
+      warp_deriv_contract<W>(pl, smem, smem + pl.acc0, smem + pl.accA, smem + pl.accB, 1.0, 1.0, la, lb, lc, AB,
+                             lane, g);
+    }
     double wgt = (sa == sb) ? 1.0 : 2.0;
     for (int i = 0; i < 6; ++i) g[i] = warp_sum<W>(g[i]) * wgt;
     if (lane == 0) {
@@ -294,7 +310,7 @@ __global__ void __launch_bounds__(32) grad_eri2_kernel(DevShells aux, const doub
     // (la, lb+1) term vanishes
     for (int i = lane; i < accsz; i += 32) smem[pl.accB + i] = 0.0;
     __syncwarp();
-    warp_deriv_contract(pl, smem, la, 0, lc, AB, lane, g);
+    warp_deriv_contract(pl, smem, smem + pl.acc0, smem + pl.accA, smem + pl.accB, 1.0, 1.0, la, 0, lc, AB, lane, g);
     // E term -1/2 sum_PQ Z_PQ (P|Q)^xi over ordered pairs: off-diagonal shell
     // pairs appear twice.
     double wgt = (sa == sc) ? -0.5 : -1.0;
@@ -454,7 +470,7 @@ __global__ void __launch_bounds__(32) grad_one_electron_kernel(DevShells prim, i
                         1, smem + pl.t1, smem + pl.t2, smem + pl.ycart, lane);
     double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
     double g[6];
-    warp_deriv_contract(pl, smem, la, lb, 0, AB, lane, g);
+    warp_deriv_contract(pl, smem, smem + pl.acc0, smem + pl.accA, smem + pl.accB, 1.0, 1.0, la, lb, 0, AB, lane, g);
     for (int i = 0; i < 6; ++i) g[i] = warp_sum(g[i]) * wgt;
     if (lane == 0) {
       for (int x = 0; x < 3; ++x) {

@@ -163,15 +163,19 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
     double* vrr = smem + pl.vrr;
     double* etr = smem + pl.etr;
     double* acc = smem + pl.acc;
+    const int nab = prim.nprim[sa] * prim.nprim[sb];
+    // one primitive triple and a ket above s: the last electron-transfer level
+    // ([e][ke][kc], e in [emin, emax]) is the accumulator itself, read in place
+    const bool single = nab == 1 && aux.nprim[sc] == 1 && lc > 0;
     int accsz = acc_size(emin, emax, lc);
-    for (int i = lane; i < accsz; i += W) acc[i] = 0.0;
+    if (!single)
+      for (int i = lane; i < accsz; i += W) acc[i] = 0.0;
     const double* A = prim.xyz + 3 * sa;
     const double* B = prim.xyz + 3 * sb;
     const double* C = aux.xyz + 3 * sc;
     const double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
     EtrShape sh{lc, emin, emax};
     const PairPrim* pr = ptab.pp + ptab.off[ip];
-    const int nab = prim.nprim[sa] * prim.nprim[sb];
     for (int ab = 0; ab < nab; ++ab) {
       const PairPrim q = pr[ab];
       for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
@@ -180,10 +184,12 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
         for (int m = lane; m <= L; m += W) Fm[m] = boys_eval(m, t.T, boys);
         __syncwarp(lane_group_mask<W>());
         warp_vrr<W>(vrr, L, t, Fm, lane);
-        warp_etr_accumulate<W>(vrr, L, etr, sh, t, 1.0, acc, Fm, lane);
+        if (single) warp_etr<W>(vrr, L, etr, sh, t, Fm, lane);
+        else warp_etr_accumulate<W>(vrr, L, etr, sh, t, 1.0, acc, Fm, lane);
       }
     }
-    const double* cart = warp_hrr<W>(acc, emin, la, lb, lc, AB, smem + pl.hrr, pl.half, lane);
+    const double* cart = warp_hrr<W>(single ? etr + sh.level_off(lc) : acc, emin, la, lb, lc, AB, smem + pl.hrr,
+                                     pl.half, lane);
     int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
     const double* out = warp_transform3<W>(cart, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
                                         prim.tr + lb * kTrStride * kTrStride, aux.tr + lc * kTrStride * kTrStride,
@@ -733,6 +739,7 @@ void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lpr
                 const std::vector<int>& aatom, const std::vector<int>& nf, double* eri3, double* grad3) {
   constexpr int nl = kMaxLPrim + 1, nc = kMaxLAux + 1;
   double e_prim[nl][nl][nc], e_task[nl][nl][nc], g_prim[nl][nl][nc], g_task[nl][nl][nc];
+  double e_acc[nl][nl][nc], g_acc[nl][nl][nc];   // accumulation passes (skipped by single-triple tasks with lc > 0)
   for (int la = 0; la < nl; ++la)
     for (int lb = 0; lb <= la; ++lb)
       for (int lc = 0; lc < nc; ++lc) {
@@ -741,15 +748,15 @@ void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lpr
         const double setup = 25.0;
         {
           const int L = la + lb + lc;
-          e_prim[la][lb][lc] = setup + 14.0 * (L + 1) + vrr_flops(L) + etr_flops(EtrShape{lc, la, la + lb}) +
-                               2.0 * acc_size(la, la + lb, lc);
+          e_prim[la][lb][lc] = setup + 14.0 * (L + 1) + vrr_flops(L) + etr_flops(EtrShape{lc, la, la + lb});
+          e_acc[la][lb][lc] = 2.0 * acc_size(la, la + lb, lc);
           e_task[la][lb][lc] = hrr_flops(la, lb, lc) +
                                2.0 * ((double)na * nb * fc * ncc + (double)na * fb * fc * nb + (double)fa * fb * fc * na);
         }
         {
           const int emin = la > 0 ? la - 1 : 0, emax = la + lb + 1, L = emax + lc;
-          g_prim[la][lb][lc] = setup + 14.0 * (L + 1) + vrr_flops(L) + etr_flops(EtrShape{lc, emin, emax}) +
-                               6.0 * acc_size(emin, emax, lc);
+          g_prim[la][lb][lc] = setup + 14.0 * (L + 1) + vrr_flops(L) + etr_flops(EtrShape{lc, emin, emax});
+          g_acc[la][lb][lc] = 6.0 * acc_size(emin, emax, lc);
           g_task[la][lb][lc] = 2.0 * ((double)fa * fb * ncc * fc + (double)fa * nb * ncc * fb + (double)na * nb * ncc * fa) +
                                hrr_flops(la + 1, lb, lc) + (la > 0 ? hrr_flops(la - 1, lb, lc) : 0.0) +
                                hrr_flops(la, lb + 1, lc) + (lb > 0 ? hrr_flops(la, lb - 1, lc) : 0.0) +
@@ -765,8 +772,10 @@ void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lpr
     for (int c = 0; c < (int)laux.size(); ++c) {
       const int lc = laux[c];
       const double np3 = npab * naux_prim[c];
-      fe += np3 * e_prim[la][lb][lc] + e_task[la][lb][lc];
-      if (!(patom[a] == patom[b] && patom[b] == aatom[c])) fg += np3 * g_prim[la][lb][lc] + g_task[la][lb][lc];
+      const bool single = np3 == 1.0 && lc > 0;   // the kernels read the last transfer level in place
+      fe += np3 * e_prim[la][lb][lc] + e_task[la][lb][lc] + (single ? 0.0 : np3 * e_acc[la][lb][lc]);
+      if (!(patom[a] == patom[b] && patom[b] == aatom[c]))
+        fg += np3 * g_prim[la][lb][lc] + g_task[la][lb][lc] + (single ? 6.0 : np3 * g_acc[la][lb][lc]);
     }
   }
   *eri3 = fe;
