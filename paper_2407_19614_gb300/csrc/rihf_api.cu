@@ -1659,9 +1659,10 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   const long long ldx = (long long)no * no + 1;   // row P of Xt: X~^P (nocc^2) then c_P
   // Hb[P] = B^P Ct ; Bij[P] = Ct^T Hb[P]
   const bool tc = c->Gz.planes != nullptr;   // mixed mode: 7-digit tensor-core GEMMs (FP64-class products)
+  OzOperand Cop;   // C~^T planes: rows i, K = mu (tensor-core path)
   if (tc) {
     TraceScope t(c->tracer, s, "grad H=B C~ (tcgen05 7 digits)", 0.0, 0);
-    OzOperand Cop = oz_slice(la, c->Ct, no, N, 1, no, 0, N, kOzMaxDigits, 0, c->Cz);
+    Cop = oz_slice(la, c->Ct, no, N, 1, no, 0, N, kOzMaxDigits, 0, c->Cz);
     OzGemmArgs g1;
     g1.A = c->Bop; g1.B = Cop; g1.M = NA * N; g1.N = no; g1.s = kOzMaxDigits; g1.C = c->Hb; g1.cs_m1 = no;
     g1.cs_n = 1;
@@ -1672,17 +1673,33 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
     gh.ldc = no;
     dgemm(la, gh);
   }
-  { TraceScope t(c->tracer, s, "grad Bij = C~^T H (batched dgemm)", 2.0 * NA * N * no * no, 0);
+  // Bij on the tensor cores when K = N fits one exponent block and the idle
+  // G' plane buffer holds the rows (P, j) of H
+  const bool tc_bij = tc && (N + kOzChunk - 1) / kOzChunk <= kOzMaxChunksPerBlock &&
+                      oz_plane_elems(NA * no, N, kOzMaxDigits) <= c->Gz.cap &&
+                      (size_t)((NA * no + kOzTileM - 1) / kOzTileM * kOzTileM) <= c->Gz.ecap;
+  if (tc_bij) {
+    // rows (P, j) of H (element (P, mu, j) at Hb[P N nocc + mu nocc + j]), K = mu; Bij[P]
+    // is symmetric in (i, j) and goes per P as [j][i] straight into [X~ | c]
+    TraceScope t(c->tracer, s, "grad Bij = C~^T H (tcgen05 7 digits)", 0.0, 0);
+    OzOperand Hop = oz_slice(la, c->Hb, NA * no, N, 1, no, 0, N, kOzMaxDigits, 0, c->Gz, no, (long long)N * no);
+    OzGemmArgs gb;
+    gb.A = Hop; gb.B = Cop; gb.M = NA * no; gb.N = no; gb.s = kOzMaxDigits; gb.C = c->Xt;
+    gb.MR = no; gb.cs_m1 = no; gb.cs_m2 = ldx; gb.cs_n = 1;
+    oz_gemm(la, gb);
+  } else {
+    TraceScope t(c->tracer, s, "grad Bij = C~^T H (batched dgemm)", 2.0 * NA * N * no * no, 0);
     GemmArgs gb;
     gb.M = no; gb.N = no; gb.K = N; gb.A = c->Ct; gb.lda = no; gb.transA = true;
     gb.B = c->Hb; gb.ldb = no; gb.sB = (long long)N * no; gb.C = c->Bij; gb.ldc = no; gb.sC = (long long)no * no;
     gb.batch = NA;
-    dgemm(la, gb); }
+    dgemm(la, gb);
+    RIHF_CUDA(cudaMemcpy2DAsync(c->Xt, ldx * sizeof(double), c->Bij, (size_t)no * no * sizeof(double),
+                                (size_t)no * no * sizeof(double), NA, cudaMemcpyDeviceToDevice, s));
+  }
   // [X~ | c] = L^{-T} [Bij | d]  (NA x (nocc^2 + 1)): the paper's X^P_ij = sum_Q A^L_PQ B^Q_ij
   // and L^P in one blocked solve (the solve is latency-bound, one extra column is free)
   { TraceScope t(c->tracer, s, "grad [X | c] = L^-T [Bij | d] (trsm)", (double)NA * NA * ldx, 0);
-    RIHF_CUDA(cudaMemcpy2DAsync(c->Xt, ldx * sizeof(double), c->Bij, (size_t)no * no * sizeof(double),
-                                (size_t)no * no * sizeof(double), NA, cudaMemcpyDeviceToDevice, s));
     RIHF_CUDA(cudaMemcpy2DAsync(c->Xt + (size_t)no * no, ldx * sizeof(double), c->dvec, sizeof(double),
                                 sizeof(double), NA, cudaMemcpyDeviceToDevice, s));
     trsm_lower(la, c->L, NA, c->Xt, ldx, true, 0, c->trsm_tmp);
@@ -1713,14 +1730,28 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   if (tc) {
     // G'[P] = Ct Xt[P] (N x nocc, Xt[P] symmetric), then one GEMM over rows
     // (P, mu): Y[(P, mu)][nu] += -1/2 sum_i G'[(P, mu)][i] Ct[nu][i]
-    { TraceScope t(c->tracer, s, "grad G' = C~ X (batched dgemm)", 2.0 * NA * N * no * no, 0);
+    OzOperand Top = oz_slice(la, c->Ct, N, no, no, 1, 0, no, kOzMaxDigits, 0, c->Ctz);   // rows mu, K = j
+    const bool tc_g = (no + kOzChunk - 1) / kOzChunk <= kOzMaxChunksPerBlock &&
+                      oz_plane_elems(NA * no, no, kOzMaxDigits) <= c->Hz.cap &&
+                      (size_t)((NA * no + kOzTileM - 1) / kOzTileM * kOzTileM) <= c->Hz.ecap;
+    if (tc_g) {
+      // rows (P, i) of X~ (element (P, i, j) at Xt[P ldx + i nocc + j]), K = j, in the
+      // idle RI-K H plane buffer; G'[P][mu][i] through the output's row split
+      TraceScope t(c->tracer, s, "grad G' = C~ X (tcgen05 7 digits)", 0.0, 0);
+      OzOperand Xr = oz_slice(la, c->Xt, NA * no, no, no, 1, 0, no, kOzMaxDigits, 0, c->Hz, no, ldx);
+      OzGemmArgs gg;
+      gg.A = Xr; gg.B = Top; gg.M = NA * no; gg.N = N; gg.s = kOzMaxDigits; gg.C = c->G;
+      gg.MR = no; gg.cs_m1 = 1; gg.cs_m2 = (long long)N * no; gg.cs_n = no;
+      oz_gemm(la, gg);
+    } else {
+      TraceScope t(c->tracer, s, "grad G' = C~ X (batched dgemm)", 2.0 * NA * N * no * no, 0);
       GemmArgs gg;
       gg.M = N; gg.N = no; gg.K = no; gg.A = c->Ct; gg.lda = no; gg.B = c->Xt; gg.ldb = no;
       gg.sB = ldx; gg.C = c->G; gg.ldc = no; gg.sC = (long long)N * no; gg.batch = NA;
-      dgemm(la, gg); }
+      dgemm(la, gg);
+    }
     TraceScope t(c->tracer, s, "grad Y=Dc-1/2 C~XC~^T (tcgen05 7 digits)", 0.0, 0);
     OzOperand Gop = oz_slice(la, c->G, NA * N, no, no, 1, 0, no, kOzMaxDigits, 0, c->Gz);
-    OzOperand Top = oz_slice(la, c->Ct, N, no, no, 1, 0, no, kOzMaxDigits, 0, c->Ctz);
     OzGemmArgs gy;
     gy.A = Gop; gy.B = Top; gy.M = NA * N; gy.N = N; gy.s = kOzMaxDigits; gy.alpha = -0.5; gy.C = c->Y;
     gy.cs_m1 = N; gy.cs_n = 1; gy.accumulate = true;

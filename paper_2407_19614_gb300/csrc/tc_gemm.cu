@@ -169,12 +169,15 @@ struct OzSrc {
   int rows, K;
   long long s_r, s_k1, s_k2;
   int KR;
+  int RR;             // > 0: rows split as (r % RR, r / RR) with strides s_r, s_r2
+  long long s_r2;
 };
 
 __device__ inline double oz_load(const OzSrc& S, int r, int k) {
   if (r >= S.rows || k >= S.K) return 0.0;
   const int q = k / S.KR, m = k - q * S.KR;
-  return S.X[(long long)r * S.s_r + (long long)m * S.s_k1 + (long long)q * S.s_k2];
+  const long long ro = S.RR > 0 ? (long long)(r % S.RR) * S.s_r + (long long)(r / S.RR) * S.s_r2 : (long long)r * S.s_r;
+  return S.X[ro + (long long)m * S.s_k1 + (long long)q * S.s_k2];
 }
 
 // exps[r * nkb + kb] = largest biased exponent of row r over K block kb
@@ -614,7 +617,7 @@ void oz_buf_free(OzBuf& b) {
 }
 
 OzOperand oz_slice(const LaCtx& la, const double* X, int rows, int K, long long s_r, long long s_k1,
-                   long long s_k2, int KR, int smax, int kb_chunks, const OzBuf& buf) {
+                   long long s_k2, int KR, int smax, int kb_chunks, const OzBuf& buf, int RR, long long s_r2) {
   if (rows <= 0 || K <= 0 || smax < 1 || smax > kOzMaxDigits || KR <= 0)
     throw RihfError(RIHF_ERR_INVALID_ARG, "oz_slice: bad arguments");
   uint16_t* planes = buf.planes;
@@ -631,7 +634,7 @@ OzOperand oz_slice(const LaCtx& la, const double* X, int rows, int K, long long 
   if (oz_plane_elems(rows, K, smax) > buf.cap || (size_t)op.rows_pad * op.nkb > buf.ecap)
     throw RihfError(RIHF_ERR_INVALID_ARG, "oz_slice: digit-plane buffer too small");
   if (op.kchunks > 65535) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_slice: K too long");
-  OzSrc S{X, rows, K, s_r, s_k1, s_k2, KR};
+  OzSrc S{X, rows, K, s_r, s_k1, s_k2, KR, RR, s_r2};
   dim3 grid(op.rows_pad / (kOzThreads / kCoreK), op.kchunks);
   RIHF_CUDA(cudaMemsetAsync(exps, 0, sizeof(int) * (size_t)op.rows_pad * op.nkb, la.stream));
   oz_emax_kernel<<<grid, kOzThreads, 0, la.stream>>>(S, op.kb_chunks, op.nkb, exps);
