@@ -611,11 +611,24 @@ void trsm_lower(const LaCtx& la, const double* L, int n, double* X, long long nc
 
 void trsm_lower_tc(const LaCtx& la, const double* L, int n, double* X, long long ncol, int symcols,
                    const TrsmTcScratch& sc) {
-  constexpr int PB = kTrsmPanel;   // panel width (K of each digit-plane update)
+  constexpr int PB = kTrsmPanel;   // inner panel width (K of the inner digit-plane updates)
   int blocks, threads;
   trsv_shape(la, ncol, blocks, threads);
-  for (int k = 0; k < n; k += PB) {
-    const int pb = std::min(PB, n - k);
+  // X[r0 + M rows] -= L[r0.., k..k+kk) X[k..k+kk) on the tensor cores
+  auto tc_update = [&](int r0, int M, int k, int kk) {
+    if (M <= 0) return;
+    OzGemmArgs g;
+    g.A = oz_slice(la, L + (size_t)r0 * n + k, M, kk, n, 1, 0, kk, kOzMaxDigits, 0, sc.L);
+    g.B = oz_slice(la, X + (size_t)k * ncol, (int)ncol, kk, 1, ncol, 0, kk, kOzMaxDigits, 0, sc.X);
+    g.M = M; g.N = (int)ncol; g.s = kOzMaxDigits; g.alpha = -1.0;
+    g.C = X + (size_t)r0 * ncol; g.cs_m1 = ncol; g.cs_n = 1;
+    g.accumulate = true; g.symcols = symcols;
+    oz_gemm(la, g);
+  };
+  for (int ko = 0; ko < n; ko += kTrsmOuter) {
+  const int ke = std::min(n, ko + kTrsmOuter);
+  for (int k = ko; k < ke; k += PB) {
+    const int pb = std::min(PB, ke - k);
     // the panel in FP64: 32-row substitution blocks and their in-panel updates
     for (int k2 = k; k2 < k + pb; k2 += CB) {
       const int b = std::min(CB, k + pb - k2);
@@ -633,16 +646,11 @@ void trsm_lower_tc(const LaCtx& la, const double* L, int n, double* X, long long
         dgemm(la, u);
       }
     }
-    // rows below the panel: X2 -= L21 X1 on the tensor cores
-    const int M = n - k - pb;
-    if (M <= 0) continue;
-    OzGemmArgs g;
-    g.A = oz_slice(la, L + (size_t)(k + pb) * n + k, M, pb, n, 1, 0, pb, kOzMaxDigits, 0, sc.L);
-    g.B = oz_slice(la, X + (size_t)k * ncol, (int)ncol, pb, 1, ncol, 0, pb, kOzMaxDigits, 0, sc.X);
-    g.M = M; g.N = (int)ncol; g.s = kOzMaxDigits; g.alpha = -1.0;
-    g.C = X + (size_t)(k + pb) * ncol; g.cs_m1 = ncol; g.cs_n = 1;
-    g.accumulate = true; g.symcols = symcols;
-    oz_gemm(la, g);
+    // rows of the outer panel below this panel
+    tc_update(k + pb, ke - k - pb, k, pb);
+  }
+  // all rows below the outer panel: one rank-(ke - ko) update
+  tc_update(ke, n - ke, ko, ke - ko);
   }
 }
 

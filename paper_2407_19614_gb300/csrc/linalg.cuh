@@ -74,12 +74,16 @@ void to_float(const LaCtx& la, const double* in, long long n, float* out, double
 // Mirror the lower triangle into the upper one for each of `batch` n x n slices.
 void symmetrize_lower(const LaCtx& la, double* X, int n, int batch);
 
-// Forward substitution X <- L^{-1} X (as trsm_lower with trans = false) whose
-// rank-64 updates of the rows below each 64-row panel run on the tensor cores
-// as 7-digit BF16 digit-plane GEMMs (FP64-class products, tc_gemm.cuh); the
-// panels themselves are solved in FP64.  Scratch: oz_buf_alloc(n, kTrsmPanel,
-// 7, 1) for L and oz_buf_alloc(ncol, kTrsmPanel, 7, 1) for the panel of X.
+// Forward substitution X <- L^{-1} X (as trsm_lower with trans = false) in two
+// levels: inside each kTrsmOuter-row panel, 64-row panels solved in FP64 with
+// rank-64 updates of the panel's rows below them; then one rank-kTrsmOuter
+// update of all rows below the outer panel.  The updates run on the tensor
+// cores as 7-digit BF16 digit-plane GEMMs (FP64-class products, tc_gemm.cuh);
+// the outer ones touch the rows below once per 256 rows of L instead of once
+// per 64.  Scratch: oz_buf_alloc(n, kTrsmOuter, 7, 1) for L and
+// oz_buf_alloc(ncol, kTrsmOuter, 7, 1) for a panel of X.
 constexpr int kTrsmPanel = 64;
+constexpr int kTrsmOuter = 256;
 struct TrsmTcScratch {
   OzBuf L, X;   // kTrsmPanel-column slices of L (n rows) and of the X panel (ncol rows)
 };

@@ -941,8 +941,8 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
       c->Bz = oz_buf_alloc(NA * N, N, kOzMaxDigits, 1);
       c->Cz = oz_buf_alloc(no, N, kOzMaxDigits, 1);
       c->Hz = oz_buf_alloc(N, NA * no, kOzMaxDigits, nkb_max);
-      c->trsm_sc.L = oz_buf_alloc(NA, kTrsmPanel, kOzMaxDigits, 1);
-      c->trsm_sc.X = oz_buf_alloc(N * N, kTrsmPanel, kOzMaxDigits, 1);
+      c->trsm_sc.L = oz_buf_alloc(NA, kTrsmOuter, kOzMaxDigits, 1);
+      c->trsm_sc.X = oz_buf_alloc(N * N, kTrsmOuter, kOzMaxDigits, 1);
       c->Ctz = oz_buf_alloc(N, no, kOzMaxDigits, 1);
       c->Gz = oz_buf_alloc(NA * N, no, kOzMaxDigits, 1);
       c->Xz = oz_buf_alloc(NA, no * no, kOzMaxDigits, 1);
