@@ -654,6 +654,51 @@ void trsm_lower_tc(const LaCtx& la, const double* L, int n, double* X, long long
   }
 }
 
+void trsm_lower_t_tc(const LaCtx& la, const double* L, int n, double* X, long long ncol, int symcols,
+                     const TrsmTcScratch& sc) {
+  constexpr int PB = kTrsmPanel;
+  int blocks, threads;
+  trsv_shape(la, ncol, blocks, threads);
+  // X[r0 .. r0+M) -= L[k..k+kk, r0..r0+M)^T X[k..k+kk) on the tensor cores
+  auto tc_update = [&](int r0, int M, int k, int kk) {
+    if (M <= 0) return;
+    OzGemmArgs g;
+    g.A = oz_slice(la, L + (size_t)k * n + r0, M, kk, 1, n, 0, kk, kOzMaxDigits, 0, sc.L);
+    g.B = oz_slice(la, X + (size_t)k * ncol, (int)ncol, kk, 1, ncol, 0, kk, kOzMaxDigits, 0, sc.X);
+    g.M = M; g.N = (int)ncol; g.s = kOzMaxDigits; g.alpha = -1.0;
+    g.C = X + (size_t)r0 * ncol; g.cs_m1 = ncol; g.cs_n = 1;
+    g.accumulate = true; g.symcols = symcols;
+    oz_gemm(la, g);
+  };
+  // outer panels [ko, ke) from the bottom; inner 64-row panels and 32-row
+  // substitution blocks aligned to multiples of their size, also from the bottom
+  for (int ko = (n - 1) / kTrsmOuter * kTrsmOuter; ko >= 0; ko -= kTrsmOuter) {
+    const int ke = std::min(n, ko + kTrsmOuter);
+    for (int k = ko + (ke - ko - 1) / PB * PB; k >= ko; k -= PB) {
+      const int kend = std::min(ke, k + PB);
+      for (int k2 = k + (kend - k - 1) / CB * CB; k2 >= k; k2 -= CB) {
+        const int b = std::min(CB, kend - k2);
+        trsv_block_kernel<<<blocks, threads, 0, la.stream>>>(L, n, k2, b, X, ncol, 1, symcols);
+        RIHF_LAUNCH_CHECK();
+        count(la);
+        if (k2 > k) {   // rows [k, k2) of the panel: X -= L[k2:k2+b, k:k2]^T X_k2
+          GemmArgs u;
+          u.M = k2 - k; u.N = (int)ncol; u.K = b;
+          u.A = L + (size_t)k2 * n + k; u.lda = n; u.transA = true;
+          u.B = X + (size_t)k2 * ncol; u.ldb = (int)ncol;
+          u.C = X + (size_t)k * ncol; u.ldc = (int)ncol;
+          u.alpha = -1.0; u.beta = 1.0; u.symcols = symcols;
+          dgemm(la, u);
+        }
+      }
+      // rows of the outer panel above this panel
+      tc_update(ko, k - ko, k, kend - k);
+    }
+    // all rows above the outer panel: one rank-(ke - ko) update
+    tc_update(0, ko, ko, ke - ko);
+  }
+}
+
 // ------------------------------------------------------------ eigensolver
 
 constexpr int JT = 1024;   // Jacobi threads (one CTA)

@@ -89,6 +89,11 @@ struct TrsmTcScratch {
 };
 void trsm_lower_tc(const LaCtx& la, const double* L, int n, double* X, long long ncol, int symcols,
                    const TrsmTcScratch& sc);
+// Backward substitution X <- L^{-T} X (as trsm_lower with trans = true), blocked
+// the same way from the bottom: the updates of the rows above a panel,
+// X[0:k] -= L[k:k+b, 0:k]^T X[k:k+b], run as 7-digit tensor-core GEMMs.
+void trsm_lower_t_tc(const LaCtx& la, const double* L, int n, double* X, long long ncol, int symcols,
+                     const TrsmTcScratch& sc);
 
 // In-place Cholesky A = L L^T (lower, upper part zeroed) of an n x n matrix;
 // sets *flag = 1 on a non-positive pivot.  Then Linv = L^{-1} (n x n).

@@ -1699,10 +1699,14 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   }
   // [X~ | c] = L^{-T} [Bij | d]  (NA x (nocc^2 + 1)): the paper's X^P_ij = sum_Q A^L_PQ B^Q_ij
   // and L^P in one blocked solve (the solve is latency-bound, one extra column is free)
-  { TraceScope t(c->tracer, s, "grad [X | c] = L^-T [Bij | d] (trsm)", (double)NA * NA * ldx, 0);
+  { TraceScope t(c->tracer, s, "grad [X | c] = L^-T [Bij | d] (trsm; tcgen05 updates in mixed mode)",
+                 (double)NA * NA * ldx, 0);
     RIHF_CUDA(cudaMemcpy2DAsync(c->Xt + (size_t)no * no, ldx * sizeof(double), c->dvec, sizeof(double),
                                 sizeof(double), NA, cudaMemcpyDeviceToDevice, s));
-    trsm_lower(la, c->L, NA, c->Xt, ldx, true, 0, c->trsm_tmp);
+    if (c->trsm_sc.X.planes && oz_plane_elems(ldx, kTrsmOuter, kOzMaxDigits) <= c->trsm_sc.X.cap)
+      trsm_lower_t_tc(la, c->L, NA, c->Xt, ldx, 0, c->trsm_sc);   // mixed mode: tensor-core updates
+    else
+      trsm_lower(la, c->L, NA, c->Xt, ldx, true, 0, c->trsm_tmp);
     RIHF_CUDA(cudaMemcpy2DAsync(c->cvec, sizeof(double), c->Xt + (size_t)no * no, ldx * sizeof(double),
                                 sizeof(double), NA, cudaMemcpyDeviceToDevice, s)); }
   // Z = c c^T - 1/2 Xt Xt^T
