@@ -272,6 +272,7 @@ struct OzBook {
   uint32_t tslot;
   int abort;
   int issued, consumed;
+  int dwait[2];        // the drain poller's wait results, alternating slots
 };
 static_assert(sizeof(OzBook) <= kBookBytes, "bookkeeping block");
 
@@ -347,10 +348,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       mbar_init(&bk->empty[i], 1);
     }
     mbar_init(&bk->accfull, 1);
-    for (int d = 0; d < kOzMaxDigits; ++d) mbar_init(&bk->accempty[d], kDrainThreads);
+    // one arrival per drain warp (its lane 0, after the warp's reads)
+    for (int d = 0; d < kOzMaxDigits; ++d) mbar_init(&bk->accempty[d], kDrainThreads / 32);
     for (int k = 0; k < kItemSlots; ++k) {
       mbar_init(&bk->item_full[k], 1);
-      mbar_init(&bk->item_empty[k], kDrainThreads + 1);
+      mbar_init(&bk->item_empty[k], kDrainThreads / 32 + 1);
     }
     bk->abort = 0;
     bk->issued = bk->consumed = 0;
@@ -476,13 +478,24 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int row = 32 * (warp & 3) + lane;
     const int ncol = TN / 2, col0 = (warp >> 2) * ncol;
     const uint32_t t_row = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
+    // one thread polls, the other drain threads wait on a hardware named
+    // barrier (spinning 256 threads would compete with the copy and MMA
+    // threads for issue slots and for the barrier unit)
+    int nwait = 0;
+    auto drain_wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+      const int k = nwait++ & 1;
+      if (tid == 0) bk->dwait[k] = oz_wait(bar, parity, abort) ? 1 : 0;
+      asm volatile("bar.sync 1, %0;" ::"r"(kDrainThreads) : "memory");
+      return *(volatile int*)&bk->dwait[k] != 0;
+    };
     uint32_t grp = 0;
     for (int q = 0;; ++q) {
       const int slot = q % kItemSlots;
-      bool ok = oz_wait(&bk->item_full[slot], (q / kItemSlots) & 1, abort);
-      if (!__all_sync(0xffffffffu, ok)) break;
+      bool ok = drain_wait(&bk->item_full[slot], (q / kItemSlots) & 1);
+      if (!ok) break;
       const int idx = *(volatile int*)&bk->item[slot];
-      mbar_arrive(&bk->item_empty[slot]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bk->item_empty[slot]);
       if (idx < 0) break;
       int mt, nt, split, c0, c1;
       oz_decode(T, idx, mt, nt, split, c0, c1);
@@ -490,11 +503,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 #pragma unroll
       for (int k = 0; k < kOzMaxTN / 2; ++k) acc[k] = 0;
       for (int c = c0; c < c1 && ok; c += T.G) {
-        ok = oz_wait(&bk->accfull, grp & 1, abort);
-        if (!__all_sync(0xffffffffu, ok)) {
-          ok = false;
-          break;
-        }
+        ok = drain_wait(&bk->accfull, grp & 1);
+        if (!ok) break;
         tc_fence_after();
         for (int g = 2; g <= s + 1; ++g) {
           const int sh = 37 - 8 * (g - 2);
@@ -505,7 +515,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             if (8 * q8 < ncol) tmem_ld8(tg + 8 * q8, r[q8]);
           tmem_wait_ld();
           tc_fence_before();
-          mbar_arrive(&bk->accempty[g - 2]);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bk->accempty[g - 2]);
 #pragma unroll
           for (int q8 = 0; q8 < kOzMaxTN / 16; ++q8) {
             if (8 * q8 < ncol) {
