@@ -411,8 +411,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     __syncwarp();
   } else if (warp == 8) {
     if (lane == 0) {   // ---------------- MMA issuer
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                             ((uint32_t)(kOzTileM >> 4) << 24);
+      // BF16 x BF16 -> FP32, M = 128; N is set per MMA
+      const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzTileM >> 4) << 24);
+      const int planes_per_mma = 256 / TN;
       uint32_t i = 0, grp = 0;
       int last_st = -1;
       uint32_t last_par = 0;
@@ -437,24 +438,25 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           // into the 14-bit address field (shared addresses stay below 256 KB)
           const uint32_t a_s = smem_addr(smem + (size_t)st * T.stage_bytes);
           const uint64_t a_d0 = smem_desc(a_s), b_d0 = smem_desc(a_s + a_bytes);
+          // one MMA per (K step, A plane t, group of B planes): the B planes
+          // u = 1..s+1-t lie one after another in shared memory with the same
+          // 8-row-group stride, so up to 256 / TN of them form one operand of
+          // N = count * TN rows, and the product (t, u) lands on the columns
+          // of anti-diagonal t + u
           for (int j = 0; j < kOzChunk / 16 && ok; ++j)
-            for (int g = 2; g <= s + 1; ++g) {
-              if (first && j == 0 && grp > 0) {
-                if (!oz_wait(&bk->accempty[g - 2], (grp - 1) & 1, abort)) {
-                  ok = false;
-                  break;
-                }
+            for (int t = 1; t <= s && ok; ++t) {
+              if (t == 1 && j == 0 && first && grp > 0) {   // every diagonal read out
+                for (int d = 0; d < s && ok; ++d)
+                  if (!oz_wait(&bk->accempty[d], (grp - 1) & 1, abort)) ok = false;
+                if (!ok) break;
                 tc_fence_after();
               }
-              const uint32_t d = taddr + (uint32_t)((g - 2) * TN);
-              uint64_t ad = a_d0 + (uint64_t)((j * 256) >> 4);
-              uint64_t bd = b_d0 + (uint64_t)(((g - 2) * b_plane + j * 256) >> 4);
-              const uint64_t a_step = (kPlaneElems * 2) >> 4, b_step = b_plane >> 4;
-              mma_bf16(d, ad, bd, idesc, (first && j == 0) ? 0u : 1u);
-              for (int t = 2; t < g; ++t) {
-                ad += a_step;
-                bd -= b_step;
-                mma_bf16(d, ad, bd, idesc, 1u);
+              const uint64_t ad = a_d0 + (uint64_t)(((t - 1) * kPlaneElems * 2 + j * 256) >> 4);
+              for (int u0 = 1; u0 <= s + 1 - t; u0 += planes_per_mma) {
+                const int np = min(planes_per_mma, s + 2 - t - u0);
+                const uint32_t id = idesc0 | ((uint32_t)((np * TN) >> 3) << 17);
+                const uint64_t bd = b_d0 + (uint64_t)(((u0 - 1) * b_plane + j * 256) >> 4);
+                mma_bf16(taddr + (uint32_t)((t + u0 - 2) * TN), ad, bd, id, (t == 1 && j == 0 && first) ? 0u : 1u);
               }
             }
           mma_commit(&bk->empty[st]);   // the stage is free once these MMAs are done

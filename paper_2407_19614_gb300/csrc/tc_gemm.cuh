@@ -14,8 +14,12 @@
 // integer and the two block exponents.
 //
 // s = 7 keeps 55 bits relative to max|row| * max|col| of each K block;
-// fewer digits trade accuracy for tensor work (s (s + 1) / 2 BF16 MMAs per
-// output tile and K chunk).
+// fewer digits trade accuracy for tensor work (s (s + 1) / 2 digit products
+// per output tile and K step).  The products of one A digit plane with all
+// the B planes it pairs with run as one MMA (or a few, N <= 256): the B planes
+// are adjacent in shared memory and form a single operand whose output
+// columns fall on the anti-diagonals, so a K step costs about s MMA
+// instructions instead of s (s + 1) / 2 small ones.
 #pragma once
 #include <cstdint>
 
