@@ -401,6 +401,40 @@ __global__ void potrf_diag_kernel(double* A, int n, int k, int b, double* inv, i
   }
 }
 
+// The factorisation alone, one warp: lane r keeps row r of the b x b block in
+// registers (columns unrolled), pivots and column entries travel by shuffle,
+// and each pivot costs one reciprocal square root (l_jj = d r, the column
+// scaled by r) -- the pivots form the kernel's serial chain.
+__global__ void __launch_bounds__(32) potrf_diag_reg_kernel(double* A, int n, int k, int b, int* flag) {
+  const int lane = threadIdx.x;
+  double a[CB];
+#pragma unroll
+  for (int c = 0; c < CB; ++c) a[c] = (lane < b && c < b && c <= lane) ? A[(size_t)(k + lane) * n + k + c] : 0.0;
+#pragma unroll
+  for (int j = 0; j < CB; ++j) {
+    if (j < b) {
+      double d = __shfl_sync(0xffffffffu, a[j], j);
+      if (!(d > 0.0)) {
+        if (lane == 0) atomicExch(flag, 1);
+        d = 1.0;
+      }
+      const double r = rsqrt(d);
+      if (lane == j) a[j] = d * r;
+      else if (lane > j) a[j] *= r;
+#pragma unroll
+      for (int c = j + 1; c < CB; ++c) {
+        const double lcj = __shfl_sync(0xffffffffu, a[j], c);
+        if (lane >= c) a[c] = fma(-a[j], lcj, a[c]);
+      }
+    }
+  }
+  if (lane < b) {
+#pragma unroll
+    for (int c = 0; c < CB; ++c)
+      if (c < b) A[(size_t)(k + lane) * n + k + c] = c <= lane ? a[c] : 0.0;
+  }
+}
+
 __global__ void zero_upper_kernel(double* A, int n) {
   long long total = (long long)n * n;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -444,9 +478,10 @@ __global__ void __launch_bounds__(256) chol_panel_kernel(double* A, int n, int k
 }
 
 void cholesky(const LaCtx& la, double* A, int n, double* scratch) {
+  (void)scratch;   // the diagonal blocks are factored in registers
   for (int k = 0; k < n; k += CB) {
     int b = std::min(CB, n - k);
-    potrf_diag_kernel<<<1, 32, 0, la.stream>>>(A, n, k, b, scratch, la.flag, 1, 0);
+    potrf_diag_reg_kernel<<<1, 32, 0, la.stream>>>(A, n, k, b, la.flag);
     RIHF_LAUNCH_CHECK();
     count(la);
     int rest = n - k - b;
