@@ -850,25 +850,12 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ A
   for (int i = threadIdx.x; i < m; i += JT) W[i] = a[i * m + i];
 }
 
-// One-sided (Hestenes) Jacobi in FP32, one CTA: with B = A + sigma I positive
-// definite (sigma from a Gershgorin bound), column rotations U <- U J drive the
-// columns of U = B V to mutual orthogonality; then v_j = u_j / |u_j| and
-// lambda_j = |u_j| - sigma.  Only U (n x n, column-major, shared memory when it
-// fits) is stored; a warp owns one column pair per round (round-robin pairing),
-// its dot products reduced with shuffles.  For n <= 256 a pair's columns stay
-// in registers between the dot product and the rotation, and the squared
-// column norms are carried along by the rotation identities
-// |u_p'|^2 = |u_p|^2 - t (u_p . u_q), |u_q'|^2 = |u_q|^2 + t (u_p . u_q)
-// (recomputed at every sweep), so a pair costs one reduction, not three.
-__global__ void __launch_bounds__(JT) jacobi1s_kernel(const double* __restrict__ A, int n, int m, float* gU, float* V,
-                                                      float* W, int use_smem, int max_sweeps, float tol) {
-  extern __shared__ float sm[];
-  __shared__ float red[32];
-  __shared__ float nrm[32 * kJRows];
-  __shared__ int notconv;
-  float* U = use_smem ? sm : gU;   // column j at U[j*n .. j*n+n)
+constexpr int kJB = 64;   // column blocks of the block one-sided Jacobi (two per warp)
+
+// U (column-major, n x n) = A + sigma I with the Gershgorin shift sigma =
+// 1.05 max_i sum_j |A_ij|, which makes the matrix positive definite.
+__device__ float jacobi_shifted_copy(const double* __restrict__ A, int n, float* U, float* red) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // Gershgorin shift: sigma = max_i sum_j |A_ij| (+ a margin) makes A + sigma I PD
   float g = 0.f;
   for (int i = warp; i < n; i += JT / 32) {
     float s = 0.f;
@@ -888,6 +875,44 @@ __global__ void __launch_bounds__(JT) jacobi1s_kernel(const double* __restrict__
   for (int j = warp; j < n; j += JT / 32)
     for (int i = lane; i < n; i += 32) U[(size_t)j * n + i] = (float)A[(size_t)i * n + j] + (i == j ? sigma : 0.f);
   __syncthreads();
+  return sigma;
+}
+
+// Eigenpairs of the orthogonalised columns: v_j = u_j / |u_j|, lambda_j =
+// |u_j| - sigma; V row-major n x m.
+__device__ void jacobi_eigenpairs(const float* U, int n, int m, float sigma, float* V, float* W) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = warp; j < n; j += JT / 32) {
+    const float* u = U + (size_t)j * n;
+    float s = 0.f;
+    for (int i = lane; i < n; i += 32) s = fmaf(u[i], u[i], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    float nrm = sqrtf(s);
+    float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+    for (int i = lane; i < n; i += 32) V[(size_t)i * m + j] = u[i] * inv;
+    if (lane == 0) W[j] = nrm - sigma;
+  }
+}
+
+// One-sided (Hestenes) Jacobi in FP32, one CTA: with B = A + sigma I positive
+// definite (sigma from a Gershgorin bound), column rotations U <- U J drive the
+// columns of U = B V to mutual orthogonality; then v_j = u_j / |u_j| and
+// lambda_j = |u_j| - sigma.  Only U (n x n, column-major, shared memory when it
+// fits) is stored; a warp owns one column pair per round (round-robin pairing),
+// its dot products reduced with shuffles.  For n <= 256 a pair's columns stay
+// in registers between the dot product and the rotation, and the squared
+// column norms are carried along by the rotation identities
+// |u_p'|^2 = |u_p|^2 - t (u_p . u_q), |u_q'|^2 = |u_q|^2 + t (u_p . u_q)
+// (recomputed at every sweep), so a pair costs one reduction, not three.
+__global__ void __launch_bounds__(JT) jacobi1s_kernel(const double* __restrict__ A, int n, int m, float* gU, float* V,
+                                                      float* W, int use_smem, int max_sweeps, float tol) {
+  extern __shared__ float sm[];
+  __shared__ float red[32];
+  __shared__ float nrm[32 * kJRows];
+  __shared__ int notconv;
+  float* U = use_smem ? sm : gU;   // column j at U[j*n .. j*n+n)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float sigma = jacobi_shifted_copy(A, n, U, red);
   const int half = m / 2;
   const bool in_regs = n <= 32 * kJRows;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -977,17 +1002,113 @@ __global__ void __launch_bounds__(JT) jacobi1s_kernel(const double* __restrict__
     if (!notconv) break;
     __syncthreads();
   }
-  // eigenpairs: v_j = u_j / |u_j|, lambda_j = |u_j| - sigma; V row-major n x m
-  for (int j = warp; j < n; j += JT / 32) {
-    const float* u = U + (size_t)j * n;
-    float s = 0.f;
-    for (int i = lane; i < n; i += 32) s = fmaf(u[i], u[i], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    float nrm = sqrtf(s);
-    float inv = nrm > 0.f ? 1.f / nrm : 0.f;
-    for (int i = lane; i < n; i += 32) V[(size_t)i * m + j] = u[i] * inv;
-    if (lane == 0) W[j] = nrm - sigma;
+  jacobi_eigenpairs(U, n, m, sigma, V, W);
+}
+
+// Block one-sided Jacobi (n <= 64 H): the columns form kJB = 64 blocks of H;
+// warp w holds two blocks in registers (H columns x R rows per lane each), and
+// a round rotates every pair across its two blocks (round 0 also the pairs
+// inside each block) before the blocks move on through U in shared memory.
+// The block pairs follow the round-robin order of the column kernel, so a
+// sweep is kJB - 1 rounds instead of n - 1 and moves a third of the shared-
+// memory traffic; column norms are carried as there.
+template <int H>
+__global__ void __launch_bounds__(JT) jacobi1s_block_kernel(const double* __restrict__ A, int n, int m, float* gU,
+                                                            float* V, float* W, int use_smem, int max_sweeps,
+                                                            float tol) {
+  constexpr int R = 2 * H;   // rows per lane
+  extern __shared__ float sm[];
+  __shared__ float red[32];
+  __shared__ float nrm[kJB * H];
+  __shared__ int notconv;
+  float* U = use_smem ? sm : gU;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float sigma = jacobi_shifted_copy(A, n, U, red);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) notconv = 0;
+    for (int j = warp; j < kJB * H; j += JT / 32) {
+      float s2 = 0.f;
+      if (j < n) {
+        const float* u = U + (size_t)j * n;
+        for (int i = lane; i < n; i += 32) s2 = fmaf(u[i], u[i], s2);
+      }
+      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      if (lane == 0) nrm[j] = s2;
+    }
+    __syncthreads();
+    for (int r = 0; r < kJB - 1; ++r) {
+      int bA, bB;
+      if (warp == 0) {
+        bA = kJB - 1;
+        bB = r;
+      } else {
+        bA = (r + warp) % (kJB - 1);
+        bB = (r - warp + (kJB - 1)) % (kJB - 1);
+      }
+      float x[2 * H][R];
+      float cn[2 * H];
+#pragma unroll
+      for (int c = 0; c < 2 * H; ++c) {
+        const int g = (c < H ? bA * H + c : bB * H + c - H);
+        cn[c] = nrm[g];
+#pragma unroll
+        for (int e = 0; e < R; ++e) {
+          const int i = lane + 32 * e;
+          x[c][e] = (g < n && i < n) ? U[(size_t)g * n + i] : 0.f;
+        }
+      }
+      bool rotated = false;
+      auto rot = [&](float (&xp)[R], float (&xq)[R], float& a, float& b) {
+        float c = 0.f;
+#pragma unroll
+        for (int e = 0; e < R; ++e) c = fmaf(xp[e], xq[e], c);
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (fabsf(c) <= tol * sqrtf(a * b)) return;   // converged pair, or a zero (padding) column
+        rotated = true;
+        const float zeta = (b - a) / (2.f * c);
+        const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        const float cs = rsqrtf(1.f + t * t), sn = cs * t;
+#pragma unroll
+        for (int e = 0; e < R; ++e) {
+          const float u = xp[e], v = xq[e];
+          xp[e] = cs * u - sn * v;
+          xq[e] = sn * u + cs * v;
+        }
+        a -= t * c;
+        b += t * c;
+      };
+      if (r == 0) {
+#pragma unroll
+        for (int p = 0; p < H; ++p)
+#pragma unroll
+          for (int q = p + 1; q < H; ++q) {
+            rot(x[p], x[q], cn[p], cn[q]);
+            rot(x[H + p], x[H + q], cn[H + p], cn[H + q]);
+          }
+      }
+#pragma unroll
+      for (int p = 0; p < H; ++p)
+#pragma unroll
+        for (int q = 0; q < H; ++q) rot(x[p], x[H + q], cn[p], cn[H + q]);
+#pragma unroll
+      for (int c = 0; c < 2 * H; ++c) {
+        const int g = (c < H ? bA * H + c : bB * H + c - H);
+        if (g < n) {
+#pragma unroll
+          for (int e = 0; e < R; ++e) {
+            const int i = lane + 32 * e;
+            if (i < n) U[(size_t)g * n + i] = x[c][e];
+          }
+          if (lane == 0) nrm[g] = cn[c];
+        }
+      }
+      if (rotated && lane == 0) notconv = 1;
+      __syncthreads();
+    }
+    if (!notconv) break;
+    __syncthreads();
   }
+  jacobi_eigenpairs(U, n, m, sigma, V, W);
 }
 
 // Sort eigenpairs ascending (rank sort) and expand to FP64: X[:, rank] = V[:, i].
@@ -1166,12 +1287,25 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
   }
   size_t smem = (size_t)n * n * sizeof(float);
   int use_smem = smem <= 215 * 1024 ? 1 : 0;
-  if (use_smem)
-    raise_smem_limit((const void*)jacobi1s_kernel, (int)smem);
   // a looser stop (n eps) leaves close clusters too coarse for the FP64
   // refinement to separate
   const float tol = 2e-6f;
-  jacobi1s_kernel<<<1, JT, use_smem ? smem : 0, la.stream>>>(Ain, n, m, fA, fV, fW, use_smem, max_sweeps, tol);
+  const int hb = (n + kJB - 1) / kJB;   // block width of the block kernel
+  if (hb <= 3) {
+    const void* fn = hb == 1 ? (const void*)jacobi1s_block_kernel<1>
+                   : hb == 2 ? (const void*)jacobi1s_block_kernel<2> : (const void*)jacobi1s_block_kernel<3>;
+    if (use_smem) raise_smem_limit(fn, (int)smem);
+    const int sz = use_smem ? (int)smem : 0;
+    if (hb == 1)
+      jacobi1s_block_kernel<1><<<1, JT, sz, la.stream>>>(Ain, n, m, fA, fV, fW, use_smem, max_sweeps, tol);
+    else if (hb == 2)
+      jacobi1s_block_kernel<2><<<1, JT, sz, la.stream>>>(Ain, n, m, fA, fV, fW, use_smem, max_sweeps, tol);
+    else
+      jacobi1s_block_kernel<3><<<1, JT, sz, la.stream>>>(Ain, n, m, fA, fV, fW, use_smem, max_sweeps, tol);
+  } else {
+    if (use_smem) raise_smem_limit((const void*)jacobi1s_kernel, (int)smem);
+    jacobi1s_kernel<<<1, JT, use_smem ? smem : 0, la.stream>>>(Ain, n, m, fA, fV, fW, use_smem, max_sweeps, tol);
+  }
   RIHF_LAUNCH_CHECK();
   count(la);
   eig_sort_kernel<<<1, 1024, 0, la.stream>>>(fV, fW, n, m, V, W);
