@@ -1125,11 +1125,11 @@ __global__ void eig_sort_kernel(const float* __restrict__ V, const float* __rest
     rank[i] = r;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    int row = idx / n, i = idx % n;
-    X[(size_t)row * n + rank[i]] = (double)V[row * m + i];
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) Wd[rank[i]] = (double)W[i];
+  // every block ranks all n values, then moves its own rows
+  for (int row = blockIdx.x; row < n; row += gridDim.x)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) X[(size_t)row * n + rank[i]] = (double)V[row * m + i];
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Wd[rank[i]] = (double)W[i];
 }
 
 // Ogita-Aishima step pieces: lam_i = S_ii/(1-R_ii); E_ij as in their Algorithm 1.
@@ -1234,11 +1234,11 @@ __global__ void eig_sort64_kernel(const double* __restrict__ V, const double* __
     rank[i] = r;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    int row = idx / n, i = idx % n;
-    Vout[(size_t)row * n + rank[i]] = V[(size_t)row * n + i];
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) Wout[rank[i]] = lam[i];
+  // every block ranks all n values, then moves its own rows
+  for (int row = blockIdx.x; row < n; row += gridDim.x)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Vout[(size_t)row * n + rank[i]] = V[(size_t)row * n + i];
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Wout[rank[i]] = lam[i];
 }
 
 void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double* ws, int refine,
@@ -1252,7 +1252,7 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
     double* lam = d + 6 * (size_t)n * n;
     RIHF_CUDA(cudaMemcpyAsync(V, Vguess, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, la.stream));
     eigh(la, A, n, W, V, ws, -refine, nullptr, false, max_sweeps, ns_steps);
-    eig_sort64_kernel<<<1, 1024, 0, la.stream>>>(V, lam, n, Vs, W);
+    eig_sort64_kernel<<<std::min(n, 32), 256, 0, la.stream>>>(V, lam, n, Vs, W);
     RIHF_LAUNCH_CHECK();
     count(la);
     RIHF_CUDA(cudaMemcpyAsync(V, Vs, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, la.stream));
@@ -1308,7 +1308,7 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
   }
   RIHF_LAUNCH_CHECK();
   count(la);
-  eig_sort_kernel<<<1, 1024, 0, la.stream>>>(fV, fW, n, m, V, W);
+  eig_sort_kernel<<<std::min(n, 32), 256, 0, la.stream>>>(fV, fW, n, m, V, W);
   RIHF_LAUNCH_CHECK();
   count(la);
   if (Vguess) {
@@ -1403,25 +1403,6 @@ __global__ void dot_kernel(long long n, const double* x, const double* y, double
 }
 void dot(const LaCtx& la, int n, const double* x, const double* y, double* out) {
   dot_kernel<<<1, 1024, 0, la.stream>>>(n, x, y, out);
-  RIHF_LAUNCH_CHECK();
-  count(la);
-}
-
-__global__ void maxabs_kernel(long long n, const double* x, double* out) {
-  __shared__ double r[32];
-  double s = 0.0;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) s = fmax(s, fabs(x[i]));
-  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
-  if ((threadIdx.x & 31) == 0) r[threadIdx.x / 32] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)blockDim.x / 32; ++w) t = fmax(t, r[w]);
-    *out = t;
-  }
-}
-void maxabs(const LaCtx& la, int n, const double* x, double* out) {
-  maxabs_kernel<<<1, 1024, 0, la.stream>>>(n, x, out);
   RIHF_LAUNCH_CHECK();
   count(la);
 }

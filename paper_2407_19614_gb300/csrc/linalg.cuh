@@ -125,7 +125,6 @@ void axpby(const LaCtx& la, int n, double a, const double* x, double b, const do
 void add3(const LaCtx& la, int n, const double* x, const double* y, const double* z, double* out);
 // out[0] = sum x*y (deterministic two-level reduction)
 void dot(const LaCtx& la, int n, const double* x, const double* y, double* out);
-void maxabs(const LaCtx& la, int n, const double* x, double* out);
 void scale_copy(const LaCtx& la, int n, double a, const double* x, double* out);
 // C = A - A^T for square n x n
 void antisym(const LaCtx& la, const double* A, double* C, int n);

@@ -203,25 +203,6 @@ void upload(T* d, const std::vector<T>& h, cudaStream_t s) {
 
 // ============================================================ DIIS kernels
 
-__global__ void diis_dots_kernel(const double* __restrict__ ring, long long len, int s, int m, double* Bm, int ld) {
-  __shared__ double red[32];
-  int j = blockIdx.x;
-  if (j >= m) return;
-  const double* a = ring + (long long)s * len;
-  const double* b = ring + (long long)j * len;
-  double v = 0.0;
-  for (long long i = threadIdx.x; i < len; i += blockDim.x) v += a[i] * b[i];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)blockDim.x / 32; ++w) t += red[w];
-    Bm[s * ld + j] = t;
-    Bm[j * ld + s] = t;
-  }
-}
-
 // Pulay system [B -1; -1 0] [c; lambda] = [0; -1], B scaled by its largest
 // diagonal entry; Gaussian elimination with partial pivoting (one warp).
 __global__ void diis_solve_kernel(const double* __restrict__ Bm, int ld, int m, double* coef) {
@@ -277,41 +258,120 @@ __global__ void diis_extrap_kernel(const double* __restrict__ ring, long long le
 // out[0] = max_ij |A_ij - sub * delta_ij| over all i, j (offdiag = 0), over
 // i != j (offdiag = 1), or over the block i < offdiag - 1 <= j, i.e. between
 // the first (offdiag - 1) indices and the rest (offdiag > 1); one block.
-__global__ void eig_check_kernel(const double* __restrict__ A, int n, double sub, int offdiag, double* out) {
+// ---------------------------------------------------------------- multi-block reductions
+// Small reductions over n^2 elements spread over kRedBlocks blocks: every block
+// leaves a partial in part[], the last block to finish (a ticket counter)
+// folds the partials in block order -- deterministic -- and resets the ticket.
+constexpr int kRedBlocks = 32;
+constexpr int kRedDiis = 8;   // blocks per DIIS dot product
+constexpr int kRedSlots = 128;
+
+__device__ inline double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;   // valid in thread 0
+}
+
+__device__ inline double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+  return t;
+}
+
+// Thread 0 stores the block's result; true in the block that finishes last.
+__device__ inline bool red_finish(double v, double* part, int slot, int* ticket) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    part[slot] = v;
+    __threadfence();
+    last = atomicAdd(ticket, 1) == (int)(gridDim.x * gridDim.y) - 1;
+  }
+  __syncthreads();
+  return last;
+}
+
+// out[0] = 1/2 sum D (h + F) + Vnn (Vnn read from out[5], so graphs stay valid).
+__global__ void energy_mb_kernel(const double* __restrict__ D, const double* __restrict__ h,
+                                 const double* __restrict__ F, long long n2, double* part, int* ticket,
+                                 double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
+    s += D[i] * (h[i] + F[i]);
+  const double b = block_sum(s, red);
+  if (red_finish(b, part, blockIdx.x, ticket) && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) t += __ldcg(part + k);
+    out[0] = 0.5 * t + out[5];
+    *ticket = 0;
+  }
+}
+
+// out[0] = max |x_i|
+__global__ void maxabs_mb_kernel(long long n, const double* __restrict__ x, double* part, int* ticket, double* out) {
   __shared__ double red[32];
   double m = 0.0;
-  for (long long idx = threadIdx.x; idx < (long long)n * n; idx += blockDim.x) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[i]));
+  const double b = block_max(m, red);
+  if (red_finish(b, part, blockIdx.x, ticket) && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) t = fmax(t, __ldcg(part + k));
+    out[0] = t;
+    *ticket = 0;
+  }
+}
+
+// out[0] = max |A_ij - sub delta_ij| over all (i, j) (offdiag 0), i != j
+// (offdiag 1), or i < offdiag - 1 <= j (offdiag > 1: an off-diagonal block).
+__global__ void eig_check_mb_kernel(const double* __restrict__ A, int n, double sub, int offdiag, double* part,
+                                    int* ticket, double* out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * n;
+       idx += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(idx / n), j = (int)(idx % n);
     if (offdiag == 1 && i == j) continue;
     if (offdiag > 1 && !(i < offdiag - 1 && j >= offdiag - 1)) continue;
     m = fmax(m, fabs(A[idx] - (i == j ? sub : 0.0)));
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  const double b = block_max(m, red);
+  if (red_finish(b, part, blockIdx.x, ticket) && threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+    for (int k = 0; k < (int)gridDim.x; ++k) t = fmax(t, __ldcg(part + k));
     out[0] = t;
+    *ticket = 0;
   }
 }
 
-// E = 1/2 sum D (h + F) + Vnn written to out[0]; out[1] untouched.
-// vnn is read from device memory (out[5]) so that captured CUDA graphs stay
-// valid when the geometry changes.
-__global__ void energy_kernel(const double* __restrict__ D, const double* __restrict__ h,
-                              const double* __restrict__ F, long long n2, double* out) {
-  const double vnn = out[5];
+// Row / column s of the DIIS matrix: Bm[s][j] = Bm[j][s] = <e_s, e_j> for j < m,
+// each dot over kRedDiis blocks (blockIdx.x the slice, blockIdx.y = j).
+__global__ void diis_dots_mb_kernel(const double* __restrict__ ring, long long len, int s, int m, double* Bm, int ld,
+                                    double* part, int* ticket) {
   __shared__ double red[32];
-  double s = 0.0;
-  for (long long i = threadIdx.x; i < n2; i += blockDim.x) s += D[i] * (h[i] + F[i]);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)blockDim.x / 32; ++w) t += red[w];
-    out[0] = 0.5 * t + vnn;
+  const int j = blockIdx.y;
+  const double* a = ring + (long long)s * len;
+  const double* b = ring + (long long)j * len;
+  double v = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    v += a[i] * b[i];
+  const double t = block_sum(v, red);
+  if (red_finish(t, part, j * kRedDiis + blockIdx.x, ticket) && threadIdx.x == 0) {
+    for (int jj = 0; jj < m; ++jj) {
+      double d = 0.0;
+      for (int k = 0; k < kRedDiis; ++k) d += __ldcg(part + jj * kRedDiis + k);
+      Bm[s * ld + jj] = d;
+      Bm[jj * ld + s] = d;
+    }
+    *ticket = 0;
   }
 }
 
@@ -427,6 +487,8 @@ struct rihf_ctx {
   int* d_counter = nullptr;
   int* d_flag = nullptr;
   int* d_sched = nullptr;   // work counter of the tensor-core GEMM (zero between launches)
+  double* d_red = nullptr;  // partials of the multi-block reductions
+  int* d_ticket = nullptr;  // their ticket counter (zero between launches)
   ShellPair* d_pairs = nullptr;
   int2* d_tasks = nullptr;           // (pair, auxiliary shell) tasks, grouped by shared-memory class
   TaskGroup groups[kTaskGroups];
@@ -590,7 +652,7 @@ static void free_all(rihf_ctx* c) {
                   c->d_ao_atom, c->d_ao_l, c->hist_D[0], c->hist_D[1], c->hist_D[2], c->hist_S, c->hist_xyz[0],
                   c->hist_xyz[1], c->Dpred, c->mlX, c->mly, c->mlt, c->mlDx, c->ml_sums, c->rep_X, c->rep_t, c->net.master, c->net.wbf, c->net.grad,
                   c->net.m, c->net.v, c->net.loss,
-                  c->d_tr, c->d_nf, c->d_Z, c->d_xyz, c->d_boys, c->d_counter, c->d_flag, c->d_sched, c->d_pairs, c->d_tasks, c->d_schwarz,
+                  c->d_tr, c->d_nf, c->d_Z, c->d_xyz, c->d_boys, c->d_counter, c->d_flag, c->d_sched, c->d_red, c->d_ticket, c->d_pairs, c->d_tasks, c->d_schwarz,
                   c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->T3, c->B, c->Xo, c->Sw, c->Sv,
                   c->C, c->eps, c->Ct, c->D, c->J, c->K, c->F, c->Fx, c->T1, c->T2, c->Err, c->Fp, c->Cp, c->Hb,
                   c->dvec, c->Fring, c->Ering, c->Bdiis, c->coef, c->scal, c->Cprev,
@@ -895,6 +957,9 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     c->d_flag = dalloc<int>(4);
     c->d_sched = dalloc<int>(2);
     RIHF_CUDA(cudaMemset(c->d_sched, 0, 2 * sizeof(int)));
+    c->d_red = dalloc<double>(kRedSlots);
+    c->d_ticket = dalloc<int>(1);
+    RIHF_CUDA(cudaMemset(c->d_ticket, 0, sizeof(int)));
     // shell pairs a >= b; compute_geometry screens them (Schwarz) when the
     // four-centre class fits in shared memory, otherwise all pairs are kept
     for (int a = 0; a < c->hp.nshell; ++a)
@@ -1098,7 +1163,7 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
       go.M = n; go.N = n; go.K = n; go.A = c->Cp; go.lda = n; go.transA = true; go.B = c->Cp; go.ldb = n;
       go.C = c->T2; go.ldc = n;
       dgemm(la, go);
-      eig_check_kernel<<<1, 1024, 0, c->stream>>>(c->T2, n, 1.0, 0, c->scal + 2);
+      eig_check_mb_kernel<<<kRedBlocks, 256, 0, c->stream>>>(c->T2, n, 1.0, 0, c->d_red, c->d_ticket, c->scal + 2);
       RIHF_LAUNCH_CHECK();
       GemmArgs gf;   // T1 = F' Cp, T2 = Cp^T T1
       gf.M = n; gf.N = n; gf.K = n; gf.A = c->Fp; gf.lda = n; gf.B = c->Cp; gf.ldb = n; gf.C = c->T1; gf.ldc = n;
@@ -1109,7 +1174,8 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
       dgemm(la, gt);
       // occupied-virtual block only: rotations inside the occupied or the
       // virtual space (near-degenerate pairs) leave the density unchanged
-      eig_check_kernel<<<1, 1024, 0, c->stream>>>(c->T2, n, 0.0, c->nocc + 1, c->scal + 3);
+      eig_check_mb_kernel<<<kRedBlocks, 256, 0, c->stream>>>(c->T2, n, 0.0, c->nocc + 1, c->d_red, c->d_ticket,
+                                                             c->scal + 3);
       RIHF_LAUNCH_CHECK();
       c->launches += 2;
     });
@@ -1170,7 +1236,8 @@ static void fock_build(rihf_ctx* c) {
     dgemm(la, gk);
     symmetrize_lower(la, c->K, N, 1); }
   add3(la, (int)n2, c->H, c->J, c->K, c->F);
-  energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->scal);
+  energy_mb_kernel<<<kRedBlocks, 256, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->d_red, c->d_ticket,
+                                                        c->scal);
   RIHF_LAUNCH_CHECK();
   c->launches += 1;
 }
@@ -1267,7 +1334,8 @@ static void fock_build_tc(rihf_ctx* c, int digits) {
     oz_gemm(la, g2);
     symmetrize_lower(la, c->K, N, 1); }
   add3(la, (int)n2, c->H, c->J, c->K, c->F);
-  energy_kernel<<<1, 1024, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->scal);
+  energy_mb_kernel<<<kRedBlocks, 256, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->d_red, c->d_ticket,
+                                                        c->scal);
   RIHF_LAUNCH_CHECK();
   c->launches += 1;
 }
@@ -1290,7 +1358,9 @@ static void diis_error(rihf_ctx* c) {
   g4.M = n; g4.N = n; g4.K = N; g4.A = c->Xo; g4.lda = n; g4.transA = true; g4.B = c->T2; g4.ldb = n;
   g4.C = c->Err; g4.ldc = n;
   dgemm(la, g4);
-  maxabs(la, n * n, c->Err, c->scal + 1);
+  maxabs_mb_kernel<<<kRedBlocks, 256, 0, c->stream>>>((long long)n * n, c->Err, c->d_red, c->d_ticket, c->scal + 1);
+  RIHF_LAUNCH_CHECK();
+  c->launches += 1;
 }
 
 // After a converged SCF: one online training step of the network on this
@@ -1582,7 +1652,8 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
     const double* Fuse = c->F;
     {
       TraceScope t(c->tracer, s, "DIIS (dots, solve, extrapolation)", 0.0, 0);
-      diis_dots_kernel<<<m, 256, 0, s>>>(c->Ering, (long long)n * n, slot, m, c->Bdiis, 16);
+      diis_dots_mb_kernel<<<dim3(kRedDiis, m), 256, 0, s>>>(c->Ering, (long long)n * n, slot, m, c->Bdiis, 16, c->d_red,
+                                                             c->d_ticket);
       RIHF_LAUNCH_CHECK();
       if (m >= 2) {
         diis_solve_kernel<<<1, 32, 0, s>>>(c->Bdiis, 16, m, c->coef);
