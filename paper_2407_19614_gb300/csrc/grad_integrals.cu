@@ -357,20 +357,25 @@ __device__ inline double s1(const double* s, int i, int j) { return (i < 0 || j 
 
 // Task = primary shell pair (a >= b) x (1 + natoms): slot 0 handles overlap and
 // kinetic, slot 1 + C the attraction of nucleus C.
+template <int G>
 __global__ void __launch_bounds__(32) grad_one_electron_kernel(DevShells prim, int natoms, const int* __restrict__ Z,
                                                                const double* __restrict__ axyz,
                                                                const double* __restrict__ boys, int* counter,
                                                                const double* __restrict__ D,
                                                                const double* __restrict__ W, double* grad_one,
-                                                               double* grad_ovl) {
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x;
+                                                               double* grad_ovl, int slice) {
+  extern __shared__ double smem_all[];
+  const int lane = threadIdx.x % G;
+  double* smem = smem_all + (threadIdx.x / G) * slice;   // this task group's slice
+  __shared__ double one_tr[kTrStride];   // the unit transform of the s "c" function
+  if (threadIdx.x < kTrStride) one_tr[threadIdx.x] = threadIdx.x == 0 ? 1.0 : 0.0;
+  __syncwarp();
   const int ns = prim.nshell;
   const long long npair = (long long)ns * (ns + 1) / 2;
   const long long ntask = npair * (1 + natoms);
   const int N = prim.nfunc;
   for (;;) {
-    long long task = warp_next(counter, lane);
+    long long task = warp_next<G>(counter, lane);
     if (task >= ntask) break;
     long long pidx = task % npair;
     int slot = (int)(task / npair);
@@ -388,18 +393,15 @@ __global__ void __launch_bounds__(32) grad_one_electron_kernel(DevShells prim, i
     double wgt = (sa == sb) ? 1.0 : 2.0;
     DerivPlan pl(la, lb, 0);
     const int na = ncart(la), nb = ncart(lb);
-    __shared__ double one_tr[kTrStride];
-    if (lane < kTrStride) one_tr[lane] = (lane == 0) ? 1.0 : 0.0;
-    __syncwarp();
     if (slot == 0) {
       if (ata == atb) continue;   // overlap and kinetic depend on A - B only
       // Dcart (for T) into ycart, Wcart into t1-region copy
       double* Dc = smem + pl.ycart;
       double* Wc = smem + pl.total;   // past the plan (the HRR region holds t1/t2)
       double* s1d = Wc + 128;         // 3 x 64
-      warp_back_transform(D + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa,
+      warp_back_transform<G>(D + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa,
                           nfb, 1, smem + pl.t1, smem + pl.t2, Dc, lane);
-      warp_back_transform(W + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa,
+      warp_back_transform<G>(W + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa,
                           nfb, 1, smem + pl.t1, smem + pl.t2, Wc, lane);
       double gT[3] = {0, 0, 0}, gS[3] = {0, 0, 0};
       for (int pa = 0; pa < prim.nprim[sa]; ++pa)
@@ -407,8 +409,8 @@ __global__ void __launch_bounds__(32) grad_one_electron_kernel(DevShells prim, i
           double al = prim.exps[prim.pstart[sa] + pa], be = prim.exps[prim.pstart[sb] + pb];
           double w = prim.coefs[prim.pstart[sa] + pa] * prim.coefs[prim.pstart[sb] + pb];
           if (lane < 3) os_overlap_1d_g(al, be, A[lane], B[lane], la + 1, lb + 2, s1d + lane * 64, 8);
-          __syncwarp();
-          for (int idx = lane; idx < na * nb; idx += 32) {
+          __syncwarp(lane_group_mask<G>());
+          for (int idx = lane; idx < na * nb; idx += G) {
             int ka = idx / nb, kb = idx % nb;
             int c[3], d[3];
             cart_decode(la, ka, c[0], c[1], c[2]);
@@ -431,10 +433,10 @@ __global__ void __launch_bounds__(32) grad_one_electron_kernel(DevShells prim, i
               gT[x] += w * Dc[idx] * dTfull;
             }
           }
-          __syncwarp();
+          __syncwarp(lane_group_mask<G>());
         }
       for (int x = 0; x < 3; ++x) {
-        double t = warp_sum(gT[x]) * wgt, s = warp_sum(gS[x]) * wgt;
+        double t = warp_sum<G>(gT[x]) * wgt, s = warp_sum<G>(gS[x]) * wgt;
         if (lane == 0) {
           atomicAdd(grad_one + 3 * ata + x, t);
           atomicAdd(grad_one + 3 * atb + x, -t);
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(32) grad_one_electron_kernel(DevShells prim, i
           atomicAdd(grad_ovl + 3 * atb + x, s);
         }
       }
-      __syncwarp();
+      __syncwarp(lane_group_mask<G>());
       continue;
     }
     // nuclear attraction of nucleus C = slot - 1
@@ -452,26 +454,26 @@ __global__ void __launch_bounds__(32) grad_one_electron_kernel(DevShells prim, i
     double* Fm = smem + pl.fm;
     double* vrr = smem + pl.vrr;
     int accsz = acc_size(pl.emin, pl.emax, 0);
-    for (int i = lane; i < 3 * accsz; i += 32) smem[pl.acc0 + i] = 0.0;
+    for (int i = lane; i < 3 * accsz; i += G) smem[pl.acc0 + i] = 0.0;
     EtrShape sh{0, pl.emin, pl.emax};
     for (int pa = 0; pa < prim.nprim[sa]; ++pa)
       for (int pb = 0; pb < prim.nprim[sb]; ++pb) {
         double al = prim.exps[prim.pstart[sa] + pa], be = prim.exps[prim.pstart[sb] + pb];
         double w = -Z[Cn] * prim.coefs[prim.pstart[sa] + pa] * prim.coefs[prim.pstart[sb] + pb];
         Prim3 t = make_prim_point(al, A, be, B, Cx);
-        if (lane <= pl.L) Fm[lane] = boys_eval(lane, t.T, boys);
-        __syncwarp();
-        warp_vrr(vrr, pl.L, t, Fm, lane);
-        warp_acc_level(vrr, pl.L, nullptr, sh, w, smem + pl.acc0, lane);
-        warp_acc_level(vrr, pl.L, nullptr, sh, 2.0 * al * w, smem + pl.accA, lane);
-        warp_acc_level(vrr, pl.L, nullptr, sh, 2.0 * be * w, smem + pl.accB, lane);
+        for (int m = lane; m <= pl.L; m += G) Fm[m] = boys_eval(m, t.T, boys);
+        __syncwarp(lane_group_mask<G>());
+        warp_vrr<G>(vrr, pl.L, t, Fm, lane);
+        warp_acc_level<G>(vrr, pl.L, nullptr, sh, w, smem + pl.acc0, lane);
+        warp_acc_level<G>(vrr, pl.L, nullptr, sh, 2.0 * al * w, smem + pl.accA, lane);
+        warp_acc_level<G>(vrr, pl.L, nullptr, sh, 2.0 * be * w, smem + pl.accB, lane);
       }
-    warp_back_transform(D + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa, nfb,
+    warp_back_transform<G>(D + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa, nfb,
                         1, smem + pl.t1, smem + pl.t2, smem + pl.ycart, lane);
     double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
     double g[6];
-    warp_deriv_contract(pl, smem, smem + pl.acc0, smem + pl.accA, smem + pl.accB, 1.0, 1.0, la, lb, 0, AB, lane, g);
-    for (int i = 0; i < 6; ++i) g[i] = warp_sum(g[i]) * wgt;
+    warp_deriv_contract<G>(pl, smem, smem + pl.acc0, smem + pl.accA, smem + pl.accB, 1.0, 1.0, la, lb, 0, AB, lane, g);
+    for (int i = 0; i < 6; ++i) g[i] = warp_sum<G>(g[i]) * wgt;
     if (lane == 0) {
       for (int x = 0; x < 3; ++x) {
         atomicAdd(grad_one + 3 * ata + x, g[x]);
@@ -479,7 +481,7 @@ __global__ void __launch_bounds__(32) grad_one_electron_kernel(DevShells prim, i
         atomicAdd(grad_one + 3 * Cn + x, -(g[x] + g[3 + x]));
       }
     }
-    __syncwarp();
+    __syncwarp(lane_group_mask<G>());
   }
 }
 
@@ -547,11 +549,16 @@ void launch_grad_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, c
 void launch_grad_one_electron(const IntegralCtx& ic, const DevShells& prim, int max_lp, int natoms, const int* Z,
                               const double* axyz, const double* D, const double* W, double* grad_one,
                               double* grad_ovl) {
-  int smem = deriv_smem(max_lp, max_lp, 0) + (128 + 3 * 64) * (int)sizeof(double);
-  raise_smem_limit((const void*)grad_one_electron_kernel, smem);
+  // every class of this kernel is small (la, lb <= 2 for the primary sets
+  // here): 8-lane task groups, four tasks per warp, each with its own slice
+  const int bytes = deriv_smem(max_lp, max_lp, 0) + (128 + 3 * 64) * (int)sizeof(double);
+  const int slice = (bytes + (int)sizeof(double) - 1) / (int)sizeof(double);
+  const int smem = 4 * slice * (int)sizeof(double);
+  raise_smem_limit((const void*)grad_one_electron_kernel<8>, smem);
   RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
-  grad_one_electron_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, natoms, Z, axyz, ic.boys, ic.counter,
-                                                                         D, W, grad_one, grad_ovl);
+  grad_one_electron_kernel<8><<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, natoms, Z, axyz, ic.boys,
+                                                                            ic.counter, D, W, grad_one, grad_ovl,
+                                                                            slice);
   RIHF_LAUNCH_CHECK();
   if (ic.launches) *ic.launches += 1;
 }
