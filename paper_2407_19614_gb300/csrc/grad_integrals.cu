@@ -256,15 +256,23 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
 
 // ------------------------------------------------------------ 2-centre
 
+// G = 8 runs the classes set in small_mask (bit 8 la + lc), G = 32 the others.
+template <int G>
 __global__ void __launch_bounds__(32) grad_eri2_kernel(DevShells aux, const double* __restrict__ boys, int* counter,
-                                                       const double* __restrict__ Z, double* grad) {
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x;
+                                                       const double* __restrict__ Z, double* grad,
+                                                       unsigned long long small_mask, int slice) {
+  extern __shared__ double smem_all[];
+  const int lane = threadIdx.x % G;
+  double* smem = smem_all + (threadIdx.x / G) * slice;   // this task group's slice
+  const unsigned gm = lane_group_mask<G>();
+  __shared__ double one_tr[kTrStride];   // the unit transform of the s "b" function
+  if (threadIdx.x < kTrStride) one_tr[threadIdx.x] = threadIdx.x == 0 ? 1.0 : 0.0;
+  __syncwarp();
   const int ns = aux.nshell;
   const long long ntask = (long long)ns * (ns + 1) / 2;
   const int NA = aux.nfunc;
   for (;;) {
-    long long task = warp_next(counter, lane);
+    long long task = warp_next<G>(counter, lane);
     if (task >= ntask) break;
     int sa = (int)((sqrt(8.0 * (double)task + 1.0) - 1.0) * 0.5);
     while ((long long)sa * (sa + 1) / 2 > task) --sa;
@@ -273,12 +281,13 @@ __global__ void __launch_bounds__(32) grad_eri2_kernel(DevShells aux, const doub
     int ata = aux.atom[sa], atc = aux.atom[sc];
     if (ata == atc) continue;
     int la = aux.l[sa], lc = aux.l[sc];
+    if ((int)((small_mask >> (8 * la + lc)) & 1ull) != (G == 8 ? 1 : 0)) continue;
     DerivPlan pl(la, 0, lc);
     double* Fm = smem + pl.fm;
     double* vrr = smem + pl.vrr;
     double* etr = smem + pl.etr;
     int accsz = acc_size(pl.emin, pl.emax, lc);
-    for (int i = lane; i < 3 * accsz; i += 32) smem[pl.acc0 + i] = 0.0;
+    for (int i = lane; i < 3 * accsz; i += G) smem[pl.acc0 + i] = 0.0;
     const double* PA = aux.xyz + 3 * sa;
     const double* PC = aux.xyz + 3 * sc;
     EtrShape sh{lc, pl.emin, pl.emax};
@@ -287,41 +296,38 @@ __global__ void __launch_bounds__(32) grad_eri2_kernel(DevShells aux, const doub
         double al = aux.exps[aux.pstart[sa] + pa], ga = aux.exps[aux.pstart[sc] + pc];
         double w = aux.coefs[aux.pstart[sa] + pa] * aux.coefs[aux.pstart[sc] + pc];
         Prim3 t = make_prim3(al, PA, 0.0, PA, ga, PC);
-        if (lane <= pl.L) Fm[lane] = boys_eval(lane, t.T, boys);
-        __syncwarp();
-        warp_vrr(vrr, pl.L, t, Fm, lane);
-        warp_etr(vrr, pl.L, etr, sh, t, Fm, lane);
-        warp_acc_level(vrr, pl.L, etr, sh, w, smem + pl.acc0, lane);
-        warp_acc_level(vrr, pl.L, etr, sh, 2.0 * al * w, smem + pl.accA, lane);
+        for (int m = lane; m <= pl.L; m += G) Fm[m] = boys_eval(m, t.T, boys);
+        __syncwarp(gm);
+        warp_vrr<G>(vrr, pl.L, t, Fm, lane);
+        warp_etr<G>(vrr, pl.L, etr, sh, t, Fm, lane);
+        warp_acc_level<G>(vrr, pl.L, etr, sh, w, smem + pl.acc0, lane);
+        warp_acc_level<G>(vrr, pl.L, etr, sh, 2.0 * al * w, smem + pl.accA, lane);
       }
     // Z block (P in sa, Q in sc) -> Cartesian with a unit s "b" function
     int nfa = aux.nf[la], nfc = aux.nf[lc];
     const double* src = Z + (long long)aux.ao[sa] * NA + aux.ao[sc];
     // layout Y(sa, sb=0, sc) = src[sa*NA + sc]
-    __shared__ double one_tr[kTrStride];
-    if (lane < kTrStride) one_tr[lane] = (lane == 0) ? 1.0 : 0.0;
-    __syncwarp();
-    warp_back_transform(src, 1, NA, 0, la, 0, lc, aux.tr + la * kTrStride * kTrStride, one_tr,
+    warp_back_transform<G>(src, 1, NA, 0, la, 0, lc, aux.tr + la * kTrStride * kTrStride, one_tr,
                         aux.tr + lc * kTrStride * kTrStride, nfa, 1, nfc, smem + pl.t1, smem + pl.t2,
                         smem + pl.ycart, lane);
     double AB[3] = {0.0, 0.0, 0.0};
     double g[6];
     // only the A-side derivative is needed (lb = 0, beta = 0): zero accB so the
     // (la, lb+1) term vanishes
-    for (int i = lane; i < accsz; i += 32) smem[pl.accB + i] = 0.0;
-    __syncwarp();
-    warp_deriv_contract(pl, smem, smem + pl.acc0, smem + pl.accA, smem + pl.accB, 1.0, 1.0, la, 0, lc, AB, lane, g);
+    for (int i = lane; i < accsz; i += G) smem[pl.accB + i] = 0.0;
+    __syncwarp(gm);
+    warp_deriv_contract<G>(pl, smem, smem + pl.acc0, smem + pl.accA, smem + pl.accB, 1.0, 1.0, la, 0, lc, AB, lane, g);
     // E term -1/2 sum_PQ Z_PQ (P|Q)^xi over ordered pairs: off-diagonal shell
     // pairs appear twice.
     double wgt = (sa == sc) ? -0.5 : -1.0;
-    for (int i = 0; i < 3; ++i) g[i] = warp_sum(g[i]) * wgt;
+    for (int i = 0; i < 3; ++i) g[i] = warp_sum<G>(g[i]) * wgt;
     if (lane == 0) {
       for (int x = 0; x < 3; ++x) {
         atomicAdd(grad + 3 * ata + x, g[x]);
         atomicAdd(grad + 3 * atc + x, -g[x]);
       }
     }
-    __syncwarp();
+    __syncwarp(gm);
   }
 }
 
@@ -538,10 +544,23 @@ void launch_grad_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShe
 }
 
 void launch_grad_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, const double* Z, double* grad) {
-  int smem = deriv_smem(max_la, 0, max_la);
-  raise_smem_limit((const void*)grad_eri2_kernel, smem);
+  // small classes as 8-lane groups (four tasks per warp), then the rest with
+  // whole warps; each launch claims every task and skips the other's classes
+  int small_slice = 0;
+  const unsigned long long mask = eri2_small_classes(max_la, &small_slice);
+  if (mask) {
+    const int smem = 4 * small_slice * (int)sizeof(double);
+    raise_smem_limit((const void*)grad_eri2_kernel<8>, smem);
+    RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+    grad_eri2_kernel<8><<<grid_for_smem(smem), 32, smem, ic.stream>>>(aux, ic.boys, ic.counter, Z, grad, mask,
+                                                                      small_slice);
+    RIHF_LAUNCH_CHECK();
+    if (ic.launches) *ic.launches += 1;
+  }
+  const int smem = deriv_smem(max_la, 0, max_la);
+  raise_smem_limit((const void*)grad_eri2_kernel<32>, smem);
   RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
-  grad_eri2_kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(aux, ic.boys, ic.counter, Z, grad);
+  grad_eri2_kernel<32><<<grid_for_smem(smem), 32, smem, ic.stream>>>(aux, ic.boys, ic.counter, Z, grad, mask, 0);
   RIHF_LAUNCH_CHECK();
   if (ic.launches) *ic.launches += 1;
 }

@@ -208,15 +208,20 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
 
 // ------------------------------------------------------------ (P|Q)
 
+// G = 8 runs the classes set in small_mask (bit 8 la + lc), G = 32 the others.
+template <int G>
 __global__ void __launch_bounds__(32) eri2_kernel(DevShells aux, const double* __restrict__ boys, int* counter,
-                                                  double* __restrict__ A) {
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x;
+                                                  double* __restrict__ A, unsigned long long small_mask,
+                                                  int slice) {
+  extern __shared__ double smem_all[];
+  const int lane = threadIdx.x % G;
+  double* smem = smem_all + (threadIdx.x / G) * slice;   // this task group's slice
+  const unsigned gm = lane_group_mask<G>();
   const int ns = aux.nshell;
   const long long ntask = (long long)ns * (ns + 1) / 2;
   const int NA = aux.nfunc;
   for (;;) {
-    long long task = warp_next_task(counter, lane);
+    long long task = warp_next_task<G>(counter, lane);
     if (task >= ntask) break;
     // task -> (sa >= sc)
     int sa = (int)((sqrt(8.0 * (double)task + 1.0) - 1.0) * 0.5);
@@ -224,6 +229,7 @@ __global__ void __launch_bounds__(32) eri2_kernel(DevShells aux, const double* _
     while ((long long)(sa + 1) * (sa + 2) / 2 <= task) ++sa;
     int sc = (int)(task - (long long)sa * (sa + 1) / 2);
     int la = aux.l[sa], lc = aux.l[sc];
+    if ((int)((small_mask >> (8 * la + lc)) & 1ull) != (G == 8 ? 1 : 0)) continue;
     int emin = la, emax = la, L = la + lc;
     Eri3Plan pl(la, 0, lc, emin, emax, 1);
     double* Fm = smem + pl.fm;
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(32) eri2_kernel(DevShells aux, const double* _
     double* etr = smem + pl.etr;
     double* acc = smem + pl.acc;
     int accsz = acc_size(emin, emax, lc);
-    for (int i = lane; i < accsz; i += 32) acc[i] = 0.0;
+    for (int i = lane; i < accsz; i += G) acc[i] = 0.0;
     const double* PA = aux.xyz + 3 * sa;
     const double* PC = aux.xyz + 3 * sc;
     EtrShape sh{lc, emin, emax};
@@ -240,10 +246,10 @@ __global__ void __launch_bounds__(32) eri2_kernel(DevShells aux, const double* _
         double al = aux.exps[aux.pstart[sa] + pa], ga = aux.exps[aux.pstart[sc] + pc];
         double w = aux.coefs[aux.pstart[sa] + pa] * aux.coefs[aux.pstart[sc] + pc];
         Prim3 t = make_prim3(al, PA, 0.0, PA, ga, PC);
-        if (lane <= L) Fm[lane] = boys_eval(lane, t.T, boys);
-        __syncwarp();
-        warp_vrr(vrr, L, t, Fm, lane);
-        warp_etr_accumulate(vrr, L, etr, sh, t, w, acc, Fm, lane);
+        for (int m = lane; m <= L; m += G) Fm[m] = boys_eval(m, t.T, boys);
+        __syncwarp(gm);
+        warp_vrr<G>(vrr, L, t, Fm, lane);
+        warp_etr_accumulate<G>(vrr, L, etr, sh, t, w, acc, Fm, lane);
       }
     // acc holds [a][c] directly (lb = 0); transform with b = s (identity 1x1)
     int nfa = aux.nf[la], nfc = aux.nf[lc];
@@ -252,28 +258,28 @@ __global__ void __launch_bounds__(32) eri2_kernel(DevShells aux, const double* _
     double* s1 = smem + pl.t1;
     double* s2 = smem + pl.t2;
     const int na = ncart(la), nc = ncart(lc);
-    for (int idx = lane; idx < na * nfc; idx += 32) {
+    for (int idx = lane; idx < na * nfc; idx += G) {
       int scc = idx % nfc, ka = idx / nfc;
       double v = 0.0;
       for (int k = 0; k < nc; ++k) v += trc[scc * kTrStride + k] * acc[ka * nc + k];
       s1[idx] = v;
     }
-    __syncwarp();
-    for (int idx = lane; idx < nfa * nfc; idx += 32) {
+    __syncwarp(gm);
+    for (int idx = lane; idx < nfa * nfc; idx += G) {
       int scc = idx % nfc, saa = idx / nfc;
       double v = 0.0;
       for (int k = 0; k < na; ++k) v += tra[saa * kTrStride + k] * s1[k * nfc + scc];
       s2[idx] = v;
     }
-    __syncwarp();
+    __syncwarp(gm);
     const int P0 = aux.ao[sa], Q0 = aux.ao[sc];
-    for (int idx = lane; idx < nfa * nfc; idx += 32) {
+    for (int idx = lane; idx < nfa * nfc; idx += G) {
       int scc = idx % nfc, saa = idx / nfc;
       double v = s2[idx];
       A[(size_t)(P0 + saa) * NA + Q0 + scc] = v;
       A[(size_t)(Q0 + scc) * NA + P0 + saa] = v;
     }
-    __syncwarp();
+    __syncwarp(gm);
   }
 }
 
@@ -300,18 +306,21 @@ __device__ inline void os_overlap_1d(double a, double b, double XA, double XB, i
     }
 }
 
+template <int G>
 __global__ void __launch_bounds__(32) one_electron_kernel(DevShells prim, int natoms, const int* __restrict__ Z,
                                                           const double* __restrict__ axyz,
                                                           const double* __restrict__ boys, int* counter,
                                                           double* __restrict__ S, double* __restrict__ Tk,
-                                                          double* __restrict__ V) {
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x;
+                                                          double* __restrict__ V, int slice) {
+  extern __shared__ double smem_all[];
+  const int lane = threadIdx.x % G;
+  double* smem = smem_all + (threadIdx.x / G) * slice;   // this task group's slice
+  const unsigned gm = lane_group_mask<G>();
   const int ns = prim.nshell;
   const long long ntask = (long long)ns * (ns + 1) / 2;
   const int N = prim.nfunc;
   for (;;) {
-    long long task = warp_next_task(counter, lane);
+    long long task = warp_next_task<G>(counter, lane);
     if (task >= ntask) break;
     int sa = (int)((sqrt(8.0 * (double)task + 1.0) - 1.0) * 0.5);
     while ((long long)sa * (sa + 1) / 2 > task) --sa;
@@ -331,20 +340,20 @@ __global__ void __launch_bounds__(32) one_electron_kernel(DevShells prim, int na
     double* Fm = base + pl.fm;
     double* vrr = base + pl.vrr;
     double* acc = base + pl.acc;
-    for (int i = lane; i < na * nb; i += 32) {
+    for (int i = lane; i < na * nb; i += G) {
       sacc[i] = 0.0;
       tacc[i] = 0.0;
     }
-    for (int i = lane; i < acc_size(emin, emax, 0); i += 32) acc[i] = 0.0;
-    __syncwarp();
+    for (int i = lane; i < acc_size(emin, emax, 0); i += G) acc[i] = 0.0;
+    __syncwarp(gm);
     EtrShape sh{0, emin, emax};
     for (int pa = 0; pa < prim.nprim[sa]; ++pa)
       for (int pb = 0; pb < prim.nprim[sb]; ++pb) {
         double al = prim.exps[prim.pstart[sa] + pa], be = prim.exps[prim.pstart[sb] + pb];
         double w = prim.coefs[prim.pstart[sa] + pa] * prim.coefs[prim.pstart[sb] + pb];
         if (lane < 3) os_overlap_1d(al, be, A[lane], B[lane], la, lb + 2, s1d + lane * 64, 8);
-        __syncwarp();
-        for (int idx = lane; idx < na * nb; idx += 32) {
+        __syncwarp(gm);
+        for (int idx = lane; idx < na * nb; idx += G) {
           int ka = idx / nb, kb = idx % nb;
           int ca[3], cb[3];
           cart_decode(la, ka, ca[0], ca[1], ca[2]);
@@ -361,17 +370,17 @@ __global__ void __launch_bounds__(32) one_electron_kernel(DevShells prim, int na
           sacc[idx] += w * sd[0] * sd[1] * sd[2];
           tacc[idx] += -0.5 * w * (kd[0] * sd[1] * sd[2] + sd[0] * kd[1] * sd[2] + sd[0] * sd[1] * kd[2]);
         }
-        __syncwarp();
+        __syncwarp(gm);
         for (int C = 0; C < natoms; ++C) {
           Prim3 t = make_prim_point(al, A, be, B, axyz + 3 * C);
-          if (lane <= L) Fm[lane] = boys_eval(lane, t.T, boys);
-          __syncwarp();
-          warp_vrr(vrr, L, t, Fm, lane);
-          warp_etr_accumulate(vrr, L, nullptr, sh, t, -w * Z[C], acc, Fm, lane);
+          for (int m = lane; m <= L; m += G) Fm[m] = boys_eval(m, t.T, boys);
+          __syncwarp(gm);
+          warp_vrr<G>(vrr, L, t, Fm, lane);
+          warp_etr_accumulate<G>(vrr, L, nullptr, sh, t, -w * Z[C], acc, Fm, lane);
         }
       }
     double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
-    const double* vcart = warp_hrr(acc, emin, la, lb, 0, AB, base + pl.hrr, pl.half, lane);
+    const double* vcart = warp_hrr<G>(acc, emin, la, lb, 0, AB, base + pl.hrr, pl.half, lane);
     int nfa = prim.nf[la], nfb = prim.nf[lb];
     const double* tra = prim.tr + la * kTrStride * kTrStride;
     const double* trb = prim.tr + lb * kTrStride * kTrStride;
@@ -381,27 +390,27 @@ __global__ void __launch_bounds__(32) one_electron_kernel(DevShells prim, int na
     double* dsts[3] = {S, Tk, V};
     for (int q = 0; q < 3; ++q) {
       const double* src = srcs[q];
-      for (int idx = lane; idx < na * nfb; idx += 32) {
+      for (int idx = lane; idx < na * nfb; idx += G) {
         int sbb = idx % nfb, ka = idx / nfb;
         double v = 0.0;
         for (int k = 0; k < nb; ++k) v += trb[sbb * kTrStride + k] * src[ka * nb + k];
         o1[idx] = v;
       }
-      __syncwarp();
-      for (int idx = lane; idx < nfa * nfb; idx += 32) {
+      __syncwarp(gm);
+      for (int idx = lane; idx < nfa * nfb; idx += G) {
         int sbb = idx % nfb, saa = idx / nfb;
         double v = 0.0;
         for (int k = 0; k < na; ++k) v += tra[saa * kTrStride + k] * o1[k * nfb + sbb];
         o2[idx] = v;
       }
-      __syncwarp();
+      __syncwarp(gm);
       const int mu0 = prim.ao[sa], nu0 = prim.ao[sb];
-      for (int idx = lane; idx < nfa * nfb; idx += 32) {
+      for (int idx = lane; idx < nfa * nfb; idx += G) {
         int sbb = idx % nfb, saa = idx / nfb;
         dsts[q][(size_t)(mu0 + saa) * N + nu0 + sbb] = o2[idx];
         dsts[q][(size_t)(nu0 + sbb) * N + mu0 + saa] = o2[idx];
       }
-      __syncwarp();
+      __syncwarp(gm);
     }
   }
 }
@@ -816,11 +825,39 @@ void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<in
     }
 }
 
+unsigned long long eri2_small_classes(int max_la, int* slice_doubles) {
+  // the 3.5 KB working-set limit of the 8-lane 3-centre group, applied to
+  // both the (P|Q) integrals and their derivatives
+  unsigned long long mask = 0;
+  int slice = 0;
+  for (int la = 0; la <= max_la; ++la)
+    for (int lc = 0; lc <= max_la; ++lc) {
+      const int e = smem_eri3_doubles(la, 0, lc), g = smem_grad_doubles(la, 0, lc);
+      if (std::max(e, g) * (int)sizeof(double) > 3584) continue;
+      mask |= 1ull << (8 * la + lc);
+      slice = std::max(slice, std::max(e, g));
+    }
+  if (slice_doubles) *slice_doubles = slice;
+  return mask;
+}
+
 void launch_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, double* A) {
-  int smem = max_smem_eri3(max_la, 0, max_la) * (int)sizeof(double);
-  set_smem((const void*)eri2_kernel, smem);
+  // small classes as 8-lane groups (four tasks per warp), then the rest with
+  // whole warps; each launch claims every task and skips the other's classes
+  int small_slice = 0;
+  const unsigned long long mask = eri2_small_classes(max_la, &small_slice);
+  if (mask) {
+    const int smem = 4 * small_slice * (int)sizeof(double);
+    set_smem((const void*)eri2_kernel<8>, smem);
+    RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+    eri2_kernel<8><<<grid_for(smem), 32, smem, ic.stream>>>(aux, ic.boys, ic.counter, A, mask, small_slice);
+    RIHF_LAUNCH_CHECK();
+    if (ic.launches) *ic.launches += 1;
+  }
+  const int smem = max_smem_eri3(max_la, 0, max_la) * (int)sizeof(double);
+  set_smem((const void*)eri2_kernel<32>, smem);
   RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
-  eri2_kernel<<<grid_for(smem), 32, smem, ic.stream>>>(aux, ic.boys, ic.counter, A);
+  eri2_kernel<32><<<grid_for(smem), 32, smem, ic.stream>>>(aux, ic.boys, ic.counter, A, mask, 0);
   RIHF_LAUNCH_CHECK();
   if (ic.launches) *ic.launches += 1;
 }
@@ -843,12 +880,15 @@ void launch_schwarz(const IntegralCtx& ic, const DevShells& prim, int max_lp, do
 
 void launch_one_electron(const IntegralCtx& ic, const DevShells& prim, int max_lp, int natoms, const int* Z,
                          const double* axyz, double* S, double* Tk, double* V) {
-  int nc = ncart(max_lp);
-  int smem = (2 * nc * nc + 3 * 64 + max_smem_eri3(max_lp, max_lp, 0, false)) * (int)sizeof(double);
-  set_smem((const void*)one_electron_kernel, smem);
+  // every class of this kernel is small (la, lb <= 2 for the primary sets
+  // here): 8-lane task groups, four tasks per warp, each with its own slice
+  const int nc = ncart(max_lp);
+  const int slice = 2 * nc * nc + 3 * 64 + max_smem_eri3(max_lp, max_lp, 0, false);
+  const int smem = 4 * slice * (int)sizeof(double);
+  set_smem((const void*)one_electron_kernel<8>, smem);
   RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
-  one_electron_kernel<<<grid_for(smem), 32, smem, ic.stream>>>(prim, natoms, Z, axyz, ic.boys, ic.counter, S, Tk,
-                                                               V);
+  one_electron_kernel<8><<<grid_for(smem), 32, smem, ic.stream>>>(prim, natoms, Z, axyz, ic.boys, ic.counter, S,
+                                                                  Tk, V, slice);
   RIHF_LAUNCH_CHECK();
   if (ic.launches) *ic.launches += 1;
 }

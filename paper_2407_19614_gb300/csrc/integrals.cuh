@@ -56,6 +56,9 @@ void launch_pair_prims(const IntegralCtx& ic, const DevShells& prim, const Shell
 // integral and of the derivative kernel.
 int smem_eri3_doubles(int la, int lb, int lc);
 int smem_grad_doubles(int la, int lb, int lc);
+// (P|Q) classes (bit 8 la + lc, la, lc <= max_la) run by 8-lane task groups,
+// and the shared-memory slice (doubles) one such group needs.
+unsigned long long eri2_small_classes(int max_la, int* slice_doubles);
 
 // (pair index, auxiliary shell) tasks of one shared-memory class group.
 constexpr int kTaskGroups = 4;
