@@ -444,14 +444,20 @@ __host__ __device__ inline int schwarz_smem(int la, int lb, int* half_out) {
 // Four-centre recursion with the ket pair equal to the bra pair: bra VRR with
 // W = (pP + qQ)/(p+q), electron transfer to f = lc..lc+ld with the
 // -(beta AB + delta CD)/q term, bra HRR on every ket level f, then ket HRR.
+// G = 8 runs the classes set in small_mask (bit 8 la + lb, la >= lb), G = 32
+// the others.
+template <int G>
 __global__ void __launch_bounds__(32) schwarz_kernel(DevShells prim, const double* __restrict__ boys, int* counter,
-                                                     double* __restrict__ Q) {
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x;
+                                                     double* __restrict__ Q, unsigned long long small_mask,
+                                                     int slice) {
+  extern __shared__ double smem_all[];
+  const int lane = threadIdx.x % G;
+  double* smem = smem_all + (threadIdx.x / G) * slice;   // this task group's slice
+  const unsigned gm = lane_group_mask<G>();
   const int ns = prim.nshell;
   const long long ntask = (long long)ns * (ns + 1) / 2;
   for (;;) {
-    long long task = warp_next_task(counter, lane);
+    long long task = warp_next_task<G>(counter, lane);
     if (task >= ntask) break;
     int sa = (int)((sqrt(8.0 * (double)task + 1.0) - 1.0) * 0.5);
     while ((long long)sa * (sa + 1) / 2 > task) --sa;
@@ -459,6 +465,7 @@ __global__ void __launch_bounds__(32) schwarz_kernel(DevShells prim, const doubl
     int sb = (int)(task - (long long)sa * (sa + 1) / 2);
     if (prim.l[sa] < prim.l[sb]) { int t = sa; sa = sb; sb = t; }
     const int la = prim.l[sa], lb = prim.l[sb];
+    if ((int)((small_mask >> (8 * la + lb)) & 1ull) != (G == 8 ? 1 : 0)) continue;
     const int lc = la, ld = lb, lf = lc + ld;          // ket pair = bra pair
     const int emin = la, emax = la + lb, L = emax + lf;
     const int na = ncart(la), nb = ncart(lb);
@@ -476,7 +483,7 @@ __global__ void __launch_bounds__(32) schwarz_kernel(DevShells prim, const doubl
     double* scr = bra + brasz;
     int half = 0;
     schwarz_smem(la, lb, &half);
-    for (int i = lane; i < accsz; i += 32) acc[i] = 0.0;
+    for (int i = lane; i < accsz; i += G) acc[i] = 0.0;
     const double* A = prim.xyz + 3 * sa;
     const double* B = prim.xyz + 3 * sb;
     for (int pa = 0; pa < prim.nprim[sa]; ++pa)
@@ -507,16 +514,16 @@ __global__ void __launch_bounds__(32) schwarz_kernel(DevShells prim, const doubl
             t.T = t.rho * R2pq;
             t.pref = 34.98683665524972 / (p * q * sqrt(p + q)) * exp(-al * be / p * R2ab) * exp(-ga * de / q * R2ab);
             prim3_factors(t);
-            if (lane <= L) Fm[lane] = boys_eval(lane, t.T, boys);
-            __syncwarp();
-            warp_vrr(vrr, L, t, Fm, lane);
-            warp_etr(vrr, L, etr, sh, t, Fm, lane);
+            for (int m = lane; m <= L; m += G) Fm[m] = boys_eval(m, t.T, boys);
+            __syncwarp(gm);
+            warp_vrr<G>(vrr, L, t, Fm, lane);
+            warp_etr<G>(vrr, L, etr, sh, t, Fm, lane);
             // acc[f-block][e][ke][kf] += w * level f, e in [emin, emax]
             int off = 0;
             for (int f = lc; f <= lf; ++f) {
               int ncf = ncart(f);
               int n = (cart_offset(emax + 1) - cart_offset(emin)) * ncf;
-              for (int idx = lane; idx < n; idx += 32) {
+              for (int idx = lane; idx < n; idx += G) {
                 int r = idx / ncf, kf = idx - r * ncf;
                 int e = emin;
                 while (cart_offset(e + 1) - cart_offset(emin) <= r) ++e;
@@ -525,7 +532,7 @@ __global__ void __launch_bounds__(32) schwarz_kernel(DevShells prim, const doubl
               }
               off += n;
             }
-            __syncwarp();
+            __syncwarp(gm);
           }
     // bra HRR for every ket level f
     double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
@@ -533,9 +540,9 @@ __global__ void __launch_bounds__(32) schwarz_kernel(DevShells prim, const doubl
       int aoff = 0, boff = 0;
       for (int f = lc; f <= lf; ++f) {
         int ncf = ncart(f);
-        const double* out = warp_hrr(acc + aoff, emin, la, lb, f, AB, scr, half, lane);
-        for (int i = lane; i < na * nb * ncf; i += 32) bra[boff + i] = out[i];
-        __syncwarp();
+        const double* out = warp_hrr<G>(acc + aoff, emin, la, lb, f, AB, scr, half, lane);
+        for (int i = lane; i < na * nb * ncf; i += G) bra[boff + i] = out[i];
+        __syncwarp(gm);
         aoff += (cart_offset(emax + 1) - cart_offset(emin)) * ncf;
         boff += na * nb * ncf;
       }
@@ -554,7 +561,7 @@ __global__ void __launch_bounds__(32) schwarz_kernel(DevShells prim, const doubl
         int fhi = lf - d;
         int n = 0;
         for (int f = lc; f <= fhi; ++f) n += nab * ncart(f) * nd;
-        for (int idx = lane; idx < n; idx += 32) {
+        for (int idx = lane; idx < n; idx += G) {
           // decode idx -> (f, ab, kf, kd) with layout [f-block][ab][kf][kd]
           int rem = idx, f = lc;
           while (rem >= nab * ncart(f) * nd) { rem -= nab * ncart(f) * nd; ++f; }
@@ -578,23 +585,23 @@ __global__ void __launch_bounds__(32) schwarz_kernel(DevShells prim, const doubl
                      AB[i] * prev[o_f + (ab * ncf + kf) * prev_nd + kdl];
           cur[idx] = v;
         }
-        __syncwarp();
+        __syncwarp(gm);
         prev = cur;
         prev_nd = nd;
       }
       // prev now holds level f = lc only: [ab][kc][kd] with (kc, kd) over (la, lb) = (ka, kb)
-      for (int idx = lane; idx < nab; idx += 32) {
+      for (int idx = lane; idx < nab; idx += G) {
         int ka = idx / nb, kb = idx % nb;
         double v = prev[(idx * ncart(lc) + ka) * prev_nd + kb];
         qmax = fmax(qmax, fabs(v));
       }
     }
-    for (int o = 16; o > 0; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+    for (int o = G / 2; o > 0; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(gm, qmax, o));
     if (lane == 0) {
       int a0 = max(sa, sb), b0 = min(sa, sb);
       Q[(long long)a0 * (a0 + 1) / 2 + b0] = sqrt(qmax);
     }
-    __syncwarp();
+    __syncwarp(gm);
   }
 }
 
@@ -870,10 +877,30 @@ int schwarz_smem_bytes(int max_lp) {
 }
 
 void launch_schwarz(const IntegralCtx& ic, const DevShells& prim, int max_lp, double* Q) {
-  int smem = schwarz_smem_bytes(max_lp);
-  set_smem((const void*)schwarz_kernel, smem);
+  // small classes (working set within 3.5 KB) as 8-lane groups, four tasks
+  // per warp, then the rest with whole warps; each launch claims every task
+  // and skips the other's classes
+  unsigned long long mask = 0;
+  int small_slice = 0;
+  for (int la = 0; la <= max_lp; ++la)
+    for (int lb = 0; lb <= la; ++lb) {
+      const int d = schwarz_smem(la, lb, nullptr);
+      if (d * (int)sizeof(double) > 3584) continue;
+      mask |= 1ull << (8 * la + lb);
+      small_slice = std::max(small_slice, d);
+    }
+  if (mask) {
+    const int smem = 4 * small_slice * (int)sizeof(double);
+    set_smem((const void*)schwarz_kernel<8>, smem);
+    RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+    schwarz_kernel<8><<<grid_for(smem), 32, smem, ic.stream>>>(prim, ic.boys, ic.counter, Q, mask, small_slice);
+    RIHF_LAUNCH_CHECK();
+    if (ic.launches) *ic.launches += 1;
+  }
+  const int smem = schwarz_smem_bytes(max_lp);
+  set_smem((const void*)schwarz_kernel<32>, smem);
   RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
-  schwarz_kernel<<<grid_for(smem), 32, smem, ic.stream>>>(prim, ic.boys, ic.counter, Q);
+  schwarz_kernel<32><<<grid_for(smem), 32, smem, ic.stream>>>(prim, ic.boys, ic.counter, Q, mask, 0);
   RIHF_LAUNCH_CHECK();
   if (ic.launches) *ic.launches += 1;
 }
