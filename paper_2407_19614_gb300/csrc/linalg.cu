@@ -401,95 +401,102 @@ __global__ void potrf_diag_kernel(double* A, int n, int k, int b, double* inv, i
   }
 }
 
-// The factorisation alone, one warp: lane r keeps row r of the b x b block in
-// registers (columns unrolled), pivots and column entries travel by shuffle,
-// and each pivot costs one reciprocal square root (l_jj = d r, the column
-// scaled by r) -- the pivots form the kernel's serial chain.
-__global__ void __launch_bounds__(32) potrf_diag_reg_kernel(double* A, int n, int k, int b, int* flag) {
-  const int lane = threadIdx.x;
-  double a[CB];
+// One step of the right-looking blocked Cholesky (block CB = 32), in one launch
+// of 128-thread blocks.  Every block factors the diagonal block L_kk itself
+// (the same instructions on the same data, so every block gets the same bits):
+// lane r holds row r, warp w the columns c = 4 t + w, and each pivot column is
+// broadcast through shared memory, so the narrow FP64 pipes of all four SM
+// sub-partitions share the rank-1 updates while one warp runs the pivot's
+// reciprocal square root.  Block 0 stores L_kk in Ld (the diagonal block of A
+// is still being read by the other blocks; chol_finish_kernel copies it in).
+// Then the panel rows r >= k + b solve y L_kk^T = a_r by forward substitution,
+// four lanes per row (eight rows per warp) splitting each dot product.
+__global__ void __launch_bounds__(128) chol_step_kernel(double* A, int n, int k, int b, int* flag, double* Ld) {
+  __shared__ double l[CB][CB + 1];
+  __shared__ double piv[2][CB];
+  __shared__ double rd[CB];
+  __shared__ double ys[4][8][CB + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double a[CB / 4];
 #pragma unroll
-  for (int c = 0; c < CB; ++c) a[c] = (lane < b && c < b && c <= lane) ? A[(size_t)(k + lane) * n + k + c] : 0.0;
+  for (int t = 0; t < CB / 4; ++t) {
+    const int c = 4 * t + w;
+    a[t] = (lane < b && c < b && c <= lane) ? A[(size_t)(k + lane) * n + k + c] : 0.0;
+  }
 #pragma unroll
   for (int j = 0; j < CB; ++j) {
     if (j < b) {
-      double d = __shfl_sync(0xffffffffu, a[j], j);
-      if (!(d > 0.0)) {
-        if (lane == 0) atomicExch(flag, 1);
-        d = 1.0;
+      if (w == (j & 3)) {
+        double d = __shfl_sync(0xffffffffu, a[j >> 2], j);
+        if (!(d > 0.0)) {
+          if (lane == 0 && blockIdx.x == 0) atomicExch(flag, 1);
+          d = 1.0;
+        }
+        const double r = rsqrt(d);
+        if (lane == j) a[j >> 2] = d * r;
+        else if (lane > j) a[j >> 2] *= r;
+        piv[j & 1][lane] = a[j >> 2];
       }
-      const double r = rsqrt(d);
-      if (lane == j) a[j] = d * r;
-      else if (lane > j) a[j] *= r;
+      __syncthreads();   // also orders the reuse of piv[j & 1] two steps on
+      const double lj = piv[j & 1][lane];
 #pragma unroll
-      for (int c = j + 1; c < CB; ++c) {
-        const double lcj = __shfl_sync(0xffffffffu, a[j], c);
-        if (lane >= c) a[c] = fma(-a[j], lcj, a[c]);
+      for (int t = 0; t < CB / 4; ++t) {
+        const int c = 4 * t + w;
+        if (c > j && lane >= c) a[t] = fma(-lj, piv[j & 1][c], a[t]);
       }
     }
   }
-  if (lane < b) {
 #pragma unroll
-    for (int c = 0; c < CB; ++c)
-      if (c < b) A[(size_t)(k + lane) * n + k + c] = c <= lane ? a[c] : 0.0;
+  for (int t = 0; t < CB / 4; ++t) {
+    const int c = 4 * t + w;
+    l[lane][c] = a[t];
+    if (blockIdx.x == 0 && lane < b && c < b) Ld[(size_t)(k + lane) * CB + c] = a[t];
+  }
+  __syncthreads();
+  if (threadIdx.x < CB) rd[threadIdx.x] = threadIdx.x < b ? 1.0 / l[threadIdx.x][threadIdx.x] : 0.0;
+  __syncthreads();
+  const int rs = lane >> 2, sub = lane & 3;
+  double* y = ys[w][rs];
+  for (int r0 = k + b + (blockIdx.x * 4 + w) * 8; r0 < n; r0 += gridDim.x * 32) {
+    const int r = r0 + rs;
+    const bool valid = r < n;
+    for (int i = sub; i < b; i += 4) y[i] = valid ? A[(size_t)r * n + k + i] : 0.0;
+    __syncwarp();
+    for (int i = 0; i < b; ++i) {
+      double part = sub == 0 ? y[i] : 0.0;
+      for (int q = sub; q < i; q += 4) part = fma(-l[i][q], y[q], part);
+      part += __shfl_xor_sync(0xffffffffu, part, 1);
+      part += __shfl_xor_sync(0xffffffffu, part, 2);
+      if (sub == 0) y[i] = part * rd[i];
+      __syncwarp();
+    }
+    if (valid)
+      for (int i = sub; i < b; i += 4) A[(size_t)r * n + k + i] = y[i];
+    __syncwarp();
   }
 }
 
-__global__ void zero_upper_kernel(double* A, int n) {
+// The diagonal blocks from Ld into A; the upper triangle zeroed.
+__global__ void chol_finish_kernel(double* A, int n, const double* __restrict__ Ld) {
   long long total = (long long)n * n;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     int i = (int)(idx / n), j = (int)(idx % n);
     if (j > i) A[idx] = 0.0;
-  }
-}
-
-// Panel of the blocked Cholesky: rows r >= k+b of A[:, k:k+b] solve
-// y L_kk^T = a_r by forward substitution (one thread per row; the blocks are
-// one warp wide so that the rows, each a chain of dependent FP64 operations,
-// spread over as many SMs as there are warps of rows).
-__global__ void __launch_bounds__(256) chol_panel_kernel(double* A, int n, int k, int b) {
-  __shared__ double l[CB][CB + 1];
-  __shared__ double rd[CB];
-  for (int i = threadIdx.x; i < CB * CB; i += blockDim.x) {
-    int r = i / CB, c = i % CB;
-    l[r][c] = (r < b && c < b) ? A[(size_t)(k + r) * n + k + c] : 0.0;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < CB; i += blockDim.x) rd[i] = i < b ? 1.0 / l[i][i] : 0.0;
-  __syncthreads();
-  for (int r = k + b + blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-    double* row = A + (size_t)r * n + k;
-    double y[CB];
-#pragma unroll
-    for (int i = 0; i < CB; ++i) y[i] = i < b ? row[i] : 0.0;
-#pragma unroll
-    for (int i = 0; i < CB; ++i) {
-      if (i >= b) break;
-      double s = y[i];
-#pragma unroll
-      for (int q = 0; q < i; ++q) s -= l[i][q] * y[q];
-      y[i] = s * rd[i];
-    }
-#pragma unroll
-    for (int i = 0; i < CB; ++i)
-      if (i < b) row[i] = y[i];
+    else if (i / CB == j / CB) A[idx] = Ld[(size_t)i * CB + (j % CB)];
   }
 }
 
 void cholesky(const LaCtx& la, double* A, int n, double* scratch) {
-  (void)scratch;   // the diagonal blocks are factored in registers
+  double* Ld = scratch;   // n x CB: the factored diagonal blocks
   for (int k = 0; k < n; k += CB) {
     int b = std::min(CB, n - k);
-    potrf_diag_reg_kernel<<<1, 32, 0, la.stream>>>(A, n, k, b, la.flag);
-    RIHF_LAUNCH_CHECK();
-    count(la);
     int rest = n - k - b;
-    if (rest <= 0) break;
-    // panel: A[k+b:, k:k+b] <- A[k+b:, k:k+b] L_kk^{-T} by substitution
-    chol_panel_kernel<<<std::max(1, std::min(ceil_div(rest, 32), 8 * la.sms)), 32, 0, la.stream>>>(A, n, k, b);
+    // L_kk, and A[k+b:, k:k+b] <- A[k+b:, k:k+b] L_kk^{-T}
+    chol_step_kernel<<<std::max(1, ceil_div(rest, 32)), 128, 0, la.stream>>>(A, n, k, b, la.flag, Ld);
     RIHF_LAUNCH_CHECK();
     count(la);
+    if (rest <= 0) break;
     // trailing update: A[k+b:, k+b:] -= panel panel^T, lower tiles only (the
     // factorisation never reads the upper triangle; it is zeroed at the end)
     GemmArgs u;
@@ -501,7 +508,8 @@ void cholesky(const LaCtx& la, double* A, int n, double* scratch) {
     u.lower_only = true;
     dgemm(la, u);
   }
-  zero_upper_kernel<<<std::max(1, std::min(ceil_div((long long)n * n, 256), 8 * la.sms)), 256, 0, la.stream>>>(A, n);
+  chol_finish_kernel<<<std::max(1, std::min(ceil_div((long long)n * n, 256), 8 * la.sms)), 256, 0, la.stream>>>(
+      A, n, Ld);
   RIHF_LAUNCH_CHECK();
   count(la);
 }
