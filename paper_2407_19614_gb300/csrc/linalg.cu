@@ -346,61 +346,6 @@ void symmetrize_lower(const LaCtx& la, double* X, int n, int batch) {
 
 constexpr int CB = 32;
 
-// Factor the b x b diagonal block at (k, k) of A (leading dim n) and write its
-// inverse into inv (CB x CB, lower).  One warp.
-// want_inv = 0 skips the block inverse (the Cholesky panel substitutes instead).
-__global__ void potrf_diag_kernel(double* A, int n, int k, int b, double* inv, int* flag, int factor,
-                                  int want_inv = 1) {
-  __shared__ double a[CB][CB + 1];
-  __shared__ double li[CB][CB + 1];
-  __shared__ double rpiv;
-  int lane = threadIdx.x;
-  for (int i = 0; i < b; ++i) a[i][lane] = (lane < b) ? A[(size_t)(k + i) * n + k + lane] : 0.0;
-  __syncwarp();
-  if (factor) {
-    for (int j = 0; j < b; ++j) {
-      if (lane == 0) {
-        double d = a[j][j];
-        if (!(d > 0.0)) {
-          atomicExch(flag, 1);
-          d = 1.0;
-        }
-        a[j][j] = sqrt(d);
-        rpiv = 1.0 / a[j][j];
-      }
-      __syncwarp();
-      if (lane > j && lane < b) a[lane][j] *= rpiv;
-      __syncwarp();
-      if (lane > j && lane < b)
-        for (int c = j + 1; c <= lane; ++c) a[lane][c] -= a[lane][j] * a[c][j];
-      __syncwarp();
-    }
-  }
-  if (!want_inv) {
-    if (factor)
-      for (int i = 0; i < b; ++i)
-        if (lane < b) A[(size_t)(k + i) * n + k + lane] = lane <= i ? a[i][lane] : 0.0;
-    return;
-  }
-  // inverse of the lower factor, column `lane`
-  for (int i = 0; i < CB; ++i) li[i][lane] = 0.0;
-  __syncwarp();
-  if (lane < b) {
-    int j = lane;
-    li[j][j] = 1.0 / a[j][j];
-    for (int i = j + 1; i < b; ++i) {
-      double s = 0.0;
-      for (int q = j; q < i; ++q) s += a[i][q] * li[q][j];
-      li[i][j] = -s / a[i][i];
-    }
-  }
-  __syncwarp();
-  for (int i = 0; i < b; ++i) {
-    if (factor && lane < b) A[(size_t)(k + i) * n + k + lane] = lane <= i ? a[i][lane] : 0.0;
-    inv[i * CB + lane] = li[i][lane];
-  }
-}
-
 // One step of the right-looking blocked Cholesky (block CB = 32), in one launch
 // of 128-thread blocks.  Every block factors the diagonal block L_kk itself
 // (the same instructions on the same data, so every block gets the same bits):
@@ -431,10 +376,11 @@ __global__ void __launch_bounds__(128) chol_step_kernel(double* A, int n, int k,
         if (!(d > 0.0)) {
           if (lane == 0 && blockIdx.x == 0) atomicExch(flag, 1);
           d = 1.0;
+          if (lane == j) a[j >> 2] = 1.0;
         }
-        const double r = rsqrt(d);
-        if (lane == j) a[j >> 2] = d * r;
-        else if (lane > j) a[j >> 2] *= r;
+        // rows above the pivot hold zeros and row j holds d itself, so one
+        // multiply gives l_jj = d r and the column below scaled by r
+        a[j >> 2] *= rsqrt(d);
         piv[j & 1][lane] = a[j >> 2];
       }
       __syncthreads();   // also orders the reuse of piv[j & 1] two steps on
@@ -525,43 +471,6 @@ void identity(const LaCtx& la, double* X, int n) {
   identity_kernel<<<std::max(1, std::min(ceil_div((long long)n * n, 256), 8 * la.sms)), 256, 0, la.stream>>>(X, n);
   RIHF_LAUNCH_CHECK();
   count(la);
-}
-
-// X = L^{-1} by blocked forward substitution on the identity; scratch holds
-// CB*CB + n*CB doubles.
-void tri_inverse_lower(const LaCtx& la, const double* L, double* X, int n, double* scratch) {
-  identity(la, X, n);
-  double* inv = scratch;
-  double* tmp = scratch + CB * CB;
-  for (int k = 0; k < n; k += CB) {
-    int b = std::min(CB, n - k);
-    potrf_diag_kernel<<<1, 32, 0, la.stream>>>(const_cast<double*>(L), n, k, b, inv, la.flag, 0);
-    RIHF_LAUNCH_CHECK();
-    count(la);
-    int ncol = k + b;
-    // tmp (b x ncol) = inv * X[k:k+b, 0:ncol]
-    GemmArgs g;
-    g.M = b; g.N = ncol; g.K = b;
-    g.A = inv; g.lda = CB;
-    g.B = X + (size_t)k * n; g.ldb = n;
-    g.C = tmp; g.ldc = ncol;
-    dgemm(la, g);
-    // X[k:k+b, 0:ncol] = tmp
-    GemmArgs c2;   // copy via identity product would waste flops; use a plain copy
-    RIHF_CUDA(cudaMemcpy2DAsync(X + (size_t)k * n, n * sizeof(double), tmp, ncol * sizeof(double),
-                                ncol * sizeof(double), b, cudaMemcpyDeviceToDevice, la.stream));
-    (void)c2;
-    int rest = n - k - b;
-    if (rest <= 0) break;
-    // X[k+b:, 0:ncol] -= L[k+b:, k:k+b] * X[k:k+b, 0:ncol]
-    GemmArgs u;
-    u.M = rest; u.N = ncol; u.K = b;
-    u.A = L + (size_t)(k + b) * n + k; u.lda = n;
-    u.B = X + (size_t)k * n; u.ldb = n;
-    u.C = X + (size_t)(k + b) * n; u.ldc = n;
-    u.alpha = -1.0; u.beta = 1.0;
-    dgemm(la, u);
-  }
 }
 
 // Substitution inside one diagonal block: every thread owns one column j of the

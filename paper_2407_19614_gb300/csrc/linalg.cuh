@@ -97,9 +97,7 @@ void trsm_lower_t_tc(const LaCtx& la, const double* L, int n, double* X, long lo
 
 // In-place Cholesky A = L L^T (lower, upper part zeroed) of an n x n matrix;
 // sets *flag = 1 on a non-positive pivot.  scratch holds n x 32 doubles.
-// Then Linv = L^{-1} (n x n).
 void cholesky(const LaCtx& la, double* A, int n, double* scratch);
-void tri_inverse_lower(const LaCtx& la, const double* L, double* Linv, int n, double* scratch);
 
 // Blocked triangular solve in place: X <- L^{-1} X (trans = false, forward) or
 // X <- L^{-T} X (trans = true, backward), L lower n x n, X n x ncol row-major
