@@ -527,17 +527,14 @@ void launch_grad_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShe
     const int W = groups[g].width, slice = groups[g].smem_grad / (int)sizeof(double);
     const int smem = (32 / W) * slice * (int)sizeof(double);
     RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
-    if (W == 8) {
-      raise_smem_limit((const void*)grad_eri3_kernel<8>, smem);
-      grad_eri3_kernel<8><<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks,
-                                                                        groups[g].ntask, ic.boys, ic.counter, Y,
-                                                                        grad, slice);
-    } else {
-      raise_smem_limit((const void*)grad_eri3_kernel<32>, smem);
-      grad_eri3_kernel<32><<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks,
-                                                                         groups[g].ntask, ic.boys, ic.counter, Y,
-                                                                         grad, slice);
-    }
+    auto run = [&](auto kernel) {
+      raise_smem_limit((const void*)kernel, smem);
+      kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks, groups[g].ntask,
+                                                           ic.boys, ic.counter, Y, grad, slice);
+    };
+    if (W == 8) run(grad_eri3_kernel<8>);
+    else if (W == 16) run(grad_eri3_kernel<16>);
+    else run(grad_eri3_kernel<32>);
     RIHF_LAUNCH_CHECK();
     if (ic.launches) *ic.launches += 1;
   }

@@ -641,15 +641,14 @@ void launch_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& 
     const int W = groups[g].width, slice = groups[g].smem_eri3 / (int)sizeof(double);
     const int smem = (32 / W) * slice * (int)sizeof(double);
     RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
-    if (W == 8) {
-      set_smem((const void*)eri3_kernel<8>, smem);
-      eri3_kernel<8><<<grid_for(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks,
-                                                              groups[g].ntask, ic.boys, ic.counter, T, slice);
-    } else {
-      set_smem((const void*)eri3_kernel<32>, smem);
-      eri3_kernel<32><<<grid_for(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks,
-                                                               groups[g].ntask, ic.boys, ic.counter, T, slice);
-    }
+    auto run = [&](auto kernel) {
+      set_smem((const void*)kernel, smem);
+      kernel<<<grid_for(smem), 32, smem, ic.stream>>>(prim, aux, pairs, pt, groups[g].tasks, groups[g].ntask, ic.boys,
+                                                      ic.counter, T, slice);
+    };
+    if (W == 8) run(eri3_kernel<8>);
+    else if (W == 16) run(eri3_kernel<16>);
+    else run(eri3_kernel<32>);
     RIHF_LAUNCH_CHECK();
     if (ic.launches) *ic.launches += 1;
   }
@@ -804,9 +803,11 @@ void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lpr
 void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim,
                        const std::vector<int>& laux, std::vector<std::vector<int2>>& tasks,
                        std::vector<int>& smem_eri3, std::vector<int>& smem_grad) {
-  // group 0: tiny classes as 8-lane groups (4 tasks per warp); then about 17,
-  // 7 and at most 2 warps per SM (228 KB shared memory, 1 KB reserved per block)
-  const int limits[kTaskGroups] = {3584, 12 * 1024, 28 * 1024, 1 << 30};
+  // group 0: tiny classes as 8-lane groups (4 tasks per warp); group 1: small
+  // classes as 16-lane groups (2 tasks per warp, about 15 warps per SM); then
+  // about 17, 7 and at most 2 warps per SM (228 KB shared memory, 1 KB
+  // reserved per block)
+  const int limits[kTaskGroups] = {3584, 7168, 12 * 1024, 28 * 1024, 1 << 30};
   constexpr int nl = kMaxLPrim + 1, nc = kMaxLAux + 1;
   int se[nl][nl][nc], sg[nl][nl][nc], grp[nl][nl][nc];
   for (int la = 0; la < nl; ++la)

@@ -61,15 +61,15 @@ int smem_grad_doubles(int la, int lb, int lc);
 unsigned long long eri2_small_classes(int max_la, int* slice_doubles);
 
 // (pair index, auxiliary shell) tasks of one shared-memory class group.
-constexpr int kTaskGroups = 4;
+constexpr int kTaskGroups = 5;
 struct TaskGroup {
   const int2* tasks = nullptr;
   long long ntask = 0;
   int smem_eri3 = 0, smem_grad = 0;   // bytes per task
-  int width = 32;                     // lanes per task (8: four tasks per warp)
+  int width = 32;                     // lanes per task (8: four tasks per warp, 16: two)
 };
 // Lanes per task of class group g (group 0 holds the tiny classes).
-inline int task_group_width(int g) { return g == 0 ? 8 : 32; }
+inline int task_group_width(int g) { return g == 0 ? 8 : g == 1 ? 16 : 32; }
 void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim,
                        const std::vector<int>& laux, std::vector<std::vector<int2>>& tasks,
                        std::vector<int>& smem_eri3, std::vector<int>& smem_grad);
