@@ -66,7 +66,7 @@ class Molecule:
 PRIMARY_SMALL = {"O": (3, 2, 1), "H": (2, 1)}            # 24 spherical functions / water
 AUX_SMALL = {"O": (8, 6, 4, 2), "H": (4, 3, 2)}          # 106 spherical functions / water
 PRIMARY_LARGE = {"O": (4, 3, 2, 1), "H": (3, 2, 1)}      # 58 spherical functions / water
-AUX_LARGE = {"O": (11, 8, 6, 3, 2), "H": (6, 4, 3)}      # 137 spherical functions / water
+AUX_LARGE = {"O": (11, 8, 6, 3, 2), "H": (6, 4, 3)}      # 170 spherical functions / water
 
 PRIMARY_A0, PRIMARY_RATIO = 0.1, 3.0
 AUX_A0, AUX_RATIO = 0.15, 2.5
