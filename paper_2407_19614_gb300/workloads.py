@@ -165,7 +165,7 @@ def water16(seed=0):
 
 
 def water32_large(seed=0):
-    """(H2O)32 in an 11 A cube with the larger basis: 1856 primary / 4384 auxiliary."""
+    """(H2O)32 in an 11 A cube with the larger basis: 1856 primary / 5440 auxiliary."""
     return make_molecule(32, 11.0, seed, "large")
 
 
