@@ -50,3 +50,30 @@ def test_binding_loads_and_matches_header(libpath):
     assert o.diis_size == 8 and o.pure == 1
     assert o.cuda_graphs == 1 and o.confirm_fp64 == 0   # the struct's tail matches the header
 
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof and every field offset of rihf_options and rihf_shell, as a C
+    compiler lays them out from include/rihf.h, against the binding's ctypes
+    structures (a field added on one side only shifts everything after it)."""
+    import ctypes
+    from paper_2407_19614_gb300 import rihf as R
+    structs = {"rihf_options": R.rihf_options, "rihf_shell": R.rihf_shell}
+    lines = []
+    for sname, cls in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (sname, sname))
+        for fname, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (sname, fname, sname, fname))
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "rihf.h"\nint main(void) {\n%s\nreturn 0;\n}\n'
+                   % "\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        k, v = line.rsplit(" ", 1)
+        got[k] = int(v)
+    for sname, cls in structs.items():
+        assert got["%s size" % sname] == ctypes.sizeof(cls), sname
+        for fname, _ in cls._fields_:
+            assert got["%s %s" % (sname, fname)] == getattr(cls, fname).offset, (sname, fname)
