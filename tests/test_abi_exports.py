@@ -77,3 +77,15 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got["%s size" % sname] == ctypes.sizeof(cls), sname
         for fname, _ in cls._fields_:
             assert got["%s %s" % (sname, fname)] == getattr(cls, fname).offset, (sname, fname)
+
+
+def test_enums_match_the_header():
+    """The matrix selectors, error codes and precision values of the binding
+    against the enums of include/rihf.h."""
+    from paper_2407_19614_gb300 import rihf as R
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    enum = {k: int(v) for k, v in re.findall(r"\b(RIHF_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+    mats = {k[len("RIHF_MAT_"):]: v for k, v in enum.items() if k.startswith("RIHF_MAT_")}
+    assert mats == R.MAT
+    assert enum["RIHF_OK"] == 0 and enum["RIHF_ERR_STATE"] == -7
+    assert enum["RIHF_PRECISION_FP64"] == 0 and enum["RIHF_PRECISION_MIXED"] == 1
