@@ -28,6 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "RI-HF AIMD steps/s (E+grad), mixed vs FP64 at |dE|<=1e-6 Eh; % of roofline"
+WORKLOAD = ("(H2O)8 RI-HF E+grad AIMD step, N=192, Naux=848, spherical, dt 0.5 fs, previous-orbital guess")
 UNIT = "AIMD steps/s"
 DT_FS = 0.5
 CONV = dict(conv_e=1e-8, conv_diis=1e-7, max_iter=60)
@@ -126,74 +127,149 @@ def barrier(pg):
 
 
 class Trajectory:
-    """Velocity-Verlet driver over one context (host-side integrator, 3*natoms doubles)."""
+    """Velocity-Verlet driver over one context (host-side integrator, 3*natoms
+    doubles).  With `replay` (a list of geometries) the steps visit those
+    geometries instead of integrating, so that another path (the FP64 one) is
+    evaluated on exactly the geometries of the first."""
 
-    def __init__(self, ctx, mol, seed, R):
+    def __init__(self, ctx, mol, seed, R, replay=None):
         from paper_2407_19614_gb300 import workloads as W
         self.ctx, self.R = ctx, R
         self.m = W.masses_au(mol.Z)[:, None]
         self.x = mol.xyz.copy()
         self.v = W.maxwell_boltzmann(mol.Z, 300.0, seed)
         self.dt = DT_FS * W.FS_TO_AU
+        self.replay = replay
+        self.k = 0
+        self.geoms = []
         out = ctx.scf(guess=0, outputs=False)
         self.E = out["energy"]
         self.g = ctx.gradient()
         self.iters = [out["iterations"]]
 
-    def step(self):
+    def next_geometry(self):
+        if self.replay is not None:
+            return self.replay[self.k]
         a = -self.g / self.m
-        self.x = self.x + self.v * self.dt + 0.5 * a * self.dt ** 2
-        self.ctx.update_geometry(self.x)
-        out = self.ctx.scf(guess=2, outputs=False)
-        self.E = out["energy"]
-        self.iters.append(out["iterations"])
-        g_new = self.ctx.gradient()
+        return self.x + self.v * self.dt + 0.5 * a * self.dt ** 2
+
+    def finish(self, x, E, g_new):
+        """Velocity update and bookkeeping after the energy and forces at x."""
+        a = -self.g / self.m
+        self.x = x
+        self.E = E
         self.v = self.v + 0.5 * (a - g_new / self.m) * self.dt
         self.g = g_new
+        self.geoms.append(x.copy())
+        self.k += 1
+
+    def step(self):
+        x = self.next_geometry()
+        self.ctx.update_geometry(x)
+        out = self.ctx.scf(guess=2, outputs=False)
+        self.iters.append(out["iterations"])
+        self.finish(x, out["energy"], self.ctx.gradient())
+
+    def state(self):
+        return dict(x=self.x.copy(), v=self.v.copy(), g=self.g.copy(), E=self.E, k=self.k)
+
+    def restore(self, st):
+        """Back to a saved state; the context is re-converged at its geometry
+        (from the core-Hamiltonian guess: the same fixed point as before)."""
+        self.x, self.v, self.g, self.E, self.k = st["x"].copy(), st["v"].copy(), st["g"].copy(), st["E"], st["k"]
+        self.ctx.update_geometry(self.x)
+        self.ctx.scf(guess=0, outputs=False)
+        self.ctx.gradient()
 
     def total_energy(self):
         return self.E + 0.5 * float(np.sum(self.m * self.v ** 2))
 
 
-def cpu_oracle_sample(n_iter):
-    """Time the CPU oracle on a bounded sample of one (H2O)8 AIMD step and scale
-    to a full step: integrals + fit, 2 SCF iterations (scaled to n_iter), the
-    gradient terms of 1 of 24 atoms (scaled to all atoms)."""
-    import scipy.linalg as sla
-    from oracle import integrals as OI
+def oracle_aimd(budget_s, max_steps, conv=CONV, molecule="water8"):
+    """The CPU oracle, as it stands, running the benchmark's own AIMD: (H2O)8
+    from the same start (positions, seeded 300 K velocities), velocity Verlet at
+    0.5 fs, each step the full method -- integrals, fit, SCF to the bench's
+    convergence criteria from the previous step's orbitals, and the analytic
+    gradient.  The untimed start is the core-guess SCF and gradient that any
+    Verlet run needs; then whole steps are timed one by one until `max_steps`
+    or until the next step would pass `budget_s` of timed work.  Returns the
+    per-step times and a description of what ran."""
     from oracle import rihf as O
     from paper_2407_19614_gb300 import workloads as W
-    mol = W.water8(0)
+    mol = W.water8(0) if molecule == "water8" else W.water_monomer(0)
+    m = W.masses_au(mol.Z)[:, None]
+    dt = DT_FS * W.FS_TO_AU
+    x = mol.xyz.copy()
+    v = W.maxwell_boltzmann(mol.Z, 300.0, 0)
+    okw = dict(conv_e=conv["conv_e"], conv_diis=conv["conv_diis"], max_iter=conv["max_iter"])
+
+    def energy_grad(xyz, C):
+        import copy
+        mk = copy.copy(mol)
+        mk.xyz = xyz
+        s = O.System(mk)
+        r = O.rihf_energy(s, C_guess=C, **okw)
+        g = O.rihf_gradient_terms(s, r)
+        return r, g.grad
+
     t0 = time.perf_counter()
-    s = O.System(mol)
-    L, B = O.cholesky_fit(s.A, s.T3)
-    t1 = time.perf_counter()
-    X = O.canonical_orthogonaliser(s.S)
-    e, Cp = np.linalg.eigh(X.T @ s.h @ X)
-    C = X @ Cp
-    for _ in range(2):
-        Co = C[:, : s.nocc]
-        D = 2 * Co @ Co.T
-        F = s.h + O.coulomb_ri(B, D) + O.exchange_ri(B, Co)
-        e, Cp = np.linalg.eigh(X.T @ F @ X)
-        C = X @ Cp
-    t2 = time.perf_counter()
-    # gradient: shared prep, then one atom's derivative integrals
-    Ct = np.sqrt(2.0) * C[:, : s.nocc]
-    cho = sla.cho_factor(s.A, lower=True)
-    Tij = np.einsum("mi,pmn,nj->pij", Ct, s.T3, Ct, optimize=True)
-    Xf = sla.cho_solve(cho, Tij.reshape(s.naux, -1))
-    t3 = time.perf_counter()
-    for d in range(3):
-        s.eri3_ao(datom=0, ddim=d)
-        OI.eri2(s.aux.cb, datom=0, ddim=d)
-        OI.one_electron(2, s.bas.cb, s.Z, s.xyz, datom=0, ddim=d)
-    t4 = time.perf_counter()
-    del Xf
-    step_s = (t1 - t0) + (t2 - t1) / 2 * n_iter + (t3 - t2) + (t4 - t3) * mol.natoms
-    return {"step_s": step_s, "sample_s": t4 - t0,
-            "sample": "(H2O)8 oracle: integrals+fit, 2 SCF iterations (scaled to %.1f), gradient terms of 1/24 atoms "
-                      "(scaled to 24)" % n_iter}
+    r, g = energy_grad(x, None)
+    t_start = time.perf_counter() - t0
+    times, iters = [], []
+    while len(times) < max_steps:
+        if times and sum(times) + statistics.mean(times) > budget_s:
+            break
+        t1 = time.perf_counter()
+        a = -g / m
+        x = x + v * dt + 0.5 * a * dt * dt
+        r, g_new = energy_grad(x, r.C)
+        v = v + 0.5 * (a - g_new / m) * dt
+        g = g_new
+        times.append(time.perf_counter() - t1)
+        iters.append(r.iterations)
+    return {"times": times, "start_s": t_start, "iters": iters,
+            "sample": ("(H2O)8" if molecule == "water8" else "H2O") + " oracle AIMD from the benchmark's start: %d whole steps timed (integrals, fit, SCF from "
+                      "the previous orbitals to conv_e %g / conv_diis %g, analytic gradient), %.1f s each on "
+                      "average, %.1f SCF iterations per step; untimed core-guess start %.1f s"
+                      % (len(times), conv["conv_e"], conv["conv_diis"], statistics.mean(times),
+                         statistics.mean(iters), t_start)}
+
+
+_ONE_CORE_PIECE = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+from oracle import rihf as O
+from paper_2407_19614_gb300 import workloads as W
+import numpy as np
+mol = W.water8(0)
+t0 = time.perf_counter()
+s = O.System(mol)
+L, B = O.cholesky_fit(s.A, s.T3)
+X = O.canonical_orthogonaliser(s.S)
+e, Cp = np.linalg.eigh(X.T @ s.h @ X)
+Co = (X @ Cp)[:, :s.nocc]
+F = s.h + O.coulomb_ri(B, 2 * Co @ Co.T) + O.exchange_ri(B, Co)
+s.eri3_ao(datom=0, ddim=0)
+print(json.dumps({"s": time.perf_counter() - t0}))
+"""
+
+
+def oracle_piece_cores():
+    """Seconds of one fixed piece of the oracle's step -- integrals, fit, one
+    Fock build and one coordinate's derivative 3-centre integrals -- on all host
+    cores and, in a child process with every thread pool at one thread, on one
+    core."""
+    out = {}
+    for label, nthreads in (("all", None), ("one", "1")):
+        env = dict(os.environ)
+        if nthreads:
+            for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+                env[k] = nthreads
+        r = subprocess.run([sys.executable, "-c", _ONE_CORE_PIECE % ROOT], env=env, capture_output=True, text=True)
+        if r.returncode != 0:
+            return None
+        out[label] = json.loads(r.stdout.strip().splitlines()[-1])["s"]
+    return out
 
 
 def run_reference(args):
@@ -201,27 +277,27 @@ def run_reference(args):
     if rank != 0:
         return 0
     ncore = os.cpu_count()
-    for _ in range(args.warmup):
-        cpu_oracle_sample(12.0)
-    times = []
-    samples = []
-    for _ in range(args.steps):
-        r = cpu_oracle_sample(12.0)
-        times.append(r["step_s"])
-        samples.append(r["sample_s"])
-    step_s = statistics.median(times)
+    res = oracle_aimd(budget_s=args.ref_budget, max_steps=args.steps, molecule=args.ref_molecule)
+    step_s = statistics.mean(res["times"])
     value = 1.0 / step_s
+    piece = oracle_piece_cores() if args.ref_molecule == "water8" else None
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "(H2O)8 RI-HF E+grad AIMD step, N=192, Naux=848, spherical, dt 0.5 fs, "
-                               "previous-orbital guess",
-                   "precision": "fp64 (CPU oracle)", "scf_iters_assumed": 12},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncore, "kind": "oracle",
-                         "sample": r["sample"] + "; per step %.1f s of CPU work" % statistics.median(samples)},
+        "steps": args.steps, "steps_timed": len(res["times"]), "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.ref_molecule == "water8" else "H2O monomer (host-logic check)",
+                   "precision": "fp64 (CPU oracle)",
+                   "timing": "whole oracle AIMD steps, timed one by one; the oracle has nothing to warm up, so "
+                             "no warm-up steps run; at most --ref-budget seconds of timed steps",
+                   "scf_iters_avg": float(np.mean(res["iters"]))},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncore, "kind": "oracle", "sample": res["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    if piece:
+        line["cpu_baseline"]["one_core"] = {
+            "piece": "integrals, fit, one Fock build, one coordinate's derivative 3-centre integrals",
+            "s_all_cores": piece["all"], "s_one_core": piece["one"], "speedup": piece["one"] / piece["all"],
+            "steps_per_s_one_core_scaled": value * piece["all"] / piece["one"]}
     print(json.dumps(line))
     return 0
 
@@ -285,6 +361,12 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison run (mixed only)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=75.0,
+                    help="seconds of timed whole oracle steps for the cpu_baseline of the main line")
+    ap.add_argument("--ref-budget", type=float, default=240.0,
+                    help="seconds of timed whole oracle steps for --impl reference")
+    ap.add_argument("--ref-molecule", default="water8", choices=["water8", "monomer"],
+                    help="workload of --impl reference (the monomer only checks the arm's host logic quickly)")
     ap.add_argument("--batch", type=int, default=0,
                     help="batched mode: this many independent clusters of 3..--batch-max waters per AIMD step")
     ap.add_argument("--batch-max", type=int, default=8)
@@ -318,9 +400,10 @@ def main():
     res = measure_path(R, W, torch, main_prec, args, rank, local, pg, trace=True)
     cmp = None
     if main_prec == "mixed" and not args.no_compare:
-        # the FP64 path on the same trajectory: its throughput, and the largest
-        # per-step energy difference of the two paths (the |dE| of the metric)
-        cmp = measure_path(R, W, torch, "fp64", args, rank, local, pg, trace=False)
+        # the FP64 path on the same geometries (warm-up and timed steps of the
+        # run above): its throughput, and per step |E_mixed - E_fp64| and the
+        # largest force difference -- the |dE| of the metric
+        cmp = measure_path(R, W, torch, "fp64", args, rank, local, pg, trace=False, replay=res["all_geoms"])
     if rank != 0:
         return 0
     world = res["world"]
@@ -360,21 +443,23 @@ def main():
                 "dominant_kernel": dom["name"], "dominant_share": dom["ms"] / sum(s["ms"] for s in stats)}
     cpu = None
     if not args.no_cpu_baseline:
-        r = cpu_oracle_sample(float(np.mean(res["iters"])))
-        cpu = {"value": 1.0 / r["step_s"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+        r = oracle_aimd(budget_s=args.cpu_budget, max_steps=args.steps)
+        cpu = {"value": 1.0 / statistics.mean(r["times"]), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": r["sample"]}
     grad_bytes = res["natoms"] * 3 * 8
-    config = {"workload": "(H2O)8 RI-HF E+grad AIMD step, N=192, Naux=848, spherical, dt 0.5 fs, "
-                          "previous-orbital guess",
-              "precision": main_prec, "parallelism": "replicas" if world > 1 else "1 GPU",
+    config = {"workload": WORKLOAD, "precision": main_prec, "parallelism": "replicas" if world > 1 else "1 GPU",
               "l2": "inputs larger than L2 (B = 250 MB)", "scf_conv": CONV,
               "scf_iters_avg": float(np.mean(res["iters"])), "energy_drift_eh": res["drift"],
               "kernel_times": "CUDA events per launch on the library stream during the timed steps; SCF "
-                              "iterations replay as CUDA graphs and are timed as a unit"}
+                              "iterations replay as CUDA graphs and are timed as a unit",
+              "e2e_region": "the timed steps again from the same start state (same geometries), through the "
+                            "public API with pinned host buffers",
+              "e2e_replay_max_abs_dE_eh": res["e2e_replay_dE"]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": res["ms_max"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if main_prec == "fp64" else "bf16 digit planes (RI-K, fit, gradient products) + f64", "data": "synthetic",
+        "dtype": "f64" if main_prec == "fp64" else "bf16 digit planes (RI-K, fit, gradient products) + f64",
+        "data": "synthetic",
         "config": config,
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -386,34 +471,41 @@ def main():
                     sorted(stats, key=lambda s: -s["ms"])],
     }
     if cmp is not None:
-        dE = float(np.max(np.abs(np.array(res["energies"]) - np.array(cmp["energies"]))))
+        dE = np.abs(np.array(res["energies"]) - np.array(cmp["energies"]))
+        dF = max(float(np.abs(a - b).max()) for a, b in zip(res["grads"], cmp["grads"]))
         line["fp64_path"] = {"value": world * args.steps / (cmp["ms_max"] / 1e3), "unit": UNIT,
                              "ms_per_step": cmp["ms_max"] / args.steps,
                              "scf_iters_avg": float(np.mean(cmp["iters"])),
-                             "gpu_launches": int(cmp["launches"])}
-        config["max_abs_dE_vs_fp64_path_eh"] = dE
+                             "gpu_launches": int(cmp["launches"]),
+                             "geometries": "the mixed path's warm-up and timed geometries, replayed"}
+        config["max_abs_dE_vs_fp64_path_eh"] = float(dE.max())
+        config["max_abs_dF_vs_fp64_path_eh_bohr"] = dF
+        config["speedup_vs_fp64_path"] = value / line["fp64_path"]["value"]
     print(json.dumps(line))
     return 0
 
 
-def measure_path(R, W, torch, precision, args, rank, local, pg, trace):
+def measure_path(R, W, torch, precision, args, rank, local, pg, trace, replay=None):
     """Warm-up and timed AIMD steps of one context (device time by CUDA events on
-    the library stream, then the end-to-end pass through the public API)."""
+    the library stream), then the same steps again end to end through the public
+    API from the same start state.  With `replay`, the steps visit those
+    geometries instead of integrating."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     prec = R.PRECISION_MIXED if precision == "mixed" else R.PRECISION_FP64
     mol = W.water8(rank)
     ctx = R.Context(mol, precision=prec, device=local, **CONV)
-    traj = Trajectory(ctx, mol, rank, R)
+    traj = Trajectory(ctx, mol, rank, R, replay=replay)
     stream = torch.cuda.ExternalStream(ctx.stream(), device=local)
     for _ in range(max(args.warmup, 0)):
         traj.step()
+    start = traj.state()
     # ---- timed region 1: device time (CUDA events on the library stream)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     launches0 = ctx.timings()["launches"]
     it0 = len(traj.iters)
     Etot0 = traj.total_energy()
-    energies = []
+    energies, grads = [], []
     ctx.trace(bool(trace))
     barrier(pg)
     torch.cuda.synchronize()
@@ -422,6 +514,7 @@ def measure_path(R, W, torch, precision, args, rank, local, pg, trace):
         for _ in range(args.steps):
             traj.step()
             energies.append(traj.E)
+            grads.append(traj.g.copy())
         e1.record(stream)
         torch.cuda.synchronize()
     barrier(pg)
@@ -432,26 +525,30 @@ def measure_path(R, W, torch, precision, args, rank, local, pg, trace):
     ctx.trace(False)
     iters = traj.iters[it0:]
     drift = traj.total_energy() - Etot0
+    all_geoms = list(traj.geoms)
 
-    # ---- timed region 2: end to end through the public API, host buffers
+    # ---- timed region 2: the same steps end to end through the public API,
+    # with the geometry uploaded from and the energy and forces read into host
+    # buffers, starting again from the state before region 1
+    traj.restore(start)
     xyz_pinned = torch.empty(mol.natoms * 3, dtype=torch.float64, pin_memory=True).numpy()
+    e2e_E = []
     barrier(pg)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        a = -traj.g / traj.m
-        traj.x = traj.x + traj.v * traj.dt + 0.5 * a * traj.dt ** 2
-        xyz_pinned[:] = traj.x.reshape(-1)
+        x = traj.next_geometry()
+        xyz_pinned[:] = x.reshape(-1)
         ctx.update_geometry(xyz_pinned.reshape(-1, 3))
         out = ctx.scf(guess=2, outputs=False)
-        g_new = ctx.gradient()
-        traj.v = traj.v + 0.5 * (a - g_new / traj.m) * traj.dt
-        traj.g, traj.E = g_new, out["energy"]
+        traj.finish(x, out["energy"], ctx.gradient())
+        e2e_E.append(out["energy"])
     torch.cuda.synchronize()
     e2e_s = allreduce_max(pg, time.perf_counter() - t0, local)
     barrier(pg)
     out = dict(world=world, ms_max=ms_max, launches=launches, stats=stats, iters=iters, drift=drift,
-               e2e_s=e2e_s, clocks=clk.summary(), energies=energies, natoms=mol.natoms)
+               e2e_s=e2e_s, clocks=clk.summary(), energies=energies, grads=grads, natoms=mol.natoms,
+               all_geoms=all_geoms, e2e_replay_dE=float(np.max(np.abs(np.array(e2e_E) - np.array(energies)))))
     ctx.close()
     return out
 

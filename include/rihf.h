@@ -237,7 +237,11 @@ int rihf_eigh(int n, const double* A, double* W, double* V, int device);
    The first call on each device resolves the array's device address (make it
    before any stream capture).  All calls share the array: calls whose work
    overlaps on the GPU (different streams or host threads) race and must be
-   serialised by the caller.  Errors: INVALID_ARG, CUDA. */
+   serialised by the caller.  The return code covers argument checks and
+   launch errors only: the call does not wait for the GPU, so a Jacobi pass
+   that stops at its sweep limit before converging is not reported (the FP64
+   refinement still runs on its vectors); a caller that needs a guarantee
+   checks the residual A V - V diag(W) itself.  Errors: INVALID_ARG, CUDA. */
 int rihf_eigh_noalloc(int n, const double* A, double* W, double* V, void* stream);
 
 /* C = A B^T on the tensor cores with FP64-class accuracy (the engine of the

@@ -214,8 +214,10 @@ def hf4c_energy(sysm, C_guess=None, **kw):
     return r
 
 
-def rihf_gradient_terms(sysm, res):
-    """dE/dR (natoms, 3) by Eq. rihf_gradient, and its pieces."""
+def rihf_gradient_terms(sysm, res, atoms=None):
+    """dE/dR (natoms, 3) by Eq. rihf_gradient, and its pieces.  With `atoms`
+    (a list of atom indices) only those atoms' rows are evaluated; the others
+    stay zero."""
     nocc = sysm.nocc
     Ct = np.sqrt(2.0) * res.C[:, :nocc]
     D = Ct @ Ct.T
@@ -232,7 +234,7 @@ def rihf_gradient_terms(sysm, res):
     natoms = len(sysm.Z)
     g1, gS, g3, g2 = (np.zeros((natoms, 3)) for _ in range(4))
     tb, ta = sysm.bas, sysm.aux
-    for a in range(natoms):
+    for a in range(natoms) if atoms is None else atoms:
         for d in range(3):
             dT = tb.to_ao2(I.one_electron(1, tb.cb, datom=a, ddim=d))
             dV = tb.to_ao2(I.one_electron(2, tb.cb, sysm.Z, sysm.xyz, datom=a, ddim=d))

@@ -22,12 +22,13 @@ namespace {
 
 // Largest matrix order the fixed workspace supports.
 constexpr int kNoAllocMaxN = 256;
-// Eigen-decomposition workspace for n = kNoAllocMaxN (see eig_workspace) and
-// the split-K partial sums of its GEMMs (8 n^2 doubles), plus a small tail for
-// the error flag.
-constexpr size_t kEigWs = ((size_t)kNoAllocMaxN * kNoAllocMaxN * 2 + kNoAllocMaxN + 1) / 2 +
-                          6 * (size_t)kNoAllocMaxN * kNoAllocMaxN + 2 * kNoAllocMaxN + 8;
+// Eigen-decomposition workspace for n = kNoAllocMaxN and the split-K partial
+// sums of its GEMMs (8 n^2 doubles), plus a small tail for the error flag.
+constexpr size_t kEigWs = eig_workspace(kNoAllocMaxN);
 constexpr size_t kWork = 8 * (size_t)kNoAllocMaxN * kNoAllocMaxN;
+// every order the entry point accepts fits: the workspace grows with n
+static_assert(eig_workspace(kNoAllocMaxN - 1) <= kEigWs && eig_workspace(kNoAllocMaxN) <= kEigWs,
+              "fixed eigensolver workspace smaller than eig_workspace(kNoAllocMaxN)");
 constexpr size_t kScratch = kEigWs + kWork + 64;
 
 static __device__ __align__(256) double g_eigh_scratch[kScratch];

@@ -1127,11 +1127,6 @@ __global__ void i_minus_kernel(double* R, int n) {   // R <- I - R
   }
 }
 
-size_t eig_workspace(int n) {
-  int m = n + (n & 1);
-  size_t f32 = (size_t)m * m + (size_t)n * m + m;       // floats
-  return (f32 + 1) / 2 + 6 * (size_t)n * n + 2 * n + 8;  // doubles
-}
 
 static int elem_blocks(const LaCtx& la, long long n) {
   return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 8LL * la.sms));

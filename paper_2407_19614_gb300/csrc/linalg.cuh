@@ -110,8 +110,12 @@ void trsm_lower(const LaCtx& la, const double* L, int n, double* X, long long nc
 // Symmetric eigen-decomposition of an n x n FP64 matrix A (row-major):
 // W (n, ascending) and V (n x n, column k = eigenvector k).  FP32 parallel
 // Jacobi in one CTA, then Ogita-Aishima refinement in FP64 (`refine` steps).
-// ws must hold eig_workspace(n) doubles.
-size_t eig_workspace(int n);
+// ws must hold eig_workspace(n) doubles: the FP32 Jacobi copies (A, V, W;
+// even order m), then six n x n FP64 refinement matrices and 2n + 8 scalars.
+constexpr size_t eig_workspace(int n) {
+  return ((size_t)(n + (n & 1)) * (n + (n & 1)) + (size_t)n * (n + (n & 1)) + (n + (n & 1)) + 1) / 2 +
+         6 * (size_t)n * n + 2 * (size_t)n + 8;
+}
 // skip_jacobi: start the refinement from Vguess directly (late SCF iterations).
 // max_sweeps caps the FP32 Jacobi sweeps and ns_steps the Newton-Schulz
 // re-orthonormalisation steps after the refinement (early SCF iterations need

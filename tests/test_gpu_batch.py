@@ -72,3 +72,28 @@ def test_cuda_graph_replay_matches_eager(precision):
     a, b = res
     assert abs(a[0] - b[0]) <= 1e-9 and abs(a[1] - b[1]) <= 1e-9
     assert np.abs(a[4] - b[4]).max() <= 1e-8
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_step_against_the_oracle(precision):
+    """Every molecule of a batch step against the FP64 CPU oracle at its new
+    geometry: FP64 within 1e-9 Eh / 1e-8 Eh/bohr, mixed within 1e-6 / 1e-5."""
+    import copy
+
+    from oracle import rihf as O
+    R = _R()
+    mols = MOLS[:3]
+    ctxs = [R.Context(m, precision=precision, **CONV) for m in mols]
+    for c in ctxs:
+        c.scf(guess=0, outputs=False)
+    xs = [_displaced(m, 10 + i) for i, m in enumerate(mols)]
+    E, G, it = R.batch_step(ctxs, xs, guess=2)
+    tol_e, tol_f = (1e-9, 1e-8) if precision == 0 else (1e-6, 1e-5)
+    for i, (m, x) in enumerate(zip(mols, xs)):
+        mk = copy.copy(m)
+        mk.xyz = x
+        s = O.System(mk)
+        r = O.rihf_energy(s, conv_e=1e-12, conv_diis=1e-10)
+        g = O.rihf_gradient_terms(s, r)
+        assert abs(E[i] - r.E) <= tol_e, (i, E[i] - r.E)
+        assert np.abs(G[i] - g.grad).max() <= tol_f, i

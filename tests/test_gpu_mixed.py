@@ -103,3 +103,48 @@ def test_tensor_core_fit_matches_fp64_fit():
     scale = np.abs(b64).max()
     print("\nmax |B_tc - B_fp64| = %.3e (max |B| = %.3e)" % (d, scale))
     assert d <= 1e-10 * scale
+
+
+def _k_digit_bound(B, Co, digits):
+    """Bound of |K_tc - K| for K = -sum_P (B^P C)(B^P C)^T built as on the
+    tensor cores: H = B C~ (C~ = sqrt(2) C_occ) from `digits` balanced 8-bit
+    digits of the rows of B and of C~ (every element keeps 7 + 8(digits - 1)
+    bits below its row's largest exponent; the dropped digit pairs weigh less
+    than that, constant 8 as for the plain GEMM), then K = -1/2 H H^T from
+    digits of H's rows with the same rule over the whole (P, i) axis.  First
+    order in the two errors."""
+    naux, n, _ = B.shape
+    bits = min(7 + 8 * (digits - 1), 55)
+    u = 8.0 * 2.0 ** (-bits)
+    Ct = np.sqrt(2.0) * Co
+    H = np.einsum("pmn,ni->mpi", B, Ct).reshape(n, -1)         # rows mu, columns (P, i)
+    bmax = np.abs(B).max(axis=2)                                 # max over nu of row (P, mu)
+    cmax = np.abs(Ct).max(axis=0)                                # max over nu of column i of C~
+    dH = u * n * np.einsum("pm,i->mpi", bmax, cmax).reshape(n, -1)
+    hmax = np.abs(H).max(axis=1)
+    prop = np.abs(H) @ dH.T
+    return 0.5 * (prop + prop.T + u * H.shape[1] * np.outer(hmax, hmax))
+
+
+@pytest.mark.parametrize("digits", [5, 6, 7])
+def test_mixed_exchange_elementwise_per_digit_count(digits):
+    """One tensor-core RI-K build (Eqs. k_ri_2 and tp) from the oracle's
+    converged orbitals, element by element against the oracle's FP64 K of the
+    same orbitals, inside the digit bound plus the FP64 fit's own 1e-11."""
+    R = _R()
+    mol = W.water_n(2, 0)
+    s = O.System(mol)
+    r = O.rihf_energy(s, conv_e=1e-12, conv_diis=1e-9)
+    L, B = O.cholesky_fit(s.A, s.T3)
+    Co = r.C[:, : s.nocc]
+    Kref = O.exchange_ri(B, Co)
+    ctx = R.Context(mol, precision=R.PRECISION_MIXED, mixed_digits=digits, max_iter=1, conv_e=1e-14,
+                    conv_diis=1e-14)
+    ctx.scf(guess=1, C_guess=r.C, outputs=False, allow_unconverged=True)
+    assert ctx.scf_stats()["tc_builds"] == 1
+    K = ctx.matrix("K")
+    err = np.abs(K - Kref)
+    bound = _k_digit_bound(B, Co, digits) + 1e-11 * max(1.0, np.abs(Kref).max())
+    print("\n%d digits: max |K_tc - K| = %.3e, min slack %.3e" % (digits, err.max(), (bound - err).min()))
+    assert np.all(err <= bound)
+    assert np.abs(K - K.T).max() == 0.0

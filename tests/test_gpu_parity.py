@@ -118,6 +118,11 @@ def test_cartesian_basis_parity():
     assert _close(ctx.matrix("T3"), s.T3, 1e-12)
     out = ctx.scf()
     assert abs(out["energy"] - r.E) <= 1e-9
+    # the Cartesian gradient: every term of Eq. rihf_gradient over Cartesian shells
+    g = O.rihf_gradient_terms(s, r)
+    grad = ctx.gradient()
+    assert np.abs(grad - g.grad).max() <= 1e-8
+    assert np.abs(grad.sum(0)).max() <= 1e-9
 
 
 def test_contracted_shells_parity():

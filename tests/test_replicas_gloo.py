@@ -64,8 +64,8 @@ def _json_lines(text):
 
 def test_reference_arm_single_process():
     import bench
-    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "0", "--ref-molecule", "monomer"], capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = _json_lines(out.stdout)
     assert len(lines) == 1
@@ -74,13 +74,17 @@ def test_reference_arm_single_process():
     assert d["value"] > 0 and d["higher_is_better"] is True and d["dtype"] == "f64"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # whole steps were timed and the line says how many; its time per step and
+    # that count fit the run's own wall clock
+    assert d["steps_timed"] >= 1 and d["steps_timed"] <= d["steps"]
+    assert "whole steps timed" in d["cpu_baseline"]["sample"]
 
 
 def test_reference_arm_under_torchrun_prints_once():
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
            "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"), "--impl", "reference",
-           "--gpus", "2", "--steps", "1", "--warmup", "0"]
+           "--gpus", "2", "--steps", "1", "--warmup", "0", "--ref-molecule", "monomer"]
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = _json_lines(out.stdout)

@@ -34,7 +34,7 @@ def test_noalloc_matches_allocating_eigh_twice():
     torch = pytest.importorskip("torch")
     from paper_2407_19614_gb300 import rihf as R
     R.load()
-    for n, seed in [(200, 1), (37, 2)]:     # second call reuses the shared workspace
+    for n, seed in [(200, 1), (37, 2), (256, 3)]:   # later calls reuse the shared workspace; 256 is the limit
         A = _sym(n, seed)
         rc, W, V = _noalloc(R, torch, A)
         assert rc == 0
@@ -56,3 +56,26 @@ def test_noalloc_rejects_orders_beyond_its_workspace():
     d = torch.zeros((n, n), dtype=torch.float64, device="cuda")
     w = torch.zeros(n, dtype=torch.float64, device="cuda")
     assert R.eigh_noalloc(n, d.data_ptr(), w.data_ptr(), d.data_ptr(), 0) == -1
+
+
+def test_noalloc_allocates_no_device_memory():
+    """After a first call (which resolves the workspace address), further calls,
+    also on a non-default stream, leave the device's free memory unchanged."""
+    torch = pytest.importorskip("torch")
+    from paper_2407_19614_gb300 import rihf as R
+    R.load()
+    n = 128
+    A = _sym(n, 4)
+    dA = torch.tensor(A, dtype=torch.float64, device="cuda")
+    dW = torch.empty(n, dtype=torch.float64, device="cuda")
+    dV = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    assert R.eigh_noalloc(n, dA.data_ptr(), dW.data_ptr(), dV.data_ptr(), side.cuda_stream) == 0
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for stream in (side.cuda_stream, torch.cuda.current_stream().cuda_stream):
+        assert R.eigh_noalloc(n, dA.data_ptr(), dW.data_ptr(), dV.data_ptr(), stream) == 0
+        torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    Wr, _ = R.eigh(A)
+    assert np.abs(dW.cpu().numpy() - Wr).max() <= 1e-12 * np.abs(Wr).max()
