@@ -32,17 +32,23 @@ __device__ inline double warp_sum(double v) {
 struct DerivPlan {
   int emin, emax, L;
   int fm, vrr, etr, acc0, accA, accB, ycart, t1, t2, hrr, half, total;
-  __device__ __host__ DerivPlan(int la, int lb, int lc) {
+  // mirror: the transfer region also holds the mirrored recursion's levels
+  __device__ __host__ DerivPlan(int la, int lb, int lc, bool mirror = false) {
     emin = la > 0 ? la - 1 : 0;
     emax = la + lb + 1;
     L = emax + lc;
     EtrShape sh{lc, emin, emax};
     int accsz = acc_size(emin, emax, lc);
     int nabc = ncart(la) * ncart(lb) * ncart(lc);
+    int etr_n = lc > 0 ? sh.total() : 0;
+    if (mirror) {
+      const int m = EtrShape{emax, lc, lc}.total();
+      if (m > etr_n) etr_n = m;
+    }
     fm = 0;
     vrr = kFmRegion;
     etr = vrr + vrr_size(L);
-    acc0 = etr + (lc > 0 ? sh.total() : 0);
+    acc0 = etr + etr_n;
     accA = acc0 + accsz;
     accB = accA + accsz;
     ycart = accB + accsz;
@@ -186,29 +192,34 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
     long long task = warp_next<W>(counter, lane);
     if (task >= ntask) break;
     const int2 tk = tasks[task];
-    int ip = tk.x, sc = tk.y;
+    const bool mir = tk.y < 0;   // marked task: triples with p > q run mirrored (mirror_prim3)
+    int ip = tk.x, sc = mir ? ~tk.y : tk.y;
     int sa = pairs[ip].a, sb = pairs[ip].b;
     if (prim.l[sa] < prim.l[sb]) { int t = sa; sa = sb; sb = t; }   // Y is symmetric in mu, nu
     int ata = prim.atom[sa], atb = prim.atom[sb], atc = aux.atom[sc];
     if (ata == atb && atb == atc) continue;   // one-centre: derivative sums to zero
     int la = prim.l[sa], lb = prim.l[sb], lc = aux.l[sc];
-    DerivPlan pl(la, lb, lc);
+    DerivPlan pl(la, lb, lc, mir);
     double* Fm = smem + pl.fm;
     double* vrr = smem + pl.vrr;
     double* etr = smem + pl.etr;
     int accsz = acc_size(pl.emin, pl.emax, lc);
     const PairPrim* pr = ptab.pp + ptab.off[ip];
     const int nab = prim.nprim[sa] * prim.nprim[sb];
-    // one primitive triple and a ket above s: the last electron-transfer level
-    // is the (unweighted) accumulator, read in place; the derivative weights
-    // 2 alpha and 2 beta scale the contracted sums instead
-    const bool single = nab == 1 && aux.nprim[sc] == 1 && lc > 0;
-    if (!single)
+    // one primitive triple: the derivative weights 2 alpha and 2 beta scale the
+    // contractions instead of weighted sums; a forward triple with a ket above
+    // s leaves its final values in place as the last transfer level, a
+    // mirrored one stores them once into acc0
+    const bool one = nab == 1 && aux.nprim[sc] == 1;
+    const bool one_mir = one && mir && pr[0].p > aux.exps[aux.pstart[sc]];
+    const bool single = one && !one_mir && lc > 0;
+    if (!single && !one_mir)
       for (int i = lane; i < 3 * accsz; i += W) smem[pl.acc0 + i] = 0.0;
     const double* A = prim.xyz + 3 * sa;
     const double* B = prim.xyz + 3 * sb;
     const double* C = aux.xyz + 3 * sc;
     EtrShape sh{lc, pl.emin, pl.emax};
+    const EtrShape shm{pl.emax, lc, lc};
     const double ABv[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
     for (int ab = 0; ab < nab; ++ab) {
       const PairPrim q = pr[ab];
@@ -217,6 +228,19 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
         Prim3 t = make_prim3_pp(q, aux.exps[ic], aux.iexps[ic], aux.coefs[ic], C, ABv);
         for (int m = lane; m <= pl.L; m += W) Fm[m] = boys_eval(m, t.T, boys);
         __syncwarp(lane_group_mask<W>());
+        if (mir && t.p > t.q) {
+          const Prim3 tm = mirror_prim3(t);
+          warp_vrr<W>(vrr, pl.L, tm, Fm, lane);
+          warp_etr<W>(vrr, pl.L, etr, shm, tm, Fm, lane);
+          if (one_mir) {
+            warp_acc_mirror<W, true>(vrr, pl.L, etr, shm, pl.emin, pl.emax, lc, 1.0, smem + pl.acc0, lane);
+          } else {
+            warp_acc_mirror<W>(vrr, pl.L, etr, shm, pl.emin, pl.emax, lc, 1.0, smem + pl.acc0, lane);
+            warp_acc_mirror<W>(vrr, pl.L, etr, shm, pl.emin, pl.emax, lc, 2.0 * q.alpha, smem + pl.accA, lane);
+            warp_acc_mirror<W>(vrr, pl.L, etr, shm, pl.emin, pl.emax, lc, 2.0 * q.beta, smem + pl.accB, lane);
+          }
+          continue;
+        }
         warp_vrr<W>(vrr, pl.L, t, Fm, lane);
         warp_etr<W>(vrr, pl.L, etr, sh, t, Fm, lane);
         if (!single) {
@@ -234,8 +258,8 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
                         smem + pl.t1, smem + pl.t2, smem + pl.ycart, lane);
     double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
     double g[6];
-    if (single) {
-      const double* lvl = etr + sh.level_off(lc);
+    if (single || one_mir) {
+      const double* lvl = single ? etr + sh.level_off(lc) : smem + pl.acc0;
       warp_deriv_contract<W>(pl, smem, lvl, lvl, lvl, 2.0 * pr[0].alpha, 2.0 * pr[0].beta, la, lb, lc, AB, lane, g);
     } else {
       warp_deriv_contract<W>(pl, smem, smem + pl.acc0, smem + pl.accA, smem + pl.accB, 1.0, 1.0, la, lb, lc, AB,
@@ -278,10 +302,14 @@ __global__ void __launch_bounds__(32) grad_eri2_kernel(DevShells aux, const doub
     while ((long long)sa * (sa + 1) / 2 > task) --sa;
     while ((long long)(sa + 1) * (sa + 2) / 2 <= task) ++sa;
     int sc = (int)(task - (long long)sa * (sa + 1) / 2);
+    if (aux.atom[sa] == aux.atom[sc]) continue;
+    if ((int)((small_mask >> (8 * aux.l[sa] + aux.l[sc])) & 1ull) != (G == 8 ? 1 : 0)) continue;
+    // the more diffuse shell is the bra, so the transfer's p/q factor is at
+    // most one (the small-class mask is symmetric, so the launch still holds
+    // the task; Z is symmetric, so the swapped block is read the same way)
+    if (aux_max_exp(aux, sa) > aux_max_exp(aux, sc)) { int t = sa; sa = sc; sc = t; }
     int ata = aux.atom[sa], atc = aux.atom[sc];
-    if (ata == atc) continue;
     int la = aux.l[sa], lc = aux.l[sc];
-    if ((int)((small_mask >> (8 * la + lc)) & 1ull) != (G == 8 ? 1 : 0)) continue;
     DerivPlan pl(la, 0, lc);
     double* Fm = smem + pl.fm;
     double* vrr = smem + pl.vrr;
@@ -515,8 +543,8 @@ static int deriv_smem(int max_la, int max_lb, int max_lc) {
   return (best + 8) * (int)sizeof(double);
 }
 
-int smem_grad_doubles(int la, int lb, int lc) {
-  DerivPlan p(la, lb, lc);
+int smem_grad_doubles(int la, int lb, int lc, bool mirror) {
+  DerivPlan p(la, lb, lc, mirror);
   return p.total + 8;
 }
 

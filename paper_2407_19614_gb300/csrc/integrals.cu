@@ -109,15 +109,22 @@ __device__ inline const double* warp_transform3(const double* cart, int la, int 
 }
 
 // Shared-memory plan for one (la, lb | lc) class, in doubles.
+// With `mirror` the transfer region also holds the mirrored recursion's levels
+// (tasks whose triples may need it, see mirror_prim3).
 struct Eri3Plan {
   int fm, vrr, etr, acc, hrr, half, t1, t2, total;
-  __device__ __host__ Eri3Plan(int la, int lb, int lc, int emin, int emax, int nacc) {
+  __device__ __host__ Eri3Plan(int la, int lb, int lc, int emin, int emax, int nacc, bool mirror = false) {
     int L = emax + lc;
     EtrShape sh{lc, emin, emax};
+    int etr_n = lc > 0 ? sh.total() : 0;
+    if (mirror) {
+      const int m = EtrShape{emax, lc, lc}.total();
+      if (m > etr_n) etr_n = m;
+    }
     fm = 0;
     vrr = fm + kFmRegion;
     etr = vrr + vrr_size(L);
-    acc = etr + (lc > 0 ? sh.total() : 0);
+    acc = etr + etr_n;
     int accsz = acc_size(emin, emax, lc);
     hrr = acc + nacc * accsz;
     half = hrr_scratch(la, lb, lc, emax) / 2;
@@ -130,8 +137,8 @@ struct Eri3Plan {
   }
 };
 
-int smem_eri3_doubles(int la, int lb, int lc) {
-  Eri3Plan p(la, lb, lc, la, la + lb, 1);
+int smem_eri3_doubles(int la, int lb, int lc, bool mirror) {
+  Eri3Plan p(la, lb, lc, la, la + lb, 1, mirror);
   return p.total;
 }
 
@@ -151,14 +158,17 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
     long long task = warp_next_task<W>(counter, lane);
     if (task >= ntask) break;
     const int2 tk = tasks[task];
-    int ip = tk.x, sc = tk.y;
+    // a negative auxiliary index marks a task whose triples with p > q take the
+    // mirrored recursion (see mirror_prim3)
+    const bool mir = tk.y < 0;
+    int ip = tk.x, sc = mir ? ~tk.y : tk.y;
     int sa = pairs[ip].a, sb = pairs[ip].b;
     // compute with la >= lb (cheaper HRR); the stored block keeps mu in pairs[ip].a
     const bool swp = prim.l[sa] < prim.l[sb];
     if (swp) { int t = sa; sa = sb; sb = t; }
     int la = prim.l[sa], lb = prim.l[sb], lc = aux.l[sc];
     int emin = la, emax = la + lb, L = emax + lc;
-    Eri3Plan pl(la, lb, lc, emin, emax, 1);
+    Eri3Plan pl(la, lb, lc, emin, emax, 1, mir);
     double* Fm = smem + pl.fm;
     double* vrr = smem + pl.vrr;
     double* etr = smem + pl.etr;
@@ -166,16 +176,22 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
     const int nab = prim.nprim[sa] * prim.nprim[sb];
     // one primitive triple and a ket above s: the last electron-transfer level
     // ([e][ke][kc], e in [emin, emax]) is the accumulator itself, read in place
-    const bool single = nab == 1 && aux.nprim[sc] == 1 && lc > 0;
+    const PairPrim* pr = ptab.pp + ptab.off[ip];
+    // one primitive triple: a mirrored one writes its final values into acc
+    // (no zeroing, no sums); a forward one with a ket above s leaves them in
+    // place as the last transfer level
+    const bool one = nab == 1 && aux.nprim[sc] == 1;
+    const bool one_mir = one && mir && pr[0].p > aux.exps[aux.pstart[sc]];
+    const bool single = one && !one_mir && lc > 0;
     int accsz = acc_size(emin, emax, lc);
-    if (!single)
+    if (!single && !one_mir)
       for (int i = lane; i < accsz; i += W) acc[i] = 0.0;
     const double* A = prim.xyz + 3 * sa;
     const double* B = prim.xyz + 3 * sb;
     const double* C = aux.xyz + 3 * sc;
     const double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
     EtrShape sh{lc, emin, emax};
-    const PairPrim* pr = ptab.pp + ptab.off[ip];
+    const EtrShape shm{emax, lc, lc};
     for (int ab = 0; ab < nab; ++ab) {
       const PairPrim q = pr[ab];
       for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
@@ -183,6 +199,14 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
         Prim3 t = make_prim3_pp(q, aux.exps[ic], aux.iexps[ic], aux.coefs[ic], C, AB);
         for (int m = lane; m <= L; m += W) Fm[m] = boys_eval(m, t.T, boys);
         __syncwarp(lane_group_mask<W>());
+        if (mir && t.p > t.q) {
+          const Prim3 tm = mirror_prim3(t);
+          warp_vrr<W>(vrr, L, tm, Fm, lane);
+          warp_etr<W>(vrr, L, etr, shm, tm, Fm, lane);
+          if (one_mir) warp_acc_mirror<W, true>(vrr, L, etr, shm, emin, emax, lc, 1.0, acc, lane);
+          else warp_acc_mirror<W>(vrr, L, etr, shm, emin, emax, lc, 1.0, acc, lane);
+          continue;
+        }
         warp_vrr<W>(vrr, L, t, Fm, lane);
         if (single) warp_etr<W>(vrr, L, etr, sh, t, Fm, lane);
         else warp_etr_accumulate<W>(vrr, L, etr, sh, t, 1.0, acc, Fm, lane);
@@ -228,8 +252,13 @@ __global__ void __launch_bounds__(32) eri2_kernel(DevShells aux, const double* _
     while ((long long)sa * (sa + 1) / 2 > task) --sa;
     while ((long long)(sa + 1) * (sa + 2) / 2 <= task) ++sa;
     int sc = (int)(task - (long long)sa * (sa + 1) / 2);
+    if ((int)((small_mask >> (8 * aux.l[sa] + aux.l[sc])) & 1ull) != (G == 8 ? 1 : 0)) continue;
+    // the more diffuse shell is the bra: the transfer then multiplies by p/q <= 1
+    // (with a compact bra and a diffuse ket of high l the factor p/q, raised
+    // to l, amplifies the bra recursion's rounding); the small-class mask is
+    // symmetric, and both triangles of A are written
+    if (aux_max_exp(aux, sa) > aux_max_exp(aux, sc)) { int t = sa; sa = sc; sc = t; }
     int la = aux.l[sa], lc = aux.l[sc];
-    if ((int)((small_mask >> (8 * la + lc)) & 1ull) != (G == 8 ? 1 : 0)) continue;
     int emin = la, emax = la, L = la + lc;
     Eri3Plan pl(la, 0, lc, emin, emax, 1);
     double* Fm = smem + pl.fm;
@@ -751,9 +780,11 @@ double hrr_flops(int la, int lb, int lc) {
 
 void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim, const std::vector<int>& nprim,
                 const std::vector<int>& patom, const std::vector<int>& laux, const std::vector<int>& naux_prim,
-                const std::vector<int>& aatom, const std::vector<int>& nf, double* eri3, double* grad3) {
+                const std::vector<int>& aatom, const std::vector<int>& nf, const std::vector<double>& pmax,
+                const std::vector<double>& qmin, double* eri3, double* grad3) {
   constexpr int nl = kMaxLPrim + 1, nc = kMaxLAux + 1;
   double e_prim[nl][nl][nc], e_task[nl][nl][nc], g_prim[nl][nl][nc], g_task[nl][nl][nc];
+  double e_mir[nl][nl][nc], g_mir[nl][nl][nc];   // per-triple recursion work of the mirrored path
   double e_acc[nl][nl][nc], g_acc[nl][nl][nc];   // accumulation passes (skipped by single-triple tasks with lc > 0)
   for (int la = 0; la < nl; ++la)
     for (int lb = 0; lb <= la; ++lb)
@@ -764,6 +795,7 @@ void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lpr
         {
           const int L = la + lb + lc;
           e_prim[la][lb][lc] = setup + 14.0 * (L + 1) + vrr_flops(L) + etr_flops(EtrShape{lc, la, la + lb});
+          e_mir[la][lb][lc] = setup + 14.0 * (L + 1) + vrr_flops(L) + etr_flops(EtrShape{la + lb, lc, lc});
           e_acc[la][lb][lc] = 2.0 * acc_size(la, la + lb, lc);
           e_task[la][lb][lc] = hrr_flops(la, lb, lc) +
                                2.0 * ((double)na * nb * fc * ncc + (double)na * fb * fc * nb + (double)fa * fb * fc * na);
@@ -771,6 +803,7 @@ void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lpr
         {
           const int emin = la > 0 ? la - 1 : 0, emax = la + lb + 1, L = emax + lc;
           g_prim[la][lb][lc] = setup + 14.0 * (L + 1) + vrr_flops(L) + etr_flops(EtrShape{lc, emin, emax});
+          g_mir[la][lb][lc] = setup + 14.0 * (L + 1) + vrr_flops(L) + etr_flops(EtrShape{emax, lc, lc});
           g_acc[la][lb][lc] = 6.0 * acc_size(emin, emax, lc);
           g_task[la][lb][lc] = 2.0 * ((double)fa * fb * ncc * fc + (double)fa * nb * ncc * fb + (double)na * nb * ncc * fa) +
                                hrr_flops(la + 1, lb, lc) + (la > 0 ? hrr_flops(la - 1, lb, lc) : 0.0) +
@@ -787,10 +820,16 @@ void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lpr
     for (int c = 0; c < (int)laux.size(); ++c) {
       const int lc = laux[c];
       const double np3 = npab * naux_prim[c];
-      const bool single = np3 == 1.0 && lc > 0;   // the kernels read the last transfer level in place
-      fe += np3 * e_prim[la][lb][lc] + e_task[la][lb][lc] + (single ? 0.0 : np3 * e_acc[la][lb][lc]);
+      // marked tasks run mirrored (counted so when their largest bra exponent
+      // sum exceeds the auxiliary exponent) and always accumulate
+      const bool mir = mirror_task(pmax[a] + pmax[b], qmin[c], lc);
+      // one triple: the kernels read the last transfer level in place, or
+      // (mirrored) store it once; either way no accumulation passes
+      const bool single = np3 == 1.0 && lc > 0;
+      fe += np3 * (mir ? e_mir : e_prim)[la][lb][lc] + e_task[la][lb][lc] + (single ? 0.0 : np3 * e_acc[la][lb][lc]);
       if (!(patom[a] == patom[b] && patom[b] == aatom[c]))
-        fg += np3 * g_prim[la][lb][lc] + g_task[la][lb][lc] + (single ? 6.0 : np3 * g_acc[la][lb][lc]);
+        fg += np3 * (mir ? g_mir : g_prim)[la][lb][lc] + g_task[la][lb][lc] +
+              (single ? 6.0 : np3 * g_acc[la][lb][lc]);
     }
   }
   *eri3 = fe;
@@ -801,24 +840,28 @@ void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lpr
 // group whose shared-memory bound covers both its integral and its derivative
 // class, so light classes run with many resident warps per SM.
 void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim,
-                       const std::vector<int>& laux, std::vector<std::vector<int2>>& tasks,
-                       std::vector<int>& smem_eri3, std::vector<int>& smem_grad) {
+                       const std::vector<int>& laux, const std::vector<double>& pmax, const std::vector<double>& qmin,
+                       std::vector<std::vector<int2>>& tasks, std::vector<int>& smem_eri3,
+                       std::vector<int>& smem_grad) {
   // group 0: tiny classes as 8-lane groups (4 tasks per warp); group 1: small
   // classes as 16-lane groups (2 tasks per warp, about 15 warps per SM); then
-  // about 17, 7 and at most 2 warps per SM (228 KB shared memory, 1 KB
-  // reserved per block)
-  const int limits[kTaskGroups] = {3584, 7168, 12 * 1024, 28 * 1024, 1 << 30};
+  // about 17, 7, 3, 1-2 and 1 warps per SM (228 KB shared memory, 1 KB
+  // reserved per block): the f and g classes of larger basis sets span 28 to
+  // 205 KB, and one bound for all of them would hold every such task to the
+  // residency of the largest
+  const int limits[kTaskGroups] = {3584, 7168, 12 * 1024, 28 * 1024, 56 * 1024, 112 * 1024, 1 << 30};
   constexpr int nl = kMaxLPrim + 1, nc = kMaxLAux + 1;
-  int se[nl][nl][nc], sg[nl][nl][nc], grp[nl][nl][nc];
-  for (int la = 0; la < nl; ++la)
-    for (int lb = 0; lb < nl; ++lb)
-      for (int lc = 0; lc < nc; ++lc) {
-        se[la][lb][lc] = smem_eri3_doubles(la, lb, lc) * (int)sizeof(double);
-        sg[la][lb][lc] = smem_grad_doubles(la, lb, lc) * (int)sizeof(double);
-        int need = std::max(se[la][lb][lc], sg[la][lb][lc]), g = 0;
-        while (g + 1 < kTaskGroups && need > limits[g]) ++g;
-        grp[la][lb][lc] = g;
-      }
+  int se[2][nl][nl][nc], sg[2][nl][nl][nc], grp[2][nl][nl][nc];   // [mirror][la][lb][lc]
+  for (int mi = 0; mi < 2; ++mi)
+    for (int la = 0; la < nl; ++la)
+      for (int lb = 0; lb < nl; ++lb)
+        for (int lc = 0; lc < nc; ++lc) {
+          se[mi][la][lb][lc] = smem_eri3_doubles(la, lb, lc, mi == 1) * (int)sizeof(double);
+          sg[mi][la][lb][lc] = smem_grad_doubles(la, lb, lc, mi == 1) * (int)sizeof(double);
+          int need = std::max(se[mi][la][lb][lc], sg[mi][la][lb][lc]), g = 0;
+          while (g + 1 < kTaskGroups && need > limits[g]) ++g;
+          grp[mi][la][lb][lc] = g;
+        }
   tasks.assign(kTaskGroups, {});
   smem_eri3.assign(kTaskGroups, 0);
   smem_grad.assign(kTaskGroups, 0);
@@ -826,21 +869,25 @@ void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<in
     for (int p = 0; p < (int)pairs.size(); ++p) {
       int la = lprim[pairs[p].a], lb = lprim[pairs[p].b];
       if (la < lb) std::swap(la, lb);
-      const int lc = laux[c], g = grp[la][lb][lc];
-      tasks[g].push_back(make_int2(p, c));
-      smem_eri3[g] = std::max(smem_eri3[g], se[la][lb][lc]);
-      smem_grad[g] = std::max(smem_grad[g], sg[la][lb][lc]);
+      const int lc = laux[c];
+      const int mi = mirror_task(pmax[pairs[p].a] + pmax[pairs[p].b], qmin[c], lc) ? 1 : 0;
+      const int g = grp[mi][la][lb][lc];
+      tasks[g].push_back(make_int2(p, mi ? ~c : c));
+      smem_eri3[g] = std::max(smem_eri3[g], se[mi][la][lb][lc]);
+      smem_grad[g] = std::max(smem_grad[g], sg[mi][la][lb][lc]);
     }
 }
 
 unsigned long long eri2_small_classes(int max_la, int* slice_doubles) {
   // the 3.5 KB working-set limit of the 8-lane 3-centre group, applied to
-  // both the (P|Q) integrals and their derivatives
+  // both the (P|Q) integrals and their derivatives, in both orders (the
+  // kernels may exchange bra and ket), so the mask is symmetric
   unsigned long long mask = 0;
   int slice = 0;
   for (int la = 0; la <= max_la; ++la)
     for (int lc = 0; lc <= max_la; ++lc) {
-      const int e = smem_eri3_doubles(la, 0, lc), g = smem_grad_doubles(la, 0, lc);
+      const int e = std::max(smem_eri3_doubles(la, 0, lc), smem_eri3_doubles(lc, 0, la));
+      const int g = std::max(smem_grad_doubles(la, 0, lc), smem_grad_doubles(lc, 0, la));
       if (std::max(e, g) * (int)sizeof(double) > 3584) continue;
       mask |= 1ull << (8 * la + lc);
       slice = std::max(slice, std::max(e, g));

@@ -54,14 +54,23 @@ void launch_pair_prims(const IntegralCtx& ic, const DevShells& prim, const Shell
 
 // Shared memory (doubles) one warp needs for a (la >= lb | lc) class of the
 // integral and of the derivative kernel.
-int smem_eri3_doubles(int la, int lb, int lc);
-int smem_grad_doubles(int la, int lb, int lc);
+int smem_eri3_doubles(int la, int lb, int lc, bool mirror = false);
+int smem_grad_doubles(int la, int lb, int lc, bool mirror = false);
+
+// Whether a (pair, auxiliary shell) task may take the mirrored recursion
+// (mirror_prim3): the forward transfer multiplies by p/q and by beta AB/q once
+// per unit of l_c, so with p > q and l_c >= 2 it loses digits to rounding --
+// measured against the oracle for an f/g auxiliary set, up to 1e-10 of the
+// largest integral already at p/q between 2 and 8.  A task is marked when its
+// largest bra exponent sum exceeds its smallest ket exponent; its triples with
+// p > q then run mirrored, where every factor is at most one (or |AB|).
+inline bool mirror_task(double pmax, double qmin, int lc) { return lc >= 2 && pmax > qmin; }
 // (P|Q) classes (bit 8 la + lc, la, lc <= max_la) run by 8-lane task groups,
 // and the shared-memory slice (doubles) one such group needs.
 unsigned long long eri2_small_classes(int max_la, int* slice_doubles);
 
 // (pair index, auxiliary shell) tasks of one shared-memory class group.
-constexpr int kTaskGroups = 5;
+constexpr int kTaskGroups = 7;
 struct TaskGroup {
   const int2* tasks = nullptr;
   long long ntask = 0;
@@ -70,9 +79,13 @@ struct TaskGroup {
 };
 // Lanes per task of class group g (group 0 holds the tiny classes).
 inline int task_group_width(int g) { return g == 0 ? 8 : g == 1 ? 16 : 32; }
+// pmax: largest primitive exponent per primary shell; qmin: smallest per
+// auxiliary shell (for mirror_task).  A marked task stores ~c as its auxiliary
+// index.
 void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim,
-                       const std::vector<int>& laux, std::vector<std::vector<int2>>& tasks,
-                       std::vector<int>& smem_eri3, std::vector<int>& smem_grad);
+                       const std::vector<int>& laux, const std::vector<double>& pmax, const std::vector<double>& qmin,
+                       std::vector<std::vector<int2>>& tasks, std::vector<int>& smem_eri3,
+                       std::vector<int>& smem_grad);
 
 // Algorithmic FP64 operation counts (an FMA counts two) of the 3-centre
 // integral and derivative kernels over all (pair, auxiliary shell) tasks, from
@@ -83,7 +96,8 @@ void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<in
 // are skipped by the derivative kernel and not counted.
 void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim, const std::vector<int>& nprim,
                 const std::vector<int>& patom, const std::vector<int>& laux, const std::vector<int>& naux_prim,
-                const std::vector<int>& aatom, const std::vector<int>& nf, double* eri3, double* grad3);
+                const std::vector<int>& aatom, const std::vector<int>& nf, const std::vector<double>& pmax,
+                const std::vector<double>& qmin, double* eri3, double* grad3);
 
 // Three-centre integrals T[P][mu][nu] = (mu nu|P) for the listed shell pairs
 // (mu in a, nu in b, a >= b; both triangles inside diagonal shell blocks).

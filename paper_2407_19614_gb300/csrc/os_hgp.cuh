@@ -61,6 +61,14 @@ __device__ inline double boys_eval(int m, double T, const double* __restrict__ t
   return f;
 }
 
+// Largest primitive exponent of shell sh of a device shell list.
+template <class Shells>
+__device__ inline double aux_max_exp(const Shells& b, int sh) {
+  double e = b.exps[b.pstart[sh]];
+  for (int k = 1; k < b.nprim[sh]; ++k) e = fmax(e, b.exps[b.pstart[sh] + k]);
+  return e;
+}
+
 // Decode component k of a Cartesian shell of angular momentum l.
 __host__ __device__ inline void cart_decode(int l, int k, int& lx, int& ly, int& lz) {
   int a = 0;
@@ -81,6 +89,7 @@ struct Prim3 {
   double inv2p, rp;       // 1/(2p), rho/p                  (vertical recurrence)
   double inv2q, poq;      // 1/(2q), p/q                    (electron transfer)
   double bqAB[3];         // beta AB_i / q                  (electron transfer)
+  double WQ[3];           // W - C                          (mirrored recursion)
 };
 
 // Shell-pair primitive data (a, b) with la >= lb, built once per geometry.
@@ -103,11 +112,15 @@ __device__ inline Prim3 make_prim3_pp(const PairPrim& q, double ga, double iga, 
   const double R2 = fma(CP0, CP0, fma(CP1, CP1, CP2 * CP2));
   const double r = rsqrt(q.p + ga);      // (p + gamma)^{-1/2}
   const double gi = ga * (r * r);        // gamma / (p + gamma)
+  const double pi = q.p * (r * r);       // p / (p + gamma)
   t.rho = q.p * gi;
   t.rp = gi;
   t.WP[0] = gi * CP0;
   t.WP[1] = gi * CP1;
   t.WP[2] = gi * CP2;
+  t.WQ[0] = -pi * CP0;
+  t.WQ[1] = -pi * CP1;
+  t.WQ[2] = -pi * CP2;
   t.T = t.rho * R2;
   t.pref = q.K * (cc * iga) * r;
   t.inv2p = 0.5 * q.inv_p;
@@ -151,6 +164,7 @@ __device__ inline Prim3 make_prim3(double al, const double* A, double be, const 
     double W = (p * P[i] + ga * C[i]) / pq;
     t.PA[i] = P[i] - A[i];
     t.WP[i] = W - P[i];
+    t.WQ[i] = W - C[i];
     R2pq += (P[i] - C[i]) * (P[i] - C[i]);
   }
   t.T = t.rho * R2pq;
@@ -185,7 +199,39 @@ __device__ inline Prim3 make_prim_point(double al, const double* A, double be, c
   t.inv2q = 0.0;
   t.poq = 0.0;
   t.bqAB[0] = t.bqAB[1] = t.bqAB[2] = 0.0;
+  t.WQ[0] = t.WQ[1] = t.WQ[2] = 0.0;
   return t;
+}
+
+// Mirrored recursion.  The transfer above moves the ket's angular momentum over
+// from the bra with the factor -p/q per unit; when the bra's exponent sum is
+// much larger than the ket's (a compact primary pair against a diffuse
+// auxiliary d, f or g function) that factor, raised to l_c, amplifies the
+// rounding of the bra recursion far beyond FP64 precision.  The same integrals
+// follow, with every factor bounded by one, from the Obara-Saika recursion on
+// the ket centre,
+//   [0|f+1_i]^(m) = WQ_i [0|f]^(m+1) + f_i/(2q) ([0|f-1_i]^(m) - rho/q [0|f-1_i]^(m+1))
+// (Q = C: a single auxiliary function), and the transfer in the other
+// direction (the same relation with bra and ket exchanged),
+//   [e+1_i|f] = e_i/(2p)[e-1_i|f] + f_i/(2p)[e|f-1_i] - q/p [e|f+1_i] - beta AB_i/p [e|f].
+// Both reuse warp_vrr and warp_etr with the roles of the triple exchanged:
+// mirror_prim3 gives the exchanged factors, EtrShape{emax, lc, lc} the levels
+// (bra angular momentum 1..emax, each over the ket range its successors need).
+__device__ inline Prim3 mirror_prim3(const Prim3& t) {
+  Prim3 m = t;
+  const double ip = 2.0 * t.inv2p, iq = 2.0 * t.inv2q;   // 1/p, 1/q
+  m.p = t.q;
+  m.q = t.p;
+  m.rp = t.rho * iq;       // rho/q
+  m.inv2p = t.inv2q;       // k/(2q): the ket recursion
+  m.inv2q = t.inv2p;       // k/(2p): the transfer to the bra
+  m.poq = t.q * ip;        // q/p
+  for (int i = 0; i < 3; ++i) {
+    m.PA[i] = 0.0;         // Q - C
+    m.WP[i] = t.WQ[i];
+    m.bqAB[i] = t.beta * t.AB[i] * ip;
+  }
+  return m;
 }
 
 // Lanes of one task group: W consecutive lanes of a warp (W = 32: the whole
@@ -367,6 +413,30 @@ __device__ inline void warp_etr(const double* vrr, int L, double* etr, const Etr
     }
     __syncwarp(lane_group_mask<W>());
   }
+}
+
+// acc[e][ke][kc] += w * [e|lc] for e in [emin, emax] from the mirrored tables of
+// shape EtrShape{emax, lc, lc} (level e holds [e|f] for f around lc; level 0 is
+// the m = 0 slice of the ket recursion).  Same accumulator layout as
+// warp_acc_level, so everything after the transfer is shared.
+// With Store the values are written (acc = w * value): a task of one primitive
+// triple needs no accumulation.
+template <int W = 32, bool Store = false>
+__device__ inline void warp_acc_mirror(const double* vrr, int L, const double* etr, const EtrShape& shm, int emin,
+                                       int emax, int lc, double w, double* acc, int lane) {
+  const int ncc = ncart(lc);
+  const int n = acc_size(emin, emax, lc);
+  for (int idx = lane; idx < n; idx += W) {
+    int r = idx / ncc, kc = idx - r * ncc;
+    int e = emin;
+    while (cart_offset(e + 1) - cart_offset(emin) <= r) ++e;
+    int ke = r - (cart_offset(e) - cart_offset(emin));
+    const double v = etr_get(vrr, L, etr, shm, e, lc, kc, ke);
+    if (Store) acc[idx] = v;
+    else acc[idx] += w * v;
+  }
+  (void)emax;
+  __syncwarp(lane_group_mask<W>());
 }
 
 template <int W = 32>

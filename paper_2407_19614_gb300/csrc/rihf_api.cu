@@ -631,9 +631,17 @@ static void refresh_tasks(rihf_ctx* c) {
   upload(c->d_pp_off, pair_prim_offsets(c->pairs_h, c->hp.nprim), c->stream);
   std::vector<std::vector<int2>> tasks;
   std::vector<int> se, sg;
-  build_task_groups(c->pairs_h, c->hp.l, c->ha.l, tasks, se, sg);
-  task_flops(c->pairs_h, c->hp.l, c->hp.nprim, c->hp.atom, c->ha.l, c->ha.nprim, c->ha.atom, c->nf_h, &c->flops_eri3,
-             &c->flops_grad3);
+  // largest primitive exponent per primary shell, smallest per auxiliary shell
+  std::vector<double> pmax(c->hp.nshell, 0.0), qmin(c->ha.nshell, 0.0);
+  for (int i = 0; i < c->hp.nshell; ++i)
+    for (int k = 0; k < c->hp.nprim[i]; ++k) pmax[i] = std::max(pmax[i], c->hp.exps[c->hp.pstart[i] + k]);
+  for (int i = 0; i < c->ha.nshell; ++i) {
+    qmin[i] = c->ha.exps[c->ha.pstart[i]];
+    for (int k = 1; k < c->ha.nprim[i]; ++k) qmin[i] = std::min(qmin[i], c->ha.exps[c->ha.pstart[i] + k]);
+  }
+  build_task_groups(c->pairs_h, c->hp.l, c->ha.l, pmax, qmin, tasks, se, sg);
+  task_flops(c->pairs_h, c->hp.l, c->hp.nprim, c->hp.atom, c->ha.l, c->ha.nprim, c->ha.atom, c->nf_h, pmax, qmin,
+             &c->flops_eri3, &c->flops_grad3);
   size_t off = 0;
   for (int g = 0; g < kTaskGroups; ++g) {
     c->groups[g].tasks = c->d_tasks + off;
