@@ -72,13 +72,16 @@ typedef struct {
                         /* once per precision variant and replayed as a CUDA graph        */
   int confirm_fp64;     /* mixed precision: 1 = convergence is confirmed on an FP64 Fock  */
                         /* build; 0 = on a 7-digit build (55-bit products per K block)   */
+  int aux_chunk;        /* auxiliary functions per chunk when the pair-packed fitted      */
+                        /* tensor is expanded for RI-K and the gradient; 0 = as many as   */
+                        /* the free device memory holds (all of them for small systems)  */
 } rihf_options;
 
 /* Fills *opt with the defaults: FP64, spherical, schwarz_tau 0 (no pair
    dropped; with ill-conditioned auxiliary metrics even pairs below 1e-14 move
    the energy by ~1e-6 Eh, see the screening tests), lindep_tau
    1e-8, conv_e 1e-10, conv_diis 1e-9, max_iter 100, diis_size 8,
-   mixed_digits 0, device 0, cuda_graphs 1, confirm_fp64 0.
+   mixed_digits 0, device 0, cuda_graphs 1, confirm_fp64 0, aux_chunk 0.
    Mixed precision (RIHF_PRECISION_MIXED): RI-K in the SCF iterations runs on
    the tensor cores from BF16 digit planes (see rihf_tc_dgemm) with 5, 6, then
    7 digits as the SCF error falls; the fit B = L^{-1} T and the gradient's

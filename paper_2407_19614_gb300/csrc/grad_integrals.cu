@@ -64,20 +64,26 @@ struct DerivPlan {
   }
 };
 
+// Strided source of warp_back_transform: element (k, a, b) at p[k sP + a sM + b sN].
+struct StridedSrc {
+  const double* p;
+  long long sP, sM, sN;
+  __device__ double operator()(int k, int a, int b) const { return p[k * sP + a * sM + b * sN]; }
+};
+
 // Ycart[ka][kb][kc] = sum tra[sa][ka] trb[sb][kb] trc[sc][kc] Y(sa, sb, sc), with
-// Y(sa, sb, sc) = src[(sc*sP) + (sa*sM) + sb*sN] (strides in doubles).
-template <int W = 32>
-__device__ inline void warp_back_transform(const double* src, long long sP, long long sM, long long sN, int la,
-                                           int lb, int lc, const double* tra, const double* trb, const double* trc,
-                                           int nfa, int nfb, int nfc, double* t1, double* t2, double* out,
-                                           int lane) {
+// Y(sa, sb, sc) = src(sc, sa, sb) (an accessor: strided or pair-packed).
+template <int W = 32, class Src>
+__device__ inline void warp_back_transform(const Src& src, int la, int lb, int lc, const double* tra,
+                                           const double* trb, const double* trc, int nfa, int nfb, int nfc,
+                                           double* t1, double* t2, double* out, int lane) {
   const int na = ncart(la), nb = ncart(lb), nc = ncart(lc);
   // t1[sa][sb][kc] = sum_sc trc[sc][kc] Y
   for (int idx = lane; idx < nfa * nfb * nc; idx += W) {
     int kc = idx % nc, r = idx / nc;
     int sb = r % nfb, sa = r / nfb;
     double v = 0.0;
-    for (int sc = 0; sc < nfc; ++sc) v += trc[sc * kTrStride + kc] * src[sc * sP + sa * sM + sb * sN];
+    for (int sc = 0; sc < nfc; ++sc) v += trc[sc * kTrStride + kc] * src(sc, sa, sb);
     t1[idx] = v;
   }
   __syncwarp(lane_group_mask<W>());
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
   const int lane = threadIdx.x % W;
   double* smem = smem_all + (threadIdx.x / W) * slice;   // this task group's slice
   const int N = prim.nfunc;
-  const long long N2 = (long long)N * N;
+  const long long Npp = (long long)N * (N + 1) / 2;
   for (;;) {
     long long task = warp_next<W>(counter, lane);
     if (task >= ntask) break;
@@ -250,10 +256,15 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
         }
       }
     }
-    // Y block -> Cartesian
+    // Y block -> Cartesian (Y pair-packed per auxiliary function, symmetric)
     int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
-    const double* src = Y + (long long)aux.ao[sc] * N2 + (long long)prim.ao[sa] * N + prim.ao[sb];
-    warp_back_transform<W>(src, N2, N, 1, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
+    const double* Yc = Y + (long long)aux.ao[sc] * Npp;
+    const int mu0 = prim.ao[sa], nu0 = prim.ao[sb];
+    auto ysrc = [&](int k, int a, int b) -> double {
+      const long long r = mu0 + a, q = nu0 + b;
+      return r >= q ? Yc[k * Npp + r * (r + 1) / 2 + q] : Yc[k * Npp + q * (q + 1) / 2 + r];
+    };
+    warp_back_transform<W>(ysrc, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
                         prim.tr + lb * kTrStride * kTrStride, aux.tr + lc * kTrStride * kTrStride, nfa, nfb, nfc,
                         smem + pl.t1, smem + pl.t2, smem + pl.ycart, lane);
     double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
@@ -333,9 +344,10 @@ __global__ void __launch_bounds__(32) grad_eri2_kernel(DevShells aux, const doub
       }
     // Z block (P in sa, Q in sc) -> Cartesian with a unit s "b" function
     int nfa = aux.nf[la], nfc = aux.nf[lc];
-    const double* src = Z + (long long)aux.ao[sa] * NA + aux.ao[sc];
-    // layout Y(sa, sb=0, sc) = src[sa*NA + sc]
-    warp_back_transform<G>(src, 1, NA, 0, la, 0, lc, aux.tr + la * kTrStride * kTrStride, one_tr,
+    const double* zsrc = Z + (long long)aux.ao[sa] * NA + aux.ao[sc];
+    // layout Y(sa, sb=0, sc) = Z[P0 + sa][Q0 + sc]
+    auto src = [&](int k, int a, int b) -> double { return zsrc[(long long)a * NA + k + 0 * b]; };
+    warp_back_transform<G>(src, la, 0, lc, aux.tr + la * kTrStride * kTrStride, one_tr,
                         aux.tr + lc * kTrStride * kTrStride, nfa, 1, nfc, smem + pl.t1, smem + pl.t2,
                         smem + pl.ycart, lane);
     double AB[3] = {0.0, 0.0, 0.0};
@@ -433,9 +445,9 @@ __global__ void __launch_bounds__(32) grad_one_electron_kernel(DevShells prim, i
       double* Dc = smem + pl.ycart;
       double* Wc = smem + pl.total;   // past the plan (the HRR region holds t1/t2)
       double* s1d = Wc + 128;         // 3 x 64
-      warp_back_transform<G>(D + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa,
+      warp_back_transform<G>(StridedSrc{D + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1}, la, lb, 0, tra, trb, one_tr, nfa,
                           nfb, 1, smem + pl.t1, smem + pl.t2, Dc, lane);
-      warp_back_transform<G>(W + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa,
+      warp_back_transform<G>(StridedSrc{W + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1}, la, lb, 0, tra, trb, one_tr, nfa,
                           nfb, 1, smem + pl.t1, smem + pl.t2, Wc, lane);
       double gT[3] = {0, 0, 0}, gS[3] = {0, 0, 0};
       for (int pa = 0; pa < prim.nprim[sa]; ++pa)
@@ -502,7 +514,7 @@ __global__ void __launch_bounds__(32) grad_one_electron_kernel(DevShells prim, i
         warp_acc_level<G>(vrr, pl.L, nullptr, sh, 2.0 * al * w, smem + pl.accA, lane);
         warp_acc_level<G>(vrr, pl.L, nullptr, sh, 2.0 * be * w, smem + pl.accB, lane);
       }
-    warp_back_transform<G>(D + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1, la, lb, 0, tra, trb, one_tr, nfa, nfb,
+    warp_back_transform<G>(StridedSrc{D + (long long)prim.ao[sa] * N + prim.ao[sb], 0, N, 1}, la, lb, 0, tra, trb, one_tr, nfa, nfb,
                         1, smem + pl.t1, smem + pl.t2, smem + pl.ycart, lane);
     double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
     double g[6];

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
   const int lane = threadIdx.x % W;
   double* smem = smem_all + (threadIdx.x / W) * slice;   // this task group's slice
   const int N = prim.nfunc;
-  const size_t N2 = (size_t)N * N;
+  const size_t Npp = (size_t)N * (N + 1) / 2;
   for (;;) {
     long long task = warp_next_task<W>(counter, lane);
     if (task >= ntask) break;
@@ -218,13 +218,18 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
     const double* out = warp_transform3<W>(cart, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
                                         prim.tr + lb * kTrStride * kTrStride, aux.tr + lc * kTrStride * kTrStride,
                                         nfa, nfb, nfc, smem + pl.t1, smem + pl.t2, lane);
+    // pair-packed store: row = the function of pairs[ip].a (the larger shell
+    // index, so the larger function index), column = that of pairs[ip].b;
+    // inside a diagonal shell block only row >= column
     const int mu0 = prim.ao[sa], nu0 = prim.ao[sb], P0 = aux.ao[sc];
+    const bool diag = pairs[ip].a == pairs[ip].b;
     const int n = nfa * nfb * nfc;
     for (int idx = lane; idx < n; idx += W) {
       int sbb = idx % nfb, r = idx / nfb;
       int saa = r % nfa, scc = r / nfa;
-      size_t dst = swp ? (size_t)(nu0 + sbb) * N + mu0 + saa : (size_t)(mu0 + saa) * N + nu0 + sbb;
-      T[(size_t)(P0 + scc) * N2 + dst] = out[(saa * nfb + sbb) * nfc + scc];
+      const long long row = swp ? nu0 + sbb : mu0 + saa, col = swp ? mu0 + saa : nu0 + sbb;
+      if (diag && row < col) continue;
+      T[(size_t)(P0 + scc) * Npp + row * (row + 1) / 2 + col] = out[(saa * nfb + sbb) * nfc + scc];
     }
     __syncwarp(lane_group_mask<W>());
   }

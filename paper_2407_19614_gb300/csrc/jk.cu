@@ -226,4 +226,61 @@ void outer_fill(const LaCtx& la, const double* c, int naux, const double* D, lon
   if (la.launches) *la.launches += 1;
 }
 
+// ------------------------------------------------------------ packed storage
+//
+// One CTA per (matrix, row mu) at a time; its threads run along the row, so the
+// packed row segment nu <= mu (contiguous) and the unpacked row are both
+// accessed with coalesced loads and stores, and no index needs a square root.
+
+__global__ void __launch_bounds__(256) pack_sym_batch_kernel(const double* __restrict__ A, int nmat, int N, double w,
+                                                             double* __restrict__ Ap, long long ldp) {
+  const long long rows = (long long)nmat * N, n2 = (long long)N * N;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const long long m = r / N;
+    const int mu = (int)(r - m * N);
+    const double* src = A + m * n2 + (long long)mu * N;
+    double* dst = Ap + m * ldp + (long long)mu * (mu + 1) / 2;
+    for (int nu = threadIdx.x; nu <= mu; nu += blockDim.x) dst[nu] = src[nu] * (nu == mu ? 1.0 : w);
+  }
+}
+
+void pack_sym_batch(const LaCtx& la, const double* A, int nmat, int N, double* Ap, long long ldp) {
+  const long long rows = (long long)nmat * N;
+  pack_sym_batch_kernel<<<(int)std::max<long long>(1, std::min<long long>(rows, 32LL * la.sms)), 256, 0, la.stream>>>(
+      A, nmat, N, 1.0, Ap, ldp);
+  RIHF_LAUNCH_CHECK();
+  if (la.launches) *la.launches += 1;
+}
+
+void pack_sym(const LaCtx& la, const double* A, int N, double w, double* Ap) {
+  pack_sym_batch_kernel<<<std::max(1, std::min(N, 32 * la.sms)), 256, 0, la.stream>>>(A, 1, N, w, Ap, 0);
+  RIHF_LAUNCH_CHECK();
+  if (la.launches) *la.launches += 1;
+}
+
+// Row mu of A[m]: nu <= mu from the packed row (coalesced), nu > mu from
+// column mu of the lower triangle (entry mu of the packed rows nu > mu).
+__global__ void __launch_bounds__(256) unpack_sym_batch_kernel(const double* __restrict__ Ap, int nmat, int N,
+                                                               long long ldp, double* __restrict__ A) {
+  const long long rows = (long long)nmat * N, n2 = (long long)N * N;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const long long m = r / N;
+    const int mu = (int)(r - m * N);
+    const double* src = Ap + m * ldp;
+    double* dst = A + m * n2 + (long long)mu * N;
+    for (int nu = threadIdx.x; nu < N; nu += blockDim.x)
+      dst[nu] = nu <= mu ? src[(long long)mu * (mu + 1) / 2 + nu] : src[(long long)nu * (nu + 1) / 2 + mu];
+  }
+}
+
+void unpack_sym_batch(const LaCtx& la, const double* Ap, int nmat, int N, long long ldp, double* A) {
+  const long long rows = (long long)nmat * N;
+  unpack_sym_batch_kernel<<<(int)std::max<long long>(1, std::min<long long>(rows, 32LL * la.sms)), 256, 0,
+                            la.stream>>>(Ap, nmat, N, ldp, A);
+  RIHF_LAUNCH_CHECK();
+  if (la.launches) *la.launches += 1;
+}
+
+void unpack_sym(const LaCtx& la, const double* Ap, int N, double* A) { unpack_sym_batch(la, Ap, 1, N, 0, A); }
+
 }  // namespace rihf

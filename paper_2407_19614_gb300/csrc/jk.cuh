@@ -24,4 +24,20 @@ void gemv_cols_f32(const LaCtx& la, const float* A, int M, long long K, const do
 // Y[P][e] = c[P] * D[e] for e < n2, P < naux.
 void outer_fill(const LaCtx& la, const double* c, int naux, const double* D, long long n2, double* Y);
 
+// Pair-packed symmetric storage: element (mu, nu) of an N x N symmetric
+// matrix at tri(max) + min, tri(i) = i (i + 1) / 2; N (N + 1) / 2 entries.
+__host__ __device__ inline long long tri_index(int mu, int nu) {
+  const long long a = mu > nu ? mu : nu, b = mu > nu ? nu : mu;
+  return a * (a + 1) / 2 + b;
+}
+// Ap = packed A with the off-diagonal entries times w (w = 2 turns a packed
+// dot product into the full symmetric one).
+void pack_sym(const LaCtx& la, const double* A, int N, double w, double* Ap);
+// A (N x N) from packed Ap, both triangles.
+void unpack_sym(const LaCtx& la, const double* Ap, int N, double* A);
+// nmat matrices: A[m][mu][nu] = Ap[m * ldp + tri_index(mu, nu)], and back
+// (pack_sym_batch reads the lower triangle of each A[m]).
+void unpack_sym_batch(const LaCtx& la, const double* Ap, int nmat, int N, long long ldp, double* A);
+void pack_sym_batch(const LaCtx& la, const double* A, int nmat, int N, double* Ap, long long ldp);
+
 }  // namespace rihf

@@ -499,7 +499,18 @@ struct rihf_ctx {
   // geometry-dependent matrices
   double *S = nullptr, *H = nullptr, *Tk = nullptr, *V = nullptr;
   double *A = nullptr, *L = nullptr, *Linv = nullptr;
-  double *T3 = nullptr, *B = nullptr;
+  // The fitted tensor, pair-packed: Bp[P][tri(mu) + nu] (mu >= nu), Naux x
+  // N(N+1)/2 FP64.  The 3-centre integrals are written here and the fit
+  // B = L^{-1} T runs in place.  Consumers that need whole N x N slices (the
+  // RI-K and gradient products) expand chunks of `pc` auxiliary functions:
+  // into Bu (FP64) or straight into digit planes (mixed mode).  When every
+  // slice fits at once the expansion is done once per geometry: Bu holds all
+  // of B (bu_is_B, FP64 mode) or Bz all of B's 7-digit planes (planes_all).
+  long long npp = 0;
+  double *Bp = nullptr, *Yp = nullptr, *Bu = nullptr;
+  double *Dp = nullptr, *Jp = nullptr;   // packed weighted density and packed J of the RI-J passes
+  int pc = 0;
+  bool bu_is_B = false, planes_all = false;
   double *Xo = nullptr;     // N x nind orthogonaliser
   double *Sw = nullptr, *Sv = nullptr;
 
@@ -558,7 +569,8 @@ struct rihf_ctx {
   double ml_lr = 1e-3, ml_scale = 0.0, ml_last_ratio = 1e300;
   double ml_ratios[3] = {1e300, 1e300, 1e300};        // last three out-of-sample ratios
   double* trsm_tmp = nullptr;
-  double *cvec = nullptr, *W = nullptr, *Bij = nullptr, *Xt = nullptr, *Zm = nullptr, *G = nullptr, *Y = nullptr;
+  double *cvec = nullptr, *W = nullptr, *Bij = nullptr, *Xt = nullptr, *Zm = nullptr;
+  double* G = nullptr;   // the gradient's G' = C~ X~ (shares Hb's memory: H is spent by then)
   double* grad_parts = nullptr;   // 5 x natoms x 3 on device (one, overlap, three, two, nuc)
   std::vector<double> grad_parts_h;
 
@@ -662,10 +674,10 @@ static void free_all(rihf_ctx* c) {
                   c->hist_xyz[1], c->Dpred, c->mlX, c->mly, c->mlt, c->mlDx, c->ml_sums, c->rep_X, c->rep_t, c->net.master, c->net.wbf, c->net.grad,
                   c->net.m, c->net.v, c->net.loss,
                   c->d_tr, c->d_nf, c->d_Z, c->d_xyz, c->d_boys, c->d_counter, c->d_flag, c->d_sched, c->d_red, c->d_ticket, c->d_pairs, c->d_tasks, c->d_schwarz,
-                  c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->T3, c->B, c->Xo, c->Sw, c->Sv,
+                  c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->Bp, c->Yp, c->Bu, c->Dp, c->Jp, c->Xo, c->Sw, c->Sv,
                   c->C, c->eps, c->Ct, c->D, c->J, c->K, c->F, c->Fx, c->T1, c->T2, c->Err, c->Fp, c->Cp, c->Hb,
                   c->dvec, c->Fring, c->Ering, c->Bdiis, c->coef, c->scal, c->Cprev,
-                  c->na2tmp, c->trsm_tmp, c->cvec, c->W, c->Bij, c->Xt, c->Zm, c->G, c->Y, c->grad_parts, c->work, c->eigws, c->scratch};
+                  c->na2tmp, c->trsm_tmp, c->cvec, c->W, c->Bij, c->Xt, c->Zm, c->grad_parts, c->work, c->eigws, c->scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (OzBuf* b : {&c->Bz, &c->Cz, &c->Hz, &c->Ctz, &c->Gz, &c->Xz, &c->trsm_sc.L, &c->trsm_sc.X}) oz_buf_free(*b);
@@ -733,26 +745,30 @@ static void compute_geometry(rihf_ctx* c) {
       refresh_tasks(c);
     }
   }
-  // (mu nu|P) for shell pairs a >= b, then B = L^{-1} T (Eq. biap with A^L = L^{-T})
-  // by blocked forward substitution on the lower-triangle columns; an explicit
-  // L^{-1} product loses accuracy when cond(A) reaches 1e9 (diffuse auxiliary sets)
-  RIHF_CUDA(cudaMemsetAsync(c->T3, 0, sizeof(double) * (size_t)NA * N * N, s));
+  // (mu nu|P) for shell pairs a >= b into the pair-packed Bp, then
+  // B = L^{-1} T (Eq. biap with A^L = L^{-T}) in place by blocked forward
+  // substitution over the Naux x N(N+1)/2 matrix; an explicit L^{-1} product
+  // loses accuracy when cond(A) reaches 1e9 (diffuse auxiliary sets)
+  RIHF_CUDA(cudaMemsetAsync(c->Bp, 0, sizeof(double) * (size_t)NA * c->npp, s));
   { TraceScope t(c->tracer, s, "eri3_kernel (mu nu|P)", c->flops_eri3, 0);
     launch_pair_prims(ic, P, c->d_pairs, c->npairs, c->d_pp_off, c->d_pp);
-    launch_eri3(ic, P, X, c->d_pairs, c->ptab(), c->groups, kTaskGroups, c->T3); }
-  RIHF_CUDA(cudaMemcpyAsync(c->B, c->T3, sizeof(double) * (size_t)NA * N * N, cudaMemcpyDeviceToDevice, s));
+    launch_eri3(ic, P, X, c->d_pairs, c->ptab(), c->groups, kTaskGroups, c->Bp); }
   if (c->trsm_sc.X.planes) {
     // mixed mode: rank-64 updates on the tensor cores (7 digits), panels in FP64
-    TraceScope t(c->tracer, s, "fit trsm B=L^-1 T (tcgen05 digit updates)", (double)NA * NA * N * (N + 1) / 2, 0);
-    trsm_lower_tc(la, c->L, NA, c->B, (long long)N * N, N, c->trsm_sc);
+    TraceScope t(c->tracer, s, "fit trsm B=L^-1 T (tcgen05 digit updates)", (double)NA * NA * c->npp, 0);
+    trsm_lower_tc(la, c->L, NA, c->Bp, c->npp, 0, c->trsm_sc);
   } else {
-    TraceScope t(c->tracer, s, "fit trsm B=L^-1 T", (double)NA * NA * N * (N + 1) / 2, 0);
-    trsm_lower(la, c->L, NA, c->B, (long long)N * N, false, N, c->trsm_tmp);
+    TraceScope t(c->tracer, s, "fit trsm B=L^-1 T", (double)NA * NA * c->npp, 0);
+    trsm_lower(la, c->L, NA, c->Bp, c->npp, false, 0, c->trsm_tmp);
   }
-  symmetrize_lower(la, c->B, N, NA);
-  if (c->Bz.planes) {   // digit planes of B for the tensor-core RI-K (rows (P, mu), K = nu)
-    TraceScope t(c->tracer, s, "B digit planes (oz_slice)", (double)NA * N * N * (8 + 2 * kOzMaxDigits), 1);
-    c->Bop = oz_slice(la, c->B, NA * N, N, N, 1, 0, N, kOzMaxDigits, 0, c->Bz);
+  c->bu_is_B = false;
+  if (c->planes_all) {   // digit planes of all of B for the tensor-core RI-K (rows (P, mu), K = nu)
+    TraceScope t(c->tracer, s, "B digit planes (oz_slice)", (double)NA * c->npp * 8 + (double)NA * N * N * 2 * kOzMaxDigits, 1);
+    c->Bop = oz_slice(la, c->Bp, NA * N, N, 0, 0, 0, 1, kOzMaxDigits, 0, c->Bz, 0, c->npp, N);
+  } else if (!c->Bz.planes && c->pc == NA) {   // FP64 mode, all slices fit: expand B once
+    TraceScope t(c->tracer, s, "B expanded to N x N slices", (double)NA * c->npp * 8 + (double)NA * N * N * 8, 1);
+    unpack_sym_batch(la, c->Bp, NA, N, c->npp, c->Bu);
+    c->bu_is_B = true;
   }
   int flag = 0;
   RIHF_CUDA(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -862,6 +878,7 @@ void rihf_default_options(rihf_options* o) {
   o->device = 0;
   o->cuda_graphs = 1;
   o->confirm_fp64 = 0;
+  o->aux_chunk = 0;
 }
 
 const char* rihf_strerror(int code) {
@@ -989,7 +1006,10 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     size_t n2 = (size_t)N * N, na2 = (size_t)NA * NA, big = (size_t)NA * n2;
     c->S = dalloc<double>(n2); c->H = dalloc<double>(n2); c->Tk = dalloc<double>(n2); c->V = dalloc<double>(n2);
     c->A = dalloc<double>(na2); c->L = dalloc<double>(na2); c->Linv = dalloc<double>(na2);
-    c->T3 = dalloc<double>(big); c->B = dalloc<double>(big);
+    c->npp = (long long)N * (N + 1) / 2;
+    c->Bp = dalloc<double>((size_t)NA * c->npp); c->Yp = dalloc<double>((size_t)NA * c->npp);
+    c->Dp = dalloc<double>(c->npp); c->Jp = dalloc<double>(c->npp);
+    (void)big;
     c->Xo = dalloc<double>(n2); c->Sw = dalloc<double>(N); c->Sv = dalloc<double>(n2);
     c->C = dalloc<double>(n2); c->eps = dalloc<double>(N); c->Ct = dalloc<double>((size_t)N * c->nocc);
     c->D = dalloc<double>(n2); c->J = dalloc<double>(n2); c->K = dalloc<double>(n2); c->F = dalloc<double>(n2);
@@ -1007,21 +1027,20 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     c->Xt = dalloc<double>((size_t)NA * (c->nocc * c->nocc + 1));   // [X~ | c] per row P
     c->Zm = dalloc<double>(na2);
     c->na2tmp = dalloc<double>(na2);
-    c->G = dalloc<double>((size_t)NA * c->nocc * N);
-    c->Y = dalloc<double>(big);
-    if (c->opt.precision == RIHF_PRECISION_MIXED) {
+    c->G = c->Hb;   // G' of the gradient reuses H's memory (H is spent by then)
+    const bool mixed = c->opt.precision == RIHF_PRECISION_MIXED;
+    if (mixed) {
       const int nkb_max = (NA * c->nocc + kOzChunk - 1) / kOzChunk;
       const int no = c->nocc;
-      c->Bz = oz_buf_alloc(NA * N, N, kOzMaxDigits, 1);
       c->Cz = oz_buf_alloc(no, N, kOzMaxDigits, 1);
       c->Hz = oz_buf_alloc(N, NA * no, kOzMaxDigits, nkb_max);
       c->trsm_sc.L = oz_buf_alloc(NA, kTrsmOuter, kOzMaxDigits, 1);
-      c->trsm_sc.X = oz_buf_alloc(N * N, kTrsmOuter, kOzMaxDigits, 1);
+      c->trsm_sc.X = oz_buf_alloc((int)c->npp, kTrsmOuter, kOzMaxDigits, 1);
       c->Ctz = oz_buf_alloc(N, no, kOzMaxDigits, 1);
-      c->Gz = oz_buf_alloc(NA * N, no, kOzMaxDigits, 1);
-      c->Xz = oz_buf_alloc(NA, no * no, kOzMaxDigits, 1);
+      const int xch = (no * no + kOzChunk - 1) / kOzChunk;
+      c->Xz = oz_buf_alloc(NA, no * no, kOzMaxDigits, (xch + kOzMaxChunksPerBlock - 1) / kOzMaxChunksPerBlock);
     }
-    c->trsm_tmp = dalloc<double>(32 * std::max<size_t>({n2, (size_t)NA, (size_t)c->nocc * c->nocc}) + 1024);
+    c->trsm_tmp = dalloc<double>(32 * std::max<size_t>({(size_t)c->npp, (size_t)NA, (size_t)c->nocc * c->nocc}) + 1024);
     {   // guess history and learned-guess buffers
       std::vector<int> aoat(N), aol(N);
       for (int i = 0; i < c->hp.nshell; ++i)
@@ -1049,6 +1068,39 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     c->work = dalloc<double>(c->work_elems);
     c->eigws = dalloc<double>(eig_workspace(N));
     c->scratch = dalloc<double>(32 * 32 + (size_t)std::max(N, NA) * 32 + 64);
+    {
+      // Chunk buffers for the expanded N x N slices of B (and of Y): as many
+      // auxiliary functions per chunk as the free device memory holds, less a
+      // reserve, capped at Naux and at opt.aux_chunk.  FP64 slices in Bu; in
+      // mixed mode also their digit planes (Bz) and the gradient's chunk
+      // planes (Gz: rows (P, j) of H with K = N, or rows (P, mu) of G' with K = nocc).
+      const int no = c->nocc;
+      size_t fr = 0, tot = 0;
+      RIHF_CUDA(cudaMemGetInfo(&fr, &tot));
+      const size_t reserve = std::max<size_t>((size_t)2 << 30, tot / 32);
+      auto gz_elems = [&](int np) {
+        return std::max(oz_plane_elems(np * no, N, kOzMaxDigits), oz_plane_elems(np * N, no, kOzMaxDigits));
+      };
+      auto bytes = [&](int np) {
+        size_t b = (size_t)np * n2 * sizeof(double);
+        if (mixed)
+          b += oz_plane_elems(np * N, N, kOzMaxDigits) * sizeof(uint16_t) + gz_elems(np) * sizeof(uint16_t) +
+               2 * ((size_t)np * std::max(N, no) + 2 * kOzTileM) * sizeof(int);
+        return b;
+      };
+      int pc = NA;
+      if (c->opt.aux_chunk > 0) pc = std::min(pc, c->opt.aux_chunk);
+      while (pc > 1 && bytes(pc) + reserve > fr) pc = std::max(1, pc * 7 / 8);
+      if (bytes(pc) + reserve > fr) throw RihfError(RIHF_ERR_OOM, "no device memory left for one auxiliary chunk");
+      c->pc = pc;
+      c->Bu = dalloc<double>((size_t)pc * n2);
+      if (mixed) {
+        c->Bz = oz_buf_alloc(pc * N, N, kOzMaxDigits, 1);
+        c->Gz = oz_buf_alloc_raw(gz_elems(pc),
+                                 (size_t)((std::max(pc * no, pc * N) + kOzTileM - 1) / kOzTileM) * kOzTileM);
+        c->planes_all = pc == NA;
+      }
+    }
     compute_geometry(c);
   } catch (...) {
     free_all(c);
@@ -1219,6 +1271,63 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
   dgemm(la, g3);
 }
 
+// RI-J (Eq. j_ri) over the pair-packed B: d_P = sum_{mu >= nu} w B^P D (w = 2
+// off the diagonal), then J = sum_P d_P B^P; two streaming passes over B.
+static void ri_j(rihf_ctx* c) {
+  LaCtx la = c->la();
+  const int N = c->N, NA = c->NA;
+  pack_sym(la, c->D, N, 2.0, c->Dp);
+  { TraceScope t(c->tracer, c->stream, "RI-J d=B.D (gemv over packed rows)", (double)NA * c->npp * 8, 1);
+    gemv_rows(la, c->Bp, NA, c->npp, c->Dp, 1.0, c->dvec); }
+  { TraceScope t(c->tracer, c->stream, "RI-J J=B^T d (gemv over packed columns)", (double)NA * c->npp * 8, 1);
+    gemv_cols(la, c->Bp, NA, c->npp, c->dvec, 1.0, c->Jp);
+    unpack_sym(la, c->Jp, N, c->J); }
+}
+
+// Hb[(P, mu)][i] = sum_nu B^P_{mu nu} C~_{nu i} (Eq. tp) for every P: in FP64
+// (digits = 0) from the expanded slices (Bu, chunk by chunk unless it holds all
+// of B), or on the tensor cores with `digits` digits against the planes Cop of
+// C~^T (all of B's planes at once, or chunk planes cut from the packed rows).
+static void form_H(rihf_ctx* c, int digits, const OzOperand* Cop, const char* name) {
+  LaCtx la = c->la();
+  const int N = c->N, NA = c->NA, no = c->nocc;
+  const size_t n2 = (size_t)N * N;
+  const double prod = digits > 0 ? oz_products(digits) : 1.0;
+  const int npad = (no + 15) / 16 * 16, kpadN = (N + kOzChunk - 1) / kOzChunk * kOzChunk;
+  TraceScope t(c->tracer, c->stream, name,
+               digits > 0 ? 2.0 * (double)((NA * N + kOzTileM - 1) / kOzTileM * kOzTileM) * npad * kpadN * prod
+                          : 2.0 * NA * n2 * no,
+               digits > 0 ? 3 : 0);
+  if (digits > 0 && c->planes_all) {
+    OzGemmArgs g1;
+    g1.A = c->Bop; g1.B = *Cop; g1.M = NA * N; g1.N = no; g1.s = digits; g1.C = c->Hb; g1.cs_m1 = no; g1.cs_n = 1;
+    oz_gemm(la, g1);
+    return;
+  }
+  if (digits == 0 && c->bu_is_B) {
+    GemmArgs gh;
+    gh.M = NA * N; gh.N = no; gh.K = N; gh.A = c->Bu; gh.lda = N; gh.B = c->Ct; gh.ldb = no; gh.C = c->Hb; gh.ldc = no;
+    dgemm(la, gh);
+    return;
+  }
+  for (int P0 = 0; P0 < NA; P0 += c->pc) {
+    const int np = std::min(c->pc, NA - P0);
+    double* Hc = c->Hb + (size_t)P0 * N * no;
+    if (digits > 0) {
+      OzGemmArgs g1;
+      g1.A = oz_slice(la, c->Bp + (size_t)P0 * c->npp, np * N, N, 0, 0, 0, 1, digits, 0, c->Bz, 0, c->npp, N);
+      g1.B = *Cop; g1.M = np * N; g1.N = no; g1.s = digits; g1.C = Hc; g1.cs_m1 = no; g1.cs_n = 1;
+      oz_gemm(la, g1);
+    } else {
+      unpack_sym_batch(la, c->Bp + (size_t)P0 * c->npp, np, N, c->npp, c->Bu);
+      GemmArgs gh;
+      gh.M = np * N; gh.N = no; gh.K = N; gh.A = c->Bu; gh.lda = N; gh.B = c->Ct; gh.ldb = no; gh.C = Hc;
+      gh.ldc = no;
+      dgemm(la, gh);
+    }
+  }
+}
+
 // F = h + J + K for the current C; writes D, J, K, F, Ct and scal[0] = E.
 static void fock_build(rihf_ctx* c) {
   LaCtx la = c->la();
@@ -1230,16 +1339,9 @@ static void fock_build(rihf_ctx* c) {
   gd.M = N; gd.N = N; gd.K = no; gd.A = c->Ct; gd.lda = no; gd.B = c->Ct; gd.ldb = no; gd.transB = true;
   gd.C = c->D; gd.ldc = N;
   dgemm(la, gd);
-  // RI-J: d = B vec(D); J = B^T d
-  { TraceScope t(c->tracer, c->stream, "RI-J d=B.D (gemv_rows, lower triangles)", (double)NA * N * (N + 1) * 4, 1);
-    gemv_rows_sym(la, c->B, NA, N, c->D, 1.0, c->dvec); }
-  { TraceScope t(c->tracer, c->stream, "RI-J J=B^T d (gemv_cols, lower triangles)", (double)NA * N * (N + 1) * 4, 1);
-    gemv_cols_sym(la, c->B, NA, N, c->dvec, 1.0, c->J); }
+  ri_j(c);
   // RI-K: Hb[P] = B^P Ct (N x nocc); K = -1/2 sum_P Hb[P] Hb[P]^T
-  GemmArgs gh;
-  gh.M = NA * N; gh.N = no; gh.K = N; gh.A = c->B; gh.lda = N; gh.B = c->Ct; gh.ldb = no; gh.C = c->Hb; gh.ldc = no;
-  { TraceScope t(c->tracer, c->stream, "RI-K H=B C~ (dgemm)", 2.0 * NA * n2 * no, 0);
-    dgemm(la, gh); }
+  form_H(c, 0, nullptr, "RI-K H=B C~ (dgemm)");
   GemmArgs gk;
   gk.M = N; gk.N = N; gk.K = no; gk.A = c->Hb; gk.lda = no; gk.sA = (long long)N * no;
   gk.B = c->Hb; gk.ldb = no; gk.sB = (long long)N * no; gk.transB = true;
@@ -1313,18 +1415,11 @@ static void fock_build_tc(rihf_ctx* c, int digits) {
   gd.M = N; gd.N = N; gd.K = no; gd.A = c->Ct; gd.lda = no; gd.B = c->Ct; gd.ldb = no; gd.transB = true;
   gd.C = c->D; gd.ldc = N;
   dgemm(la, gd);
-  { TraceScope t(c->tracer, c->stream, "RI-J d=B.D (gemv_rows, lower triangles)", (double)NA * N * (N + 1) * 4, 1);
-    gemv_rows_sym(la, c->B, NA, N, c->D, 1.0, c->dvec); }
-  { TraceScope t(c->tracer, c->stream, "RI-J J=B^T d (gemv_cols, lower triangles)", (double)NA * N * (N + 1) * 4, 1);
-    gemv_cols_sym(la, c->B, NA, N, c->dvec, 1.0, c->J); }
+  ri_j(c);
   const double prod = oz_products(digits);
-  const int npad = (no + 15) / 16 * 16, kpadN = (N + kOzChunk - 1) / kOzChunk * kOzChunk;
   OzOperand Cop = oz_slice(la, c->Ct, no, N, 1, no, 0, N, digits, 0, c->Cz);
-  OzGemmArgs g1;   // H[(P, mu)][i] = sum_nu B[(P, mu)][nu] C~[nu][i]
-  g1.A = c->Bop; g1.B = Cop; g1.M = NA * N; g1.N = no; g1.s = digits; g1.C = c->Hb; g1.cs_m1 = no; g1.cs_n = 1;
-  { TraceScope t(c->tracer, c->stream, "RI-K H=B C~ (tcgen05 digits)",
-                 2.0 * c->Bop.rows_pad * npad * kpadN * prod, 3);
-    oz_gemm(la, g1); }
+  // H[(P, mu)][i] = sum_nu B[(P, mu)][nu] C~[nu][i]
+  form_H(c, digits, &Cop, "RI-K H=B C~ (tcgen05 digits)");
   // K blocks of the (P, i) axis: enough splits to cover the SMs, at most
   // kOzMaxChunksPerBlock chunks each (int64 headroom of the accumulators)
   const int kch = (NA * no + kOzChunk - 1) / kOzChunk;
@@ -1500,6 +1595,12 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   cudaStream_t s = c->stream;
   c->timings[1] = c->timings[2] = 0.0;
   cudaEventRecord(c->ev[7], s);   // SCF start (diagonalisation time = total - builds)
+  if (!c->Bz.planes && c->pc == c->NA && !c->bu_is_B) {
+    // FP64 mode holds all of B expanded in Bu, which the captured Fock-build
+    // graphs read; a gradient since the last geometry used Bu as scratch
+    unpack_sym_batch(la, c->Bp, c->NA, N, c->npp, c->Bu);
+    c->bu_is_B = true;
+  }
   if (guess == 1) {
     if (!C_guess) return RIHF_ERR_INVALID_ARG;
     RIHF_CUDA(cudaMemcpyAsync(c->C, C_guess, sizeof(double) * n2, cudaMemcpyHostToDevice, s));
@@ -1759,39 +1860,37 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   gw.alpha = 0.5;
   dgemm(la, gw);
   // d = B vec D; c = L^{-T} d (the paper's L^P) is solved below together with X~
-  { TraceScope t(c->tracer, s, "grad d = B D (gemv_rows, lower triangles)", (double)NA * N * (N + 1) * 4, 1);
-    gemv_rows_sym(la, c->B, NA, N, c->D, 1.0, c->dvec); }
+  { TraceScope t(c->tracer, s, "grad d = B D (gemv over packed rows)", (double)NA * c->npp * 8, 1);
+    pack_sym(la, c->D, N, 2.0, c->Dp);
+    gemv_rows(la, c->Bp, NA, c->npp, c->Dp, 1.0, c->dvec); }
   const long long ldx = (long long)no * no + 1;   // row P of Xt: X~^P (nocc^2) then c_P
   // Hb[P] = B^P Ct ; Bij[P] = Ct^T Hb[P]
   const bool tc = c->Gz.planes != nullptr;   // mixed mode: 7-digit tensor-core GEMMs (FP64-class products)
   OzOperand Cop;   // C~^T planes: rows i, K = mu (tensor-core path)
   if (tc) {
-    TraceScope t(c->tracer, s, "grad H=B C~ (tcgen05 7 digits)", 0.0, 0);
     Cop = oz_slice(la, c->Ct, no, N, 1, no, 0, N, kOzMaxDigits, 0, c->Cz);
-    OzGemmArgs g1;
-    g1.A = c->Bop; g1.B = Cop; g1.M = NA * N; g1.N = no; g1.s = kOzMaxDigits; g1.C = c->Hb; g1.cs_m1 = no;
-    g1.cs_n = 1;
-    oz_gemm(la, g1);
+    form_H(c, kOzMaxDigits, &Cop, "grad H=B C~ (tcgen05 7 digits)");
   } else {
-    GemmArgs gh;
-    gh.M = NA * N; gh.N = no; gh.K = N; gh.A = c->B; gh.lda = N; gh.B = c->Ct; gh.ldb = no; gh.C = c->Hb;
-    gh.ldc = no;
-    dgemm(la, gh);
+    form_H(c, 0, nullptr, "grad H=B C~ (dgemm)");
   }
-  // Bij on the tensor cores when K = N fits one exponent block and the idle
-  // G' plane buffer holds the rows (P, j) of H
+  // Bij on the tensor cores when K = N fits one exponent block, chunk by chunk
+  // of auxiliary functions in the G' plane buffer (rows (P, j) of H)
   const bool tc_bij = tc && (N + kOzChunk - 1) / kOzChunk <= kOzMaxChunksPerBlock &&
-                      oz_plane_elems(NA * no, N, kOzMaxDigits) <= c->Gz.cap &&
-                      (size_t)((NA * no + kOzTileM - 1) / kOzTileM * kOzTileM) <= c->Gz.ecap;
+                      oz_plane_elems(c->pc * no, N, kOzMaxDigits) <= c->Gz.cap &&
+                      (size_t)((c->pc * no + kOzTileM - 1) / kOzTileM * kOzTileM) <= c->Gz.ecap;
   if (tc_bij) {
     // rows (P, j) of H (element (P, mu, j) at Hb[P N nocc + mu nocc + j]), K = mu; Bij[P]
     // is symmetric in (i, j) and goes per P as [j][i] straight into [X~ | c]
     TraceScope t(c->tracer, s, "grad Bij = C~^T H (tcgen05 7 digits)", 0.0, 0);
-    OzOperand Hop = oz_slice(la, c->Hb, NA * no, N, 1, no, 0, N, kOzMaxDigits, 0, c->Gz, no, (long long)N * no);
-    OzGemmArgs gb;
-    gb.A = Hop; gb.B = Cop; gb.M = NA * no; gb.N = no; gb.s = kOzMaxDigits; gb.C = c->Xt;
-    gb.MR = no; gb.cs_m1 = no; gb.cs_m2 = ldx; gb.cs_n = 1;
-    oz_gemm(la, gb);
+    for (int P0 = 0; P0 < NA; P0 += c->pc) {
+      const int np = std::min(c->pc, NA - P0);
+      OzOperand Hop = oz_slice(la, c->Hb + (size_t)P0 * N * no, np * no, N, 1, no, 0, N, kOzMaxDigits, 0, c->Gz, no,
+                               (long long)N * no);
+      OzGemmArgs gb;
+      gb.A = Hop; gb.B = Cop; gb.M = np * no; gb.N = no; gb.s = kOzMaxDigits; gb.C = c->Xt + (size_t)P0 * ldx;
+      gb.MR = no; gb.cs_m1 = no; gb.cs_m2 = ldx; gb.cs_n = 1;
+      oz_gemm(la, gb);
+    }
   } else {
     TraceScope t(c->tracer, s, "grad Bij = C~^T H (batched dgemm)", 2.0 * NA * N * no * no, 0);
     GemmArgs gb;
@@ -1814,13 +1913,18 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
       trsm_lower(la, c->L, NA, c->Xt, ldx, true, 0, c->trsm_tmp);
     RIHF_CUDA(cudaMemcpy2DAsync(c->cvec, sizeof(double), c->Xt + (size_t)no * no, ldx * sizeof(double),
                                 sizeof(double), NA, cudaMemcpyDeviceToDevice, s)); }
-  // Z = c c^T - 1/2 Xt Xt^T
-  if (tc && (no * no + kOzChunk - 1) / kOzChunk <= kOzMaxChunksPerBlock) {
+  // Z = c c^T - 1/2 Xt Xt^T (tensor cores: K = nocc^2 in exponent blocks of at
+  // most kOzMaxChunksPerBlock chunks, summed atomically into a zeroed Zm)
+  if (tc) {
     TraceScope t(c->tracer, s, "grad Z=-1/2 X X^T (tcgen05 7 digits)", 0.0, 0);
-    OzOperand Xop = oz_slice(la, c->Xt, NA, no * no, ldx, 1, 0, no * no, kOzMaxDigits, 0, c->Xz);
+    const int kch = (no * no + kOzChunk - 1) / kOzChunk;
+    const bool blocks = kch > kOzMaxChunksPerBlock;
+    OzOperand Xop = oz_slice(la, c->Xt, NA, no * no, ldx, 1, 0, no * no, kOzMaxDigits,
+                             blocks ? kOzMaxChunksPerBlock : 0, c->Xz);
+    if (blocks) RIHF_CUDA(cudaMemsetAsync(c->Zm, 0, sizeof(double) * (size_t)NA * NA, s));
     OzGemmArgs gz;
     gz.A = Xop; gz.B = Xop; gz.M = NA; gz.N = NA; gz.s = kOzMaxDigits; gz.alpha = -0.5; gz.C = c->Zm;
-    gz.cs_m1 = NA; gz.cs_n = 1; gz.lower_only = true;
+    gz.cs_m1 = NA; gz.cs_n = 1; gz.lower_only = true; gz.atomic = blocks;
     oz_gemm(la, gz);
   } else {
     GemmArgs gz;
@@ -1834,8 +1938,9 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   gc.beta = 1.0;
   dgemm(la, gc);
   symmetrize_lower(la, c->Zm, NA, 1);
-  // Y[P] = D c_P - 1/2 Ct Xt[P] Ct^T
-  outer_fill(la, c->cvec, NA, c->D, (long long)n2, c->Y);
+  // Y[P] = D c_P - 1/2 Ct Xt[P] Ct^T: G'[P] = Ct Xt[P] for all P, then per chunk of
+  // auxiliary functions the N x N slices in Bu (D c_P plus the product), packed into Yp
+  c->bu_is_B = false;
   if (tc) {
     // G'[P] = Ct Xt[P] (N x nocc, Xt[P] symmetric), then one GEMM over rows
     // (P, mu): Y[(P, mu)][nu] += -1/2 sum_i G'[(P, mu)][i] Ct[nu][i]
@@ -1860,22 +1965,33 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
       dgemm(la, gg);
     }
     TraceScope t(c->tracer, s, "grad Y=Dc-1/2 C~XC~^T (tcgen05 7 digits)", 0.0, 0);
-    OzOperand Gop = oz_slice(la, c->G, NA * N, no, no, 1, 0, no, kOzMaxDigits, 0, c->Gz);
-    OzGemmArgs gy;
-    gy.A = Gop; gy.B = Top; gy.M = NA * N; gy.N = N; gy.s = kOzMaxDigits; gy.alpha = -0.5; gy.C = c->Y;
-    gy.cs_m1 = N; gy.cs_n = 1; gy.accumulate = true;
-    oz_gemm(la, gy);
+    for (int P0 = 0; P0 < NA; P0 += c->pc) {
+      const int np = std::min(c->pc, NA - P0);
+      outer_fill(la, c->cvec + P0, np, c->D, (long long)n2, c->Bu);
+      OzOperand Gop = oz_slice(la, c->G + (size_t)P0 * N * no, np * N, no, no, 1, 0, no, kOzMaxDigits, 0, c->Gz);
+      OzGemmArgs gy;
+      gy.A = Gop; gy.B = Top; gy.M = np * N; gy.N = N; gy.s = kOzMaxDigits; gy.alpha = -0.5; gy.C = c->Bu;
+      gy.cs_m1 = N; gy.cs_n = 1; gy.accumulate = true;
+      oz_gemm(la, gy);
+      pack_sym_batch(la, c->Bu, np, N, c->Yp + (size_t)P0 * c->npp, c->npp);
+    }
   } else {
     // G[P] = Xt[P] Ct^T (nocc x N)
     GemmArgs gg;
     gg.M = no; gg.N = N; gg.K = no; gg.A = c->Xt; gg.lda = no; gg.sA = ldx;
     gg.B = c->Ct; gg.ldb = no; gg.transB = true; gg.C = c->G; gg.ldc = N; gg.sC = (long long)no * N; gg.batch = NA;
     dgemm(la, gg);
-    GemmArgs gy;
-    gy.M = N; gy.N = N; gy.K = no; gy.A = c->Ct; gy.lda = no; gy.B = c->G; gy.ldb = N; gy.sB = (long long)no * N;
-    gy.C = c->Y; gy.ldc = N; gy.sC = (long long)n2; gy.batch = NA; gy.alpha = -0.5; gy.beta = 1.0;
     TraceScope t(c->tracer, s, "grad Y=Dc-1/2 C~XC~^T (dgemm)", 2.0 * NA * n2 * no, 0);
-    dgemm(la, gy);
+    for (int P0 = 0; P0 < NA; P0 += c->pc) {
+      const int np = std::min(c->pc, NA - P0);
+      outer_fill(la, c->cvec + P0, np, c->D, (long long)n2, c->Bu);
+      GemmArgs gy;
+      gy.M = N; gy.N = N; gy.K = no; gy.A = c->Ct; gy.lda = no; gy.B = c->G + (size_t)P0 * no * N; gy.ldb = N;
+      gy.sB = (long long)no * N; gy.C = c->Bu; gy.ldc = N; gy.sC = (long long)n2; gy.batch = np; gy.alpha = -0.5;
+      gy.beta = 1.0;
+      dgemm(la, gy);
+      pack_sym_batch(la, c->Bu, np, N, c->Yp + (size_t)P0 * c->npp, c->npp);
+    }
   }
   // fused derivative-integral contractions
   RIHF_CUDA(cudaMemsetAsync(c->grad_parts, 0, sizeof(double) * 15 * nat, s));
@@ -1886,7 +2002,7 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   { TraceScope t(c->tracer, s, "grad_one_electron_kernel", 0.0, 0);
     launch_grad_one_electron(ic, c->prim(), c->max_lp, nat, c->d_Z, c->d_xyz, c->D, c->W, g_one, g_ovl); }
   { TraceScope t(c->tracer, s, "grad_eri3_kernel (fused d(mu nu|P) . Y)", c->flops_grad3, 0);
-    launch_grad_eri3(ic, c->prim(), c->aux(), c->d_pairs, c->ptab(), c->groups, kTaskGroups, c->Y, g_three); }
+    launch_grad_eri3(ic, c->prim(), c->aux(), c->d_pairs, c->ptab(), c->groups, kTaskGroups, c->Yp, g_three); }
   { TraceScope t(c->tracer, s, "grad_eri2_kernel (fused d(P|Q) . Z)", (double)NA * NA * 8, 1);
     launch_grad_eri2(ic, c->aux(), c->max_la, c->Zm, g_two); }
   c->grad_parts_h.assign(15 * nat, 0.0);
@@ -1954,21 +2070,32 @@ int rihf_get_matrix(rihf_ctx* c, int which, double* out) {
       RIHF_CUDA(cudaMemcpy(out, c->Linv, na2 * 8, cudaMemcpyDeviceToHost));
       break;
     }
-    case RIHF_MAT_B: RIHF_CUDA(cudaMemcpy(out, c->B, (size_t)c->NA * n2 * 8, cudaMemcpyDeviceToHost)); break;
+    case RIHF_MAT_B:
     case RIHF_MAT_T3: {
-      RIHF_CUDA(cudaMemcpy(out, c->T3, (size_t)c->NA * n2 * 8, cudaMemcpyDeviceToHost));
-      // the device copy holds the lower shell-pair triangle; mirror on the host
-      const int N = c->N;
-      for (int P = 0; P < c->NA; ++P) {
-        double* s = out + (size_t)P * n2;
-        for (const ShellPair& sp : c->pairs_h) {
-          if (sp.a == sp.b) continue;
-          int a0 = c->hp.ao[sp.a], b0 = c->hp.ao[sp.b];
-          int na = c->nf_h[c->hp.l[sp.a]], nb = c->nf_h[c->hp.l[sp.b]];
-          for (int i = 0; i < na; ++i)
-            for (int j = 0; j < nb; ++j) s[(size_t)(b0 + j) * N + a0 + i] = s[(size_t)(a0 + i) * N + b0 + j];
+      // B: the packed device tensor; T3: the fit overwrote it, so the
+      // integrals are evaluated again into a temporary packed buffer.  Both are
+      // expanded to Naux x N x N on the host.
+      const int N = c->N, NA = c->NA;
+      std::vector<double> pk((size_t)NA * c->npp);
+      if (which == RIHF_MAT_B) {
+        RIHF_CUDA(cudaMemcpy(pk.data(), c->Bp, sizeof(double) * pk.size(), cudaMemcpyDeviceToHost));
+      } else {
+        double* tmp = dalloc<double>(pk.size());
+        try {
+          RIHF_CUDA(cudaMemsetAsync(tmp, 0, sizeof(double) * pk.size(), c->stream));
+          launch_eri3(c->ic(), c->prim(), c->aux(), c->d_pairs, c->ptab(), c->groups, kTaskGroups, tmp);
+          RIHF_CUDA(cudaMemcpyAsync(pk.data(), tmp, sizeof(double) * pk.size(), cudaMemcpyDeviceToHost, c->stream));
+          RIHF_CUDA(cudaStreamSynchronize(c->stream));
+        } catch (...) {
+          cudaFree(tmp);
+          throw;
         }
+        cudaFree(tmp);
       }
+      for (int P = 0; P < NA; ++P)
+        for (int mu = 0; mu < N; ++mu)
+          for (int nu = 0; nu < N; ++nu)
+            out[(size_t)P * n2 + (size_t)mu * N + nu] = pk[(size_t)P * c->npp + tri_index(mu, nu)];
       break;
     }
     case RIHF_MAT_FEATURES: {

@@ -171,10 +171,17 @@ struct OzSrc {
   int KR;
   int RR;             // > 0: rows split as (r % RR, r / RR) with strides s_r, s_r2
   long long s_r2;
+  int PN;             // > 0: pair-packed symmetric PN x PN matrices, s_r2 apart:
+                      // row r = (matrix r / PN, mu = r % PN), column k = nu
 };
 
 __device__ inline double oz_load(const OzSrc& S, int r, int k) {
   if (r >= S.rows || k >= S.K) return 0.0;
+  if (S.PN > 0) {
+    const int mu = r % S.PN;
+    const long long a = mu > k ? mu : k, b = mu > k ? k : mu;
+    return S.X[(long long)(r / S.PN) * S.s_r2 + a * (a + 1) / 2 + b];
+  }
   const int q = k / S.KR, m = k - q * S.KR;
   const long long ro = S.RR > 0 ? (long long)(r % S.RR) * S.s_r + (long long)(r / S.RR) * S.s_r2 : (long long)r * S.s_r;
   return S.X[ro + (long long)m * S.s_k1 + (long long)q * S.s_k2];
@@ -609,9 +616,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 }  // namespace
 
 OzBuf oz_buf_alloc(int rows, int K, int smax, int nkb) {
+  return oz_buf_alloc_raw(oz_plane_elems(rows, K, smax),
+                          (size_t)((rows + kOzTileM - 1) / kOzTileM) * kOzTileM * std::max(nkb, 1));
+}
+
+OzBuf oz_buf_alloc_raw(size_t plane_elems, size_t exp_elems) {
   OzBuf b;
-  b.cap = oz_plane_elems(rows, K, smax);
-  b.ecap = (size_t)((rows + kOzTileM - 1) / kOzTileM) * kOzTileM * std::max(nkb, 1);
+  b.cap = plane_elems;
+  b.ecap = exp_elems;
   void* p = nullptr;
   if (cudaMalloc(&p, sizeof(uint16_t) * b.cap) != cudaSuccess) throw RihfError(RIHF_ERR_OOM, "cudaMalloc failed");
   b.planes = static_cast<uint16_t*>(p);
@@ -630,7 +642,8 @@ void oz_buf_free(OzBuf& b) {
 }
 
 OzOperand oz_slice(const LaCtx& la, const double* X, int rows, int K, long long s_r, long long s_k1,
-                   long long s_k2, int KR, int smax, int kb_chunks, const OzBuf& buf, int RR, long long s_r2) {
+                   long long s_k2, int KR, int smax, int kb_chunks, const OzBuf& buf, int RR, long long s_r2,
+                   int packed_n) {
   if (rows <= 0 || K <= 0 || smax < 1 || smax > kOzMaxDigits || KR <= 0)
     throw RihfError(RIHF_ERR_INVALID_ARG, "oz_slice: bad arguments");
   uint16_t* planes = buf.planes;
@@ -647,7 +660,9 @@ OzOperand oz_slice(const LaCtx& la, const double* X, int rows, int K, long long 
   if (oz_plane_elems(rows, K, smax) > buf.cap || (size_t)op.rows_pad * op.nkb > buf.ecap)
     throw RihfError(RIHF_ERR_INVALID_ARG, "oz_slice: digit-plane buffer too small");
   if (op.kchunks > 65535) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_slice: K too long");
-  OzSrc S{X, rows, K, s_r, s_k1, s_k2, KR, RR, s_r2};
+  if (packed_n > 0 && (K != packed_n || rows % packed_n != 0))
+    throw RihfError(RIHF_ERR_INVALID_ARG, "oz_slice: packed rows must be whole matrices");
+  OzSrc S{X, rows, K, s_r, s_k1, s_k2, KR, RR, s_r2, packed_n};
   dim3 grid(op.rows_pad / (kOzThreads / kCoreK), op.kchunks);
   RIHF_CUDA(cudaMemsetAsync(exps, 0, sizeof(int) * (size_t)op.rows_pad * op.nkb, la.stream));
   oz_emax_kernel<<<grid, kOzThreads, 0, la.stream>>>(S, op.kb_chunks, op.nkb, exps);

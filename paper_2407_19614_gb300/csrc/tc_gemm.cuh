@@ -46,12 +46,15 @@ struct OzOperand {
 
 // Slice X (rows x K, element (r, k) at X[r*s_r + (k % KR)*s_k1 + (k / KR)*s_k2],
 // or, with RR > 0, at X[(r % RR)*s_r + (r / RR)*s_r2 + ...]) into smax digit
-// planes; K blocks of kb_chunks chunks get their own exponent.  Needs
+// planes; K blocks of kb_chunks chunks get their own exponent.  With
+// packed_n > 0 the source is pair-packed symmetric packed_n x packed_n
+// matrices s_r2 apart: row r is row r % packed_n of matrix r / packed_n, and
+// K = packed_n (s_r, s_k1, s_k2, KR and RR unused).  Needs
 // oz_plane_elems(rows, K, smax) plane and rows_pad * nkb exponent entries in buf
 // (RIHF_ERR_INVALID_ARG otherwise).
 OzOperand oz_slice(const LaCtx& la, const double* X, int rows, int K, long long s_r, long long s_k1,
                    long long s_k2, int KR, int smax, int kb_chunks, const OzBuf& buf, int RR = 0,
-                   long long s_r2 = 0);
+                   long long s_r2 = 0, int packed_n = 0);
 
 // C(m, n) = alpha * sum_k A(m, k) B(n, k) using s <= min(A.smax, B.smax) digits.
 // Output element (m, n) at C[(m % MR) * cs_m1 + (m / MR) * cs_m2 + n * cs_n];

@@ -29,6 +29,9 @@ struct OzBuf {
 };
 // Buffer for up to `rows` x `K` with smax digits and at most nkb K blocks.
 OzBuf oz_buf_alloc(int rows, int K, int smax, int nkb);
+// Buffer with the given plane and exponent capacities (entries), for one
+// buffer that serves operands of different shapes in turn.
+OzBuf oz_buf_alloc_raw(size_t plane_elems, size_t exp_elems);
 void oz_buf_free(OzBuf& b);
 
 }  // namespace rihf

@@ -37,7 +37,8 @@ class rihf_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("pure", ctypes.c_int), ("schwarz_tau", ctypes.c_double),
                 ("lindep_tau", ctypes.c_double), ("conv_e", ctypes.c_double), ("conv_diis", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("diis_size", ctypes.c_int), ("mixed_digits", ctypes.c_int),
-                ("device", ctypes.c_int), ("cuda_graphs", ctypes.c_int), ("confirm_fp64", ctypes.c_int)]
+                ("device", ctypes.c_int), ("cuda_graphs", ctypes.c_int), ("confirm_fp64", ctypes.c_int),
+                ("aux_chunk", ctypes.c_int)]
 
 
 EXPORTS = ["rihf_default_options", "rihf_setup", "rihf_update_geometry", "rihf_scf", "rihf_gradient",
