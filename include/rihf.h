@@ -224,8 +224,9 @@ int rihf_trace_stats(rihf_ctx* ctx, int max, char* names, double* launches, doub
 /* The library's symmetric eigensolver (the diagonalisation step of Alg. 1) on
    one n x n host matrix A (row-major, symmetric): eigenvalues W (n, ascending)
    and eigenvectors V (n x n, column k = eigenvector k).  FP32 parallel Jacobi
-   followed by FP64 Ogita-Aishima refinement, on device `device`.  Allocates
-   and frees its own device workspace.  Errors: INVALID_ARG, OOM, CUDA. */
+   (one CTA up to n = 256, a two-sided block Jacobi over many CTAs above)
+   followed by FP64 Ogita-Aishima refinement, on device `device`; n <= 4096.
+   Allocates and frees its own device workspace.  Errors: INVALID_ARG, OOM, CUDA. */
 int rihf_eigh(int n, const double* A, double* W, double* V, int device);
 
 /* Allocation-free variant of rihf_eigh (the paper has no counterpart: this is a

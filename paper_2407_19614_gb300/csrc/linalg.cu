@@ -1103,12 +1103,19 @@ __global__ void oa_e_kernel(const double* R, const double* S, const double* lam,
   }
   __syncthreads();
   const double delta = sh_delta;
+  // A pair is rotated when its gap exceeds the global cluster threshold (as in
+  // the method), or when its own first-order correction is small, |E_ij| < 1/8.
+  // The threshold bounds the spectral norms of the residuals by their
+  // Frobenius norms, which for large n exceed them by up to sqrt(n): pairs far
+  // apart relative to their own coupling would otherwise count as clustered and
+  // never rotate (at n = 1856 the refinement then stalls near FP32 accuracy).
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * n;
        idx += (long long)gridDim.x * blockDim.x) {
     int i = (int)(idx / n), j = (int)(idx % n);
     double r = R[idx];
+    const double num = S[idx] + lam[j] * r, dl = lam[j] - lam[i];
     double e;
-    if (i != j && fabs(lam[i] - lam[j]) > delta) e = (S[idx] + lam[j] * r) / (lam[j] - lam[i]);
+    if (i != j && (fabs(dl) > delta || fabs(dl) > 8.0 * fabs(num))) e = num / dl;
     else e = 0.5 * r;
     E[idx] = e;
   }
@@ -1151,6 +1158,236 @@ __global__ void eig_sort64_kernel(const double* __restrict__ V, const double* __
     for (int i = threadIdx.x; i < n; i += blockDim.x) Vout[(size_t)row * n + rank[i]] = V[(size_t)row * n + i];
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i < n; i += blockDim.x) Wout[rank[i]] = lam[i];
+}
+
+// ------------------------------------------------------------ block Jacobi (large n)
+//
+// Two-sided cyclic Jacobi in FP32 for orders above kBlockJacobiMin, spread over
+// many CTAs.  The (padded) indices form nb = np / kBJW blocks; a sweep is nb - 1
+// rounds of the round-robin pairing of blocks (block 0 fixed, the others
+// circulating); in a round every block pair -- one CTA -- diagonalises its
+// 2 kBJW x 2 kBJW submatrix by one cyclic sweep of plane rotations, giving Q;
+// then all pairs' columns are rotated (A <- A Q, V <- V Q) and, after them, all
+// rows (A <- Q^T A).  Pairs own disjoint rows and columns, so the three launches
+// of a round are the only synchronisation.  Padding indices (n..np) have zero
+// coupling and are never rotated.  After each sweep the squared off-diagonal
+// norm over the real indices is folded in a fixed order and compared with
+// tol^2 times the diagonal's; a device flag then turns the remaining launches
+// into no-ops (no host synchronisation, so the sweeps can sit in a CUDA graph).
+constexpr int kBJW = 16, kBJ2 = 2 * kBJW, kBJParts = 256;
+
+__device__ inline int bj_index(int pair, int k, int round, int nb) {
+  const int pos = k < kBJW ? pair : nb - 1 - pair;
+  const int blk = pos == 0 ? 0 : 1 + (pos - 1 + round) % (nb - 1);
+  return blk * kBJW + (k % kBJW);
+}
+
+__global__ void bj_init_kernel(const double* __restrict__ A, int n, int np, float* __restrict__ A32,
+                               float* __restrict__ V32, int* done) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)np * np;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / np), j = (int)(e % np);
+    A32[e] = (i < n && j < n) ? (float)A[(size_t)i * n + j] : 0.f;
+    V32[e] = i == j ? 1.f : 0.f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *done = 0;
+}
+
+__global__ void __launch_bounds__(256) bj_solve_kernel(const float* __restrict__ A, int np, int round, int nb,
+                                                       float* __restrict__ Qg, const int* done) {
+  if (*done) return;
+  __shared__ float S[kBJ2][kBJ2 + 1], Q[kBJ2][kBJ2 + 1];
+  __shared__ float cs[kBJW], sn[kBJW];
+  __shared__ int ra[kBJW], rb[kBJW], idx[kBJ2];
+  const int pair = blockIdx.x, t = threadIdx.x;
+  if (t < kBJ2) idx[t] = bj_index(pair, t, round, nb);
+  __syncthreads();
+  for (int e = t; e < kBJ2 * kBJ2; e += blockDim.x) {
+    const int i = e / kBJ2, j = e % kBJ2;
+    S[i][j] = A[(size_t)idx[i] * np + idx[j]];
+    Q[i][j] = i == j ? 1.f : 0.f;
+  }
+  __syncthreads();
+  // one cyclic sweep over the 2w indices: 2w - 1 rounds of w disjoint rotations
+  for (int r = 0; r < kBJ2 - 1; ++r) {
+    if (t < kBJW) {
+      int a = t == 0 ? 0 : 1 + (t - 1 + r) % (kBJ2 - 1);
+      int b = 1 + (kBJ2 - 2 - t + r) % (kBJ2 - 1);   // position 2w - 1 - t
+      if (a > b) { const int x = a; a = b; b = x; }
+      const float app = S[a][a], aqq = S[b][b], apq = S[a][b];
+      float c = 1.f, s = 0.f;
+      if (apq != 0.f) {
+        // symmetric Schur rotation: J = [c s; -s c] zeroes the (a, b) entry of J^T S J
+        const float th = (aqq - app) / (2.f * apq);
+        const float tt = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+        c = rsqrtf(fmaf(tt, tt, 1.f));
+        s = tt * c;
+      }
+      cs[t] = c; sn[t] = s; ra[t] = a; rb[t] = b;
+    }
+    __syncthreads();
+    for (int e = t; e < kBJW * kBJ2; e += blockDim.x) {   // S <- S J, Q <- Q J (columns a, b)
+      const int k = e / kBJ2, i = e % kBJ2, a = ra[k], b = rb[k];
+      const float c = cs[k], s = sn[k];
+      const float x = S[i][a], y = S[i][b];
+      S[i][a] = c * x - s * y;
+      S[i][b] = s * x + c * y;
+      const float u = Q[i][a], v = Q[i][b];
+      Q[i][a] = c * u - s * v;
+      Q[i][b] = s * u + c * v;
+    }
+    __syncthreads();
+    for (int e = t; e < kBJW * kBJ2; e += blockDim.x) {   // S <- J^T S (rows a, b)
+      const int k = e / kBJ2, j = e % kBJ2, a = ra[k], b = rb[k];
+      const float c = cs[k], s = sn[k];
+      const float x = S[a][j], y = S[b][j];
+      S[a][j] = c * x - s * y;
+      S[b][j] = s * x + c * y;
+    }
+    __syncthreads();
+  }
+  // one Newton-Schulz step, Q <- Q (3 I - Q^T Q) / 2: the 496 rotations leave Q
+  // orthogonal to ~1e-6 only, and V multiplies about a thousand such blocks
+  for (int e = t; e < kBJ2 * kBJ2; e += blockDim.x) {   // S <- (3 I - Q^T Q) / 2
+    const int i = e / kBJ2, j = e % kBJ2;
+    float g = 0.f;
+    for (int k = 0; k < kBJ2; ++k) g = fmaf(Q[k][i], Q[k][j], g);
+    S[i][j] = 0.5f * ((i == j ? 3.f : 0.f) - g);
+  }
+  __syncthreads();
+  float* q = Qg + (size_t)pair * kBJ2 * kBJ2;
+  for (int e = t; e < kBJ2 * kBJ2; e += blockDim.x) {
+    const int i = e / kBJ2, j = e % kBJ2;
+    float v = 0.f;
+    for (int k = 0; k < kBJ2; ++k) v = fmaf(Q[i][k], S[k][j], v);
+    q[e] = v;
+  }
+}
+
+// A[r][idx] <- A[r][idx] Q and V[r][idx] <- V[r][idx] Q for every row r: one
+// warp per row, lane k holds entry idx[k] (two 64-byte segments per row).
+__global__ void __launch_bounds__(256) bj_cols_kernel(float* __restrict__ A, float* __restrict__ V, int np, int round,
+                                                      int nb, const float* __restrict__ Qg, const int* done) {
+  if (*done) return;
+  __shared__ float Q[kBJ2][kBJ2 + 1];
+  const int pair = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float* q = Qg + (size_t)pair * kBJ2 * kBJ2;
+  for (int e = threadIdx.x; e < kBJ2 * kBJ2; e += blockDim.x) Q[e / kBJ2][e % kBJ2] = q[e];
+  __syncthreads();
+  const int col = bj_index(pair, lane, round, nb);
+  for (int r = blockIdx.y * 8 + warp; r < np; r += gridDim.y * 8) {
+    float x = A[(size_t)r * np + col], y = 0.f;
+    float u = V[(size_t)r * np + col], w = 0.f;
+#pragma unroll
+    for (int m = 0; m < kBJ2; ++m) {
+      const float qm = Q[m][lane];
+      y = fmaf(__shfl_sync(0xffffffffu, x, m), qm, y);
+      w = fmaf(__shfl_sync(0xffffffffu, u, m), qm, w);
+    }
+    A[(size_t)r * np + col] = y;
+    V[(size_t)r * np + col] = w;
+  }
+}
+
+// A[idx][c] <- Q^T A[idx][c] for every column c: one thread per column holds
+// the 2w entries of its column (coalesced across the warp).
+__global__ void __launch_bounds__(128) bj_rows_kernel(float* __restrict__ A, int np, int round, int nb,
+                                                      const float* __restrict__ Qg, const int* done) {
+  if (*done) return;
+  __shared__ float Q[kBJ2][kBJ2 + 1];
+  __shared__ int idx[kBJ2];
+  const int pair = blockIdx.x;
+  const float* q = Qg + (size_t)pair * kBJ2 * kBJ2;
+  for (int e = threadIdx.x; e < kBJ2 * kBJ2; e += blockDim.x) Q[e / kBJ2][e % kBJ2] = q[e];
+  if (threadIdx.x < kBJ2) idx[threadIdx.x] = bj_index(pair, threadIdx.x, round, nb);
+  __syncthreads();
+  for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < np; c += gridDim.y * blockDim.x) {
+    float o[kBJ2];
+#pragma unroll
+    for (int l = 0; l < kBJ2; ++l) o[l] = 0.f;
+#pragma unroll 1
+    for (int m = 0; m < kBJ2; ++m) {   // kept rolled: unrolled, the 1024 FMAs spill the outputs
+      const float zm = A[(size_t)idx[m] * np + c];
+#pragma unroll
+      for (int l = 0; l < kBJ2; ++l) o[l] = fmaf(Q[m][l], zm, o[l]);
+    }
+#pragma unroll
+    for (int l = 0; l < kBJ2; ++l) A[(size_t)idx[l] * np + c] = o[l];
+  }
+}
+
+// Squared off-diagonal and diagonal norms over the real indices, per block.
+__global__ void __launch_bounds__(256) bj_norm_kernel(const float* __restrict__ A, int n, int np, double* part,
+                                                      const int* done) {
+  if (*done) return;
+  __shared__ double r0[8], r1[8];
+  double off = 0.0, dg = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    const double v = A[(size_t)i * np + j];
+    if (i == j) dg += v * v;
+    else off += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    off += __shfl_xor_sync(0xffffffffu, off, o);
+    dg += __shfl_xor_sync(0xffffffffu, dg, o);
+  }
+  if ((threadIdx.x & 31) == 0) { r0[threadIdx.x >> 5] = off; r1[threadIdx.x >> 5] = dg; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < 8; ++w) { a += r0[w]; b += r1[w]; }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+
+__global__ void bj_check_kernel(const double* part, int nparts, double tol2, int* done) {
+  if (*done) return;
+  double a = 0.0, b = 0.0;
+  for (int k = 0; k < nparts; ++k) { a += part[2 * k]; b += part[2 * k + 1]; }   // fixed order
+  if (a <= tol2 * b) *done = 1;
+}
+
+// Diagonal of the rotated matrix (the eigenvalue estimates) for the sort.
+__global__ void bj_diag_kernel(const float* __restrict__ A, int n, int np, float* __restrict__ w) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) w[i] = A[(size_t)i * np + i];
+}
+
+// FP32 eigenpairs of the n x n FP64 matrix Ain into V (FP64, sorted) and W.
+static void block_jacobi(const LaCtx& la, const double* Ain, int n, double* V, double* W, double* bjws,
+                         int max_sweeps, float tol) {
+  const int np = (n + kBJ2 - 1) / kBJ2 * kBJ2, nb = np / kBJW, npair = nb / 2;
+  float* A32 = reinterpret_cast<float*>(bjws);
+  float* V32 = A32 + (size_t)np * np;
+  float* Qg = V32 + (size_t)np * np;
+  float* W32 = Qg + (size_t)npair * kBJ2 * kBJ2;
+  double* part = bjws + (2 * (size_t)np * np + (size_t)npair * kBJ2 * kBJ2 + np + 1) / 2;
+  int* done = reinterpret_cast<int*>(part + 2 * kBJParts);
+  bj_init_kernel<<<elem_blocks(la, (long long)np * np), 256, 0, la.stream>>>(Ain, n, np, A32, V32, done);
+  RIHF_LAUNCH_CHECK();
+  count(la);
+  const int rowblk = std::max(1, std::min(ceil_div(np, 8), 4 * la.sms / std::max(1, npair)));
+  const int colblk = std::max(1, std::min(ceil_div(np, 128), 4 * la.sms / std::max(1, npair)));
+  const int nparts = std::min(kBJParts, ceil_div(n * n, 256));
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int r = 0; r < nb - 1; ++r) {
+      bj_solve_kernel<<<npair, 256, 0, la.stream>>>(A32, np, r, nb, Qg, done);
+      bj_cols_kernel<<<dim3(npair, rowblk), 256, 0, la.stream>>>(A32, V32, np, r, nb, Qg, done);
+      bj_rows_kernel<<<dim3(npair, colblk), 128, 0, la.stream>>>(A32, np, r, nb, Qg, done);
+      RIHF_LAUNCH_CHECK();
+      count(la, 3);
+    }
+    bj_norm_kernel<<<nparts, 256, 0, la.stream>>>(A32, n, np, part, done);
+    bj_check_kernel<<<1, 1, 0, la.stream>>>(part, nparts, (double)tol * tol, done);
+    RIHF_LAUNCH_CHECK();
+    count(la, 2);
+  }
+  bj_diag_kernel<<<std::max(1, ceil_div(n, 256)), 256, 0, la.stream>>>(A32, n, np, W32);
+  eig_sort_kernel<<<std::min(n, 32), 256, 0, la.stream>>>(V32, W32, n, np, V, W);
+  RIHF_LAUNCH_CHECK();
+  count(la, 2);
 }
 
 void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double* ws, int refine,
@@ -1203,6 +1440,9 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
   // refinement to separate
   const float tol = 2e-6f;
   const int hb = (n + kJB - 1) / kJB;   // block width of the block kernel
+  if (n > kBlockJacobiMin) {
+    block_jacobi(la, Ain, n, V, W, ws + eig_workspace_base(n), max_sweeps, tol);
+  } else {
   if (hb <= 3) {
     const void* fn = hb == 1 ? (const void*)jacobi1s_block_kernel<1>
                    : hb == 2 ? (const void*)jacobi1s_block_kernel<2> : (const void*)jacobi1s_block_kernel<3>;
@@ -1223,6 +1463,7 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
   eig_sort_kernel<<<std::min(n, 32), 256, 0, la.stream>>>(fV, fW, n, m, V, W);
   RIHF_LAUNCH_CHECK();
   count(la);
+  }   // one-CTA Jacobi
   if (Vguess) {
     // V <- Vguess * V
     GemmArgs g;

@@ -109,13 +109,24 @@ void trsm_lower(const LaCtx& la, const double* L, int n, double* X, long long nc
 
 // Symmetric eigen-decomposition of an n x n FP64 matrix A (row-major):
 // W (n, ascending) and V (n x n, column k = eigenvector k).  FP32 parallel
-// Jacobi in one CTA, then Ogita-Aishima refinement in FP64 (`refine` steps).
+// Jacobi (one CTA up to kBlockJacobiMin, a two-sided block Jacobi over many
+// CTAs above), then Ogita-Aishima refinement in FP64 (`refine` steps).
 // ws must hold eig_workspace(n) doubles: the FP32 Jacobi copies (A, V, W;
-// even order m), then six n x n FP64 refinement matrices and 2n + 8 scalars.
-constexpr size_t eig_workspace(int n) {
+// even order m), then six n x n FP64 refinement matrices and 2n + 8 scalars;
+// above kBlockJacobiMin, also the parallel block Jacobi's FP32 matrices (order
+// n rounded up to a multiple of 32), rotations and reduction partials.
+constexpr int kBlockJacobiMin = 256;
+constexpr size_t eig_workspace_base(int n) {
   return ((size_t)(n + (n & 1)) * (n + (n & 1)) + (size_t)n * (n + (n & 1)) + (n + (n & 1)) + 1) / 2 +
          6 * (size_t)n * n + 2 * (size_t)n + 8;
 }
+constexpr size_t eig_workspace_bj(int n) {
+  return n <= kBlockJacobiMin ? 0
+                              : (2 * (size_t)((n + 31) / 32 * 32) * ((n + 31) / 32 * 32) +
+                                 (size_t)((n + 31) / 32) * 32 * 32 + (size_t)((n + 31) / 32 * 32) + 1) / 2 +
+                                    2 * 256 + 16;
+}
+constexpr size_t eig_workspace(int n) { return eig_workspace_base(n) + eig_workspace_bj(n); }
 // skip_jacobi: start the refinement from Vguess directly (late SCF iterations).
 // max_sweeps caps the FP32 Jacobi sweeps and ns_steps the Newton-Schulz
 // re-orthonormalisation steps after the refinement (early SCF iterations need

@@ -2378,7 +2378,9 @@ int rihf_eigh(int n, const double* A, double* W, double* V, int device) {
     RIHF_CUDA(cudaMemcpyAsync(dA, A, n2 * 8, cudaMemcpyHostToDevice, s));
     LaCtx la;
     la.stream = s; la.work = work; la.work_elems = work_elems; la.sms = sms; la.flag = flag;
-    eigh(la, dA, n, dW, dV, ws, 4, nullptr);
+    // above order 1024 the block Jacobi's FP32 start carries the rounding of
+    // more rounds: two more refinement steps
+    eigh(la, dA, n, dW, dV, ws, n > 1024 ? 6 : 4, nullptr);
     RIHF_CUDA(cudaMemcpyAsync(W, dW, n * 8, cudaMemcpyDeviceToHost, s));
     RIHF_CUDA(cudaMemcpyAsync(V, dV, n2 * 8, cudaMemcpyDeviceToHost, s));
     RIHF_CUDA(cudaStreamSynchronize(s));

@@ -186,8 +186,10 @@ def test_errors_are_reported():
     assert e2.value.code == -1
 
 
-@pytest.mark.parametrize("n", [7, 24, 192, 231])
+@pytest.mark.parametrize("n", [7, 24, 192, 231, 300, 701, 1856])
 def test_eigensolver_against_lapack(n):
+    """One-CTA Jacobi up to order 256, the multi-CTA block Jacobi above (orders
+    not multiples of its 32-wide block pairs: padded), then FP64 refinement."""
     R = _gpu()
     rng = np.random.default_rng(n)
     M = rng.normal(size=(n, n))
