@@ -130,6 +130,13 @@ int rihf_update_geometry(rihf_ctx* ctx, const double* xyz);
  *            example (else D_x; falls back to 2).  With guesses 3 and 4 the
  *            previous occupied orbitals are projected onto the predicted
  *            density (C <- D_pred S C, then S-orthonormalised).
+ *          5 superposition of atomic densities (SAD, the paper's cold start,
+ *            Sec. 2.2): one RI-HF SCF per atom type of the isolated,
+ *            spherically averaged atom (fractional occupations, H to Ne; the
+ *            same basis sets), D_SAD block-diagonal over the atoms; the first
+ *            iteration builds J from D_SAD and K from its factor (the density
+ *            form, Eq. k_ri_1).  Falls back to 0 when unavailable (other
+ *            elements, an atom's shells not contiguous).
  *          Every converged SCF pushes its D, S and nuclear positions into the
  *          three-deep history; a guess-4 SCF first trains the network on its
  *          own example (rihf_learn_config).
@@ -178,6 +185,8 @@ int rihf_query(rihf_ctx* ctx, int* N, int* Naux, int* nocc, int* natoms);
                           components of shells a >= b, packed a(a+1)/2 + b
                           (nshell(nshell+1)/2 values; zeros when the screen
                           is not evaluated)
+     RIHF_MAT_DSAD: N x N, the SAD guess density (after a guess-5 SCF built
+                          it; RIHF_ERR_STATE before, or when SAD was unavailable)
      RIHF_MAT_DPRED: N x N, the predicted density of the last guess-3 or
                           guess-4 SCF (extrapolation plus network correction)
      RIHF_MAT_FEATURES: N(N+1)/2 x 12, the network's features of that guess
@@ -186,7 +195,7 @@ int rihf_query(rihf_ctx* ctx, int* N, int* Naux, int* nocc, int* natoms);
 enum {
   RIHF_MAT_S = 0, RIHF_MAT_H = 1, RIHF_MAT_A = 2, RIHF_MAT_LINV = 3, RIHF_MAT_T3 = 4, RIHF_MAT_B = 5,
   RIHF_MAT_J = 6, RIHF_MAT_K = 7, RIHF_MAT_F = 8, RIHF_MAT_D = 9, RIHF_MAT_GRAD_PARTS = 10,
-  RIHF_MAT_SCHWARZ = 11, RIHF_MAT_DPRED = 12, RIHF_MAT_FEATURES = 13
+  RIHF_MAT_SCHWARZ = 11, RIHF_MAT_DPRED = 12, RIHF_MAT_FEATURES = 13, RIHF_MAT_DSAD = 14
 };
 int rihf_get_matrix(rihf_ctx* ctx, int which, double* out);
 
@@ -281,7 +290,7 @@ int rihf_learn_config(rihf_ctx* ctx, int hidden, int train_steps, int adam_iters
 /* trained_steps; last_ratio = sum (y - t)^2 / sum t^2 of the last training
    example before its update (below 1: the network beat D_x on an unseen
    example; guess 4 uses the network only below 0.9); last_guess = the guess
-   kind the last rihf_scf actually used (0, 1, 2, 3 or 4; guess 4 runs the
+   kind the last rihf_scf actually used (0, 1, 2, 3, 4 or 5; guess 4 runs the
    network once it has trained on three examples and the median of its last
    three out-of-sample ratios is below 0.8); scale.  Any pointer may be NULL. */
 int rihf_learn_stats(rihf_ctx* ctx, int* trained_steps, double* last_ratio, int* last_guess, double* scale);

@@ -130,12 +130,75 @@ class SCFResult:
     pass
 
 
-def scf(h, S, Vnn, nocc, fock_2e, C_guess=None, max_iter=128, conv_e=1e-11, conv_diis=1e-10, diis_size=8):
-    """Closed-shell Roothaan SCF.  fock_2e(C_occ, D) -> J + K."""
+def spherical_average(F, labels):
+    """Rotation average of a matrix over real solid harmonics: labels[i] =
+    (first function of i's shell, l, m index).  Entries between different l or
+    m vanish; for equal l and m the mean over m of the shell pair's (m, m)
+    entries remains."""
+    n = F.shape[0]
+    out = np.zeros_like(F)
+    for i in range(n):
+        a, li, mi = labels[i]
+        for j in range(n):
+            b, lj, mj = labels[j]
+            if li == lj and mi == mj:
+                out[i, j] = np.mean([F[a + m, b + m] for m in range(2 * li + 1)])
+    return out
+
+
+def sph_labels(shells):
+    """(first function of the shell, l, m index) per spherical function."""
+    out, k = [], 0
+    for sh in shells:
+        for m in range(2 * sh.l + 1):
+            out.append((k, sh.l, m))
+        k += 2 * sh.l + 1
+    return out
+
+
+def occupied_by_l(C, eps, labels, occ_l):
+    """Columns of C reordered so that the occupied ones follow occ_l (the l of
+    each occupied orbital, in order): for every l, the lowest-eps columns whose
+    weight lies in functions of that l.  The spherical average makes every
+    eigenvector pure in l; a configuration such as 1s2 2s2 2p4 then fixes which
+    orbitals carry which occupation even where the basis puts 2p below 2s."""
+    lcol = [labels[int(np.argmax(np.abs(C[:, j])))][1] for j in range(C.shape[1])]
+    order = list(np.argsort(eps, kind="stable"))
+    chosen = []
+    for l in occ_l:
+        j = next(j for j in order if lcol[j] == l and j not in chosen)
+        chosen.append(j)
+    rest = [j for j in order if j not in chosen]
+    idx = chosen + rest
+    return C[:, idx], eps[idx]
+
+
+def scf(h, S, Vnn, nocc, fock_2e, C_guess=None, max_iter=128, conv_e=1e-11, conv_diis=1e-10, diis_size=8,
+        occ=None, sph=None, occ_l=None):
+    """Closed-shell Roothaan SCF.  fock_2e(C_occ, D) -> J + K.
+
+    occ: occupation numbers n_i of the len(occ) lowest orbitals (the
+    spherically averaged atoms of the SAD guess); the closed-shell formulas
+    then hold with C_occ -> C_occ diag(sqrt(n_i / 2)), i.e. D = sum_i n_i C_i C_i^T
+    and K = -1/2 sum_P sum_i n_i (B^P C_i)(B^P C_i)^T.  None: n_i = 2.
+    sph: labels of sph_labels; every Fock matrix is then replaced by its
+    spherical average (an isolated atom with a spherically symmetric density).
+    occ_l (with sph): the l of each occupied orbital; occupation then follows
+    the configuration instead of the eigenvalue order (occupied_by_l)."""
+    w = None
+    if occ is not None:
+        nocc = len(occ)
+        w = np.sqrt(np.asarray(occ, dtype=np.float64) / 2.0)
     X = canonical_orthogonaliser(S)
-    if C_guess is None:
-        e, Cp = np.linalg.eigh(X.T @ h @ X)
+    def orbitals(Fm):
+        e, Cp = np.linalg.eigh(X.T @ Fm @ X)
         C = X @ Cp
+        if occ_l is not None:
+            C, e = occupied_by_l(C, e, sph, occ_l)
+        return e, C
+
+    if C_guess is None:
+        e, C = orbitals(h)
     else:
         C = np.array(C_guess, dtype=np.float64)
     Fs, Es = [], []
@@ -143,9 +206,11 @@ def scf(h, S, Vnn, nocc, fock_2e, C_guess=None, max_iter=128, conv_e=1e-11, conv
     res = SCFResult()
     res.converged = False
     for it in range(1, max_iter + 1):
-        Co = C[:, :nocc]
+        Co = C[:, :nocc] if w is None else C[:, :nocc] * w
         D = density(Co)
         F = h + fock_2e(Co, D)
+        if sph is not None:
+            F = spherical_average(F, sph)
         E = 0.5 * np.sum(D * (h + F)) + Vnn
         err = X.T @ (F @ D @ S - S @ D @ F) @ X
         Fs.append(F)
@@ -172,15 +237,13 @@ def scf(h, S, Vnn, nocc, fock_2e, C_guess=None, max_iter=128, conv_e=1e-11, conv
             Fx = sum(c * f for c, f in zip(coef, Fs))
         else:
             Fx = F
-        eps, Cp = np.linalg.eigh(X.T @ Fx @ X)
-        C = X @ Cp
+        eps, C = orbitals(Fx)
     else:
         res.iterations = max_iter
     # Final orbitals diagonalise the converged (unextrapolated) Fock matrix.
-    eps, Cp = np.linalg.eigh(X.T @ F @ X)
-    res.C = X @ Cp
+    eps, res.C = orbitals(F)
     res.eps = eps
-    res.D = density(res.C[:, :nocc])
+    res.D = density(res.C[:, :nocc] if w is None else res.C[:, :nocc] * w)
     res.F = F
     res.E = E
     res.max_err = emax

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "../../include/rihf.h"
 #include "linalg.cuh"
 #include "tc_gemm.cuh"
 
@@ -137,9 +138,50 @@ __global__ void splitk_reduce_kernel(GemmArgs g, int nsplit, const double* __res
   }
 }
 
+// The tensor-core route of dgemm (see LaCtx::tcA): op(A) as rows M, K and
+// op(B)^T as rows N, K, both sliced into 7 digits; C stored (beta 0) or
+// accumulated (beta 1).  Returns false when the product does not qualify.
+static bool dgemm_tc(const LaCtx& la, const GemmArgs& g) {
+  if (!la.tcA || !la.tcB || g.batch != 1 || g.reduce_batch || g.lowerA || g.symcols != 0 ||
+      !(g.beta == 0.0 || g.beta == 1.0) || g.K <= 0)
+    return false;
+  if ((double)g.M * g.N * g.K < la.tc_min_work) return false;
+  if ((g.K + kOzChunk - 1) / kOzChunk > kOzMaxChunksPerBlock) return false;
+  auto fits = [](const OzBuf* b, int rows, int K) {
+    return oz_plane_elems(rows, K, kOzMaxDigits) <= b->cap &&
+           (size_t)((rows + kOzTileM - 1) / kOzTileM * kOzTileM) <= b->ecap;
+  };
+  if (!fits(la.tcA, g.M, g.K) || !fits(la.tcB, g.N, g.K)) return false;
+  // element (m, k) of op(A) and (n, k) of op(B)^T
+  OzGemmArgs o;
+  o.A = oz_slice(la, g.A, g.M, g.K, g.transA ? 1 : g.lda, g.transA ? g.lda : 1, 0, g.K, kOzMaxDigits, 0, *la.tcA);
+  o.B = oz_slice(la, g.B, g.N, g.K, g.transB ? g.ldb : 1, g.transB ? 1 : g.ldb, 0, g.K, kOzMaxDigits, 0, *la.tcB);
+  o.M = g.M; o.N = g.N; o.s = kOzMaxDigits; o.alpha = g.alpha; o.C = g.C; o.cs_m1 = g.ldc; o.cs_n = 1;
+  o.accumulate = g.beta == 1.0;
+  o.lower_only = g.lower_only;
+  oz_gemm(la, o);
+  return true;
+}
+
 void dgemm(const LaCtx& la, const GemmArgs& g) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  if (dgemm_tc(la, g)) return;
   int tm = ceil_div(g.M, GT), tn = ceil_div(g.N, GT);
+  if (tm > 65535) {
+    // row tiles run on grid.y (at most 65535): tall products (rows (P, mu) of
+    // Naux N) go in row slabs
+    if (g.batch != 1 || g.reduce_batch || g.lowerA || g.lower_only || g.symcols)
+      throw RihfError(RIHF_ERR_INVALID_ARG, "dgemm: too many row tiles for this product shape");
+    const int slab = 65535 * GT;
+    for (int r0 = 0; r0 < g.M; r0 += slab) {
+      GemmArgs h = g;
+      h.M = std::min(slab, g.M - r0);
+      h.A = g.A + (size_t)r0 * (g.transA ? 1 : g.lda);
+      h.C = g.C + (size_t)r0 * g.ldc;
+      dgemm(la, h);
+    }
+    return;
+  }
   long long tiles = (long long)tm * tn * (g.reduce_batch ? 1 : g.batch);
   int nsplit = 1, kper = g.K, bper = g.batch;
   const long long target = 4LL * la.sms;
@@ -1162,18 +1204,28 @@ __global__ void eig_sort64_kernel(const double* __restrict__ V, const double* __
 
 // ------------------------------------------------------------ block Jacobi (large n)
 //
-// Two-sided cyclic Jacobi in FP32 for orders above kBlockJacobiMin, spread over
-// many CTAs.  The (padded) indices form nb = np / kBJW blocks; a sweep is nb - 1
-// rounds of the round-robin pairing of blocks (block 0 fixed, the others
-// circulating); in a round every block pair -- one CTA -- diagonalises its
-// 2 kBJW x 2 kBJW submatrix by one cyclic sweep of plane rotations, giving Q;
-// then all pairs' columns are rotated (A <- A Q, V <- V Q) and, after them, all
-// rows (A <- Q^T A).  Pairs own disjoint rows and columns, so the three launches
-// of a round are the only synchronisation.  Padding indices (n..np) have zero
-// coupling and are never rotated.  After each sweep the squared off-diagonal
-// norm over the real indices is folded in a fixed order and compared with
-// tol^2 times the diagonal's; a device flag then turns the remaining launches
-// into no-ops (no host synchronisation, so the sweeps can sit in a CUDA graph).
+// Two-sided cyclic Jacobi for orders above kBlockJacobiMin, spread over many
+// CTAs, in FP32 (fast, to ~1e-6 of the norm) and then in FP64 from the FP32
+// vectors (a few quadratically convergent sweeps).  The FP64 stage is what
+// resolves the small end of a spectrum spanning many orders of magnitude: an
+// overlap matrix with eigenvalues down to 3e-9 (the canonical orthogonaliser
+// must drop those below 1e-8), or the orthonormal-basis Fock matrix built from
+// it, whose near-dependent directions lie at ~1e8 Eh while the occupied ones,
+// a few Eh apart, are all that the SCF needs: FP32 rounding of such a matrix
+// is larger than the occupied spectrum.
+//
+// The (padded) indices form nb = np / kBJW blocks; a sweep is nb - 1 rounds of
+// the round-robin pairing of blocks (block 0 fixed, the others circulating); in
+// a round every block pair -- one CTA -- diagonalises its 2 kBJW x 2 kBJW
+// submatrix by one cyclic sweep of plane rotations and a Newton-Schulz step,
+// giving Q; then all pairs' columns are rotated (A <- A Q, V <- V Q) and, after
+// them, all rows (A <- Q^T A).  Pairs own disjoint rows and columns, so the
+// three launches of a round are the only synchronisation.  Padding indices
+// (n..np) have zero coupling and are never rotated.  After each sweep the
+// squared off-diagonal norm over the real indices is folded in a fixed order
+// and compared with tol^2 times the diagonal's; a device flag then turns the
+// remaining launches into no-ops (no host synchronisation, so the sweeps can
+// sit in a CUDA graph).
 constexpr int kBJW = 16, kBJ2 = 2 * kBJW, kBJParts = 256;
 
 __device__ inline int bj_index(int pair, int k, int round, int nb) {
@@ -1182,22 +1234,27 @@ __device__ inline int bj_index(int pair, int k, int round, int nb) {
   return blk * kBJW + (k % kBJW);
 }
 
-__global__ void bj_init_kernel(const double* __restrict__ A, int n, int np, float* __restrict__ A32,
-                               float* __restrict__ V32, int* done) {
+__device__ inline float bj_sqrt(float x) { return sqrtf(x); }
+__device__ inline double bj_sqrt(double x) { return sqrt(x); }
+
+template <class T>
+__global__ void bj_init_kernel(const double* __restrict__ A, int n, int np, T* __restrict__ At, T* __restrict__ Vt,
+                               int* done) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)np * np;
        e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e / np), j = (int)(e % np);
-    A32[e] = (i < n && j < n) ? (float)A[(size_t)i * n + j] : 0.f;
-    V32[e] = i == j ? 1.f : 0.f;
+    At[e] = (i < n && j < n) ? (T)A[(size_t)i * n + j] : (T)0;
+    Vt[e] = i == j ? (T)1 : (T)0;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *done = 0;
 }
 
-__global__ void __launch_bounds__(256) bj_solve_kernel(const float* __restrict__ A, int np, int round, int nb,
-                                                       float* __restrict__ Qg, const int* done) {
+template <class T>
+__global__ void __launch_bounds__(256) bj_solve_kernel(const T* __restrict__ A, int np, int round, int nb,
+                                                       T* __restrict__ Qg, const int* done) {
   if (*done) return;
-  __shared__ float S[kBJ2][kBJ2 + 1], Q[kBJ2][kBJ2 + 1];
-  __shared__ float cs[kBJW], sn[kBJW];
+  __shared__ T S[kBJ2][kBJ2 + 1], Q[kBJ2][kBJ2 + 1];
+  __shared__ T cs[kBJW], sn[kBJW];
   __shared__ int ra[kBJW], rb[kBJW], idx[kBJ2];
   const int pair = blockIdx.x, t = threadIdx.x;
   if (t < kBJ2) idx[t] = bj_index(pair, t, round, nb);
@@ -1205,7 +1262,7 @@ __global__ void __launch_bounds__(256) bj_solve_kernel(const float* __restrict__
   for (int e = t; e < kBJ2 * kBJ2; e += blockDim.x) {
     const int i = e / kBJ2, j = e % kBJ2;
     S[i][j] = A[(size_t)idx[i] * np + idx[j]];
-    Q[i][j] = i == j ? 1.f : 0.f;
+    Q[i][j] = i == j ? (T)1 : (T)0;
   }
   __syncthreads();
   // one cyclic sweep over the 2w indices: 2w - 1 rounds of w disjoint rotations
@@ -1214,13 +1271,13 @@ __global__ void __launch_bounds__(256) bj_solve_kernel(const float* __restrict__
       int a = t == 0 ? 0 : 1 + (t - 1 + r) % (kBJ2 - 1);
       int b = 1 + (kBJ2 - 2 - t + r) % (kBJ2 - 1);   // position 2w - 1 - t
       if (a > b) { const int x = a; a = b; b = x; }
-      const float app = S[a][a], aqq = S[b][b], apq = S[a][b];
-      float c = 1.f, s = 0.f;
-      if (apq != 0.f) {
+      const T app = S[a][a], aqq = S[b][b], apq = S[a][b];
+      T c = 1, s = 0;
+      if (apq != (T)0) {
         // symmetric Schur rotation: J = [c s; -s c] zeroes the (a, b) entry of J^T S J
-        const float th = (aqq - app) / (2.f * apq);
-        const float tt = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
-        c = rsqrtf(fmaf(tt, tt, 1.f));
+        const T th = (aqq - app) / (2 * apq);
+        const T tt = (th >= 0 ? (T)1 : (T)-1) / (fabs(th) + bj_sqrt(th * th + 1));
+        c = 1 / bj_sqrt(tt * tt + 1);
         s = tt * c;
       }
       cs[t] = c; sn[t] = s; ra[t] = a; rb[t] = b;
@@ -1228,61 +1285,63 @@ __global__ void __launch_bounds__(256) bj_solve_kernel(const float* __restrict__
     __syncthreads();
     for (int e = t; e < kBJW * kBJ2; e += blockDim.x) {   // S <- S J, Q <- Q J (columns a, b)
       const int k = e / kBJ2, i = e % kBJ2, a = ra[k], b = rb[k];
-      const float c = cs[k], s = sn[k];
-      const float x = S[i][a], y = S[i][b];
+      const T c = cs[k], s = sn[k];
+      const T x = S[i][a], y = S[i][b];
       S[i][a] = c * x - s * y;
       S[i][b] = s * x + c * y;
-      const float u = Q[i][a], v = Q[i][b];
+      const T u = Q[i][a], v = Q[i][b];
       Q[i][a] = c * u - s * v;
       Q[i][b] = s * u + c * v;
     }
     __syncthreads();
     for (int e = t; e < kBJW * kBJ2; e += blockDim.x) {   // S <- J^T S (rows a, b)
       const int k = e / kBJ2, j = e % kBJ2, a = ra[k], b = rb[k];
-      const float c = cs[k], s = sn[k];
-      const float x = S[a][j], y = S[b][j];
+      const T c = cs[k], s = sn[k];
+      const T x = S[a][j], y = S[b][j];
       S[a][j] = c * x - s * y;
       S[b][j] = s * x + c * y;
     }
     __syncthreads();
   }
   // one Newton-Schulz step, Q <- Q (3 I - Q^T Q) / 2: the 496 rotations leave Q
-  // orthogonal to ~1e-6 only, and V multiplies about a thousand such blocks
+  // orthogonal to a few hundred rounding units only, and V multiplies about a
+  // thousand such blocks
   for (int e = t; e < kBJ2 * kBJ2; e += blockDim.x) {   // S <- (3 I - Q^T Q) / 2
     const int i = e / kBJ2, j = e % kBJ2;
-    float g = 0.f;
-    for (int k = 0; k < kBJ2; ++k) g = fmaf(Q[k][i], Q[k][j], g);
-    S[i][j] = 0.5f * ((i == j ? 3.f : 0.f) - g);
+    T g = 0;
+    for (int k = 0; k < kBJ2; ++k) g += Q[k][i] * Q[k][j];
+    S[i][j] = (T)0.5 * ((i == j ? (T)3 : (T)0) - g);
   }
   __syncthreads();
-  float* q = Qg + (size_t)pair * kBJ2 * kBJ2;
+  T* q = Qg + (size_t)pair * kBJ2 * kBJ2;
   for (int e = t; e < kBJ2 * kBJ2; e += blockDim.x) {
     const int i = e / kBJ2, j = e % kBJ2;
-    float v = 0.f;
-    for (int k = 0; k < kBJ2; ++k) v = fmaf(Q[i][k], S[k][j], v);
+    T v = 0;
+    for (int k = 0; k < kBJ2; ++k) v += Q[i][k] * S[k][j];
     q[e] = v;
   }
 }
 
 // A[r][idx] <- A[r][idx] Q and V[r][idx] <- V[r][idx] Q for every row r: one
-// warp per row, lane k holds entry idx[k] (two 64-byte segments per row).
-__global__ void __launch_bounds__(256) bj_cols_kernel(float* __restrict__ A, float* __restrict__ V, int np, int round,
-                                                      int nb, const float* __restrict__ Qg, const int* done) {
+// warp per row, lane k holds entry idx[k] (two contiguous segments per row).
+template <class T>
+__global__ void __launch_bounds__(256) bj_cols_kernel(T* __restrict__ A, T* __restrict__ V, int np, int round, int nb,
+                                                      const T* __restrict__ Qg, const int* done) {
   if (*done) return;
-  __shared__ float Q[kBJ2][kBJ2 + 1];
+  __shared__ T Q[kBJ2][kBJ2 + 1];
   const int pair = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float* q = Qg + (size_t)pair * kBJ2 * kBJ2;
+  const T* q = Qg + (size_t)pair * kBJ2 * kBJ2;
   for (int e = threadIdx.x; e < kBJ2 * kBJ2; e += blockDim.x) Q[e / kBJ2][e % kBJ2] = q[e];
   __syncthreads();
   const int col = bj_index(pair, lane, round, nb);
   for (int r = blockIdx.y * 8 + warp; r < np; r += gridDim.y * 8) {
-    float x = A[(size_t)r * np + col], y = 0.f;
-    float u = V[(size_t)r * np + col], w = 0.f;
+    T x = A[(size_t)r * np + col], y = 0;
+    T u = V[(size_t)r * np + col], w = 0;
 #pragma unroll
     for (int m = 0; m < kBJ2; ++m) {
-      const float qm = Q[m][lane];
-      y = fmaf(__shfl_sync(0xffffffffu, x, m), qm, y);
-      w = fmaf(__shfl_sync(0xffffffffu, u, m), qm, w);
+      const T qm = Q[m][lane];
+      y += __shfl_sync(0xffffffffu, x, m) * qm;
+      w += __shfl_sync(0xffffffffu, u, m) * qm;
     }
     A[(size_t)r * np + col] = y;
     V[(size_t)r * np + col] = w;
@@ -1290,26 +1349,27 @@ __global__ void __launch_bounds__(256) bj_cols_kernel(float* __restrict__ A, flo
 }
 
 // A[idx][c] <- Q^T A[idx][c] for every column c: one thread per column holds
-// the 2w entries of its column (coalesced across the warp).
-__global__ void __launch_bounds__(128) bj_rows_kernel(float* __restrict__ A, int np, int round, int nb,
-                                                      const float* __restrict__ Qg, const int* done) {
+// the 2w results of its column (coalesced across the warp).
+template <class T>
+__global__ void __launch_bounds__(128) bj_rows_kernel(T* __restrict__ A, int np, int round, int nb,
+                                                      const T* __restrict__ Qg, const int* done) {
   if (*done) return;
-  __shared__ float Q[kBJ2][kBJ2 + 1];
+  __shared__ T Q[kBJ2][kBJ2 + 1];
   __shared__ int idx[kBJ2];
   const int pair = blockIdx.x;
-  const float* q = Qg + (size_t)pair * kBJ2 * kBJ2;
+  const T* q = Qg + (size_t)pair * kBJ2 * kBJ2;
   for (int e = threadIdx.x; e < kBJ2 * kBJ2; e += blockDim.x) Q[e / kBJ2][e % kBJ2] = q[e];
   if (threadIdx.x < kBJ2) idx[threadIdx.x] = bj_index(pair, threadIdx.x, round, nb);
   __syncthreads();
   for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < np; c += gridDim.y * blockDim.x) {
-    float o[kBJ2];
+    T o[kBJ2];
 #pragma unroll
-    for (int l = 0; l < kBJ2; ++l) o[l] = 0.f;
+    for (int l = 0; l < kBJ2; ++l) o[l] = 0;
 #pragma unroll 1
     for (int m = 0; m < kBJ2; ++m) {   // kept rolled: unrolled, the 1024 FMAs spill the outputs
-      const float zm = A[(size_t)idx[m] * np + c];
+      const T zm = A[(size_t)idx[m] * np + c];
 #pragma unroll
-      for (int l = 0; l < kBJ2; ++l) o[l] = fmaf(Q[m][l], zm, o[l]);
+      for (int l = 0; l < kBJ2; ++l) o[l] += Q[m][l] * zm;
     }
 #pragma unroll
     for (int l = 0; l < kBJ2; ++l) A[(size_t)idx[l] * np + c] = o[l];
@@ -1317,7 +1377,8 @@ __global__ void __launch_bounds__(128) bj_rows_kernel(float* __restrict__ A, int
 }
 
 // Squared off-diagonal and diagonal norms over the real indices, per block.
-__global__ void __launch_bounds__(256) bj_norm_kernel(const float* __restrict__ A, int n, int np, double* part,
+template <class T>
+__global__ void __launch_bounds__(256) bj_norm_kernel(const T* __restrict__ A, int n, int np, double* part,
                                                       const int* done) {
   if (*done) return;
   __shared__ double r0[8], r1[8];
@@ -1350,22 +1411,29 @@ __global__ void bj_check_kernel(const double* part, int nparts, double tol2, int
   if (a <= tol2 * b) *done = 1;
 }
 
-// Diagonal of the rotated matrix (the eigenvalue estimates) for the sort.
-__global__ void bj_diag_kernel(const float* __restrict__ A, int n, int np, float* __restrict__ w) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) w[i] = A[(size_t)i * np + i];
+// FP64 copies of the real block: Vd (n x n) and the diagonal lam (n).
+template <class T>
+__global__ void bj_extract_kernel(const T* __restrict__ A, const T* __restrict__ V, int n, int np,
+                                  double* __restrict__ Vd, double* __restrict__ lam) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    Vd[e] = (double)V[(size_t)i * np + j];
+    if (i == j) lam[i] = (double)A[(size_t)i * np + i];
+  }
 }
 
-// FP32 eigenpairs of the n x n FP64 matrix Ain into V (FP64, sorted) and W.
-static void block_jacobi(const LaCtx& la, const double* Ain, int n, double* V, double* W, double* bjws,
-                         int max_sweeps, float tol) {
+// Unsorted eigenpairs of the n x n FP64 matrix Ain: Vd (n x n, FP64) and lam.
+template <class T>
+static void block_jacobi(const LaCtx& la, const double* Ain, int n, double* Vd, double* lam, double* bjws,
+                         int max_sweeps, double tol) {
   const int np = (n + kBJ2 - 1) / kBJ2 * kBJ2, nb = np / kBJW, npair = nb / 2;
-  float* A32 = reinterpret_cast<float*>(bjws);
-  float* V32 = A32 + (size_t)np * np;
-  float* Qg = V32 + (size_t)np * np;
-  float* W32 = Qg + (size_t)npair * kBJ2 * kBJ2;
-  double* part = bjws + (2 * (size_t)np * np + (size_t)npair * kBJ2 * kBJ2 + np + 1) / 2;
+  T* At = reinterpret_cast<T*>(bjws);
+  T* Vt = At + (size_t)np * np;
+  T* Qg = Vt + (size_t)np * np;
+  double* part = bjws + 2 * (size_t)np * np + (size_t)npair * kBJ2 * kBJ2;
   int* done = reinterpret_cast<int*>(part + 2 * kBJParts);
-  bj_init_kernel<<<elem_blocks(la, (long long)np * np), 256, 0, la.stream>>>(Ain, n, np, A32, V32, done);
+  bj_init_kernel<T><<<elem_blocks(la, (long long)np * np), 256, 0, la.stream>>>(Ain, n, np, At, Vt, done);
   RIHF_LAUNCH_CHECK();
   count(la);
   const int rowblk = std::max(1, std::min(ceil_div(np, 8), 4 * la.sms / std::max(1, npair)));
@@ -1373,21 +1441,54 @@ static void block_jacobi(const LaCtx& la, const double* Ain, int n, double* V, d
   const int nparts = std::min(kBJParts, ceil_div(n * n, 256));
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int r = 0; r < nb - 1; ++r) {
-      bj_solve_kernel<<<npair, 256, 0, la.stream>>>(A32, np, r, nb, Qg, done);
-      bj_cols_kernel<<<dim3(npair, rowblk), 256, 0, la.stream>>>(A32, V32, np, r, nb, Qg, done);
-      bj_rows_kernel<<<dim3(npair, colblk), 128, 0, la.stream>>>(A32, np, r, nb, Qg, done);
+      bj_solve_kernel<T><<<npair, 256, 0, la.stream>>>(At, np, r, nb, Qg, done);
+      bj_cols_kernel<T><<<dim3(npair, rowblk), 256, 0, la.stream>>>(At, Vt, np, r, nb, Qg, done);
+      bj_rows_kernel<T><<<dim3(npair, colblk), 128, 0, la.stream>>>(At, np, r, nb, Qg, done);
       RIHF_LAUNCH_CHECK();
       count(la, 3);
     }
-    bj_norm_kernel<<<nparts, 256, 0, la.stream>>>(A32, n, np, part, done);
-    bj_check_kernel<<<1, 1, 0, la.stream>>>(part, nparts, (double)tol * tol, done);
+    bj_norm_kernel<T><<<nparts, 256, 0, la.stream>>>(At, n, np, part, done);
+    bj_check_kernel<<<1, 1, 0, la.stream>>>(part, nparts, tol * tol, done);
     RIHF_LAUNCH_CHECK();
     count(la, 2);
   }
-  bj_diag_kernel<<<std::max(1, ceil_div(n, 256)), 256, 0, la.stream>>>(A32, n, np, W32);
-  eig_sort_kernel<<<std::min(n, 32), 256, 0, la.stream>>>(V32, W32, n, np, V, W);
+  bj_extract_kernel<T><<<elem_blocks(la, (long long)n * n), 256, 0, la.stream>>>(At, Vt, n, np, Vd, lam);
   RIHF_LAUNCH_CHECK();
-  count(la, 2);
+  count(la);
+}
+
+// Both stages for order n > kBlockJacobiMin: sorted eigenpairs (V, W) of Ain.
+// FP32 sweeps to tol32, one FP64 Newton-Schulz step on the vectors, then FP64
+// sweeps on Vs^T Ain Vs (nearly diagonal) to 1e-13 and V = Vs V2.  Scratch:
+// the refinement slots R, S, AX, E, XE of the eigh workspace.
+static void block_jacobi_2stage(const LaCtx& la, const double* Ain, int n, double* V, double* W, double* bjws,
+                                int max_sweeps, float tol32, double* R, double* S, double* AX, double* E,
+                                double* XE, double* lam) {
+  block_jacobi<float>(la, Ain, n, XE, lam, bjws, max_sweeps, tol32);
+  // XE holds the FP32 vectors (orthogonal to ~1e-6): Newton-Schulz, then
+  // E = Vs^T Ain Vs and the FP64 sweeps
+  GemmArgs gr;
+  gr.M = n; gr.N = n; gr.K = n; gr.A = XE; gr.lda = n; gr.transA = true; gr.B = XE; gr.ldb = n; gr.C = R; gr.ldc = n;
+  gr.alpha = -0.5;
+  dgemm(la, gr);
+  identity(la, S, n);
+  axpby(la, n * n, 1.0, R, 1.5, S, R);   // R = (3 I - Vs^T Vs) / 2
+  GemmArgs gn;
+  gn.M = n; gn.N = n; gn.K = n; gn.A = XE; gn.lda = n; gn.B = R; gn.ldb = n; gn.C = S; gn.ldc = n;
+  dgemm(la, gn);                          // S = Vs (orthonormal to ~1e-12)
+  GemmArgs ga;
+  ga.M = n; ga.N = n; ga.K = n; ga.A = Ain; ga.lda = n; ga.B = S; ga.ldb = n; ga.C = AX; ga.ldc = n;
+  dgemm(la, ga);
+  GemmArgs gs;
+  gs.M = n; gs.N = n; gs.K = n; gs.A = S; gs.lda = n; gs.transA = true; gs.B = AX; gs.ldb = n; gs.C = E; gs.ldc = n;
+  dgemm(la, gs);
+  block_jacobi<double>(la, E, n, R, lam, bjws, 6, 1e-13);
+  GemmArgs gv;
+  gv.M = n; gv.N = n; gv.K = n; gv.A = S; gv.lda = n; gv.B = R; gv.ldb = n; gv.C = XE; gv.ldc = n;
+  dgemm(la, gv);
+  eig_sort64_kernel<<<std::min(n, 32), 256, 0, la.stream>>>(XE, lam, n, V, W);
+  RIHF_LAUNCH_CHECK();
+  count(la);
 }
 
 void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double* ws, int refine,
@@ -1441,7 +1542,7 @@ void eigh(const LaCtx& la, const double* A, int n, double* W, double* V, double*
   const float tol = 2e-6f;
   const int hb = (n + kJB - 1) / kJB;   // block width of the block kernel
   if (n > kBlockJacobiMin) {
-    block_jacobi(la, Ain, n, V, W, ws + eig_workspace_base(n), max_sweeps, tol);
+    block_jacobi_2stage(la, Ain, n, V, W, ws + eig_workspace_base(n), max_sweeps, tol, R, S, AX, E, XE, lam);
   } else {
   if (hb <= 3) {
     const void* fn = hb == 1 ? (const void*)jacobi1s_block_kernel<1>

@@ -15,6 +15,14 @@ struct LaCtx {
   int sms = 152;
   int* flag = nullptr;          // device error flag (non-positive pivot, ...)
   int* sched = nullptr;         // two ints, zero between launches: work counter of the tensor-core GEMM
+  // Optional: digit-plane scratch for the two operands.  When set, dgemm runs
+  // unbatched products with beta 0 or 1 and at least tc_min_work M N K on the
+  // tensor cores with 7 BF16 digits (FP64-class: 55 bits of each row's and
+  // column's largest element), as long as K fits one exponent block and the
+  // operands fit the scratch; everything else stays FP64 DFMA.
+  const OzBuf* tcA = nullptr;
+  const OzBuf* tcB = nullptr;
+  double tc_min_work = 0.0;
 };
 
 // C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b] for b < batch.
@@ -120,11 +128,10 @@ constexpr size_t eig_workspace_base(int n) {
   return ((size_t)(n + (n & 1)) * (n + (n & 1)) + (size_t)n * (n + (n & 1)) + (n + (n & 1)) + 1) / 2 +
          6 * (size_t)n * n + 2 * (size_t)n + 8;
 }
-constexpr size_t eig_workspace_bj(int n) {
+constexpr size_t eig_workspace_bj(int n) {   // FP64 matrices, rotations, partials, flag (the FP32 stage fits)
   return n <= kBlockJacobiMin ? 0
-                              : (2 * (size_t)((n + 31) / 32 * 32) * ((n + 31) / 32 * 32) +
-                                 (size_t)((n + 31) / 32) * 32 * 32 + (size_t)((n + 31) / 32 * 32) + 1) / 2 +
-                                    2 * 256 + 16;
+                              : 2 * (size_t)((n + 31) / 32 * 32) * ((n + 31) / 32 * 32) +
+                                    (size_t)((n + 31) / 32) * 32 * 32 + 2 * 256 + 16;
 }
 constexpr size_t eig_workspace(int n) { return eig_workspace_base(n) + eig_workspace_bj(n); }
 // skip_jacobi: start the refinement from Vguess directly (late SCF iterations).

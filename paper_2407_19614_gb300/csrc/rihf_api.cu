@@ -142,6 +142,7 @@ struct HostShells {
   int nshell = 0, nfunc = 0, lmax = 0;
   std::vector<int> l, atom, nprim, pstart, ao;
   std::vector<double> exps, coefs;
+  std::vector<double> raw_coefs;   // the caller's coefficients (before normalisation)
 };
 
 // Primitive normalisation of x^l e^{-a r^2} times the caller's coefficient,
@@ -179,6 +180,7 @@ int build_host_shells(int n, const rihf_shell* sh, int natoms, int lmax_allowed,
     for (int k = 0; k < x.nprim; ++k) {
       out.exps.push_back(x.exps[k]);
       out.coefs.push_back(c[k] * f);
+      out.raw_coefs.push_back(x.coefs[k]);
     }
   }
   out.nfunc = ao;
@@ -533,6 +535,10 @@ struct rihf_ctx {
   // tensor-core gradient GEMMs (mixed mode): planes of C~ as a B operand
   // (rows N, K = nocc), of G' (rows Naux N, K = nocc) and of X~ (rows Naux, K = nocc^2)
   OzBuf Ctz, Gz, Xz;
+  // mixed mode, N > 256: operand planes for the dense N^3 products routed to
+  // the tensor cores by dgemm (DIIS error, orthogonalisation, eigenvector
+  // refinement), see LaCtx::tcA
+  OzBuf tcA, tcB;
   int tc_builds = 0, confirm_builds = 0, last_iters = 0, last_digits = 0;
   double flops_eri3 = 0.0, flops_grad3 = 0.0;   // algorithmic FP64 operations of the 3-centre kernels
   int k_nsplit = 0;             // K splits of the tensor-core K GEMM (0: not tuned yet)
@@ -579,6 +585,23 @@ struct rihf_ctx {
   double* eigws = nullptr;
   double* scratch = nullptr;
 
+  // Occupations: empty = closed shell (2 per occupied orbital, C~ = sqrt(2) C_occ);
+  // otherwise n_i per occupied column (C~ = C_occ diag(sqrt(n_i))), as for the
+  // spherically averaged atoms of the SAD guess
+  std::vector<double> occ;
+  double* d_occw = nullptr;
+  // SAD guess (guess 5): block-diagonal factor Fs (N x sad_m) of the
+  // superposition of atomic densities, D_SAD = Fs Fs^T, built on first use
+  double* d_sad = nullptr;
+  int sad_m = 0;
+  // SAD atoms (spherical basis): every Fock matrix is replaced by its spherical
+  // average (per function: first function of its shell, l, m index)
+  bool sph_avg = false;
+  int *d_fao0 = nullptr, *d_fl = nullptr, *d_fm = nullptr;
+  std::vector<int> fl_h;     // l of every basis function (host)
+  std::vector<int> occ_l;    // l of each occupied orbital: occupation by configuration, not eigenvalue order
+  bool sad_built = false, sad_ok = false;
+  std::string sad_note;
   bool converged = false;
   bool have_orbitals = false;
   bool verbose = getenv("RIHF_VERBOSE") != nullptr;
@@ -598,6 +621,11 @@ struct rihf_ctx {
     l.sms = sms;
     l.flag = d_flag;
     l.sched = d_sched;
+    if (tcA.planes) {
+      l.tcA = &tcA;
+      l.tcB = &tcB;
+      l.tc_min_work = 256.0 * 256.0 * 256.0;
+    }
     return l;
   }
   IntegralCtx ic() const {
@@ -677,10 +705,12 @@ static void free_all(rihf_ctx* c) {
                   c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->Bp, c->Yp, c->Bu, c->Dp, c->Jp, c->Xo, c->Sw, c->Sv,
                   c->C, c->eps, c->Ct, c->D, c->J, c->K, c->F, c->Fx, c->T1, c->T2, c->Err, c->Fp, c->Cp, c->Hb,
                   c->dvec, c->Fring, c->Ering, c->Bdiis, c->coef, c->scal, c->Cprev,
-                  c->na2tmp, c->trsm_tmp, c->cvec, c->W, c->Bij, c->Xt, c->Zm, c->grad_parts, c->work, c->eigws, c->scratch};
+                  c->na2tmp, c->trsm_tmp, c->cvec, c->W, c->Bij, c->Xt, c->Zm, c->grad_parts, c->work, c->eigws, c->scratch,
+                  c->d_occw, c->d_sad, c->d_fao0, c->d_fl, c->d_fm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  for (OzBuf* b : {&c->Bz, &c->Cz, &c->Hz, &c->Ctz, &c->Gz, &c->Xz, &c->trsm_sc.L, &c->trsm_sc.X}) oz_buf_free(*b);
+  for (OzBuf* b : {&c->Bz, &c->Cz, &c->Hz, &c->Ctz, &c->Gz, &c->Xz, &c->trsm_sc.L, &c->trsm_sc.X, &c->tcA, &c->tcB})
+    oz_buf_free(*b);
 }
 
 // Geometry-dependent part of setup: shell centres, one-electron, metric,
@@ -805,6 +835,10 @@ static void compute_geometry(rihf_ctx* c) {
     if (k0 == N) throw RihfError(RIHF_ERR_NOT_POSITIVE_DEFINITE, "overlap matrix has no eigenvalue above lindep_tau");
   }
   int nind = N - k0;
+  if (c->verbose || getenv("RIHF_VERBOSE"))
+    fprintf(stderr, "rihf: orthogonaliser %s, %d of %d functions kept%s\n",
+            chol_ok ? "L_S^-T (Cholesky bound proves nothing would be dropped)" : "canonical", nind, N,
+            chol_ok ? "" : (" (smallest kept overlap eigenvalue " + std::to_string(sw.empty() ? 0.0 : sw[k0]) + ")").c_str());
   if (c->nind != 0 && nind != c->nind) {
     c->have_cprev = false;
     for (auto* arr : {c->graphs, c->diag_graphs}) {   // captured work assumes the old basis size
@@ -913,15 +947,14 @@ const char* rihf_last_error(void) { return g_last_error.c_str(); }
     return RIHF_ERR_INVALID_ARG;                      \
   }
 
-int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, const rihf_shell* prim,
-               int naux_shells, const rihf_shell* aux, int nelec, const rihf_options* opt, rihf_ctx** out) {
-  RIHF_API_BEGIN
-  if (!out || natoms <= 0 || !Z || !xyz || nprim_shells <= 0 || !prim || naux_shells <= 0 || !aux || nelec <= 0 ||
-      (nelec & 1)) {
-    g_last_error = "invalid sizes or pointers (nelec must be positive and even)";
-    return RIHF_ERR_INVALID_ARG;
-  }
-  *out = nullptr;
+}  // extern "C"
+
+// Context construction.  occ: occupation numbers of the nocc = occ->size()
+// lowest orbitals (spherically averaged atoms of the SAD guess), or NULL for
+// the closed shell with nelec / 2 doubly occupied orbitals.
+static rihf_ctx* setup_impl(int natoms, const int* Z, const double* xyz, int nprim_shells, const rihf_shell* prim,
+                            int naux_shells, const rihf_shell* aux, int nelec, const rihf_options* opt,
+                            const std::vector<double>* occ) {
   rihf_ctx* c = new rihf_ctx();
   if (opt) c->opt = *opt; else rihf_default_options(&c->opt);
   if (c->opt.diis_size < 2) c->opt.diis_size = 2;
@@ -933,7 +966,7 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     for (auto& e : c->ev) RIHF_CUDA(cudaEventCreate(&e));
     c->natoms = natoms;
     c->nelec = nelec;
-    c->nocc = nelec / 2;
+    c->nocc = occ ? (int)occ->size() : nelec / 2;
     c->Z.assign(Z, Z + natoms);
     c->xyz.assign(xyz, xyz + 3 * natoms);
     build_transforms(c->opt.pure != 0, c->tr_h, c->nf_h);
@@ -1039,6 +1072,10 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
       c->Ctz = oz_buf_alloc(N, no, kOzMaxDigits, 1);
       const int xch = (no * no + kOzChunk - 1) / kOzChunk;
       c->Xz = oz_buf_alloc(NA, no * no, kOzMaxDigits, (xch + kOzMaxChunksPerBlock - 1) / kOzMaxChunksPerBlock);
+      if (N > 256) {
+        c->tcA = oz_buf_alloc(std::max(N, NA), N, kOzMaxDigits, 1);
+        c->tcB = oz_buf_alloc(std::max(N, NA), N, kOzMaxDigits, 1);
+      }
     }
     c->trsm_tmp = dalloc<double>(32 * std::max<size_t>({(size_t)c->npp, (size_t)NA, (size_t)c->nocc * c->nocc}) + 1024);
     {   // guess history and learned-guess buffers
@@ -1101,6 +1138,13 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
         c->planes_all = pc == NA;
       }
     }
+    if (occ) {
+      c->occ = *occ;
+      std::vector<double> w(occ->size());
+      for (size_t k = 0; k < w.size(); ++k) w[k] = std::sqrt((*occ)[k]);
+      c->d_occw = dalloc<double>(w.size());
+      upload(c->d_occw, w, s);
+    }
     compute_geometry(c);
   } catch (...) {
     free_all(c);
@@ -1108,7 +1152,21 @@ int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, co
     delete c;
     throw;
   }
-  *out = c;
+  return c;
+}
+
+extern "C" {
+
+int rihf_setup(int natoms, const int* Z, const double* xyz, int nprim_shells, const rihf_shell* prim,
+               int naux_shells, const rihf_shell* aux, int nelec, const rihf_options* opt, rihf_ctx** out) {
+  RIHF_API_BEGIN
+  if (!out || natoms <= 0 || !Z || !xyz || nprim_shells <= 0 || !prim || naux_shells <= 0 || !aux || nelec <= 0 ||
+      (nelec & 1)) {
+    g_last_error = "invalid sizes or pointers (nelec must be positive and even)";
+    return RIHF_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  *out = setup_impl(natoms, Z, xyz, nprim_shells, prim, naux_shells, aux, nelec, opt, nullptr);
   return RIHF_OK;
   RIHF_API_END
 }
@@ -1176,6 +1234,8 @@ static void graph_or_eager(rihf_ctx* c, rihf_ctx::IterGraph& g, const char* name
   c->launches += g.launches;
 }
 }  // extern "C++"
+
+static void occupy_by_l(rihf_ctx* c);
 
 static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
   LaCtx la = c->la();
@@ -1269,6 +1329,34 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
   GemmArgs g3;
   g3.M = N; g3.N = n; g3.K = n; g3.A = c->Xo; g3.lda = n; g3.B = c->Cp; g3.ldb = n; g3.C = c->C; g3.ldc = N;
   dgemm(la, g3);
+  if (c->sph_avg && !c->occ_l.empty()) occupy_by_l(c);
+}
+
+// Spherical average of a matrix over real solid harmonics: zero between
+// different l or m, and for equal l and m the mean over m of the shell pair's
+// (m, m) entries (the rotation average, exact for the Fock operator of a
+// spherically symmetric density).
+__global__ void sph_avg_kernel(const double* __restrict__ F, int N, const int* __restrict__ ao0,
+                               const int* __restrict__ fl, const int* __restrict__ fm, double* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)N * N;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    double v = 0.0;
+    if (fl[i] == fl[j] && fm[i] == fm[j]) {
+      const int l = fl[i];
+      for (int m = 0; m <= 2 * l; ++m) v += F[(size_t)(ao0[i] + m) * N + ao0[j] + m];
+      v /= (2 * l + 1);
+    }
+    out[e] = v;
+  }
+}
+
+// C~ = C_occ diag(sqrt(n_i)): sqrt(2) C_occ for the closed shell (D = C~ C~^T).
+static void form_Ct(rihf_ctx* c) {
+  LaCtx la = c->la();
+  const int N = c->N, no = c->nocc;
+  copy_cols(la, c->C, N, N, no, c->d_occw ? 1.0 : std::sqrt(2.0), c->Ct);
+  if (c->d_occw) scale_cols(la, c->Ct, c->d_occw, N, no, c->Ct);
 }
 
 // RI-J (Eq. j_ri) over the pair-packed B: d_P = sum_{mu >= nu} w B^P D (w = 2
@@ -1334,7 +1422,7 @@ static void fock_build(rihf_ctx* c) {
   const int N = c->N, NA = c->NA, no = c->nocc;
   const size_t n2 = (size_t)N * N;
   // Ct = sqrt(2) C[:, :nocc]; D = Ct Ct^T
-  copy_cols(la, c->C, N, N, no, std::sqrt(2.0), c->Ct);
+  form_Ct(c);
   GemmArgs gd;
   gd.M = N; gd.N = N; gd.K = no; gd.A = c->Ct; gd.lda = no; gd.B = c->Ct; gd.ldb = no; gd.transB = true;
   gd.C = c->D; gd.ldc = N;
@@ -1351,6 +1439,13 @@ static void fock_build(rihf_ctx* c) {
     dgemm(la, gk);
     symmetrize_lower(la, c->K, N, 1); }
   add3(la, (int)n2, c->H, c->J, c->K, c->F);
+  if (c->sph_avg) {
+    sph_avg_kernel<<<std::max(1, std::min(ceil_div((long long)n2, 256), 8 * c->sms)), 256, 0, c->stream>>>(
+        c->F, N, c->d_fao0, c->d_fl, c->d_fm, c->T1);
+    RIHF_LAUNCH_CHECK();
+    RIHF_CUDA(cudaMemcpyAsync(c->F, c->T1, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
+    c->launches += 1;
+  }
   energy_mb_kernel<<<kRedBlocks, 256, 0, c->stream>>>(c->D, c->H, c->F, (long long)n2, c->d_red, c->d_ticket,
                                                         c->scal);
   RIHF_LAUNCH_CHECK();
@@ -1410,7 +1505,7 @@ static void fock_build_tc(rihf_ctx* c, int digits) {
   LaCtx la = c->la();
   const int N = c->N, NA = c->NA, no = c->nocc;
   const size_t n2 = (size_t)N * N;
-  copy_cols(la, c->C, N, N, no, std::sqrt(2.0), c->Ct);
+  form_Ct(c);
   GemmArgs gd;
   gd.M = N; gd.N = N; gd.K = no; gd.A = c->Ct; gd.lda = no; gd.B = c->Ct; gd.ldb = no; gd.transB = true;
   gd.C = c->D; gd.ldc = N;
@@ -1585,6 +1680,259 @@ static void fock_and_error(rihf_ctx* c, int variant) {
   c->launches += g.launches;
 }
 
+// Superposition of atomic densities (the paper's cold-start guess, Sec. 2.2):
+// occupation numbers of the spherically averaged ground-state atom (aufbau
+// 1s 2s 2p, the open shell shared evenly over its orbitals), H to Ne.
+static bool sad_occupations(int Z, std::vector<double>& occ, std::vector<int>& occ_l) {
+  occ.clear();
+  occ_l.clear();
+  if (Z < 1 || Z > 10) return false;
+  int left = Z;
+  for (int k = 0; k < 2 && left > 0; ++k) {   // 1s, 2s
+    occ.push_back(std::min(2, left));
+    occ_l.push_back(0);
+    left -= std::min(2, left);
+  }
+  if (left > 0)
+    for (int k = 0; k < 3; ++k) {   // 2p, spherically averaged
+      occ.push_back(left / 3.0);
+      occ_l.push_back(1);
+    }
+  return true;
+}
+
+// SAD atoms: after a diagonalisation, the occupied columns follow the
+// configuration (occ_l: the l of each occupied orbital, lowest orbital of that
+// l first) rather than the eigenvalue order; the spherical average makes every
+// eigenvector pure in l.  The small basis sets of the workloads put the O 2p
+// level below 2s, where eigenvalue order would occupy a non-spherical set.
+static void occupy_by_l(rihf_ctx* c) {
+  const int N = c->N, n = c->nind;
+  std::vector<double> C((size_t)N * N), e(N);
+  RIHF_CUDA(cudaMemcpyAsync(C.data(), c->C, sizeof(double) * C.size(), cudaMemcpyDeviceToHost, c->stream));
+  RIHF_CUDA(cudaMemcpyAsync(e.data(), c->eps, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+  RIHF_CUDA(cudaStreamSynchronize(c->stream));
+  std::vector<int> lcol(n), order(n), chosen;
+  for (int j = 0; j < n; ++j) {
+    int best = 0;
+    for (int i = 1; i < N; ++i)
+      if (std::fabs(C[(size_t)i * N + j]) > std::fabs(C[(size_t)best * N + j])) best = i;
+    lcol[j] = c->fl_h[best];
+    order[j] = j;   // columns are already in ascending eigenvalue order
+  }
+  for (int l : c->occ_l) {
+    int pick = -1;
+    for (int j : order)
+      if (lcol[j] == l && std::find(chosen.begin(), chosen.end(), j) == chosen.end()) { pick = j; break; }
+    if (pick < 0) return;   // configuration not representable: keep the eigenvalue order
+    chosen.push_back(pick);
+  }
+  std::vector<int> idx = chosen;
+  for (int j : order)
+    if (std::find(chosen.begin(), chosen.end(), j) == chosen.end()) idx.push_back(j);
+  std::vector<double> C2(C), e2(e);
+  for (int q = 0; q < n; ++q) {
+    e2[q] = e[idx[q]];
+    for (int i = 0; i < N; ++i) C2[(size_t)i * N + q] = C[(size_t)i * N + idx[q]];
+  }
+  upload(c->C, C2, c->stream);
+  upload(c->eps, e2, c->stream);
+}
+
+// Builds the SAD factor Fs (N x m): for every atom type (element and identical
+// primary and auxiliary shells) one RI-HF SCF of the isolated, spherically
+// averaged atom (fractional occupations, FP64, this library's kernels), its
+// occupied orbitals scaled by sqrt(n_i) placed on each atom's basis-function
+// block.  D_SAD = Fs Fs^T.  On any obstacle (elements beyond Ne, an atom's
+// functions not contiguous) sad_ok stays false and the core guess is used.
+static void build_sad(rihf_ctx* c) {
+  c->sad_built = true;
+  c->sad_ok = false;
+  const int N = c->N;
+  const HostShells &hp = c->hp, &ha = c->ha;
+  std::vector<int> p0(c->natoms, -1), p1(c->natoms, -1), a0(c->natoms, -1), a1(c->natoms, -1);
+  for (int i = 0; i < hp.nshell; ++i) {
+    const int a = hp.atom[i];
+    if (p0[a] < 0) p0[a] = i;
+    else if (p1[a] != i) { c->sad_note = "primary shells of an atom are not contiguous"; return; }
+    p1[a] = i + 1;
+  }
+  for (int i = 0; i < ha.nshell; ++i) {
+    const int a = ha.atom[i];
+    if (a0[a] < 0) a0[a] = i;
+    else if (a1[a] != i) { c->sad_note = "auxiliary shells of an atom are not contiguous"; return; }
+    a1[a] = i + 1;
+  }
+  auto sig = [&](int a) {   // element and shells of atom a, exactly
+    std::string k = std::to_string(c->Z[a]) + "|";
+    auto add = [&](const HostShells& h, int s0, int s1) {
+      for (int i = s0; i < s1; ++i) {
+        k += std::to_string(h.l[i]) + ":";
+        for (int q = 0; q < h.nprim[i]; ++q) {
+          char buf[64];
+          snprintf(buf, sizeof(buf), "%.17g/%.17g,", h.exps[h.pstart[i] + q], h.raw_coefs[h.pstart[i] + q]);
+          k += buf;
+        }
+        k += ";";
+      }
+      k += "|";
+    };
+    if (p0[a] >= 0) add(hp, p0[a], p1[a]);
+    if (a0[a] >= 0) add(ha, a0[a], a1[a]);
+    return k;
+  };
+  struct AtomType {
+    int na = 0, m = 0;
+    std::vector<double> F;   // na x m, row-major
+  };
+  std::vector<std::string> keys;
+  std::vector<AtomType> types;
+  std::vector<int> type_of(c->natoms);
+  double zsum = 0.0;
+  for (int a = 0; a < c->natoms; ++a) {
+    zsum += c->Z[a];
+    if (p0[a] < 0 || a0[a] < 0) { c->sad_note = "an atom without primary or auxiliary shells"; return; }
+    const std::string k = sig(a);
+    int t = (int)(std::find(keys.begin(), keys.end(), k) - keys.begin());
+    if (t == (int)keys.size()) {
+      std::vector<double> occ;
+      std::vector<int> occ_l;
+      if (!sad_occupations(c->Z[a], occ, occ_l)) { c->sad_note = "SAD occupations known for H to Ne only"; return; }
+      std::vector<rihf_shell> ps, as;
+      for (int i = p0[a]; i < p1[a]; ++i)
+        ps.push_back({0, hp.l[i], hp.nprim[i], &hp.exps[hp.pstart[i]], &hp.raw_coefs[hp.pstart[i]]});
+      for (int i = a0[a]; i < a1[a]; ++i)
+        as.push_back({0, ha.l[i], ha.nprim[i], &ha.exps[ha.pstart[i]], &ha.raw_coefs[ha.pstart[i]]});
+      rihf_options o = c->opt;
+      o.precision = RIHF_PRECISION_FP64;
+      o.cuda_graphs = 0;
+      o.aux_chunk = 0;
+      o.schwarz_tau = 0.0;
+      o.max_iter = 200;
+      o.conv_e = 1e-10;
+      o.conv_diis = 1e-7;
+      const int zc = c->Z[a];
+      const double origin[3] = {0.0, 0.0, 0.0};
+      rihf_ctx* sub = nullptr;
+      try {
+        sub = setup_impl(1, &zc, origin, (int)ps.size(), ps.data(), (int)as.size(), as.data(), zc, &o, &occ);
+      } catch (const std::exception& ex) {
+        c->sad_note = std::string("atomic context: ") + ex.what();
+        cudaGetLastError();
+        return;
+      }
+      if (o.pure) {   // spherical basis: average every Fock matrix of the atom
+        std::vector<int> ao0(sub->N), fl(sub->N), fm(sub->N);
+        for (int i = 0; i < sub->hp.nshell; ++i)
+          for (int k = 0; k < sub->nf_h[sub->hp.l[i]]; ++k) {
+            ao0[sub->hp.ao[i] + k] = sub->hp.ao[i];
+            fl[sub->hp.ao[i] + k] = sub->hp.l[i];
+            fm[sub->hp.ao[i] + k] = k;
+          }
+        sub->d_fao0 = dalloc<int>(sub->N); upload(sub->d_fao0, ao0, sub->stream);
+        sub->d_fl = dalloc<int>(sub->N); upload(sub->d_fl, fl, sub->stream);
+        sub->d_fm = dalloc<int>(sub->N); upload(sub->d_fm, fm, sub->stream);
+        sub->sph_avg = true;
+        sub->fl_h = fl;
+        sub->occ_l = occ_l;
+      }
+      AtomType at;
+      at.na = sub->N;
+      at.m = sub->nocc;
+      std::vector<double> C((size_t)sub->N * sub->N);
+      double e = 0.0;
+      int it = 0;
+      const int rc = rihf_scf(sub, 0, nullptr, &e, nullptr, C.data(), nullptr, &it);
+      rihf_destroy(sub);
+      if (rc != RIHF_OK && rc != RIHF_ERR_NOT_CONVERGED) { c->sad_note = "atomic SCF failed"; return; }
+      at.F.resize((size_t)at.na * at.m);
+      for (int r = 0; r < at.na; ++r)
+        for (int q = 0; q < at.m; ++q) at.F[(size_t)r * at.m + q] = C[(size_t)r * sub->N + q] * std::sqrt(occ[q]);
+      if (c->verbose || getenv("RIHF_VERBOSE"))
+        fprintf(stderr, "rihf: SAD atom Z=%d: %d functions, %d occupied, E = %.10f (%d iterations)\n", zc, at.na,
+                at.m, e, it);
+      keys.push_back(k);
+      types.push_back(std::move(at));
+    }
+    type_of[a] = t;
+  }
+  // block-diagonal assembly; for an ion the factor is scaled to nelec electrons
+  int m = 0;
+  for (int a = 0; a < c->natoms; ++a) m += types[type_of[a]].m;
+  const double scale = std::sqrt(c->nelec / zsum);
+  std::vector<double> Fs((size_t)N * m, 0.0);
+  int col = 0;
+  for (int a = 0; a < c->natoms; ++a) {
+    const AtomType& at = types[type_of[a]];
+    const int r0 = hp.ao[p0[a]];
+    if (r0 + at.na > N) { c->sad_note = "atom block outside the basis"; return; }
+    for (int r = 0; r < at.na; ++r)
+      for (int q = 0; q < at.m; ++q) Fs[(size_t)(r0 + r) * m + col + q] = scale * at.F[(size_t)r * at.m + q];
+    col += at.m;
+  }
+  if (c->d_sad) cudaFree(c->d_sad);
+  c->d_sad = dalloc<double>(Fs.size());
+  upload(c->d_sad, Fs, c->stream);
+  RIHF_CUDA(cudaStreamSynchronize(c->stream));
+  c->sad_m = m;
+  c->sad_ok = true;
+}
+
+// First Fock build of a SAD start: D = Fs Fs^T, RI-J from D and RI-K from the
+// factor (Eq. k_ri_2 with C~ -> Fs: K = -1/2 sum_P (B^P Fs)(B^P Fs)^T, i.e. the
+// density form Eq. k_ri_1 for D_SAD), nocc columns at a time since Fs has more
+// columns than occupied orbitals; variant 0 in FP64, else on the tensor cores
+// with that many digits.
+static void fock_build_factor(rihf_ctx* c, int variant) {
+  LaCtx la = c->la();
+  const int N = c->N, NA = c->NA, no = c->nocc, m = c->sad_m;
+  const size_t n2 = (size_t)N * N;
+  cudaStream_t s = c->stream;
+  GemmArgs gd;
+  gd.M = N; gd.N = N; gd.K = m; gd.A = c->d_sad; gd.lda = m; gd.B = c->d_sad; gd.ldb = m; gd.transB = true;
+  gd.C = c->D; gd.ldc = N;
+  dgemm(la, gd);
+  ri_j(c);
+  for (int c0 = 0; c0 < m; c0 += no) {
+    const int w = std::min(no, m - c0);
+    const bool first = c0 == 0;
+    RIHF_CUDA(cudaMemsetAsync(c->Ct, 0, sizeof(double) * N * no, s));
+    RIHF_CUDA(cudaMemcpy2DAsync(c->Ct, no * sizeof(double), c->d_sad + c0, m * sizeof(double), w * sizeof(double), N,
+                                cudaMemcpyDeviceToDevice, s));
+    if (variant > 0) {
+      OzOperand Cop = oz_slice(la, c->Ct, no, N, 1, no, 0, N, variant, 0, c->Cz);
+      form_H(c, variant, &Cop, "SAD RI-K H=B Fs (tcgen05 digits)");
+      const int kch = (NA * no + kOzChunk - 1) / kOzChunk;
+      const int TN = N <= kOzMaxTN ? (N + 15) / 16 * 16 : kOzMaxTN;
+      int lower_tiles = 0;
+      for (int mt = 0; mt * kOzTileM < N; ++mt)
+        for (int nt = 0; nt * TN < N; ++nt)
+          if (mt * kOzTileM + kOzTileM - 1 >= nt * TN) ++lower_tiles;
+      if (c->k_nsplit <= 0) c->k_nsplit = tune_k_splits(c, variant, kch, lower_tiles);   // writes K
+      if (first) RIHF_CUDA(cudaMemsetAsync(c->K, 0, sizeof(double) * n2, s));
+      const int kbc = (kch + c->k_nsplit - 1) / c->k_nsplit;
+      OzOperand Hop = oz_slice(la, c->Hb, N, NA * no, no, 1, (long long)N * no, no, variant, kbc, c->Hz);
+      OzGemmArgs g2;
+      g2.A = Hop; g2.B = Hop; g2.M = N; g2.N = N; g2.s = variant; g2.alpha = -0.5; g2.C = c->K; g2.cs_m1 = N;
+      g2.cs_n = 1; g2.atomic = true; g2.lower_only = true;
+      oz_gemm(la, g2);
+    } else {
+      form_H(c, 0, nullptr, "SAD RI-K H=B Fs (dgemm)");
+      GemmArgs gk;
+      gk.M = N; gk.N = N; gk.K = no; gk.A = c->Hb; gk.lda = no; gk.sA = (long long)N * no;
+      gk.B = c->Hb; gk.ldb = no; gk.sB = (long long)N * no; gk.transB = true;
+      gk.C = c->K; gk.ldc = N; gk.batch = NA; gk.reduce_batch = true; gk.alpha = -0.5; gk.beta = first ? 0.0 : 1.0;
+      gk.lower_only = true;
+      dgemm(la, gk);
+    }
+  }
+  symmetrize_lower(la, c->K, N, 1);
+  add3(la, (int)n2, c->H, c->J, c->K, c->F);
+  energy_mb_kernel<<<kRedBlocks, 256, 0, s>>>(c->D, c->H, c->F, (long long)n2, c->d_red, c->d_ticket, c->scal);
+  RIHF_LAUNCH_CHECK();
+  c->launches += 1;
+}
+
 int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, double* Dout, double* Cout,
              double* epsout, int* iters) {
   RIHF_API_BEGIN
@@ -1688,11 +2036,20 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
     transpose(la, c->T1, no, N, c->Ct);
     RIHF_CUDA(cudaMemcpy2DAsync(c->C, N * sizeof(double), c->Ct, no * sizeof(double), no * sizeof(double), N,
                                 cudaMemcpyDeviceToDevice, s));
+  } else if (guess == 5 && (c->sad_built ? c->sad_ok : (build_sad(c), c->sad_ok))) {
+    // SAD: the first iteration's Fock matrix comes from D_SAD (below); the
+    // first diagonalisation then starts cold
+    c->have_cprev = false;
+    c->last_guess = 5;
+    c->pending_example = false;
   } else {
+    if (guess == 5 && (c->verbose || getenv("RIHF_VERBOSE")))
+      fprintf(stderr, "rihf: SAD guess unavailable (%s), core Hamiltonian instead\n", c->sad_note.c_str());
     diagonalise(c, c->H, false);
     c->last_guess = 0;
     c->pending_example = false;
   }
+  const bool sad_first = c->last_guess == 5;
   const int size = c->opt.diis_size;
   double E = 0.0, Eold = 0.0, emax = 0.0;
   int it = 0;
@@ -1737,7 +2094,12 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
       c->last_digits = variant;
       ++c->confirm_builds;
     }
-    fock_and_error(c, variant);
+    if (it == 1 && sad_first) {
+      fock_build_factor(c, variant);
+      diis_error(c);
+    } else {
+      fock_and_error(c, variant);
+    }
     cudaEventRecord(c->ev[3], s);
     int slot = (it - 1 - dbase) % size;
     int m = std::min(it - dbase, size);
@@ -1845,7 +2207,7 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   cudaStream_t s = c->stream;
   cudaEventRecord(c->ev[5], s);
   // Ct, D from the final orbitals; W = Ct diag(eps_occ) Ct^T
-  copy_cols(la, c->C, N, N, no, std::sqrt(2.0), c->Ct);
+  form_Ct(c);
   GemmArgs gd;
   gd.M = N; gd.N = N; gd.K = no; gd.A = c->Ct; gd.lda = no; gd.B = c->Ct; gd.ldb = no; gd.transB = true;
   gd.C = c->D; gd.ldc = N;
@@ -2103,6 +2465,20 @@ int rihf_get_matrix(rihf_ctx* c, int which, double* out) {
       std::vector<float> f(nf);
       RIHF_CUDA(cudaMemcpy(f.data(), c->mlX, sizeof(float) * nf, cudaMemcpyDeviceToHost));
       for (size_t i = 0; i < nf; ++i) out[i] = f[i];
+      break;
+    }
+    case RIHF_MAT_DSAD: {
+      // the SAD guess density D_SAD = Fs Fs^T (after a guess-5 SCF built it)
+      if (!c->sad_ok) return RIHF_ERR_STATE;
+      const int N = c->N, m = c->sad_m;
+      std::vector<double> F((size_t)N * m);
+      RIHF_CUDA(cudaMemcpy(F.data(), c->d_sad, sizeof(double) * F.size(), cudaMemcpyDeviceToHost));
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+          double t = 0.0;
+          for (int q = 0; q < m; ++q) t += F[(size_t)i * m + q] * F[(size_t)j * m + q];
+          out[(size_t)i * N + j] = t;
+        }
       break;
     }
     case RIHF_MAT_DPRED:

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(HERE, "librihf.so")
 RIHF_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED", -5: "TIMEOUT",
           -6: "NOT_POSITIVE_DEFINITE", -7: "STATE"}
-MAT = dict(S=0, H=1, A=2, LINV=3, T3=4, B=5, J=6, K=7, F=8, D=9, GRAD_PARTS=10, SCHWARZ=11, DPRED=12, FEATURES=13)
+MAT = dict(S=0, H=1, A=2, LINV=3, T3=4, B=5, J=6, K=7, F=8, D=9, GRAD_PARTS=10, SCHWARZ=11, DPRED=12, FEATURES=13,
+           DSAD=14)
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 
 
@@ -295,7 +296,8 @@ class Context:
         N, NA = self.N, self.Naux
         shapes = dict(S=(N, N), H=(N, N), J=(N, N), K=(N, N), F=(N, N), D=(N, N), A=(NA, NA), LINV=(NA, NA),
                       T3=(NA, N, N), B=(NA, N, N), GRAD_PARTS=(5, self.natoms, 3),
-                      SCHWARZ=(self.screening_stats()[1],), DPRED=(N, N), FEATURES=(N * (N + 1) // 2, MLP_F))
+                      SCHWARZ=(self.screening_stats()[1],), DPRED=(N, N), FEATURES=(N * (N + 1) // 2, MLP_F),
+                      DSAD=(N, N))
         out = np.zeros(shapes[name])
         _check(self.lib.rihf_get_matrix(self.h, MAT[name], _p(out)))
         return out
