@@ -29,6 +29,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RI-HF AIMD steps/s (E+grad), mixed vs FP64 at |dE|<=1e-6 Eh; % of roofline"
 WORKLOAD = ("(H2O)8 RI-HF E+grad AIMD step, N=192, Naux=848, spherical, dt 0.5 fs, previous-orbital guess")
+# (H2O)32 with the larger basis: overlap eigenvalues down to 3e-9, so the
+# canonical orthogonaliser drops those below 1e-6 (83 of 1856 functions) and the
+# DIIS error is resolved to ~1e-7 at most; energies converge to 1e-10 by then
+C2_CONV = dict(conv_e=1e-8, conv_diis=1e-6, max_iter=60, lindep_tau=1e-6)
+C2_WORKLOAD = ("(H2O)32 RI-HF E+grad AIMD step, larger basis (primary O 4s3p2d1f / H 3s2p1d, auxiliary "
+               "O 11s8p6d3f2g / H 6s4p3d), N=1856, Naux=5440, spherical, dt 0.5 fs, SAD cold start then "
+               "previous-orbital guess, overlap eigenvalues below 1e-6 dropped (1773 functions kept)")
 UNIT = "AIMD steps/s"
 DT_FS = 0.5
 CONV = dict(conv_e=1e-8, conv_diis=1e-7, max_iter=60)
@@ -132,7 +139,7 @@ class Trajectory:
     geometries instead of integrating, so that another path (the FP64 one) is
     evaluated on exactly the geometries of the first."""
 
-    def __init__(self, ctx, mol, seed, R, replay=None):
+    def __init__(self, ctx, mol, seed, R, replay=None, guess0=0):
         from paper_2407_19614_gb300 import workloads as W
         self.ctx, self.R = ctx, R
         self.m = W.masses_au(mol.Z)[:, None]
@@ -142,7 +149,7 @@ class Trajectory:
         self.replay = replay
         self.k = 0
         self.geoms = []
-        out = ctx.scf(guess=0, outputs=False)
+        out = ctx.scf(guess=guess0, outputs=False)
         self.E = out["energy"]
         self.g = ctx.gradient()
         self.iters = [out["iterations"]]
@@ -367,11 +374,15 @@ def main():
                     help="seconds of timed whole oracle steps for --impl reference")
     ap.add_argument("--ref-molecule", default="water8", choices=["water8", "monomer"],
                     help="workload of --impl reference (the monomer only checks the arm's host logic quickly)")
+    ap.add_argument("--c2-steps", type=int, default=2,
+                    help="timed AIMD steps of the (H2O)32 larger-basis measurement on each path (0: skip it)")
     ap.add_argument("--batch", type=int, default=0,
                     help="batched mode: this many independent clusters of 3..--batch-max waters per AIMD step")
     ap.add_argument("--batch-max", type=int, default=8)
     ap.add_argument("--profile-step", action="store_true",
                     help="untimed: setup, one SCF and one gradient of the workload (for ncu captures)")
+    ap.add_argument("--profile-workload", default="water8", choices=["water8", "water16", "water4-large"],
+                    help="workload of --profile-step (small cases for ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -382,8 +393,10 @@ def main():
         from paper_2407_19614_gb300 import workloads as W
         R.load()
         prec = R.PRECISION_MIXED if args.precision == "mixed" else R.PRECISION_FP64
-        ctx = R.Context(W.water8(0), precision=prec, **CONV)
-        out = ctx.scf(outputs=False)
+        mol = {"water8": lambda: W.water8(0), "water16": lambda: W.water16(0),
+               "water4-large": lambda: W.water_n(4, 0, "large")}[args.profile_workload]()
+        ctx = R.Context(mol, precision=prec, **CONV)
+        out = ctx.scf(guess=5, outputs=False)
         g = ctx.gradient()
         print(json.dumps({"energy": out["energy"], "iterations": out["iterations"], "grad_max": float(abs(g).max())}))
         ctx.close()
@@ -404,43 +417,16 @@ def main():
         # run above): its throughput, and per step |E_mixed - E_fp64| and the
         # largest force difference -- the |dE| of the metric
         cmp = measure_path(R, W, torch, "fp64", args, rank, local, pg, trace=False, replay=res["all_geoms"])
+    c2 = None
+    if args.c2_steps > 0 and rank == 0:
+        c2 = measure_config2(R, W, torch, args, local)
     if rank != 0:
         return 0
     world = res["world"]
     value = world * args.steps / (res["ms_max"] / 1e3)
     stats = res["stats"]
     pk, pk_src = peaks()
-    roof = None
-    kernels = [s for s in stats if not s["name"].startswith("SCF iteration graph")]
-    if kernels:
-        dom = max(kernels, key=lambda s: s["ms"])
-        timed = [s for s in kernels if s["work"] > 0]
-        roof_k = dom if dom["work"] > 0 else max(timed, key=lambda s: s["ms"])
-        per_launch_s = roof_k["ms"] / roof_k["launches"] / 1e3
-        work = roof_k["work"] / roof_k["launches"]
-        if roof_k["kind"] == "hbm_bytes":
-            achieved, peak, unit, bound = work / per_launch_s / 1e9, pk["hbm_gbs"], "GB/s", "hbm"
-            src = "hbm_gbs of %s" % pk_src
-        elif roof_k["kind"] == "fp64_flops":
-            achieved, peak, unit, bound = work / per_launch_s / 1e12, FP64_PEAK_GFLOPS / 1e3, "TFLOP/s", "alu"
-            src = "FP64 DFMA peak derived from unit counts (152 SMs x 2 DFMA/clk x 2.07 GHz)"
-        elif roof_k["kind"] == "bf16_tensor_flops":
-            # BF16 MMA flops issued (digit-pair products included); the kernel runs
-            # inside a long step, so the sustained cuBLAS figure is the peak
-            key = "bf16_tflops_sustained" if "bf16_tflops_sustained" in pk else "bf16_tflops"
-            achieved, peak, unit, bound = work / per_launch_s / 1e12, pk[key], "TFLOP/s", "tensor"
-            src = "%s of %s" % (key, pk_src)
-        else:
-            achieved, peak, unit, bound = work / per_launch_s / 1e12, pk["bf16_tflops"] / 2, "TFLOP/s", "alu"
-            src = "FP32 SIMT: half the bf16 tensor figure of %s (fallback)" % pk_src
-        traffic = None
-        tpath = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tpath):
-            with open(tpath) as f:
-                traffic = json.load(f).get(roof_k["name"])
-        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": traffic, "kernel": roof_k["name"], "peak_source": src,
-                "dominant_kernel": dom["name"], "dominant_share": dom["ms"] / sum(s["ms"] for s in stats)}
+    roof = roofline_of(stats, pk, pk_src)
     cpu = None
     if not args.no_cpu_baseline:
         r = oracle_aimd(budget_s=args.cpu_budget, max_steps=args.steps)
@@ -470,6 +456,8 @@ def main():
         "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()} for s in
                     sorted(stats, key=lambda s: -s["ms"])],
     }
+    if c2 is not None:
+        line["config2"] = c2
     if cmp is not None:
         dE = np.abs(np.array(res["energies"]) - np.array(cmp["energies"]))
         dF = max(float(np.abs(a - b).max()) for a, b in zip(res["grads"], cmp["grads"]))
@@ -483,6 +471,96 @@ def main():
         config["speedup_vs_fp64_path"] = value / line["fp64_path"]["value"]
     print(json.dumps(line))
     return 0
+
+
+def roofline_of(stats, pk, pk_src):
+    """The roofline object of the dominant traced kernel (or of the longest one
+    with a work count when the dominant one has none)."""
+    kernels = [s for s in stats if not s["name"].startswith("SCF iteration graph")]
+    if not kernels:
+        return None
+    dom = max(kernels, key=lambda s: s["ms"])
+    timed = [s for s in kernels if s["work"] > 0]
+    roof_k = dom if dom["work"] > 0 else max(timed, key=lambda s: s["ms"])
+    per_launch_s = roof_k["ms"] / roof_k["launches"] / 1e3
+    work = roof_k["work"] / roof_k["launches"]
+    if roof_k["kind"] == "hbm_bytes":
+        achieved, peak, unit, bound = work / per_launch_s / 1e9, pk["hbm_gbs"], "GB/s", "hbm"
+        src = "hbm_gbs of %s" % pk_src
+    elif roof_k["kind"] == "fp64_flops":
+        achieved, peak, unit, bound = work / per_launch_s / 1e12, FP64_PEAK_GFLOPS / 1e3, "TFLOP/s", "alu"
+        src = "FP64 DFMA peak derived from unit counts (152 SMs x 2 DFMA/clk x 2.07 GHz)"
+    elif roof_k["kind"] == "bf16_tensor_flops":
+        # BF16 MMA flops issued (digit-pair products included); the kernel runs
+        # inside a long step, so the sustained cuBLAS figure is the peak
+        key = "bf16_tflops_sustained" if "bf16_tflops_sustained" in pk else "bf16_tflops"
+        achieved, peak, unit, bound = work / per_launch_s / 1e12, pk[key], "TFLOP/s", "tensor"
+        src = "%s of %s" % (key, pk_src)
+    else:
+        achieved, peak, unit, bound = work / per_launch_s / 1e12, pk["bf16_tflops"] / 2, "TFLOP/s", "alu"
+        src = "FP32 SIMT: half the bf16 tensor figure of %s (fallback)" % pk_src
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get(roof_k["name"])
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "traffic": traffic, "kernel": roof_k["name"], "peak_source": src,
+            "dominant_kernel": dom["name"], "dominant_share": dom["ms"] / sum(s["ms"] for s in stats)}
+
+
+def measure_config2(R, W, torch, args, local):
+    """(H2O)32 with the larger basis on both paths: per path an untimed SAD
+    cold start and gradient, then args.c2_steps AIMD steps timed on the device
+    (the FP64 path replays the mixed path's geometries); per-step |dE| and
+    max |dF| between the paths."""
+    mol = W.water32_large(0)
+    res = {}
+    geoms = None
+    for precision in ("mixed", "fp64"):
+        prec = R.PRECISION_MIXED if precision == "mixed" else R.PRECISION_FP64
+        t0 = time.perf_counter()
+        ctx = R.Context(mol, precision=prec, device=local, **C2_CONV)
+        traj = Trajectory(ctx, mol, 0, R, replay=geoms, guess0=5)
+        cold_s = time.perf_counter() - t0
+        stream = torch.cuda.ExternalStream(ctx.stream(), device=local)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ctx.trace(precision == "mixed")
+        launches0 = ctx.timings()["launches"]
+        it0 = len(traj.iters)
+        E, F = [], []
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.c2_steps):
+            traj.step()
+            E.append(traj.E)
+            F.append(traj.g.copy())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        stats = ctx.trace_stats() if precision == "mixed" else []
+        res[precision] = dict(ms=ms, E=E, F=F, iters=traj.iters[it0:], cold_s=cold_s, stats=stats,
+                              launches=ctx.timings()["launches"] - launches0, N=ctx.N, Naux=ctx.Naux)
+        if precision == "mixed":
+            geoms = list(traj.geoms)
+        ctx.close()
+    m, f = res["mixed"], res["fp64"]
+    pk, pk_src = peaks()
+    value = args.c2_steps / (m["ms"] / 1e3)
+    v64 = args.c2_steps / (f["ms"] / 1e3)
+    return {"workload": C2_WORKLOAD, "metric": METRIC, "value": value, "unit": UNIT, "steps": args.c2_steps,
+            "ms_per_step": m["ms"] / args.c2_steps, "scf_iters": m["iters"], "gpu_launches": int(m["launches"]),
+            "scf_conv": C2_CONV, "untimed_cold_start_s": m["cold_s"],
+            "fp64_path": {"value": v64, "unit": UNIT, "ms_per_step": f["ms"] / args.c2_steps, "scf_iters": f["iters"],
+                          "untimed_cold_start_s": f["cold_s"],
+                          "geometries": "the mixed path's timed geometries, replayed"},
+            "speedup_vs_fp64_path": value / v64,
+            "max_abs_dE_vs_fp64_path_eh": float(np.max(np.abs(np.array(m["E"]) - np.array(f["E"])))),
+            "max_abs_dF_vs_fp64_path_eh_bohr": max(float(np.abs(a - b).max()) for a, b in zip(m["F"], f["F"])),
+            "roofline": roofline_of(m["stats"], pk, pk_src),
+            "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()} for s in
+                        sorted(m["stats"], key=lambda s: -s["ms"])[:16]]}
 
 
 def measure_path(R, W, torch, precision, args, rank, local, pg, trace, replay=None):
