@@ -10,6 +10,11 @@ own guess reuses the previous orbitals, Sec. 3.3): for features x (12),
 loss L = (1/M) sum_e (y_e - t_e)^2 over the M lower-triangle elements, Adam
 (beta1 0.9, beta2 0.999, eps 1e-8).  Parameters are used rounded to BF16 (round
 to nearest, ties to even, applied to their FP32 values).
+
+The densities entering the features, the extrapolation and the target are
+Loewdin densities D_L = S^{1/2} D S^{1/2} of their own geometries
+(lowdin_factors); the predicted D_L goes back to the AO basis with the new
+geometry's S^{-1/2} (apply).
 """
 import numpy as np
 
@@ -115,11 +120,32 @@ def features(D0, D1, D2, S1, S0, R1, R0, Rm, ao_atom, ao_l, sd=1.0, ss=1.0, sr=1
     return X, Dx[mu, nu]
 
 
-def apply(Dx_lower, y, scale, N):
-    """Symmetric N x N density from lower-triangle values D_x + scale * y."""
+def apply(Dx_lower, y, scale, N, S_mhalf=None):
+    """Symmetric N x N density from lower-triangle values D_x + scale * y;
+    with S_mhalf (the S^{-1/2} of lowdin_factors) the values are Loewdin
+    densities and the result is taken back to the AO basis,
+    D = S^{-1/2} D_L S^{-1/2}."""
     mu, nu = lower_index(N)
     D = np.zeros((N, N))
     v = Dx_lower + scale * np.asarray(y, dtype=np.float64)
     D[mu, nu] = v
     D[nu, mu] = v
+    if S_mhalf is not None:
+        D = S_mhalf @ D @ S_mhalf
     return D
+
+
+def lowdin_factors(S, tau):
+    """S^{1/2} over all eigenpairs of the overlap matrix and the pseudo-inverse
+    S^{-1/2} over the eigenvalues above tau (the linear-dependence threshold of
+    the orthogonaliser).  The guess history holds Loewdin densities
+    D_L = S^{1/2} D S^{1/2}: the density in the symmetrically orthonormalised
+    basis, idempotent with elements bounded by one, continuous in the nuclear
+    positions, so that its extrapolation and the network's correction are not
+    dominated by the large, nearly unphysical AO-basis components that an
+    almost linearly dependent basis gives D."""
+    w, U = np.linalg.eigh(np.asarray(S, dtype=np.float64))
+    keep = w > tau
+    Sh = (U * np.sqrt(np.clip(w, 0.0, None))) @ U.T
+    Smh = (U[:, keep] / np.sqrt(w[keep])) @ U[:, keep].T
+    return Sh, Smh

@@ -94,3 +94,34 @@ def test_features_on_a_hand_built_case():
     sd0, ss0, sr0 = O.scales(D0, D1, S1, S0, R1, R0, [0, 0, 1])
     assert np.isclose(sd0, np.sqrt(np.mean((0.5 * D0[mu, nu]) ** 2)))
     assert np.isclose(ss0, np.sqrt(3 / 6)) and np.isclose(sr0, np.sqrt(2 / 6))   # pairs (2,0), (2,1) move
+
+
+def test_lowdin_factors_square_roots_and_projector():
+    """S^{1/2} squares to S, S^{-1/2} inverts it on the kept space; the Loewdin
+    density of a closed-shell density is idempotent with eigenvalues 0 and 1;
+    the round trip through apply() gives the AO density back.  A dropped
+    eigenvalue turns S^{-1/2} S S^{-1/2} into the projector on the kept space."""
+    rng = np.random.default_rng(4)
+    N, nocc = 7, 3
+    G = rng.normal(size=(N, N))
+    S = G @ G.T + 0.05 * np.eye(N)
+    Sh, Smh = O.lowdin_factors(S, 1e-10)
+    assert np.allclose(Sh @ Sh, S, atol=1e-12 * np.abs(S).max())
+    assert np.allclose(Smh @ S @ Smh, np.eye(N), atol=1e-10)
+    # a closed-shell density: D = C C^T with C^T S C = I
+    X = Smh
+    C = X @ np.linalg.qr(rng.normal(size=(N, nocc)))[0]
+    D = C @ C.T
+    DL = Sh @ D @ Sh
+    assert np.allclose(DL @ DL, DL, atol=1e-10)
+    assert np.allclose(np.sort(np.linalg.eigvalsh(DL)), [0] * (N - nocc) + [1] * nocc, atol=1e-10)
+    mu, nu = O.lower_index(N)
+    assert np.allclose(O.apply(DL[mu, nu], np.zeros(len(mu)), 1.0, N, Smh), D, atol=1e-10)
+    # a near-null direction below the threshold is dropped
+    w, U = np.linalg.eigh(S)
+    w2 = w.copy()
+    w2[0] = 1e-12
+    S2 = (U * w2) @ U.T
+    _, Smh2 = O.lowdin_factors(S2, 1e-9)
+    P = Smh2 @ S2 @ Smh2
+    assert np.allclose(P, np.eye(N) - np.outer(U[:, 0], U[:, 0]), atol=1e-8)
