@@ -38,6 +38,7 @@ C2_WORKLOAD = ("(H2O)32 RI-HF E+grad AIMD step, larger basis (primary O 4s3p2d1f
                "previous-orbital guess, overlap eigenvalues below 1e-6 dropped (1773 functions kept)")
 UNIT = "AIMD steps/s"
 DT_FS = 0.5
+LA_LINDEP = 1e-6
 CONV = dict(conv_e=1e-8, conv_diis=1e-7, max_iter=60)
 # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07
@@ -170,10 +171,15 @@ class Trajectory:
         self.geoms.append(x.copy())
         self.k += 1
 
-    def step(self):
+    def step(self, guess=2, allow_unconverged=False):
         x = self.next_geometry()
         self.ctx.update_geometry(x)
-        out = self.ctx.scf(guess=2, outputs=False)
+        out = self.ctx.scf(guess=guess, outputs=False, allow_unconverged=allow_unconverged)
+        if not out["converged"]:
+            # a step the history-based guess could not converge: again from SAD
+            re = self.ctx.scf(guess=5, outputs=False)
+            out = dict(re, iterations=out["iterations"] + re["iterations"], converged=False)
+        self.last = out
         self.iters.append(out["iterations"])
         self.finish(x, out["energy"], self.ctx.gradient())
 
@@ -190,6 +196,57 @@ class Trajectory:
 
     def total_energy(self):
         return self.E + 0.5 * float(np.sum(self.m * self.v ** 2))
+
+
+def run_learned_aimd(args):
+    """The learned-guess AIMD experiment: (H2O)16 (small basis) from the
+    generated geometry and seeded 300 K velocities, velocity Verlet at 0.5 fs
+    for --la-steps steps, one arm per guess: the extrapolated Loewdin density
+    (3) and the learned guess (4, the network trained online on the first
+    --la-train steps, then frozen), mixed precision.  Each arm integrates its
+    own trajectory.  Overlap eigenvalues below LA_LINDEP are dropped: where
+    molecules of this hot trajectory come close, S approaches singularity and
+    the commutator's rounding floor (|F| eps / lambda_min(S)) would otherwise
+    sit near the convergence threshold.  Prints one JSON line: per arm the SCF iterations per
+    step (all steps, and after training), the total-energy drift, how often
+    the network was used, and the wall time."""
+    import torch
+    from paper_2407_19614_gb300 import rihf as R
+    from paper_2407_19614_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    R.load()
+    mol = W.water16(0)
+    arms = {}
+    for name, guess in (("extrapolated", 3), ("learned", 4)):
+        ctx = R.Context(mol, precision=R.PRECISION_MIXED, lindep_tau=LA_LINDEP, **CONV)
+        ctx.learn_config(hidden=256, train_steps=args.la_train, adam_iters=4, lr=1e-3, seed=0)
+        t0 = time.perf_counter()
+        tr = Trajectory(ctx, mol, 0, R, guess0=5)
+        etot = [tr.total_energy()]
+        its, used, bad = [], [], 0
+        for _ in range(args.la_steps):
+            tr.step(guess=guess, allow_unconverged=True)
+            its.append(tr.last["iterations"])
+            bad += 0 if tr.last["converged"] else 1
+            used.append(ctx.learn_stats()["last_guess"] == 4)
+            etot.append(tr.total_energy())
+        wall = time.perf_counter() - t0
+        ctx.close()
+        its = np.array(its)
+        etot = np.array(etot)
+        after = slice(min(args.la_train + 3, len(its)), len(its))
+        arms[name] = {"scf_iters_per_step": float(its.mean()),
+                      "scf_iters_per_step_after_training": float(its[after].mean()) if len(its[after]) else None,
+                      "energy_drift_eh": float(etot[-1] - etot[0]),
+                      "max_abs_total_energy_change_eh": float(np.abs(etot - etot[0]).max()),
+                      "network_used_steps": int(sum(used)), "unconverged_steps": bad, "wall_s": wall}
+        print(name, json.dumps(arms[name]), file=sys.stderr, flush=True)
+    print(json.dumps({"experiment": "learned SCF guess along AIMD",
+                      "workload": "(H2O)16, N=384, Naux=1696, velocity Verlet dt 0.5 fs from seeded 300 K "
+                                  "Maxwell-Boltzmann velocities, SAD start, mixed precision",
+                      "steps": args.la_steps, "train_steps": args.la_train, "network": "12-256-1 tanh, BF16 weights",
+                      "conv": dict(CONV, lindep_tau=LA_LINDEP), "arms": arms}))
+    return 0
 
 
 def oracle_aimd(budget_s, max_steps, conv=CONV, molecule="water8"):
@@ -379,11 +436,17 @@ def main():
     ap.add_argument("--batch", type=int, default=0,
                     help="batched mode: this many independent clusters of 3..--batch-max waters per AIMD step")
     ap.add_argument("--batch-max", type=int, default=8)
+    ap.add_argument("--learned-aimd", action="store_true",
+                    help="the learned-guess AIMD experiment ((H2O)16) instead of the benchmark")
+    ap.add_argument("--la-steps", type=int, default=2000)
+    ap.add_argument("--la-train", type=int, default=200)
     ap.add_argument("--profile-step", action="store_true",
                     help="untimed: setup, one SCF and one gradient of the workload (for ncu captures)")
     ap.add_argument("--profile-workload", default="water8", choices=["water8", "water16", "water4-large"],
                     help="workload of --profile-step (small cases for ncu captures)")
     args = ap.parse_args()
+    if args.learned_aimd:
+        return run_learned_aimd(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.batch > 0:

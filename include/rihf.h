@@ -124,12 +124,18 @@ int rihf_update_geometry(rihf_ctx* ctx, const double* xyz);
  *          2 the context's previous converged orbitals (the paper's AIMD
  *            guess, Sec. 3.3; falls back to 0),
  *          3 density extrapolation D_x = 3 D_t - 3 D_{t-1} + D_{t-2} over the
- *            last three converged SCFs of this context (falls back to 2),
+ *            last three converged SCFs of this context, in the Loewdin
+ *            representation D_L = S^{1/2} D S^{1/2} of each geometry (falls
+ *            back to 2),
  *          4 learned: D_x plus the correction of the network configured by
  *            rihf_learn_config, once it beats D_x on its last training
  *            example (else D_x; falls back to 2).  With guesses 3 and 4 the
- *            previous occupied orbitals are projected onto the predicted
- *            density (C <- D_pred S C, then S-orthonormalised).
+ *            predicted Loewdin density returns to the AO basis with this
+ *            geometry's S^{-1/2} (pseudo-inverse over the overlap
+ *            eigenvalues above lindep_tau), and the previous occupied
+ *            orbitals are projected onto it (C <- D_pred S C, then
+ *            S-orthonormalised).  The first guess-3 or -4 call (or
+ *            rihf_learn_config) restarts the history in that representation.
  *          5 superposition of atomic densities (SAD, the paper's cold start,
  *            Sec. 2.2): one RI-HF SCF per atom type of the isolated,
  *            spherically averaged atom (fractional occupations, H to Ne; the
@@ -137,9 +143,10 @@ int rihf_update_geometry(rihf_ctx* ctx, const double* xyz);
  *            iteration builds J from D_SAD and K from its factor (the density
  *            form, Eq. k_ri_1).  Falls back to 0 when unavailable (other
  *            elements, an atom's shells not contiguous).
- *          Every converged SCF pushes its D, S and nuclear positions into the
- *          three-deep history; a guess-4 SCF first trains the network on its
- *          own example (rihf_learn_config).
+ *          Every converged SCF pushes its D (as D_L once guesses 3/4 are in
+ *          use), S and nuclear positions into the three-deep history; a
+ *          guess-4 SCF first trains the network on its own example
+ *          (rihf_learn_config).
  *   energy (1), D (N*N), C (N*N), eps (N), iters (1): outputs; any may be NULL.
  * Returns NOT_CONVERGED (outputs filled from the last iterate) after max_iter.
  */
@@ -187,8 +194,9 @@ int rihf_query(rihf_ctx* ctx, int* N, int* Naux, int* nocc, int* natoms);
                           is not evaluated)
      RIHF_MAT_DSAD: N x N, the SAD guess density (after a guess-5 SCF built
                           it; RIHF_ERR_STATE before, or when SAD was unavailable)
-     RIHF_MAT_DPRED: N x N, the predicted density of the last guess-3 or
-                          guess-4 SCF (extrapolation plus network correction)
+     RIHF_MAT_DPRED: N x N, the predicted AO density of the last guess-3 or
+                          guess-4 SCF (extrapolation plus network correction,
+                          taken back from the Loewdin representation)
      RIHF_MAT_FEATURES: N(N+1)/2 x 12, the network's features of that guess
                           (stored in FP32, returned as doubles)
    J, K, F, D refer to the last Fock build. */
@@ -275,7 +283,8 @@ int rihf_tc_dgemm(int M, int N, int K, const double* A, const double* B, double*
 /* Learned SCF guess (guess 4 of rihf_scf): an elementwise-shared two-layer MLP
    x (12 features) -> tanh(W1 x + b1) (hidden units) -> y = w2 . h + b2 over the
    lower-triangle density elements mu >= nu, predicting
-   (D_{t+1} - D_x) / scale.  Features: D_t, D_{t-1}, D_{t-2}, D_x, S_{t+1}, S_t,
+   (D_{t+1} - D_x) / scale, all densities Loewdin densities (rihf_scf guess 3).
+   Features: D_t, D_{t-1}, D_{t-2}, D_x, S_{t+1}, S_t,
    |R_A - R_B| / 10 bohr at t+1, t, t-1 (A, B the atoms of mu, nu), same-atom
    flag, (l_mu + l_nu) / 4, |l_mu - l_nu| / 4.  Weights are used in BF16 (FP32
    master copies), products accumulated in FP32, loss (1/M) sum (y - t)^2,

@@ -561,6 +561,12 @@ struct rihf_ctx {
   double* hist_S = nullptr;                          // S_t
   double* hist_xyz[2] = {nullptr, nullptr};          // R_t, R_{t-1}
   int nhist = 0;
+  // the history holds Loewdin densities D_L = S^{1/2} D S^{1/2} of their own
+  // geometries (from the first extrapolated or learned guess on): S^{1/2},
+  // S^{-1/2} of the current geometry (built once per geometry), D_L scratch
+  bool hist_lowdin = false;
+  double *Shalf = nullptr, *Smhalf = nullptr, *DL = nullptr;
+  long long geom_serial = 0, lowdin_serial = -1;
   double* Dpred = nullptr;
   float *mlX = nullptr, *mly = nullptr, *mlt = nullptr;
   double* mlDx = nullptr;
@@ -699,7 +705,7 @@ static void free_all(rihf_ctx* c) {
                   c->d_al, c->d_aatom, c->d_anprim, c->d_aps, c->d_aao, c->d_axyz_sh, c->d_aexp, c->d_acoef,
                   c->d_piexp, c->d_aiexp, c->d_pp_off, c->d_pp,
                   c->d_ao_atom, c->d_ao_l, c->hist_D[0], c->hist_D[1], c->hist_D[2], c->hist_S, c->hist_xyz[0],
-                  c->hist_xyz[1], c->Dpred, c->mlX, c->mly, c->mlt, c->mlDx, c->ml_sums, c->rep_X, c->rep_t, c->net.master, c->net.wbf, c->net.grad,
+                  c->hist_xyz[1], c->Shalf, c->Smhalf, c->DL, c->Dpred, c->mlX, c->mly, c->mlt, c->mlDx, c->ml_sums, c->rep_X, c->rep_t, c->net.master, c->net.wbf, c->net.grad,
                   c->net.m, c->net.v, c->net.loss,
                   c->d_tr, c->d_nf, c->d_Z, c->d_xyz, c->d_boys, c->d_counter, c->d_flag, c->d_sched, c->d_red, c->d_ticket, c->d_pairs, c->d_tasks, c->d_schwarz,
                   c->S, c->H, c->Tk, c->V, c->A, c->L, c->Linv, c->Bp, c->Yp, c->Bu, c->Dp, c->Jp, c->Xo, c->Sw, c->Sv,
@@ -718,6 +724,7 @@ static void free_all(rihf_ctx* c) {
 static void compute_geometry(rihf_ctx* c) {
   cudaStream_t s = c->stream;
   const int N = c->N, NA = c->NA;
+  ++c->geom_serial;
   LaCtx la = c->la();
   IntegralCtx ic = c->ic();
   // shell centres
@@ -1566,6 +1573,108 @@ static void diis_error(rihf_ctx* c) {
   c->launches += 1;
 }
 
+// S^{1/2} and S^{-1/2} of the current geometry's overlap matrix, once per
+// geometry.  With nothing below lindep_tau (the orthogonaliser kept all N
+// functions) by the scaled coupled Newton-Schulz iteration
+//   Y_0 = S / c, Z_0 = I,  T = (3I - Z Y) / 2,  Y <- Y T,  Z <- T Z
+// (c = ||S||_F >= lambda_max), which converges to (S/c)^{1/2}, (S/c)^{-1/2}
+// quadratically once the small eigenvalues have grown by ~1.5x per step:
+// eigenvectors of nearly degenerate small eigenvalues of S, as an eigensolver
+// returns them mixed inside their cluster, would leave errors of
+// (sqrt(w_i) - sqrt(w_j)) times the mixing.  With dropped eigenvalues, from
+// the eigenpairs: S^{1/2} over all, the pseudo-inverse S^{-1/2} over the kept.
+static void lowdin_factors(rihf_ctx* c) {
+  if (c->lowdin_serial == c->geom_serial) return;
+  LaCtx la = c->la();
+  cudaStream_t s = c->stream;
+  const int N = c->N;
+  const size_t n2 = (size_t)N * N;
+  if (!c->Shalf) {
+    c->Shalf = dalloc<double>(n2);
+    c->Smhalf = dalloc<double>(n2);
+    c->DL = dalloc<double>(n2);
+  }
+  TraceScope t(c->tracer, s, "Loewdin factors S^{+-1/2} of the guess", 0.0, 0);
+  if (c->nind == N) {
+    dot(la, N * N, c->S, c->S, c->scal + 4);
+    double fro2 = 0.0;
+    RIHF_CUDA(cudaMemcpyAsync(&fro2, c->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+    RIHF_CUDA(cudaStreamSynchronize(s));
+    const double cs = std::sqrt(fro2);
+    if (!(cs > 0.0) || !std::isfinite(cs)) throw RihfError(RIHF_ERR_NOT_POSITIVE_DEFINITE, "overlap matrix norm");
+    scale_copy(la, N * N, 1.0 / cs, c->S, c->Shalf);   // Y
+    identity(la, c->Smhalf, N);                         // Z
+    for (int it = 0; it < 80; ++it) {
+      GemmArgs e;   // T1 = Z Y
+      e.M = N; e.N = N; e.K = N; e.A = c->Smhalf; e.lda = N; e.B = c->Shalf; e.ldb = N; e.C = c->T1; e.ldc = N;
+      dgemm(la, e);
+      if (it >= 12 && it % 3 == 0) {
+        eig_check_mb_kernel<<<kRedBlocks, 256, 0, s>>>(c->T1, N, 1.0, 0, c->d_red, c->d_ticket, c->scal + 4);
+        RIHF_LAUNCH_CHECK();
+        double r = 1.0;
+        RIHF_CUDA(cudaMemcpyAsync(&r, c->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+        RIHF_CUDA(cudaStreamSynchronize(s));
+        if (r < 1e-12) break;     // Z Y = I: the factors stand
+      }
+      identity(la, c->T2, N);
+      axpby(la, N * N, -0.5, c->T1, 1.5, c->T2, c->T2);        // T2 = (3I - Z Y) / 2
+      GemmArgs y;   // T1 = Y T2
+      y.M = N; y.N = N; y.K = N; y.A = c->Shalf; y.lda = N; y.B = c->T2; y.ldb = N; y.C = c->T1; y.ldc = N;
+      dgemm(la, y);
+      GemmArgs z;   // DL = T2 Z
+      z.M = N; z.N = N; z.K = N; z.A = c->T2; z.lda = N; z.B = c->Smhalf; z.ldb = N; z.C = c->DL; z.ldc = N;
+      dgemm(la, z);
+      RIHF_CUDA(cudaMemcpyAsync(c->Shalf, c->T1, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
+      RIHF_CUDA(cudaMemcpyAsync(c->Smhalf, c->DL, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
+      c->launches += 6;
+    }
+    scale_copy(la, N * N, std::sqrt(cs), c->Shalf, c->Shalf);
+    scale_copy(la, N * N, 1.0 / std::sqrt(cs), c->Smhalf, c->Smhalf);
+    RIHF_CUDA(cudaStreamSynchronize(s));
+  } else {
+    eigh(la, c->S, N, c->Sw, c->Sv, c->eigws, 4, nullptr);
+    std::vector<double> w(N);
+    RIHF_CUDA(cudaMemcpyAsync(w.data(), c->Sw, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+    RIHF_CUDA(cudaStreamSynchronize(s));
+    int k0 = 0;
+    while (k0 < N && w[k0] <= c->opt.lindep_tau) ++k0;
+    if (k0 == N) throw RihfError(RIHF_ERR_NOT_POSITIVE_DEFINITE, "overlap matrix has no eigenvalue above lindep_tau");
+    std::vector<double> r(N);
+    for (int i = 0; i < N; ++i) r[i] = std::sqrt(std::max(w[i], 0.0));
+    RIHF_CUDA(cudaMemcpyAsync(c->dvec, r.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    scale_cols(la, c->Sv, c->dvec, N, N, c->T1);                  // U diag(sqrt w)
+    GemmArgs g1;   // S^{1/2} = T1 U^T
+    g1.M = N; g1.N = N; g1.K = N; g1.A = c->T1; g1.lda = N; g1.B = c->Sv; g1.ldb = N; g1.transB = true;
+    g1.C = c->Shalf; g1.ldc = N;
+    dgemm(la, g1);
+    RIHF_CUDA(cudaStreamSynchronize(s));
+    const int nk = N - k0;
+    for (int i = 0; i < nk; ++i) r[i] = 1.0 / std::sqrt(w[k0 + i]);
+    RIHF_CUDA(cudaMemcpyAsync(c->dvec, r.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, s));
+    copy_cols(la, c->Sv + k0, N, N, nk, 1.0, c->T2);              // kept eigenvectors
+    scale_cols(la, c->T2, c->dvec, N, nk, c->T1);                 // U_k diag(1/sqrt w_k)
+    GemmArgs g2;   // S^{-1/2} = T1 U_k^T
+    g2.M = N; g2.N = N; g2.K = nk; g2.A = c->T1; g2.lda = nk; g2.B = c->T2; g2.ldb = nk; g2.transB = true;
+    g2.C = c->Smhalf; g2.ldc = N;
+    dgemm(la, g2);
+    RIHF_CUDA(cudaStreamSynchronize(s));
+    c->launches += 6;
+  }
+  c->lowdin_serial = c->geom_serial;
+}
+
+// out = X D X for symmetric X (in place allowed: out may be D).
+static void congruence(rihf_ctx* c, const double* X, const double* D, double* out) {
+  LaCtx la = c->la();
+  const int N = c->N;
+  GemmArgs g1;   // T1 = X D
+  g1.M = N; g1.N = N; g1.K = N; g1.A = X; g1.lda = N; g1.B = D; g1.ldb = N; g1.C = c->T1; g1.ldc = N;
+  dgemm(la, g1);
+  GemmArgs g2;   // out = T1 X
+  g2.M = N; g2.N = N; g2.K = N; g2.A = c->T1; g2.lda = N; g2.B = X; g2.ldb = N; g2.C = out; g2.ldc = N;
+  dgemm(la, g2);
+}
+
 // After a converged SCF: one online training step of the network on this
 // geometry's example (features built for the guess, target = converged D minus
 // the extrapolation, scaled by the RMS of the first target), then push D, S and
@@ -1574,11 +1683,17 @@ static void learn_and_push_history(rihf_ctx* c) {
   cudaStream_t s = c->stream;
   const int N = c->N;
   const size_t n2 = (size_t)N * N;
+  const double* Dh = c->D;   // the density as the history holds it
+  if (c->hist_lowdin) {
+    lowdin_factors(c);
+    congruence(c, c->Shalf, c->D, c->DL);
+    Dh = c->DL;
+  }
   if (c->pending_example) {
     const int M = N * (N + 1) / 2;
     if (c->ml_scale <= 0.0) {
       // RMS of the first target fixes the output scale
-      mlp_target(s, N, c->D, c->mlDx, 1.0, c->mlt);
+      mlp_target(s, N, Dh, c->mlDx, 1.0, c->mlt);
       std::vector<float> t(M);
       RIHF_CUDA(cudaMemcpyAsync(t.data(), c->mlt, sizeof(float) * M, cudaMemcpyDeviceToHost, s));
       RIHF_CUDA(cudaStreamSynchronize(s));
@@ -1586,7 +1701,7 @@ static void learn_and_push_history(rihf_ctx* c) {
       for (float v : t) ss += (double)v * v;
       c->ml_scale = std::max(std::sqrt(ss / M), 1e-12);
     }
-    mlp_target(s, N, c->D, c->mlDx, c->ml_scale, c->mlt);
+    mlp_target(s, N, Dh, c->mlDx, c->ml_scale, c->mlt);
     // out-of-sample check on this (not yet seen) example, then replay
     // training on the last kReplay examples
     float first[2] = {0.f, 0.f};
@@ -1613,7 +1728,7 @@ static void learn_and_push_history(rihf_ctx* c) {
   }
   std::swap(c->hist_D[2], c->hist_D[1]);
   std::swap(c->hist_D[1], c->hist_D[0]);
-  RIHF_CUDA(cudaMemcpyAsync(c->hist_D[0], c->D, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
+  RIHF_CUDA(cudaMemcpyAsync(c->hist_D[0], Dh, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
   RIHF_CUDA(cudaMemcpyAsync(c->hist_S, c->S, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
   std::swap(c->hist_xyz[1], c->hist_xyz[0]);
   RIHF_CUDA(cudaMemcpyAsync(c->hist_xyz[0], c->d_xyz, sizeof(double) * 3 * c->natoms, cudaMemcpyDeviceToDevice, s));
@@ -1949,6 +2064,11 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
     unpack_sym_batch(la, c->Bp, c->NA, N, c->npp, c->Bu);
     c->bu_is_B = true;
   }
+  if ((guess == 3 || guess == 4) && !c->hist_lowdin) {
+    // the history restarts in the Loewdin representation
+    c->hist_lowdin = true;
+    c->nhist = 0;
+  }
   if (guess == 1) {
     if (!C_guess) return RIHF_ERR_INVALID_ARG;
     RIHF_CUDA(cudaMemcpyAsync(c->C, C_guess, sizeof(double) * n2, cudaMemcpyHostToDevice, s));
@@ -1985,10 +2105,12 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
     c->pending_example = false;
     if (guess >= 3 && c->nhist >= 3) {
       // density guess: three-point extrapolation D_x = 3 D_t - 3 D_{t-1} + D_{t-2}
-      // (guess 3) plus, for guess 4, the network's correction once it beats
-      // the extrapolation on its last training example; the previous occupied
-      // orbitals are carried into the predicted occupied space by one
-      // projection Co <- D_pred S Co before the Gram-Schmidt step below
+      // of the Loewdin densities (guess 3) plus, for guess 4, the network's
+      // correction once it beats the extrapolation on its last training
+      // example, taken back to the AO basis with this geometry's S^{-1/2};
+      // the previous occupied orbitals are carried into the predicted
+      // occupied space by one projection Co <- D_pred S Co before the
+      // Gram-Schmidt step below
       if (c->ml_sd <= 0.0) {
         // feature scales: RMS of the first observed changes (fixed from then on)
         mlp_scale_sums(s, N, c->hist_D[0], c->hist_D[1], c->S, c->hist_S, c->d_xyz, c->hist_xyz[0], c->d_ao_atom,
@@ -2012,7 +2134,9 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
       const bool use_net = guess == 4 && c->net_on && c->trained_steps >= 3 && r3[1] < 0.8;
       if (use_net) mlp_forward(s, c->net, c->mlX, M, c->mly);
       mlp_apply(s, N, c->mlDx, use_net ? c->mly : nullptr, c->ml_scale, c->Dpred);
-      c->launches += use_net ? 3 : 2;
+      lowdin_factors(c);
+      congruence(c, c->Smhalf, c->Dpred, c->Dpred);
+      c->launches += use_net ? 5 : 4;
       c->last_guess = use_net ? 4 : 3;
       c->pending_example = guess == 4 && c->net_on && c->trained_steps < c->train_steps;
       GemmArgs p1;   // T1 (N x no) = S Co
@@ -2548,6 +2672,10 @@ int rihf_learn_config(rihf_ctx* c, int hidden, int train_steps, int adam_iters, 
   mlp_round_weights(s, c->net);
   RIHF_CUDA(cudaStreamSynchronize(s));
   c->net_on = true;
+  if (!c->hist_lowdin) {   // the history restarts in the Loewdin representation
+    c->hist_lowdin = true;
+    c->nhist = 0;
+  }
   c->train_steps = train_steps;
   c->adam_iters = adam_iters;
   c->ml_lr = lr;
