@@ -271,7 +271,13 @@ constexpr int kSmemMax = 227 * 1024;
 constexpr int kSmemMin = 116 * 1024;   // more than half an SM's shared memory: one CTA per SM
 constexpr int kBookBytes = 1024;
 
+// One MMA of a K chunk, precomputed: TMEM column offset (bit 31: the MMA
+// starts its accumulator when the chunk opens a group), A and B descriptor
+// address offsets in 16-byte units, instruction descriptor.
+constexpr int kMaxChunkMmas = 32;
+
 struct OzBook {
+  uint4 mmas[kMaxChunkMmas];
   uint64_t full[kMaxStages], empty[kMaxStages];
   uint64_t accfull, accempty[kOzMaxDigits];
   uint64_t item_full[kItemSlots], item_empty[kItemSlots];
@@ -421,10 +427,33 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       // BF16 x BF16 -> FP32, M = 128; N is set per MMA
       const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzTileM >> 4) << 24);
       const int planes_per_mma = 256 / TN;
+      // the MMAs of one chunk: per K step j, A plane t and group of B planes,
+      // one MMA; the B planes u = 1..s+1-t lie one after another in shared
+      // memory with the same 8-row-group stride, so up to 256 / TN of them form
+      // one operand of N = count * TN rows, and the product (t, u) lands on the
+      // columns of anti-diagonal t + u.  Built once: the issue loop then costs
+      // a table load and two adds per MMA instead of the index arithmetic.
+      int nm = 0;
+      for (int j = 0; j < kOzChunk / 16; ++j)
+        for (int t = 1; t <= s; ++t)
+          for (int u0 = 1; u0 <= s + 1 - t; u0 += planes_per_mma) {
+            const int np = min(planes_per_mma, s + 2 - t - u0);
+            uint4 m;
+            m.x = (uint32_t)((t + u0 - 2) * TN) | ((t == 1 && j == 0) ? 0x80000000u : 0u);
+            m.y = (uint32_t)(((t - 1) * kPlaneElems * 2 + j * 256) >> 4);
+            m.z = (uint32_t)(((u0 - 1) * b_plane + j * 256) >> 4);
+            m.w = idesc0 | ((uint32_t)((np * TN) >> 3) << 17);
+            if (nm < kMaxChunkMmas) bk->mmas[nm] = m;
+            ++nm;
+          }
+      if (nm > kMaxChunkMmas) {   // cannot happen for s <= 7 and TN >= 16 (at most 28)
+        *abort = 1;
+        nm = 0;
+      }
       uint32_t i = 0, grp = 0;
       int last_st = -1;
       uint32_t last_par = 0;
-      bool ok = true;
+      bool ok = !*abort;
       for (int q = 0; ok; ++q) {
         const int slot = q % kItemSlots;
         if (!oz_wait(&bk->item_full[slot], (q / kItemSlots) & 1, abort)) break;
@@ -441,38 +470,28 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           }
           tc_fence_after();
           const bool first = (c - c0) % T.G == 0, last = (c - c0) % T.G == T.G - 1 || c == c1 - 1;
+          if (first && grp > 0) {   // every diagonal of the last group read out
+            for (int d = 0; d < s && ok; ++d)
+              if (!oz_wait(&bk->accempty[d], (grp - 1) & 1, abort)) ok = false;
+            if (!ok) {
+              ++i;
+              break;
+            }
+            tc_fence_after();
+          }
           // descriptors of the stage's first planes; plane and K-step offsets go
           // into the 14-bit address field (shared addresses stay below 256 KB)
           const uint32_t a_s = smem_addr(smem + (size_t)st * T.stage_bytes);
           const uint64_t a_d0 = smem_desc(a_s), b_d0 = smem_desc(a_s + a_bytes);
-          // one MMA per (K step, A plane t, group of B planes): the B planes
-          // u = 1..s+1-t lie one after another in shared memory with the same
-          // 8-row-group stride, so up to 256 / TN of them form one operand of
-          // N = count * TN rows, and the product (t, u) lands on the columns
-          // of anti-diagonal t + u
-          for (int j = 0; j < kOzChunk / 16 && ok; ++j)
-            for (int t = 1; t <= s && ok; ++t) {
-              if (t == 1 && j == 0 && first && grp > 0) {   // every diagonal read out
-                for (int d = 0; d < s && ok; ++d)
-                  if (!oz_wait(&bk->accempty[d], (grp - 1) & 1, abort)) ok = false;
-                if (!ok) break;
-                tc_fence_after();
-              }
-              const uint64_t ad = a_d0 + (uint64_t)(((t - 1) * kPlaneElems * 2 + j * 256) >> 4);
-              for (int u0 = 1; u0 <= s + 1 - t; u0 += planes_per_mma) {
-                const int np = min(planes_per_mma, s + 2 - t - u0);
-                const uint32_t id = idesc0 | ((uint32_t)((np * TN) >> 3) << 17);
-                const uint64_t bd = b_d0 + (uint64_t)(((u0 - 1) * b_plane + j * 256) >> 4);
-                mma_bf16(taddr + (uint32_t)((t + u0 - 2) * TN), ad, bd, id, (t == 1 && j == 0 && first) ? 0u : 1u);
-              }
-            }
+#pragma unroll 4
+          for (int e = 0; e < nm; ++e) {
+            const uint4 m = bk->mmas[e];
+            const uint32_t init = (m.x >> 31) & (first ? 1u : 0u);
+            mma_bf16(taddr + (m.x & 0x7FFFFFFFu), a_d0 + m.y, b_d0 + m.z, m.w, init ^ 1u);
+          }
           mma_commit(&bk->empty[st]);   // the stage is free once these MMAs are done
           last_st = st;
           last_par = (i / T.nst) & 1;
-          if (!ok) {
-            ++i;
-            break;
-          }
           if (last) {
             mma_commit(&bk->accfull);
             ++grp;
