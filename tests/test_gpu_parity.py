@@ -158,17 +158,19 @@ def test_water8_three_centre_integrals_full(water8):
 
 
 def test_water8_energy_and_gradient(water8):
-    """Energy to 1e-9 Eh.  Forces to 1e-7 Eh/bohr: for this even-tempered
-    auxiliary set cond((P|Q)) = 2.4e9, and a 1e-13 relative perturbation of the
-    oracle's own (mu nu|P) moves its gradient by 6.7e-8 Eh/bohr (and its energy
-    by 1.7e-8 Eh), so FP64 integrals from two different recursions cannot agree
-    to 1e-8 in the forces here; the monomer (cond ~1e6) is held to 1e-8."""
+    """Energy to 1e-9 Eh, forces to 1e-7 Eh/bohr against the oracle's stored
+    values, both sides converged to max|e| < 5e-9: an SCF error e moves these
+    forces by about e / gap times the orbital-response coupling, 6e-8 Eh/bohr
+    here (measured), so the bound follows the convergence level."""
     mol, gold, ctx = water8
     out = ctx.scf()
     assert out["converged"]
-    assert abs(out["energy"] - gold["energy"]) <= 1e-9
+    dE = abs(out["energy"] - gold["energy"])
     grad = ctx.gradient()
-    assert np.abs(grad - np.array(gold["grad"])).max() <= 1e-7
+    dF = np.abs(grad - np.array(gold["grad"])).max()
+    print("\n(H2O)8 FP64: |dE| = %.2e Eh, max|dF| = %.2e Eh/bohr" % (dE, dF))
+    assert dE <= 1e-9
+    assert dF <= 1e-7
     assert np.abs(grad.sum(0)).max() <= 1e-9
 
 
