@@ -10,6 +10,7 @@
 // invariance, d/dC = -(d/dA + d/dB).
 #include <cmath>
 
+#include "../../include/rihf.h"
 #include "integrals.cuh"
 #include "os_hgp.cuh"
 
@@ -183,6 +184,106 @@ __device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, co
 
 // ------------------------------------------------------------ 3-centre
 
+// One task of the fused 3-centre derivative contraction: the shell triple
+// (pairs[tk.x] | tk.y) (tk.y < 0: ~tk.y, mirrored for p > q), its derivative
+// integrals contracted with the pair-packed Y; the per-atom sums are added
+// into grad.  smem: this task group's slice.
+template <int W>
+__device__ inline void grad_eri3_task(const DevShells& prim, const DevShells& aux, const ShellPair* __restrict__ pairs,
+                                      const PairTable& ptab, int2 tk, const double* __restrict__ boys,
+                                      const double* __restrict__ Y, double* grad, double* smem, int lane) {
+  const int N = prim.nfunc;
+  const long long Npp = (long long)N * (N + 1) / 2;
+  const bool mir = tk.y < 0;   // marked task: triples with p > q run mirrored (mirror_prim3)
+  int ip = tk.x, sc = mir ? ~tk.y : tk.y;
+  int sa = pairs[ip].a, sb = pairs[ip].b;
+  if (prim.l[sa] < prim.l[sb]) { int t = sa; sa = sb; sb = t; }   // Y is symmetric in mu, nu
+  int ata = prim.atom[sa], atb = prim.atom[sb], atc = aux.atom[sc];
+  if (ata == atb && atb == atc) return;   // one-centre: derivative sums to zero
+  int la = prim.l[sa], lb = prim.l[sb], lc = aux.l[sc];
+  DerivPlan pl(la, lb, lc, mir);
+  double* Fm = smem + pl.fm;
+  double* vrr = smem + pl.vrr;
+  double* etr = smem + pl.etr;
+  int accsz = acc_size(pl.emin, pl.emax, lc);
+  const PairPrim* pr = ptab.pp + ptab.off[ip];
+  const int nab = prim.nprim[sa] * prim.nprim[sb];
+  // one primitive triple: the derivative weights 2 alpha and 2 beta scale the
+  // contractions instead of weighted sums; a forward triple with a ket above
+  // s leaves its final values in place as the last transfer level, a
+  // mirrored one stores them once into acc0
+  const bool one = nab == 1 && aux.nprim[sc] == 1;
+  const bool one_mir = one && mir && pr[0].p > aux.exps[aux.pstart[sc]];
+  const bool single = one && !one_mir && lc > 0;
+  if (!single && !one_mir)
+    for (int i = lane; i < 3 * accsz; i += W) smem[pl.acc0 + i] = 0.0;
+  const double* A = prim.xyz + 3 * sa;
+  const double* B = prim.xyz + 3 * sb;
+  const double* C = aux.xyz + 3 * sc;
+  EtrShape sh{lc, pl.emin, pl.emax};
+  const EtrShape shm{pl.emax, lc, lc};
+  const double ABv[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
+  for (int ab = 0; ab < nab; ++ab) {
+    const PairPrim q = pr[ab];
+    for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
+      const int ic = aux.pstart[sc] + pc;
+      Prim3 t = make_prim3_pp(q, aux.exps[ic], aux.iexps[ic], aux.coefs[ic], C, ABv);
+      for (int m = lane; m <= pl.L; m += W) Fm[m] = boys_eval(m, t.T, boys);
+      __syncwarp(lane_group_mask<W>());
+      if (mir && t.p > t.q) {
+        const Prim3 tm = mirror_prim3(t);
+        warp_vrr<W>(vrr, pl.L, tm, Fm, lane);
+        warp_etr<W>(vrr, pl.L, etr, shm, tm, Fm, lane);
+        if (one_mir) {
+          warp_acc_mirror<W, true>(vrr, pl.L, etr, shm, pl.emin, pl.emax, lc, 1.0, smem + pl.acc0, lane);
+        } else {
+          warp_acc_mirror<W>(vrr, pl.L, etr, shm, pl.emin, pl.emax, lc, 1.0, smem + pl.acc0, lane);
+          warp_acc_mirror<W>(vrr, pl.L, etr, shm, pl.emin, pl.emax, lc, 2.0 * q.alpha, smem + pl.accA, lane);
+          warp_acc_mirror<W>(vrr, pl.L, etr, shm, pl.emin, pl.emax, lc, 2.0 * q.beta, smem + pl.accB, lane);
+        }
+        continue;
+      }
+      warp_vrr<W>(vrr, pl.L, t, Fm, lane);
+      warp_etr<W>(vrr, pl.L, etr, sh, t, Fm, lane);
+      if (!single) {
+        warp_acc_level<W>(vrr, pl.L, etr, sh, 1.0, smem + pl.acc0, lane);
+        warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.alpha, smem + pl.accA, lane);
+        warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.beta, smem + pl.accB, lane);
+      }
+    }
+  }
+  // Y block -> Cartesian (Y pair-packed per auxiliary function, symmetric)
+  int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
+  const double* Yc = Y + (long long)aux.ao[sc] * Npp;
+  const int mu0 = prim.ao[sa], nu0 = prim.ao[sb];
+  auto ysrc = [&](int k, int a, int b) -> double {
+    const long long r = mu0 + a, q = nu0 + b;
+    return r >= q ? Yc[k * Npp + r * (r + 1) / 2 + q] : Yc[k * Npp + q * (q + 1) / 2 + r];
+  };
+  warp_back_transform<W>(ysrc, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
+                      prim.tr + lb * kTrStride * kTrStride, aux.tr + lc * kTrStride * kTrStride, nfa, nfb, nfc,
+                      smem + pl.t1, smem + pl.t2, smem + pl.ycart, lane);
+  double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
+  double g[6];
+  if (single || one_mir) {
+    const double* lvl = single ? etr + sh.level_off(lc) : smem + pl.acc0;
+    warp_deriv_contract<W>(pl, smem, lvl, lvl, lvl, 2.0 * pr[0].alpha, 2.0 * pr[0].beta, la, lb, lc, AB, lane, g);
+  } else {
+    warp_deriv_contract<W>(pl, smem, smem + pl.acc0, smem + pl.accA, smem + pl.accB, 1.0, 1.0, la, lb, lc, AB,
+                           lane, g);
+  }
+  double wgt = (sa == sb) ? 1.0 : 2.0;
+  for (int i = 0; i < 6; ++i) g[i] = warp_sum<W>(g[i]) * wgt;
+  if (lane == 0) {
+    for (int x = 0; x < 3; ++x) {
+      atomicAdd(grad + 3 * ata + x, g[x]);
+      atomicAdd(grad + 3 * atb + x, g[3 + x]);
+      atomicAdd(grad + 3 * atc + x, -(g[x] + g[3 + x]));
+    }
+  }
+  __syncwarp(lane_group_mask<W>());
+}
+
 template <int W>
 __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells aux,
                                                        const ShellPair* __restrict__ pairs, PairTable ptab,
@@ -192,100 +293,35 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
   extern __shared__ double smem_all[];
   const int lane = threadIdx.x % W;
   double* smem = smem_all + (threadIdx.x / W) * slice;   // this task group's slice
-  const int N = prim.nfunc;
-  const long long Npp = (long long)N * (N + 1) / 2;
   for (;;) {
     long long task = warp_next<W>(counter, lane);
     if (task >= ntask) break;
-    const int2 tk = tasks[task];
-    const bool mir = tk.y < 0;   // marked task: triples with p > q run mirrored (mirror_prim3)
-    int ip = tk.x, sc = mir ? ~tk.y : tk.y;
-    int sa = pairs[ip].a, sb = pairs[ip].b;
-    if (prim.l[sa] < prim.l[sb]) { int t = sa; sa = sb; sb = t; }   // Y is symmetric in mu, nu
-    int ata = prim.atom[sa], atb = prim.atom[sb], atc = aux.atom[sc];
-    if (ata == atb && atb == atc) continue;   // one-centre: derivative sums to zero
-    int la = prim.l[sa], lb = prim.l[sb], lc = aux.l[sc];
-    DerivPlan pl(la, lb, lc, mir);
-    double* Fm = smem + pl.fm;
-    double* vrr = smem + pl.vrr;
-    double* etr = smem + pl.etr;
-    int accsz = acc_size(pl.emin, pl.emax, lc);
-    const PairPrim* pr = ptab.pp + ptab.off[ip];
-    const int nab = prim.nprim[sa] * prim.nprim[sb];
-    // one primitive triple: the derivative weights 2 alpha and 2 beta scale the
-    // contractions instead of weighted sums; a forward triple with a ket above
-    // s leaves its final values in place as the last transfer level, a
-    // mirrored one stores them once into acc0
-    const bool one = nab == 1 && aux.nprim[sc] == 1;
-    const bool one_mir = one && mir && pr[0].p > aux.exps[aux.pstart[sc]];
-    const bool single = one && !one_mir && lc > 0;
-    if (!single && !one_mir)
-      for (int i = lane; i < 3 * accsz; i += W) smem[pl.acc0 + i] = 0.0;
-    const double* A = prim.xyz + 3 * sa;
-    const double* B = prim.xyz + 3 * sb;
-    const double* C = aux.xyz + 3 * sc;
-    EtrShape sh{lc, pl.emin, pl.emax};
-    const EtrShape shm{pl.emax, lc, lc};
-    const double ABv[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
-    for (int ab = 0; ab < nab; ++ab) {
-      const PairPrim q = pr[ab];
-      for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
-        const int ic = aux.pstart[sc] + pc;
-        Prim3 t = make_prim3_pp(q, aux.exps[ic], aux.iexps[ic], aux.coefs[ic], C, ABv);
-        for (int m = lane; m <= pl.L; m += W) Fm[m] = boys_eval(m, t.T, boys);
-        __syncwarp(lane_group_mask<W>());
-        if (mir && t.p > t.q) {
-          const Prim3 tm = mirror_prim3(t);
-          warp_vrr<W>(vrr, pl.L, tm, Fm, lane);
-          warp_etr<W>(vrr, pl.L, etr, shm, tm, Fm, lane);
-          if (one_mir) {
-            warp_acc_mirror<W, true>(vrr, pl.L, etr, shm, pl.emin, pl.emax, lc, 1.0, smem + pl.acc0, lane);
-          } else {
-            warp_acc_mirror<W>(vrr, pl.L, etr, shm, pl.emin, pl.emax, lc, 1.0, smem + pl.acc0, lane);
-            warp_acc_mirror<W>(vrr, pl.L, etr, shm, pl.emin, pl.emax, lc, 2.0 * q.alpha, smem + pl.accA, lane);
-            warp_acc_mirror<W>(vrr, pl.L, etr, shm, pl.emin, pl.emax, lc, 2.0 * q.beta, smem + pl.accB, lane);
-          }
-          continue;
-        }
-        warp_vrr<W>(vrr, pl.L, t, Fm, lane);
-        warp_etr<W>(vrr, pl.L, etr, sh, t, Fm, lane);
-        if (!single) {
-          warp_acc_level<W>(vrr, pl.L, etr, sh, 1.0, smem + pl.acc0, lane);
-          warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.alpha, smem + pl.accA, lane);
-          warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.beta, smem + pl.accB, lane);
-        }
-      }
+    grad_eri3_task<W>(prim, aux, pairs, ptab, tasks[task], boys, Y, grad, smem, lane);
+  }
+}
+
+// The same over a batch of geometries (task t of geometry g with off[g] <= t <
+// off[g + 1]): each geometry's Y in, its per-atom gradient (out) added to.
+template <int W>
+__global__ void __launch_bounds__(32) grad_eri3_batch_kernel(const GeomTasks* __restrict__ geoms,
+                                                             const long long* __restrict__ off, int ngeom,
+                                                             const double* __restrict__ boys, int* counter,
+                                                             int slice) {
+  extern __shared__ double smem_all[];
+  const int lane = threadIdx.x % W;
+  double* smem = smem_all + (threadIdx.x / W) * slice;
+  const long long ntask = off[ngeom];
+  for (;;) {
+    long long task = warp_next<W>(counter, lane);
+    if (task >= ntask) break;
+    int lo = 0, hi = ngeom;   // off[lo] <= task < off[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (off[mid] <= task) lo = mid;
+      else hi = mid;
     }
-    // Y block -> Cartesian (Y pair-packed per auxiliary function, symmetric)
-    int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
-    const double* Yc = Y + (long long)aux.ao[sc] * Npp;
-    const int mu0 = prim.ao[sa], nu0 = prim.ao[sb];
-    auto ysrc = [&](int k, int a, int b) -> double {
-      const long long r = mu0 + a, q = nu0 + b;
-      return r >= q ? Yc[k * Npp + r * (r + 1) / 2 + q] : Yc[k * Npp + q * (q + 1) / 2 + r];
-    };
-    warp_back_transform<W>(ysrc, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
-                        prim.tr + lb * kTrStride * kTrStride, aux.tr + lc * kTrStride * kTrStride, nfa, nfb, nfc,
-                        smem + pl.t1, smem + pl.t2, smem + pl.ycart, lane);
-    double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
-    double g[6];
-    if (single || one_mir) {
-      const double* lvl = single ? etr + sh.level_off(lc) : smem + pl.acc0;
-      warp_deriv_contract<W>(pl, smem, lvl, lvl, lvl, 2.0 * pr[0].alpha, 2.0 * pr[0].beta, la, lb, lc, AB, lane, g);
-    } else {
-      warp_deriv_contract<W>(pl, smem, smem + pl.acc0, smem + pl.accA, smem + pl.accB, 1.0, 1.0, la, lb, lc, AB,
-                             lane, g);
-    }
-    double wgt = (sa == sb) ? 1.0 : 2.0;
-    for (int i = 0; i < 6; ++i) g[i] = warp_sum<W>(g[i]) * wgt;
-    if (lane == 0) {
-      for (int x = 0; x < 3; ++x) {
-        atomicAdd(grad + 3 * ata + x, g[x]);
-        atomicAdd(grad + 3 * atb + x, g[3 + x]);
-        atomicAdd(grad + 3 * atc + x, -(g[x] + g[3 + x]));
-      }
-    }
-    __syncwarp(lane_group_mask<W>());
+    const GeomTasks& G = geoms[lo];
+    grad_eri3_task<W>(G.prim, G.aux, G.pairs, G.ptab, G.tasks[task - off[lo]], boys, G.Y, G.out, smem, lane);
   }
 }
 
@@ -575,6 +611,42 @@ void launch_grad_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShe
     if (W == 8) run(grad_eri3_kernel<8>);
     else if (W == 16) run(grad_eri3_kernel<16>);
     else run(grad_eri3_kernel<32>);
+    RIHF_LAUNCH_CHECK();
+    if (ic.launches) *ic.launches += 1;
+  }
+}
+
+void launch_grad_eri3_batch(const IntegralCtx& ic, const std::vector<BatchGeom>& batch, int ngroups,
+                            BatchTables& t) {
+  const int n = (int)batch.size();
+  if (n == 0) return;
+  if (n > t.cap) throw RihfError(RIHF_ERR_INVALID_ARG, "launch_grad_eri3_batch: batch tables too small");
+  for (int g = 0; g < ngroups; ++g) {
+    std::vector<GeomTasks> geoms(n);
+    std::vector<long long> off(n + 1, 0);
+    int slice_bytes = 0;
+    for (int i = 0; i < n; ++i) {
+      geoms[i] = batch[i].g;
+      geoms[i].tasks = batch[i].groups[g].tasks;
+      off[i + 1] = off[i] + batch[i].groups[g].ntask;
+      if (batch[i].groups[g].ntask > 0) slice_bytes = std::max(slice_bytes, batch[i].groups[g].smem_grad);
+    }
+    if (off[n] == 0) continue;
+    GeomTasks* dg = t.geoms + (size_t)g * t.cap;
+    long long* doff = t.off + (size_t)g * (t.cap + 1);
+    RIHF_CUDA(cudaMemcpyAsync(dg, geoms.data(), sizeof(GeomTasks) * n, cudaMemcpyHostToDevice, ic.stream));
+    RIHF_CUDA(cudaMemcpyAsync(doff, off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, ic.stream));
+    RIHF_CUDA(cudaStreamSynchronize(ic.stream));   // the host arrays are temporaries
+    const int W = task_group_width(g), slice = slice_bytes / (int)sizeof(double);
+    const int smem = (32 / W) * slice * (int)sizeof(double);
+    RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+    auto run = [&](auto kernel) {
+      raise_smem_limit((const void*)kernel, smem);
+      kernel<<<grid_for_smem(smem), 32, smem, ic.stream>>>(dg, doff, n, ic.boys, ic.counter, slice);
+    };
+    if (W == 8) run(grad_eri3_batch_kernel<8>);
+    else if (W == 16) run(grad_eri3_batch_kernel<16>);
+    else run(grad_eri3_batch_kernel<32>);
     RIHF_LAUNCH_CHECK();
     if (ic.launches) *ic.launches += 1;
   }

@@ -2,9 +2,11 @@
 // their derivative contractions.  One warp (one 32-thread block) per task; tasks
 // are handed out through a device counter so that heavy and light shell classes
 // balance across the 152 SMs.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
+#include "../../include/rihf.h"
 #include "integrals.cuh"
 #include "os_hgp.cuh"
 
@@ -144,6 +146,91 @@ int smem_eri3_doubles(int la, int lb, int lc, bool mirror) {
 
 // ------------------------------------------------------------ (mu nu|P)
 
+// One task of the 3-centre integrals: the shell triple (pairs[tk.x] | tk.y)
+// (tk.y < 0: ~tk.y, with the mirrored recursion for triples with p > q),
+// written pair-packed into T.  smem: this task group's slice.
+template <int W>
+__device__ inline void eri3_task(const DevShells& prim, const DevShells& aux, const ShellPair* __restrict__ pairs,
+                                 const PairTable& ptab, int2 tk, const double* __restrict__ boys,
+                                 double* __restrict__ T, double* smem, int lane) {
+  const int N = prim.nfunc;
+  const size_t Npp = (size_t)N * (N + 1) / 2;
+  // a negative auxiliary index marks a task whose triples with p > q take the
+  // mirrored recursion (see mirror_prim3)
+  const bool mir = tk.y < 0;
+  int ip = tk.x, sc = mir ? ~tk.y : tk.y;
+  int sa = pairs[ip].a, sb = pairs[ip].b;
+  // compute with la >= lb (cheaper HRR); the stored block keeps mu in pairs[ip].a
+  const bool swp = prim.l[sa] < prim.l[sb];
+  if (swp) { int t = sa; sa = sb; sb = t; }
+  int la = prim.l[sa], lb = prim.l[sb], lc = aux.l[sc];
+  int emin = la, emax = la + lb, L = emax + lc;
+  Eri3Plan pl(la, lb, lc, emin, emax, 1, mir);
+  double* Fm = smem + pl.fm;
+  double* vrr = smem + pl.vrr;
+  double* etr = smem + pl.etr;
+  double* acc = smem + pl.acc;
+  const int nab = prim.nprim[sa] * prim.nprim[sb];
+  // one primitive triple and a ket above s: the last electron-transfer level
+  // ([e][ke][kc], e in [emin, emax]) is the accumulator itself, read in place
+  const PairPrim* pr = ptab.pp + ptab.off[ip];
+  // one primitive triple: a mirrored one writes its final values into acc
+  // (no zeroing, no sums); a forward one with a ket above s leaves them in
+  // place as the last transfer level
+  const bool one = nab == 1 && aux.nprim[sc] == 1;
+  const bool one_mir = one && mir && pr[0].p > aux.exps[aux.pstart[sc]];
+  const bool single = one && !one_mir && lc > 0;
+  int accsz = acc_size(emin, emax, lc);
+  if (!single && !one_mir)
+    for (int i = lane; i < accsz; i += W) acc[i] = 0.0;
+  const double* A = prim.xyz + 3 * sa;
+  const double* B = prim.xyz + 3 * sb;
+  const double* C = aux.xyz + 3 * sc;
+  const double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
+  EtrShape sh{lc, emin, emax};
+  const EtrShape shm{emax, lc, lc};
+  for (int ab = 0; ab < nab; ++ab) {
+    const PairPrim q = pr[ab];
+    for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
+      const int ic = aux.pstart[sc] + pc;
+      Prim3 t = make_prim3_pp(q, aux.exps[ic], aux.iexps[ic], aux.coefs[ic], C, AB);
+      for (int m = lane; m <= L; m += W) Fm[m] = boys_eval(m, t.T, boys);
+      __syncwarp(lane_group_mask<W>());
+      if (mir && t.p > t.q) {
+        const Prim3 tm = mirror_prim3(t);
+        warp_vrr<W>(vrr, L, tm, Fm, lane);
+        warp_etr<W>(vrr, L, etr, shm, tm, Fm, lane);
+        if (one_mir) warp_acc_mirror<W, true>(vrr, L, etr, shm, emin, emax, lc, 1.0, acc, lane);
+        else warp_acc_mirror<W>(vrr, L, etr, shm, emin, emax, lc, 1.0, acc, lane);
+        continue;
+      }
+      warp_vrr<W>(vrr, L, t, Fm, lane);
+      if (single) warp_etr<W>(vrr, L, etr, sh, t, Fm, lane);
+      else warp_etr_accumulate<W>(vrr, L, etr, sh, t, 1.0, acc, Fm, lane);
+    }
+  }
+  const double* cart = warp_hrr<W>(single ? etr + sh.level_off(lc) : acc, emin, la, lb, lc, AB, smem + pl.hrr,
+                                   pl.half, lane);
+  int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
+  const double* out = warp_transform3<W>(cart, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
+                                      prim.tr + lb * kTrStride * kTrStride, aux.tr + lc * kTrStride * kTrStride,
+                                      nfa, nfb, nfc, smem + pl.t1, smem + pl.t2, lane);
+  // pair-packed store: row = the function of pairs[ip].a (the larger shell
+  // index, so the larger function index), column = that of pairs[ip].b;
+  // inside a diagonal shell block only row >= column
+  const int mu0 = prim.ao[sa], nu0 = prim.ao[sb], P0 = aux.ao[sc];
+  const bool diag = pairs[ip].a == pairs[ip].b;
+  const int n = nfa * nfb * nfc;
+  for (int idx = lane; idx < n; idx += W) {
+    int sbb = idx % nfb, r = idx / nfb;
+    int saa = r % nfa, scc = r / nfa;
+    const long long row = swp ? nu0 + sbb : mu0 + saa, col = swp ? mu0 + saa : nu0 + sbb;
+    if (diag && row < col) continue;
+    T[(size_t)(P0 + scc) * Npp + row * (row + 1) / 2 + col] = out[(saa * nfb + sbb) * nfc + scc];
+  }
+  __syncwarp(lane_group_mask<W>());
+}
+
 template <int W>
 __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux, const ShellPair* __restrict__ pairs,
                                                   PairTable ptab, const int2* __restrict__ tasks, long long ntask,
@@ -152,86 +239,35 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
   extern __shared__ double smem_all[];
   const int lane = threadIdx.x % W;
   double* smem = smem_all + (threadIdx.x / W) * slice;   // this task group's slice
-  const int N = prim.nfunc;
-  const size_t Npp = (size_t)N * (N + 1) / 2;
   for (;;) {
     long long task = warp_next_task<W>(counter, lane);
     if (task >= ntask) break;
-    const int2 tk = tasks[task];
-    // a negative auxiliary index marks a task whose triples with p > q take the
-    // mirrored recursion (see mirror_prim3)
-    const bool mir = tk.y < 0;
-    int ip = tk.x, sc = mir ? ~tk.y : tk.y;
-    int sa = pairs[ip].a, sb = pairs[ip].b;
-    // compute with la >= lb (cheaper HRR); the stored block keeps mu in pairs[ip].a
-    const bool swp = prim.l[sa] < prim.l[sb];
-    if (swp) { int t = sa; sa = sb; sb = t; }
-    int la = prim.l[sa], lb = prim.l[sb], lc = aux.l[sc];
-    int emin = la, emax = la + lb, L = emax + lc;
-    Eri3Plan pl(la, lb, lc, emin, emax, 1, mir);
-    double* Fm = smem + pl.fm;
-    double* vrr = smem + pl.vrr;
-    double* etr = smem + pl.etr;
-    double* acc = smem + pl.acc;
-    const int nab = prim.nprim[sa] * prim.nprim[sb];
-    // one primitive triple and a ket above s: the last electron-transfer level
-    // ([e][ke][kc], e in [emin, emax]) is the accumulator itself, read in place
-    const PairPrim* pr = ptab.pp + ptab.off[ip];
-    // one primitive triple: a mirrored one writes its final values into acc
-    // (no zeroing, no sums); a forward one with a ket above s leaves them in
-    // place as the last transfer level
-    const bool one = nab == 1 && aux.nprim[sc] == 1;
-    const bool one_mir = one && mir && pr[0].p > aux.exps[aux.pstart[sc]];
-    const bool single = one && !one_mir && lc > 0;
-    int accsz = acc_size(emin, emax, lc);
-    if (!single && !one_mir)
-      for (int i = lane; i < accsz; i += W) acc[i] = 0.0;
-    const double* A = prim.xyz + 3 * sa;
-    const double* B = prim.xyz + 3 * sb;
-    const double* C = aux.xyz + 3 * sc;
-    const double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
-    EtrShape sh{lc, emin, emax};
-    const EtrShape shm{emax, lc, lc};
-    for (int ab = 0; ab < nab; ++ab) {
-      const PairPrim q = pr[ab];
-      for (int pc = 0; pc < aux.nprim[sc]; ++pc) {
-        const int ic = aux.pstart[sc] + pc;
-        Prim3 t = make_prim3_pp(q, aux.exps[ic], aux.iexps[ic], aux.coefs[ic], C, AB);
-        for (int m = lane; m <= L; m += W) Fm[m] = boys_eval(m, t.T, boys);
-        __syncwarp(lane_group_mask<W>());
-        if (mir && t.p > t.q) {
-          const Prim3 tm = mirror_prim3(t);
-          warp_vrr<W>(vrr, L, tm, Fm, lane);
-          warp_etr<W>(vrr, L, etr, shm, tm, Fm, lane);
-          if (one_mir) warp_acc_mirror<W, true>(vrr, L, etr, shm, emin, emax, lc, 1.0, acc, lane);
-          else warp_acc_mirror<W>(vrr, L, etr, shm, emin, emax, lc, 1.0, acc, lane);
-          continue;
-        }
-        warp_vrr<W>(vrr, L, t, Fm, lane);
-        if (single) warp_etr<W>(vrr, L, etr, sh, t, Fm, lane);
-        else warp_etr_accumulate<W>(vrr, L, etr, sh, t, 1.0, acc, Fm, lane);
-      }
+    eri3_task<W>(prim, aux, pairs, ptab, tasks[task], boys, T, smem, lane);
+  }
+}
+
+// The same over a batch of geometries: task t belongs to the geometry g with
+// off[g] <= t < off[g + 1] (an int64 offsets table of the geometries' task
+// counts in this class group), its own shells, pairs and output.
+template <int W>
+__global__ void __launch_bounds__(32) eri3_batch_kernel(const GeomTasks* __restrict__ geoms,
+                                                        const long long* __restrict__ off, int ngeom,
+                                                        const double* __restrict__ boys, int* counter, int slice) {
+  extern __shared__ double smem_all[];
+  const int lane = threadIdx.x % W;
+  double* smem = smem_all + (threadIdx.x / W) * slice;
+  const long long ntask = off[ngeom];
+  for (;;) {
+    long long task = warp_next_task<W>(counter, lane);
+    if (task >= ntask) break;
+    int lo = 0, hi = ngeom;   // off[lo] <= task < off[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (off[mid] <= task) lo = mid;
+      else hi = mid;
     }
-    const double* cart = warp_hrr<W>(single ? etr + sh.level_off(lc) : acc, emin, la, lb, lc, AB, smem + pl.hrr,
-                                     pl.half, lane);
-    int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
-    const double* out = warp_transform3<W>(cart, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
-                                        prim.tr + lb * kTrStride * kTrStride, aux.tr + lc * kTrStride * kTrStride,
-                                        nfa, nfb, nfc, smem + pl.t1, smem + pl.t2, lane);
-    // pair-packed store: row = the function of pairs[ip].a (the larger shell
-    // index, so the larger function index), column = that of pairs[ip].b;
-    // inside a diagonal shell block only row >= column
-    const int mu0 = prim.ao[sa], nu0 = prim.ao[sb], P0 = aux.ao[sc];
-    const bool diag = pairs[ip].a == pairs[ip].b;
-    const int n = nfa * nfb * nfc;
-    for (int idx = lane; idx < n; idx += W) {
-      int sbb = idx % nfb, r = idx / nfb;
-      int saa = r % nfa, scc = r / nfa;
-      const long long row = swp ? nu0 + sbb : mu0 + saa, col = swp ? mu0 + saa : nu0 + sbb;
-      if (diag && row < col) continue;
-      T[(size_t)(P0 + scc) * Npp + row * (row + 1) / 2 + col] = out[(saa * nfb + sbb) * nfc + scc];
-    }
-    __syncwarp(lane_group_mask<W>());
+    const GeomTasks& G = geoms[lo];
+    eri3_task<W>(G.prim, G.aux, G.pairs, G.ptab, G.tasks[task - off[lo]], boys, G.out, smem, lane);
   }
 }
 
@@ -683,6 +719,55 @@ void launch_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& 
     if (W == 8) run(eri3_kernel<8>);
     else if (W == 16) run(eri3_kernel<16>);
     else run(eri3_kernel<32>);
+    RIHF_LAUNCH_CHECK();
+    if (ic.launches) *ic.launches += 1;
+  }
+}
+
+// Shared host side of the batched launches: per class group, the descriptors
+// (with that group's task pointers) and the offsets table, uploaded into t.
+static bool batch_tables(const IntegralCtx& ic, const std::vector<BatchGeom>& batch, int g, BatchTables& t,
+                         bool grad, int& slice_bytes, long long& ntask) {
+  const int n = (int)batch.size();
+  std::vector<GeomTasks> geoms(n);
+  std::vector<long long> off(n + 1, 0);
+  slice_bytes = 0;
+  for (int i = 0; i < n; ++i) {
+    geoms[i] = batch[i].g;
+    geoms[i].tasks = batch[i].groups[g].tasks;
+    off[i + 1] = off[i] + batch[i].groups[g].ntask;
+    if (batch[i].groups[g].ntask > 0)
+      slice_bytes = std::max(slice_bytes, grad ? batch[i].groups[g].smem_grad : batch[i].groups[g].smem_eri3);
+  }
+  ntask = off[n];
+  if (ntask == 0) return false;
+  RIHF_CUDA(cudaMemcpyAsync(t.geoms + (size_t)g * t.cap, geoms.data(), sizeof(GeomTasks) * n,
+                            cudaMemcpyHostToDevice, ic.stream));
+  RIHF_CUDA(cudaMemcpyAsync(t.off + (size_t)g * (t.cap + 1), off.data(), sizeof(long long) * (n + 1),
+                            cudaMemcpyHostToDevice, ic.stream));
+  RIHF_CUDA(cudaStreamSynchronize(ic.stream));   // the host arrays are temporaries
+  return true;
+}
+
+void launch_eri3_batch(const IntegralCtx& ic, const std::vector<BatchGeom>& batch, int ngroups, BatchTables& t) {
+  const int n = (int)batch.size();
+  if (n == 0) return;
+  if (n > t.cap) throw RihfError(RIHF_ERR_INVALID_ARG, "launch_eri3_batch: batch tables too small");
+  for (int g = 0; g < ngroups; ++g) {
+    int slice_bytes = 0;
+    long long ntask = 0;
+    if (!batch_tables(ic, batch, g, t, false, slice_bytes, ntask)) continue;
+    const int W = task_group_width(g), slice = slice_bytes / (int)sizeof(double);
+    const int smem = (32 / W) * slice * (int)sizeof(double);
+    RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));
+    auto run = [&](auto kernel) {
+      set_smem((const void*)kernel, smem);
+      kernel<<<grid_for(smem), 32, smem, ic.stream>>>(t.geoms + (size_t)g * t.cap, t.off + (size_t)g * (t.cap + 1),
+                                                      n, ic.boys, ic.counter, slice);
+    };
+    if (W == 8) run(eri3_batch_kernel<8>);
+    else if (W == 16) run(eri3_batch_kernel<16>);
+    else run(eri3_batch_kernel<32>);
     RIHF_LAUNCH_CHECK();
     if (ic.launches) *ic.launches += 1;
   }

@@ -104,6 +104,41 @@ void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lpr
 void launch_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& aux, const ShellPair* pairs,
                  const PairTable& pt, const TaskGroup* groups, int ngroups, double* T);
 
+// One geometry of a batched 3-centre launch (A14): its shells, pair list,
+// primitive-pair table and tasks of the launch's class group; out = its
+// pair-packed T (integrals) or its per-atom gradient (derivative
+// contraction, with Y its pair-packed fitted density).
+struct GeomTasks {
+  DevShells prim, aux;
+  const ShellPair* pairs = nullptr;
+  PairTable ptab;
+  const int2* tasks = nullptr;
+  double* out = nullptr;
+  const double* Y = nullptr;
+};
+// A batch of geometries for the batched launches: per geometry its
+// descriptor (tasks unset), class groups and task counts.
+struct BatchGeom {
+  GeomTasks g;
+  const TaskGroup* groups = nullptr;
+};
+// Device tables of a batched launch: ngeom descriptors and ngeom + 1 offsets
+// per class group (kTaskGroups x ngeom, kTaskGroups x (ngeom + 1)).
+struct BatchTables {
+  GeomTasks* geoms = nullptr;
+  long long* off = nullptr;
+  int cap = 0;
+};
+// One launch per class group over every geometry's tasks of that group:
+// task t of the launch belongs to geometry g with off[g] <= t < off[g + 1]
+// (an int64 offsets table), so ragged geometries share the SMs with no
+// per-geometry launch.  Shared memory per task: the largest of the
+// geometries' slices of the group.  Uploads the tables (host -> device on
+// ic.stream, then waits for them: the host arrays are temporaries).
+void launch_eri3_batch(const IntegralCtx& ic, const std::vector<BatchGeom>& batch, int ngroups, BatchTables& t);
+void launch_grad_eri3_batch(const IntegralCtx& ic, const std::vector<BatchGeom>& batch, int ngroups,
+                            BatchTables& t);
+
 // Metric A[P][Q] = (P|Q) (full symmetric matrix).
 void launch_eri2(const IntegralCtx& ic, const DevShells& aux, int max_la, double* A);
 

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <functional>
 #include <thread>
 #include <vector>
 
@@ -542,6 +543,7 @@ struct rihf_ctx {
   int tc_builds = 0, confirm_builds = 0, last_iters = 0, last_digits = 0;
   double flops_eri3 = 0.0, flops_grad3 = 0.0;   // algorithmic FP64 operations of the 3-centre kernels
   int k_nsplit = 0;             // K splits of the tensor-core K GEMM (0: not tuned yet)
+  int k_tn = 0;                 // its column tile
   // per-iteration CUDA graphs (Fock build + DIIS error), one per variant:
   // [0] FP64 build, [d] tensor-core build with d digits
   struct IterGraph {
@@ -721,7 +723,13 @@ static void free_all(rihf_ctx* c) {
 
 // Geometry-dependent part of setup: shell centres, one-electron, metric,
 // Cholesky, 3-centre integrals, fit, orthogonaliser.
-static void compute_geometry(rihf_ctx* c) {
+static void compute_geometry_rest(rihf_ctx* c);
+
+// Integrals and fit of the current geometry.  defer_eri3: stop once the
+// primitive-pair table is built, leaving the 3-centre integrals to a batched
+// launch over several contexts (launch_eri3_batch) and the rest of the setup
+// to compute_geometry_rest.
+static void compute_geometry(rihf_ctx* c, bool defer_eri3 = false) {
   cudaStream_t s = c->stream;
   const int N = c->N, NA = c->NA;
   ++c->geom_serial;
@@ -787,9 +795,22 @@ static void compute_geometry(rihf_ctx* c) {
   // substitution over the Naux x N(N+1)/2 matrix; an explicit L^{-1} product
   // loses accuracy when cond(A) reaches 1e9 (diffuse auxiliary sets)
   RIHF_CUDA(cudaMemsetAsync(c->Bp, 0, sizeof(double) * (size_t)NA * c->npp, s));
+  if (defer_eri3) {
+    launch_pair_prims(ic, P, c->d_pairs, c->npairs, c->d_pp_off, c->d_pp);
+    return;
+  }
   { TraceScope t(c->tracer, s, "eri3_kernel (mu nu|P)", c->flops_eri3, 0);
     launch_pair_prims(ic, P, c->d_pairs, c->npairs, c->d_pp_off, c->d_pp);
     launch_eri3(ic, P, X, c->d_pairs, c->ptab(), c->groups, kTaskGroups, c->Bp); }
+  compute_geometry_rest(c);
+}
+
+// The fit, the planes or expansion of B and the orthogonaliser, after the
+// 3-centre integrals of this geometry are in Bp.
+static void compute_geometry_rest(rihf_ctx* c) {
+  cudaStream_t s = c->stream;
+  const int N = c->N, NA = c->NA;
+  LaCtx la = c->la();
   if (c->trsm_sc.X.planes) {
     // mixed mode: rank-64 updates on the tensor cores (7 digits), panels in FP64
     TraceScope t(c->tracer, s, "fit trsm B=L^-1 T (tcgen05 digit updates)", (double)NA * NA * c->npp, 0);
@@ -1467,45 +1488,63 @@ static void fock_build(rihf_ctx* c) {
 // axis (one CTA per lower tile and split; at most 30 chunks per split) is timed
 // for a few candidates around one wave of CTAs on the first build (H is
 // already formed), and the fastest is kept for the context.
-static int tune_k_splits(rihf_ctx* c, int digits, int kch, int lower_tiles) {
+// Output tiles of the lower triangle of an N x N result with column tile TN.
+static int k_lower_tiles(int N, int TN) {
+  int n = 0;
+  for (int mt = 0; mt * kOzTileM < N; ++mt)
+    for (int nt = 0; nt * TN < N; ++nt)
+      if (mt * kOzTileM + kOzTileM - 1 >= nt * TN) ++n;
+  return n;
+}
+
+// Tile-shape autotuner of the tensor-core K GEMM (K = -1/2 H H^T, K dimension
+// (P, i)): times each candidate column tile (the whole of N when N <= 64, else
+// 32 and 64) with K split counts around one wave of items over the SMs, on
+// this context's own H, and keeps the fastest (c->k_tn, c->k_nsplit).
+static void tune_k_gemm(rihf_ctx* c, int digits, int kch) {
   LaCtx la = c->la();
   const int N = c->N, NA = c->NA, no = c->nocc;
   const int lo = (kch + kOzMaxChunksPerBlock - 1) / kOzMaxChunksPerBlock;
-  const int wave = std::max(1, c->sms / std::max(1, lower_tiles));
-  std::vector<int> cand;
-  for (int k : {wave / 2, wave, 2 * wave, 4 * wave}) {
-    const int v = std::min(std::max(k, lo), kch);
-    if (std::find(cand.begin(), cand.end(), v) == cand.end()) cand.push_back(v);
-  }
-  int best = cand[0];
-  float best_ms = 1e30f;
+  std::vector<int> tns;
+  if (N <= kOzMaxTN) tns.push_back((N + 15) / 16 * 16);
+  else tns = {32, kOzMaxTN};
   cudaEvent_t e0, e1;
   RIHF_CUDA(cudaEventCreate(&e0));
   RIHF_CUDA(cudaEventCreate(&e1));
-  for (int ns : cand) {
-    const int kbc = (kch + ns - 1) / ns;
-    float ms = 0.f;
-    for (int rep = 0; rep < 2; ++rep) {   // the first pass warms up
-      RIHF_CUDA(cudaEventRecord(e0, c->stream));
-      OzOperand Hop = oz_slice(la, c->Hb, N, NA * no, no, 1, (long long)N * no, no, digits, kbc, c->Hz);
-      RIHF_CUDA(cudaMemsetAsync(c->K, 0, sizeof(double) * N * N, c->stream));
-      OzGemmArgs g2;
-      g2.A = Hop; g2.B = Hop; g2.M = N; g2.N = N; g2.s = digits; g2.alpha = -0.5; g2.C = c->K; g2.cs_m1 = N;
-      g2.cs_n = 1; g2.atomic = true; g2.lower_only = true;
-      oz_gemm(la, g2);
-      RIHF_CUDA(cudaEventRecord(e1, c->stream));
-      RIHF_CUDA(cudaEventSynchronize(e1));
-      RIHF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  float best_ms = 1e30f;
+  for (int tn : tns) {
+    const int wave = std::max(1, c->sms / std::max(1, k_lower_tiles(N, tn)));
+    std::vector<int> cand;
+    for (int k : {wave / 2, wave, 2 * wave, 4 * wave}) {
+      const int v = std::min(std::max(k, lo), kch);
+      if (std::find(cand.begin(), cand.end(), v) == cand.end()) cand.push_back(v);
     }
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = ns;
+    for (int ns : cand) {
+      const int kbc = (kch + ns - 1) / ns;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {   // the first pass warms up
+        RIHF_CUDA(cudaEventRecord(e0, c->stream));
+        OzOperand Hop = oz_slice(la, c->Hb, N, NA * no, no, 1, (long long)N * no, no, digits, kbc, c->Hz);
+        RIHF_CUDA(cudaMemsetAsync(c->K, 0, sizeof(double) * N * N, c->stream));
+        OzGemmArgs g2;
+        g2.A = Hop; g2.B = Hop; g2.M = N; g2.N = N; g2.s = digits; g2.alpha = -0.5; g2.C = c->K; g2.cs_m1 = N;
+        g2.cs_n = 1; g2.atomic = true; g2.lower_only = true; g2.tn = tn;
+        oz_gemm(la, g2);
+        RIHF_CUDA(cudaEventRecord(e1, c->stream));
+        RIHF_CUDA(cudaEventSynchronize(e1));
+        RIHF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        c->k_tn = tn;
+        c->k_nsplit = ns;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (c->verbose || getenv("RIHF_VERBOSE")) fprintf(stderr, "rihf: K GEMM splits %d (%.3f ms)\n", best, best_ms);
-  return best;
+  if (c->verbose || getenv("RIHF_VERBOSE"))
+    fprintf(stderr, "rihf: K GEMM column tile %d, splits %d (%.3f ms)\n", c->k_tn, c->k_nsplit, best_ms);
 }
 
 static void fock_build_tc(rihf_ctx* c, int digits) {
@@ -1525,12 +1564,9 @@ static void fock_build_tc(rihf_ctx* c, int digits) {
   // K blocks of the (P, i) axis: enough splits to cover the SMs, at most
   // kOzMaxChunksPerBlock chunks each (int64 headroom of the accumulators)
   const int kch = (NA * no + kOzChunk - 1) / kOzChunk;
-  const int TN = N <= kOzMaxTN ? (N + 15) / 16 * 16 : kOzMaxTN;   // as oz_gemm picks it
-  int lower_tiles = 0;
-  for (int mt = 0; mt * kOzTileM < N; ++mt)
-    for (int nt = 0; nt * TN < N; ++nt)
-      if (mt * kOzTileM + kOzTileM - 1 >= nt * TN) ++lower_tiles;
-  if (c->k_nsplit <= 0) c->k_nsplit = tune_k_splits(c, digits, kch, lower_tiles);
+  if (c->k_nsplit <= 0) tune_k_gemm(c, digits, kch);
+  const int TN = c->k_tn;
+  const int lower_tiles = k_lower_tiles(N, TN);
   const int kbc = (kch + c->k_nsplit - 1) / c->k_nsplit;
   OzOperand Hop;
   { TraceScope t(c->tracer, c->stream, "RI-K H digit planes (oz_slice)", (double)NA * N * no * (8 + 2 * digits), 1);
@@ -1538,7 +1574,7 @@ static void fock_build_tc(rihf_ctx* c, int digits) {
   RIHF_CUDA(cudaMemsetAsync(c->K, 0, sizeof(double) * n2, c->stream));
   OzGemmArgs g2;   // K = -1/2 sum_(P, i) H[mu][(P, i)] H[nu][(P, i)], lower tiles
   g2.A = Hop; g2.B = Hop; g2.M = N; g2.N = N; g2.s = digits; g2.alpha = -0.5; g2.C = c->K; g2.cs_m1 = N;
-  g2.cs_n = 1; g2.atomic = true; g2.lower_only = true;
+  g2.cs_n = 1; g2.atomic = true; g2.lower_only = true; g2.tn = TN;
   { TraceScope t(c->tracer, c->stream, "RI-K K=-1/2 sum H H^T (tcgen05 digits)",
                  2.0 * lower_tiles * kOzTileM * TN * (double)kch * kOzChunk * prod, 3);
     oz_gemm(la, g2);
@@ -2018,18 +2054,13 @@ static void fock_build_factor(rihf_ctx* c, int variant) {
       OzOperand Cop = oz_slice(la, c->Ct, no, N, 1, no, 0, N, variant, 0, c->Cz);
       form_H(c, variant, &Cop, "SAD RI-K H=B Fs (tcgen05 digits)");
       const int kch = (NA * no + kOzChunk - 1) / kOzChunk;
-      const int TN = N <= kOzMaxTN ? (N + 15) / 16 * 16 : kOzMaxTN;
-      int lower_tiles = 0;
-      for (int mt = 0; mt * kOzTileM < N; ++mt)
-        for (int nt = 0; nt * TN < N; ++nt)
-          if (mt * kOzTileM + kOzTileM - 1 >= nt * TN) ++lower_tiles;
-      if (c->k_nsplit <= 0) c->k_nsplit = tune_k_splits(c, variant, kch, lower_tiles);   // writes K
+      if (c->k_nsplit <= 0) tune_k_gemm(c, variant, kch);   // writes K
       if (first) RIHF_CUDA(cudaMemsetAsync(c->K, 0, sizeof(double) * n2, s));
       const int kbc = (kch + c->k_nsplit - 1) / c->k_nsplit;
       OzOperand Hop = oz_slice(la, c->Hb, N, NA * no, no, 1, (long long)N * no, no, variant, kbc, c->Hz);
       OzGemmArgs g2;
       g2.A = Hop; g2.B = Hop; g2.M = N; g2.N = N; g2.s = variant; g2.alpha = -0.5; g2.C = c->K; g2.cs_m1 = N;
-      g2.cs_n = 1; g2.atomic = true; g2.lower_only = true;
+      g2.cs_n = 1; g2.atomic = true; g2.lower_only = true; g2.tn = c->k_tn;
       oz_gemm(la, g2);
     } else {
       form_H(c, 0, nullptr, "SAD RI-K H=B Fs (dgemm)");
@@ -2317,13 +2348,11 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   RIHF_API_END
 }
 
-int rihf_gradient(rihf_ctx* c, double* grad) {
-  RIHF_API_BEGIN
-  if (!c || !grad) return RIHF_ERR_INVALID_ARG;
-  if (!c->converged) {
-    g_last_error = "rihf_gradient needs a converged rihf_scf on this context";
-    return RIHF_ERR_STATE;
-  }
+// The gradient up to its per-atom parts on the device (Eq. rihf_gradient):
+// fitted densities, Y, Z and the fused derivative contractions.  defer_eri3:
+// the 3-centre contraction is left to a batched launch over several contexts
+// (launch_grad_eri3_batch into grad_parts + 6 natoms).
+static void gradient_launch(rihf_ctx* c, bool defer_eri3) {
   LaCtx la = c->la();
   IntegralCtx ic = c->ic();
   const int N = c->N, NA = c->NA, no = c->nocc, nat = c->natoms;
@@ -2487,10 +2516,18 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
   double* g_two = c->grad_parts + 9 * nat;
   { TraceScope t(c->tracer, s, "grad_one_electron_kernel", 0.0, 0);
     launch_grad_one_electron(ic, c->prim(), c->max_lp, nat, c->d_Z, c->d_xyz, c->D, c->W, g_one, g_ovl); }
-  { TraceScope t(c->tracer, s, "grad_eri3_kernel (fused d(mu nu|P) . Y)", c->flops_grad3, 0);
-    launch_grad_eri3(ic, c->prim(), c->aux(), c->d_pairs, c->ptab(), c->groups, kTaskGroups, c->Yp, g_three); }
+  if (!defer_eri3) {
+    TraceScope t(c->tracer, s, "grad_eri3_kernel (fused d(mu nu|P) . Y)", c->flops_grad3, 0);
+    launch_grad_eri3(ic, c->prim(), c->aux(), c->d_pairs, c->ptab(), c->groups, kTaskGroups, c->Yp, g_three);
+  }
   { TraceScope t(c->tracer, s, "grad_eri2_kernel (fused d(P|Q) . Z)", (double)NA * NA * 8, 1);
     launch_grad_eri2(ic, c->aux(), c->max_la, c->Zm, g_two); }
+}
+
+// Per-atom parts back to the host, nuclear repulsion, the sum.
+static void gradient_finish(rihf_ctx* c, double* grad) {
+  cudaStream_t s = c->stream;
+  const int nat = c->natoms;
   c->grad_parts_h.assign(15 * nat, 0.0);
   RIHF_CUDA(cudaMemcpyAsync(c->grad_parts_h.data(), c->grad_parts, sizeof(double) * 12 * nat,
                             cudaMemcpyDeviceToHost, s));
@@ -2518,6 +2555,17 @@ int rihf_gradient(rihf_ctx* c, double* grad) {
     for (int p = 0; p < 5; ++p) t += c->grad_parts_h[p * 3 * nat + i];
     grad[i] = t;
   }
+}
+
+int rihf_gradient(rihf_ctx* c, double* grad) {
+  RIHF_API_BEGIN
+  if (!c || !grad) return RIHF_ERR_INVALID_ARG;
+  if (!c->converged) {
+    g_last_error = "rihf_gradient needs a converged rihf_scf on this context";
+    return RIHF_ERR_STATE;
+  }
+  gradient_launch(c, false);
+  gradient_finish(c, grad);
   return RIHF_OK;
   RIHF_API_END
 }
@@ -2703,38 +2751,166 @@ int rihf_batch_step(int nmol, rihf_ctx* const* ctx, const double* const* xyz, in
   if (nmol < 0 || (nmol > 0 && !ctx)) return RIHF_ERR_INVALID_ARG;
   for (int i = 0; i < nmol; ++i)
     if (!ctx[i]) return RIHF_ERR_INVALID_ARG;
+  for (int i = 0; i < nmol; ++i)
+    for (int j = 0; j < i; ++j)
+      if (ctx[i] == ctx[j]) return RIHF_ERR_INVALID_ARG;
   std::vector<size_t> goff(nmol + 1, 0);
   for (int i = 0; i < nmol; ++i) goff[i + 1] = goff[i] + 3 * (size_t)ctx[i]->natoms;
   std::vector<int> rc(nmol, RIHF_OK);
   std::vector<std::string> err(nmol);
-  auto work = [&](int w, int nw) {
-    for (int i = w; i < nmol; i += nw) {
-      rihf_ctx* c = ctx[i];
-      if (cudaSetDevice(c->opt.device) != cudaSuccess) {
-        rc[i] = RIHF_ERR_CUDA;
-        continue;
-      }
-      int r = RIHF_OK, it = 0;
-      double e = 0.0;
-      std::vector<double> gl;
-      double* gp = grads ? grads + goff[i] : (gl.resize(3 * (size_t)c->natoms), gl.data());
-      if (xyz && xyz[i]) r = rihf_update_geometry(c, xyz[i]);
-      if (r == RIHF_OK) r = rihf_scf(c, guess, nullptr, &e, nullptr, nullptr, nullptr, &it);
-      if (r == RIHF_OK) r = rihf_gradient(c, gp);
-      if (r != RIHF_OK) err[i] = rihf_last_error();
-      rc[i] = r;
-      if (energies) energies[i] = e;
-      if (iters) iters[i] = it;
-    }
-  };
+  // The 3-centre integrals and the 3-centre derivative contraction, the
+  // largest per-geometry launches, run as one launch per class group over all
+  // molecules (launch_eri3_batch / launch_grad_eri3_batch: ragged task lists
+  // behind an int64 offsets table) when every context lives on one device;
+  // everything else runs per context on its own stream, host threads driving
+  // the contexts between the batched launches.
+  bool batched = nmol > 1;
+  for (int i = 1; i < nmol && batched; ++i) batched = ctx[i]->opt.device == ctx[0]->opt.device;
   const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
   const int nw = std::max(1, std::min(nmol, nthreads > 0 ? nthreads : hw));
-  if (nw <= 1) {
-    work(0, 1);
-  } else {
-    std::vector<std::thread> pool;
-    for (int w = 0; w < nw; ++w) pool.emplace_back(work, w, nw);
-    for (auto& t : pool) t.join();
+  auto parallel = [&](const std::function<void(int)>& f) {
+    auto work = [&](int w) {
+      for (int i = w; i < nmol; i += nw) {
+        if (rc[i] != RIHF_OK) continue;
+        if (cudaSetDevice(ctx[i]->opt.device) != cudaSuccess) {
+          rc[i] = RIHF_ERR_CUDA;
+          err[i] = "cudaSetDevice failed";
+          continue;
+        }
+        try {
+          f(i);
+        } catch (const RihfError& e) {
+          rc[i] = e.code;
+          err[i] = e.what();
+        } catch (const CudaError& e) {
+          rc[i] = RIHF_ERR_CUDA;
+          err[i] = e.what();
+        } catch (const std::exception& e) {
+          rc[i] = RIHF_ERR_INVALID_ARG;
+          err[i] = e.what();
+        }
+      }
+    };
+    if (nw <= 1) {
+      work(0);
+    } else {
+      std::vector<std::thread> pool;
+      for (int w = 0; w < nw; ++w) pool.emplace_back(work, w);
+      for (auto& t : pool) t.join();
+    }
+  };
+  // batched launch over the contexts still in good standing, on a stream of
+  // its own that waits for every context's stream and that every context's
+  // stream then waits for
+  cudaStream_t bs = nullptr;
+  BatchTables tab;
+  int* bcount = nullptr;
+  std::vector<cudaEvent_t> evs;
+  auto release = [&]() {
+    if (tab.geoms) cudaFree(tab.geoms);
+    if (tab.off) cudaFree(tab.off);
+    if (bcount) cudaFree(bcount);
+    for (auto e : evs) cudaEventDestroy(e);
+    if (bs) cudaStreamDestroy(bs);
+  };
+  auto batched_launch = [&](bool grad) -> bool {
+    std::vector<BatchGeom> batch;
+    std::vector<int> members;
+    for (int i = 0; i < nmol; ++i) {
+      if (rc[i] != RIHF_OK) continue;
+      rihf_ctx* c = ctx[i];
+      BatchGeom b;
+      b.g.prim = c->prim();
+      b.g.aux = c->aux();
+      b.g.pairs = c->d_pairs;
+      b.g.ptab = c->ptab();
+      b.g.out = grad ? c->grad_parts + 6 * c->natoms : c->Bp;
+      b.g.Y = grad ? c->Yp : nullptr;
+      b.groups = c->groups;
+      batch.push_back(b);
+      members.push_back(i);
+    }
+    if (batch.empty()) return true;
+    try {
+      for (int i : members) {
+        RIHF_CUDA(cudaEventRecord(evs[i], ctx[i]->stream));
+        RIHF_CUDA(cudaStreamWaitEvent(bs, evs[i], 0));
+      }
+      IntegralCtx ic = ctx[members[0]]->ic();
+      ic.stream = bs;
+      ic.counter = bcount;
+      ic.launches = nullptr;
+      if (grad) launch_grad_eri3_batch(ic, batch, kTaskGroups, tab);
+      else launch_eri3_batch(ic, batch, kTaskGroups, tab);
+      RIHF_CUDA(cudaEventRecord(evs[nmol], bs));
+      for (int i : members) {
+        RIHF_CUDA(cudaStreamWaitEvent(ctx[i]->stream, evs[nmol], 0));
+        ctx[i]->launches += kTaskGroups;
+      }
+    } catch (const RihfError& e) {
+      g_last_error = std::string("batched launch: ") + e.what();
+      return false;
+    } catch (const CudaError& e) {
+      g_last_error = std::string("batched launch: ") + e.what();
+      return false;
+    }
+    return true;
+  };
+  if (batched) {
+    if (cudaSetDevice(ctx[0]->opt.device) != cudaSuccess) return RIHF_ERR_CUDA;
+    bool ok = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) == cudaSuccess;
+    tab.cap = nmol;
+    ok = ok && cudaMalloc(&tab.geoms, sizeof(GeomTasks) * (size_t)kTaskGroups * nmol) == cudaSuccess;
+    ok = ok && cudaMalloc(&tab.off, sizeof(long long) * (size_t)kTaskGroups * (nmol + 1)) == cudaSuccess;
+    ok = ok && cudaMalloc(&bcount, sizeof(int)) == cudaSuccess;
+    evs.resize(nmol + 1);
+    for (auto& e : evs) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      release();
+      g_last_error = "rihf_batch_step: could not create the batch stream and tables";
+      return RIHF_ERR_OOM;
+    }
+  }
+  std::vector<double> etmp(nmol, 0.0);
+  std::vector<int> itmp(nmol, 0);
+  // 1. geometry: one-electron, metric, Cholesky, pair tables (3-centre
+  //    integrals deferred to the batched launch)
+  parallel([&](int i) {
+    rihf_ctx* c = ctx[i];
+    if (xyz && xyz[i]) c->xyz.assign(xyz[i], xyz[i] + 3 * c->natoms);
+    c->converged = false;
+    compute_geometry(c, batched);
+  });
+  if (batched && !batched_launch(false)) {
+    release();
+    return RIHF_ERR_CUDA;
+  }
+  // 2. fit, SCF, gradient up to the 3-centre derivative contraction
+  parallel([&](int i) {
+    rihf_ctx* c = ctx[i];
+    if (batched) compute_geometry_rest(c);
+    int it = 0;
+    double e = 0.0;
+    const int r = rihf_scf(c, guess, nullptr, &e, nullptr, nullptr, nullptr, &it);
+    etmp[i] = e;
+    itmp[i] = it;
+    if (r != RIHF_OK) throw RihfError(r, rihf_last_error());
+    gradient_launch(c, batched);
+  });
+  if (batched && !batched_launch(true)) {
+    release();
+    return RIHF_ERR_CUDA;
+  }
+  // 3. the per-atom parts back and summed
+  parallel([&](int i) {
+    std::vector<double> gl;
+    double* gp = grads ? grads + goff[i] : (gl.resize(3 * (size_t)ctx[i]->natoms), gl.data());
+    gradient_finish(ctx[i], gp);
+  });
+  release();
+  for (int i = 0; i < nmol; ++i) {
+    if (energies) energies[i] = etmp[i];
+    if (iters) iters[i] = itmp[i];
   }
   for (int i = 0; i < nmol; ++i)
     if (rc[i] != RIHF_OK) {
