@@ -508,11 +508,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const uint32_t t_row = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
     // one thread polls, the other drain threads wait on a hardware named
     // barrier (spinning 256 threads would compete with the copy and MMA
-    // threads for issue slots and for the barrier unit)
+    // threads for issue slots and for the barrier unit); the poller is lane 0
+    // of warp 2, on a scheduler that neither the MMA warp (8) nor the copy
+    // warp (9) uses
     int nwait = 0;
     auto drain_wait = [&](uint64_t* bar, uint32_t parity) -> bool {
       const int k = nwait++ & 1;
-      if (tid == 0) bk->dwait[k] = oz_wait(bar, parity, abort) ? 1 : 0;
+      if (tid == 64) bk->dwait[k] = oz_wait(bar, parity, abort) ? 1 : 0;
       asm volatile("bar.sync 1, %0;" ::"r"(kDrainThreads) : "memory");
       return *(volatile int*)&bk->dwait[k] != 0;
     };
@@ -708,7 +710,9 @@ void oz_gemm(const LaCtx& la, const OzGemmArgs& g) {
   OzTiling T;
   T.M = g.M;
   T.N = g.N;
-  T.TN = g.N <= kOzMaxTN ? (g.N + 15) / 16 * 16 : kOzMaxTN;
+  if (g.tn < 0 || g.tn % 16 || g.tn > kOzMaxTN || (g.tn > 0 && g.N > g.tn && 128 % g.tn))
+    throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: bad column tile");
+  T.TN = g.tn > 0 ? g.tn : (g.N <= kOzMaxTN ? (g.N + 15) / 16 * 16 : kOzMaxTN);
   T.s = g.s;
   if (T.s * T.TN > kTmemCols) throw RihfError(RIHF_ERR_INVALID_ARG, "oz_gemm: accumulators exceed TMEM");
   T.mtiles = (g.M + kOzTileM - 1) / kOzTileM;

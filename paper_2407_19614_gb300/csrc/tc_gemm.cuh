@@ -79,6 +79,10 @@ struct OzGemmArgs {
   bool accumulate = false;
   bool lower_only = false;
   int symcols = 0;
+  // column tile TN: 0 picks the whole of N when N <= kOzMaxTN, else kOzMaxTN;
+  // otherwise a multiple of 16 that is at most kOzMaxTN and, when N > tn,
+  // divides 128 (a column tile never straddles a 128-row plane)
+  int tn = 0;
 };
 void oz_gemm(const LaCtx& la, const OzGemmArgs& g);
 
