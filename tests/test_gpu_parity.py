@@ -146,7 +146,7 @@ def water8():
     mol = W.water8(0)
     with open(GOLDEN) as f:
         gold = json.load(f)
-    ctx = R.Context(mol, conv_e=1e-10, conv_diis=5e-9, max_iter=100)
+    ctx = R.Context(mol, conv_e=1e-11, conv_diis=1e-9, max_iter=150)
     return mol, gold, ctx
 
 
@@ -158,10 +158,10 @@ def test_water8_three_centre_integrals_full(water8):
 
 
 def test_water8_energy_and_gradient(water8):
-    """Energy to 1e-9 Eh, forces to 1e-7 Eh/bohr against the oracle's stored
-    values, both sides converged to max|e| < 5e-9: an SCF error e moves these
-    forces by about e / gap times the orbital-response coupling, 6e-8 Eh/bohr
-    here (measured), so the bound follows the convergence level."""
+    """Energy to 1e-9 Eh, forces to 1e-8 Eh/bohr against the oracle's stored
+    values, both sides converged to max|e| < 1e-9 (an SCF error e moves these
+    forces by about e / gap times the orbital-response coupling: 5e-9 on both
+    sides left 6e-8 Eh/bohr)."""
     mol, gold, ctx = water8
     out = ctx.scf()
     assert out["converged"]
@@ -170,7 +170,7 @@ def test_water8_energy_and_gradient(water8):
     dF = np.abs(grad - np.array(gold["grad"])).max()
     print("\n(H2O)8 FP64: |dE| = %.2e Eh, max|dF| = %.2e Eh/bohr" % (dE, dF))
     assert dE <= 1e-9
-    assert dF <= 1e-7
+    assert dF <= 1e-8
     assert np.abs(grad.sum(0)).max() <= 1e-9
 
 
