@@ -39,6 +39,7 @@ C2_WORKLOAD = ("(H2O)32 RI-HF E+grad AIMD step, larger basis (primary O 4s3p2d1f
 UNIT = "AIMD steps/s"
 DT_FS = 0.5
 LA_LINDEP = 1e-6
+LA_MAXIT = 150
 CONV = dict(conv_e=1e-8, conv_diis=1e-7, max_iter=60)
 # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07
@@ -218,14 +219,18 @@ def run_learned_aimd(args):
     mol = W.water16(0)
     arms = {}
     for name, guess in (("extrapolated", 3), ("learned", 4)):
-        ctx = R.Context(mol, precision=R.PRECISION_MIXED, lindep_tau=LA_LINDEP, **CONV)
+        ctx = R.Context(mol, precision=R.PRECISION_MIXED, lindep_tau=LA_LINDEP, **dict(CONV, max_iter=LA_MAXIT))
         ctx.learn_config(hidden=256, train_steps=args.la_train, adam_iters=4, lr=1e-3, seed=0)
         t0 = time.perf_counter()
         tr = Trajectory(ctx, mol, 0, R, guess0=5)
         etot = [tr.total_energy()]
-        its, used, bad = [], [], 0
-        for _ in range(args.la_steps):
-            tr.step(guess=guess, allow_unconverged=True)
+        its, used, bad, stopped = [], [], 0, None
+        for k in range(args.la_steps):
+            try:
+                tr.step(guess=guess, allow_unconverged=True)
+            except R.RihfError as e:   # neither the guess nor SAD converged
+                stopped = "step %d: %s" % (k + 1, e)
+                break
             its.append(tr.last["iterations"])
             bad += 0 if tr.last["converged"] else 1
             used.append(ctx.learn_stats()["last_guess"] == 4)
@@ -239,13 +244,14 @@ def run_learned_aimd(args):
                       "scf_iters_per_step_after_training": float(its[after].mean()) if len(its[after]) else None,
                       "energy_drift_eh": float(etot[-1] - etot[0]),
                       "max_abs_total_energy_change_eh": float(np.abs(etot - etot[0]).max()),
-                      "network_used_steps": int(sum(used)), "unconverged_steps": bad, "wall_s": wall}
+                      "network_used_steps": int(sum(used)), "unconverged_steps": bad, "wall_s": wall,
+                      "steps_done": len(its), "stopped": stopped}
         print(name, json.dumps(arms[name]), file=sys.stderr, flush=True)
     print(json.dumps({"experiment": "learned SCF guess along AIMD",
                       "workload": "(H2O)16, N=384, Naux=1696, velocity Verlet dt 0.5 fs from seeded 300 K "
                                   "Maxwell-Boltzmann velocities, SAD start, mixed precision",
                       "steps": args.la_steps, "train_steps": args.la_train, "network": "12-256-1 tanh, BF16 weights",
-                      "conv": dict(CONV, lindep_tau=LA_LINDEP), "arms": arms}))
+                      "conv": dict(CONV, lindep_tau=LA_LINDEP, max_iter=LA_MAXIT), "arms": arms}))
     return 0
 
 
