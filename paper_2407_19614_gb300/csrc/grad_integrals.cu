@@ -59,6 +59,13 @@ struct DerivPlan {
                    hrr_scratch(la, lb + 1, lc, emax), lb > 0 ? hrr_scratch(la, lb - 1, lc, emax) : 0};
     for (int i = 0; i < 4; ++i)
       if (cand[i] / 2 > half) half = cand[i] / 2;
+    // the single-triple path's one recurrence over a in [emin, ...]: level b
+    // holds (a, b) for a in [emin, la + 1 + lb - b] (b <= lb) and a = la (b = lb + 1)
+    for (int b = 1; b <= lb + 1; ++b) {
+      const int lo = b == lb + 1 ? la : emin, hi = b == lb + 1 ? la : la + 1 + lb - b;
+      const int sz = (cart_offset(hi + 1) - cart_offset(lo)) * ncart(b) * ncart(lc);
+      if (sz > half) half = sz;
+    }
     t1 = hrr;
     t2 = hrr + half;
     total = hrr + 2 * half;
@@ -182,6 +189,111 @@ __device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, co
   }
 }
 
+// The same contraction for a single primitive triple (one array lvl for
+// all four shifted products, sA = 2 alpha, sB = 2 beta): one horizontal
+// recurrence over a in [emin, la + 1 + lb - b] at level b yields (la +- 1, lb)
+// at level lb, (la, lb - 1) at level lb - 1 and (la, lb + 1) at level lb + 1,
+// each contracted with Y as soon as it is built, instead of four recurrences
+// from the transfer level.
+template <int W = 32>
+__device__ inline void warp_deriv_contract_single(const DerivPlan& pl, double* smem, const double* lvl, double sA,
+                                                  double sB, int la, int lb, int lc, const double* AB, int lane,
+                                                  double g[6]) {
+  const int na = ncart(la), nb = ncart(lb), nc = ncart(lc);
+  const double* Y = smem + pl.ycart;
+  double* bufs[2] = {smem + pl.hrr, smem + pl.hrr + pl.half};
+  const int alo = pl.emin;
+  double gp[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, gm[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  // (la +- 1, lb) from the level holding b = lb (rows a in [alo, ...], nbb columns of b)
+  auto a_terms = [&](const double* I, int nbb) {
+    for (int idx = lane; idx < na * nb * nc; idx += W) {
+      int kc = idx % nc, r = idx / nc, kb = r % nb, ka = r / nb;
+      int ax, ay, az;
+      cart_decode(la, ka, ax, ay, az);
+      const double y = Y[idx];
+      const int rp = cart_offset(la + 1) - cart_offset(alo);
+      gp[0] += y * I[((rp + cart_index(la + 1, ax + 1, ay)) * nbb + kb) * nc + kc];
+      gp[1] += y * I[((rp + cart_index(la + 1, ax, ay + 1)) * nbb + kb) * nc + kc];
+      gp[2] += y * I[((rp + cart_index(la + 1, ax, ay)) * nbb + kb) * nc + kc];
+      if (la > 0) {
+        const int rm = cart_offset(la - 1) - cart_offset(alo);
+        if (ax > 0) gm[0] += ax * y * I[((rm + cart_index(la - 1, ax - 1, ay)) * nbb + kb) * nc + kc];
+        if (ay > 0) gm[1] += ay * y * I[((rm + cart_index(la - 1, ax, ay - 1)) * nbb + kb) * nc + kc];
+        if (az > 0) gm[2] += az * y * I[((rm + cart_index(la - 1, ax, ay)) * nbb + kb) * nc + kc];
+      }
+    }
+  };
+  // (la, lb - 1) from the level holding b = lb - 1 (rows a in [lo, ...], nbm columns)
+  auto bminus_terms = [&](const double* I, int lo, int nbm) {
+    const int r0 = cart_offset(la) - cart_offset(lo);
+    for (int idx = lane; idx < na * nb * nc; idx += W) {
+      int kc = idx % nc, r = idx / nc, kb = r % nb, ka = r / nb;
+      int bx, by, bz;
+      cart_decode(lb, kb, bx, by, bz);
+      const double y = Y[idx];
+      const double* row = I + (size_t)(r0 + ka) * nbm * nc;
+      if (bx > 0) gm[3] += bx * y * row[cart_index(lb - 1, bx - 1, by) * nc + kc];
+      if (by > 0) gm[4] += by * y * row[cart_index(lb - 1, bx, by - 1) * nc + kc];
+      if (bz > 0) gm[5] += bz * y * row[cart_index(lb - 1, bx, by) * nc + kc];
+    }
+  };
+  // level 0 is the transfer level itself
+  if (lb == 0) a_terms(lvl, 1);
+  if (lb == 1) bminus_terms(lvl, alo, 1);
+  const double* prev = lvl;
+  int prev_lo = alo, prev_nb = 1;
+  for (int b = 1; b <= lb + 1; ++b) {
+    double* cur = bufs[(b - 1) & 1];
+    const int lo = b == lb + 1 ? la : alo, hi = b == lb + 1 ? la : la + 1 + lb - b;
+    const int ncb = ncart(b);
+    const int n = (cart_offset(hi + 1) - cart_offset(lo)) * ncb * nc;
+    for (int idx = lane; idx < n; idx += W) {
+      const int kc = idx % nc, rest = idx / nc;
+      const int kb = rest % ncb, r = rest / ncb;
+      int a = lo;
+      while (cart_offset(a + 1) - cart_offset(lo) <= r) ++a;
+      const int ka = r - (cart_offset(a) - cart_offset(lo));
+      int bx, by, bz, ax, ay, az;
+      cart_decode(b, kb, bx, by, bz);
+      cart_decode(a, ka, ax, ay, az);
+      const int i = bx > 0 ? 0 : (by > 0 ? 1 : 2);
+      int bl[3] = {bx, by, bz};
+      bl[i] -= 1;
+      const int kbl = cart_index(b - 1, bl[0], bl[1]);
+      int ap[3] = {ax, ay, az};
+      ap[i] += 1;
+      const int rp = cart_offset(a + 1) - cart_offset(prev_lo) + cart_index(a + 1, ap[0], ap[1]);
+      const int r0 = cart_offset(a) - cart_offset(prev_lo) + ka;
+      cur[idx] = prev[(rp * prev_nb + kbl) * nc + kc] + AB[i] * prev[(r0 * prev_nb + kbl) * nc + kc];
+    }
+    __syncwarp(lane_group_mask<W>());
+    if (b == lb - 1) {
+      bminus_terms(cur, lo, ncb);
+    } else if (b == lb) {
+      a_terms(cur, ncb);
+    } else if (b == lb + 1) {   // (la, lb + 1): the level holds a = la only
+      for (int idx = lane; idx < na * nb * nc; idx += W) {
+        int kc = idx % nc, r = idx / nc, kb = r % nb, ka = r / nb;
+        int bx, by, bz;
+        cart_decode(lb, kb, bx, by, bz);
+        const double y = Y[idx];
+        const double* row = cur + (size_t)ka * ncb * nc;
+        gp[3] += y * row[cart_index(lb + 1, bx + 1, by) * nc + kc];
+        gp[4] += y * row[cart_index(lb + 1, bx, by + 1) * nc + kc];
+        gp[5] += y * row[cart_index(lb + 1, bx, by) * nc + kc];
+      }
+    }
+    __syncwarp(lane_group_mask<W>());
+    prev = cur;
+    prev_lo = lo;
+    prev_nb = ncb;
+  }
+  for (int x = 0; x < 3; ++x) {
+    g[x] = sA * gp[x] - gm[x];
+    g[3 + x] = sB * gp[3 + x] - gm[3 + x];
+  }
+}
+
 // ------------------------------------------------------------ 3-centre
 
 // One task of the fused 3-centre derivative contraction: the shell triple
@@ -267,7 +379,7 @@ __device__ inline void grad_eri3_task(const DevShells& prim, const DevShells& au
   double g[6];
   if (single || one_mir) {
     const double* lvl = single ? etr + sh.level_off(lc) : smem + pl.acc0;
-    warp_deriv_contract<W>(pl, smem, lvl, lvl, lvl, 2.0 * pr[0].alpha, 2.0 * pr[0].beta, la, lb, lc, AB, lane, g);
+    warp_deriv_contract_single<W>(pl, smem, lvl, 2.0 * pr[0].alpha, 2.0 * pr[0].beta, la, lb, lc, AB, lane, g);
   } else {
     warp_deriv_contract<W>(pl, smem, smem + pl.acc0, smem + pl.accA, smem + pl.accB, 1.0, 1.0, la, lb, lc, AB,
                            lane, g);
