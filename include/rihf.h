@@ -251,18 +251,19 @@ int rihf_eigh(int n, const double* A, double* W, double* V, int device);
    that owns a fixed memory pool and forbids cudaMalloc inside its time loop).
    A, W, V are DEVICE pointers: A n x n symmetric (row-major, read only),
    W (n) ascending eigenvalues, V (n x n, column k = eigenvector k); stream is a
-   cudaStream_t (NULL = the default stream); the call is asynchronous on it.
+   cudaStream_t (NULL = the default stream); its work is queued on it.
    n must not exceed 256: the workspace is one fixed device array in the
    library (about 7.9 MB, held on every GPU that loads the library until exit);
    larger n return RIHF_ERR_INVALID_ARG.  No memory is allocated or freed.
    The first call on each device resolves the array's device address (make it
    before any stream capture).  All calls share the array: calls whose work
    overlaps on the GPU (different streams or host threads) race and must be
-   serialised by the caller.  The return code covers argument checks and
-   launch errors only: the call does not wait for the GPU, so a Jacobi pass
-   that stops at its sweep limit before converging is not reported (the FP64
-   refinement still runs on its vectors); a caller that needs a guarantee
-   checks the residual A V - V diag(W) itself.  Errors: INVALID_ARG, CUDA. */
+   serialised by the caller.  Outside stream capture the call waits for its
+   result and checks it: RIHF_ERR_NOT_CONVERGED when max|A V - V diag(W)|
+   exceeds 1e-9 n max|W| or max|V^T V - I| exceeds 1e-9 n (a Jacobi pass that
+   stopped at its sweep limit, a refinement that did not converge).  Inside a
+   stream capture it stays asynchronous and reports argument and launch errors
+   only.  Errors: INVALID_ARG, NOT_CONVERGED, CUDA. */
 int rihf_eigh_noalloc(int n, const double* A, double* W, double* V, void* stream);
 
 /* C = A B^T on the tensor cores with FP64-class accuracy (the engine of the
