@@ -384,7 +384,12 @@ def run_batch(args):
     prec = R.PRECISION_MIXED if args.precision == "mixed" else R.PRECISION_FP64
     sizes = W.batch_sizes(args.batch, seed=0, lo=3, hi=args.batch_max)
     mols = [W.water_n(int(n), seed=k) for k, n in enumerate(sizes)]
-    ctxs = [R.Context(m, precision=prec, **CONV) for m in mols]
+    # a fixed auxiliary chunk per context: the automatic sizing takes the
+    # free memory of its moment, so the first contexts of a large batch would
+    # leave none for the last
+    t_setup = time.perf_counter()
+    ctxs = [R.Context(m, precision=prec, aux_chunk=args.batch_chunk, **CONV) for m in mols]
+    setup_s = time.perf_counter() - t_setup
     ms = [W.masses_au(m.Z)[:, None] for m in mols]
     xs = [m.xyz.copy() for m in mols]
     vs = [W.maxwell_boltzmann(m.Z, 300.0, k) for k, m in enumerate(mols)]
@@ -415,7 +420,8 @@ def run_batch(args):
             "dtype": "f64" if args.precision == "fp64" else "bf16 digit planes (RI-K, fit, gradient products) + f64", "data": "synthetic",
             "config": {"workload": "%d water clusters, 3..%d molecules (sizes %s), config-1 basis, dt 0.5 fs"
                                    % (len(ctxs), args.batch_max, np.bincount(sizes).tolist()),
-                       "precision": args.precision, "scf_iters_avg": float(np.mean(iters))}}
+                       "precision": args.precision, "scf_iters_avg": float(np.mean(iters)),
+                       "aux_chunk": args.batch_chunk, "setup_s": setup_s}}
     print(json.dumps(line))
     for c in ctxs:
         c.close()
@@ -442,10 +448,15 @@ def main():
     ap.add_argument("--batch", type=int, default=0,
                     help="batched mode: this many independent clusters of 3..--batch-max waters per AIMD step")
     ap.add_argument("--batch-max", type=int, default=8)
+    ap.add_argument("--batch-chunk", type=int, default=64,
+                    help="auxiliary functions per expansion chunk of each batch context")
     ap.add_argument("--learned-aimd", action="store_true",
                     help="the learned-guess AIMD experiment ((H2O)16) instead of the benchmark")
     ap.add_argument("--la-steps", type=int, default=2000)
     ap.add_argument("--la-train", type=int, default=200)
+    ap.add_argument("--guess", type=int, default=2, choices=[2, 3],
+                    help="SCF guess of the timed path: 2 previous orbitals, 3 extrapolated Loewdin density "
+                         "(the FP64 comparison path always uses 2)")
     ap.add_argument("--profile-step", action="store_true",
                     help="untimed: setup, one SCF and one gradient of the workload (for ncu captures)")
     ap.add_argument("--profile-workload", default="water8", choices=["water8", "water16", "water4-large"],
@@ -479,7 +490,7 @@ def main():
     torch.cuda.set_device(local)
     R.load()
     main_prec = args.precision
-    res = measure_path(R, W, torch, main_prec, args, rank, local, pg, trace=True)
+    res = measure_path(R, W, torch, main_prec, args, rank, local, pg, trace=True, guess=args.guess)
     cmp = None
     if main_prec == "mixed" and not args.no_compare:
         # the FP64 path on the same geometries (warm-up and timed steps of the
@@ -502,7 +513,9 @@ def main():
         cpu = {"value": 1.0 / statistics.mean(r["times"]), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": r["sample"]}
     grad_bytes = res["natoms"] * 3 * 8
-    config = {"workload": WORKLOAD, "precision": main_prec, "parallelism": "replicas" if world > 1 else "1 GPU",
+    workload = WORKLOAD if args.guess == 2 else WORKLOAD.replace(
+        "previous-orbital guess", "extrapolated Loewdin-density guess (the FP64 path: previous orbitals)")
+    config = {"workload": workload, "precision": main_prec, "parallelism": "replicas" if world > 1 else "1 GPU",
               "l2": "inputs larger than L2 (B = 250 MB)", "scf_conv": CONV,
               "scf_iters_avg": float(np.mean(res["iters"])), "energy_drift_eh": res["drift"],
               "kernel_times": "CUDA events per launch on the library stream during the timed steps; SCF "
@@ -632,7 +645,7 @@ def measure_config2(R, W, torch, args, local):
                         sorted(m["stats"], key=lambda s: -s["ms"])[:16]]}
 
 
-def measure_path(R, W, torch, precision, args, rank, local, pg, trace, replay=None):
+def measure_path(R, W, torch, precision, args, rank, local, pg, trace, replay=None, guess=2):
     """Warm-up and timed AIMD steps of one context (device time by CUDA events on
     the library stream), then the same steps again end to end through the public
     API from the same start state.  With `replay`, the steps visit those
@@ -644,7 +657,7 @@ def measure_path(R, W, torch, precision, args, rank, local, pg, trace, replay=No
     traj = Trajectory(ctx, mol, rank, R, replay=replay)
     stream = torch.cuda.ExternalStream(ctx.stream(), device=local)
     for _ in range(max(args.warmup, 0)):
-        traj.step()
+        traj.step(guess)
     start = traj.state()
     # ---- timed region 1: device time (CUDA events on the library stream)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -659,7 +672,7 @@ def measure_path(R, W, torch, precision, args, rank, local, pg, trace, replay=No
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            traj.step()
+            traj.step(guess)
             energies.append(traj.E)
             grads.append(traj.g.copy())
         e1.record(stream)
@@ -687,7 +700,7 @@ def measure_path(R, W, torch, precision, args, rank, local, pg, trace, replay=No
         x = traj.next_geometry()
         xyz_pinned[:] = x.reshape(-1)
         ctx.update_geometry(xyz_pinned.reshape(-1, 3))
-        out = ctx.scf(guess=2, outputs=False)
+        out = ctx.scf(guess=guess, outputs=False)
         traj.finish(x, out["energy"], ctx.gradient())
         e2e_E.append(out["energy"])
     torch.cuda.synchronize()
