@@ -555,24 +555,17 @@ def main():
     return 0
 
 
-def roofline_of(stats, pk, pk_src):
-    """The roofline object of the dominant traced kernel (or of the longest one
-    with a work count when the dominant one has none)."""
-    kernels = [s for s in stats if not s["name"].startswith("SCF iteration graph")]
-    if not kernels:
-        return None
-    dom = max(kernels, key=lambda s: s["ms"])
-    timed = [s for s in kernels if s["work"] > 0]
-    roof_k = dom if dom["work"] > 0 else max(timed, key=lambda s: s["ms"])
-    per_launch_s = roof_k["ms"] / roof_k["launches"] / 1e3
-    work = roof_k["work"] / roof_k["launches"]
-    if roof_k["kind"] == "hbm_bytes":
+def roofline_entry(k, pk, pk_src):
+    """achieved / peak of one traced kernel with a work count (per launch)."""
+    per_launch_s = k["ms"] / k["launches"] / 1e3
+    work = k["work"] / k["launches"]
+    if k["kind"] == "hbm_bytes":
         achieved, peak, unit, bound = work / per_launch_s / 1e9, pk["hbm_gbs"], "GB/s", "hbm"
         src = "hbm_gbs of %s" % pk_src
-    elif roof_k["kind"] == "fp64_flops":
+    elif k["kind"] == "fp64_flops":
         achieved, peak, unit, bound = work / per_launch_s / 1e12, FP64_PEAK_GFLOPS / 1e3, "TFLOP/s", "alu"
         src = "FP64 DFMA peak derived from unit counts (152 SMs x 2 DFMA/clk x 2.07 GHz)"
-    elif roof_k["kind"] == "bf16_tensor_flops":
+    elif k["kind"] == "bf16_tensor_flops":
         # BF16 MMA flops issued (digit-pair products included); the kernel runs
         # inside a long step, so the sustained cuBLAS figure is the peak
         key = "bf16_tflops_sustained" if "bf16_tflops_sustained" in pk else "bf16_tflops"
@@ -581,14 +574,33 @@ def roofline_of(stats, pk, pk_src):
     else:
         achieved, peak, unit, bound = work / per_launch_s / 1e12, pk["bf16_tflops"] / 2, "TFLOP/s", "alu"
         src = "FP32 SIMT: half the bf16 tensor figure of %s (fallback)" % pk_src
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "kernel": k["name"], "peak_source": src}
+
+
+def roofline_of(stats, pk, pk_src):
+    """The roofline object of the dominant traced kernel (or of the longest one
+    with a work count when the dominant one has none), and the same figures for
+    every traced kernel with a work count (the contraction kernels' tensor-pipe
+    and the integral kernels' FP64 fractions), longest first."""
+    kernels = [s for s in stats if not s["name"].startswith("SCF iteration graph")]
+    if not kernels:
+        return None
+    dom = max(kernels, key=lambda s: s["ms"])
+    timed = [s for s in kernels if s["work"] > 0]
+    roof_k = dom if dom["work"] > 0 else max(timed, key=lambda s: s["ms"])
+    out = roofline_entry(roof_k, pk, pk_src)
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
             traffic = json.load(f).get(roof_k["name"])
-    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-            "traffic": traffic, "kernel": roof_k["name"], "peak_source": src,
-            "dominant_kernel": dom["name"], "dominant_share": dom["ms"] / sum(s["ms"] for s in stats)}
+    out["traffic"] = traffic
+    out["dominant_kernel"] = dom["name"]
+    out["dominant_share"] = dom["ms"] / sum(s["ms"] for s in stats)
+    out["all_kernels"] = [dict(roofline_entry(k, pk, pk_src), ms=k["ms"])
+                          for k in sorted(timed, key=lambda s: -s["ms"])]
+    return out
 
 
 def measure_config2(R, W, torch, args, local):
