@@ -2213,9 +2213,10 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
   // Precision ladder (mixed mode): RI-K on the tensor cores with a digit count
   // that follows the SCF error (5 digits, about 39 bits, while max|e| > 1e-2;
   // 6 while > 1e-5; then 7, about 55 bits), or the fixed count of
-  // opt.mixed_digits.  When the convergence test passes on a ladder build, the
-  // next build is a confirmation build and convergence is declared only on
-  // one: 7 digits (products with FP64-class accuracy, 55 bits per K block),
+  // opt.mixed_digits.  When the convergence test passes on a ladder build of
+  // fewer digits, the next build is a confirmation build and convergence is
+  // declared only on one (or on a 7-digit ladder build, which is the same
+  // arithmetic): 7 digits (products with FP64-class accuracy, 55 bits per K block),
   // or FP64 with opt.confirm_fp64; either way the converged energy and density
   // do not carry the ladder's shorter digit counts.  Three ladder builds in a
   // row without a new lowest max|e| also move on to confirmation builds.
@@ -2283,7 +2284,14 @@ int rihf_scf(rihf_ctx* c, int guess, const double* C_guess, double* energy, doub
       }
       if (crit || stall >= 3) fp64_next = true;
     }
-    if (crit && full) {
+    // a ladder build that already used 7 digits is a confirmation build (the
+    // same arithmetic): convergence on it is declared at once
+    const bool seven = mixed && !full && variant == kOzMaxDigits && !c->opt.confirm_fp64;
+    if (crit && (full || seven)) {
+      if (seven) {
+        --c->tc_builds;
+        ++c->confirm_builds;
+      }
       conv = true;
       break;
     }
