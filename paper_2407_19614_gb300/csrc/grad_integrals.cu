@@ -734,21 +734,11 @@ void launch_grad_eri3_batch(const IntegralCtx& ic, const std::vector<BatchGeom>&
   if (n == 0) return;
   if (n > t.cap) throw RihfError(RIHF_ERR_INVALID_ARG, "launch_grad_eri3_batch: batch tables too small");
   for (int g = 0; g < ngroups; ++g) {
-    std::vector<GeomTasks> geoms(n);
-    std::vector<long long> off(n + 1, 0);
     int slice_bytes = 0;
-    for (int i = 0; i < n; ++i) {
-      geoms[i] = batch[i].g;
-      geoms[i].tasks = batch[i].groups[g].tasks;
-      off[i + 1] = off[i] + batch[i].groups[g].ntask;
-      if (batch[i].groups[g].ntask > 0) slice_bytes = std::max(slice_bytes, batch[i].groups[g].smem_grad);
-    }
-    if (off[n] == 0) continue;
+    long long ntask = 0;
+    if (!batch_tables(ic, batch, g, t, true, slice_bytes, ntask)) continue;
     GeomTasks* dg = t.geoms + (size_t)g * t.cap;
     long long* doff = t.off + (size_t)g * (t.cap + 1);
-    RIHF_CUDA(cudaMemcpyAsync(dg, geoms.data(), sizeof(GeomTasks) * n, cudaMemcpyHostToDevice, ic.stream));
-    RIHF_CUDA(cudaMemcpyAsync(doff, off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, ic.stream));
-    RIHF_CUDA(cudaStreamSynchronize(ic.stream));   // the host arrays are temporaries
     const int W = task_group_width(g), slice = slice_bytes / (int)sizeof(double);
     const int smem = (32 / W) * slice * (int)sizeof(double);
     RIHF_CUDA(cudaMemsetAsync(ic.counter, 0, sizeof(int), ic.stream));

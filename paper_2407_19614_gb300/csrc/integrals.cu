@@ -724,10 +724,8 @@ void launch_eri3(const IntegralCtx& ic, const DevShells& prim, const DevShells& 
   }
 }
 
-// Shared host side of the batched launches: per class group, the descriptors
-// (with that group's task pointers) and the offsets table, uploaded into t.
-static bool batch_tables(const IntegralCtx& ic, const std::vector<BatchGeom>& batch, int g, BatchTables& t,
-                         bool grad, int& slice_bytes, long long& ntask) {
+bool batch_tables(const IntegralCtx& ic, const std::vector<BatchGeom>& batch, int g, BatchTables& t, bool grad,
+                  int& slice_bytes, long long& ntask) {
   const int n = (int)batch.size();
   std::vector<GeomTasks> geoms(n);
   std::vector<long long> off(n + 1, 0);

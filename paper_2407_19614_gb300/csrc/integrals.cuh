@@ -136,6 +136,12 @@ struct BatchTables {
 // geometries' slices of the group.  Uploads the tables (host -> device on
 // ic.stream, then waits for them: the host arrays are temporaries).
 void launch_eri3_batch(const IntegralCtx& ic, const std::vector<BatchGeom>& batch, int ngroups, BatchTables& t);
+// Host side shared by the two: for class group g, the descriptors (with that
+// group's task pointers) and the offsets table uploaded into t; the largest
+// shared-memory slice of the group (grad: the derivative kernel's) and the
+// task count.  False when the group has no task.
+bool batch_tables(const IntegralCtx& ic, const std::vector<BatchGeom>& batch, int g, BatchTables& t, bool grad,
+                  int& slice_bytes, long long& ntask);
 void launch_grad_eri3_batch(const IntegralCtx& ic, const std::vector<BatchGeom>& batch, int ngroups,
                             BatchTables& t);
 
