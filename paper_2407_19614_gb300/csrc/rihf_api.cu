@@ -1306,8 +1306,11 @@ static void diagonalise(rihf_ctx* c, const double* Fin, bool warm) {
   } else {
     graph_or_eager(c, c->diag_graphs[Fin == c->F ? 0 : 1], "eigh F' (refine only)", [&]() {
       form_fp();
-      // two quadratically convergent steps from vectors accurate to ~max|e| < 1e-2
-      eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 2, c->Cprev, true, 20);
+      // two quadratically convergent steps from vectors accurate to ~max|e| < 1e-2,
+      // then three Newton-Schulz re-orthonormalisations: refined vectors whose
+      // V^T V is off by ~1e-2 reach ~1e-4 after two and ~1e-8 after three,
+      // which the guard below needs (each miss costs a Jacobi redo)
+      eigh(la, c->Fp, n, c->eps, c->Cp, c->eigws, 2, c->Cprev, true, 20, 3);
       // guard: orthonormality and the off-diagonal of Cp^T F' Cp
       GemmArgs go;   // T2 = Cp^T Cp
       go.M = n; go.N = n; go.K = n; go.A = c->Cp; go.lda = n; go.transA = true; go.B = c->Cp; go.ldb = n;
