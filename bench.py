@@ -201,28 +201,61 @@ class Trajectory:
 
 def run_learned_aimd(args):
     """The learned-guess AIMD experiment: (H2O)16 (small basis) from the
-    generated geometry and seeded 300 K velocities, velocity Verlet at 0.5 fs
-    for --la-steps steps, one arm per guess: the extrapolated Loewdin density
-    (3) and the learned guess (4, the network trained online on the first
-    --la-train steps, then frozen), mixed precision.  Each arm integrates its
-    own trajectory.  Overlap eigenvalues below LA_LINDEP are dropped: where
+    generated geometry and seeded 300 K velocities (--la-workload water16,
+    mixed precision), or the water monomer relaxed in this basis at 300 K
+    (monomer-thermal, FP64); velocity Verlet at 0.5 fs for --la-steps steps,
+    one arm per guess: the extrapolated Loewdin density (3) and the learned
+    guess (4, the network trained online on the first --la-train steps, then
+    frozen).  Each arm integrates its own trajectory.  Overlap eigenvalues below LA_LINDEP are dropped: where
     molecules of this hot trajectory come close, S approaches singularity and
     the commutator's rounding floor (|F| eps / lambda_min(S)) would otherwise
     sit near the convergence threshold.  Prints one JSON line: per arm the SCF iterations per
     step (all steps, and after training), the total-energy drift, how often
     the network was used, and the wall time."""
+    import dataclasses
     import torch
     from paper_2407_19614_gb300 import rihf as R
     from paper_2407_19614_gb300 import workloads as W
     torch.cuda.set_device(0)
     R.load()
-    mol = W.water16(0)
+    if args.la_workload == "water16":
+        mol = W.water16(0)
+        prec, conv, guess0 = R.PRECISION_MIXED, dict(CONV, max_iter=LA_MAXIT), 5
+        workload = ("(H2O)16, N=384, Naux=1696, velocity Verlet dt 0.5 fs from seeded 300 K Maxwell-Boltzmann "
+                    "velocities, SAD start, mixed precision")
+    else:
+        # a thermal trajectory: the monomer relaxed in this basis by steepest
+        # descent (FP64 gradients), then 300 K velocity Verlet
+        mono = W.water_monomer(0)
+        rc = R.Context(mono, conv_e=1e-11, conv_diis=1e-10, max_iter=100)
+        x = mono.xyz.copy()
+        E = rc.scf(guess=0, outputs=False)["energy"]
+        g = rc.gradient()
+        step = 0.3
+        for _ in range(400):
+            if np.abs(g).max() < 2e-5:
+                break
+            xn = x - step * g
+            rc.update_geometry(xn)
+            En = rc.scf(guess=2, outputs=False)["energy"]
+            if En < E:
+                x, E, g = xn, En, rc.gradient()
+                step *= 1.2
+            else:
+                rc.update_geometry(x)
+                rc.scf(guess=2, outputs=False)
+                step *= 0.5
+        rc.close()
+        mol = dataclasses.replace(mono, xyz=x)
+        prec, conv, guess0 = R.PRECISION_FP64, dict(conv_e=1e-10, conv_diis=1e-9, max_iter=80), 0
+        workload = ("H2O monomer relaxed in this basis (max force %.1e Eh/bohr), velocity Verlet dt 0.5 fs from "
+                    "seeded 300 K Maxwell-Boltzmann velocities, FP64" % float(np.abs(g).max()))
     arms = {}
     for name, guess in (("extrapolated", 3), ("learned", 4)):
-        ctx = R.Context(mol, precision=R.PRECISION_MIXED, lindep_tau=LA_LINDEP, **dict(CONV, max_iter=LA_MAXIT))
+        ctx = R.Context(mol, precision=prec, lindep_tau=LA_LINDEP, **conv)
         ctx.learn_config(hidden=256, train_steps=args.la_train, adam_iters=4, lr=1e-3, seed=0)
         t0 = time.perf_counter()
-        tr = Trajectory(ctx, mol, 0, R, guess0=5)
+        tr = Trajectory(ctx, mol, 0, R, guess0=guess0)
         etot = [tr.total_energy()]
         its, used, bad, stopped = [], [], 0, None
         for k in range(args.la_steps):
@@ -247,11 +280,9 @@ def run_learned_aimd(args):
                       "network_used_steps": int(sum(used)), "unconverged_steps": bad, "wall_s": wall,
                       "steps_done": len(its), "stopped": stopped}
         print(name, json.dumps(arms[name]), file=sys.stderr, flush=True)
-    print(json.dumps({"experiment": "learned SCF guess along AIMD",
-                      "workload": "(H2O)16, N=384, Naux=1696, velocity Verlet dt 0.5 fs from seeded 300 K "
-                                  "Maxwell-Boltzmann velocities, SAD start, mixed precision",
+    print(json.dumps({"experiment": "learned SCF guess along AIMD", "workload": workload,
                       "steps": args.la_steps, "train_steps": args.la_train, "network": "12-256-1 tanh, BF16 weights",
-                      "conv": dict(CONV, lindep_tau=LA_LINDEP, max_iter=LA_MAXIT), "arms": arms}))
+                      "conv": dict(conv, lindep_tau=LA_LINDEP), "arms": arms}))
     return 0
 
 
@@ -454,6 +485,8 @@ def main():
                     help="the learned-guess AIMD experiment ((H2O)16) instead of the benchmark")
     ap.add_argument("--la-steps", type=int, default=2000)
     ap.add_argument("--la-train", type=int, default=200)
+    ap.add_argument("--la-workload", default="water16", choices=["water16", "monomer-thermal"],
+                    help="water16: the generated (H2O)16 cluster; monomer-thermal: the relaxed monomer at 300 K")
     ap.add_argument("--guess", type=int, default=2, choices=[2, 3],
                     help="SCF guess of the timed path: 2 previous orbitals, 3 extrapolated Loewdin density "
                          "(the FP64 comparison path always uses 2)")

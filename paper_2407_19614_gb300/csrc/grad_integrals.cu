@@ -116,11 +116,13 @@ __device__ inline void warp_back_transform(const Src& src, int la, int lb, int l
 
 // g[0..2] += sum_{ka,kb,kc} Y[ka][kb][kc] * (d/dA_x), g[3..5] += ... (d/dB_x) from
 // the four shifted HRR products of one shell triple.  Returns per-lane partials.
-// The (la+1) and (lb+1) terms come from accA and accB times sA and sB (a single
-// primitive triple passes one accumulator for all three and sA = 2 alpha,
-// sB = 2 beta; contracted triples pass their three weighted sums and 1, 1).
+// The (la+1) and (lb+1) terms come from accA and accB times sA and sB; the
+// contracted triples that use it pass their three weighted sums and 1, 1
+// (single primitive triples take warp_deriv_contract_single).  Kept out of
+// line: it is the kernel's rare path, and its code would otherwise crowd the
+// instruction cache of the common one.
 template <int W = 32>
-__device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, const double* acc0, const double* accA,
+__device__ __noinline__ void warp_deriv_contract(const DerivPlan& pl, double* smem, const double* acc0, const double* accA,
                                            const double* accB, double sA, double sB, int la, int lb, int lc,
                                            const double* AB, int lane, double g[6]) {
   const int na = ncart(la), nb = ncart(lb), nc = ncart(lc);
@@ -327,6 +329,10 @@ __device__ inline void grad_eri3_task(const DevShells& prim, const DevShells& au
   const bool one = nab == 1 && aux.nprim[sc] == 1;
   const bool one_mir = one && mir && pr[0].p > aux.exps[aux.pstart[sc]];
   const bool single = one && !one_mir && lc > 0;
+  // one primitive triple with an s auxiliary function: its values go to acc0
+  // alone (there is no transfer level to read in place), contracted like the
+  // other single triples with 2 alpha and 2 beta
+  const bool one_s = one && !one_mir && lc == 0;
   if (!single && !one_mir)
     for (int i = lane; i < 3 * accsz; i += W) smem[pl.acc0 + i] = 0.0;
   const double* A = prim.xyz + 3 * sa;
@@ -359,8 +365,10 @@ __device__ inline void grad_eri3_task(const DevShells& prim, const DevShells& au
       warp_etr<W>(vrr, pl.L, etr, sh, t, Fm, lane);
       if (!single) {
         warp_acc_level<W>(vrr, pl.L, etr, sh, 1.0, smem + pl.acc0, lane);
-        warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.alpha, smem + pl.accA, lane);
-        warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.beta, smem + pl.accB, lane);
+        if (!one_s) {
+          warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.alpha, smem + pl.accA, lane);
+          warp_acc_level<W>(vrr, pl.L, etr, sh, 2.0 * q.beta, smem + pl.accB, lane);
+        }
       }
     }
   }
@@ -377,7 +385,7 @@ __device__ inline void grad_eri3_task(const DevShells& prim, const DevShells& au
                       smem + pl.t1, smem + pl.t2, smem + pl.ycart, lane);
   double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
   double g[6];
-  if (single || one_mir) {
+  if (single || one_mir || one_s) {
     const double* lvl = single ? etr + sh.level_off(lc) : smem + pl.acc0;
     warp_deriv_contract_single<W>(pl, smem, lvl, 2.0 * pr[0].alpha, 2.0 * pr[0].beta, la, lb, lc, AB, lane, g);
   } else {
