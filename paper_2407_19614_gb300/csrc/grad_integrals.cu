@@ -118,11 +118,9 @@ __device__ inline void warp_back_transform(const Src& src, int la, int lb, int l
 // the four shifted HRR products of one shell triple.  Returns per-lane partials.
 // The (la+1) and (lb+1) terms come from accA and accB times sA and sB; the
 // contracted triples that use it pass their three weighted sums and 1, 1
-// (single primitive triples take warp_deriv_contract_single).  Kept out of
-// line: it is the kernel's rare path, and its code would otherwise crowd the
-// instruction cache of the common one.
+// (single primitive triples take warp_deriv_contract_single).
 template <int W = 32>
-__device__ __noinline__ void warp_deriv_contract(const DerivPlan& pl, double* smem, const double* acc0, const double* accA,
+__device__ inline void warp_deriv_contract(const DerivPlan& pl, double* smem, const double* acc0, const double* accA,
                                            const double* accB, double sA, double sB, int la, int lb, int lc,
                                            const double* AB, int lane, double g[6]) {
   const int na = ncart(la), nb = ncart(lb), nc = ncart(lc);
