@@ -412,9 +412,10 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
   const int lane = threadIdx.x % W;
   double* smem = smem_all + (threadIdx.x / W) * slice;   // this task group's slice
   for (;;) {
-    long long task = warp_next<W>(counter, lane);
-    if (task >= ntask) break;
-    grad_eri3_task<W>(prim, aux, pairs, ptab, tasks[task], boys, Y, grad, smem, lane);
+    const long long task = warp_claim<W>(counter) + (threadIdx.x & 31) / W;
+    if (task - (threadIdx.x & 31) / W >= ntask) break;   // the same for the whole warp
+    if (task < ntask) grad_eri3_task<W>(prim, aux, pairs, ptab, tasks[task], boys, Y, grad, smem, lane);
+    __syncwarp();
   }
 }
 
@@ -430,16 +431,19 @@ __global__ void __launch_bounds__(32) grad_eri3_batch_kernel(const GeomTasks* __
   double* smem = smem_all + (threadIdx.x / W) * slice;
   const long long ntask = off[ngeom];
   for (;;) {
-    long long task = warp_next<W>(counter, lane);
-    if (task >= ntask) break;
-    int lo = 0, hi = ngeom;   // off[lo] <= task < off[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (off[mid] <= task) lo = mid;
-      else hi = mid;
+    const long long task = warp_claim<W>(counter) + (threadIdx.x & 31) / W;
+    if (task - (threadIdx.x & 31) / W >= ntask) break;   // the same for the whole warp
+    if (task < ntask) {
+      int lo = 0, hi = ngeom;   // off[lo] <= task < off[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= task) lo = mid;
+        else hi = mid;
+      }
+      const GeomTasks& G = geoms[lo];
+      grad_eri3_task<W>(G.prim, G.aux, G.pairs, G.ptab, G.tasks[task - off[lo]], boys, G.Y, G.out, smem, lane);
     }
-    const GeomTasks& G = geoms[lo];
-    grad_eri3_task<W>(G.prim, G.aux, G.pairs, G.ptab, G.tasks[task - off[lo]], boys, G.Y, G.out, smem, lane);
+    __syncwarp();
   }
 }
 

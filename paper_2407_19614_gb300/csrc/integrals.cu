@@ -3,6 +3,8 @@
 // are handed out through a device counter so that heavy and light shell classes
 // balance across the 152 SMs.
 #include <algorithm>
+#include <array>
+#include <map>
 #include <cmath>
 #include <vector>
 
@@ -240,9 +242,10 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
   const int lane = threadIdx.x % W;
   double* smem = smem_all + (threadIdx.x / W) * slice;   // this task group's slice
   for (;;) {
-    long long task = warp_next_task<W>(counter, lane);
-    if (task >= ntask) break;
-    eri3_task<W>(prim, aux, pairs, ptab, tasks[task], boys, T, smem, lane);
+    const long long task = warp_claim<W>(counter) + (threadIdx.x & 31) / W;
+    if (task - (threadIdx.x & 31) / W >= ntask) break;   // the same for the whole warp
+    if (task < ntask) eri3_task<W>(prim, aux, pairs, ptab, tasks[task], boys, T, smem, lane);
+    __syncwarp();
   }
 }
 
@@ -258,16 +261,19 @@ __global__ void __launch_bounds__(32) eri3_batch_kernel(const GeomTasks* __restr
   double* smem = smem_all + (threadIdx.x / W) * slice;
   const long long ntask = off[ngeom];
   for (;;) {
-    long long task = warp_next_task<W>(counter, lane);
-    if (task >= ntask) break;
-    int lo = 0, hi = ngeom;   // off[lo] <= task < off[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (off[mid] <= task) lo = mid;
-      else hi = mid;
+    const long long task = warp_claim<W>(counter) + (threadIdx.x & 31) / W;
+    if (task - (threadIdx.x & 31) / W >= ntask) break;   // the same for the whole warp
+    if (task < ntask) {
+      int lo = 0, hi = ngeom;   // off[lo] <= task < off[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= task) lo = mid;
+        else hi = mid;
+      }
+      const GeomTasks& G = geoms[lo];
+      eri3_task<W>(G.prim, G.aux, G.pairs, G.ptab, G.tasks[task - off[lo]], boys, G.out, smem, lane);
     }
-    const GeomTasks& G = geoms[lo];
-    eri3_task<W>(G.prim, G.aux, G.pairs, G.ptab, G.tasks[task - off[lo]], boys, G.out, smem, lane);
+    __syncwarp();
   }
 }
 
@@ -926,11 +932,18 @@ void task_flops(const std::vector<ShellPair>& pairs, const std::vector<int>& lpr
 
 // Class-grouped task lists: every (pair, auxiliary shell) task goes to the first
 // group whose shared-memory bound covers both its integral and its derivative
-// class, so light classes run with many resident warps per SM.
+// class, so light classes run with many resident warps per SM.  Inside a group
+// the tasks are ordered by shape (mirror flag, la, lb, lc and the three shells'
+// primitive counts), the heaviest shapes first and auxiliary shell by shell
+// within a shape: the lane groups of a warp, which claim neighbouring tasks
+// together, then run the same recursion with the same trip counts in lockstep
+// instead of one after another, warps resident on one SM share their code, and
+// the lightest tasks fill the end of the launch.
 void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim,
-                       const std::vector<int>& laux, const std::vector<double>& pmax, const std::vector<double>& qmin,
-                       std::vector<std::vector<int2>>& tasks, std::vector<int>& smem_eri3,
-                       std::vector<int>& smem_grad) {
+                       const std::vector<int>& nprim, const std::vector<int>& laux,
+                       const std::vector<int>& naux_prim, const std::vector<double>& pmax,
+                       const std::vector<double>& qmin, std::vector<std::vector<int2>>& tasks,
+                       std::vector<int>& smem_eri3, std::vector<int>& smem_grad) {
   // group 0: tiny classes as 8-lane groups (4 tasks per warp); group 1: small
   // classes as 16-lane groups (2 tasks per warp, about 15 warps per SM); then
   // about 17, 7, 3, 1-2 and 1 warps per SM (228 KB shared memory, 1 KB
@@ -950,19 +963,77 @@ void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<in
           while (g + 1 < kTaskGroups && need > limits[g]) ++g;
           grp[mi][la][lb][lc] = g;
         }
+  // pair shapes (la >= lb and the primitive counts in that order; equal l:
+  // the larger count first) and auxiliary shapes (lc, primitive count)
+  std::map<std::array<int, 4>, int> pmap;
+  std::map<std::array<int, 2>, int> amap;
+  std::vector<std::array<int, 4>> pkey;
+  std::vector<std::array<int, 2>> akey;
+  std::vector<int> pshape(pairs.size()), ashape(laux.size());
+  for (size_t p = 0; p < pairs.size(); ++p) {
+    int a = pairs[p].a, b = pairs[p].b;
+    if (lprim[a] < lprim[b] || (lprim[a] == lprim[b] && nprim[a] < nprim[b])) std::swap(a, b);
+    const std::array<int, 4> k{lprim[a], lprim[b], nprim[a], nprim[b]};
+    auto it = pmap.find(k);
+    if (it == pmap.end()) {
+      it = pmap.emplace(k, (int)pkey.size()).first;
+      pkey.push_back(k);
+    }
+    pshape[p] = it->second;
+  }
+  for (size_t c = 0; c < laux.size(); ++c) {
+    const std::array<int, 2> k{laux[c], naux_prim[c]};
+    auto it = amap.find(k);
+    if (it == amap.end()) {
+      it = amap.emplace(k, (int)akey.size()).first;
+      akey.push_back(k);
+    }
+    ashape[c] = it->second;
+  }
+  const int nps = (int)pkey.size(), nas = (int)akey.size();
+  const int nbucket = 2 * nps * nas;   // (mirror, pair shape, auxiliary shape)
+  auto mirror_of = [&](int p, int c) {
+    return mirror_task(pmax[pairs[p].a] + pmax[pairs[p].b], qmin[c], laux[c]) ? 1 : 0;
+  };
+  // pass 1: bucket sizes
+  std::vector<long long> count(nbucket, 0);
+  for (int c = 0; c < (int)laux.size(); ++c)
+    for (int p = 0; p < (int)pairs.size(); ++p) ++count[((size_t)mirror_of(p, c) * nps + pshape[p]) * nas + ashape[c]];
+  // per group, its buckets heaviest first (primitive triples x derivative
+  // working set), and each bucket's start in the group's list
   tasks.assign(kTaskGroups, {});
   smem_eri3.assign(kTaskGroups, 0);
   smem_grad.assign(kTaskGroups, 0);
+  std::vector<std::vector<std::pair<double, int>>> order(kTaskGroups);
+  for (int bkt = 0; bkt < nbucket; ++bkt) {
+    if (count[bkt] == 0) continue;
+    const int mi = bkt / (nps * nas), ps = bkt / nas % nps, as = bkt % nas;
+    const int la = pkey[ps][0], lb = pkey[ps][1], lc = akey[as][0];
+    const int g = grp[mi][la][lb][lc];
+    const double cost = (double)pkey[ps][2] * pkey[ps][3] * akey[as][1] * sg[mi][la][lb][lc];
+    order[g].emplace_back(-cost, bkt);
+    smem_eri3[g] = std::max(smem_eri3[g], se[mi][la][lb][lc]);
+    smem_grad[g] = std::max(smem_grad[g], sg[mi][la][lb][lc]);
+  }
+  std::vector<long long> start(nbucket, 0);
+  std::vector<int> group_of(nbucket, 0);
+  for (int g = 0; g < kTaskGroups; ++g) {
+    std::sort(order[g].begin(), order[g].end());
+    long long n = 0;
+    for (const auto& e : order[g]) {
+      start[e.second] = n;
+      group_of[e.second] = g;
+      n += count[e.second];
+    }
+    if (n > kMaxGroupTasks) throw RihfError(RIHF_ERR_INVALID_ARG, "build_task_groups: too many 3-centre tasks");
+    tasks[g].resize((size_t)n);
+  }
+  // pass 2: fill, auxiliary shell by shell (then pair) within each bucket
   for (int c = 0; c < (int)laux.size(); ++c)
     for (int p = 0; p < (int)pairs.size(); ++p) {
-      int la = lprim[pairs[p].a], lb = lprim[pairs[p].b];
-      if (la < lb) std::swap(la, lb);
-      const int lc = laux[c];
-      const int mi = mirror_task(pmax[pairs[p].a] + pmax[pairs[p].b], qmin[c], lc) ? 1 : 0;
-      const int g = grp[mi][la][lb][lc];
-      tasks[g].push_back(make_int2(p, mi ? ~c : c));
-      smem_eri3[g] = std::max(smem_eri3[g], se[mi][la][lb][lc]);
-      smem_grad[g] = std::max(smem_grad[g], sg[mi][la][lb][lc]);
+      const int mi = mirror_of(p, c);
+      const size_t bkt = ((size_t)mi * nps + pshape[p]) * nas + ashape[c];
+      tasks[group_of[bkt]][(size_t)start[bkt]++] = make_int2(p, mi ? ~c : c);
     }
 }
 

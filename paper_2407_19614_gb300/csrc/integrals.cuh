@@ -79,13 +79,18 @@ struct TaskGroup {
 };
 // Lanes per task of class group g (group 0 holds the tiny classes).
 inline int task_group_width(int g) { return g == 0 ? 8 : g == 1 ? 16 : 32; }
-// pmax: largest primitive exponent per primary shell; qmin: smallest per
-// auxiliary shell (for mirror_task).  A marked task stores ~c as its auxiliary
-// index.
+// Largest task count of one class group: the kernels claim tasks through an
+// int counter, which runs past the count by 32 / W per resident warp.
+constexpr long long kMaxGroupTasks = (1LL << 31) - (1LL << 24);
+// nprim / naux_prim: primitives per primary / auxiliary shell; pmax: largest
+// primitive exponent per primary shell; qmin: smallest per auxiliary shell (for
+// mirror_task).  A marked task stores ~c as its auxiliary index.  Each group's
+// tasks come ordered by shape, heaviest first.
 void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<int>& lprim,
-                       const std::vector<int>& laux, const std::vector<double>& pmax, const std::vector<double>& qmin,
-                       std::vector<std::vector<int2>>& tasks, std::vector<int>& smem_eri3,
-                       std::vector<int>& smem_grad);
+                       const std::vector<int>& nprim, const std::vector<int>& laux,
+                       const std::vector<int>& naux_prim, const std::vector<double>& pmax,
+                       const std::vector<double>& qmin, std::vector<std::vector<int2>>& tasks,
+                       std::vector<int>& smem_eri3, std::vector<int>& smem_grad);
 
 // Algorithmic FP64 operation counts (an FMA counts two) of the 3-centre
 // integral and derivative kernels over all (pair, auxiliary shell) tasks, from

@@ -242,6 +242,16 @@ __device__ inline unsigned lane_group_mask() {
   return W == 32 ? 0xffffffffu : (((1u << W) - 1u) << ((threadIdx.x & 31) / W * W));
 }
 
+// One atomic per warp claims 32 / W consecutive tasks, task first + k for the
+// k-th lane group, so the groups of a warp start together on neighbouring
+// tasks.  Every lane of the warp calls it, converged.
+template <int W>
+__device__ inline long long warp_claim(int* counter) {
+  int t = 0;
+  if ((threadIdx.x & 31) == 0) t = atomicAdd(counter, 32 / W);
+  return __shfl_sync(0xffffffffu, t, 0);
+}
+
 // ---------------------------------------------------------------- layouts
 
 // VRR table [e][m][k], e = 0..L, m = 0..L-e.

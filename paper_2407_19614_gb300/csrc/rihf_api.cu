@@ -687,7 +687,7 @@ static void refresh_tasks(rihf_ctx* c) {
     qmin[i] = c->ha.exps[c->ha.pstart[i]];
     for (int k = 1; k < c->ha.nprim[i]; ++k) qmin[i] = std::min(qmin[i], c->ha.exps[c->ha.pstart[i] + k]);
   }
-  build_task_groups(c->pairs_h, c->hp.l, c->ha.l, pmax, qmin, tasks, se, sg);
+  build_task_groups(c->pairs_h, c->hp.l, c->hp.nprim, c->ha.l, c->ha.nprim, pmax, qmin, tasks, se, sg);
   task_flops(c->pairs_h, c->hp.l, c->hp.nprim, c->hp.atom, c->ha.l, c->ha.nprim, c->ha.atom, c->nf_h, pmax, qmin,
              &c->flops_eri3, &c->flops_grad3);
   size_t off = 0;
