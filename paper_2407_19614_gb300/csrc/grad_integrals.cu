@@ -33,8 +33,12 @@ __device__ inline double warp_sum(double v) {
 struct DerivPlan {
   int emin, emax, L;
   int fm, vrr, etr, acc0, accA, accB, ycart, t1, t2, hrr, half, total;
-  // mirror: the transfer region also holds the mirrored recursion's levels
-  __device__ __host__ DerivPlan(int la, int lb, int lc, bool mirror = false) {
+  // mirror: the transfer region also holds the mirrored recursion's levels.
+  // one (3-centre tasks of one primitive triple): acc0 alone -- such tasks
+  // never touch accA and accB, which alias acc0 here -- and the HRR scratch
+  // (with the Y back-transform's t1, t2) over the VRR table and the F_m block,
+  // both dead once the primitive loop ends
+  __device__ __host__ DerivPlan(int la, int lb, int lc, bool mirror = false, bool one = false) {
     emin = la > 0 ? la - 1 : 0;
     emax = la + lb + 1;
     L = emax + lc;
@@ -46,14 +50,6 @@ struct DerivPlan {
       const int m = EtrShape{emax, lc, lc}.total();
       if (m > etr_n) etr_n = m;
     }
-    fm = 0;
-    vrr = kFmRegion;
-    etr = vrr + vrr_size(L);
-    acc0 = etr + etr_n;
-    accA = acc0 + accsz;
-    accB = accA + accsz;
-    ycart = accB + accsz;
-    hrr = ycart + nabc;
     half = nabc;   // the Y back-transform scratch (t1, t2) reuses the HRR region
     int cand[4] = {hrr_scratch(la + 1, lb, lc, emax), la > 0 ? hrr_scratch(la - 1, lb, lc, emax) : 0,
                    hrr_scratch(la, lb + 1, lc, emax), lb > 0 ? hrr_scratch(la, lb - 1, lc, emax) : 0};
@@ -66,9 +62,26 @@ struct DerivPlan {
       const int sz = (cart_offset(hi + 1) - cart_offset(lo)) * ncart(b) * ncart(lc);
       if (sz > half) half = sz;
     }
+    fm = 0;
+    vrr = kFmRegion;
+    if (one) {
+      hrr = 0;
+      const int lo = kFmRegion + vrr_size(L), hi = 2 * half + 8;   // 8: the slack that followed the HRR region
+      etr = lo > hi ? lo : hi;
+      acc0 = accA = accB = etr + etr_n;
+      ycart = acc0 + accsz;
+      total = ycart + nabc;
+    } else {
+      etr = vrr + vrr_size(L);
+      acc0 = etr + etr_n;
+      accA = acc0 + accsz;
+      accB = accA + accsz;
+      ycart = accB + accsz;
+      hrr = ycart + nabc;
+      total = hrr + 2 * half;
+    }
     t1 = hrr;
     t2 = hrr + half;
-    total = hrr + 2 * half;
   }
 };
 
@@ -313,18 +326,18 @@ __device__ inline void grad_eri3_task(const DevShells& prim, const DevShells& au
   int ata = prim.atom[sa], atb = prim.atom[sb], atc = aux.atom[sc];
   if (ata == atb && atb == atc) return;   // one-centre: derivative sums to zero
   int la = prim.l[sa], lb = prim.l[sb], lc = aux.l[sc];
-  DerivPlan pl(la, lb, lc, mir);
+  const int nab = prim.nprim[sa] * prim.nprim[sb];
+  // one primitive triple: the derivative weights 2 alpha and 2 beta scale the
+  // contractions instead of weighted sums; a forward triple with a ket above
+  // s leaves its final values in place as the last transfer level, a
+  // mirrored one stores them once into acc0 (the compact plan: no accA, accB)
+  const bool one = nab == 1 && aux.nprim[sc] == 1;
+  DerivPlan pl(la, lb, lc, mir, one);
   double* Fm = smem + pl.fm;
   double* vrr = smem + pl.vrr;
   double* etr = smem + pl.etr;
   int accsz = acc_size(pl.emin, pl.emax, lc);
   const PairPrim* pr = ptab.pp + ptab.off[ip];
-  const int nab = prim.nprim[sa] * prim.nprim[sb];
-  // one primitive triple: the derivative weights 2 alpha and 2 beta scale the
-  // contractions instead of weighted sums; a forward triple with a ket above
-  // s leaves its final values in place as the last transfer level, a
-  // mirrored one stores them once into acc0
-  const bool one = nab == 1 && aux.nprim[sc] == 1;
   const bool one_mir = one && mir && pr[0].p > aux.exps[aux.pstart[sc]];
   const bool single = one && !one_mir && lc > 0;
   // one primitive triple with an s auxiliary function: its values go to acc0
@@ -332,7 +345,7 @@ __device__ inline void grad_eri3_task(const DevShells& prim, const DevShells& au
   // other single triples with 2 alpha and 2 beta
   const bool one_s = one && !one_mir && lc == 0;
   if (!single && !one_mir)
-    for (int i = lane; i < 3 * accsz; i += W) smem[pl.acc0 + i] = 0.0;
+    for (int i = lane; i < (one_s ? 1 : 3) * accsz; i += W) smem[pl.acc0 + i] = 0.0;
   const double* A = prim.xyz + 3 * sa;
   const double* B = prim.xyz + 3 * sb;
   const double* C = aux.xyz + 3 * sc;
@@ -713,8 +726,8 @@ static int deriv_smem(int max_la, int max_lb, int max_lc) {
   return (best + 8) * (int)sizeof(double);
 }
 
-int smem_grad_doubles(int la, int lb, int lc, bool mirror) {
-  DerivPlan p(la, lb, lc, mirror);
+int smem_grad_doubles(int la, int lb, int lc, bool mirror, bool one) {
+  DerivPlan p(la, lb, lc, mirror, one);
   return p.total + 8;
 }
 

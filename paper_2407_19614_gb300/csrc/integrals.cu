@@ -114,10 +114,14 @@ __device__ inline const double* warp_transform3(const double* cart, int la, int 
 
 // Shared-memory plan for one (la, lb | lc) class, in doubles.
 // With `mirror` the transfer region also holds the mirrored recursion's levels
-// (tasks whose triples may need it, see mirror_prim3).
+// (tasks whose triples may need it, see mirror_prim3).  With `alias` (the
+// 3-centre task) the HRR and transform scratch lie over the F_m block and the
+// VRR table, both dead once the primitive loop ends; the transfer levels and
+// the accumulator, which the HRR reads, stay apart.
 struct Eri3Plan {
   int fm, vrr, etr, acc, hrr, half, t1, t2, total;
-  __device__ __host__ Eri3Plan(int la, int lb, int lc, int emin, int emax, int nacc, bool mirror = false) {
+  __device__ __host__ Eri3Plan(int la, int lb, int lc, int emin, int emax, int nacc, bool mirror = false,
+                               bool alias = false) {
     int L = emax + lc;
     EtrShape sh{lc, emin, emax};
     int etr_n = lc > 0 ? sh.total() : 0;
@@ -125,24 +129,33 @@ struct Eri3Plan {
       const int m = EtrShape{emax, lc, lc}.total();
       if (m > etr_n) etr_n = m;
     }
-    fm = 0;
-    vrr = fm + kFmRegion;
-    etr = vrr + vrr_size(L);
-    acc = etr + etr_n;
     int accsz = acc_size(emin, emax, lc);
-    hrr = acc + nacc * accsz;
     half = hrr_scratch(la, lb, lc, emax) / 2;
     int big = ncart(la + 1) * ncart(lb + 1) * ncart(lc);
     if (big > half) half = big;
-    t1 = hrr + 2 * half;
-    t2 = t1 + big;
-    total = t2 + big;
-    // transform scratch reuses the VRR/ETR region when it is large enough
+    fm = 0;
+    vrr = fm + kFmRegion;
+    if (alias) {
+      hrr = 0;
+      t1 = hrr + 2 * half;
+      t2 = t1 + big;
+      const int lo = vrr + vrr_size(L), hi = t2 + big + 8;   // 8 doubles of slack after the scratch
+      etr = lo > hi ? lo : hi;
+      acc = etr + etr_n;
+      total = acc + nacc * accsz;
+    } else {
+      etr = vrr + vrr_size(L);
+      acc = etr + etr_n;
+      hrr = acc + nacc * accsz;
+      t1 = hrr + 2 * half;
+      t2 = t1 + big;
+      total = t2 + big;
+    }
   }
 };
 
-int smem_eri3_doubles(int la, int lb, int lc, bool mirror) {
-  Eri3Plan p(la, lb, lc, la, la + lb, 1, mirror);
+int smem_eri3_doubles(int la, int lb, int lc, bool mirror, bool alias) {
+  Eri3Plan p(la, lb, lc, la, la + lb, 1, mirror, alias);
   return p.total;
 }
 
@@ -167,7 +180,7 @@ __device__ inline void eri3_task(const DevShells& prim, const DevShells& aux, co
   if (swp) { int t = sa; sa = sb; sb = t; }
   int la = prim.l[sa], lb = prim.l[sb], lc = aux.l[sc];
   int emin = la, emax = la + lb, L = emax + lc;
-  Eri3Plan pl(la, lb, lc, emin, emax, 1, mir);
+  Eri3Plan pl(la, lb, lc, emin, emax, 1, mir, true);
   double* Fm = smem + pl.fm;
   double* vrr = smem + pl.vrr;
   double* etr = smem + pl.etr;
@@ -951,18 +964,6 @@ void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<in
   // 205 KB, and one bound for all of them would hold every such task to the
   // residency of the largest
   const int limits[kTaskGroups] = {3584, 7168, 12 * 1024, 28 * 1024, 56 * 1024, 112 * 1024, 1 << 30};
-  constexpr int nl = kMaxLPrim + 1, nc = kMaxLAux + 1;
-  int se[2][nl][nl][nc], sg[2][nl][nl][nc], grp[2][nl][nl][nc];   // [mirror][la][lb][lc]
-  for (int mi = 0; mi < 2; ++mi)
-    for (int la = 0; la < nl; ++la)
-      for (int lb = 0; lb < nl; ++lb)
-        for (int lc = 0; lc < nc; ++lc) {
-          se[mi][la][lb][lc] = smem_eri3_doubles(la, lb, lc, mi == 1) * (int)sizeof(double);
-          sg[mi][la][lb][lc] = smem_grad_doubles(la, lb, lc, mi == 1) * (int)sizeof(double);
-          int need = std::max(se[mi][la][lb][lc], sg[mi][la][lb][lc]), g = 0;
-          while (g + 1 < kTaskGroups && need > limits[g]) ++g;
-          grp[mi][la][lb][lc] = g;
-        }
   // pair shapes (la >= lb and the primitive counts in that order; equal l:
   // the larger count first) and auxiliary shapes (lc, primitive count)
   std::map<std::array<int, 4>, int> pmap;
@@ -999,6 +1000,8 @@ void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<in
   std::vector<long long> count(nbucket, 0);
   for (int c = 0; c < (int)laux.size(); ++c)
     for (int p = 0; p < (int)pairs.size(); ++p) ++count[((size_t)mirror_of(p, c) * nps + pshape[p]) * nas + ashape[c]];
+  // per bucket its shared-memory plans (the derivative task's compact plan
+  // when it has one primitive triple) and the first group that holds both;
   // per group, its buckets heaviest first (primitive triples x derivative
   // working set), and each bucket's start in the group's list
   tasks.assign(kTaskGroups, {});
@@ -1009,11 +1012,14 @@ void build_task_groups(const std::vector<ShellPair>& pairs, const std::vector<in
     if (count[bkt] == 0) continue;
     const int mi = bkt / (nps * nas), ps = bkt / nas % nps, as = bkt % nas;
     const int la = pkey[ps][0], lb = pkey[ps][1], lc = akey[as][0];
-    const int g = grp[mi][la][lb][lc];
-    const double cost = (double)pkey[ps][2] * pkey[ps][3] * akey[as][1] * sg[mi][la][lb][lc];
-    order[g].emplace_back(-cost, bkt);
-    smem_eri3[g] = std::max(smem_eri3[g], se[mi][la][lb][lc]);
-    smem_grad[g] = std::max(smem_grad[g], sg[mi][la][lb][lc]);
+    const int np3 = pkey[ps][2] * pkey[ps][3] * akey[as][1];
+    const int se = smem_eri3_doubles(la, lb, lc, mi == 1, true) * (int)sizeof(double);
+    const int sg = smem_grad_doubles(la, lb, lc, mi == 1, np3 == 1) * (int)sizeof(double);
+    int g = 0;
+    while (g + 1 < kTaskGroups && std::max(se, sg) > limits[g]) ++g;
+    order[g].emplace_back(-(double)np3 * sg, bkt);
+    smem_eri3[g] = std::max(smem_eri3[g], se);
+    smem_grad[g] = std::max(smem_grad[g], sg);
   }
   std::vector<long long> start(nbucket, 0);
   std::vector<int> group_of(nbucket, 0);

@@ -54,8 +54,10 @@ void launch_pair_prims(const IntegralCtx& ic, const DevShells& prim, const Shell
 
 // Shared memory (doubles) one warp needs for a (la >= lb | lc) class of the
 // integral and of the derivative kernel.
-int smem_eri3_doubles(int la, int lb, int lc, bool mirror = false);
-int smem_grad_doubles(int la, int lb, int lc, bool mirror = false);
+// alias: the 3-centre integral task's plan (scratch over the dead VRR table);
+// one: the derivative task's plan for one primitive triple
+int smem_eri3_doubles(int la, int lb, int lc, bool mirror = false, bool alias = false);
+int smem_grad_doubles(int la, int lb, int lc, bool mirror = false, bool one = false);
 
 // Whether a (pair, auxiliary shell) task may take the mirrored recursion
 // (mirror_prim3): the forward transfer multiplies by p/q and by beta AB/q once
