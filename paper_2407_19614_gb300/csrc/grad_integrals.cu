@@ -416,7 +416,7 @@ __device__ inline void grad_eri3_task(const DevShells& prim, const DevShells& au
 }
 
 template <int W>
-__global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells aux,
+__global__ void __launch_bounds__(32, kGradBlocksPerSM) grad_eri3_kernel(DevShells prim, DevShells aux,
                                                        const ShellPair* __restrict__ pairs, PairTable ptab,
                                                        const int2* __restrict__ tasks, long long ntask,
                                                        const double* __restrict__ boys, int* counter,
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(32) grad_eri3_kernel(DevShells prim, DevShells
 // The same over a batch of geometries (task t of geometry g with off[g] <= t <
 // off[g + 1]): each geometry's Y in, its per-atom gradient (out) added to.
 template <int W>
-__global__ void __launch_bounds__(32) grad_eri3_batch_kernel(const GeomTasks* __restrict__ geoms,
+__global__ void __launch_bounds__(32, kGradBlocksPerSM) grad_eri3_batch_kernel(const GeomTasks* __restrict__ geoms,
                                                              const long long* __restrict__ off, int ngeom,
                                                              const double* __restrict__ boys, int* counter,
                                                              int slice) {

@@ -247,7 +247,7 @@ __device__ inline void eri3_task(const DevShells& prim, const DevShells& aux, co
 }
 
 template <int W>
-__global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux, const ShellPair* __restrict__ pairs,
+__global__ void __launch_bounds__(32, kEri3BlocksPerSM) eri3_kernel(DevShells prim, DevShells aux, const ShellPair* __restrict__ pairs,
                                                   PairTable ptab, const int2* __restrict__ tasks, long long ntask,
                                                   const double* __restrict__ boys, int* counter,
                                                   double* __restrict__ T, int slice) {
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(32) eri3_kernel(DevShells prim, DevShells aux,
 // off[g] <= t < off[g + 1] (an int64 offsets table of the geometries' task
 // counts in this class group), its own shells, pairs and output.
 template <int W>
-__global__ void __launch_bounds__(32) eri3_batch_kernel(const GeomTasks* __restrict__ geoms,
+__global__ void __launch_bounds__(32, kEri3BlocksPerSM) eri3_batch_kernel(const GeomTasks* __restrict__ geoms,
                                                         const long long* __restrict__ off, int ngeom,
                                                         const double* __restrict__ boys, int* counter, int slice) {
   extern __shared__ double smem_all[];

@@ -73,6 +73,13 @@ unsigned long long eri2_small_classes(int max_la, int* slice_doubles);
 
 // (pair index, auxiliary shell) tasks of one shared-memory class group.
 constexpr int kTaskGroups = 7;
+// Resident one-warp blocks per SM the 3-centre kernels are compiled for.  The
+// integral kernel at 20 (at most 96 registers a thread): its light class
+// groups, whose shared-memory slices allow more, were held to 13 warps per SM
+// by 150 registers alone.  The derivative kernel at 16 (126 registers, no
+// spills): at 20 its spills cost what the extra warps gain.
+constexpr int kEri3BlocksPerSM = 20;
+constexpr int kGradBlocksPerSM = 16;
 struct TaskGroup {
   const int2* tasks = nullptr;
   long long ntask = 0;
