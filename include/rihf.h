@@ -190,8 +190,11 @@ int rihf_query(rihf_ctx* ctx, int* N, int* Naux, int* nocc, int* natoms);
                           2-centre, nuclear-repulsion terms of Eq. rihf_gradient)
      RIHF_MAT_SCHWARZ: Q_ab = sqrt(max (mu nu|mu nu)) over the Cartesian
                           components of shells a >= b, packed a(a+1)/2 + b
-                          (nshell(nshell+1)/2 values; zeros when the screen
-                          is not evaluated)
+                          (nshell(nshell+1)/2 values, of the current
+                          geometry; zeros when the four-centre class does not
+                          fit the kernel's shared memory).  With schwarz_tau
+                          <= 0 no pair is screened and Q is computed only for
+                          this request
      RIHF_MAT_DSAD: N x N, the SAD guess density (after a guess-5 SCF built
                           it; RIHF_ERR_STATE before, or when SAD was unavailable)
      RIHF_MAT_DPRED: N x N, the predicted AO density of the last guess-3 or

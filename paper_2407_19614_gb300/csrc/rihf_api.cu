@@ -497,6 +497,7 @@ struct rihf_ctx {
   TaskGroup groups[kTaskGroups];
   double* d_schwarz = nullptr;
   bool schwarz_ok = false;
+  bool schwarz_fresh = false;   // d_schwarz holds Q of the current geometry
   double schwarz_max_dropped = 0.0;
 
   // geometry-dependent matrices
@@ -765,10 +766,14 @@ static void compute_geometry(rihf_ctx* c, bool defer_eri3 = false) {
   { TraceScope t(c->tracer, s, "cholesky A=LL^T", (double)NA * NA * NA / 3.0, 0);
     cholesky(la, c->L, NA, c->scratch); }
   c->have_linv = false;
-  // Schwarz screening (Sec. 3.1.1): keep shell pairs with max (mu nu|mu nu) > tau
-  if (c->schwarz_ok) {
+  // Schwarz screening (Sec. 3.1.1): keep shell pairs with max (mu nu|mu nu) > tau.
+  // With tau <= 0 no pair can drop out (every Q_ab > 0): the pair list stays
+  // complete, and the factors are computed only when rihf_get_matrix asks
+  c->schwarz_fresh = false;
+  if (c->schwarz_ok && c->opt.schwarz_tau > 0.0) {
     TraceScope t(c->tracer, s, "schwarz_kernel (ab|ab)", 0.0, 0);
     launch_schwarz(ic, P, c->max_lp, c->d_schwarz);
+    c->schwarz_fresh = true;
     std::vector<double> q(c->npairs_total);
     RIHF_CUDA(cudaMemcpyAsync(q.data(), c->d_schwarz, sizeof(double) * q.size(), cudaMemcpyDeviceToHost, s));
     RIHF_CUDA(cudaStreamSynchronize(s));
@@ -2668,8 +2673,16 @@ int rihf_get_matrix(rihf_ctx* c, int which, double* out) {
       RIHF_CUDA(cudaMemcpy(out, c->Dpred, n2 * 8, cudaMemcpyDeviceToHost));
       break;
     case RIHF_MAT_SCHWARZ:
-      if (c->schwarz_ok) RIHF_CUDA(cudaMemcpy(out, c->d_schwarz, sizeof(double) * c->npairs_total, cudaMemcpyDeviceToHost));
-      else std::memset(out, 0, sizeof(double) * c->npairs_total);
+      if (c->schwarz_ok) {
+        if (!c->schwarz_fresh) {   // tau <= 0: not needed for the screening, computed on request
+          launch_schwarz(c->ic(), c->prim(), c->max_lp, c->d_schwarz);
+          RIHF_CUDA(cudaStreamSynchronize(c->stream));
+          c->schwarz_fresh = true;
+        }
+        RIHF_CUDA(cudaMemcpy(out, c->d_schwarz, sizeof(double) * c->npairs_total, cudaMemcpyDeviceToHost));
+      } else {
+        std::memset(out, 0, sizeof(double) * c->npairs_total);
+      }
       break;
     case RIHF_MAT_GRAD_PARTS:
       if (c->grad_parts_h.empty()) return RIHF_ERR_STATE;
