@@ -29,6 +29,15 @@ __device__ inline double warp_sum(double v) {
   return v;
 }
 
+// 8-byte asynchronous global -> shared copies (cp.async), waited for by the
+// issuing thread; a group barrier then makes them visible to its other lanes.
+__device__ inline void cp_async8(double* smem_dst, const double* gsrc) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(gsrc) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Shared-memory plan of the derivative kernels.
 struct DerivPlan {
   int emin, emax, L;
@@ -337,6 +346,23 @@ __device__ inline void grad_eri3_task(const DevShells& prim, const DevShells& au
   double* vrr = smem + pl.vrr;
   double* etr = smem + pl.etr;
   int accsz = acc_size(pl.emin, pl.emax, lc);
+  // the task's block of Y (auxiliary function k, then the functions a of sa
+  // and b of sb; Y pair-packed per auxiliary function, symmetric) copied
+  // asynchronously into the slice's Y region, which the primitive loop leaves
+  // alone: the scattered loads overlap the recursion instead of stalling the
+  // back-transform (the block, spherical, never exceeds the Cartesian region)
+  const int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
+  double* ystage = smem + pl.ycart;
+  {
+    const double* Yc = Y + (long long)aux.ao[sc] * Npp;
+    const long long mu0 = prim.ao[sa], nu0 = prim.ao[sb];
+    for (int idx = lane; idx < nfa * nfb * nfc; idx += W) {
+      const int b = idx % nfb, r = idx / nfb, a = r % nfa, k = r / nfa;
+      const long long row = mu0 + a, col = nu0 + b;
+      cp_async8(ystage + idx, Yc + k * Npp + (row >= col ? row * (row + 1) / 2 + col : col * (col + 1) / 2 + row));
+    }
+    cp_async_commit();
+  }
   const PairPrim* pr = ptab.pp + ptab.off[ip];
   const bool one_mir = one && mir && pr[0].p > aux.exps[aux.pstart[sc]];
   const bool single = one && !one_mir && lc > 0;
@@ -383,14 +409,10 @@ __device__ inline void grad_eri3_task(const DevShells& prim, const DevShells& au
       }
     }
   }
-  // Y block -> Cartesian (Y pair-packed per auxiliary function, symmetric)
-  int nfa = prim.nf[la], nfb = prim.nf[lb], nfc = aux.nf[lc];
-  const double* Yc = Y + (long long)aux.ao[sc] * Npp;
-  const int mu0 = prim.ao[sa], nu0 = prim.ao[sb];
-  auto ysrc = [&](int k, int a, int b) -> double {
-    const long long r = mu0 + a, q = nu0 + b;
-    return r >= q ? Yc[k * Npp + r * (r + 1) / 2 + q] : Yc[k * Npp + q * (q + 1) / 2 + r];
-  };
+  // staged Y block -> Cartesian (its last pass overwrites the staged block)
+  cp_async_wait_all();
+  __syncwarp(lane_group_mask<W>());
+  const StridedSrc ysrc{ystage, (long long)nfa * nfb, nfb, 1};
   warp_back_transform<W>(ysrc, la, lb, lc, prim.tr + la * kTrStride * kTrStride,
                       prim.tr + lb * kTrStride * kTrStride, aux.tr + lc * kTrStride * kTrStride, nfa, nfb, nfc,
                       smem + pl.t1, smem + pl.t2, smem + pl.ycart, lane);

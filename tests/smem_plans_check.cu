@@ -2,7 +2,8 @@
 // (no device calls).  Built against the kernel sources themselves, so the plans
 // checked are the ones the kernels use:
 //  * every region live during the primitive loop (F_m, VRR table, transfer
-//    levels, accumulators) and every region live after it (transfer level or
+//    levels, accumulators, the Y block staged by asynchronous copies) and
+//    every region live after it (transfer level or
 //    accumulator read by the HRR, back-transformed Y, HRR and transform
 //    scratch) are pairwise disjoint and inside the plan, for every class
 //    (la <= 3, lb <= la, lc <= 4), with and without the mirrored recursion,
@@ -62,7 +63,8 @@ void check_plans() {
             std::vector<Region> loop = {{p.fm, p.fm + p.L + 1, "F_m"},
                                         {p.vrr, p.vrr + vrr_size(p.L), "VRR"},
                                         {p.etr, p.etr + etr_n, "transfer levels"},
-                                        {p.acc0, p.acc0 + accsz, "acc0"}};
+                                        {p.acc0, p.acc0 + accsz, "acc0"},
+                                        {p.ycart, p.ycart + nabc, "Y block (staged during the loop)"}};
             std::vector<Region> post = {{p.etr, p.etr + etr_n, "transfer levels"},
                                         {p.acc0, p.acc0 + accsz, "acc0"},
                                         {p.ycart, p.ycart + nabc, "Y (Cartesian)"},
