@@ -89,3 +89,23 @@ def test_enums_match_the_header():
     assert mats == R.MAT
     assert enum["RIHF_OK"] == 0 and enum["RIHF_ERR_STATE"] == -7
     assert enum["RIHF_PRECISION_FP64"] == 0 and enum["RIHF_PRECISION_MIXED"] == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2407_19614_gb300 import rihf as R
+    monkeypatch.setattr(R, "_lib", None)
+    with pytest.raises(RuntimeError, match="librihf.so not found"):
+        R.load(str(tmp_path / "librihf.so"))
+
+
+def test_no_cpu_fallback_without_a_device(libpath):
+    """Without a usable CUDA device the setup call returns a CUDA error: the
+    library has no CPU path to fall back to."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2407_19614_gb300 import rihf as R
+    from paper_2407_19614_gb300 import workloads as W
+    R.load(libpath)
+    with pytest.raises(R.RihfError, match="CUDA"):
+        R.Context(W.water_monomer(0))
