@@ -10,7 +10,8 @@
 //    and for derivative tasks of one primitive triple and of several;
 //  * the task lists of a synthetic shell set (mixed l and primitive counts)
 //    hold every (pair, auxiliary shell) task once, with the right mirror mark,
-//    in a group whose slices cover the task's plans, each shape contiguous.
+//    in a group whose slices cover the task's plans, each shape contiguous and
+//    the shapes heaviest first.
 // Prints "OK" and exits 0, or names the first violations and exits 1.
 #include "integrals.cu"
 #include "grad_integrals.cu"
@@ -136,6 +137,7 @@ void check_task_lists() {
   for (int g = 0; g < kTaskGroups; ++g) {
     std::set<std::array<int, 7>> done;   // shapes already closed in this group
     std::array<int, 7> cur{-1, -1, -1, -1, -1, -1, -1};
+    double last_cost = 1e300;   // shapes come heaviest first (primitive triples x derivative plan)
     for (const int2& t : tasks[g]) {
       ++n;
       const int p = t.x, c = t.y < 0 ? ~t.y : t.y, mi = t.y < 0 ? 1 : 0;
@@ -164,6 +166,9 @@ void check_task_lists() {
         if (cur[0] >= 0) done.insert(cur);
         if (done.count(shape) && g_fail++ < 20) printf("task lists: shape split in group %d\n", g);
         cur = shape;
+        const double cost = (double)nprim[a] * nprim[b] * naux_prim[c] * need_g;
+        if (cost > last_cost && g_fail++ < 20) printf("task lists: a lighter shape before a heavier one in group %d\n", g);
+        last_cost = cost;
       }
     }
   }
